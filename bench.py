@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Ray-volume steps per second of the MS-GWaM-3D hot path on GB300.
+
+Workload (one "step" = one full gwam_step: RK3 advance of every ray volume, exits, splitting,
+re-binning, cap, saturation, flux projection, smoothing, divergence, budget): the global
+lat-lon sphere 256 x 128 columns x 90 levels (1 km), two 60 m/s jets, isothermal 240 K
+atmosphere, the latitude-dependent background source at 5 km launching 8 azimuths x 4 phase
+speeds per column (983 040 ray volumes), dt = 180 s, FP64.  Synthetic inputs, seeded.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own replica of the
+workload on its own GPU (the replicas exchange nothing); value = all ranks' ray-volume steps
+divided by the slowest rank's time.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ray-volume steps/s"
+UNIT = "ray-volume steps/s"
+WORKLOAD = "sphere 256x128x90, background source 983040 ray volumes, dt 180 s, FP64"
+# Algorithmic FP64 operations per ray-volume step of the advance kernel (RK3: 3 evaluations of
+# the ray equations at the centre and 6 faces, incl. the trilinear gather of 4 fields with
+# gradients, plus exits and split decisions), counted from the formulas with every add, multiply,
+# divide, square root and trigonometric call as one operation.
+FLOPS_PER_RAY_STEP = 1460.0
+FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+HBM_PEAK = None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------- oracle arm
+
+def oracle_throughput(steps: int, warmup: int):
+    """FP64 CPU oracle on the same workload: launch (untimed), `warmup` untimed steps, then
+    `steps` timed steps; returns ray-volume steps/s and the timed sample."""
+    import oracle
+    from paper_2309_11257_gb300 import synth
+    w = synth.workload("sphere")
+    M = oracle.Model(w["grid"], w["params"])
+    M.set_background(*w["background"])
+    M.launch_background(w["source"])
+    for _ in range(warmup):
+        M.step(w["dt"])
+    ray_steps = 0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        ray_steps += M.n_rays
+        M.step(w["dt"])
+    dt = time.perf_counter() - t0
+    return ray_steps / dt, dict(steps=steps, warmup=warmup, ray_steps=ray_steps, seconds=dt)
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    steps = max(1, min(args.steps, 4))
+    warm = min(args.warmup, 1)
+    value, sample = oracle_throughput(steps, warm)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sample["seconds"] / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d timed oracle steps (after %d untimed) of the full workload, single thread"
+                                   % (steps, warm)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------- GPU arm
+
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2309_11257_gb300 import gwam, synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = synth.workload("sphere")
+    grid, params = w["grid"], w["params"]
+    nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
+    T = gwam.Tracer(grid, params, max_rays=2_500_000)
+    bg_dev = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in w["background"]]
+    T.set_background(*bg_dev)
+    T.launch_sources(w["source"])
+    du = torch.zeros((nz, ny, nx), dtype=torch.float64, device=dev)
+    dv = torch.zeros_like(du)
+    for _ in range(args.warmup):
+        T.step(w["dt"], du, dv)
+    T.profile(True)
+    s0 = T.stats()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        T.step(w["dt"], du, dv)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    s1 = T.stats()
+    phases, nprof = T.profile_read()
+    T.profile(False)
+    ray_steps = s1["ray_steps"] - s0["ray_steps"]
+    tot_rs = ray_steps
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        r = torch.tensor([float(ray_steps)], dtype=torch.float64, device=dev)
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+        tot_rs = float(r.item())
+    value = tot_rs / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel (advance: FP64-pipe bound)
+    adv_ms = phases["advance"] / max(nprof, 1)
+    rays_per_launch = ray_steps / args.steps
+    achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)",
+                "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
+
+    # end to end through the public API with host buffers: each step uploads that step's
+    # background from pinned host memory and reads du/dt, dv/dt back into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        bg_host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in w["background"]]
+        du_h = torch.zeros((nz, ny, nx), dtype=torch.float64).pin_memory().numpy()
+        dv_h = torch.zeros((nz, ny, nx), dtype=torch.float64).pin_memory().numpy()
+        ke = max(1, min(args.steps, 10))
+        T.set_background(*bg_host)
+        T.step_host(w["dt"], du_h, dv_h)
+        a0 = T.stats()["ray_steps"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            T.set_background(*bg_host)
+            T.step_host(w["dt"], du_h, dv_h)
+        t1 = time.perf_counter()
+        rs = T.stats()["ray_steps"] - a0
+        e2e_val = rs / (t1 - t0)
+        if world > 1:
+            r = torch.tensor([e2e_val], dtype=torch.float64, device=dev)
+            dist.all_reduce(r, op=dist.ReduceOp.SUM)
+            e2e_val = float(r.item())
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * nz * ny * nx,
+               "d2h_bytes_per_step": 2 * 8 * nz * ny * nx, "steps": ke}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cval, sample = oracle_throughput(2, 0)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "2 oracle steps right after the launch of the full workload (%d ray-volume steps, "
+                         "%.1f s), single thread" % (sample["ray_steps"], sample["seconds"])}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rays_live_start": s0["n_live"], "rays_live_end": s1["n_live"],
+                       "ray_steps_timed": ray_steps, "l2": "working set > L2 (ray state ~0.12-0.24 GB + "
+                       "grid fields ~0.4 GB per step), no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "gpu_launches": None,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+        }
+        line["gpu_launches"] = args.steps * launches_per_step(params)
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def launches_per_step(params) -> int:
+    """Kernels of the library per gwam_step (memsets excluded)."""
+    # begin, advance, 2 scans (3 kernels each), scatter, segsort x2, set_nnew, materialize, project,
+    # divergence, finalize
+    n = 1 + 1 + 3 + 3 + 1 + 2 + 1 + 1 + 1 + 1 + 1
+    if params.get("cap_per_column", 0) > 0:
+        n += 2 + 3                                   # cap find/apply + scan
+    if params.get("saturation", 0):
+        n += 1
+    if params.get("smoothing", 0):
+        n += 9
+    return n
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    rc = gpu_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,510 @@
+// gwam_api.cu -- the extern "C" entry points declared in include/gwam.h.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "gwam_common.cuh"
+
+struct gwam_ctx {
+    gwam::Context c;
+};
+
+namespace gwam {
+
+#define GWAM_CUDA(call)                                                                                \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            c.err = std::string(#call) + ": " + cudaGetErrorString(e_);                                \
+            throw (int)(e_ == cudaErrorMemoryAllocation ? GWAM_ENOMEM : GWAM_ECUDA);                  \
+        }                                                                                              \
+    } while (0)
+
+template <typename T>
+static void dalloc(Context& c, T*& p, size_t count)
+{
+    GWAM_CUDA(cudaMalloc((void**)&p, sizeof(T) * std::max<size_t>(count, 1)));
+}
+
+static void free_all(Context& c)
+{
+    void* ptrs[] = {c.bg, c.rho, c.bg_scratch, c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
+                    c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.ecap, c.cnt, c.off, c.off2,
+                    c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
+                    c.flag_dev};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int f = 0; f < NFIELD; ++f) {
+        if (c.field[f]) cudaFree(c.field[f]);
+        if (c.smooth[f]) cudaFree(c.smooth[f]);
+    }
+    for (int q = 0; q < Context::kRing; ++q)
+        for (int p = 0; p <= Context::kPhases; ++p)
+            if (c.prof_ev[q][p]) cudaEventDestroy(c.prof_ev[q][p]);
+    if (c.ctl_host) cudaFreeHost(c.ctl_host);
+    if (c.budget_host) cudaFreeHost(c.budget_host);
+    if (c.flag_host) cudaFreeHost(c.flag_host);
+}
+
+static void check_pending(Context& c)
+{
+    GWAM_CUDA(cudaMemcpyAsync(c.ctl_host, c.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaMemcpyAsync(c.budget_host, c.budget, sizeof(DevBudget), cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
+    if (c.ctl_host->status != 0) {
+        const int st = c.ctl_host->status;
+        c.err = st == GWAM_ECAPACITY ? "device: ray capacity (max_rays) exceeded" : "device: status set";
+        throw st;
+    }
+}
+
+// Same-extent host/device copy helpers
+static void h2d(Context& c, void* dst, const void* src, size_t bytes)
+{
+    GWAM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.stream));
+}
+
+}  // namespace gwam
+
+using namespace gwam;
+
+#define API_BEGIN(ctx)                                                                                 \
+    if (!(ctx)) return GWAM_EINVAL;                                                                    \
+    Context& c = (ctx)->c;                                                                             \
+    try {
+#define API_END                                                                                        \
+    }                                                                                                  \
+    catch (int code) { return code; }                                                                  \
+    catch (std::bad_alloc&) { c.err = "host allocation failed"; return GWAM_ENOMEM; }                  \
+    return GWAM_OK;
+
+extern "C" {
+
+const char* gwam_version(void) { return "gwam-gb300 0.1 (sm_103a, FP64 form)"; }
+
+int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, void* stream)
+{
+    if (!out || !grid || !params) return GWAM_EINVAL;
+    *out = nullptr;
+    if (grid->geometry != 0 && grid->geometry != 1) return GWAM_EINVAL;
+    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2 || !(grid->dz > 0.0)) return GWAM_EINVAL;
+    if (grid->geometry == 0 && !(grid->dx > 0.0 && grid->dy > 0.0)) return GWAM_EINVAL;
+    if (grid->geometry == 1 && !(grid->radius > 0.0)) return GWAM_EINVAL;
+    if (!(grid->g > 0.0)) return GWAM_EINVAL;
+    if ((int64_t)grid->nx * grid->ny * (grid->nz + 1) >= (int64_t)1 << 31) return GWAM_EINVAL;
+    if (grid->nz > 192) return GWAM_EINVAL;   // column tiles of the transposing kernels live in shared memory
+    if (params->precision != 0) return GWAM_EINVAL;
+    if (params->max_rays < 1 || params->max_rays >= ((int64_t)1 << 29)) return GWAM_EINVAL;
+    if (!(params->alpha_s > 0.0) || !(params->min_split_dz >= 0.0)) return GWAM_EINVAL;
+    if (params->flux_form != 0 && params->flux_form != 1) return GWAM_EINVAL;
+    gwam_ctx* h = new (std::nothrow) gwam_ctx();
+    if (!h) return GWAM_ENOMEM;
+    Context& c = h->c;
+    try {
+        GWAM_CUDA(cudaGetDevice(&c.device));
+        GWAM_CUDA(cudaDeviceGetAttribute(&c.num_sms, cudaDevAttrMultiProcessorCount, c.device));
+        c.stream = (cudaStream_t)stream;
+        Grid& G = c.G;
+        G.geometry = grid->geometry;
+        G.nx = grid->nx;
+        G.ny = grid->ny;
+        G.nz = grid->nz;
+        G.ncol = grid->nx * grid->ny;
+        G.ncell = G.ncol * grid->nz;
+        G.dz = grid->dz;
+        G.f0 = grid->f0;
+        G.radius = grid->radius;
+        G.omega = grid->omega;
+        G.g = grid->g;
+        G.ztop = grid->nz * grid->dz;
+        if (G.geometry == 1) {
+            G.dX = 2.0 * kPi / grid->nx;
+            G.dY = kPi / grid->ny;
+            G.y0 = -0.5 * kPi;
+            G.Lx = 2.0 * kPi;
+            G.Ly = kPi;
+        } else {
+            G.dX = grid->dx;
+            G.dY = grid->dy;
+            G.y0 = 0.0;
+            G.Lx = grid->nx * grid->dx;
+            G.Ly = grid->ny * grid->dy;
+        }
+        G.phimax = 0.5 * kPi - 0.5 * G.dY;
+        Params& P = c.P;
+        P.gamma_mode = params->gamma_mode;
+        P.saturation = params->saturation;
+        P.smoothing = params->smoothing;
+        P.flux_form = params->flux_form;
+        P.splitting = params->splitting;
+        P.cap = params->cap_per_column;
+        P.alpha_s = params->alpha_s;
+        P.min_split_dz = params->min_split_dz;
+        c.max_rays = params->max_rays;
+        // persistent grid: resident blocks of the heaviest ray kernel, a multiple of the SM count
+        c.grid_blocks = c.num_sms * 4;
+
+        const size_t nr = (size_t)c.max_rays;
+        const size_t ncell = (size_t)G.ncell;
+        dalloc(c, c.bg, ncell);
+        dalloc(c, c.rho, ncell);
+        for (int b = 0; b < 2; ++b) {
+            dalloc(c, c.ray_mem[b], 7 * nr);
+            RaySoA& R = b == 0 ? c.A : c.B;
+            for (int q = 0; q < 7; ++q) R.a[q] = c.ray_mem[b] + q * nr;
+        }
+        dalloc(c, c.info, nr);
+        dalloc(c, c.ccell, nr);
+        dalloc(c, c.cslot, nr);
+        dalloc(c, c.newid, nr + 1);
+        dalloc(c, c.ent_id, nr);
+        dalloc(c, c.ent_src, nr);
+        dalloc(c, c.sorted_src, nr);
+        dalloc(c, c.pj, nr);
+        dalloc(c, c.k2, nr);
+        dalloc(c, c.kappa, nr);
+        dalloc(c, c.ecap, nr);
+        dalloc(c, c.cnt, ncell + 1);
+        dalloc(c, c.off, ncell + 1);
+        dalloc(c, c.off2, ncell + 1);
+        dalloc(c, c.overlist, (size_t)G.ncol);
+        dalloc(c, c.biglist, ncell);
+        const size_t scan_blocks = (std::max(nr, ncell) + 2047) / 2048 + 2;
+        dalloc(c, c.scan_tmp, scan_blocks + 1);
+        c.scan_tmp_cap = (int64_t)scan_blocks + 1;
+        for (int f = 0; f < NFIELD; ++f) {
+            dalloc(c, c.field[f], (size_t)c.field_len(f));
+            dalloc(c, c.smooth[f], (size_t)c.field_len(f));
+            GWAM_CUDA(cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), c.stream));
+            GWAM_CUDA(cudaMemsetAsync(c.smooth[f], 0, sizeof(double) * (size_t)c.field_len(f), c.stream));
+        }
+        dalloc(c, c.dudt_buf, ncell);
+        dalloc(c, c.dvdt_buf, ncell);
+        dalloc(c, c.ctl, 1);
+        dalloc(c, c.budget, 1);
+        dalloc(c, c.partials, (size_t)NTALLY * c.grid_blocks);
+        dalloc(c, c.flag_dev, 1);
+        GWAM_CUDA(cudaMallocHost((void**)&c.ctl_host, sizeof(Ctl)));
+        GWAM_CUDA(cudaMallocHost((void**)&c.budget_host, sizeof(DevBudget)));
+        GWAM_CUDA(cudaMallocHost((void**)&c.flag_host, sizeof(int)));
+        GWAM_CUDA(cudaMemsetAsync(c.ctl, 0, sizeof(Ctl), c.stream));
+        GWAM_CUDA(cudaMemsetAsync(c.budget, 0, sizeof(DevBudget), c.stream));
+        GWAM_CUDA(cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * c.grid_blocks, c.stream));
+        configure_kernels();
+        GWAM_CUDA(cudaStreamSynchronize(c.stream));
+        GWAM_CUDA(cudaGetLastError());
+    } catch (int code) {
+        free_all(c);
+        delete h;
+        return code;
+    }
+    *out = h;
+    return GWAM_OK;
+}
+
+void gwam_destroy(gwam_ctx* ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->c.stream);
+    free_all(ctx->c);
+    delete ctx;
+}
+
+static int set_background_impl(gwam_ctx* ctx, const double* u, const double* v, const double* n2, const double* rho,
+                               bool host)
+{
+    API_BEGIN(ctx)
+    if (!u || !v || !n2 || !rho) return GWAM_EINVAL;
+    const size_t nc = (size_t)c.G.ncell;
+    const double* src[4] = {u, v, n2, rho};
+    if (host) {
+        if (!c.bg_scratch) dalloc(c, c.bg_scratch, 4 * nc);
+        for (int q = 0; q < 4; ++q) h2d(c, c.bg_scratch + q * nc, src[q], sizeof(double) * nc);
+        for (int q = 0; q < 4; ++q) src[q] = c.bg_scratch + q * nc;
+    }
+    GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
+    launch_set_background(c, src[0], src[1], src[2], src[3]);
+    GWAM_CUDA(cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
+    if (*c.flag_host) {
+        c.err = "gwam_set_background: non-finite value, rho <= 0 or N^2 <= f^2";
+        c.have_bg = false;
+        return GWAM_ENUMERIC;
+    }
+    c.have_bg = true;
+    API_END
+}
+
+int gwam_set_background(gwam_ctx* ctx, const double* u, const double* v, const double* n2, const double* rho)
+{
+    return set_background_impl(ctx, u, v, n2, rho, false);
+}
+
+int gwam_set_background_host(gwam_ctx* ctx, const double* u, const double* v, const double* n2, const double* rho)
+{
+    return set_background_impl(ctx, u, v, n2, rho, true);
+}
+
+static int add_rays_impl(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n, bool host)
+{
+    API_BEGIN(ctx)
+    if (!r || n < 0) return GWAM_EINVAL;
+    if (n == 0) return GWAM_OK;
+    if (n > c.max_rays) return GWAM_ECAPACITY;
+    const double* in[13] = {r->x, r->y, r->z, r->k, r->l, r->m, r->ex, r->ey, r->ez, r->dk, r->dl, r->dm, r->n};
+    for (int q = 0; q < 13; ++q)
+        if (!in[q]) return GWAM_EINVAL;
+    double* tmp = nullptr;
+    if (host) {
+        GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * 13 * (size_t)n));
+        for (int q = 0; q < 13; ++q) {
+            h2d(c, tmp + q * n, in[q], sizeof(double) * (size_t)n);
+            in[q] = tmp + q * n;
+        }
+    }
+    int rc = GWAM_OK;
+    try {
+        launch_add_rays(c, in, n);
+        check_pending(c);
+    } catch (int code) {
+        rc = code;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(c.stream);
+        cudaFree(tmp);
+    }
+    if (rc) return rc;
+    API_END
+}
+
+int gwam_add_rays(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n) { return add_rays_impl(ctx, r, n, false); }
+int gwam_add_rays_host(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n) { return add_rays_impl(ctx, r, n, true); }
+
+int gwam_launch_sources(gwam_ctx* ctx, const gwam_bg_source* src)
+{
+    API_BEGIN(ctx)
+    if (!src) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_launch_sources: no background";
+        return GWAM_ESTATE;
+    }
+    if (c.G.geometry != 1 || src->n_az < 1 || src->n_c < 1 || src->n_az * src->n_c > 1024) return GWAM_EINVAL;
+    if (!(src->lambda_h > 0.0) || !(src->dz_launch > 0.0) || !(src->c_min > 0.0) || !(src->c_max > 0.0))
+        return GWAM_EINVAL;
+    launch_background_source(c, *src);
+    GWAM_CUDA(cudaGetLastError());
+    API_END
+}
+
+static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n, bool host)
+{
+    API_BEGIN(ctx)
+    if (n < 0 || (n > 0 && !specs)) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_launch_spectral: no background";
+        return GWAM_ESTATE;
+    }
+    if (n == 0) return GWAM_OK;
+    if (n >= ((int64_t)1 << 30)) return GWAM_EINVAL;
+    const gwam_spec* d = specs;
+    gwam_spec* tmp = nullptr;
+    if (host) {
+        for (int64_t q = 0; q < n; ++q) {
+            const gwam_spec& s = specs[q];
+            if (s.i < 0 || s.i >= c.G.nx || s.j < 0 || s.j >= c.G.ny || !(s.lambda_h > 0.0) || !(s.dz_launch > 0.0))
+                return GWAM_EINVAL;
+        }
+        GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(gwam_spec) * (size_t)n));
+        h2d(c, tmp, specs, sizeof(gwam_spec) * (size_t)n);
+        d = tmp;
+    }
+    int rc = GWAM_OK;
+    try {
+        launch_spectral(c, d, n);
+        GWAM_CUDA(cudaGetLastError());
+    } catch (int code) {
+        rc = code;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(c.stream);
+        cudaFree(tmp);
+    }
+    if (rc) return rc;
+    API_END
+}
+
+int gwam_launch_spectral(gwam_ctx* ctx, const gwam_spec* specs, int64_t n)
+{
+    return launch_spectral_impl(ctx, specs, n, false);
+}
+
+int gwam_launch_spectral_host(gwam_ctx* ctx, const gwam_spec* specs, int64_t n)
+{
+    return launch_spectral_impl(ctx, specs, n, true);
+}
+
+int gwam_step(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
+{
+    API_BEGIN(ctx)
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_step: no background";
+        return GWAM_ESTATE;
+    }
+    run_step(c, dt, dudt, dvdt);
+    GWAM_CUDA(cudaGetLastError());
+    API_END
+}
+
+int gwam_step_host(gwam_ctx* ctx, double dt, double* dudt_host, double* dvdt_host)
+{
+    API_BEGIN(ctx)
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_step_host: no background";
+        return GWAM_ESTATE;
+    }
+    run_step(c, dt, nullptr, nullptr);
+    const size_t bytes = sizeof(double) * (size_t)c.G.ncell;
+    if (dudt_host) GWAM_CUDA(cudaMemcpyAsync(dudt_host, c.dudt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
+    if (dvdt_host) GWAM_CUDA(cudaMemcpyAsync(dvdt_host, c.dvdt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
+    API_END
+}
+
+int gwam_num_rays(gwam_ctx* ctx, int64_t* n)
+{
+    API_BEGIN(ctx)
+    if (!n) return GWAM_EINVAL;
+    check_pending(c);
+    *n = c.ctl_host->n;
+    API_END
+}
+
+int gwam_get_rays_host(gwam_ctx* ctx, double* state13, int64_t* ids, int32_t* cells, int64_t cap)
+{
+    API_BEGIN(ctx)
+    check_pending(c);
+    const int64_t n = c.ctl_host->n;
+    if (cap < n) return GWAM_ECAPACITY;
+    if (n == 0) return GWAM_OK;
+    double* tmp = nullptr;
+    long long* tid = nullptr;
+    int* tcell = nullptr;
+    GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * 13 * (size_t)n));
+    GWAM_CUDA(cudaMalloc((void**)&tid, sizeof(long long) * (size_t)n));
+    GWAM_CUDA(cudaMalloc((void**)&tcell, sizeof(int) * (size_t)n));
+    launch_gather_rays(c, tmp, tid, tcell, n);
+    for (int q = 0; q < 13 && state13; ++q)
+        GWAM_CUDA(cudaMemcpyAsync(state13 + q * cap, tmp + q * n, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                                  c.stream));
+    if (ids) GWAM_CUDA(cudaMemcpyAsync(ids, tid, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, c.stream));
+    if (cells) GWAM_CUDA(cudaMemcpyAsync(cells, tcell, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    cudaFree(tmp);
+    cudaFree(tid);
+    cudaFree(tcell);
+    API_END
+}
+
+int gwam_get_stats(gwam_ctx* ctx, gwam_stats* out)
+{
+    API_BEGIN(ctx)
+    if (!out) return GWAM_EINVAL;
+    check_pending(c);
+    const Ctl& t = *c.ctl_host;
+    const DevBudget& b = *c.budget_host;
+    out->n_live = t.n;
+    out->n_launched = t.n_launched;
+    out->n_filtered = t.n_filtered;
+    out->n_split_v = t.n_split_v;
+    out->n_split_h = t.n_split_h;
+    out->n_exited = t.n_exited;
+    out->n_capped = t.n_capped;
+    out->n_merged = 0;
+    out->n_invalid = t.n_invalid;
+    out->n_steps = t.n_steps;
+    out->ray_steps = t.ray_steps;
+    out->w_total = b.w_total;
+    out->w_launched = b.w_launched;
+    out->w_saturated = b.w_saturated;
+    out->w_exited = b.w_exited;
+    out->w_capped = b.w_capped;
+    out->w_invalid = b.w_invalid;
+    API_END
+}
+
+int gwam_get_field_host(gwam_ctx* ctx, int which, double* out_host)
+{
+    API_BEGIN(ctx)
+    if (which < 0 || which >= NFIELD || !out_host) return GWAM_EINVAL;
+    const double* src = c.P.smoothing ? c.smooth[which] : c.field[which];
+    const int nlev = which <= F_ZP ? c.G.nz + 1 : c.G.nz;
+    double* tmp = nullptr;
+    GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * (size_t)c.field_len(which)));
+    launch_field_to_caller(c, src, tmp, nlev);
+    GWAM_CUDA(cudaMemcpyAsync(out_host, tmp, sizeof(double) * (size_t)c.field_len(which), cudaMemcpyDeviceToHost,
+                              c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    cudaFree(tmp);
+    API_END
+}
+
+int gwam_get_gamma2_host(gwam_ctx* ctx, double* out_host)
+{
+    API_BEGIN(ctx)
+    if (!out_host) return GWAM_EINVAL;
+    double* tmp = nullptr;
+    GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * (size_t)c.G.ncell));
+    launch_gamma_to_caller(c, tmp);
+    GWAM_CUDA(cudaMemcpyAsync(out_host, tmp, sizeof(double) * (size_t)c.G.ncell, cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    cudaFree(tmp);
+    API_END
+}
+
+int gwam_synchronize(gwam_ctx* ctx)
+{
+    API_BEGIN(ctx)
+    check_pending(c);
+    API_END
+}
+
+int gwam_profile_enable(gwam_ctx* ctx, int enable)
+{
+    API_BEGIN(ctx)
+    if (enable && !c.prof_ev[0][0]) {
+        for (int q = 0; q < Context::kRing; ++q)
+            for (int p = 0; p <= Context::kPhases; ++p) GWAM_CUDA(cudaEventCreate(&c.prof_ev[q][p]));
+    }
+    if (c.prof) prof_harvest(c);
+    c.prof = enable != 0;
+    c.prof_pending = 0;
+    c.prof_steps = 0;
+    for (int p = 0; p < Context::kPhases; ++p) c.prof_ms[p] = 0.0;
+    API_END
+}
+
+int gwam_profile_read(gwam_ctx* ctx, double* ms_host, int64_t* steps)
+{
+    API_BEGIN(ctx)
+    if (!ms_host || !steps) return GWAM_EINVAL;
+    prof_harvest(c);
+    for (int p = 0; p < Context::kPhases; ++p) ms_host[p] = c.prof_ms[p];
+    *steps = c.prof_steps;
+    API_END
+}
+
+const char* gwam_last_error(const gwam_ctx* ctx)
+{
+    if (!ctx) return "null context";
+    return ctx->c.err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// gwam_ctx.cuh -- the context behind the C ABI: device buffers and kernel entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+
+#include "../../include/gwam.h"
+#include "gwam_device.cuh"
+
+namespace gwam {
+
+// Device control block: counts the host never needs to read inside a step.
+struct Ctl {
+    int n;               // live ray volumes (array A)
+    int n_new;           // ray volumes after this step's re-binning
+    int n_children;      // children produced this step (before the cap)
+    int n_over;          // columns above the cap this step
+    int n_big;           // cells too large for the per-thread segment sort
+    int status;          // sticky device status (gwam_status values)
+    long long next_id;   // next unused ray id
+    long long new_ids;   // ids issued this step
+    // cumulative counters
+    long long n_launched, n_filtered, n_split_v, n_split_h, n_exited, n_capped, n_invalid, n_steps, ray_steps;
+};
+
+// FP64 tallies are reduced deterministically: every kernel that produces one writes one
+// partial per block (fixed grid) into its slot; a single-block kernel folds them in order.
+enum TallySlot { T_EXIT, T_INVALID, T_CAP, T_SAT, T_LAUNCH, T_TOTAL, NTALLY };
+
+struct DevBudget {
+    double w_total, w_launched, w_saturated, w_exited, w_capped, w_invalid;
+};
+
+enum FieldId { F_ZL, F_ZP, F_LL, F_LP, F_PL, F_PP, F_EL, F_EP, F_WAD, NFIELD };
+
+struct Context {
+    int device = 0;
+    int num_sms = 0;
+    int grid_blocks = 0;            // persistent grid for ray kernels
+    cudaStream_t stream = nullptr;
+    Grid G{};
+    Params P{};
+    int64_t max_rays = 0;
+    bool have_bg = false;
+    std::string err;
+
+    // background (column-major)
+    Node* bg = nullptr;          // U V N2 G2 per node
+    double* rho = nullptr;          // rho per node
+    double* bg_scratch = nullptr;   // staging of caller fields ([nz][ny][nx], 4 fields)
+
+    // ray volumes: A holds the canonical array between steps, B is the re-binned output
+    RaySoA A{}, B{};
+    double2* ray_mem[2] = {nullptr, nullptr};
+
+    // per-ray scratch
+    int* info = nullptr;            // split code | children << 4 | status << 8
+    int4* ccell = nullptr;          // child cells (-1 = left the domain)
+    int4* cslot = nullptr;          // child slot inside its cell
+    int* newid = nullptr;           // ids needed per ray -> exclusive prefix
+    long long* ent_id = nullptr;    // entry id (in cell-offset order)
+    int* ent_src = nullptr;         // entry source: parent * 4 + child, < 0 removed by the cap
+    int* sorted_src = nullptr;      // entry source in canonical order
+    double* pj = nullptr;           // saturation: P_j (incl. alpha_j)
+    double* k2 = nullptr;           // saturation: K_j^2
+    double* kappa = nullptr;        // saturation: kappa of the carrier cell, per ray
+    double* ecap = nullptr;         // cap: energies of the entries of over-full columns
+
+    // per-cell scratch
+    int* cnt = nullptr;             // entries per cell (then live entries per cell)
+    int* off = nullptr;             // exclusive prefix of cnt (ncell + 1)
+    int* off2 = nullptr;            // exclusive prefix after the cap (ncell + 1)
+    int* overlist = nullptr;        // columns above the cap
+    int* biglist = nullptr;         // cells with long segments
+    int* scan_tmp = nullptr;        // block sums of the scans
+    int64_t scan_tmp_cap = 0;
+
+    // grid fields (column-major; interface fields [col][nz+1])
+    double* field[NFIELD] = {};
+    double* smooth[NFIELD] = {};
+    double* dudt_buf = nullptr;     // [nz][ny][nx]
+    double* dvdt_buf = nullptr;
+
+    // control, tallies
+    Ctl* ctl = nullptr;
+    DevBudget* budget = nullptr;
+    double* partials = nullptr;     // NTALLY * grid_blocks
+    Ctl* ctl_host = nullptr;        // pinned mirror
+    DevBudget* budget_host = nullptr;
+    int* flag_dev = nullptr;        // validation flags
+    int* flag_host = nullptr;
+
+    // per-phase timing: a ring of event sets, harvested on read (or when the ring is full)
+    static constexpr int kPhases = 5;
+    static constexpr int kRing = 128;
+    bool prof = false;
+    cudaEvent_t prof_ev[kRing][kPhases + 1] = {};
+    int prof_pending = 0;
+    int64_t prof_steps = 0;
+    double prof_ms[kPhases] = {};
+
+    int64_t field_len(int f) const { return (int64_t)G.ncol * (f <= F_ZP ? G.nz + 1 : G.nz); }
+};
+
+// kernels, launched from the host side (gwam_step.cu / gwam_launch.cu)
+void launch_set_background(Context& c, const double* u, const double* v, const double* n2, const double* rho);
+void launch_add_rays(Context& c, const double* const in[13], int64_t n);
+void launch_background_source(Context& c, const gwam_bg_source& src);
+void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
+void run_step(Context& c, double dt, double* du, double* dv);
+void configure_kernels();
+void prof_mark(Context& c, int phase);
+void prof_harvest(Context& c);
+void launch_gather_rays(Context& c, double* state13, long long* ids, int* cells, int64_t cap);
+void launch_field_to_caller(Context& c, const double* src, double* dst, int nlev);
+void launch_gamma_to_caller(Context& c, double* dst);
+void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n_dev);
+void finalize_tallies(Context& c, int slot_mask, int mode);
+
+}  // namespace gwam

@@ -1,0 +1,449 @@
+// gwam_device.cuh -- device-side data layout and per-ray-volume arithmetic (FP64 form).
+//
+// Ray equations of Voelker et al. (arXiv:2309.11257):
+//   dispersion relation with scale-height correction ........ Sec. 2a, Eq. dispersion
+//   c_g = grad_k Omega, rdot = c_g ........................... Eq. eikonal, Eq. group-velocity
+//   wavenumber tendencies with spherical metric terms ......... Eq. eikonal-sphere:1-3
+//   face group velocities from first-order Taylor values ...... Sec. 3b, App. B.1
+//   per-axis phase-space products P = h dX dk ................. Sec. 3a, Eq. vpvol_cons_cart, Eq. dkxdkl
+//   low-storage RK3 (Williamson 1980) ......................... App. B.2
+//   splitting thresholds ...................................... App. B.3
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gwam {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------- layouts
+
+// Grid geometry as the kernels see it (derived once on the host).
+struct Grid {
+    int geometry;          // 0 f-plane, 1 sphere
+    int nx, ny, nz;
+    int ncol, ncell;       // nx*ny, nx*ny*nz
+    double dX, dY, dz;     // coordinate spacings (radians on the sphere)
+    double y0;             // southern edge (-pi/2) or 0
+    double Lx, Ly;         // periods in x (2 pi or nx dx) and y (f-plane)
+    double ztop;
+    double f0, radius, omega, g;
+    double phimax;         // carriers poleward of this latitude leave (centre of the last row)
+};
+
+struct Params {
+    int gamma_mode, saturation, smoothing, flux_form, splitting, cap;
+    double alpha_s, min_split_dz;
+};
+
+// Ray-volume state, structure of arrays of double2 (16-byte vector loads):
+//   a[0] = (x, y)  a[1] = (z, k)  a[2] = (l, m)  a[3] = (ex, ey)
+//   a[4] = (ez, Px)  a[5] = (Py, Pz)  a[6] = (N, id as int64 bits)
+struct RaySoA {
+    double2* a[7];
+};
+
+enum { SX, SY, SZ, SK, SL, SM, SEX, SEY, SEZ, SPX, SPY, SPZ, SN, NSTATE };
+
+__device__ __forceinline__ void load_ray(const RaySoA& R, int64_t i, double s[NSTATE], long long& id)
+{
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        double2 v = __ldg(&R.a[q][i]);
+        s[2 * q] = v.x;
+        s[2 * q + 1] = v.y;
+    }
+    double2 v = __ldg(&R.a[6][i]);
+    s[SN] = v.x;
+    id = __double_as_longlong(v.y);
+}
+
+__device__ __forceinline__ void store_ray(const RaySoA& R, int64_t i, const double s[NSTATE], long long id)
+{
+#pragma unroll
+    for (int q = 0; q < 6; ++q) R.a[q][i] = make_double2(s[2 * q], s[2 * q + 1]);
+    R.a[6][i] = make_double2(s[SN], __longlong_as_double(id));
+}
+
+// Background nodes at cell centres, column-major: node (i, j, k) at (j*nx + i)*nz + k,
+// each node 32 bytes (U, V, N^2, Gamma^2).
+struct __align__(32) Node {
+    double x, y, z, w;   // U, V, N^2, Gamma^2
+};
+__host__ __device__ __forceinline__ int64_t node_index(const Grid& G, int i, int j, int k)
+{
+    return ((int64_t)j * G.nx + i) * G.nz + k;
+}
+
+// ---------------------------------------------------------------------------- background gather
+
+struct Bg {
+    double v[4];     // U V N2 G2
+    double d[4][3];  // coordinate derivatives of each
+};
+
+__device__ __forceinline__ int wrap_int(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// periodic bracketing node pair; s in node units
+__device__ __forceinline__ void bracket_periodic(double s, int n, int& q0, int& q1, double& t)
+{
+    if (!isfinite(s)) s = 0.0;
+    s = s - (double)n * floor(s / (double)n);
+    double fl = floor(s);
+    t = s - fl;
+    q0 = wrap_int((int)fl, n);
+    q1 = q0 + 1 == n ? 0 : q0 + 1;
+}
+
+// clamped bracketing: constant value, zero gradient outside the first/last node
+__device__ __forceinline__ void bracket_clamped(double s, int n, int& q0, int& q1, double& t, double& on)
+{
+    if (!isfinite(s)) s = 0.0;
+    if (s < 0.0) {
+        q0 = 0; q1 = 1; t = 0.0; on = 0.0;
+    } else if (s >= (double)(n - 1)) {
+        q0 = n - 2; q1 = n - 1; t = 1.0; on = 0.0;
+    } else {
+        double fl = floor(s);
+        q0 = (int)fl; q1 = q0 + 1; t = s - fl; on = 1.0;
+    }
+}
+
+__device__ __forceinline__ Node ldg4(const Node* __restrict__ p)
+{
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    return Node{a.x, a.y, b.x, b.y};
+}
+
+// Trilinear interpolation of the node fields and of their gradients (exact derivative of the
+// interpolant) to (X, Y, Z) -- the linear interpolation of Sec. 3b / App. B.1.
+__device__ __forceinline__ void gather(const Grid& G, const Node* __restrict__ bg, double X, double Y, double Z,
+                                       Bg& b)
+{
+    int i0, i1, j0, j1, k0, k1;
+    double tx, ty, tz, gy, gz;
+    bracket_periodic(X / G.dX - 0.5, G.nx, i0, i1, tx);
+    if (G.geometry == 1) {
+        bracket_clamped((Y - G.y0) / G.dY - 0.5, G.ny, j0, j1, ty, gy);
+    } else {
+        bracket_periodic(Y / G.dY - 0.5, G.ny, j0, j1, ty);
+        gy = 1.0;
+    }
+    bracket_clamped(Z / G.dz - 0.5, G.nz, k0, k1, tz, gz);
+    const Node* c00 = bg + node_index(G, i0, j0, k0);
+    const Node* c10 = bg + node_index(G, i1, j0, k0);
+    const Node* c01 = bg + node_index(G, i0, j1, k0);
+    const Node* c11 = bg + node_index(G, i1, j1, k0);
+    const int dk = k1 - k0;
+    const Node a000 = ldg4(c00), a001 = ldg4(c00 + dk);
+    const Node a100 = ldg4(c10), a101 = ldg4(c10 + dk);
+    const Node a010 = ldg4(c01), a011 = ldg4(c01 + dk);
+    const Node a110 = ldg4(c11), a111 = ldg4(c11 + dk);
+    const double ux = 1.0 - tx, uy = 1.0 - ty, uz = 1.0 - tz;
+    const double sx = 1.0 / G.dX, sy = gy / G.dY, sz = gz / G.dz;
+    double c[8];
+#define GWAM_FIELD(F, f)                                                                                    \
+    c[0] = a000.F; c[1] = a001.F; c[2] = a010.F; c[3] = a011.F;                                           \
+    c[4] = a100.F; c[5] = a101.F; c[6] = a110.F; c[7] = a111.F;                                           \
+    {                                                                                                     \
+        /* along z at the four columns */                                                                 \
+        double z00 = uz * c[0] + tz * c[1], z01 = uz * c[2] + tz * c[3];                                  \
+        double z10 = uz * c[4] + tz * c[5], z11 = uz * c[6] + tz * c[7];                                  \
+        double y0v = uy * z00 + ty * z01, y1v = uy * z10 + ty * z11;                                      \
+        b.v[f] = ux * y0v + tx * y1v;                                                                     \
+        b.d[f][0] = sx * (y1v - y0v);                                                                     \
+        b.d[f][1] = sy * (ux * (z01 - z00) + tx * (z11 - z10));                                           \
+        double d00 = c[1] - c[0], d01 = c[3] - c[2], d10 = c[5] - c[4], d11 = c[7] - c[6];                \
+        b.d[f][2] = sz * (ux * (uy * d00 + ty * d01) + tx * (uy * d10 + ty * d11));                       \
+    }
+    GWAM_FIELD(x, 0)
+    GWAM_FIELD(y, 1)
+    GWAM_FIELD(z, 2)
+    GWAM_FIELD(w, 3)
+#undef GWAM_FIELD
+}
+
+// f^2 and d(f^2)/dphi (f = 2 Omega sin phi on the sphere, f0 on the f-plane)
+__device__ __forceinline__ void coriolis(const Grid& G, double sphi, double cphi, double& f2, double& df2)
+{
+    if (G.geometry == 1) {
+        double f = 2.0 * G.omega * sphi;
+        f2 = f * f;
+        df2 = 8.0 * G.omega * G.omega * sphi * cphi;
+    } else {
+        f2 = G.f0 * G.f0;
+        df2 = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------- dispersion (Eq. dispersion)
+
+// Positive intrinsic branch: w^2 = (f^2 (m^2 + G^2) + N^2 k_h^2) / K^2, K^2 = k_h^2 + m^2 + G^2.
+// The intrinsic group velocity is ch = (k, l) D (m^2 + G^2) / (w K^4), ch_r = -m D k_h^2 / (w K^4),
+// D = N^2 - f^2, so each component is (its factor) * c with c = D / (w K^4).
+struct Disp {
+    double K2, D, w2, w, c;
+};
+
+__device__ __forceinline__ void dispersion(double kh2, double mg2, double n2, double f2, Disp& d)
+{
+    d.K2 = kh2 + mg2;
+    d.D = n2 - f2;
+    double iK2 = 1.0 / d.K2;
+    d.w2 = (f2 * mg2 + n2 * kh2) * iK2;
+    d.w = sqrt(d.w2);
+    d.c = d.D * iK2 * iK2 / d.w;
+}
+
+// ---------------------------------------------------------------------------- ray equations
+
+struct Geo {
+    double r, hX, hY, sphi, cphi, tphi;
+};
+
+__device__ __forceinline__ void geometry_at(const Grid& G, double Y, double Z, Geo& g)
+{
+    if (G.geometry == 1) {
+        sincos(Y, &g.sphi, &g.cphi);
+        g.r = G.radius + Z;
+        g.hX = g.r * g.cphi;
+        g.hY = g.r;
+        g.tphi = g.sphi / g.cphi;
+    } else {
+        g.sphi = 0.0; g.cphi = 1.0; g.tphi = 0.0;
+        g.r = 1.0; g.hX = 1.0; g.hY = 1.0;
+    }
+}
+
+// Right-hand side for y = (X, Y, Z, k, l, m, eX, eY, eZ): the carrier moves with the mean of the
+// opposing face group velocities, the extents with their difference (Sec. 3b, App. B.1); the
+// wavenumber follows Eq. eikonal-sphere:1-3 (sphere) or kdot = -grad Omega (f-plane) with the
+// centre values.
+__device__ __forceinline__ void ray_rhs(const Grid& G, const Node* __restrict__ bg, const double y[9], double F[9])
+{
+    const double k = y[3], l = y[4], m = y[5];
+    Bg b;
+    gather(G, bg, y[0], y[1], y[2], b);
+    Geo g;
+    geometry_at(G, y[1], y[2], g);
+    double f2, df2;
+    coriolis(G, g.sphi, g.cphi, f2, df2);
+    const double U = b.v[0], V = b.v[1], N2 = b.v[2], G2 = b.v[3];
+    const double kh2 = k * k + l * l, m2 = m * m;
+    const double mg2 = m2 + G2;
+    Disp d;
+    dispersion(kh2, mg2, N2, f2, d);
+    const double cgx = k * mg2 * d.c + U;
+    const double cgy = l * mg2 * d.c + V;
+    const double cgz = -m * kh2 * d.c;
+    // d Omega / d q at fixed wavevector
+    const double aN = kh2 / (2.0 * d.w * d.K2);
+    const double aG = aN * d.D / d.K2;
+    const double aF = mg2 / (2.0 * d.w * d.K2);
+    double Gq[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) Gq[q] = k * b.d[0][q] + l * b.d[1][q] + aN * b.d[2][q] - aG * b.d[3][q];
+    Gq[1] += aF * df2;
+    if (G.geometry == 1) {
+        const double ir = 1.0 / g.r;
+        F[3] = -Gq[0] / g.hX + k * ir * (g.tphi * cgy - cgz);
+        F[4] = -Gq[1] * ir - ir * (l * cgz + k * g.tphi * cgx);
+        F[5] = -Gq[2] + ir * (k * cgx + l * cgy);
+    } else {
+        F[3] = -Gq[0];
+        F[4] = -Gq[1];
+        F[5] = -Gq[2];
+    }
+    // faces: first-order Taylor values along the face's own axis
+    const double ihX = 1.0 / g.hX, ihY = 1.0 / g.hY;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double vel[2];
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            const double h = (sd == 0 ? 0.5 : -0.5) * y[6 + q];
+            const double N2f = N2 + b.d[2][q] * h;
+            const double G2f = G2 + b.d[3][q] * h;
+            const double f2f = (q == 1) ? f2 + df2 * h : f2;
+            const double mg2f = m2 + G2f;
+            Disp e;
+            dispersion(kh2, mg2f, N2f, f2f, e);
+            if (q == 0) vel[sd] = (k * mg2f * e.c + U + b.d[0][0] * h) * ihX;
+            else if (q == 1) vel[sd] = (l * mg2f * e.c + V + b.d[1][1] * h) * ihY;
+            else vel[sd] = -m * kh2 * e.c;
+        }
+        F[q] = 0.5 * (vel[0] + vel[1]);
+        F[6 + q] = vel[0] - vel[1];
+    }
+}
+
+// Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.
+__device__ __forceinline__ void rk3(const Grid& G, const Node* __restrict__ bg, double s[NSTATE], double dt)
+{
+    const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
+    const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
+    double q[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) q[c] = 0.0;
+#pragma unroll 1
+    for (int st = 0; st < 3; ++st) {
+        double F[9];
+        ray_rhs(G, bg, s, F);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            q[c] = A[st] * q[c] + dt * F[c];
+            s[c] += B[st] * q[c];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------- bookkeeping
+
+__device__ __forceinline__ double wrap_period(double x, double L)
+{
+    double w = x - L * floor(x / L);
+    if (w < 0.0) w += L;
+    if (w >= L) w = 0.0;
+    return w;
+}
+
+__device__ __forceinline__ void wrap_position(const Grid& G, double s[NSTATE])
+{
+    s[SX] = wrap_period(s[SX], G.Lx);
+    if (G.geometry == 0) s[SY] = wrap_period(s[SY], G.Ly);
+}
+
+__device__ __forceinline__ double ray_action(const double s[NSTATE])
+{
+    return s[SN] * s[SPX] * s[SPY] * s[SPZ];
+}
+
+// 0 inside, 1 left the domain, 2 not a valid ray volume
+__device__ __forceinline__ int ray_status(const Grid& G, const double s[NSTATE])
+{
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < NSTATE; ++c) finite = finite && isfinite(s[c]);
+    if (!finite) return 2;
+    if (!(s[SEX] > 0.0 && s[SEY] > 0.0 && s[SEZ] > 0.0)) return 2;
+    if (!(s[SZ] >= 0.0 && s[SZ] < G.ztop)) return 1;
+    if (G.geometry == 1 && !(fabs(s[SY]) <= G.phimax)) return 1;
+    return 0;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ void cell_ijk(const Grid& G, const double s[NSTATE], int& i, int& j, int& k)
+{
+    i = clampi((int)floor(s[SX] / G.dX), 0, G.nx - 1);
+    j = clampi((int)floor((s[SY] - G.y0) / G.dY), 0, G.ny - 1);
+    k = clampi((int)floor(s[SZ] / G.dz), 0, G.nz - 1);
+}
+
+__device__ __forceinline__ int cell_of(const Grid& G, const double s[NSTATE])
+{
+    int i, j, k;
+    cell_ijk(G, s, i, j, k);
+    return (j * G.nx + i) * G.nz + k;
+}
+
+__device__ __forceinline__ double row_lat(const Grid& G, int j) { return G.y0 + (j + 0.5) * G.dY; }
+
+// Split decision (App. B.3): bit 0 vertical, bit 1 horizontal, bit 2 horizontal axis is y.
+__device__ __forceinline__ int split_code(const Grid& G, const Params& P, const double s[NSTATE])
+{
+    if (!P.splitting) return 0;
+    int code = 0;
+    if (s[SEZ] > fmax(P.alpha_s * G.dz, P.min_split_dz)) code |= 1;
+    double xlen, ylen, thr, area, athr;
+    if (G.geometry == 1) {
+        int i, j, k;
+        cell_ijk(G, s, i, j, k);
+        const double cj = cos(row_lat(G, j));
+        const double cp = cos(s[SY]);
+        xlen = cp * s[SEX];
+        ylen = s[SEY];
+        thr = P.alpha_s * sqrt(cj * G.dX * G.dY);
+        area = cp * s[SEX] * s[SEY];
+        athr = P.alpha_s * cj * G.dX * G.dY;
+    } else {
+        xlen = s[SEX];
+        ylen = s[SEY];
+        thr = P.alpha_s * sqrt(G.dX * G.dY);
+        area = s[SEX] * s[SEY];
+        athr = P.alpha_s * G.dX * G.dY;
+    }
+    if (xlen > thr || ylen > thr || area > athr) code |= (xlen >= ylen) ? 2 : 6;
+    return code;
+}
+
+__device__ __forceinline__ int num_children(int code) { return ((code & 1) ? 2 : 1) * ((code & 2) ? 2 : 1); }
+
+__device__ __forceinline__ void halve(double s[NSTATE], int axis, bool plus)
+{
+    s[SX + axis] += (plus ? 0.25 : -0.25) * s[SEX + axis];
+    s[SEX + axis] *= 0.5;
+    s[SPX + axis] *= 0.5;
+}
+
+// Child c of a split parent: children are ordered (lower, upper) x (minus, plus) with the
+// vertical index fastest; child 0 keeps the parent id, child c > 0 takes the (c-1)-th new id.
+__device__ __forceinline__ void make_child(const Grid& G, const double p[NSTATE], int code, int c, double s[NSTATE])
+{
+#pragma unroll
+    for (int q = 0; q < NSTATE; ++q) s[q] = p[q];
+    const int nv = (code & 1) ? 2 : 1;
+    if (code & 1) halve(s, 2, (c % nv) == 1);
+    if (code & 2) halve(s, (code & 4) ? 1 : 0, (c / nv) == 1);
+    if (code) wrap_position(G, s);
+}
+
+// physical volume of the ray volume, and the volume of grid cell (j, k)
+__device__ __forceinline__ double ray_volume(const Grid& G, const double s[NSTATE], const Geo& g)
+{
+    return g.hX * s[SEX] * g.hY * s[SEY] * s[SEZ];
+}
+
+__device__ __forceinline__ double cell_volume(const Grid& G, int j, int k)
+{
+    if (G.geometry == 1) {
+        const double rc = G.radius + (k + 0.5) * G.dz;
+        return rc * rc * cos(row_lat(G, j)) * G.dX * G.dY * G.dz;
+    }
+    return G.dX * G.dY * G.dz;
+}
+
+// Intrinsic properties of a ray volume at its carrier position (saturation, projection, cap).
+struct Intr {
+    double kh2, m2, mg2, K2, D, w, w2, c, f2, n2;
+};
+
+__device__ __forceinline__ void intrinsic_at(const Grid& G, const Node* __restrict__ bg, const double s[NSTATE],
+                                             Geo& g, Intr& in)
+{
+    Bg b;
+    gather(G, bg, s[SX], s[SY], s[SZ], b);
+    geometry_at(G, s[SY], s[SZ], g);
+    double df2;
+    coriolis(G, g.sphi, g.cphi, in.f2, df2);
+    in.kh2 = s[SK] * s[SK] + s[SL] * s[SL];
+    in.m2 = s[SM] * s[SM];
+    in.n2 = b.v[2];
+    in.mg2 = in.m2 + b.v[3];
+    Disp d;
+    dispersion(in.kh2, in.mg2, b.v[2], in.f2, d);
+    in.K2 = d.K2;
+    in.D = d.D;
+    in.w = d.w;
+    in.w2 = d.w2;
+    in.c = d.c;
+}
+
+}  // namespace gwam

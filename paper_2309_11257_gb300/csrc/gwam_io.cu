@@ -1,0 +1,59 @@
+// gwam_io.cu -- copies of device state into caller layouts (results, diagnostics, tests).
+#include "gwam_common.cuh"
+
+namespace gwam {
+
+__global__ void k_gather_rays(Grid G, RaySoA A, const Ctl* ctl, double* __restrict__ out, long long* __restrict__ ids,
+                              int* __restrict__ cells, int64_t n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double s[NSTATE];
+        long long id;
+        load_ray(A, p, s, id);
+        for (int q = 0; q < NSTATE; ++q) out[q * n + p] = s[q];
+        ids[p] = id;
+        cells[p] = cell_of(G, s);
+    }
+}
+
+void launch_gather_rays(Context& c, double* state13, long long* ids, int* cells, int64_t n)
+{
+    const int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096);
+    k_gather_rays<<<blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, state13, ids, cells, n);
+}
+
+// column-major [col][nlev] -> [nlev][ny][nx]
+__global__ void k_to_caller(Grid G, const double* __restrict__ src, double* __restrict__ dst, int nlev)
+{
+    const int64_t total = (int64_t)G.ncol * nlev;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = t % G.ncol;
+        const int lev = (int)(t / G.ncol);
+        dst[t] = src[col * nlev + lev];
+    }
+}
+
+__global__ void k_gamma_to_caller(Grid G, const Node* __restrict__ bg, double* __restrict__ dst)
+{
+    const int64_t total = (int64_t)G.ncell;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t col = t % G.ncol;
+        const int lev = (int)(t / G.ncol);
+        dst[t] = bg[col * G.nz + lev].w;
+    }
+}
+
+void launch_field_to_caller(Context& c, const double* src, double* dst, int nlev)
+{
+    const int64_t total = (int64_t)c.G.ncol * nlev;
+    const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 8192);
+    k_to_caller<<<blocks, kThreads, 0, c.stream>>>(c.G, src, dst, nlev);
+}
+
+void launch_gamma_to_caller(Context& c, double* dst)
+{
+    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 8192);
+    k_gamma_to_caller<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg, dst);
+}
+
+}  // namespace gwam

@@ -1,0 +1,342 @@
+// gwam_launch.cu -- background upload, explicit ray volumes, and the wave sources.
+//
+//   background: column-major node fields + Gamma^2 from rho (Sec. 2a; Gamma^2 = (d ln rho / dz)^2 / 4,
+//               centred differences between node levels, one-sided at the ends)
+//   sources:    background source of Sec. 3c (alpha(phi), F_sol, F_am) and explicit spectral bins;
+//               intrinsic frequency w = |k_h| c - k.U, bins outside |f| < w < N or with m^2 <= 0 are
+//               filtered, m from the inverted Eq. dispersion, m < 0 (upward group velocity),
+//               A = F / (|k_h| ch_r).
+#include "gwam_common.cuh"
+
+namespace gwam {
+
+enum { BG_NONFINITE = 1, BG_RHO = 2, BG_N2F2 = 4 };
+
+// caller [nz][ny][nx] -> column-major nodes, transposed through shared memory (32 columns of a row)
+__global__ void k_set_background(Grid G, int gamma_mode, const double* __restrict__ u, const double* __restrict__ v,
+                                 const double* __restrict__ n2, const double* __restrict__ rho, Node* __restrict__ bg,
+                                 double* __restrict__ rho_c, int* flags)
+{
+    extern __shared__ double sh[];   // 4 fields x nz x 32
+    const int TW = 32;
+    const int nz = G.nz;
+    const int ntx = (G.nx + TW - 1) / TW;
+    const int j = blockIdx.x / ntx, i0 = (blockIdx.x % ntx) * TW;
+    double* su = sh;
+    double* sv = sh + nz * TW;
+    double* sn = sh + 2 * nz * TW;
+    double* sr = sh + 3 * nz * TW;
+    int bad = 0;
+    for (int t = threadIdx.x; t < nz * TW; t += blockDim.x) {
+        const int ii = t % TW, k = t / TW, i = i0 + ii;
+        if (i >= G.nx) continue;
+        const int64_t o = ((int64_t)k * G.ny + j) * G.nx + i;
+        const double a = u[o], b = v[o], c = n2[o], d = rho[o];
+        su[k * TW + ii] = a;
+        sv[k * TW + ii] = b;
+        sn[k * TW + ii] = c;
+        sr[k * TW + ii] = d;
+        if (!(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d))) bad |= BG_NONFINITE;
+        else if (!(d > 0.0)) bad |= BG_RHO;
+    }
+    __syncthreads();
+    double f2 = G.f0 * G.f0;
+    if (G.geometry == 1) {
+        const double f = 2.0 * G.omega * sin(row_lat(G, j));
+        f2 = f * f;
+    }
+    for (int t = threadIdx.x; t < nz * TW; t += blockDim.x) {
+        const int k = t % nz, ii = t / nz, i = i0 + ii;
+        if (i >= G.nx) continue;
+        double g2 = 0.0;
+        if (gamma_mode) {
+            double dl;
+            if (k == 0) dl = (log(sr[1 * TW + ii]) - log(sr[ii])) / G.dz;
+            else if (k == nz - 1) dl = (log(sr[(nz - 1) * TW + ii]) - log(sr[(nz - 2) * TW + ii])) / G.dz;
+            else dl = (log(sr[(k + 1) * TW + ii]) - log(sr[(k - 1) * TW + ii])) / (2.0 * G.dz);
+            g2 = 0.25 * dl * dl;
+        }
+        const double nn = sn[k * TW + ii];
+        if (!(nn > f2)) bad |= BG_N2F2;
+        const int64_t c = node_index(G, i, j, k);
+        bg[c] = Node{su[k * TW + ii], sv[k * TW + ii], nn, g2};
+        rho_c[c] = sr[k * TW + ii];
+    }
+    if (bad) atomicOr(flags, bad);
+}
+
+void configure_launch_kernels()
+{
+    cudaFuncSetAttribute(k_set_background, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void launch_set_background(Context& c, const double* u, const double* v, const double* n2, const double* rho)
+{
+    const int TW = 32;
+    const int ntx = (c.G.nx + TW - 1) / TW;
+    const size_t shm = sizeof(double) * 4 * (size_t)c.G.nz * TW;
+    k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg, c.rho,
+                                                                c.flag_dev);
+}
+
+// ----------------------------------------------------------------------------- explicit rays
+
+// pass 0 validates, pass 1 writes at n + q with id next_id + q
+struct RayInputPtrs {
+    const double* p[13];
+};
+
+__global__ void k_add_rays(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, RayInputPtrs in, int n_add, int pass,
+                           int* flags, double* partials)
+{
+    const int n0 = ctl->n;
+    const long long next = ctl->next_id;
+    double w = 0.0;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_add; q += gridDim.x * blockDim.x) {
+        double s[NSTATE];
+        s[SX] = in.p[0][q]; s[SY] = in.p[1][q]; s[SZ] = in.p[2][q];
+        s[SK] = in.p[3][q]; s[SL] = in.p[4][q]; s[SM] = in.p[5][q];
+        s[SEX] = in.p[6][q]; s[SEY] = in.p[7][q]; s[SEZ] = in.p[8][q];
+        Geo g;
+        geometry_at(G, s[SY], s[SZ], g);
+        s[SPX] = g.hX * s[SEX] * in.p[9][q];
+        s[SPY] = g.hY * s[SEY] * in.p[10][q];
+        s[SPZ] = s[SEZ] * in.p[11][q];
+        s[SN] = in.p[12][q];
+        wrap_position(G, s);
+        if (ray_status(G, s) != 0) {
+            atomicOr(flags, 1);
+            continue;
+        }
+        if (pass == 1) {
+            const int64_t pos = (int64_t)n0 + q;
+            if (pos >= max_rays) {
+                set_status(ctl, GWAM_ECAPACITY);
+                continue;
+            }
+            store_ray(A, pos, s, next + q);
+            w += ray_action(s);
+        }
+    }
+    const double wb = block_sum(w);
+    if (threadIdx.x == 0 && pass == 1) partials[T_LAUNCH * gridDim.x + blockIdx.x] = wb;
+}
+
+__global__ void k_append_close(Ctl* ctl, int64_t max_rays, int added)
+{
+    int n = ctl->n + added;
+    if ((int64_t)n > max_rays) n = (int)max_rays;
+    ctl->n = n;
+    ctl->next_id += added;
+    ctl->n_launched += added;
+}
+
+void launch_add_rays(Context& c, const double* const in[13], int64_t n)
+{
+    RayInputPtrs d_in;
+    for (int q = 0; q < 13; ++q) d_in.p[q] = in[q];
+    cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream);
+    k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, c.max_rays, d_in, (int)n, 0, c.flag_dev,
+                                                         c.partials);
+    cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    cudaStreamSynchronize(c.stream);
+    if (*c.flag_host) {
+        c.err = "gwam_add_rays: a ray volume lies outside the domain or is invalid";
+        throw (int)GWAM_EINVAL;
+    }
+    k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, c.max_rays, d_in, (int)n, 1, c.flag_dev,
+                                                         c.partials);
+    finalize_tallies(c, 1 << T_LAUNCH, 0);
+    k_append_close<<<1, 1, 0, c.stream>>>(c.ctl, c.max_rays, (int)n);
+}
+
+// ----------------------------------------------------------------------------- sources (Sec. 3c)
+
+// latitudinal profile alpha(phi), phi in degrees north
+__device__ __forceinline__ double alpha_profile(double p)
+{
+    if (p >= 80.0) return fmin(1.0, fmax(0.0, 1.0 - (p - 80.0) / 5.0));
+    if (p >= 50.0) return 1.0;
+    if (p >= 20.0) return 0.5 * (1.0 - cos(kPi * (p - 20.0) / 30.0));
+    return 0.0;
+}
+
+__device__ __forceinline__ double f_am(double p, double tau, double fs, double fw)
+{
+    const double sol_p = alpha_profile(p) * fs + alpha_profile(-p) * fw;
+    const double sol_m = alpha_profile(-p) * fs + alpha_profile(p) * fw;
+    const double ct = cos(tau);
+    return 0.5 * (sol_p * (1.0 + ct) + sol_m * (1.0 - ct));
+}
+
+struct Bin {
+    int i, j;
+    double z_launch, dz_launch, theta, c, lambda_h, flux, frac;
+};
+
+// 0 = filtered, 1 = launched (state in s)
+__device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict__ bg, const Bin& b,
+                                           double s[NSTATE])
+{
+    const double X = (b.i + 0.5) * G.dX;
+    const double Y = row_lat(G, b.j);
+    const double Z = b.z_launch + 0.5 * b.dz_launch;
+    Bg bk;
+    gather(G, bg, X, Y, Z, bk);
+    Geo g;
+    geometry_at(G, Y, Z, g);
+    double f2, df2;
+    coriolis(G, g.sphi, g.cphi, f2, df2);
+    const double U = bk.v[0], V = bk.v[1], N2 = bk.v[2], G2 = bk.v[3];
+    const double kh = 2.0 * kPi / b.lambda_h;
+    double st, ct;
+    sincos(b.theta, &st, &ct);
+    const double k = kh * ct, l = kh * st;
+    const double w = kh * b.c - (k * U + l * V);
+    if (!(w > 0.0 && w * w > f2 && w * w < N2)) return 0;
+    const double m2 = kh * kh * (N2 - w * w) / (w * w - f2) - G2;
+    if (!(m2 > 0.0)) return 0;
+    const double m = -sqrt(m2);
+    Disp d;
+    dispersion(kh * kh, m2 + G2, N2, f2, d);
+    const double chr = -m * kh * kh * d.c;
+    const double A = b.flux / (kh * chr);
+    const double dk = b.frac * kh, dl = b.frac * kh, dm = b.frac * fabs(m);
+    s[SX] = X; s[SY] = Y; s[SZ] = Z;
+    s[SK] = k; s[SL] = l; s[SM] = m;
+    s[SEX] = G.dX; s[SEY] = G.dY; s[SEZ] = b.dz_launch;
+    s[SPX] = g.hX * G.dX * dk;
+    s[SPY] = g.hY * G.dY * dl;
+    s[SPZ] = b.dz_launch * dm;
+    s[SN] = A / (dk * dl * dm);
+    return ray_status(G, s) == 0 ? 1 : 0;
+}
+
+__device__ __forceinline__ bool source_bin(const Grid& G, const gwam_bg_source& src, int t, Bin& b)
+{
+    const int nbins = src.n_az * src.n_c;
+    const int col = t / nbins, bin = t % nbins;
+    b.j = col / G.nx;
+    b.i = col % G.nx;
+    const double pdeg = row_lat(G, b.j) * (180.0 / kPi);
+    if (fabs(pdeg) > src.phi_max_deg) return false;
+    const double fbin = f_am(pdeg, src.tau, src.f_s, src.f_w) / nbins;
+    if (fbin == 0.0 && !src.launch_zero_flux) return false;
+    const int a = bin / src.n_c, q = bin % src.n_c;
+    b.theta = 2.0 * kPi * a / src.n_az;
+    b.c = src.n_c == 1 ? src.c_min : src.c_min * pow(src.c_max / src.c_min, (double)q / (src.n_c - 1));
+    b.z_launch = src.z_launch;
+    b.dz_launch = src.dz_launch;
+    b.lambda_h = src.lambda_h;
+    b.flux = fbin;
+    b.frac = src.spectral_frac;
+    return true;
+}
+
+__device__ __forceinline__ bool spec_bin(const gwam_spec& sp, Bin& b)
+{
+    b.i = sp.i; b.j = sp.j;
+    b.z_launch = sp.z_launch; b.dz_launch = sp.dz_launch; b.theta = sp.theta; b.c = sp.c;
+    b.lambda_h = sp.lambda_h; b.flux = sp.flux; b.frac = sp.spectral_frac;
+    return true;
+}
+
+// pass 0: flag[t] = launches?, count filtered bins; pass 1: write launched rays in order
+template <bool kSpec>
+__global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ctl* ctl, int64_t max_rays,
+                         gwam_bg_source src, const gwam_spec* __restrict__ specs, int total, int pass,
+                         int* __restrict__ flag, double* __restrict__ partials)
+{
+    const int n0 = ctl->n;
+    const long long next = ctl->next_id;
+    double w = 0.0;
+    long long filtered = 0;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        Bin b;
+        bool eligible = kSpec ? spec_bin(specs[t], b) : source_bin(G, src, t, b);
+        double s[NSTATE];
+        int ok = 0;
+        if (eligible) {
+            ok = make_launch(G, bg, b, s);
+            if (!ok) ++filtered;
+        }
+        if (pass == 0) {
+            flag[t] = ok;
+        } else if (ok) {
+            const int64_t pos = (int64_t)n0 + flag[t];
+            if (pos >= max_rays) {
+                set_status(ctl, GWAM_ECAPACITY);
+                continue;
+            }
+            store_ray(A, pos, s, next + flag[t]);
+            w += ray_action(s);
+        }
+    }
+    const double wb = block_sum(w);
+    const long long fb = block_sum(filtered);
+    if (threadIdx.x == 0) {
+        if (pass == 1) partials[T_LAUNCH * gridDim.x + blockIdx.x] = wb;
+        if (pass == 0 && fb) atomicAdd((unsigned long long*)&ctl->n_filtered, (unsigned long long)fb);
+    }
+}
+
+__global__ void k_launch_close(Ctl* ctl, int64_t max_rays, const int* off, int total)
+{
+    const int added = off[total];
+    int n = ctl->n + added;
+    if ((int64_t)n > max_rays) n = (int)max_rays;
+    ctl->n = n;
+    ctl->next_id += added;
+    ctl->n_launched += added;
+}
+
+static int* launch_scratch(Context& c, int64_t need)
+{
+    if (need + 1 > c.max_rays + 1) {
+        // the per-ray scratch `newid` holds max_rays + 1 ints; larger launches need their own
+        int* p = nullptr;
+        if (cudaMallocAsync((void**)&p, sizeof(int) * (size_t)(need + 1), c.stream) != cudaSuccess) {
+            c.err = "launch: scratch allocation failed";
+            throw (int)GWAM_ENOMEM;
+        }
+        return p;
+    }
+    return c.newid;
+}
+
+static void launch_common(Context& c, const gwam_bg_source* src, const gwam_spec* specs, int64_t total)
+{
+    if (total <= 0) return;
+    int* flag = launch_scratch(c, total);
+    gwam_bg_source s0{};
+    if (src) s0 = *src;
+    const int nb = c.grid_blocks;
+    if (specs) {
+        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 0,
+                                                      flag, c.partials);
+    } else {
+        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 0,
+                                                       flag, c.partials);
+    }
+    exclusive_scan(c, flag, flag, total, nullptr);
+    if (specs) {
+        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 1,
+                                                      flag, c.partials);
+    } else {
+        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 1,
+                                                       flag, c.partials);
+    }
+    finalize_tallies(c, 1 << T_LAUNCH, 0);
+    k_launch_close<<<1, 1, 0, c.stream>>>(c.ctl, c.max_rays, flag, (int)total);
+    if (flag != c.newid) cudaFreeAsync(flag, c.stream);
+}
+
+void launch_background_source(Context& c, const gwam_bg_source& src)
+{
+    const int64_t total = (int64_t)c.G.ncol * src.n_az * src.n_c;
+    launch_common(c, &src, nullptr, total);
+}
+
+void launch_spectral(Context& c, const gwam_spec* specs, int64_t n) { launch_common(c, nullptr, specs, n); }
+
+}  // namespace gwam

@@ -1,0 +1,804 @@
+// gwam_step.cu -- one ray-volume step of the FP64 form on the device.
+//
+// Order inside a step (the paper leaves it open; this is the reading taken):
+//   advance (RK3, App. B.2) -> exits -> split (App. B.3) -> re-bin by cell (parent-cell
+//   storage, App. B.2) -> per-column cap (App. B.5) -> saturation (Sec. 3c) -> projection
+//   (Sec. 3b, Eq. fluxes:momentum, Eq. fluxes:buoyancy) -> smoothing (App. B.4) ->
+//   divergence (Eq. mean-flow-impact) -> wave-action budget (Sec. 4).
+//
+// Kernels read the live count from device memory, so a whole step is enqueued without a
+// host synchronisation.  Ray kernels run a fixed persistent grid so that the per-block FP64
+// partial sums, folded in block order, are deterministic.
+#include <algorithm>
+
+#include "gwam_common.cuh"
+
+namespace gwam {
+
+// ============================================================================ scans
+
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__device__ __forceinline__ int scan_len(int64_t n, const int* n_dev) { return n_dev ? *n_dev : (int)n; }
+
+__global__ void k_scan_reduce(const int* __restrict__ in, int64_t n, const int* n_dev, int* __restrict__ bsum)
+{
+    const int len = scan_len(n, n_dev);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    long long s = 0;
+    for (int q = threadIdx.x; q < kScanTile; q += kThreads) {
+        int64_t i = base + q;
+        if (i < len) s += in[i];
+    }
+    long long t = block_sum(s);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = (int)t;
+}
+
+__global__ void k_scan_blocks(int* bsum, int nb)
+{
+    // single block: exclusive scan of nb block sums in chunks of 1024; total into bsum[nb]
+    __shared__ int sh[1024];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        int v = i < nb ? bsum[i] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int d = 1; d < 1024; d <<= 1) {
+            int o = threadIdx.x >= d ? sh[threadIdx.x - d] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += o;
+            __syncthreads();
+        }
+        if (i < nb) bsum[i] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sh[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void k_scan_apply(const int* in, int* out, int64_t n, const int* n_dev, const int* __restrict__ bsum,
+                             int nb)
+{
+    __shared__ int tile[kScanTile];
+    __shared__ int wsum[kThreads / 32];
+    const int len = scan_len(n, n_dev);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    for (int q = threadIdx.x; q < kScanTile; q += kThreads) {
+        int64_t i = base + q;
+        tile[q] = i < len ? in[i] : 0;
+    }
+    __syncthreads();
+    int loc[kScanItems];
+    int run = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        loc[q] = run;
+        run += tile[threadIdx.x * kScanItems + q];
+    }
+    // exclusive scan of the thread totals
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = lane < kThreads / 32 ? wsum[lane] : 0;
+        int iv = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int o = __shfl_up_sync(0xffffffffu, iv, d);
+            if (lane >= d) iv += o;
+        }
+        if (lane < kThreads / 32) wsum[lane] = iv - v;
+    }
+    __syncthreads();
+    const int offset = bsum[blockIdx.x] + wsum[wid] + incl - run;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) tile[threadIdx.x * kScanItems + q] = offset + loc[q];
+    __syncthreads();
+    for (int q = threadIdx.x; q < kScanTile; q += kThreads) {
+        int64_t i = base + q;
+        if (i < len) out[i] = tile[q];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[len] = bsum[nb];
+}
+
+// Exclusive prefix of in[0..len) into out[0..len], out[len] = total; len = *n_dev if given
+// (then n is its upper bound).  in == out is allowed.
+void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n_dev)
+{
+    const int nb = (int)((n + kScanTile - 1) / kScanTile) + 1;
+    int* tmp = c.scan_tmp;
+    if ((int64_t)nb + 1 > c.scan_tmp_cap) {
+        // larger than any per-step scan (a very large launch): block sums in their own buffer
+        if (cudaMallocAsync((void**)&tmp, sizeof(int) * (size_t)(nb + 1), c.stream) != cudaSuccess) {
+            c.err = "scan: allocation failed";
+            throw (int)GWAM_ENOMEM;
+        }
+    }
+    k_scan_reduce<<<nb, kThreads, 0, c.stream>>>(in, n, n_dev, tmp);
+    k_scan_blocks<<<1, 1024, 0, c.stream>>>(tmp, nb);
+    k_scan_apply<<<nb, kThreads, 0, c.stream>>>(in, out, n, n_dev, tmp, nb);
+    if (tmp != c.scan_tmp) cudaFreeAsync(tmp, c.stream);
+}
+
+// ============================================================================ advance
+
+__global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A, const Node* __restrict__ bg,
+                                                        Ctl* ctl, double dt, int* __restrict__ info,
+                                                        int4* __restrict__ ccell, int4* __restrict__ cslot,
+                                                        int* __restrict__ newid, int* __restrict__ cnt,
+                                                        double* __restrict__ partials)
+{
+    const int n = ctl->n;
+    double w_exit = 0.0, w_inv = 0.0;
+    long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s[NSTATE];
+        long long id;
+        load_ray(A, i, s, id);
+        rk3(G, bg, s, dt);
+        wrap_position(G, s);
+        const int st = ray_status(G, s);
+        int code = 0, nch = 0;
+        int cc[4] = {-1, -1, -1, -1}, sl[4] = {0, 0, 0, 0};
+        if (st == 2) {
+            ++n_inv;
+            const double w = ray_action(s);
+            if (isfinite(w)) w_inv += w;
+        } else if (st == 1) {
+            ++n_exit;
+            w_exit += ray_action(s);
+        } else {
+            code = split_code(G, P, s);
+            nch = num_children(code);
+            if (code & 1) ++n_sv;
+            if (code & 2) n_sh += (code & 1) ? 2 : 1;
+            for (int c = 0; c < nch; ++c) {
+                double ch[NSTATE];
+                make_child(G, s, code, c, ch);
+                if (ray_status(G, ch) != 0) {
+                    ++n_exit;
+                    w_exit += ray_action(ch);
+                } else {
+                    cc[c] = cell_of(G, ch);
+                    sl[c] = atomicAdd(&cnt[cc[c]], 1);
+                }
+            }
+            store_ray(A, i, s, id);
+        }
+        info[i] = code | (nch << 4) | (st << 8);
+        ccell[i] = make_int4(cc[0], cc[1], cc[2], cc[3]);
+        cslot[i] = make_int4(sl[0], sl[1], sl[2], sl[3]);
+        newid[i] = nch > 0 ? nch - 1 : 0;
+    }
+    const double we = block_sum(w_exit);
+    const double wi = block_sum(w_inv);
+    const long long ne = block_sum(n_exit), ni = block_sum(n_inv), nv = block_sum(n_sv), nh = block_sum(n_sh);
+    if (threadIdx.x == 0) {
+        partials[T_EXIT * gridDim.x + blockIdx.x] = we;
+        partials[T_INVALID * gridDim.x + blockIdx.x] = wi;
+        if (ne) atomicAdd((unsigned long long*)&ctl->n_exited, (unsigned long long)ne);
+        if (ni) atomicAdd((unsigned long long*)&ctl->n_invalid, (unsigned long long)ni);
+        if (nv) atomicAdd((unsigned long long*)&ctl->n_split_v, (unsigned long long)nv);
+        if (nh) atomicAdd((unsigned long long*)&ctl->n_split_h, (unsigned long long)nh);
+    }
+}
+
+// ============================================================================ re-binning
+
+__global__ void k_scatter(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, const int* __restrict__ info,
+                          const int4* __restrict__ ccell, const int4* __restrict__ cslot,
+                          const int* __restrict__ newid, const int* __restrict__ off, long long* __restrict__ ent_id,
+                          int* __restrict__ ent_src)
+{
+    const int n = ctl->n;
+    const long long next = ctl->next_id;
+    const int total = off[G.ncell];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->n_children = total;
+        ctl->new_ids = newid[n];
+        if ((int64_t)total > max_rays) set_status(ctl, GWAM_ECAPACITY);
+    }
+    if ((int64_t)total > max_rays) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int nch = (info[i] >> 4) & 7;
+        if (!nch) continue;
+        const int4 cc = ccell[i], sl = cslot[i];
+        const int cs[4] = {cc.x, cc.y, cc.z, cc.w}, ss[4] = {sl.x, sl.y, sl.z, sl.w};
+        const long long pid = __double_as_longlong(A.a[6][i].y);
+        for (int c = 0; c < nch; ++c) {
+            if (cs[c] < 0) continue;
+            const int64_t pos = (int64_t)off[cs[c]] + ss[c];
+            if (pos >= max_rays) continue;
+            ent_id[pos] = c == 0 ? pid : next + newid[i] + c - 1;
+            ent_src[pos] = i * 4 + c;
+        }
+    }
+}
+
+// columns above the cap (App. B.5)
+__global__ void k_cap_find(Grid G, Params P, Ctl* ctl, const int* __restrict__ off, int* __restrict__ overlist)
+{
+    if (ctl->status) return;
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < G.ncol; col += gridDim.x * blockDim.x) {
+        const int cnt = off[(col + 1) * G.nz] - off[col * G.nz];
+        if (cnt > P.cap) overlist[atomicAdd(&ctl->n_over, 1)] = col;
+    }
+}
+
+// Remove the lowest-energy ray volumes of each over-full column (energy w_hat * N Px Py Pz;
+// ties: the larger id goes first).  One block per column, rank by counting.
+__global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA A, const Node* __restrict__ bg,
+                                                          Ctl* ctl, const int* __restrict__ info,
+                                                          const int* __restrict__ off,
+                                                          const int* __restrict__ overlist,
+                                                          const long long* __restrict__ ent_id, int* ent_src,
+                                                          double* ecap, int* cnt, double* __restrict__ partials)
+{
+    double w_cap = 0.0;
+    long long n_cap = 0;
+    const int nover = ctl->status ? 0 : ctl->n_over;
+    for (int w = blockIdx.x; w < nover; w += gridDim.x) {
+        const int col = overlist[w];
+        const int a = off[col * G.nz], b = off[(col + 1) * G.nz];
+        const int count = b - a;
+        for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+            const int src = ent_src[e];
+            double s[NSTATE], ch[NSTATE];
+            long long id;
+            load_ray(A, src >> 2, s, id);
+            make_child(G, s, info[src >> 2] & 7, src & 3, ch);
+            Geo g;
+            Intr in;
+            intrinsic_at(G, bg, ch, g, in);
+            ecap[e] = in.w * ray_action(ch);
+        }
+        __syncthreads();
+        for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+            const double E = ecap[e];
+            const long long id = ent_id[e];
+            int rank = 0;
+            for (int q = a; q < b; ++q) {
+                const double Eq = ecap[q];
+                rank += (Eq < E) || (Eq == E && ent_id[q] > id);
+            }
+            if (rank < count - P.cap) {
+                const int src = ent_src[e];
+                double s[NSTATE], ch[NSTATE];
+                long long pid;
+                load_ray(A, src >> 2, s, pid);
+                make_child(G, s, info[src >> 2] & 7, src & 3, ch);
+                w_cap += ray_action(ch);
+                ++n_cap;
+                atomicSub(&cnt[cell_of(G, ch)], 1);
+                ent_src[e] = -1 - src;
+            }
+        }
+        __syncthreads();
+    }
+    const double wc = block_sum(w_cap);
+    const long long nc = block_sum(n_cap);
+    if (threadIdx.x == 0) {
+        partials[T_CAP * gridDim.x + blockIdx.x] = wc;
+        if (nc) atomicAdd((unsigned long long*)&ctl->n_capped, (unsigned long long)nc);
+    }
+}
+
+constexpr int kSmallSeg = 16;
+
+// Sort every cell's entries by id (canonical order) and drop the capped ones; long segments
+// are deferred to k_segsort_big.
+__global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
+                          const long long* __restrict__ ent_id, const int* __restrict__ ent_src,
+                          int* __restrict__ sorted_src, int* __restrict__ biglist)
+{
+    if (ctl->status) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell; c += gridDim.x * blockDim.x) {
+        const int a = off[c];
+        const int L = off[c + 1] - a;
+        if (L == 0) continue;
+        const int dest = off2[c];
+        if (L == 1) {
+            if (ent_src[a] >= 0) sorted_src[dest] = ent_src[a];
+            continue;
+        }
+        if (L > kSmallSeg) {
+            biglist[atomicAdd(&ctl->n_big, 1)] = c;
+            continue;
+        }
+        long long ids[kSmallSeg];
+        int srcs[kSmallSeg];
+        int m = 0;
+        for (int e = 0; e < L; ++e) {
+            const int src = ent_src[a + e];
+            if (src < 0) continue;
+            const long long id = ent_id[a + e];
+            int q = m;
+            while (q > 0 && ids[q - 1] > id) {
+                ids[q] = ids[q - 1];
+                srcs[q] = srcs[q - 1];
+                --q;
+            }
+            ids[q] = id;
+            srcs[q] = src;
+            ++m;
+        }
+        for (int e = 0; e < m; ++e) sorted_src[dest + e] = srcs[e];
+    }
+}
+
+__global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
+                              const int* __restrict__ biglist, const long long* __restrict__ ent_id,
+                              const int* __restrict__ ent_src, int* __restrict__ sorted_src)
+{
+    const int nbig = ctl->status ? 0 : ctl->n_big;
+    for (int w = blockIdx.x; w < nbig; w += gridDim.x) {
+        const int c = biglist[w];
+        const int a = off[c], b = off[c + 1], dest = off2[c];
+        for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+            const int src = ent_src[e];
+            if (src < 0) continue;
+            const long long id = ent_id[e];
+            int rank = 0;
+            for (int q = a; q < b; ++q) rank += (ent_src[q] >= 0) && (ent_id[q] < id);
+            sorted_src[dest + rank] = src;
+        }
+    }
+}
+
+// Build the canonical array B from the advanced parents in A; with saturation on, also the
+// per-ray saturation terms P_j = m^2 k_h^2 / (w K^2) A_j alpha_j (with A_j alpha_j = N Px Py Pz / V_c)
+// and K_j^2 (Eq. instability-threshold).
+__global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RaySoA A, RaySoA B,
+                                                            const Node* __restrict__ bg, Ctl* ctl,
+                                                            const int* __restrict__ off2,
+                                                            const int* __restrict__ sorted_src,
+                                                            const int* __restrict__ info,
+                                                            const int* __restrict__ newid, double* __restrict__ pj,
+                                                            double* __restrict__ k2)
+{
+    if (ctl->status) return;
+    const int n_new = off2[G.ncell];
+    const int n_old = ctl->n;
+    const long long next = ctl->next_id;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_new; p += gridDim.x * blockDim.x) {
+        const int src = sorted_src[p];
+        const int i = src >> 2, c = src & 3;
+        if (src < 0 || i >= n_old) {   // inconsistent re-binning: never read past the parents
+            set_status(ctl, GWAM_ECUDA);
+            continue;
+        }
+        double s[NSTATE], ch[NSTATE];
+        long long id;
+        load_ray(A, i, s, id);
+        make_child(G, s, info[i] & 7, c, ch);
+        const long long cid = c == 0 ? id : next + newid[i] + c - 1;
+        store_ray(B, p, ch, cid);
+        if (P.saturation) {
+            Geo g;
+            Intr in;
+            intrinsic_at(G, bg, ch, g, in);
+            int ci, cj, ck;
+            cell_ijk(G, ch, ci, cj, ck);
+            const double av = ray_action(ch) / cell_volume(G, cj, ck);
+            pj[p] = in.m2 * in.kh2 / (in.w * in.K2) * av;
+            k2[p] = in.K2;
+        }
+    }
+}
+
+// kappa = max(0, (P - rho/2) / (2 dt sum_j P_j K_j^2)) of every carrier cell (Eq. turbulent-diffusivity)
+__global__ void k_sat_kappa(Grid G, const Ctl* ctl, const int* __restrict__ off2, const double* __restrict__ rho,
+                            const double* __restrict__ pj, const double* __restrict__ k2, double dt,
+                            double* __restrict__ kappa)
+{
+    if (ctl->status) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell; c += gridDim.x * blockDim.x) {
+        const int a = off2[c], b = off2[c + 1];
+        if (a == b) continue;
+        double Pc = 0.0, Q = 0.0;
+        for (int p = a; p < b; ++p) {
+            Pc += pj[p];
+            Q += pj[p] * k2[p];
+        }
+        const double kap = Q > 0.0 ? fmax(0.0, (Pc - 0.5 * rho[c]) / (2.0 * dt * Q)) : 0.0;
+        for (int p = a; p < b; ++p) kappa[p] = kap;
+    }
+}
+
+// ============================================================================ saturation + projection
+
+// Saturation N -> N max(0, 1 - 2 kappa K^2 dt); then each ray volume's fluxes:
+//   direct form (Eq. fluxes:momentum): T^{ab} = [w^2 ch_a k_b + f^2 (e_r x ch)_a (e_r x k_h)_b] / (w^2 - f^2) A
+//   elastic term (Eq. fluxes:buoyancy, theta cancels): -f^2 N^2 ch_r / (w^2 - f^2) k_h A (without 1/(g rho))
+//   pseudomomentum form (App. A): T^{ab} = ch_a k_b A
+// Centre fields: cell averages over the ray volumes whose carrier is in the cell, weight V_j/V_c.
+// Interface fields (z = kk dz, 1 <= kk < nz): staggered-cell overlap, weight w_h * overlap / dz.
+__global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B, const Node* __restrict__ bg,
+                                                        const Ctl* ctl, const int* __restrict__ off2,
+                                                        const double* __restrict__ kappa,
+                                                        const double* __restrict__ k2, double dt,
+                                                        double* __restrict__ fz_l, double* __restrict__ fz_p,
+                                                        double* __restrict__ f_ll, double* __restrict__ f_lp,
+                                                        double* __restrict__ f_pl, double* __restrict__ f_pp,
+                                                        double* __restrict__ e_l, double* __restrict__ e_p,
+                                                        double* __restrict__ wad, double* __restrict__ partials)
+{
+    const int n = ctl->status ? 0 : off2[G.ncell];
+    double w_sat = 0.0, w_tot = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < n; p0 += stride) {
+        const int p = p0 + threadIdx.x;
+        const bool act = p < n;
+        int key = -1;
+        double hv[7] = {0, 0, 0, 0, 0, 0, 0};
+        double zl = 0.0, zp = 0.0, wh = 0.0, lo = 0.0, hi = 0.0;
+        int col = 0, kk0 = 1, nkk = 0;
+        if (act) {
+            double s[NSTATE];
+            long long id;
+            load_ray(B, p, s, id);
+            if (P.saturation) {
+                const double kap = kappa[p];
+                if (kap > 0.0) {
+                    const double fac = fmax(0.0, 1.0 - 2.0 * kap * k2[p] * dt);
+                    const double nold = s[SN];
+                    s[SN] = nold * fac;
+                    w_sat += (nold - s[SN]) * s[SPX] * s[SPY] * s[SPZ];
+                    B.a[6][p].x = s[SN];
+                }
+            }
+            const double W = ray_action(s);
+            w_tot += W;
+            Geo g;
+            Intr in;
+            intrinsic_at(G, bg, s, g, in);
+            int ci, cj, ck;
+            cell_ijk(G, s, ci, cj, ck);
+            key = (cj * G.nx + ci) * G.nz + ck;
+            col = cj * G.nx + ci;
+            const double Vj = ray_volume(G, s, g);
+            const double A = W / Vj;                       // N dk dl dm
+            const double alpha = Vj / cell_volume(G, cj, ck);
+            const double k = s[SK], l = s[SL], m = s[SM];
+            const double mg2c = in.mg2 * in.c;             // (m^2 + Gamma^2) D / (w K^4)
+            const double chx = k * mg2c, chy = l * mg2c, chr = -m * in.kh2 * in.c;
+            double t_ll, t_lp, t_pl, t_pp, el, ep;
+            if (P.flux_form == 0) {
+                const double iden = 1.0 / (in.w2 - in.f2);
+                t_ll = (in.w2 * chx * k + in.f2 * chy * l) * iden;
+                t_lp = (in.w2 * chx * l - in.f2 * chy * k) * iden;
+                t_pl = (in.w2 * chy * k - in.f2 * chx * l) * iden;
+                t_pp = (in.w2 * chy * l + in.f2 * chx * k) * iden;
+                zl = in.w2 * chr * k * iden;
+                zp = in.w2 * chr * l * iden;
+                el = -in.f2 * in.n2 * chr * iden * k;
+                ep = -in.f2 * in.n2 * chr * iden * l;
+            } else {
+                t_ll = chx * k; t_lp = chx * l; t_pl = chy * k; t_pp = chy * l;
+                zl = chr * k; zp = chr * l;
+                el = 0.0; ep = 0.0;
+            }
+            const double aw = alpha * A;
+            hv[0] = aw * t_ll; hv[1] = aw * t_lp; hv[2] = aw * t_pl; hv[3] = aw * t_pp;
+            hv[4] = aw * el; hv[5] = aw * ep; hv[6] = aw;
+            zl *= A;
+            zp *= A;
+            if (G.geometry == 1)
+                wh = g.cphi * s[SEX] * s[SEY] / (cos(row_lat(G, cj)) * G.dX * G.dY);
+            else
+                wh = s[SEX] * s[SEY] / (G.dX * G.dY);
+            lo = s[SZ] - 0.5 * s[SEZ];
+            hi = s[SZ] + 0.5 * s[SEZ];
+            kk0 = max(1, (int)floor(lo / G.dz - 0.5));
+            const int kk1 = min(G.nz - 1, (int)ceil(hi / G.dz + 0.5));
+            nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
+        }
+        // centre fields: warp-segmented reduction over runs of equal cells, one atomic per run
+        if (warp_segment_reduce(key, hv) && key >= 0) {
+            atomicAdd(&f_ll[key], hv[0]);
+            atomicAdd(&f_lp[key], hv[1]);
+            atomicAdd(&f_pl[key], hv[2]);
+            atomicAdd(&f_pp[key], hv[3]);
+            atomicAdd(&e_l[key], hv[4]);
+            atomicAdd(&e_p[key], hv[5]);
+            atomicAdd(&wad[key], hv[6]);
+        }
+        // interface fields
+        int maxk = nkk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) maxk = max(maxk, __shfl_xor_sync(0xffffffffu, maxk, o));
+        for (int o = 0; o < maxk; ++o) {
+            double zv[2] = {0.0, 0.0};
+            int zkey = -1;
+            if (o < nkk) {
+                const int kk = kk0 + o;
+                const double slo = (kk - 0.5) * G.dz, shi = (kk + 0.5) * G.dz;
+                const double ov = fmin(hi, shi) - fmax(lo, slo);
+                if (ov > 0.0) {
+                    const double w = wh * ov / G.dz;
+                    zv[0] = w * zl;
+                    zv[1] = w * zp;
+                    zkey = col * (G.nz + 1) + kk;
+                }
+            }
+            if (warp_segment_reduce(zkey, zv) && zkey >= 0) {
+                atomicAdd(&fz_l[zkey], zv[0]);
+                atomicAdd(&fz_p[zkey], zv[1]);
+            }
+        }
+    }
+    const double ws = block_sum(w_sat);
+    const double wt = block_sum(w_tot);
+    if (threadIdx.x == 0) {
+        partials[T_SAT * gridDim.x + blockIdx.x] = ws;
+        partials[T_TOTAL * gridDim.x + blockIdx.x] = wt;
+    }
+}
+
+// ============================================================================ smoothing + divergence
+
+// 1-2-1 x 1-2-1 horizontal smoothing (App. B.4 on a lat-lon grid): periodic in x, the edge row
+// reused beyond the pole rows on the sphere, periodic in y on the f-plane.
+__global__ void k_smooth(Grid G, const double* __restrict__ in, double* __restrict__ out, int nlev)
+{
+    const int64_t total = (int64_t)G.ncol * nlev;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int lev = (int)(t % nlev);
+        const int col = (int)(t / nlev);
+        const int i = col % G.nx, j = col / G.nx;
+        double acc = 0.0;
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj) {
+            int jj = j + dj;
+            if (G.geometry == 1) jj = clampi(jj, 0, G.ny - 1);
+            else jj = wrap_int(jj, G.ny);
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+                const int ii = wrap_int(i + di, G.nx);
+                const double w = (di == 0 ? 2.0 : 1.0) * (dj == 0 ? 2.0 : 1.0);
+                acc += w * in[((int64_t)jj * G.nx + ii) * nlev + lev];
+            }
+        }
+        out[t] = acc * (1.0 / 16.0);
+    }
+}
+
+// du/dt = -(1/rho) [ (1/(r cos phi)) (d_lambda F^{ll} + d_phi (cos phi F^{pl})) + d_z F^z_l ] + E_l / (g rho),
+// dv/dt likewise (Eq. mean-flow-impact; centred differences, flux zero beyond the pole rows).
+// One block per (row, tile of TW columns); results transposed through shared memory into the
+// caller's [nz][ny][nx] layout.
+__global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, const double* __restrict__ fzp,
+                             const double* __restrict__ fll, const double* __restrict__ flp,
+                             const double* __restrict__ fpl, const double* __restrict__ fpp,
+                             const double* __restrict__ el, const double* __restrict__ ep,
+                             const double* __restrict__ rho, double* __restrict__ du, double* __restrict__ dv)
+{
+    extern __shared__ double tile[];
+    double* tu = tile;
+    double* tv = tile + (size_t)TW * G.nz;
+    const int ntx = (G.nx + TW - 1) / TW;
+    const int j = blockIdx.x / ntx;
+    const int i0 = (blockIdx.x % ntx) * TW;
+    const int nz = G.nz;
+    const int n = TW * nz;
+    double rcp_cos = 1.0, cn = 0.0, cs = 0.0;
+    if (G.geometry == 1) {
+        rcp_cos = 1.0 / cos(row_lat(G, j));
+        if (j + 1 < G.ny) cn = cos(row_lat(G, j + 1));
+        if (j - 1 >= 0) cs = cos(row_lat(G, j - 1));
+    }
+    const int jn = G.geometry == 1 ? j + 1 : wrap_int(j + 1, G.ny);
+    const int js = G.geometry == 1 ? j - 1 : wrap_int(j - 1, G.ny);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int k = t % nz, ii = t / nz;
+        const int i = i0 + ii;
+        if (i >= G.nx) continue;
+        const int ie = wrap_int(i + 1, G.nx), iw = wrap_int(i - 1, G.nx);
+        const int64_t c = ((int64_t)j * G.nx + i) * nz + k;
+        const int64_t ce = ((int64_t)j * G.nx + ie) * nz + k;
+        const int64_t cw = ((int64_t)j * G.nx + iw) * nz + k;
+        const int64_t zc = ((int64_t)j * G.nx + i) * (nz + 1) + k;
+        double pl_n = 0.0, pl_s = 0.0, pp_n = 0.0, pp_s = 0.0;
+        if (jn >= 0 && jn < G.ny) {
+            const int64_t cc = ((int64_t)jn * G.nx + i) * nz + k;
+            pl_n = fpl[cc];
+            pp_n = fpp[cc];
+        }
+        if (js >= 0 && js < G.ny) {
+            const int64_t cc = ((int64_t)js * G.nx + i) * nz + k;
+            pl_s = fpl[cc];
+            pp_s = fpp[cc];
+        }
+        const double r = rho[c];
+        double div_u, div_v;
+        const double dzl = (fzl[zc + 1] - fzl[zc]) / G.dz;
+        const double dzp = (fzp[zc + 1] - fzp[zc]) / G.dz;
+        if (G.geometry == 1) {
+            const double rr = G.radius + (k + 0.5) * G.dz;
+            const double dl_u = (fll[ce] - fll[cw]) / (2.0 * G.dX);
+            const double dp_u = (cn * pl_n - cs * pl_s) / (2.0 * G.dY);
+            const double dl_v = (flp[ce] - flp[cw]) / (2.0 * G.dX);
+            const double dp_v = (cn * pp_n - cs * pp_s) / (2.0 * G.dY);
+            div_u = (dl_u + dp_u) * rcp_cos / rr + dzl;
+            div_v = (dl_v + dp_v) * rcp_cos / rr + dzp;
+        } else {
+            div_u = (fll[ce] - fll[cw]) / (2.0 * G.dX) + (pl_n - pl_s) / (2.0 * G.dY) + dzl;
+            div_v = (flp[ce] - flp[cw]) / (2.0 * G.dX) + (pp_n - pp_s) / (2.0 * G.dY) + dzp;
+        }
+        tu[k * TW + ii] = -div_u / r + el[c] / (G.g * r);
+        tv[k * TW + ii] = -div_v / r + ep[c] / (G.g * r);
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int ii = t % TW, k = t / TW;
+        const int i = i0 + ii;
+        if (i >= G.nx) continue;
+        const int64_t o = ((int64_t)k * G.ny + j) * G.nx + i;
+        if (du) du[o] = tu[k * TW + ii];
+        if (dv) dv[o] = tv[k * TW + ii];
+    }
+}
+
+// ============================================================================ budget, control
+
+// Fold the per-block partials of the slots in `mask` (block order: deterministic) into the
+// budget; mode 1 also closes a step (live count, ids, step counter).
+__global__ void k_finalize(Ctl* ctl, DevBudget* bud, const double* __restrict__ partials, int nb, int mask, int mode)
+{
+    __shared__ double acc[NTALLY];
+    for (int s = 0; s < NTALLY; ++s) {
+        double v = 0.0;
+        if (mask & (1 << s))
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[s * nb + b];
+        // fixed-order block reduction
+        const double t = block_sum(v);
+        if (threadIdx.x == 0) acc[s] = t;
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    if (mask & (1 << T_EXIT)) bud->w_exited += acc[T_EXIT];
+    if (mask & (1 << T_INVALID)) bud->w_invalid += acc[T_INVALID];
+    if (mask & (1 << T_CAP)) bud->w_capped += acc[T_CAP];
+    if (mask & (1 << T_SAT)) bud->w_saturated += acc[T_SAT];
+    if (mask & (1 << T_LAUNCH)) {
+        bud->w_launched += acc[T_LAUNCH];
+        bud->w_total += acc[T_LAUNCH];
+    }
+    if (mask & (1 << T_TOTAL)) bud->w_total = acc[T_TOTAL];
+    if (mode == 1) {
+        // after a device failure the population is not trustworthy: drop it (the status stays set)
+        ctl->n = ctl->status ? 0 : ctl->n_new;
+        ctl->next_id += ctl->new_ids;
+        ctl->n_steps += 1;
+    }
+}
+
+__global__ void k_step_begin(Ctl* ctl)
+{
+    ctl->n_over = 0;
+    ctl->n_big = 0;
+    ctl->n_children = 0;
+    ctl->new_ids = 0;
+    ctl->ray_steps += ctl->n;
+}
+
+__global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl) { ctl->n_new = off2[ncell]; }
+
+// ============================================================================ orchestration
+
+static void swap_soa(Context& c)
+{
+    RaySoA t = c.A;
+    c.A = c.B;
+    c.B = t;
+}
+
+void finalize_tallies(Context& c, int mask, int mode)
+{
+    k_finalize<<<1, kThreads, 0, c.stream>>>(c.ctl, c.budget, c.partials, c.grid_blocks, mask, mode);
+}
+
+void configure_launch_kernels();
+
+void configure_kernels()
+{
+    cudaFuncSetAttribute(k_divergence, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    configure_launch_kernels();
+}
+
+// event `phase` of the current profiled step (phase 0 = step start, kPhases = step end)
+void prof_mark(Context& c, int phase)
+{
+    if (!c.prof) return;
+    if (phase == 0 && c.prof_pending == Context::kRing) prof_harvest(c);
+    cudaEventRecord(c.prof_ev[c.prof_pending][phase], c.stream);
+    if (phase == Context::kPhases) ++c.prof_pending;
+}
+
+void prof_harvest(Context& c)
+{
+    for (int q = 0; q < c.prof_pending; ++q) {
+        cudaEventSynchronize(c.prof_ev[q][Context::kPhases]);
+        for (int p = 0; p < Context::kPhases; ++p) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, c.prof_ev[q][p], c.prof_ev[q][p + 1]);
+            c.prof_ms[p] += ms;
+        }
+    }
+    c.prof_steps += c.prof_pending;
+    c.prof_pending = 0;
+}
+
+void run_step(Context& c, double dt, double* du, double* dv)
+{
+    const Grid& G = c.G;
+    const Params& P = c.P;
+    cudaStream_t s = c.stream;
+    const int nb = c.grid_blocks;
+    const int cell_blocks = (int)std::min<int64_t>((G.ncell + kThreads - 1) / kThreads, 65535LL * 4);
+    k_step_begin<<<1, 1, 0, s>>>(c.ctl);
+    cudaMemsetAsync(c.cnt, 0, sizeof(int) * (size_t)(G.ncell + 1), s);
+    prof_mark(c, 0);
+    k_advance<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bg, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
+                                      c.partials);
+    prof_mark(c, 1);
+    exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
+    exclusive_scan(c, c.cnt, c.off, G.ncell, nullptr);
+    k_scatter<<<nb, kThreads, 0, s>>>(G, c.A, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off, c.ent_id,
+                                      c.ent_src);
+    int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
+    const int* off2 = c.off;
+    if (P.cap > 0) {
+        k_cap_find<<<cell_blocks, kThreads, 0, s>>>(G, P, c.ctl, c.off, c.overlist);
+        k_cap_apply<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bg, c.ctl, c.info, c.off, c.overlist, c.ent_id, c.ent_src,
+                                            c.ecap, c.cnt, c.partials);
+        exclusive_scan(c, c.cnt, c.off2, G.ncell, nullptr);
+        off2 = c.off2;
+        mask |= 1 << T_CAP;
+    }
+    k_segsort<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.sorted_src, c.biglist);
+    k_segsort_big<<<nb, kThreads, 0, s>>>(c.ctl, c.off, off2, c.biglist, c.ent_id, c.ent_src, c.sorted_src);
+    k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell, c.ctl);
+    k_materialize<<<nb, kThreads, 0, s>>>(G, P, c.A, c.B, c.bg, c.ctl, off2, c.sorted_src, c.info, c.newid, c.pj,
+                                          c.k2);
+    prof_mark(c, 2);
+    if (P.saturation)
+        k_sat_kappa<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, off2, c.rho, c.pj, c.k2, dt, c.kappa);
+    prof_mark(c, 3);
+    for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
+    k_project<<<nb, kThreads, 0, s>>>(G, P, c.B, c.bg, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL], c.field[F_ZP],
+                                      c.field[F_LL], c.field[F_LP], c.field[F_PL], c.field[F_PP], c.field[F_EL],
+                                      c.field[F_EP], c.field[F_WAD], c.partials);
+    prof_mark(c, 4);
+    double* const* fl = c.field;
+    if (P.smoothing) {
+        for (int f = 0; f < NFIELD; ++f) {
+            const int nlev = f <= F_ZP ? G.nz + 1 : G.nz;
+            const int blocks = (int)std::min<int64_t>((c.field_len(f) + kThreads - 1) / kThreads, 8192);
+            k_smooth<<<blocks, kThreads, 0, s>>>(G, c.field[f], c.smooth[f], nlev);
+        }
+        fl = c.smooth;
+    }
+    const int TW = G.nz <= 96 ? 32 : 16;
+    const size_t shm = sizeof(double) * 2 * (size_t)TW * G.nz;
+    const int ntx = (G.nx + TW - 1) / TW;
+    k_divergence<<<ntx * G.ny, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP], fl[F_PL], fl[F_PP],
+                                                   fl[F_EL], fl[F_EP], c.rho, du ? du : c.dudt_buf,
+                                                   dv ? dv : c.dvdt_buf);
+    k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, nb, mask, 1);
+    prof_mark(c, 5);
+    swap_soa(c);
+}
+
+}  // namespace gwam

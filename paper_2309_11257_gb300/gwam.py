@@ -1,0 +1,254 @@
+"""ctypes binding of libgwam.so (include/gwam.h).
+
+Argument marshalling only: every step of the ray-volume path runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (float64, contiguous); the context's stream
+is the torch stream current at construction.  Importing this module loads libgwam.so and
+raises if it is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgwam.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libgwam.so is not built (run __graft_entry__.build() or paper_2309_11257_gb300/build.py); "
+                      "the ray-volume path has no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+GWAM_OK, GWAM_EINVAL, GWAM_ENOMEM, GWAM_ECAPACITY, GWAM_ENUMERIC, GWAM_ECUDA, GWAM_ETIMEOUT, GWAM_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+STATUS_NAMES = {0: "GWAM_OK", -1: "GWAM_EINVAL", -2: "GWAM_ENOMEM", -3: "GWAM_ECAPACITY", -4: "GWAM_ENUMERIC",
+                -5: "GWAM_ECUDA", -6: "GWAM_ETIMEOUT", -7: "GWAM_ESTATE"}
+STATE_NAMES = ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "px", "py", "pz", "n")
+FIELD_NAMES = ("fz_l", "fz_p", "f_ll", "f_lp", "f_pl", "f_pp", "e_l", "e_p", "wad")
+
+
+class GwamError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, code), msg))
+        self.code = code
+
+
+class Grid(C.Structure):
+    _fields_ = [("geometry", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double), ("f0", C.c_double),
+                ("radius", C.c_double), ("omega", C.c_double), ("g", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("precision", C.c_int), ("gamma_mode", C.c_int), ("saturation", C.c_int), ("smoothing", C.c_int),
+                ("flux_form", C.c_int), ("splitting", C.c_int), ("cap_per_column", C.c_int),
+                ("alpha_s", C.c_double), ("min_split_dz", C.c_double), ("max_rays", C.c_int64)]
+
+
+class BgSource(C.Structure):
+    _fields_ = [("f_s", C.c_double), ("f_w", C.c_double), ("tau", C.c_double), ("z_launch", C.c_double),
+                ("dz_launch", C.c_double), ("lambda_h", C.c_double), ("c_min", C.c_double),
+                ("c_max", C.c_double), ("n_az", C.c_int), ("n_c", C.c_int), ("spectral_frac", C.c_double),
+                ("phi_max_deg", C.c_double), ("launch_zero_flux", C.c_int)]
+
+
+class Spec(C.Structure):
+    _fields_ = [("i", C.c_int), ("j", C.c_int), ("pad_", C.c_int), ("z_launch", C.c_double),
+                ("dz_launch", C.c_double), ("theta", C.c_double), ("c", C.c_double),
+                ("lambda_h", C.c_double), ("flux", C.c_double), ("spectral_frac", C.c_double)]
+
+
+class RayInput(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "dk", "dl", "dm", "n")]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_live", "n_launched", "n_filtered", "n_split_v", "n_split_h",
+                                         "n_exited", "n_capped", "n_merged", "n_invalid", "n_steps",
+                                         "ray_steps")] + \
+               [(n, C.c_double) for n in ("w_total", "w_launched", "w_saturated", "w_exited", "w_capped",
+                                          "w_invalid")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_vp = C.c_void_p
+_P = C.POINTER
+# name -> (restype, argtypes); every entry point declared in include/gwam.h
+SIGNATURES = {
+    "gwam_init": (C.c_int, [_P(_vp), _P(Grid), _P(Params), _vp]),
+    "gwam_destroy": (None, [_vp]),
+    "gwam_set_background": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gwam_set_background_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gwam_add_rays": (C.c_int, [_vp, _P(RayInput), C.c_int64]),
+    "gwam_add_rays_host": (C.c_int, [_vp, _P(RayInput), C.c_int64]),
+    "gwam_launch_sources": (C.c_int, [_vp, _P(BgSource)]),
+    "gwam_launch_spectral": (C.c_int, [_vp, _vp, C.c_int64]),
+    "gwam_launch_spectral_host": (C.c_int, [_vp, _vp, C.c_int64]),
+    "gwam_step": (C.c_int, [_vp, C.c_double, _vp, _vp]),
+    "gwam_step_host": (C.c_int, [_vp, C.c_double, _vp, _vp]),
+    "gwam_num_rays": (C.c_int, [_vp, _P(C.c_int64)]),
+    "gwam_get_rays_host": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64]),
+    "gwam_get_stats": (C.c_int, [_vp, _P(Stats)]),
+    "gwam_get_field_host": (C.c_int, [_vp, C.c_int, _vp]),
+    "gwam_get_gamma2_host": (C.c_int, [_vp, _vp]),
+    "gwam_synchronize": (C.c_int, [_vp]),
+    "gwam_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
+    "gwam_last_error": (C.c_char_p, [_vp]),
+    "gwam_version": (C.c_char_p, []),
+}
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def lib():
+    return _lib
+
+
+def version() -> str:
+    return _lib.gwam_version().decode()
+
+
+def _struct(cls, d: dict):
+    s = cls()
+    for name, _ in cls._fields_:
+        if name in d:
+            setattr(s, name, d[name])
+    return s
+
+
+def _ptr(t):
+    import torch
+    assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    return C.c_void_p(t.data_ptr())
+
+
+class Tracer:
+    """One ray-volume context on the current CUDA device."""
+
+    def __init__(self, grid: dict, params: dict, max_rays: int, stream=None):
+        import torch
+        self.grid = dict(grid)
+        self.params = dict(params)
+        self.nx, self.ny, self.nz = grid["nx"], grid["ny"], grid["nz"]
+        self.max_rays = int(max_rays)
+        p = dict(params, max_rays=self.max_rays)
+        p.setdefault("precision", 0)
+        self._g = _struct(Grid, grid)
+        self._p = _struct(Params, p)
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        h = C.c_void_p()
+        rc = _lib.gwam_init(C.byref(h), C.byref(self._g), C.byref(self._p), C.c_void_p(s.cuda_stream))
+        if rc != 0:
+            raise GwamError(rc, "gwam_init")
+        self._h = h
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib.gwam_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise GwamError(rc, "%s: %s" % (what, _lib.gwam_last_error(self._h).decode()))
+
+    # -------------------------------------------------------------- inputs
+    def set_background(self, u, v, n2, rho):
+        """Device tensors (float64, [nz][ny][nx]) or numpy arrays (host path)."""
+        if isinstance(u, np.ndarray):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, n2, rho)]
+            self._check(_lib.gwam_set_background_host(self._h, *[a.ctypes.data_as(_vp) for a in arrs]),
+                        "set_background_host")
+        else:
+            self._check(_lib.gwam_set_background(self._h, *[_ptr(a) for a in (u, v, n2, rho)]), "set_background")
+
+    def add_rays(self, r: dict):
+        names = ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "dk", "dl", "dm", "n")
+        arrs = [np.ascontiguousarray(r[n], dtype=np.float64) for n in names]
+        ri = RayInput(*[a.ctypes.data_as(_vp) for a in arrs])
+        self._check(_lib.gwam_add_rays_host(self._h, C.byref(ri), len(arrs[0])), "add_rays_host")
+
+    def launch_sources(self, src: dict):
+        s = _struct(BgSource, src)
+        self._check(_lib.gwam_launch_sources(self._h, C.byref(s)), "launch_sources")
+
+    def launch_spectral(self, specs: np.ndarray):
+        """specs: numpy structured array with the fields of gwam_spec (host)."""
+        n = len(specs)
+        arr = (Spec * max(n, 1))()
+        for q in range(n):
+            for name, _ in Spec._fields_:
+                setattr(arr[q], name, specs[name][q].item())
+        self._check(_lib.gwam_launch_spectral_host(self._h, C.cast(arr, _vp), n), "launch_spectral_host")
+
+    # -------------------------------------------------------------- step
+    def step(self, dt: float, dudt=None, dvdt=None):
+        """Stream-ordered step; dudt/dvdt: device tensors [nz][ny][nx] float64 or None."""
+        self._check(_lib.gwam_step(self._h, float(dt), _ptr(dudt) if dudt is not None else None,
+                                   _ptr(dvdt) if dvdt is not None else None), "step")
+
+    def step_host(self, dt: float, dudt: np.ndarray, dvdt: np.ndarray):
+        """Step with host (numpy, ideally pinned) output buffers; synchronising."""
+        self._check(_lib.gwam_step_host(self._h, float(dt), dudt.ctypes.data_as(_vp), dvdt.ctypes.data_as(_vp)),
+                    "step_host")
+
+    # -------------------------------------------------------------- outputs
+    def num_rays(self) -> int:
+        n = C.c_int64()
+        self._check(_lib.gwam_num_rays(self._h, C.byref(n)), "num_rays")
+        return n.value
+
+    def rays(self) -> dict:
+        n = self.num_rays()
+        cap = max(n, 1)
+        st = np.zeros((13, cap))
+        ids = np.zeros(cap, dtype=np.int64)
+        cells = np.zeros(cap, dtype=np.int32)
+        self._check(_lib.gwam_get_rays_host(self._h, st.ctypes.data_as(_vp), ids.ctypes.data_as(_vp),
+                                            cells.ctypes.data_as(_vp), cap), "get_rays_host")
+        out = {name: st[q, :n].copy() for q, name in enumerate(STATE_NAMES)}
+        out["id"] = ids[:n].copy()
+        out["cell"] = cells[:n].copy()
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(_lib.gwam_get_stats(self._h, C.byref(s)), "get_stats")
+        return s.as_dict()
+
+    def field(self, name: str) -> np.ndarray:
+        which = FIELD_NAMES.index(name)
+        nl = self.nz + 1 if which < 2 else self.nz
+        out = np.zeros((nl, self.ny, self.nx))
+        self._check(_lib.gwam_get_field_host(self._h, which, out.ctypes.data_as(_vp)), "get_field_host")
+        return out
+
+    def gamma2(self) -> np.ndarray:
+        out = np.zeros((self.nz, self.ny, self.nx))
+        self._check(_lib.gwam_get_gamma2_host(self._h, out.ctypes.data_as(_vp)), "get_gamma2_host")
+        return out
+
+    PHASES = ("advance", "rebin", "saturation", "projection", "grid")
+
+    def profile(self, enable: bool = True):
+        self._check(_lib.gwam_profile_enable(self._h, 1 if enable else 0), "profile_enable")
+
+    def profile_read(self):
+        ms = np.zeros(5)
+        n = C.c_int64()
+        self._check(_lib.gwam_profile_read(self._h, ms.ctypes.data_as(_vp), C.byref(n)), "profile_read")
+        return dict(zip(self.PHASES, ms.tolist())), n.value
+
+    def synchronize(self):
+        self._check(_lib.gwam_synchronize(self._h), "synchronize")

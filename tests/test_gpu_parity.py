@@ -1,0 +1,291 @@
+"""CUDA path (libgwam.so through the C ABI) against the FP64 CPU oracle, element by element.
+
+Small cases run both sides over many steps (several tiles and ragged tails: ray counts are not
+multiples of the block size, grids not multiples of the divergence tile); the full-size sphere
+workload (256 x 128 x 90 columns, 983 040 launched ray volumes, launch configuration of the
+benchmark) compares the launch and a complete step in full.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_11257_gb300 import synth
+from parity_util import (RTOL, assert_fields_match, assert_rays_match, assert_stats_match, level_error,
+                         state_errors)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gw():
+    from paper_2309_11257_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2309_11257_gb300 import gwam
+    return gwam
+
+
+def _pair(gw, grid, params, bg, max_rays):
+    import torch
+    T = gw.Tracer(grid, params, max_rays=max_rays)
+    O = oracle.Model(grid, params)
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in bg]
+    T.set_background(*dev)
+    O.set_background(*bg)
+    return T, O
+
+
+def _step_both(T, O, dt, nz, ny, nx):
+    import torch
+    du = torch.zeros((nz, ny, nx), dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    T.step(dt, du, dv)
+    odu, odv = O.step(dt)
+    return du.cpu().numpy(), dv.cpu().numpy(), odu, odv
+
+
+def _compare_all(T, O, grid, du=None, dv=None, odu=None, odv=None, fields=True):
+    errs = assert_rays_match(T.rays(), O.rays(), grid)
+    assert_stats_match(T.stats(), O.stats())
+    if du is not None:
+        assert_fields_match(du, odu)
+        assert_fields_match(dv, odv)
+    if fields:
+        for name in oracle.FIELD_NAMES:
+            assert_fields_match(T.field(name), O.field(name))
+    return errs
+
+
+def test_fplane_workload_parity(gw):
+    """f-plane box (16 x 16 x 64), 1000 ray volumes, 20 steps of 300 s."""
+    w = synth.workload("fplane")
+    grid, params = w["grid"], w["params"]
+    rays = synth.fplane_rays(grid, 1000, tag=11)
+    T, O = _pair(gw, grid, params, w["background"], 8192)
+    T.add_rays(rays)
+    O.add_rays(rays)
+    _compare_all(T, O, grid, fields=False)
+    for s in range(20):
+        du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
+        if s % 5 == 4:
+            _compare_all(T, O, grid, du, dv, odu, odv)
+    assert O.stats()["n_exited"] > 0
+
+
+@pytest.mark.parametrize("variant", ["direct", "pseudomomentum_gamma0"])
+def test_fplane_inhomogeneous_parity(gw, variant):
+    """f-plane with a smoothly perturbed background: refraction, splits, saturation on."""
+    grid = synth.fplane_grid(nx=24, ny=20, nz=40, dx=40e3, dy=30e3, dz=500.0)
+    bg = synth.perturbed(synth.uniform_background(grid, U=5.0), tag=21, rel=0.1)
+    params = dict(synth.DEFAULT_PARAMS, smoothing=1, saturation=1, cap_per_column=30)
+    if variant != "direct":
+        params.update(flux_form=1, gamma_mode=0)
+    rays = synth.fplane_rays(grid, 1500, tag=22, z_lo=3e3, z_hi=15e3, ext_z=1100.0)
+    rays["n"] = rays["n"] * 3e4
+    T, O = _pair(gw, grid, params, bg, 20000)
+    T.add_rays(rays)
+    O.add_rays(rays)
+    for s in range(12):
+        du, dv, odu, odv = _step_both(T, O, 240.0, grid["nz"], grid["ny"], grid["nx"])
+        if s % 4 == 3:
+            _compare_all(T, O, grid, du, dv, odu, odv)
+    st = O.stats()
+    assert st["n_split_v"] > 0 and st["w_saturated"] > 0 and st["n_capped"] > 0
+
+
+def test_sphere_parity_with_launches_caps_and_exits(gw):
+    """Sphere 40 x 20 x 24 with jets, two background launches, explicit ray volumes near the top,
+    saturation, smoothing, splitting and a per-column cap."""
+    grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+    bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+    params = dict(synth.DEFAULT_PARAMS, cap_per_column=45)
+    T, O = _pair(gw, grid, params, bg, 200000)
+    src = synth.background_source(z_launch=2e3)
+    T.launch_sources(src)
+    O.launch_background(src)
+    rays = synth.sphere_rays(grid, 777, tag=32, z_lo=14e3, z_hi=23.5e3, ext_scale=3.0)
+    rays["n"] = rays["n"] * 30.0
+    T.add_rays(rays)
+    O.add_rays(rays)
+    _compare_all(T, O, grid, fields=False)
+    for s in range(10):
+        if s == 5:
+            T.launch_sources(src)
+            O.launch_background(src)
+        du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
+        if s % 3 == 2 or s == 9:
+            _compare_all(T, O, grid, du, dv, odu, odv)
+    st = O.stats()
+    assert st["n_exited"] > 0 and st["n_capped"] > 0 and st["n_split_h"] > 0 and st["w_saturated"] > 0
+
+
+def test_spectral_launch_parity(gw):
+    """Explicit spectral launches (convective-like source) incl. filtered bins."""
+    grid = synth.sphere_grid(nx=36, ny=18, nz=30, dz=1000.0)
+    bg = synth.jet_background(grid, z_peak=20e3, z_width=8e3)
+    specs = synth.convective_specs(grid, tag=41, median=4.0, cap=20, z_launch=8e3)
+    specs["c"][::7] = 0.01     # w below |f|: filtered
+    T, O = _pair(gw, grid, dict(synth.DEFAULT_PARAMS), bg, 100000)
+    T.launch_spectral(specs)
+    O.launch_spectral(specs)
+    assert T.stats()["n_filtered"] == O.stats()["n_filtered"] > 0
+    for _ in range(4):
+        du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
+    _compare_all(T, O, grid, du, dv, odu, odv)
+
+
+def test_full_size_sphere_launch_and_step(gw):
+    """The benchmark configuration: 256 x 128 x 90, background source (983 040 ray volumes),
+    one full step of 180 s, compared in full (state, counters, tendencies, fields)."""
+    w = synth.workload("sphere")
+    grid = w["grid"]
+    T, O = _pair(gw, grid, w["params"], w["background"], 2_500_000)
+    T.launch_sources(w["source"])
+    O.launch_background(w["source"])
+    assert T.stats()["n_launched"] == O.stats()["n_launched"] == 120 * 256 * 32
+    _compare_all(T, O, grid, fields=False)
+    du, dv, odu, odv = _step_both(T, O, w["dt"], grid["nz"], grid["ny"], grid["nx"])
+    _compare_all(T, O, grid, du, dv, odu, odv)
+
+
+def test_full_size_sampled_rays_over_several_steps(gw):
+    """Full-size run for 5 steps on the GPU; sampled ray volumes that neither split nor left are
+    advanced one by one from the oracle's own launch state with the oracle's single-ray RK3."""
+    w = synth.workload("sphere")
+    grid = w["grid"]
+    T, O = _pair(gw, grid, dict(w["params"], splitting=0), w["background"], 2_500_000)
+    T.launch_sources(w["source"])
+    O.launch_background(w["source"])
+    r0 = O.rays()
+    for _ in range(5):
+        T.step(w["dt"])
+    g = T.rays()
+    pos = {int(i): q for q, i in enumerate(g["id"])}
+    rng = np.random.default_rng(5)
+    sample = rng.choice(len(r0["id"]), size=600, replace=False)
+    checked = 0
+    for q in sample:
+        s = np.array([r0[n][q] for n in oracle.STATE_NAMES])
+        for _ in range(5):
+            s = O.advance_ray(s, w["dt"])
+        i = int(r0["id"][q])
+        if i not in pos:
+            continue
+        p = pos[i]
+        got = np.array([g[n][p] for n in oracle.STATE_NAMES])
+        d = got - s
+        d[0] = (d[0] + math.pi) % (2 * math.pi) - math.pi
+        scale = np.maximum(np.abs(s), 1e-300)
+        # per-ray relative error; k, l near zero measured against |k_h|
+        kh = math.hypot(s[3], s[4])
+        scale[3] = scale[4] = kh
+        scale[0] = 2 * math.pi
+        assert np.all(np.abs(d) <= 1e-9 * scale), (i, d / scale)
+        checked += 1
+    assert checked > 500
+    # saturation sink and budget closure at full size (W after = W0 + launched - sinks)
+    st = T.stats()
+    rhs = st["w_launched"] - st["w_saturated"] - st["w_exited"] - st["w_capped"] - st["w_invalid"]
+    assert st["w_total"] == pytest.approx(rhs, rel=1e-12)
+
+
+def test_deterministic_ray_state(gw):
+    grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+    bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+    outs = []
+    for _ in range(2):
+        T, _ = _pair(gw, grid, dict(synth.DEFAULT_PARAMS), bg, 200000)
+        T.launch_sources(synth.background_source(z_launch=2e3))
+        for _ in range(6):
+            T.step(300.0)
+        outs.append((T.rays(), T.stats()))
+    for n in ("id", "cell") + tuple(oracle.STATE_NAMES):
+        np.testing.assert_array_equal(outs[0][0][n], outs[1][0][n])
+    assert outs[0][1] == outs[1][1]
+
+
+def test_edge_cases(gw):
+    import torch
+    grid = synth.fplane_grid(nx=8, ny=8, nz=16)
+    bg = synth.uniform_background(grid)
+    params = dict(synth.DEFAULT_PARAMS, saturation=0, smoothing=0)
+    # step before any background
+    T = gw.Tracer(grid, params, max_rays=100)
+    with pytest.raises(gw.GwamError) as e:
+        T.step(10.0)
+    assert e.value.code == gw.GWAM_ESTATE
+    # empty population: a step is valid and yields zero tendencies
+    dev = [torch.from_numpy(a.copy()).cuda() for a in bg]
+    T.set_background(*dev)
+    du = torch.ones((16, 8, 8), dtype=torch.float64, device="cuda")
+    dv = torch.ones_like(du)
+    T.step(10.0, du, dv)
+    assert float(du.abs().max()) == 0.0 and T.num_rays() == 0
+    # invalid dt
+    with pytest.raises(gw.GwamError) as e:
+        T.step(0.0)
+    assert e.value.code == gw.GWAM_EINVAL
+    # a ray outside the domain is rejected and nothing is added
+    r = synth.fplane_rays(grid, 5, tag=3)
+    r["z"][2] = 1e9
+    with pytest.raises(gw.GwamError) as e:
+        T.add_rays(r)
+    assert e.value.code == gw.GWAM_EINVAL and T.num_rays() == 0
+    # capacity: more ray volumes than max_rays
+    with pytest.raises(gw.GwamError) as e:
+        T.add_rays(synth.fplane_rays(grid, 101, tag=4))
+    assert e.value.code == gw.GWAM_ECAPACITY
+    # a bad background is refused
+    bad = [a.copy() for a in bg]
+    bad[3][3, 2, 1] = -1.0
+    with pytest.raises(gw.GwamError) as e:
+        T.set_background(*[torch.from_numpy(a).cuda() for a in bad])
+    assert e.value.code == gw.GWAM_ENUMERIC
+    bad = [a.copy() for a in bg]
+    bad[0][0, 0, 0] = np.nan
+    with pytest.raises(gw.GwamError) as e:
+        T.set_background(*bad)
+    assert e.value.code == gw.GWAM_ENUMERIC
+    # capacity reached inside a step (splits) is reported, not written past the buffers
+    T2 = gw.Tracer(grid, dict(params, splitting=1), max_rays=12)
+    T2.set_background(*dev)
+    r = synth.fplane_rays(grid, 10, tag=5, ext_z=2000.0)
+    T2.add_rays(r)
+    T2.step(10.0)
+    with pytest.raises(gw.GwamError) as e:
+        T2.stats()
+    assert e.value.code == gw.GWAM_ECAPACITY
+
+
+def test_host_entry_points_match_device_ones(gw):
+    """gwam_set_background_host / gwam_step_host (host buffers) give the device-path results."""
+    import torch
+    w = synth.workload("fplane")
+    grid, params = w["grid"], w["params"]
+    rays = synth.fplane_rays(grid, 300, tag=12)
+    outs = []
+    for host in (False, True):
+        T = gw.Tracer(grid, params, max_rays=4096)
+        if host:
+            T.set_background(*w["background"])
+        else:
+            T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in w["background"]])
+        T.add_rays(rays)
+        shape = (grid["nz"], grid["ny"], grid["nx"])
+        if host:
+            du, dv = np.zeros(shape), np.zeros(shape)
+            for _ in range(3):
+                T.step_host(300.0, du, dv)
+        else:
+            dud = torch.zeros(shape, dtype=torch.float64, device="cuda")
+            dvd = torch.zeros_like(dud)
+            for _ in range(3):
+                T.step(300.0, dud, dvd)
+            du, dv = dud.cpu().numpy(), dvd.cpu().numpy()
+        outs.append((T.rays(), du, dv))
+    for n in oracle.STATE_NAMES:
+        np.testing.assert_array_equal(outs[0][0][n], outs[1][0][n])
+    assert level_error(outs[1][1], outs[0][1]) <= 1e-12
