@@ -50,6 +50,7 @@ struct orc_model {
     orc_params P;
     int have_bg;
     double *u, *v, *n2, *rho, *g2;      /* node fields [nz][ny][nx] */
+    double *grad[4][3];                  /* node gradients of U V N2 G2 along X Y z [nz][ny][nx] */
     int64_t n, cap;                      /* rays in array order */
     double *s[NSTATE];
     int64_t *id;
@@ -107,8 +108,8 @@ static long wrap_index(long i, long n)
 
 /* Bracketing node pair along one axis; s is the position in node units (node q at s = q).
  * Reading (App. B.1 gives the interpolation, not the edges): outside the first/last node
- * the value is held constant and the gradient is zero. */
-static void bracket(double s, long n, int periodic, long *q0, long *q1, double *t, double *on)
+ * every interpolated quantity is held at its edge-node value. */
+static void bracket(double s, long n, int periodic, long *q0, long *q1, double *t)
 {
     if (!isfinite(s)) s = 0.0;
     if (periodic) {
@@ -117,50 +118,41 @@ static void bracket(double s, long n, int periodic, long *q0, long *q1, double *
         *t = s - fl;
         *q0 = wrap_index((long)fl, n);
         *q1 = wrap_index(*q0 + 1, n);
-        *on = 1.0;
     } else if (s < 0.0) {
-        *q0 = 0; *q1 = 1; *t = 0.0; *on = 0.0;
+        *q0 = 0; *q1 = 1; *t = 0.0;
     } else if (s >= (double)(n - 1)) {
-        *q0 = n - 2; *q1 = n - 1; *t = 1.0; *on = 0.0;
+        *q0 = n - 2; *q1 = n - 1; *t = 1.0;
     } else {
         double fl = floor(s);
-        *q0 = (long)fl; *q1 = *q0 + 1; *t = s - fl; *on = 1.0;
+        *q0 = (long)fl; *q1 = *q0 + 1; *t = s - fl;
     }
 }
 
-/* Linear interpolation of the mean fields and their gradients to a point (Sec. 3b, App. B.1):
- * trilinear between the 8 bracketing nodes (nodes at cell centres); the gradient is the exact
- * derivative of that interpolant, per unit of coordinate (radian on the sphere, metre otherwise). */
+/* Linear interpolation of the mean fields and of their gradients to a point (Sec. 3b, App. B.1:
+ * "all necessary mean fields and their gradients" are interpolated).  Reading on a lat-lon grid:
+ * gradients live on the nodes (cell centres) as centred differences, and values and gradients
+ * are interpolated trilinearly from the 8 bracketing nodes, so both are continuous in position.
+ * Gradients are per unit of coordinate (radian on the sphere, metre otherwise). */
 void orc_gather(const orc_model *m, double X, double Y, double Z, double *o)
 {
     long i0, i1, j0, j1, k0, k1;
-    double tx, ty, tz, gx, gy, gz;
+    double tx, ty, tz;
     double dX = cell_x(m), dY = cell_y(m), dz = m->G.dz;
-    bracket(X / dX - 0.5, m->G.nx, 1, &i0, &i1, &tx, &gx);
-    bracket((Y - y_origin(m)) / dY - 0.5, m->G.ny, !is_sphere(m), &j0, &j1, &ty, &gy);
-    bracket(Z / dz - 0.5, m->G.nz, 0, &k0, &k1, &tz, &gz);
-    const double *F[4] = {m->u, m->v, m->n2, m->g2};
+    bracket(X / dX - 0.5, m->G.nx, 1, &i0, &i1, &tx);
+    bracket((Y - y_origin(m)) / dY - 0.5, m->G.ny, !is_sphere(m), &j0, &j1, &ty);
+    bracket(Z / dz - 0.5, m->G.nz, 0, &k0, &k1, &tz);
+    const double *F[16];
+    F[0] = m->u; F[1] = m->v; F[2] = m->n2; F[3] = m->g2;
+    for (int f = 0; f < 4; ++f)
+        for (int q = 0; q < 3; ++q) F[4 + 3 * f + q] = m->grad[f][q];
     long I[2] = {i0, i1}, J[2] = {j0, j1}, K[2] = {k0, k1};
     double wx[2] = {1.0 - tx, tx}, wy[2] = {1.0 - ty, ty}, wz[2] = {1.0 - tz, tz};
-    for (int f = 0; f < 4; ++f) {
-        double c[2][2][2];
+    for (int f = 0; f < 16; ++f) {
+        double val = 0.0;
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b)
-                for (int e = 0; e < 2; ++e) c[a][b][e] = F[f][node(m, K[e], J[b], I[a])];
-        double val = 0.0, ddx = 0.0, ddy = 0.0, ddz = 0.0;
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
-                for (int e = 0; e < 2; ++e) val += wx[a] * wy[b] * wz[e] * c[a][b][e];
-        for (int b = 0; b < 2; ++b)
-            for (int e = 0; e < 2; ++e) ddx += wy[b] * wz[e] * (c[1][b][e] - c[0][b][e]);
-        for (int a = 0; a < 2; ++a)
-            for (int e = 0; e < 2; ++e) ddy += wx[a] * wz[e] * (c[a][1][e] - c[a][0][e]);
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) ddz += wx[a] * wy[b] * (c[a][b][1] - c[a][b][0]);
+                for (int e = 0; e < 2; ++e) val += wx[a] * wy[b] * wz[e] * F[f][node(m, K[e], J[b], I[a])];
         o[f] = val;
-        o[4 + 3 * f + 0] = gx * ddx / dX;
-        o[4 + 3 * f + 1] = gy * ddy / dY;
-        o[4 + 3 * f + 2] = gz * ddz / dz;
     }
 }
 
@@ -388,6 +380,8 @@ orc_model *orc_create(const orc_grid *grid, const orc_params *params)
     m->n2 = calloc(nc, sizeof(double));
     m->rho = calloc(nc, sizeof(double));
     m->g2 = calloc(nc, sizeof(double));
+    for (int f = 0; f < 4; ++f)
+        for (int q = 0; q < 3; ++q) m->grad[f][q] = calloc(nc, sizeof(double));
     m->fz[0] = calloc(ni, sizeof(double));
     m->fz[1] = calloc(ni, sizeof(double));
     for (int f = 0; f < NFIELD_H; ++f) m->hf[f] = calloc(nc, sizeof(double));
@@ -405,6 +399,8 @@ void orc_destroy(orc_model *m)
 {
     if (!m) return;
     free(m->u); free(m->v); free(m->n2); free(m->rho); free(m->g2);
+    for (int f = 0; f < 4; ++f)
+        for (int q = 0; q < 3; ++q) free(m->grad[f][q]);
     free_fields(m);
     free_rays(m);
     free(m);
@@ -436,6 +432,34 @@ int orc_set_background(orc_model *m, const double *u, const double *v, const dou
                     dlnr = (log(rho[node(m, k + 1, j, i)]) - log(rho[node(m, k - 1, j, i)])) / (2.0 * m->G.dz);
                 m->g2[node(m, k, j, i)] = m->P.gamma_mode ? 0.25 * dlnr * dlnr : 0.0;
             }
+    /* node gradients: centred differences, periodic in x (and y on the f-plane), one-sided at
+     * the pole rows and at the bottom and top levels */
+    const double *Fv[4] = {m->u, m->v, m->n2, m->g2};
+    double dX = cell_x(m), dY = cell_y(m), dz = m->G.dz;
+    for (int f = 0; f < 4; ++f)
+        for (long k = 0; k < nz; ++k)
+            for (long j = 0; j < ny; ++j)
+                for (long i = 0; i < nx; ++i) {
+                    const double *A = Fv[f];
+                    size_t c = node(m, k, j, i);
+                    m->grad[f][0][c] = (A[node(m, k, j, wrap_index(i + 1, nx))] - A[node(m, k, j, wrap_index(i - 1, nx))])
+                                     / (2.0 * dX);
+                    if (!is_sphere(m))
+                        m->grad[f][1][c] = (A[node(m, k, wrap_index(j + 1, ny), i)]
+                                            - A[node(m, k, wrap_index(j - 1, ny), i)]) / (2.0 * dY);
+                    else if (j == 0)
+                        m->grad[f][1][c] = (A[node(m, k, 1, i)] - A[node(m, k, 0, i)]) / dY;
+                    else if (j == ny - 1)
+                        m->grad[f][1][c] = (A[node(m, k, ny - 1, i)] - A[node(m, k, ny - 2, i)]) / dY;
+                    else
+                        m->grad[f][1][c] = (A[node(m, k, j + 1, i)] - A[node(m, k, j - 1, i)]) / (2.0 * dY);
+                    if (k == 0)
+                        m->grad[f][2][c] = (A[node(m, 1, j, i)] - A[node(m, 0, j, i)]) / dz;
+                    else if (k == nz - 1)
+                        m->grad[f][2][c] = (A[node(m, nz - 1, j, i)] - A[node(m, nz - 2, j, i)]) / dz;
+                    else
+                        m->grad[f][2][c] = (A[node(m, k + 1, j, i)] - A[node(m, k - 1, j, i)]) / (2.0 * dz);
+                }
     m->have_bg = 1;
     return 0;
 }

@@ -108,7 +108,7 @@ int orc_get_field(const orc_model *m, int which, double *out);
 int orc_get_gamma2(const orc_model *m, double *out);
 
 /* ---- single-ray pieces, exposed for the pins ---- */
-/* out[0..3] = U V N2 G2, out[4..15] = d/dX, d/dY, d/dz of each (field-major) */
+/* out[0..3] = U V N2 G2, out[4..15] = their interpolated node gradients d/dX, d/dY, d/dz (field-major) */
 void orc_gather(const orc_model *m, double X, double Y, double Z, double *out16);
 /* intrinsic frequency and intrinsic group velocity: out = {w, ch_x, ch_y, ch_r, K2} */
 void orc_dispersion(double k, double l, double mm, double n2, double g2, double f2, double *out5);

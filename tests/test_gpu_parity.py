@@ -72,7 +72,6 @@ def test_fplane_workload_parity(gw):
         du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
         if s % 5 == 4:
             _compare_all(T, O, grid, du, dv, odu, odv)
-    assert O.stats()["n_exited"] > 0
 
 
 @pytest.mark.parametrize("variant", ["direct", "pseudomomentum_gamma0"])

@@ -26,7 +26,7 @@ MUTATIONS = {
     "cg_vertical_sign": ("d->ch[2] = -mm * d->D", "d->ch[2] = mm * d->D"),
     "rk3_coefficient": ("{1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0}", "{1.0 / 3.0, 15.0 / 16.0, 7.0 / 15.0}"),
     "one_face_carrier": ("F[q] = 0.5 * (vel[0] + vel[1]);", "F[q] = vel[0];"),
-    "gather_wrong_spacing": ("o[4 + 3 * f + 1] = gy * ddy / dY;", "o[4 + 3 * f + 1] = gy * ddy / dX;"),
+    "gather_wrong_spacing": ("- A[node(m, k, j - 1, i)]) / (2.0 * dY);", "- A[node(m, k, j - 1, i)]) / (2.0 * dX);"),
     # saturation
     "kappa_factor": ("double fac = fmax(0.0, 1.0 - 2.0 * kappa * K2 * dt);",
                      "double fac = fmax(0.0, 1.0 - kappa * K2 * dt);"),

@@ -140,6 +140,20 @@ def _sphere_bg(grid):
     return u, v, n2, rho
 
 
+def _sphere_linear_bg(grid):
+    """Linear in lambda, phi and z (exactly represented by the interpolated node gradients away
+    from the periodic seam); density exp(-z sqrt(g0 + g1 phi)) so that Gamma^2 = (g0 + g1 phi)/4
+    is linear in phi as well."""
+    x, y, z = synth.node_coords(grid)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    u = 5.0 + 3.0 * X + 20.0 * Y + 1e-3 * Z
+    v = -2.0 + 1.5 * X - 10.0 * Y - 5e-4 * Z
+    n2 = 4e-4 + 1e-5 * X + 2e-5 * Y + 1e-9 * Z
+    g0 = 1.0 / 7000.0 ** 2
+    rho = 1.2 * np.exp(-Z * np.sqrt(g0 * (1.0 + 0.3 * Y)))
+    return u, v, n2, rho
+
+
 def _canonical(M, a):
     """Hamiltonian in canonical coordinates (lambda, phi, r, p_lambda = r cos(phi) k, p_phi = r l, p_r = m)."""
     def H(q):
@@ -163,13 +177,13 @@ def test_spherical_ray_equations_are_hamiltonian():
     """Eq. eikonal-sphere:1-3 with their metric terms equal Hamilton's equations in canonical
     momenta (r cos(phi) k_lambda, r k_phi, k_r), checked by finite differences of Omega."""
     grid = synth.sphere_grid(nx=64, ny=40, nz=30, dz=1000.0)
-    M = model(grid, bg=_sphere_bg(grid))
+    M = model(grid, bg=_sphere_linear_bg(grid))
     a = grid["radius"]
     H = _canonical(M, a)
     g = np.random.default_rng(22)
     dlam, dphi = 2 * math.pi / 64, math.pi / 40
     for _ in range(20):
-        lam = (g.integers(0, 64) + g.uniform(0.6, 1.4)) * dlam
+        lam = (g.integers(2, 60) + g.uniform(0.6, 1.4)) * dlam
         phi = -0.5 * math.pi + (g.integers(6, 32) + g.uniform(0.6, 1.4)) * dphi
         r = a + (g.integers(3, 25) + g.uniform(0.6, 1.4)) * 1000.0
         k, l = 2 * math.pi / 3e5 * g.normal(size=2)
@@ -201,7 +215,7 @@ def test_phase_space_velocity_is_divergence_free():
         assert abs(d_pos + d_wav) <= 1e-6 * (abs(d_pos) + abs(d_wav)) + 1e-20
     # sphere, canonical coordinates
     gs = synth.sphere_grid(nx=64, ny=40, nz=30, dz=1000.0)
-    Ms = model(gs, bg=_sphere_bg(gs))
+    Ms = model(gs, bg=_sphere_linear_bg(gs))
     a = gs["radius"]
     q0 = np.array([1.1, 0.4, a + 12345.0, 0.0, 0.0, -1.5e-3])
     q0[3] = q0[2] * math.cos(q0[1]) * 2e-5
@@ -342,7 +356,7 @@ def test_great_circles_in_a_uniform_atmosphere_at_rest():
 
 def test_steady_background_conserves_frequency():
     """Steady background: the Hamiltonian Omega = k.U + w is constant along rays (third order)."""
-    grid = synth.fplane_grid(nx=40, ny=40, nz=40, dz=500.0, f0=1e-4)
+    grid = synth.fplane_grid(nx=56, ny=56, nz=40, dz=500.0, f0=1e-4)
     M = model(grid, bg=linear_background(grid))
     y0 = [20.3 * grid["dx"], 19.6 * grid["dy"], 15.2 * grid["dz"], 2 * math.pi / 2e5, -2 * math.pi / 4e5,
           -2 * math.pi / 3e3, 0.0, 0.0, 0.0]
