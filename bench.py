@@ -158,10 +158,10 @@ def gpu_arm(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = synth.workload("sphere")
+    w = synth.workload(args.workload)
     grid, params = w["grid"], w["params"]
     nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
-    T = gwam.Tracer(grid, params, max_rays=2_500_000)
+    T = gwam.Tracer(grid, params, max_rays=int(2.5 * 32 * nx * ny))
     bg_dev = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in w["background"]]
     T.set_background(*bg_dev)
     T.launch_sources(w["source"])
@@ -251,7 +251,7 @@ def gpu_arm(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "rays_live_start": s0["n_live"], "rays_live_end": s1["n_live"],
+            "config": {"workload": WORKLOAD if args.workload == "sphere" else args.workload, "rays_live_start": s0["n_live"], "rays_live_end": s1["n_live"],
                        "ray_steps_timed": ray_steps, "l2": "working set > L2 (ray state ~0.12-0.24 GB + "
                        "grid fields ~0.4 GB per step), no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "gpu_launches": None,
@@ -287,6 +287,8 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "sphere_half"],
+                    help="sphere_half: the same physics on 128 x 64 columns (profiling captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

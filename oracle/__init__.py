@@ -96,6 +96,8 @@ def _declare(lib):
     lib.orc_get_stats.argtypes = [C.c_void_p, _P(Stats)]
     lib.orc_get_field.argtypes = [C.c_void_p, C.c_int, _D]
     lib.orc_get_gamma2.argtypes = [C.c_void_p, _D]
+    lib.orc_get_field_abs.argtypes = [C.c_void_p, C.c_int, _D]
+    lib.orc_tendency_scale.argtypes = [C.c_void_p, _D, _D]
     lib.orc_gather.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D]
     lib.orc_dispersion.argtypes = [C.c_double] * 6 + [_D]
     lib.orc_rhs.argtypes = [C.c_void_p, _D, _D]
@@ -260,6 +262,22 @@ class Model:
         out = np.zeros((nl, self.ny, self.nx))
         self._lib.orc_get_field(self._h, which, _dp(out))
         return out
+
+    def field_abs(self, name: str) -> np.ndarray:
+        """Sum of |contribution| of a projected field (the scale of its rounding error)."""
+        which = FIELD_NAMES.index(name)
+        nl = self.nz + 1 if which < 2 else self.nz
+        out = np.zeros((nl, self.ny, self.nx))
+        self._lib.orc_get_field_abs(self._h, which, _dp(out))
+        return out
+
+    def tendency_scale(self):
+        """Error scales of du/dt and dv/dt of the last step (magnitudes through the divergence)."""
+        shape = (self.nz, self.ny, self.nx)
+        du = np.zeros(shape)
+        dv = np.zeros(shape)
+        self._lib.orc_tendency_scale(self._h, _dp(du), _dp(dv))
+        return du, dv
 
     def gamma2(self) -> np.ndarray:
         out = np.zeros((self.nz, self.ny, self.nx))

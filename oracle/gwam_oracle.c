@@ -59,6 +59,7 @@ struct orc_model {
     orc_stats st;
     double *fz[2];                       /* vertical fluxes at level interfaces [nz+1][ny][nx] */
     double *hf[NFIELD_H];                /* F_ll F_lp F_pl F_pp E_l E_p wave-action density [nz][ny][nx] */
+    double *fzabs[2], *hfabs[NFIELD_H];  /* sums of |contribution| of the same fields (error scales) */
 };
 
 /* ------------------------------------------------------------------ geometry */
@@ -361,7 +362,11 @@ static int32_t cell_of(const orc_model *m, const double *s)
 static void free_fields(orc_model *m)
 {
     free(m->fz[0]); free(m->fz[1]);
-    for (int f = 0; f < NFIELD_H; ++f) free(m->hf[f]);
+    free(m->fzabs[0]); free(m->fzabs[1]);
+    for (int f = 0; f < NFIELD_H; ++f) {
+        free(m->hf[f]);
+        free(m->hfabs[f]);
+    }
 }
 
 orc_model *orc_create(const orc_grid *grid, const orc_params *params)
@@ -384,7 +389,12 @@ orc_model *orc_create(const orc_grid *grid, const orc_params *params)
         for (int q = 0; q < 3; ++q) m->grad[f][q] = calloc(nc, sizeof(double));
     m->fz[0] = calloc(ni, sizeof(double));
     m->fz[1] = calloc(ni, sizeof(double));
-    for (int f = 0; f < NFIELD_H; ++f) m->hf[f] = calloc(nc, sizeof(double));
+    m->fzabs[0] = calloc(ni, sizeof(double));
+    m->fzabs[1] = calloc(ni, sizeof(double));
+    for (int f = 0; f < NFIELD_H; ++f) {
+        m->hf[f] = calloc(nc, sizeof(double));
+        m->hfabs[f] = calloc(nc, sizeof(double));
+    }
     return m;
 }
 
@@ -917,7 +927,12 @@ static void project(orc_model *m)
     size_t nc = (size_t)nx * ny * nz, ni = (size_t)nx * ny * (nz + 1);
     memset(m->fz[0], 0, ni * sizeof(double));
     memset(m->fz[1], 0, ni * sizeof(double));
-    for (int f = 0; f < NFIELD_H; ++f) memset(m->hf[f], 0, nc * sizeof(double));
+    memset(m->fzabs[0], 0, ni * sizeof(double));
+    memset(m->fzabs[1], 0, ni * sizeof(double));
+    for (int f = 0; f < NFIELD_H; ++f) {
+        memset(m->hf[f], 0, nc * sizeof(double));
+        memset(m->hfabs[f], 0, nc * sizeof(double));
+    }
     double dz = m->G.dz;
     for (int64_t q = 0; q < m->n; ++q) {
         double s[NSTATE], f2, n2, dk, dl, dm;
@@ -962,6 +977,8 @@ static void project(orc_model *m)
         m->hf[4][c] += alpha * e_l;
         m->hf[5][c] += alpha * e_p;
         m->hf[6][c] += alpha * A;
+        double hv[NFIELD_H] = {t_ll, t_lp, t_pl, t_pp, e_l, e_p, A};
+        for (int f = 0; f < NFIELD_H; ++f) m->hfabs[f][c] += fabs(alpha * hv[f]);
         /* vertical fluxes at the cell interfaces z = kk dz, 1 <= kk <= nz-1: integrate over the
          * staggered cell [(kk - 1/2) dz, (kk + 1/2) dz] of the carrier column; the weight is the
          * horizontal share times the vertical overlap share.  Reading: F^z = 0 at z = 0, z_top. */
@@ -980,6 +997,8 @@ static void project(orc_model *m)
             size_t ci = ((size_t)kk2 * ny + (size_t)j) * nx + (size_t)i;
             m->fz[0][ci] += w * z_l;
             m->fz[1][ci] += w * z_p;
+            m->fzabs[0][ci] += fabs(w * z_l);
+            m->fzabs[1][ci] += fabs(w * z_p);
         }
     }
 }
@@ -1010,6 +1029,18 @@ int orc_smooth(const orc_model *m, double *fld, int nlev)
     }
     free(tmp);
     return 0;
+}
+
+static void smooth_all(orc_model *m)
+{
+    for (int q = 0; q < 2; ++q) {
+        orc_smooth(m, m->fz[q], m->G.nz + 1);
+        orc_smooth(m, m->fzabs[q], m->G.nz + 1);
+    }
+    for (int f = 0; f < NFIELD_H; ++f) {
+        orc_smooth(m, m->hf[f], m->G.nz);
+        orc_smooth(m, m->hfabs[f], m->G.nz);
+    }
 }
 
 /* Eq. mean-flow-impact: du/dt = -(1/rho) div(rho <v'u'>) + (f/g) e_r x <u'b'>.
@@ -1067,6 +1098,59 @@ int orc_divergence(const orc_model *m, const double *fz_l, const double *fz_p,
                 dvdt[c] = -div_v / rho + e_p[c] / (m->G.g * rho);
             }
     return 0;
+}
+
+/* Error scale of the tendencies: the divergence formula applied to the sums of |contribution|
+ * with every term taken in magnitude.  Test infrastructure: rounding of the sums is bounded by
+ * a small multiple of the machine epsilon times this. */
+int orc_tendency_scale(const orc_model *m, double *du_s, double *dv_s)
+{
+    long nx = m->G.nx, ny = m->G.ny, nz = m->G.nz;
+    double dX = cell_x(m), dY = cell_y(m), dz = m->G.dz;
+    const double *A[2][4] = {{m->hfabs[0], m->hfabs[2], m->fzabs[0], m->hfabs[4]},
+                             {m->hfabs[1], m->hfabs[3], m->fzabs[1], m->hfabs[5]}};
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                size_t c = node(m, k, j, i);
+                size_t ce = node(m, k, j, wrap_index(i + 1, nx)), cw = node(m, k, j, wrap_index(i - 1, nx));
+                double hx = 1.0, hy = 1.0, cn = 1.0, cs = 1.0;
+                long jn = j + 1, js = j - 1;
+                if (is_sphere(m)) {
+                    double r = m->G.radius + (k + 0.5) * dz, cphi = cos(row_lat(m, j));
+                    hx = r * cphi;
+                    hy = r * cphi;
+                    cn = jn < ny ? cos(row_lat(m, jn)) : 0.0;
+                    cs = js >= 0 ? cos(row_lat(m, js)) : 0.0;
+                } else {
+                    jn = wrap_index(jn, ny);
+                    js = wrap_index(js, ny);
+                }
+                for (int q = 0; q < 2; ++q) {
+                    double yn = (jn >= 0 && jn < ny) ? A[q][1][node(m, k, jn, i)] : 0.0;
+                    double ys = (js >= 0 && js < ny) ? A[q][1][node(m, k, js, i)] : 0.0;
+                    double v = (A[q][0][ce] + A[q][0][cw]) / (2.0 * dX * hx) + (cn * yn + cs * ys) / (2.0 * dY * hy)
+                             + (A[q][2][((size_t)(k + 1) * ny + j) * nx + i] + A[q][2][((size_t)k * ny + j) * nx + i]) / dz;
+                    v = v / m->rho[c] + A[q][3][c] / (m->G.g * m->rho[c]);
+                    (q == 0 ? du_s : dv_s)[c] = v;
+                }
+            }
+    return 0;
+}
+
+/* sums of |contribution| of field `which` (layout as orc_get_field) */
+int orc_get_field_abs(const orc_model *m, int which, double *out)
+{
+    size_t nc = (size_t)m->G.nx * m->G.ny * m->G.nz, ni = (size_t)m->G.nx * m->G.ny * (m->G.nz + 1);
+    if (which == 0 || which == 1) {
+        memcpy(out, m->fzabs[which], ni * sizeof(double));
+        return 0;
+    }
+    if (which >= 2 && which < 2 + NFIELD_H) {
+        memcpy(out, m->hfabs[which - 2], nc * sizeof(double));
+        return 0;
+    }
+    return -1;
 }
 
 int orc_get_field(const orc_model *m, int which, double *out)
@@ -1140,11 +1224,7 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
     if (m->P.saturation) apply_saturation(m, dt);
     /* 5. projection, smoothing, divergence */
     project(m);
-    if (m->P.smoothing) {
-        orc_smooth(m, m->fz[0], m->G.nz + 1);
-        orc_smooth(m, m->fz[1], m->G.nz + 1);
-        for (int f = 0; f < NFIELD_H; ++f) orc_smooth(m, m->hf[f], m->G.nz);
-    }
+    if (m->P.smoothing) smooth_all(m);
     size_t nc = (size_t)m->G.nx * m->G.ny * m->G.nz;
     double *du = dudt ? dudt : malloc(nc * sizeof(double));
     double *dv = dvdt ? dvdt : malloc(nc * sizeof(double));
@@ -1170,11 +1250,7 @@ int orc_diagnose(orc_model *m, double *dudt, double *dvdt)
     if (!m->have_bg) return -1;
     sort_rays(m);
     project(m);
-    if (m->P.smoothing) {
-        orc_smooth(m, m->fz[0], m->G.nz + 1);
-        orc_smooth(m, m->fz[1], m->G.nz + 1);
-        for (int f = 0; f < NFIELD_H; ++f) orc_smooth(m, m->hf[f], m->G.nz);
-    }
+    if (m->P.smoothing) smooth_all(m);
     if (dudt && dvdt)
         orc_divergence(m, m->fz[0], m->fz[1], m->hf[0], m->hf[1], m->hf[2], m->hf[3], m->hf[4], m->hf[5],
                        dudt, dvdt);

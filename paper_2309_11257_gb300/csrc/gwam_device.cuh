@@ -67,11 +67,14 @@ __device__ __forceinline__ void store_ray(const RaySoA& R, int64_t i, const doub
     R.a[6][i] = make_double2(s[SN], __longlong_as_double(id));
 }
 
-// Background nodes at cell centres, column-major: node (i, j, k) at (j*nx + i)*nz + k,
-// each node 32 bytes (U, V, N^2, Gamma^2).
-struct __align__(32) Node {
-    double x, y, z, w;   // U, V, N^2, Gamma^2
+// Background nodes at cell centres, column-major: node (i, j, k) at (j*nx + i)*nz + k.
+// Each node holds U, V, N^2, Gamma^2 and their gradients along X, Y, z (centred differences),
+// 128 bytes: the quantities the ray equations interpolate (Sec. 3b, App. B.1).
+struct __align__(128) Node {
+    double v[4];       // U, V, N^2, Gamma^2
+    double d[4][3];    // d/dX, d/dY, d/dz of each
 };
+
 __host__ __device__ __forceinline__ int64_t node_index(const Grid& G, int i, int j, int k)
 {
     return ((int64_t)j * G.nx + i) * G.nz + k;
@@ -101,73 +104,63 @@ __device__ __forceinline__ void bracket_periodic(double s, int n, int& q0, int& 
     q1 = q0 + 1 == n ? 0 : q0 + 1;
 }
 
-// clamped bracketing: constant value, zero gradient outside the first/last node
-__device__ __forceinline__ void bracket_clamped(double s, int n, int& q0, int& q1, double& t, double& on)
+// clamped bracketing: every interpolated quantity held at its edge-node value outside
+__device__ __forceinline__ void bracket_clamped(double s, int n, int& q0, int& q1, double& t)
 {
     if (!isfinite(s)) s = 0.0;
     if (s < 0.0) {
-        q0 = 0; q1 = 1; t = 0.0; on = 0.0;
+        q0 = 0; q1 = 1; t = 0.0;
     } else if (s >= (double)(n - 1)) {
-        q0 = n - 2; q1 = n - 1; t = 1.0; on = 0.0;
+        q0 = n - 2; q1 = n - 1; t = 1.0;
     } else {
         double fl = floor(s);
-        q0 = (int)fl; q1 = q0 + 1; t = s - fl; on = 1.0;
+        q0 = (int)fl; q1 = q0 + 1; t = s - fl;
     }
 }
 
-__device__ __forceinline__ Node ldg4(const Node* __restrict__ p)
+__device__ __forceinline__ void accumulate_node(const Node* __restrict__ p, double w, double* acc)
 {
     const double2* q = reinterpret_cast<const double2*>(p);
-    const double2 a = __ldg(q), b = __ldg(q + 1);
-    return Node{a.x, a.y, b.x, b.y};
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const double2 a = __ldg(q + e);
+        acc[2 * e] += w * a.x;
+        acc[2 * e + 1] += w * a.y;
+    }
 }
 
-// Trilinear interpolation of the node fields and of their gradients (exact derivative of the
-// interpolant) to (X, Y, Z) -- the linear interpolation of Sec. 3b / App. B.1.
-__device__ __forceinline__ void gather(const Grid& G, const Node* __restrict__ bg, double X, double Y, double Z,
-                                       Bg& b)
+// Trilinear interpolation of the node values and node gradients to (X, Y, Z).
+__device__ __forceinline__ void gather(const Grid& G, const Node* __restrict__ bg, double X, double Y, double Z, Bg& b)
 {
     int i0, i1, j0, j1, k0, k1;
-    double tx, ty, tz, gy, gz;
+    double tx, ty, tz;
     bracket_periodic(X / G.dX - 0.5, G.nx, i0, i1, tx);
-    if (G.geometry == 1) {
-        bracket_clamped((Y - G.y0) / G.dY - 0.5, G.ny, j0, j1, ty, gy);
-    } else {
-        bracket_periodic(Y / G.dY - 0.5, G.ny, j0, j1, ty);
-        gy = 1.0;
-    }
-    bracket_clamped(Z / G.dz - 0.5, G.nz, k0, k1, tz, gz);
+    if (G.geometry == 1) bracket_clamped((Y - G.y0) / G.dY - 0.5, G.ny, j0, j1, ty);
+    else bracket_periodic(Y / G.dY - 0.5, G.ny, j0, j1, ty);
+    bracket_clamped(Z / G.dz - 0.5, G.nz, k0, k1, tz);
+    double acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+    const double ux = 1.0 - tx, uy = 1.0 - ty, uz = 1.0 - tz;
+    const int dk = k1 - k0;
     const Node* c00 = bg + node_index(G, i0, j0, k0);
     const Node* c10 = bg + node_index(G, i1, j0, k0);
     const Node* c01 = bg + node_index(G, i0, j1, k0);
     const Node* c11 = bg + node_index(G, i1, j1, k0);
-    const int dk = k1 - k0;
-    const Node a000 = ldg4(c00), a001 = ldg4(c00 + dk);
-    const Node a100 = ldg4(c10), a101 = ldg4(c10 + dk);
-    const Node a010 = ldg4(c01), a011 = ldg4(c01 + dk);
-    const Node a110 = ldg4(c11), a111 = ldg4(c11 + dk);
-    const double ux = 1.0 - tx, uy = 1.0 - ty, uz = 1.0 - tz;
-    const double sx = 1.0 / G.dX, sy = gy / G.dY, sz = gz / G.dz;
-    double c[8];
-#define GWAM_FIELD(F, f)                                                                                    \
-    c[0] = a000.F; c[1] = a001.F; c[2] = a010.F; c[3] = a011.F;                                           \
-    c[4] = a100.F; c[5] = a101.F; c[6] = a110.F; c[7] = a111.F;                                           \
-    {                                                                                                     \
-        /* along z at the four columns */                                                                 \
-        double z00 = uz * c[0] + tz * c[1], z01 = uz * c[2] + tz * c[3];                                  \
-        double z10 = uz * c[4] + tz * c[5], z11 = uz * c[6] + tz * c[7];                                  \
-        double y0v = uy * z00 + ty * z01, y1v = uy * z10 + ty * z11;                                      \
-        b.v[f] = ux * y0v + tx * y1v;                                                                     \
-        b.d[f][0] = sx * (y1v - y0v);                                                                     \
-        b.d[f][1] = sy * (ux * (z01 - z00) + tx * (z11 - z10));                                           \
-        double d00 = c[1] - c[0], d01 = c[3] - c[2], d10 = c[5] - c[4], d11 = c[7] - c[6];                \
-        b.d[f][2] = sz * (ux * (uy * d00 + ty * d01) + tx * (uy * d10 + ty * d11));                       \
+    accumulate_node(c00, ux * uy * uz, acc);
+    accumulate_node(c00 + dk, ux * uy * tz, acc);
+    accumulate_node(c10, tx * uy * uz, acc);
+    accumulate_node(c10 + dk, tx * uy * tz, acc);
+    accumulate_node(c01, ux * ty * uz, acc);
+    accumulate_node(c01 + dk, ux * ty * tz, acc);
+    accumulate_node(c11, tx * ty * uz, acc);
+    accumulate_node(c11 + dk, tx * ty * tz, acc);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        b.v[f] = acc[f];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) b.d[f][q] = acc[4 + 3 * f + q];
     }
-    GWAM_FIELD(x, 0)
-    GWAM_FIELD(y, 1)
-    GWAM_FIELD(z, 2)
-    GWAM_FIELD(w, 3)
-#undef GWAM_FIELD
 }
 
 // f^2 and d(f^2)/dphi (f = 2 Omega sin phi on the sphere, f0 on the f-plane)
@@ -354,7 +347,8 @@ __device__ __forceinline__ int cell_of(const Grid& G, const double s[NSTATE])
     return (j * G.nx + i) * G.nz + k;
 }
 
-__device__ __forceinline__ double row_lat(const Grid& G, int j) { return G.y0 + (j + 0.5) * G.dY; }
+// latitude of row j's centre, multiply then add (never contracted into an FMA)
+__device__ __forceinline__ double row_lat(const Grid& G, int j) { return __dadd_rn(G.y0, __dmul_rn(j + 0.5, G.dY)); }
 
 // Split decision (App. B.3): bit 0 vertical, bit 1 horizontal, bit 2 horizontal axis is y.
 __device__ __forceinline__ int split_code(const Grid& G, const Params& P, const double s[NSTATE])

@@ -39,7 +39,7 @@ __global__ void k_gamma_to_caller(Grid G, const Node* __restrict__ bg, double* _
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t col = t % G.ncol;
         const int lev = (int)(t / G.ncol);
-        dst[t] = bg[col * G.nz + lev].w;
+        dst[t] = bg[col * G.nz + lev].v[3];
     }
 }
 

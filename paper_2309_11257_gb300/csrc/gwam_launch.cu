@@ -12,7 +12,9 @@ namespace gwam {
 
 enum { BG_NONFINITE = 1, BG_RHO = 2, BG_N2F2 = 4 };
 
-// caller [nz][ny][nx] -> column-major nodes, transposed through shared memory (32 columns of a row)
+// caller [nz][ny][nx] -> column-major node values (U, V, N^2, Gamma^2) and rho, transposed through
+// shared memory (32 columns of a row per block); Gamma^2 = (d ln rho / dz)^2 / 4 by centred
+// differences of ln rho (one-sided at the bottom and top)
 __global__ void k_set_background(Grid G, int gamma_mode, const double* __restrict__ u, const double* __restrict__ v,
                                  const double* __restrict__ n2, const double* __restrict__ rho, Node* __restrict__ bg,
                                  double* __restrict__ rho_c, int* flags)
@@ -59,10 +61,67 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
         const double nn = sn[k * TW + ii];
         if (!(nn > f2)) bad |= BG_N2F2;
         const int64_t c = node_index(G, i, j, k);
-        bg[c] = Node{su[k * TW + ii], sv[k * TW + ii], nn, g2};
+        Node& nd = bg[c];
+        nd.v[0] = su[k * TW + ii];
+        nd.v[1] = sv[k * TW + ii];
+        nd.v[2] = nn;
+        nd.v[3] = g2;
         rho_c[c] = sr[k * TW + ii];
     }
     if (bad) atomicOr(flags, bad);
+}
+
+// node gradients by centred differences: periodic in x (and y on the f-plane), one-sided at the
+// pole rows and at the bottom and top levels
+__global__ void k_node_gradients(Grid G, Node* __restrict__ bg)
+{
+    const int64_t total = (int64_t)G.ncell;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(c % G.nz);
+        const int col = (int)(c / G.nz);
+        const int i = col % G.nx, j = col / G.nx;
+        const Node* e = bg + node_index(G, wrap_int(i + 1, G.nx), j, k);
+        const Node* w = bg + node_index(G, wrap_int(i - 1, G.nx), j, k);
+        const Node *nn, *ss;
+        double sy;
+        if (G.geometry == 0) {
+            nn = bg + node_index(G, i, wrap_int(j + 1, G.ny), k);
+            ss = bg + node_index(G, i, wrap_int(j - 1, G.ny), k);
+            sy = 1.0 / (2.0 * G.dY);
+        } else if (j == 0) {
+            nn = bg + node_index(G, i, 1, k);
+            ss = bg + node_index(G, i, 0, k);
+            sy = 1.0 / G.dY;
+        } else if (j == G.ny - 1) {
+            nn = bg + node_index(G, i, G.ny - 1, k);
+            ss = bg + node_index(G, i, G.ny - 2, k);
+            sy = 1.0 / G.dY;
+        } else {
+            nn = bg + node_index(G, i, j + 1, k);
+            ss = bg + node_index(G, i, j - 1, k);
+            sy = 1.0 / (2.0 * G.dY);
+        }
+        const Node *up, *dn;
+        double sz;
+        if (k == 0) {
+            up = bg + c + 1; dn = bg + c; sz = 1.0 / G.dz;
+        } else if (k == G.nz - 1) {
+            up = bg + c; dn = bg + c - 1; sz = 1.0 / G.dz;
+        } else {
+            up = bg + c + 1; dn = bg + c - 1; sz = 1.0 / (2.0 * G.dz);
+        }
+        double d[4][3];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            d[f][0] = (e->v[f] - w->v[f]) / (2.0 * G.dX);
+            d[f][1] = (nn->v[f] - ss->v[f]) * sy;
+            d[f][2] = (up->v[f] - dn->v[f]) * sz;
+        }
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) bg[c].d[f][q] = d[f][q];
+    }
 }
 
 void configure_launch_kernels()
@@ -77,6 +136,8 @@ void launch_set_background(Context& c, const double* u, const double* v, const d
     const size_t shm = sizeof(double) * 4 * (size_t)c.G.nz * TW;
     k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg, c.rho,
                                                                 c.flag_dev);
+    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg);
 }
 
 // ----------------------------------------------------------------------------- explicit rays
