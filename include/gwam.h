@@ -178,6 +178,16 @@ int gwam_get_field_host(gwam_ctx *ctx, int which, double *out_host);
 int gwam_get_gamma2_host(gwam_ctx *ctx, double *out_host);
 int gwam_synchronize(gwam_ctx *ctx);
 
+/* Per-cell segment offsets of a ray array ordered by cell (the parent-cell storage of App. B.2):
+ * offsets[c] = number of entries of cells[] smaller than c, offsets[ncell] = n, so the entries of
+ * cell c are [offsets[c], offsets[c+1]) when cells[] is sorted.  cells: n int32 device values in
+ * [0, ncell); offsets: ncell + 1 int32 device values, overwritten.  Work is enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and the call synchronises it.  The call allocates
+ * its block-sum scratch (stream-ordered) and frees it before returning.  Errors: GWAM_EINVAL for
+ * bad sizes or null pointers, or when a cell lies outside [0, ncell) (such entries are not
+ * counted); GWAM_ENOMEM; GWAM_ECUDA. */
+int gwam_cell_offsets(const int32_t *cells, int64_t n, int32_t ncell, int32_t *offsets, void *stream);
+
 /* Per-phase device timing with CUDA events recorded on the context's stream around each phase
  * of gwam_step (for measurement tools; off by default).  enable != 0 resets and starts the
  * accumulation, 0 stops it.  Phases: 0 advance (RK3, exits, split decisions), 1 re-binning

@@ -112,6 +112,18 @@ __global__ void k_scan_apply(const int* in, int* out, int64_t n, const int* n_de
     if (blockIdx.x == 0 && threadIdx.x == 0) out[len] = bsum[nb];
 }
 
+int scan_block_count(int64_t n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
+
+// The same exclusive scan of n host-known elements with caller-provided block-sum scratch
+// (scan_block_count(n) + 1 ints).
+void scan_with_scratch(const int* in, int* out, int64_t n, int* bsum, cudaStream_t s)
+{
+    const int nb = scan_block_count(n);
+    k_scan_reduce<<<nb, kThreads, 0, s>>>(in, n, nullptr, bsum);
+    k_scan_blocks<<<1, 1024, 0, s>>>(bsum, nb);
+    k_scan_apply<<<nb, kThreads, 0, s>>>(in, out, n, nullptr, bsum, nb);
+}
+
 // Exclusive prefix of in[0..len) into out[0..len], out[len] = total; len = *n_dev if given
 // (then n is its upper bound).  in == out is allowed.
 void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n_dev)

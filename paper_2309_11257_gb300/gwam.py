@@ -96,6 +96,7 @@ SIGNATURES = {
     "gwam_get_field_host": (C.c_int, [_vp, C.c_int, _vp]),
     "gwam_get_gamma2_host": (C.c_int, [_vp, _vp]),
     "gwam_synchronize": (C.c_int, [_vp]),
+    "gwam_cell_offsets": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp, _vp]),
     "gwam_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
     "gwam_last_error": (C.c_char_p, [_vp]),
@@ -127,6 +128,19 @@ def _ptr(t):
     import torch
     assert isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
     return C.c_void_p(t.data_ptr())
+
+
+def cell_offsets(cells, ncell: int, offsets=None, stream=None):
+    """Per-cell segment offsets (ncell + 1 int32) of a cell-ordered int32 CUDA tensor of cells."""
+    import torch
+    if offsets is None:
+        offsets = torch.empty(ncell + 1, dtype=torch.int32, device=cells.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = _lib.gwam_cell_offsets(_ptr(cells) if cells.numel() else None, cells.numel(), int(ncell), _ptr(offsets),
+                                C.c_void_p(s.cuda_stream))
+    if rc != 0:
+        raise GwamError(rc, "gwam_cell_offsets")
+    return offsets
 
 
 class Tracer:
