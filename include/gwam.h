@@ -188,6 +188,21 @@ int gwam_synchronize(gwam_ctx *ctx);
  * counted); GWAM_ENOMEM; GWAM_ECUDA. */
 int gwam_cell_offsets(const int32_t *cells, int64_t n, int32_t ncell, int32_t *offsets, void *stream);
 
+/* gwam_cell_offsets for callers that cannot allocate device memory.  (The paper has no counterpart:
+ * it concerns how this library is called, not the method.)  Host models that hand all device memory
+ * to their own pool allocator at start-up, or run under a fixed device-memory budget, must not call
+ * cudaMalloc later; this entry point allocates nothing -- no cudaMalloc/cudaFree and no allocating
+ * library routine.  Same arguments, results and errors as gwam_cell_offsets, computed by the same
+ * kernels, with the scratch in a fixed array inside the library (about 32 KB, held on every GPU that
+ * loads the library until the process exits).
+ *   - ncell must not exceed GWAM_NOALLOC_MAX_CELLS, else GWAM_ECAPACITY and nothing is done.
+ *   - The first call on a device, with that device current, looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (concurrent streams, threads or
+ *     processes sharing a context) race with each other; serialise them. */
+#define GWAM_NOALLOC_MAX_CELLS 16775168
+int gwam_cell_offsets_noalloc(const int32_t *cells, int64_t n, int32_t ncell, int32_t *offsets, void *stream);
+
 /* Per-phase device timing with CUDA events recorded on the context's stream around each phase
  * of gwam_step (for measurement tools; off by default).  enable != 0 resets and starts the
  * accumulation, 0 stops it.  Phases: 0 advance (RK3, exits, split decisions), 1 re-binning
