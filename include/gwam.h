@@ -203,6 +203,11 @@ int gwam_cell_offsets(const int32_t *cells, int64_t n, int32_t ncell, int32_t *o
 #define GWAM_NOALLOC_MAX_CELLS 16775168
 int gwam_cell_offsets_noalloc(const int32_t *cells, int64_t n, int32_t ncell, int32_t *offsets, void *stream);
 
+/* Self-test of the arithmetic helpers the kernels use instead of FP64 division and square root
+ * (Newton-Raphson refinement of the hardware approximations): rcp_out[i] ~ 1/x[i],
+ * rsqrt_out[i] ~ 1/sqrt(x[i]) for positive normal x.  Device pointers, n values; synchronises. */
+int gwam_selftest_math(const double *x, int64_t n, double *rcp_out, double *rsqrt_out, void *stream);
+
 /* Per-phase device timing with CUDA events recorded on the context's stream around each phase
  * of gwam_step (for measurement tools; off by default).  enable != 0 resets and starts the
  * accumulation, 0 stops it.  Phases: 0 advance (RK3, exits, split decisions), 1 re-binning

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gwam_common.cuh"
 
@@ -31,7 +32,7 @@ static void dalloc(Context& c, T*& p, size_t count)
 
 static void free_all(Context& c)
 {
-    void* ptrs[] = {c.bg, c.rho, c.bg_scratch, c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
+    void* ptrs[] = {c.bg, c.rho, c.rho_inv, c.tables, c.bg_scratch, c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
                     c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.ecap, c.cnt, c.off, c.off2,
                     c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
                     c.flag_dev};
@@ -135,6 +136,12 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.Ly = grid->ny * grid->dy;
         }
         G.phimax = 0.5 * kPi - 0.5 * G.dY;
+        G.inv_dX = 1.0 / G.dX;
+        G.inv_dY = 1.0 / G.dY;
+        G.inv_dz = 1.0 / G.dz;
+        G.inv_nx = 1.0 / G.nx;
+        G.inv_ny = 1.0 / G.ny;
+        G.inv_g = 1.0 / G.g;
         Params& P = c.P;
         P.gamma_mode = params->gamma_mode;
         P.saturation = params->saturation;
@@ -152,6 +159,23 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         const size_t ncell = (size_t)G.ncell;
         dalloc(c, c.bg, ncell);
         dalloc(c, c.rho, ncell);
+        dalloc(c, c.rho_inv, ncell);
+        {
+            // row and level tables (host-computed once)
+            std::vector<double> tab(2 * (size_t)G.ny + G.nz);
+            for (int j = 0; j < G.ny; ++j) {
+                const double phi = G.y0 + (j + 0.5) * G.dY;
+                tab[j] = G.geometry == 1 ? cos(phi) : 1.0;
+                tab[G.ny + j] = 1.0 / tab[j];
+            }
+            for (int k = 0; k < G.nz; ++k)
+                tab[2 * G.ny + k] = G.geometry == 1 ? 1.0 / (G.radius + (k + 0.5) * G.dz) : 1.0;
+            dalloc(c, c.tables, tab.size());
+            GWAM_CUDA(cudaMemcpy(c.tables, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice));
+            G.row_cos = c.tables;
+            G.row_inv_cos = c.tables + G.ny;
+            G.lev_inv_r = c.tables + 2 * G.ny;
+        }
         for (int b = 0; b < 2; ++b) {
             dalloc(c, c.ray_mem[b], 7 * nr);
             RaySoA& R = b == 0 ? c.A : c.B;

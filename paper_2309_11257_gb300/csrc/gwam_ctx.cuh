@@ -50,6 +50,8 @@ struct Context {
     // background (column-major)
     Node* bg = nullptr;          // U V N2 G2 per node
     double* rho = nullptr;          // rho per node
+    double* rho_inv = nullptr;      // 1 / rho per node
+    double* tables = nullptr;       // row_cos[ny], row_inv_cos[ny], lev_inv_r[nz]
     double* bg_scratch = nullptr;   // staging of caller fields ([nz][ny][nx], 4 fields)
 
     // ray volumes: A holds the canonical array between steps, B is the re-binned output

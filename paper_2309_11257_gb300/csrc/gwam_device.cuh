@@ -18,6 +18,34 @@ namespace gwam {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 256;
 
+// ---------------------------------------------------------------------------- arithmetic
+
+// Reciprocal: the hardware approximation (PTX rcp.approx.ftz.f64, about 20 correct bits) refined by
+// two Newton-Raphson steps y <- y + y (1 - x y), each of which doubles the number of correct bits.
+// For the positive, finite, normal-range operands of the ray equations (within an ulp or so of the
+// IEEE quotient, tested against it); FP64 division would cost several times as many instructions.
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+}
+
+// Reciprocal square root: the hardware approximation (PTX rsqrt.approx.ftz.f64) refined by two
+// Newton-Raphson steps y <- y + (y/2) (1 - x y^2).
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+    e = fma(-x * y, y, 1.0);
+    return fma(0.5 * y, e, y);
+}
+
 // ---------------------------------------------------------------------------- layouts
 
 // Grid geometry as the kernels see it (derived once on the host).
@@ -31,6 +59,11 @@ struct Grid {
     double ztop;
     double f0, radius, omega, g;
     double phimax;         // carriers poleward of this latitude leave (centre of the last row)
+    // precomputed reciprocals and tables (FP64 division is a long instruction sequence)
+    double inv_dX, inv_dY, inv_dz, inv_nx, inv_ny, inv_g;
+    const double* row_cos;      // cos(phi_j) of every row centre (sphere), 1 on the f-plane
+    const double* row_inv_cos;  // 1 / row_cos
+    const double* lev_inv_r;    // 1 / (a + z_k) of every level centre (sphere), 1 on the f-plane
 };
 
 struct Params {
@@ -93,11 +126,11 @@ __device__ __forceinline__ int wrap_int(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-// periodic bracketing node pair; s in node units
-__device__ __forceinline__ void bracket_periodic(double s, int n, int& q0, int& q1, double& t)
+// periodic bracketing node pair; s in node units, inv_n = 1/n
+__device__ __forceinline__ void bracket_periodic(double s, int n, double inv_n, int& q0, int& q1, double& t)
 {
     if (!isfinite(s)) s = 0.0;
-    s = s - (double)n * floor(s / (double)n);
+    s = s - (double)n * floor(s * inv_n);
     double fl = floor(s);
     t = s - fl;
     q0 = wrap_int((int)fl, n);
@@ -134,10 +167,10 @@ __device__ __forceinline__ void gather(const Grid& G, const Node* __restrict__ b
 {
     int i0, i1, j0, j1, k0, k1;
     double tx, ty, tz;
-    bracket_periodic(X / G.dX - 0.5, G.nx, i0, i1, tx);
-    if (G.geometry == 1) bracket_clamped((Y - G.y0) / G.dY - 0.5, G.ny, j0, j1, ty);
-    else bracket_periodic(Y / G.dY - 0.5, G.ny, j0, j1, ty);
-    bracket_clamped(Z / G.dz - 0.5, G.nz, k0, k1, tz);
+    bracket_periodic(X * G.inv_dX - 0.5, G.nx, G.inv_nx, i0, i1, tx);
+    if (G.geometry == 1) bracket_clamped((Y - G.y0) * G.inv_dY - 0.5, G.ny, j0, j1, ty);
+    else bracket_periodic(Y * G.inv_dY - 0.5, G.ny, G.inv_ny, j0, j1, ty);
+    bracket_clamped(Z * G.inv_dz - 0.5, G.nz, k0, k1, tz);
     double acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc[q] = 0.0;
@@ -182,23 +215,24 @@ __device__ __forceinline__ void coriolis(const Grid& G, double sphi, double cphi
 // The intrinsic group velocity is ch = (k, l) D (m^2 + G^2) / (w K^4), ch_r = -m D k_h^2 / (w K^4),
 // D = N^2 - f^2, so each component is (its factor) * c with c = D / (w K^4).
 struct Disp {
-    double K2, D, w2, w, c;
+    double K2, iK2, D, w2, w, iw, c;
 };
 
 __device__ __forceinline__ void dispersion(double kh2, double mg2, double n2, double f2, Disp& d)
 {
     d.K2 = kh2 + mg2;
     d.D = n2 - f2;
-    double iK2 = 1.0 / d.K2;
-    d.w2 = (f2 * mg2 + n2 * kh2) * iK2;
-    d.w = sqrt(d.w2);
-    d.c = d.D * iK2 * iK2 / d.w;
+    d.iK2 = rcp_nr(d.K2);
+    d.w2 = (f2 * mg2 + n2 * kh2) * d.iK2;
+    d.iw = rsqrt_nr(d.w2);
+    d.w = d.w2 * d.iw;
+    d.c = d.D * d.iK2 * d.iK2 * d.iw;
 }
 
 // ---------------------------------------------------------------------------- ray equations
 
 struct Geo {
-    double r, hX, hY, sphi, cphi, tphi;
+    double r, ir, hX, ihX, hY, sphi, cphi, tphi;
 };
 
 __device__ __forceinline__ void geometry_at(const Grid& G, double Y, double Z, Geo& g)
@@ -206,12 +240,15 @@ __device__ __forceinline__ void geometry_at(const Grid& G, double Y, double Z, G
     if (G.geometry == 1) {
         sincos(Y, &g.sphi, &g.cphi);
         g.r = G.radius + Z;
+        g.ir = rcp_nr(g.r);
+        const double ic = rcp_nr(g.cphi);
         g.hX = g.r * g.cphi;
+        g.ihX = g.ir * ic;
         g.hY = g.r;
-        g.tphi = g.sphi / g.cphi;
+        g.tphi = g.sphi * ic;
     } else {
         g.sphi = 0.0; g.cphi = 1.0; g.tphi = 0.0;
-        g.r = 1.0; g.hX = 1.0; g.hY = 1.0;
+        g.r = 1.0; g.ir = 1.0; g.hX = 1.0; g.ihX = 1.0; g.hY = 1.0;
     }
 }
 
@@ -237,16 +274,17 @@ __device__ __forceinline__ void ray_rhs(const Grid& G, const Node* __restrict__ 
     const double cgy = l * mg2 * d.c + V;
     const double cgz = -m * kh2 * d.c;
     // d Omega / d q at fixed wavevector
-    const double aN = kh2 / (2.0 * d.w * d.K2);
-    const double aG = aN * d.D / d.K2;
-    const double aF = mg2 / (2.0 * d.w * d.K2);
+    const double hwK = 0.5 * d.iw * d.iK2;           // 1 / (2 w K^2)
+    const double aN = kh2 * hwK;
+    const double aG = aN * d.D * d.iK2;
+    const double aF = mg2 * hwK;
     double Gq[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) Gq[q] = k * b.d[0][q] + l * b.d[1][q] + aN * b.d[2][q] - aG * b.d[3][q];
     Gq[1] += aF * df2;
     if (G.geometry == 1) {
-        const double ir = 1.0 / g.r;
-        F[3] = -Gq[0] / g.hX + k * ir * (g.tphi * cgy - cgz);
+        const double ir = g.ir;
+        F[3] = -Gq[0] * g.ihX + k * ir * (g.tphi * cgy - cgz);
         F[4] = -Gq[1] * ir - ir * (l * cgz + k * g.tphi * cgx);
         F[5] = -Gq[2] + ir * (k * cgx + l * cgy);
     } else {
@@ -255,7 +293,7 @@ __device__ __forceinline__ void ray_rhs(const Grid& G, const Node* __restrict__ 
         F[5] = -Gq[2];
     }
     // faces: first-order Taylor values along the face's own axis
-    const double ihX = 1.0 / g.hX, ihY = 1.0 / g.hY;
+    const double ihX = g.ihX, ihY = g.ir;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         double vel[2];
@@ -309,8 +347,9 @@ __device__ __forceinline__ double wrap_period(double x, double L)
 
 __device__ __forceinline__ void wrap_position(const Grid& G, double s[NSTATE])
 {
-    s[SX] = wrap_period(s[SX], G.Lx);
-    if (G.geometry == 0) s[SY] = wrap_period(s[SY], G.Ly);
+    // most carriers stay inside the period: skip the division then
+    if (!(s[SX] >= 0.0 && s[SX] < G.Lx)) s[SX] = wrap_period(s[SX], G.Lx);
+    if (G.geometry == 0 && !(s[SY] >= 0.0 && s[SY] < G.Ly)) s[SY] = wrap_period(s[SY], G.Ly);
 }
 
 __device__ __forceinline__ double ray_action(const double s[NSTATE])
@@ -335,9 +374,9 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? l
 
 __device__ __forceinline__ void cell_ijk(const Grid& G, const double s[NSTATE], int& i, int& j, int& k)
 {
-    i = clampi((int)floor(s[SX] / G.dX), 0, G.nx - 1);
-    j = clampi((int)floor((s[SY] - G.y0) / G.dY), 0, G.ny - 1);
-    k = clampi((int)floor(s[SZ] / G.dz), 0, G.nz - 1);
+    i = clampi((int)floor(s[SX] * G.inv_dX), 0, G.nx - 1);
+    j = clampi((int)floor((s[SY] - G.y0) * G.inv_dY), 0, G.ny - 1);
+    k = clampi((int)floor(s[SZ] * G.inv_dz), 0, G.nz - 1);
 }
 
 __device__ __forceinline__ int cell_of(const Grid& G, const double s[NSTATE])
@@ -360,7 +399,7 @@ __device__ __forceinline__ int split_code(const Grid& G, const Params& P, const 
     if (G.geometry == 1) {
         int i, j, k;
         cell_ijk(G, s, i, j, k);
-        const double cj = cos(row_lat(G, j));
+        const double cj = G.row_cos[j];
         const double cp = cos(s[SY]);
         xlen = cp * s[SEX];
         ylen = s[SEY];
@@ -409,14 +448,24 @@ __device__ __forceinline__ double cell_volume(const Grid& G, int j, int k)
 {
     if (G.geometry == 1) {
         const double rc = G.radius + (k + 0.5) * G.dz;
-        return rc * rc * cos(row_lat(G, j)) * G.dX * G.dY * G.dz;
+        return rc * rc * G.row_cos[j] * G.dX * G.dY * G.dz;
     }
     return G.dX * G.dY * G.dz;
 }
 
+// 1 / cell_volume
+__device__ __forceinline__ double inv_cell_volume(const Grid& G, int j, int k)
+{
+    if (G.geometry == 1) {
+        const double ir = G.lev_inv_r[k];
+        return ir * ir * G.row_inv_cos[j] * G.inv_dX * G.inv_dY * G.inv_dz;
+    }
+    return G.inv_dX * G.inv_dY * G.inv_dz;
+}
+
 // Intrinsic properties of a ray volume at its carrier position (saturation, projection, cap).
 struct Intr {
-    double kh2, m2, mg2, K2, D, w, w2, c, f2, n2;
+    double kh2, m2, mg2, K2, iK2, D, w, iw, w2, c, f2, n2;
 };
 
 __device__ __forceinline__ void intrinsic_at(const Grid& G, const Node* __restrict__ bg, const double s[NSTATE],
@@ -434,8 +483,10 @@ __device__ __forceinline__ void intrinsic_at(const Grid& G, const Node* __restri
     Disp d;
     dispersion(in.kh2, in.mg2, b.v[2], in.f2, d);
     in.K2 = d.K2;
+    in.iK2 = d.iK2;
     in.D = d.D;
     in.w = d.w;
+    in.iw = d.iw;
     in.w2 = d.w2;
     in.c = d.c;
 }

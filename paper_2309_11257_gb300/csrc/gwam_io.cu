@@ -56,4 +56,24 @@ void launch_gamma_to_caller(Context& c, double* dst)
     k_gamma_to_caller<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg, dst);
 }
 
+__global__ void k_selftest_math(const double* __restrict__ x, int64_t n, double* __restrict__ r,
+                                double* __restrict__ q)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        r[i] = rcp_nr(x[i]);
+        q[i] = rsqrt_nr(x[i]);
+    }
+}
+
 }  // namespace gwam
+
+extern "C" int gwam_selftest_math(const double* x, int64_t n, double* rcp_out, double* rsqrt_out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !rcp_out || !rsqrt_out))) return GWAM_EINVAL;
+    if (n == 0) return GWAM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>((n + gwam::kThreads - 1) / gwam::kThreads, 4096);
+    gwam::k_selftest_math<<<blocks, gwam::kThreads, 0, s>>>(x, n, rcp_out, rsqrt_out);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GWAM_ECUDA;
+    return GWAM_OK;
+}

@@ -17,7 +17,7 @@ enum { BG_NONFINITE = 1, BG_RHO = 2, BG_N2F2 = 4 };
 // differences of ln rho (one-sided at the bottom and top)
 __global__ void k_set_background(Grid G, int gamma_mode, const double* __restrict__ u, const double* __restrict__ v,
                                  const double* __restrict__ n2, const double* __restrict__ rho, Node* __restrict__ bg,
-                                 double* __restrict__ rho_c, int* flags)
+                                 double* __restrict__ rho_c, double* __restrict__ rho_inv, int* flags)
 {
     extern __shared__ double sh[];   // 4 fields x nz x 32
     const int TW = 32;
@@ -67,6 +67,7 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
         nd.v[2] = nn;
         nd.v[3] = g2;
         rho_c[c] = sr[k * TW + ii];
+        rho_inv[c] = 1.0 / sr[k * TW + ii];
     }
     if (bad) atomicOr(flags, bad);
 }
@@ -135,7 +136,7 @@ void launch_set_background(Context& c, const double* u, const double* v, const d
     const int ntx = (c.G.nx + TW - 1) / TW;
     const size_t shm = sizeof(double) * 4 * (size_t)c.G.nz * TW;
     k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg, c.rho,
-                                                                c.flag_dev);
+                                                                c.rho_inv, c.flag_dev);
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
     k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg);
 }
@@ -239,7 +240,7 @@ struct Bin {
 __device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict__ bg, const Bin& b,
                                            double s[NSTATE])
 {
-    const double X = (b.i + 0.5) * G.dX;
+    const double X = __dmul_rn(b.i + 0.5, G.dX);
     const double Y = row_lat(G, b.j);
     const double Z = b.z_launch + 0.5 * b.dz_launch;
     Bg bk;
@@ -261,7 +262,7 @@ __device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict
     Disp d;
     dispersion(kh * kh, m2 + G2, N2, f2, d);
     const double chr = -m * kh * kh * d.c;
-    const double A = b.flux / (kh * chr);
+    const double A = b.flux / (kh * chr);   // once per launched ray: IEEE division is fine here
     const double dk = b.frac * kh, dl = b.frac * kh, dm = b.frac * fabs(m);
     s[SX] = X; s[SY] = Y; s[SZ] = Z;
     s[SK] = k; s[SL] = l; s[SM] = m;

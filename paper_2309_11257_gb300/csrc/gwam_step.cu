@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
             intrinsic_at(G, bg, ch, g, in);
             int ci, cj, ck;
             cell_ijk(G, ch, ci, cj, ck);
-            const double av = ray_action(ch) / cell_volume(G, cj, ck);
-            pj[p] = in.m2 * in.kh2 / (in.w * in.K2) * av;
+            const double av = ray_action(ch) * inv_cell_volume(G, cj, ck);
+            pj[p] = in.m2 * in.kh2 * in.iw * in.iK2 * av;
             k2[p] = in.K2;
         }
     }
@@ -480,14 +480,14 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
             key = (cj * G.nx + ci) * G.nz + ck;
             col = cj * G.nx + ci;
             const double Vj = ray_volume(G, s, g);
-            const double A = W / Vj;                       // N dk dl dm
-            const double alpha = Vj / cell_volume(G, cj, ck);
+            const double A = W * rcp_nr(Vj);               // N dk dl dm
+            const double aw = W * inv_cell_volume(G, cj, ck);   // alpha_j A_j with alpha_j = V_j / V_c
             const double k = s[SK], l = s[SL], m = s[SM];
             const double mg2c = in.mg2 * in.c;             // (m^2 + Gamma^2) D / (w K^4)
             const double chx = k * mg2c, chy = l * mg2c, chr = -m * in.kh2 * in.c;
             double t_ll, t_lp, t_pl, t_pp, el, ep;
             if (P.flux_form == 0) {
-                const double iden = 1.0 / (in.w2 - in.f2);
+                const double iden = rcp_nr(in.w2 - in.f2);
                 t_ll = (in.w2 * chx * k + in.f2 * chy * l) * iden;
                 t_lp = (in.w2 * chx * l - in.f2 * chy * k) * iden;
                 t_pl = (in.w2 * chy * k - in.f2 * chx * l) * iden;
@@ -501,19 +501,15 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                 zl = chr * k; zp = chr * l;
                 el = 0.0; ep = 0.0;
             }
-            const double aw = alpha * A;
             hv[0] = aw * t_ll; hv[1] = aw * t_lp; hv[2] = aw * t_pl; hv[3] = aw * t_pp;
             hv[4] = aw * el; hv[5] = aw * ep; hv[6] = aw;
             zl *= A;
             zp *= A;
-            if (G.geometry == 1)
-                wh = g.cphi * s[SEX] * s[SEY] / (cos(row_lat(G, cj)) * G.dX * G.dY);
-            else
-                wh = s[SEX] * s[SEY] / (G.dX * G.dY);
+            wh = g.cphi * s[SEX] * s[SEY] * G.row_inv_cos[cj] * G.inv_dX * G.inv_dY;
             lo = s[SZ] - 0.5 * s[SEZ];
             hi = s[SZ] + 0.5 * s[SEZ];
-            kk0 = max(1, (int)floor(lo / G.dz - 0.5));
-            const int kk1 = min(G.nz - 1, (int)ceil(hi / G.dz + 0.5));
+            kk0 = max(1, (int)floor(lo * G.inv_dz - 0.5));
+            const int kk1 = min(G.nz - 1, (int)ceil(hi * G.inv_dz + 0.5));
             nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
         }
         // centre fields: warp-segmented reduction over runs of equal cells, one atomic per run
@@ -538,7 +534,7 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                 const double slo = (kk - 0.5) * G.dz, shi = (kk + 0.5) * G.dz;
                 const double ov = fmin(hi, shi) - fmax(lo, slo);
                 if (ov > 0.0) {
-                    const double w = wh * ov / G.dz;
+                    const double w = wh * ov * G.inv_dz;
                     zv[0] = w * zl;
                     zv[1] = w * zp;
                     zkey = col * (G.nz + 1) + kk;
@@ -594,7 +590,7 @@ __global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, con
                              const double* __restrict__ fll, const double* __restrict__ flp,
                              const double* __restrict__ fpl, const double* __restrict__ fpp,
                              const double* __restrict__ el, const double* __restrict__ ep,
-                             const double* __restrict__ rho, double* __restrict__ du, double* __restrict__ dv)
+                             const double* __restrict__ rho_inv, double* __restrict__ du, double* __restrict__ dv)
 {
     extern __shared__ double tile[];
     double* tu = tile;
@@ -604,11 +600,12 @@ __global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, con
     const int i0 = (blockIdx.x % ntx) * TW;
     const int nz = G.nz;
     const int n = TW * nz;
+    const double h2x = 0.5 * G.inv_dX, h2y = 0.5 * G.inv_dY;
     double rcp_cos = 1.0, cn = 0.0, cs = 0.0;
     if (G.geometry == 1) {
-        rcp_cos = 1.0 / cos(row_lat(G, j));
-        if (j + 1 < G.ny) cn = cos(row_lat(G, j + 1));
-        if (j - 1 >= 0) cs = cos(row_lat(G, j - 1));
+        rcp_cos = G.row_inv_cos[j];
+        if (j + 1 < G.ny) cn = G.row_cos[j + 1];
+        if (j - 1 >= 0) cs = G.row_cos[j - 1];
     }
     const int jn = G.geometry == 1 ? j + 1 : wrap_int(j + 1, G.ny);
     const int js = G.geometry == 1 ? j - 1 : wrap_int(j - 1, G.ny);
@@ -616,7 +613,7 @@ __global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, con
         const int k = t % nz, ii = t / nz;
         const int i = i0 + ii;
         if (i >= G.nx) continue;
-        const int ie = wrap_int(i + 1, G.nx), iw = wrap_int(i - 1, G.nx);
+        const int ie = i + 1 == G.nx ? 0 : i + 1, iw = i == 0 ? G.nx - 1 : i - 1;
         const int64_t c = ((int64_t)j * G.nx + i) * nz + k;
         const int64_t ce = ((int64_t)j * G.nx + ie) * nz + k;
         const int64_t cw = ((int64_t)j * G.nx + iw) * nz + k;
@@ -632,24 +629,20 @@ __global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, con
             pl_s = fpl[cc];
             pp_s = fpp[cc];
         }
-        const double r = rho[c];
+        const double ri = rho_inv[c];
         double div_u, div_v;
-        const double dzl = (fzl[zc + 1] - fzl[zc]) / G.dz;
-        const double dzp = (fzp[zc + 1] - fzp[zc]) / G.dz;
+        const double dzl = (fzl[zc + 1] - fzl[zc]) * G.inv_dz;
+        const double dzp = (fzp[zc + 1] - fzp[zc]) * G.inv_dz;
         if (G.geometry == 1) {
-            const double rr = G.radius + (k + 0.5) * G.dz;
-            const double dl_u = (fll[ce] - fll[cw]) / (2.0 * G.dX);
-            const double dp_u = (cn * pl_n - cs * pl_s) / (2.0 * G.dY);
-            const double dl_v = (flp[ce] - flp[cw]) / (2.0 * G.dX);
-            const double dp_v = (cn * pp_n - cs * pp_s) / (2.0 * G.dY);
-            div_u = (dl_u + dp_u) * rcp_cos / rr + dzl;
-            div_v = (dl_v + dp_v) * rcp_cos / rr + dzp;
+            const double mh = rcp_cos * G.lev_inv_r[k];
+            div_u = ((fll[ce] - fll[cw]) * h2x + (cn * pl_n - cs * pl_s) * h2y) * mh + dzl;
+            div_v = ((flp[ce] - flp[cw]) * h2x + (cn * pp_n - cs * pp_s) * h2y) * mh + dzp;
         } else {
-            div_u = (fll[ce] - fll[cw]) / (2.0 * G.dX) + (pl_n - pl_s) / (2.0 * G.dY) + dzl;
-            div_v = (flp[ce] - flp[cw]) / (2.0 * G.dX) + (pp_n - pp_s) / (2.0 * G.dY) + dzp;
+            div_u = (fll[ce] - fll[cw]) * h2x + (pl_n - pl_s) * h2y + dzl;
+            div_v = (flp[ce] - flp[cw]) * h2x + (pp_n - pp_s) * h2y + dzp;
         }
-        tu[k * TW + ii] = -div_u / r + el[c] / (G.g * r);
-        tv[k * TW + ii] = -div_v / r + ep[c] / (G.g * r);
+        tu[k * TW + ii] = (el[c] * G.inv_g - div_u) * ri;
+        tv[k * TW + ii] = (ep[c] * G.inv_g - div_v) * ri;
     }
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -806,7 +799,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     const size_t shm = sizeof(double) * 2 * (size_t)TW * G.nz;
     const int ntx = (G.nx + TW - 1) / TW;
     k_divergence<<<ntx * G.ny, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP], fl[F_PL], fl[F_PP],
-                                                   fl[F_EL], fl[F_EP], c.rho, du ? du : c.dudt_buf,
+                                                   fl[F_EL], fl[F_EP], c.rho_inv, du ? du : c.dudt_buf,
                                                    dv ? dv : c.dvdt_buf);
     k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, nb, mask, 1);
     prof_mark(c, 5);

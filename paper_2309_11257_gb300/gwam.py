@@ -98,6 +98,7 @@ SIGNATURES = {
     "gwam_synchronize": (C.c_int, [_vp]),
     "gwam_cell_offsets": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp, _vp]),
     "gwam_cell_offsets_noalloc": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp, _vp]),
+    "gwam_selftest_math": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
     "gwam_last_error": (C.c_char_p, [_vp]),
