@@ -82,7 +82,9 @@ typedef struct {
     int cap_per_column;   /* ray volumes kept per column (App. B.5); <= 0: no cap */
     double alpha_s;       /* splitting scale factor (2.5 in App. B.3) */
     double min_split_dz;  /* minimum vertical split threshold (1 km in App. B.3) */
-    int64_t max_rays;     /* capacity: live ray volumes plus split children of one step */
+    int64_t max_rays;     /* capacity: live ray volumes plus split children of one step (all members) */
+    int members;          /* ensemble members: independent backgrounds and ray populations advanced
+                             together (0 or 1: a single member; at most 255) */
 } gwam_params;
 
 /* Background source of Sec. 3c: alpha(phi) profile, F_sol = alpha(phi) F_s + alpha(-phi) F_w,
@@ -102,10 +104,10 @@ typedef struct {
     int launch_zero_flux;     /* 1: launch zero-action rays where F_am = 0 */
 } gwam_bg_source;
 
-/* One explicit spectral launch in column (i, j) (convective-like sources). */
+/* One explicit spectral launch in column (i, j) of ensemble member `member` (convective-like sources). */
 typedef struct {
     int i, j;
-    int pad_;
+    int member;
     double z_launch, dz_launch, theta, c, lambda_h, flux, spectral_frac;
 } gwam_spec;
 
@@ -133,10 +135,15 @@ void gwam_destroy(gwam_ctx *ctx);
 
 /* Mean state (Sec. 3b): U, V, N^2, rho, each [nz][ny][nx] doubles, copied into the
  * context's own layout; Gamma^2 is derived from rho.  Device pointers.  Checks (device
- * reduction, synchronising): finite, rho > 0, N^2 > f^2 -> GWAM_ENUMERIC. */
+ * reduction, synchronising): finite, rho > 0, N^2 > f^2 -> GWAM_ENUMERIC.  gwam_set_background
+ * gives every ensemble member this background; gwam_set_member_background one member. */
 int gwam_set_background(gwam_ctx *ctx, const double *u, const double *v, const double *n2, const double *rho);
 int gwam_set_background_host(gwam_ctx *ctx, const double *u, const double *v, const double *n2,
                              const double *rho);
+int gwam_set_member_background(gwam_ctx *ctx, int member, const double *u, const double *v, const double *n2,
+                               const double *rho);
+int gwam_set_member_background_host(gwam_ctx *ctx, int member, const double *u, const double *v,
+                                    const double *n2, const double *rho);
 
 /* Append explicit ray volumes (ids next_id, next_id+1, ...), P_x = hX ex dk, P_y = hY ey dl,
  * P_z = ez dm (Sec. 3a).  A ray outside the domain -> GWAM_EINVAL and nothing is added.
@@ -144,8 +151,8 @@ int gwam_set_background_host(gwam_ctx *ctx, const double *u, const double *v, co
 int gwam_add_rays(gwam_ctx *ctx, const gwam_ray_input *rays, int64_t n);
 int gwam_add_rays_host(gwam_ctx *ctx, const gwam_ray_input *rays, int64_t n);
 
-/* Launch the background source (Sec. 3c) at the end of the current ray array, in column
- * order (j, then i) and bin order (azimuth, then phase speed).  Bins with w_hat outside
+/* Launch the background source (Sec. 3c) into every member, at the end of the current ray array,
+ * in member order, column order (j, then i) and bin order (azimuth, then phase speed).  Bins with w_hat outside
  * (|f|, N) or m^2 <= 0 are counted in n_filtered.  Stream-ordered (no host sync). */
 int gwam_launch_sources(gwam_ctx *ctx, const gwam_bg_source *src);
 /* Explicit spectral launches, in array order; `specs` device pointer / host pointer. */
@@ -155,26 +162,42 @@ int gwam_launch_spectral_host(gwam_ctx *ctx, const gwam_spec *specs, int64_t n);
 /* One full step of dt seconds (dt > 0): RK3 ray propagation (App. B.2), exits, splitting
  * (App. B.3), re-binning by cell, per-column cap (App. B.5), saturation (Sec. 3c), flux
  * projection (Sec. 3b), smoothing (App. B.4), divergence (Eq. mean-flow-impact) into
- * dudt, dvdt ([nz][ny][nx] device buffers, may be NULL), wave-action budget (Sec. 4).
+ * dudt, dvdt ([members][nz][ny][nx] device buffers, may be NULL), wave-action budget (Sec. 4).
  * Stream-ordered: no host synchronisation. */
 int gwam_step(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
+/* The same step replayed from a CUDA graph: the first call for a given (dt, dudt, dvdt) captures the
+ * step's kernels (two graphs, one per ray-buffer parity) on an internal stream; later calls launch
+ * the graph on the context's stream -- one launch per step.  Launches and backgrounds may change
+ * between calls (the kernels read counts from device memory).  Per-phase profiling is not recorded
+ * inside graphs. */
+int gwam_step_graph(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
 /* The same with host output buffers (copied back and synchronised). */
 int gwam_step_host(gwam_ctx *ctx, double dt, double *dudt_host, double *dvdt_host);
+
+/* Launch shapes of the three heavy ray kernels (0 advance, 1 materialise, 2 projection): threads
+ * per block (64..256, a multiple of 32) and blocks (1..8 x the SM count).  gwam_autotune advances
+ * the simulation by (candidates x steps_per_candidate) real steps of dt, timing each kernel with
+ * CUDA events under each candidate shape, and keeps the fastest shape per kernel (host-side
+ * search; the caller may persist the result and restore it with gwam_set_launch_config). */
+int gwam_set_launch_config(gwam_ctx *ctx, int kernel, int threads, int blocks);
+int gwam_get_launch_config(gwam_ctx *ctx, int kernel, int *threads, int *blocks);
+int gwam_autotune(gwam_ctx *ctx, double dt, int steps_per_candidate, double *dudt, double *dvdt);
 
 /* Number of live ray volumes (synchronising). */
 int gwam_num_rays(gwam_ctx *ctx, int64_t *n);
 /* Ray volumes in canonical order into host memory: state13_host is 13 blocks of `cap`
  * doubles (x y z k l m ex ey ez Px Py Pz N), ids/cells `cap` entries each (either may be
- * NULL).  cap < number of rays -> GWAM_ECAPACITY. */
+ * NULL).  Ids carry the ensemble member in their top 8 bits; cells are member * ncell + the
+ * member's cell index.  cap < number of rays -> GWAM_ECAPACITY. */
 int gwam_get_rays_host(gwam_ctx *ctx, double *state13_host, int64_t *ids_host, int32_t *cells_host,
                        int64_t cap);
 /* Counters and budget (synchronising; returns a pending device status). */
 int gwam_get_stats(gwam_ctx *ctx, gwam_stats *out);
-/* Grid field of the last step into host memory: 0 Fz_lambda, 1 Fz_phi ([nz+1][ny][nx]),
- * 2 F_ll, 3 F_lp, 4 F_pl, 5 F_pp, 6 E_lambda, 7 E_phi, 8 wave-action density ([nz][ny][nx]);
+/* Grid field of the last step into host memory, [members] outermost: 0 Fz_lambda, 1 Fz_phi
+ * ([nz+1][ny][nx]), 2 F_ll, 3 F_lp, 4 F_pl, 5 F_pp, 6 E_lambda, 7 E_phi, 8 wave-action density ([nz][ny][nx]);
  * fluxes after smoothing when it is on; E_* without the 1/(g rho) factor. */
 int gwam_get_field_host(gwam_ctx *ctx, int which, double *out_host);
-/* Gamma^2 node field [nz][ny][nx] into host memory. */
+/* Gamma^2 node field [members][nz][ny][nx] into host memory. */
 int gwam_get_gamma2_host(gwam_ctx *ctx, double *out_host);
 int gwam_synchronize(gwam_ctx *ctx);
 

@@ -45,6 +45,12 @@ static void free_all(Context& c)
     for (int q = 0; q < Context::kRing; ++q)
         for (int p = 0; p <= Context::kPhases; ++p)
             if (c.prof_ev[q][p]) cudaEventDestroy(c.prof_ev[q][p]);
+    for (int q = 0; q < Context::kTuneRing; ++q)
+        for (int p = 0; p < 6; ++p)
+            if (c.tune_ev[q][p]) cudaEventDestroy(c.tune_ev[q][p]);
+    for (int q = 0; q < 2; ++q)
+        if (c.gexec[q]) cudaGraphExecDestroy(c.gexec[q]);
+    if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     if (c.ctl_host) cudaFreeHost(c.ctl_host);
     if (c.budget_host) cudaFreeHost(c.budget_host);
     if (c.flag_host) cudaFreeHost(c.flag_host);
@@ -102,6 +108,9 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
     if (params->max_rays < 1 || params->max_rays >= ((int64_t)1 << 29)) return GWAM_EINVAL;
     if (!(params->alpha_s > 0.0) || !(params->min_split_dz >= 0.0)) return GWAM_EINVAL;
     if (params->flux_form != 0 && params->flux_form != 1) return GWAM_EINVAL;
+    const int members = params->members <= 0 ? 1 : params->members;
+    if (members > 255) return GWAM_EINVAL;
+    if ((int64_t)grid->nx * grid->ny * (grid->nz + 1) * members >= (int64_t)1 << 31) return GWAM_EINVAL;
     gwam_ctx* h = new (std::nothrow) gwam_ctx();
     if (!h) return GWAM_ENOMEM;
     Context& c = h->c;
@@ -116,6 +125,10 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         G.nz = grid->nz;
         G.ncol = grid->nx * grid->ny;
         G.ncell = G.ncol * grid->nz;
+        G.members = members;
+        G.ncol_all = G.ncol * members;
+        G.ncell_all = G.ncell * members;
+        c.member_bg.assign(members, false);
         G.dz = grid->dz;
         G.f0 = grid->f0;
         G.radius = grid->radius;
@@ -152,11 +165,14 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         P.alpha_s = params->alpha_s;
         P.min_split_dz = params->min_split_dz;
         c.max_rays = params->max_rays;
-        // persistent grid: resident blocks of the heaviest ray kernel, a multiple of the SM count
+        // persistent grids: multiples of the SM count; the three heavy ray kernels are autotunable
         c.grid_blocks = c.num_sms * 4;
+        c.max_blocks = c.num_sms * 8;
+        for (int q = 0; q < 3; ++q) c.lcfg[q] = LaunchCfg{kThreads, c.num_sms * 4};
+        GWAM_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
 
         const size_t nr = (size_t)c.max_rays;
-        const size_t ncell = (size_t)G.ncell;
+        const size_t ncell = (size_t)G.ncell_all;
         dalloc(c, c.bg, ncell);
         dalloc(c, c.rho, ncell);
         dalloc(c, c.rho_inv, ncell);
@@ -195,7 +211,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         dalloc(c, c.cnt, ncell + 1);
         dalloc(c, c.off, ncell + 1);
         dalloc(c, c.off2, ncell + 1);
-        dalloc(c, c.overlist, (size_t)G.ncol);
+        dalloc(c, c.overlist, (size_t)G.ncol_all);
         dalloc(c, c.biglist, ncell);
         const size_t scan_blocks = (std::max(nr, ncell) + 2047) / 2048 + 2;
         dalloc(c, c.scan_tmp, scan_blocks + 1);
@@ -210,14 +226,14 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         dalloc(c, c.dvdt_buf, ncell);
         dalloc(c, c.ctl, 1);
         dalloc(c, c.budget, 1);
-        dalloc(c, c.partials, (size_t)NTALLY * c.grid_blocks);
+        dalloc(c, c.partials, (size_t)NTALLY * c.max_blocks);
         dalloc(c, c.flag_dev, 1);
         GWAM_CUDA(cudaMallocHost((void**)&c.ctl_host, sizeof(Ctl)));
         GWAM_CUDA(cudaMallocHost((void**)&c.budget_host, sizeof(DevBudget)));
         GWAM_CUDA(cudaMallocHost((void**)&c.flag_host, sizeof(int)));
         GWAM_CUDA(cudaMemsetAsync(c.ctl, 0, sizeof(Ctl), c.stream));
         GWAM_CUDA(cudaMemsetAsync(c.budget, 0, sizeof(DevBudget), c.stream));
-        GWAM_CUDA(cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * c.grid_blocks, c.stream));
+        GWAM_CUDA(cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * c.max_blocks, c.stream));
         configure_kernels();
         GWAM_CUDA(cudaStreamSynchronize(c.stream));
         GWAM_CUDA(cudaGetLastError());
@@ -238,11 +254,12 @@ void gwam_destroy(gwam_ctx* ctx)
     delete ctx;
 }
 
-static int set_background_impl(gwam_ctx* ctx, const double* u, const double* v, const double* n2, const double* rho,
-                               bool host)
+static int set_background_impl(gwam_ctx* ctx, int member, const double* u, const double* v, const double* n2,
+                               const double* rho, bool host)
 {
     API_BEGIN(ctx)
     if (!u || !v || !n2 || !rho) return GWAM_EINVAL;
+    if (member < -1 || member >= c.G.members) return GWAM_EINVAL;
     const size_t nc = (size_t)c.G.ncell;
     const double* src[4] = {u, v, n2, rho};
     if (host) {
@@ -250,28 +267,46 @@ static int set_background_impl(gwam_ctx* ctx, const double* u, const double* v, 
         for (int q = 0; q < 4; ++q) h2d(c, c.bg_scratch + q * nc, src[q], sizeof(double) * nc);
         for (int q = 0; q < 4; ++q) src[q] = c.bg_scratch + q * nc;
     }
+    const int m0 = member < 0 ? 0 : member, m1 = member < 0 ? c.G.members : member + 1;
     GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
-    launch_set_background(c, src[0], src[1], src[2], src[3]);
+    for (int m = m0; m < m1; ++m) launch_set_background(c, m, src[0], src[1], src[2], src[3]);
     GWAM_CUDA(cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     GWAM_CUDA(cudaGetLastError());
     if (*c.flag_host) {
         c.err = "gwam_set_background: non-finite value, rho <= 0 or N^2 <= f^2";
+        for (int m = m0; m < m1; ++m) c.member_bg[m] = false;
         c.have_bg = false;
         return GWAM_ENUMERIC;
     }
+    for (int m = m0; m < m1; ++m) c.member_bg[m] = true;
     c.have_bg = true;
+    for (int m = 0; m < c.G.members; ++m) c.have_bg = c.have_bg && c.member_bg[m];
     API_END
 }
 
 int gwam_set_background(gwam_ctx* ctx, const double* u, const double* v, const double* n2, const double* rho)
 {
-    return set_background_impl(ctx, u, v, n2, rho, false);
+    return set_background_impl(ctx, -1, u, v, n2, rho, false);
 }
 
 int gwam_set_background_host(gwam_ctx* ctx, const double* u, const double* v, const double* n2, const double* rho)
 {
-    return set_background_impl(ctx, u, v, n2, rho, true);
+    return set_background_impl(ctx, -1, u, v, n2, rho, true);
+}
+
+int gwam_set_member_background(gwam_ctx* ctx, int member, const double* u, const double* v, const double* n2,
+                               const double* rho)
+{
+    if (member < 0) return GWAM_EINVAL;
+    return set_background_impl(ctx, member, u, v, n2, rho, false);
+}
+
+int gwam_set_member_background_host(gwam_ctx* ctx, int member, const double* u, const double* v, const double* n2,
+                                    const double* rho)
+{
+    if (member < 0) return GWAM_EINVAL;
+    return set_background_impl(ctx, member, u, v, n2, rho, true);
 }
 
 static int add_rays_impl(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n, bool host)
@@ -340,7 +375,8 @@ static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n
     if (host) {
         for (int64_t q = 0; q < n; ++q) {
             const gwam_spec& s = specs[q];
-            if (s.i < 0 || s.i >= c.G.nx || s.j < 0 || s.j >= c.G.ny || !(s.lambda_h > 0.0) || !(s.dz_launch > 0.0))
+            if (s.i < 0 || s.i >= c.G.nx || s.j < 0 || s.j >= c.G.ny || s.member < 0 || s.member >= c.G.members ||
+                !(s.lambda_h > 0.0) || !(s.dz_launch > 0.0))
                 return GWAM_EINVAL;
         }
         GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(gwam_spec) * (size_t)n));
@@ -394,11 +430,137 @@ int gwam_step_host(gwam_ctx* ctx, double dt, double* dudt_host, double* dvdt_hos
         return GWAM_ESTATE;
     }
     run_step(c, dt, nullptr, nullptr);
-    const size_t bytes = sizeof(double) * (size_t)c.G.ncell;
+    const size_t bytes = sizeof(double) * (size_t)c.G.ncell_all;
     if (dudt_host) GWAM_CUDA(cudaMemcpyAsync(dudt_host, c.dudt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
     if (dvdt_host) GWAM_CUDA(cudaMemcpyAsync(dvdt_host, c.dvdt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     GWAM_CUDA(cudaGetLastError());
+    API_END
+}
+
+int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
+{
+    API_BEGIN(ctx)
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_step_graph: no background";
+        return GWAM_ESTATE;
+    }
+    const int par = c.parity();
+    if (!c.gexec[par] || c.gdt[par] != dt || c.gdu[par] != dudt || c.gdv[par] != dvdt) {
+        if (c.gexec[par]) {
+            GWAM_CUDA(cudaGraphExecDestroy(c.gexec[par]));
+            c.gexec[par] = nullptr;
+        }
+        // capture one step on the internal stream; the ray buffers are swapped back afterwards
+        GWAM_CUDA(cudaStreamSynchronize(c.stream));
+        const bool prof = c.prof, tune = c.tune_active;
+        c.prof = false;
+        c.tune_active = false;
+        cudaStream_t user = c.stream;
+        c.stream = c.cap_stream;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            run_step(c, dt, dudt, dvdt);
+            e = cudaStreamEndCapture(c.cap_stream, &graph);
+            // run_step swapped A and B while capturing: restore the parity of the live state
+            RaySoA t = c.A;
+            c.A = c.B;
+            c.B = t;
+        }
+        c.stream = user;
+        c.prof = prof;
+        c.tune_active = tune;
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            c.err = std::string("graph capture: ") + cudaGetErrorString(e);
+            return GWAM_ECUDA;
+        }
+        e = cudaGraphInstantiate(&c.gexec[par], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c.gexec[par] = nullptr;
+            c.err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+            return GWAM_ECUDA;
+        }
+        c.gdt[par] = dt;
+        c.gdu[par] = dudt;
+        c.gdv[par] = dvdt;
+    }
+    GWAM_CUDA(cudaGraphLaunch(c.gexec[par], c.stream));
+    RaySoA t = c.A;
+    c.A = c.B;
+    c.B = t;
+    API_END
+}
+
+int gwam_set_launch_config(gwam_ctx* ctx, int kernel, int threads, int blocks)
+{
+    API_BEGIN(ctx)
+    if (kernel < 0 || kernel > 2 || threads < 64 || threads > kThreads || threads % 32 || blocks < 1 ||
+        blocks > c.max_blocks)
+        return GWAM_EINVAL;
+    c.lcfg[kernel] = LaunchCfg{threads, blocks};
+    for (int q = 0; q < 2; ++q)
+        if (c.gexec[q]) {
+            cudaGraphExecDestroy(c.gexec[q]);
+            c.gexec[q] = nullptr;
+        }
+    API_END
+}
+
+int gwam_get_launch_config(gwam_ctx* ctx, int kernel, int* threads, int* blocks)
+{
+    API_BEGIN(ctx)
+    if (kernel < 0 || kernel > 2 || !threads || !blocks) return GWAM_EINVAL;
+    *threads = c.lcfg[kernel].threads;
+    *blocks = c.lcfg[kernel].blocks;
+    API_END
+}
+
+int gwam_autotune(gwam_ctx* ctx, double dt, int steps_per_candidate, double* dudt, double* dvdt)
+{
+    API_BEGIN(ctx)
+    if (!(dt > 0.0) || steps_per_candidate < 1 || steps_per_candidate > Context::kTuneRing) return GWAM_EINVAL;
+    if (!c.have_bg) return GWAM_ESTATE;
+    if (!c.tune_ev[0][0])
+        for (int q = 0; q < Context::kTuneRing; ++q)
+            for (int p = 0; p < 6; ++p) GWAM_CUDA(cudaEventCreate(&c.tune_ev[q][p]));
+    // candidate shapes: threads x blocks-per-SM
+    const int cand_threads[] = {256, 128, 256, 128, 256, 128, 64};
+    const int cand_per_sm[] = {1, 2, 2, 4, 4, 8, 8};
+    const int ncand = 7;
+    double best_ms[3] = {1e300, 1e300, 1e300};
+    LaunchCfg best[3] = {c.lcfg[0], c.lcfg[1], c.lcfg[2]};
+    for (int q = 0; q < ncand; ++q) {
+        const LaunchCfg cfg{cand_threads[q], std::min(c.max_blocks, c.num_sms * cand_per_sm[q])};
+        for (int k = 0; k < 3; ++k) c.lcfg[k] = cfg;
+        c.tune_active = true;
+        c.tune_pending = 0;
+        for (int st = 0; st < steps_per_candidate; ++st) run_step(c, dt, dudt, dvdt);
+        c.tune_active = false;
+        GWAM_CUDA(cudaStreamSynchronize(c.stream));
+        GWAM_CUDA(cudaGetLastError());
+        double ms[3] = {0.0, 0.0, 0.0};
+        for (int st = 0; st < c.tune_pending; ++st)
+            for (int k = 0; k < 3; ++k) {
+                float v = 0.0f;
+                GWAM_CUDA(cudaEventElapsedTime(&v, c.tune_ev[st][2 * k], c.tune_ev[st][2 * k + 1]));
+                ms[k] += v;
+            }
+        for (int k = 0; k < 3; ++k)
+            if (ms[k] < best_ms[k]) {
+                best_ms[k] = ms[k];
+                best[k] = cfg;
+            }
+    }
+    for (int k = 0; k < 3; ++k) c.lcfg[k] = best[k];
+    for (int q = 0; q < 2; ++q)
+        if (c.gexec[q]) {
+            cudaGraphExecDestroy(c.gexec[q]);
+            c.gexec[q] = nullptr;
+        }
     API_END
 }
 
@@ -485,9 +647,10 @@ int gwam_get_gamma2_host(gwam_ctx* ctx, double* out_host)
     API_BEGIN(ctx)
     if (!out_host) return GWAM_EINVAL;
     double* tmp = nullptr;
-    GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * (size_t)c.G.ncell));
+    GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * (size_t)c.G.ncell_all));
     launch_gamma_to_caller(c, tmp);
-    GWAM_CUDA(cudaMemcpyAsync(out_host, tmp, sizeof(double) * (size_t)c.G.ncell, cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaMemcpyAsync(out_host, tmp, sizeof(double) * (size_t)c.G.ncell_all, cudaMemcpyDeviceToHost,
+                              c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     cudaFree(tmp);
     API_END

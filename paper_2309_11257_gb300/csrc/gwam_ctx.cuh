@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <string>
+#include <vector>
 
 #include "../../include/gwam.h"
 #include "gwam_device.cuh"
@@ -36,10 +37,16 @@ struct DevBudget {
 
 enum FieldId { F_ZL, F_ZP, F_LL, F_LP, F_PL, F_PP, F_EL, F_EP, F_WAD, NFIELD };
 
+struct LaunchCfg {
+    int threads, blocks;
+};
+
 struct Context {
     int device = 0;
     int num_sms = 0;
-    int grid_blocks = 0;            // persistent grid for ray kernels
+    int grid_blocks = 0;            // persistent grid of the lighter ray kernels
+    int max_blocks = 0;             // largest grid of a tally-producing kernel (partial-sum stride)
+    LaunchCfg lcfg[3] = {};         // advance, materialise, projection (autotuned)
     cudaStream_t stream = nullptr;
     Grid G{};
     Params P{};
@@ -104,17 +111,34 @@ struct Context {
     int64_t prof_steps = 0;
     double prof_ms[kPhases] = {};
 
-    int64_t field_len(int f) const { return (int64_t)G.ncol * (f <= F_ZP ? G.nz + 1 : G.nz); }
+    // CUDA graphs of the step, one per ray-buffer parity, keyed by (dt, dudt, dvdt)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    double gdt[2] = {0.0, 0.0};
+    double* gdu[2] = {nullptr, nullptr};
+    double* gdv[2] = {nullptr, nullptr};
+    std::vector<bool> member_bg;
+
+    // autotuning: event sets around the three heavy kernels, one per step
+    static constexpr int kTuneRing = 64;
+    bool tune_active = false;
+    int tune_pending = 0;
+    cudaEvent_t tune_ev[kTuneRing][6] = {};
+
+    int parity() const { return A.a[0] == ray_mem[0] ? 0 : 1; }
+    int64_t field_len(int f) const { return (int64_t)G.ncol_all * (f <= F_ZP ? G.nz + 1 : G.nz); }
 };
 
 // kernels, launched from the host side (gwam_step.cu / gwam_launch.cu)
-void launch_set_background(Context& c, const double* u, const double* v, const double* n2, const double* rho);
+void launch_set_background(Context& c, int member, const double* u, const double* v, const double* n2,
+                           const double* rho);
 void launch_add_rays(Context& c, const double* const in[13], int64_t n);
 void launch_background_source(Context& c, const gwam_bg_source& src);
 void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
 void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();
 void prof_mark(Context& c, int phase);
+void tune_mark(Context& c, int idx);
 void prof_harvest(Context& c);
 void launch_gather_rays(Context& c, double* state13, long long* ids, int* cells, int64_t cap);
 void launch_field_to_caller(Context& c, const double* src, double* dst, int nlev);

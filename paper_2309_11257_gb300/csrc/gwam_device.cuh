@@ -52,7 +52,9 @@ __device__ __forceinline__ double rsqrt_nr(double x)
 struct Grid {
     int geometry;          // 0 f-plane, 1 sphere
     int nx, ny, nz;
-    int ncol, ncell;       // nx*ny, nx*ny*nz
+    int ncol, ncell;       // per member: nx*ny, nx*ny*nz
+    int members;           // ensemble members (independent backgrounds and ray populations)
+    int ncol_all, ncell_all;   // members * ncol, members * ncell
     double dX, dY, dz;     // coordinate spacings (radians on the sphere)
     double y0;             // southern edge (-pi/2) or 0
     double Lx, Ly;         // periods in x (2 pi or nx dx) and y (f-plane)
@@ -79,6 +81,15 @@ struct RaySoA {
 };
 
 enum { SX, SY, SZ, SK, SL, SM, SEX, SEY, SEZ, SPX, SPY, SPZ, SN, NSTATE };
+
+// Ray ids are 64-bit: the ensemble member in the top 8 bits, a running number below.  Cells are
+// global: member * ncell + (j * nx + i) * nz + k, so the canonical array is member-major.
+constexpr int kMemberShift = 56;
+__host__ __device__ __forceinline__ int member_of(long long id) { return (int)((unsigned long long)id >> kMemberShift); }
+__host__ __device__ __forceinline__ long long with_member(int m, long long local)
+{
+    return (long long)(((unsigned long long)m << kMemberShift) | (unsigned long long)local);
+}
 
 __device__ __forceinline__ void load_ray(const RaySoA& R, int64_t i, double s[NSTATE], long long& id)
 {

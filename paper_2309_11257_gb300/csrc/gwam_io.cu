@@ -12,7 +12,7 @@ __global__ void k_gather_rays(Grid G, RaySoA A, const Ctl* ctl, double* __restri
         load_ray(A, p, s, id);
         for (int q = 0; q < NSTATE; ++q) out[q * n + p] = s[q];
         ids[p] = id;
-        cells[p] = cell_of(G, s);
+        cells[p] = member_of(id) * G.ncell + cell_of(G, s);
     }
 }
 
@@ -22,37 +22,41 @@ void launch_gather_rays(Context& c, double* state13, long long* ids, int* cells,
     k_gather_rays<<<blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, state13, ids, cells, n);
 }
 
-// column-major [col][nlev] -> [nlev][ny][nx]
+// column-major [member][col][nlev] -> [member][nlev][ny][nx]
 __global__ void k_to_caller(Grid G, const double* __restrict__ src, double* __restrict__ dst, int nlev)
 {
-    const int64_t total = (int64_t)G.ncol * nlev;
+    const int64_t per = (int64_t)G.ncol * nlev;
+    const int64_t total = per * G.members;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t col = t % G.ncol;
-        const int lev = (int)(t / G.ncol);
-        dst[t] = src[col * nlev + lev];
+        const int64_t m = t / per, r = t - m * per;
+        const int64_t col = r % G.ncol;
+        const int lev = (int)(r / G.ncol);
+        dst[t] = src[m * per + col * nlev + lev];
     }
 }
 
 __global__ void k_gamma_to_caller(Grid G, const Node* __restrict__ bg, double* __restrict__ dst)
 {
-    const int64_t total = (int64_t)G.ncell;
+    const int64_t per = (int64_t)G.ncell;
+    const int64_t total = per * G.members;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t col = t % G.ncol;
-        const int lev = (int)(t / G.ncol);
-        dst[t] = bg[col * G.nz + lev].v[3];
+        const int64_t m = t / per, r = t - m * per;
+        const int64_t col = r % G.ncol;
+        const int lev = (int)(r / G.ncol);
+        dst[t] = bg[m * per + col * G.nz + lev].v[3];
     }
 }
 
 void launch_field_to_caller(Context& c, const double* src, double* dst, int nlev)
 {
-    const int64_t total = (int64_t)c.G.ncol * nlev;
+    const int64_t total = (int64_t)c.G.ncol_all * nlev;
     const int blocks = (int)std::min<int64_t>((total + kThreads - 1) / kThreads, 8192);
     k_to_caller<<<blocks, kThreads, 0, c.stream>>>(c.G, src, dst, nlev);
 }
 
 void launch_gamma_to_caller(Context& c, double* dst)
 {
-    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 8192);
+    const int blocks = (int)std::min<int64_t>((c.G.ncell_all + kThreads - 1) / kThreads, 8192);
     k_gamma_to_caller<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg, dst);
 }
 

@@ -130,15 +130,17 @@ void configure_launch_kernels()
     cudaFuncSetAttribute(k_set_background, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-void launch_set_background(Context& c, const double* u, const double* v, const double* n2, const double* rho)
+void launch_set_background(Context& c, int member, const double* u, const double* v, const double* n2,
+                           const double* rho)
 {
     const int TW = 32;
     const int ntx = (c.G.nx + TW - 1) / TW;
     const size_t shm = sizeof(double) * 4 * (size_t)c.G.nz * TW;
-    k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg, c.rho,
-                                                                c.rho_inv, c.flag_dev);
+    const int64_t o = (int64_t)member * c.G.ncell;
+    k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg + o,
+                                                                c.rho + o, c.rho_inv + o, c.flag_dev);
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
-    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg);
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o);
 }
 
 // ----------------------------------------------------------------------------- explicit rays
@@ -149,7 +151,7 @@ struct RayInputPtrs {
 };
 
 __global__ void k_add_rays(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, RayInputPtrs in, int n_add, int pass,
-                           int* flags, double* partials)
+                           int* flags, double* partials, int pstride)
 {
     const int n0 = ctl->n;
     const long long next = ctl->next_id;
@@ -181,7 +183,7 @@ __global__ void k_add_rays(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, RayInpu
         }
     }
     const double wb = block_sum(w);
-    if (threadIdx.x == 0 && pass == 1) partials[T_LAUNCH * gridDim.x + blockIdx.x] = wb;
+    if (threadIdx.x == 0 && pass == 1) partials[T_LAUNCH * pstride + blockIdx.x] = wb;
 }
 
 __global__ void k_append_close(Ctl* ctl, int64_t max_rays, int added)
@@ -199,15 +201,16 @@ void launch_add_rays(Context& c, const double* const in[13], int64_t n)
     for (int q = 0; q < 13; ++q) d_in.p[q] = in[q];
     cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream);
     k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, c.max_rays, d_in, (int)n, 0, c.flag_dev,
-                                                         c.partials);
+                                                         c.partials, c.max_blocks);
     cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
     cudaStreamSynchronize(c.stream);
     if (*c.flag_host) {
         c.err = "gwam_add_rays: a ray volume lies outside the domain or is invalid";
         throw (int)GWAM_EINVAL;
     }
+    cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, c.stream);
     k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, c.max_rays, d_in, (int)n, 1, c.flag_dev,
-                                                         c.partials);
+                                                         c.partials, c.max_blocks);
     finalize_tallies(c, 1 << T_LAUNCH, 0);
     k_append_close<<<1, 1, 0, c.stream>>>(c.ctl, c.max_rays, (int)n);
 }
@@ -232,14 +235,15 @@ __device__ __forceinline__ double f_am(double p, double tau, double fs, double f
 }
 
 struct Bin {
-    int i, j;
+    int i, j, member;
     double z_launch, dz_launch, theta, c, lambda_h, flux, frac;
 };
 
 // 0 = filtered, 1 = launched (state in s)
-__device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict__ bg, const Bin& b,
+__device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict__ bg_all, const Bin& b,
                                            double s[NSTATE])
 {
+    const Node* bg = bg_all + (int64_t)b.member * G.ncell;
     const double X = __dmul_rn(b.i + 0.5, G.dX);
     const double Y = row_lat(G, b.j);
     const double Z = b.z_launch + 0.5 * b.dz_launch;
@@ -277,7 +281,9 @@ __device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict
 __device__ __forceinline__ bool source_bin(const Grid& G, const gwam_bg_source& src, int t, Bin& b)
 {
     const int nbins = src.n_az * src.n_c;
-    const int col = t / nbins, bin = t % nbins;
+    const int gcol = t / nbins, bin = t % nbins;
+    b.member = gcol / G.ncol;
+    const int col = gcol - b.member * G.ncol;
     b.j = col / G.nx;
     b.i = col % G.nx;
     const double pdeg = row_lat(G, b.j) * (180.0 / kPi);
@@ -297,7 +303,7 @@ __device__ __forceinline__ bool source_bin(const Grid& G, const gwam_bg_source& 
 
 __device__ __forceinline__ bool spec_bin(const gwam_spec& sp, Bin& b)
 {
-    b.i = sp.i; b.j = sp.j;
+    b.i = sp.i; b.j = sp.j; b.member = sp.member;
     b.z_launch = sp.z_launch; b.dz_launch = sp.dz_launch; b.theta = sp.theta; b.c = sp.c;
     b.lambda_h = sp.lambda_h; b.flux = sp.flux; b.frac = sp.spectral_frac;
     return true;
@@ -307,7 +313,7 @@ __device__ __forceinline__ bool spec_bin(const gwam_spec& sp, Bin& b)
 template <bool kSpec>
 __global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ctl* ctl, int64_t max_rays,
                          gwam_bg_source src, const gwam_spec* __restrict__ specs, int total, int pass,
-                         int* __restrict__ flag, double* __restrict__ partials)
+                         int* __restrict__ flag, double* __restrict__ partials, int pstride)
 {
     const int n0 = ctl->n;
     const long long next = ctl->next_id;
@@ -330,14 +336,14 @@ __global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ctl* ctl
                 set_status(ctl, GWAM_ECAPACITY);
                 continue;
             }
-            store_ray(A, pos, s, next + flag[t]);
+            store_ray(A, pos, s, with_member(b.member, next + flag[t]));
             w += ray_action(s);
         }
     }
     const double wb = block_sum(w);
     const long long fb = block_sum(filtered);
     if (threadIdx.x == 0) {
-        if (pass == 1) partials[T_LAUNCH * gridDim.x + blockIdx.x] = wb;
+        if (pass == 1) partials[T_LAUNCH * pstride + blockIdx.x] = wb;
         if (pass == 0 && fb) atomicAdd((unsigned long long*)&ctl->n_filtered, (unsigned long long)fb);
     }
 }
@@ -375,18 +381,19 @@ static void launch_common(Context& c, const gwam_bg_source* src, const gwam_spec
     const int nb = c.grid_blocks;
     if (specs) {
         k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 0,
-                                                      flag, c.partials);
+                                                      flag, c.partials, c.max_blocks);
     } else {
         k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 0,
-                                                       flag, c.partials);
+                                                       flag, c.partials, c.max_blocks);
     }
     exclusive_scan(c, flag, flag, total, nullptr);
+    cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, c.stream);
     if (specs) {
         k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 1,
-                                                      flag, c.partials);
+                                                      flag, c.partials, c.max_blocks);
     } else {
         k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 1,
-                                                       flag, c.partials);
+                                                       flag, c.partials, c.max_blocks);
     }
     finalize_tallies(c, 1 << T_LAUNCH, 0);
     k_launch_close<<<1, 1, 0, c.stream>>>(c.ctl, c.max_rays, flag, (int)total);
@@ -395,7 +402,7 @@ static void launch_common(Context& c, const gwam_bg_source* src, const gwam_spec
 
 void launch_background_source(Context& c, const gwam_bg_source& src)
 {
-    const int64_t total = (int64_t)c.G.ncol * src.n_az * src.n_c;
+    const int64_t total = (int64_t)c.G.ncol_all * src.n_az * src.n_c;
     launch_common(c, &src, nullptr, total);
 }
 

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A
                                                         Ctl* ctl, double dt, int* __restrict__ info,
                                                         int4* __restrict__ ccell, int4* __restrict__ cslot,
                                                         int* __restrict__ newid, int* __restrict__ cnt,
-                                                        double* __restrict__ partials)
+                                                        double* __restrict__ partials, int pstride)
 {
     const int n = ctl->n;
     double w_exit = 0.0, w_inv = 0.0;
@@ -158,7 +158,9 @@ __global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A
         double s[NSTATE];
         long long id;
         load_ray(A, i, s, id);
-        rk3(G, bg, s, dt);
+        const int mem = member_of(id);
+        const Node* bgm = bg + (int64_t)mem * G.ncell;
+        rk3(G, bgm, s, dt);
         wrap_position(G, s);
         const int st = ray_status(G, s);
         int code = 0, nch = 0;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A
                     ++n_exit;
                     w_exit += ray_action(ch);
                 } else {
-                    cc[c] = cell_of(G, ch);
+                    cc[c] = mem * G.ncell + cell_of(G, ch);
                     sl[c] = atomicAdd(&cnt[cc[c]], 1);
                 }
             }
@@ -197,8 +199,8 @@ __global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A
     const double wi = block_sum(w_inv);
     const long long ne = block_sum(n_exit), ni = block_sum(n_inv), nv = block_sum(n_sv), nh = block_sum(n_sh);
     if (threadIdx.x == 0) {
-        partials[T_EXIT * gridDim.x + blockIdx.x] = we;
-        partials[T_INVALID * gridDim.x + blockIdx.x] = wi;
+        partials[T_EXIT * pstride + blockIdx.x] = we;
+        partials[T_INVALID * pstride + blockIdx.x] = wi;
         if (ne) atomicAdd((unsigned long long*)&ctl->n_exited, (unsigned long long)ne);
         if (ni) atomicAdd((unsigned long long*)&ctl->n_invalid, (unsigned long long)ni);
         if (nv) atomicAdd((unsigned long long*)&ctl->n_split_v, (unsigned long long)nv);
@@ -215,7 +217,7 @@ __global__ void k_scatter(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, const in
 {
     const int n = ctl->n;
     const long long next = ctl->next_id;
-    const int total = off[G.ncell];
+    const int total = off[G.ncell_all];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl->n_children = total;
         ctl->new_ids = newid[n];
@@ -232,7 +234,7 @@ __global__ void k_scatter(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, const in
             if (cs[c] < 0) continue;
             const int64_t pos = (int64_t)off[cs[c]] + ss[c];
             if (pos >= max_rays) continue;
-            ent_id[pos] = c == 0 ? pid : next + newid[i] + c - 1;
+            ent_id[pos] = c == 0 ? pid : with_member(member_of(pid), next + newid[i] + c - 1);
             ent_src[pos] = i * 4 + c;
         }
     }
@@ -242,7 +244,7 @@ __global__ void k_scatter(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, const in
 __global__ void k_cap_find(Grid G, Params P, Ctl* ctl, const int* __restrict__ off, int* __restrict__ overlist)
 {
     if (ctl->status) return;
-    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < G.ncol; col += gridDim.x * blockDim.x) {
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < G.ncol_all; col += gridDim.x * blockDim.x) {
         const int cnt = off[(col + 1) * G.nz] - off[col * G.nz];
         if (cnt > P.cap) overlist[atomicAdd(&ctl->n_over, 1)] = col;
     }
@@ -255,7 +257,8 @@ __global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA
                                                           const int* __restrict__ off,
                                                           const int* __restrict__ overlist,
                                                           const long long* __restrict__ ent_id, int* ent_src,
-                                                          double* ecap, int* cnt, double* __restrict__ partials)
+                                                          double* ecap, int* cnt, double* __restrict__ partials,
+                                                          int pstride)
 {
     double w_cap = 0.0;
     long long n_cap = 0;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA
             make_child(G, s, info[src >> 2] & 7, src & 3, ch);
             Geo g;
             Intr in;
-            intrinsic_at(G, bg, ch, g, in);
+            intrinsic_at(G, bg + (int64_t)member_of(id) * G.ncell, ch, g, in);
             ecap[e] = in.w * ray_action(ch);
         }
         __syncthreads();
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA
                 make_child(G, s, info[src >> 2] & 7, src & 3, ch);
                 w_cap += ray_action(ch);
                 ++n_cap;
-                atomicSub(&cnt[cell_of(G, ch)], 1);
+                atomicSub(&cnt[member_of(pid) * G.ncell + cell_of(G, ch)], 1);
                 ent_src[e] = -1 - src;
             }
         }
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA
     const double wc = block_sum(w_cap);
     const long long nc = block_sum(n_cap);
     if (threadIdx.x == 0) {
-        partials[T_CAP * gridDim.x + blockIdx.x] = wc;
+        partials[T_CAP * pstride + blockIdx.x] = wc;
         if (nc) atomicAdd((unsigned long long*)&ctl->n_capped, (unsigned long long)nc);
     }
 }
@@ -315,7 +318,7 @@ __global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const i
                           int* __restrict__ sorted_src, int* __restrict__ biglist)
 {
     if (ctl->status) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell_all; c += gridDim.x * blockDim.x) {
         const int a = off[c];
         const int L = off[c + 1] - a;
         if (L == 0) continue;
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
                                                             double* __restrict__ k2)
 {
     if (ctl->status) return;
-    const int n_new = off2[G.ncell];
+    const int n_new = off2[G.ncell_all];
     const int n_old = ctl->n;
     const long long next = ctl->next_id;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_new; p += gridDim.x * blockDim.x) {
@@ -394,12 +397,12 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
         long long id;
         load_ray(A, i, s, id);
         make_child(G, s, info[i] & 7, c, ch);
-        const long long cid = c == 0 ? id : next + newid[i] + c - 1;
+        const long long cid = c == 0 ? id : with_member(member_of(id), next + newid[i] + c - 1);
         store_ray(B, p, ch, cid);
         if (P.saturation) {
             Geo g;
             Intr in;
-            intrinsic_at(G, bg, ch, g, in);
+            intrinsic_at(G, bg + (int64_t)member_of(id) * G.ncell, ch, g, in);
             int ci, cj, ck;
             cell_ijk(G, ch, ci, cj, ck);
             const double av = ray_action(ch) * inv_cell_volume(G, cj, ck);
@@ -415,7 +418,7 @@ __global__ void k_sat_kappa(Grid G, const Ctl* ctl, const int* __restrict__ off2
                             double* __restrict__ kappa)
 {
     if (ctl->status) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell; c += gridDim.x * blockDim.x) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell_all; c += gridDim.x * blockDim.x) {
         const int a = off2[c], b = off2[c + 1];
         if (a == b) continue;
         double Pc = 0.0, Q = 0.0;
@@ -444,9 +447,10 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                                                         double* __restrict__ f_ll, double* __restrict__ f_lp,
                                                         double* __restrict__ f_pl, double* __restrict__ f_pp,
                                                         double* __restrict__ e_l, double* __restrict__ e_p,
-                                                        double* __restrict__ wad, double* __restrict__ partials)
+                                                        double* __restrict__ wad, double* __restrict__ partials,
+                                                        int pstride)
 {
-    const int n = ctl->status ? 0 : off2[G.ncell];
+    const int n = ctl->status ? 0 : off2[G.ncell_all];
     double w_sat = 0.0, w_tot = 0.0;
     const int stride = gridDim.x * blockDim.x;
     for (int p0 = blockIdx.x * blockDim.x; p0 < n; p0 += stride) {
@@ -472,13 +476,14 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
             }
             const double W = ray_action(s);
             w_tot += W;
+            const int mem = member_of(id);
             Geo g;
             Intr in;
-            intrinsic_at(G, bg, s, g, in);
+            intrinsic_at(G, bg + (int64_t)mem * G.ncell, s, g, in);
             int ci, cj, ck;
             cell_ijk(G, s, ci, cj, ck);
-            key = (cj * G.nx + ci) * G.nz + ck;
-            col = cj * G.nx + ci;
+            col = mem * G.ncol + cj * G.nx + ci;
+            key = col * G.nz + ck;
             const double Vj = ray_volume(G, s, g);
             const double A = W * rcp_nr(Vj);               // N dk dl dm
             const double aw = W * inv_cell_volume(G, cj, ck);   // alpha_j A_j with alpha_j = V_j / V_c
@@ -549,8 +554,8 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
     const double ws = block_sum(w_sat);
     const double wt = block_sum(w_tot);
     if (threadIdx.x == 0) {
-        partials[T_SAT * gridDim.x + blockIdx.x] = ws;
-        partials[T_TOTAL * gridDim.x + blockIdx.x] = wt;
+        partials[T_SAT * pstride + blockIdx.x] = ws;
+        partials[T_TOTAL * pstride + blockIdx.x] = wt;
     }
 }
 
@@ -560,11 +565,13 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
 // reused beyond the pole rows on the sphere, periodic in y on the f-plane.
 __global__ void k_smooth(Grid G, const double* __restrict__ in, double* __restrict__ out, int nlev)
 {
-    const int64_t total = (int64_t)G.ncol * nlev;
+    const int64_t total = (int64_t)G.ncol_all * nlev;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int lev = (int)(t % nlev);
-        const int col = (int)(t / nlev);
+        const int gcol = (int)(t / nlev);
+        const int mem = gcol / G.ncol, col = gcol - mem * G.ncol;
         const int i = col % G.nx, j = col / G.nx;
+        const int64_t base = (int64_t)mem * G.ncol;
         double acc = 0.0;
 #pragma unroll
         for (int dj = -1; dj <= 1; ++dj) {
@@ -575,7 +582,7 @@ __global__ void k_smooth(Grid G, const double* __restrict__ in, double* __restri
             for (int di = -1; di <= 1; ++di) {
                 const int ii = wrap_int(i + di, G.nx);
                 const double w = (di == 0 ? 2.0 : 1.0) * (dj == 0 ? 2.0 : 1.0);
-                acc += w * in[((int64_t)jj * G.nx + ii) * nlev + lev];
+                acc += w * in[(base + (int64_t)jj * G.nx + ii) * nlev + lev];
             }
         }
         out[t] = acc * (1.0 / 16.0);
@@ -596,8 +603,18 @@ __global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, con
     double* tu = tile;
     double* tv = tile + (size_t)TW * G.nz;
     const int ntx = (G.nx + TW - 1) / TW;
-    const int j = blockIdx.x / ntx;
-    const int i0 = (blockIdx.x % ntx) * TW;
+    const int mem = blockIdx.x / (ntx * G.ny);
+    const int bl = blockIdx.x - mem * ntx * G.ny;
+    const int j = bl / ntx;
+    const int i0 = (bl % ntx) * TW;
+    {
+        // this member's planes
+        const int64_t oc = (int64_t)mem * G.ncell, oz = (int64_t)mem * G.ncol * (G.nz + 1);
+        fzl += oz; fzp += oz;
+        fll += oc; flp += oc; fpl += oc; fpp += oc; el += oc; ep += oc; rho_inv += oc;
+        if (du) du += oc;
+        if (dv) dv += oc;
+    }
     const int nz = G.nz;
     const int n = TW * nz;
     const double h2x = 0.5 * G.inv_dX, h2y = 0.5 * G.inv_dY;
@@ -711,7 +728,12 @@ static void swap_soa(Context& c)
 
 void finalize_tallies(Context& c, int mask, int mode)
 {
-    k_finalize<<<1, kThreads, 0, c.stream>>>(c.ctl, c.budget, c.partials, c.grid_blocks, mask, mode);
+    k_finalize<<<1, kThreads, 0, c.stream>>>(c.ctl, c.budget, c.partials, c.max_blocks, mask, mode);
+}
+
+void tune_mark(Context& c, int idx)
+{
+    if (c.tune_active) cudaEventRecord(c.tune_ev[c.tune_pending][idx], c.stream);
 }
 
 void configure_launch_kernels();
@@ -751,15 +773,21 @@ void run_step(Context& c, double dt, double* du, double* dv)
     const Params& P = c.P;
     cudaStream_t s = c.stream;
     const int nb = c.grid_blocks;
-    const int cell_blocks = (int)std::min<int64_t>((G.ncell + kThreads - 1) / kThreads, 65535LL * 4);
+    const int cell_blocks = (int)std::min<int64_t>((G.ncell_all + kThreads - 1) / kThreads, 65535LL * 4);
+    const LaunchCfg& la = c.lcfg[0];
+    const LaunchCfg& lm = c.lcfg[1];
+    const LaunchCfg& lp = c.lcfg[2];
     k_step_begin<<<1, 1, 0, s>>>(c.ctl);
-    cudaMemsetAsync(c.cnt, 0, sizeof(int) * (size_t)(G.ncell + 1), s);
+    cudaMemsetAsync(c.cnt, 0, sizeof(int) * (size_t)(G.ncell_all + 1), s);
+    cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, s);
     prof_mark(c, 0);
-    k_advance<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bg, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
-                                      c.partials);
+    tune_mark(c, 0);
+    k_advance<<<la.blocks, la.threads, 0, s>>>(G, P, c.A, c.bg, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
+                                               c.partials, c.max_blocks);
+    tune_mark(c, 1);
     prof_mark(c, 1);
     exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
-    exclusive_scan(c, c.cnt, c.off, G.ncell, nullptr);
+    exclusive_scan(c, c.cnt, c.off, G.ncell_all, nullptr);
     k_scatter<<<nb, kThreads, 0, s>>>(G, c.A, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off, c.ent_id,
                                       c.ent_src);
     int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
@@ -767,24 +795,30 @@ void run_step(Context& c, double dt, double* du, double* dv)
     if (P.cap > 0) {
         k_cap_find<<<cell_blocks, kThreads, 0, s>>>(G, P, c.ctl, c.off, c.overlist);
         k_cap_apply<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bg, c.ctl, c.info, c.off, c.overlist, c.ent_id, c.ent_src,
-                                            c.ecap, c.cnt, c.partials);
-        exclusive_scan(c, c.cnt, c.off2, G.ncell, nullptr);
+                                            c.ecap, c.cnt, c.partials, c.max_blocks);
+        exclusive_scan(c, c.cnt, c.off2, G.ncell_all, nullptr);
         off2 = c.off2;
         mask |= 1 << T_CAP;
     }
     k_segsort<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.sorted_src, c.biglist);
     k_segsort_big<<<nb, kThreads, 0, s>>>(c.ctl, c.off, off2, c.biglist, c.ent_id, c.ent_src, c.sorted_src);
-    k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell, c.ctl);
-    k_materialize<<<nb, kThreads, 0, s>>>(G, P, c.A, c.B, c.bg, c.ctl, off2, c.sorted_src, c.info, c.newid, c.pj,
-                                          c.k2);
+    k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
+    tune_mark(c, 2);
+    k_materialize<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A, c.B, c.bg, c.ctl, off2, c.sorted_src, c.info, c.newid,
+                                                   c.pj, c.k2);
+    tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation)
         k_sat_kappa<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, off2, c.rho, c.pj, c.k2, dt, c.kappa);
     prof_mark(c, 3);
     for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
-    k_project<<<nb, kThreads, 0, s>>>(G, P, c.B, c.bg, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL], c.field[F_ZP],
-                                      c.field[F_LL], c.field[F_LP], c.field[F_PL], c.field[F_PP], c.field[F_EL],
-                                      c.field[F_EP], c.field[F_WAD], c.partials);
+    tune_mark(c, 4);
+    k_project<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B, c.bg, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL],
+                                               c.field[F_ZP], c.field[F_LL], c.field[F_LP], c.field[F_PL],
+                                               c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD],
+                                               c.partials, c.max_blocks);
+    tune_mark(c, 5);
+    if (c.tune_active) ++c.tune_pending;
     prof_mark(c, 4);
     double* const* fl = c.field;
     if (P.smoothing) {
@@ -798,10 +832,10 @@ void run_step(Context& c, double dt, double* du, double* dv)
     const int TW = G.nz <= 96 ? 32 : 16;
     const size_t shm = sizeof(double) * 2 * (size_t)TW * G.nz;
     const int ntx = (G.nx + TW - 1) / TW;
-    k_divergence<<<ntx * G.ny, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP], fl[F_PL], fl[F_PP],
+    k_divergence<<<ntx * G.ny * G.members, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP], fl[F_PL], fl[F_PP],
                                                    fl[F_EL], fl[F_EP], c.rho_inv, du ? du : c.dudt_buf,
                                                    dv ? dv : c.dvdt_buf);
-    k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, nb, mask, 1);
+    k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, c.max_blocks, mask, 1);
     prof_mark(c, 5);
     swap_soa(c);
 }

@@ -26,6 +26,7 @@ GWAM_OK, GWAM_EINVAL, GWAM_ENOMEM, GWAM_ECAPACITY, GWAM_ENUMERIC, GWAM_ECUDA, GW
 STATUS_NAMES = {0: "GWAM_OK", -1: "GWAM_EINVAL", -2: "GWAM_ENOMEM", -3: "GWAM_ECAPACITY", -4: "GWAM_ENUMERIC",
                 -5: "GWAM_ECUDA", -6: "GWAM_ETIMEOUT", -7: "GWAM_ESTATE"}
 STATE_NAMES = ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "px", "py", "pz", "n")
+MEMBER_SHIFT = 56     # ray ids carry the ensemble member in their top 8 bits
 FIELD_NAMES = ("fz_l", "fz_p", "f_ll", "f_lp", "f_pl", "f_pp", "e_l", "e_p", "wad")
 
 
@@ -44,7 +45,8 @@ class Grid(C.Structure):
 class Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("gamma_mode", C.c_int), ("saturation", C.c_int), ("smoothing", C.c_int),
                 ("flux_form", C.c_int), ("splitting", C.c_int), ("cap_per_column", C.c_int),
-                ("alpha_s", C.c_double), ("min_split_dz", C.c_double), ("max_rays", C.c_int64)]
+                ("alpha_s", C.c_double), ("min_split_dz", C.c_double), ("max_rays", C.c_int64),
+                ("members", C.c_int)]
 
 
 class BgSource(C.Structure):
@@ -55,7 +57,7 @@ class BgSource(C.Structure):
 
 
 class Spec(C.Structure):
-    _fields_ = [("i", C.c_int), ("j", C.c_int), ("pad_", C.c_int), ("z_launch", C.c_double),
+    _fields_ = [("i", C.c_int), ("j", C.c_int), ("member", C.c_int), ("z_launch", C.c_double),
                 ("dz_launch", C.c_double), ("theta", C.c_double), ("c", C.c_double),
                 ("lambda_h", C.c_double), ("flux", C.c_double), ("spectral_frac", C.c_double)]
 
@@ -83,6 +85,8 @@ SIGNATURES = {
     "gwam_destroy": (None, [_vp]),
     "gwam_set_background": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "gwam_set_background_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gwam_set_member_background": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "gwam_set_member_background_host": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "gwam_add_rays": (C.c_int, [_vp, _P(RayInput), C.c_int64]),
     "gwam_add_rays_host": (C.c_int, [_vp, _P(RayInput), C.c_int64]),
     "gwam_launch_sources": (C.c_int, [_vp, _P(BgSource)]),
@@ -90,6 +94,10 @@ SIGNATURES = {
     "gwam_launch_spectral_host": (C.c_int, [_vp, _vp, C.c_int64]),
     "gwam_step": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "gwam_step_host": (C.c_int, [_vp, C.c_double, _vp, _vp]),
+    "gwam_step_graph": (C.c_int, [_vp, C.c_double, _vp, _vp]),
+    "gwam_set_launch_config": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "gwam_get_launch_config": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(C.c_int)]),
+    "gwam_autotune": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp]),
     "gwam_num_rays": (C.c_int, [_vp, _P(C.c_int64)]),
     "gwam_get_rays_host": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int64]),
     "gwam_get_stats": (C.c_int, [_vp, _P(Stats)]),
@@ -148,13 +156,14 @@ def cell_offsets(cells, ncell: int, offsets=None, stream=None):
 class Tracer:
     """One ray-volume context on the current CUDA device."""
 
-    def __init__(self, grid: dict, params: dict, max_rays: int, stream=None):
+    def __init__(self, grid: dict, params: dict, max_rays: int, stream=None, members: int = 1):
         import torch
         self.grid = dict(grid)
-        self.params = dict(params)
+        self.params = dict(params, members=members)
+        self.members = members
         self.nx, self.ny, self.nz = grid["nx"], grid["ny"], grid["nz"]
         self.max_rays = int(max_rays)
-        p = dict(params, max_rays=self.max_rays)
+        p = dict(params, max_rays=self.max_rays, members=members)
         p.setdefault("precision", 0)
         self._g = _struct(Grid, grid)
         self._p = _struct(Params, p)
@@ -189,6 +198,15 @@ class Tracer:
         else:
             self._check(_lib.gwam_set_background(self._h, *[_ptr(a) for a in (u, v, n2, rho)]), "set_background")
 
+    def set_member_background(self, member: int, u, v, n2, rho):
+        if isinstance(u, np.ndarray):
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, n2, rho)]
+            self._check(_lib.gwam_set_member_background_host(self._h, member, *[a.ctypes.data_as(_vp) for a in arrs]),
+                        "set_member_background_host")
+        else:
+            self._check(_lib.gwam_set_member_background(self._h, member, *[_ptr(a) for a in (u, v, n2, rho)]),
+                        "set_member_background")
+
     def add_rays(self, r: dict):
         names = ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "dk", "dl", "dm", "n")
         arrs = [np.ascontiguousarray(r[n], dtype=np.float64) for n in names]
@@ -200,19 +218,46 @@ class Tracer:
         self._check(_lib.gwam_launch_sources(self._h, C.byref(s)), "launch_sources")
 
     def launch_spectral(self, specs: np.ndarray):
-        """specs: numpy structured array with the fields of gwam_spec (host)."""
-        n = len(specs)
-        arr = (Spec * max(n, 1))()
-        for q in range(n):
-            for name, _ in Spec._fields_:
-                setattr(arr[q], name, specs[name][q].item())
-        self._check(_lib.gwam_launch_spectral_host(self._h, C.cast(arr, _vp), n), "launch_spectral_host")
+        """specs: numpy structured array laid out like gwam_spec (synth.SPEC_DTYPE, host memory)."""
+        specs = np.ascontiguousarray(specs)
+        assert specs.dtype.itemsize == C.sizeof(Spec) and all(
+            specs.dtype.fields[n][1] == getattr(Spec, n).offset for n, _ in Spec._fields_), "spec layout"
+        self._check(_lib.gwam_launch_spectral_host(self._h, specs.ctypes.data_as(_vp), len(specs)),
+                    "launch_spectral_host")
 
     # -------------------------------------------------------------- step
     def step(self, dt: float, dudt=None, dvdt=None):
         """Stream-ordered step; dudt/dvdt: device tensors [nz][ny][nx] float64 or None."""
         self._check(_lib.gwam_step(self._h, float(dt), _ptr(dudt) if dudt is not None else None,
                                    _ptr(dvdt) if dvdt is not None else None), "step")
+
+    def step_graph(self, dt: float, dudt=None, dvdt=None):
+        """Step replayed from a captured CUDA graph (captured on first use for these buffers)."""
+        self._check(_lib.gwam_step_graph(self._h, float(dt), _ptr(dudt) if dudt is not None else None,
+                                         _ptr(dvdt) if dvdt is not None else None), "step_graph")
+
+    KERNELS = ("advance", "materialize", "project")
+
+    def launch_config(self) -> dict:
+        out = {}
+        for k, name in enumerate(self.KERNELS):
+            t, b = C.c_int(), C.c_int()
+            self._check(_lib.gwam_get_launch_config(self._h, k, C.byref(t), C.byref(b)), "get_launch_config")
+            out[name] = (t.value, b.value)
+        return out
+
+    def set_launch_config(self, cfg: dict):
+        for k, name in enumerate(self.KERNELS):
+            if name in cfg:
+                t, b = cfg[name]
+                self._check(_lib.gwam_set_launch_config(self._h, k, int(t), int(b)), "set_launch_config")
+
+    def autotune(self, dt: float, steps_per_candidate: int = 2, dudt=None, dvdt=None) -> dict:
+        """Advance the simulation while timing candidate launch shapes; keep the fastest per kernel."""
+        self._check(_lib.gwam_autotune(self._h, float(dt), int(steps_per_candidate),
+                                       _ptr(dudt) if dudt is not None else None,
+                                       _ptr(dvdt) if dvdt is not None else None), "autotune")
+        return self.launch_config()
 
     def step_host(self, dt: float, dudt: np.ndarray, dvdt: np.ndarray):
         """Step with host (numpy, ideally pinned) output buffers; synchronising."""
@@ -234,8 +279,10 @@ class Tracer:
         self._check(_lib.gwam_get_rays_host(self._h, st.ctypes.data_as(_vp), ids.ctypes.data_as(_vp),
                                             cells.ctypes.data_as(_vp), cap), "get_rays_host")
         out = {name: st[q, :n].copy() for q, name in enumerate(STATE_NAMES)}
-        out["id"] = ids[:n].copy()
-        out["cell"] = cells[:n].copy()
+        out["id"] = ids[:n] & ((1 << MEMBER_SHIFT) - 1)
+        out["member"] = (ids[:n] >> MEMBER_SHIFT).astype(np.int32)
+        ncell = self.nx * self.ny * self.nz
+        out["cell"] = cells[:n] - out["member"] * ncell
         return out
 
     def stats(self) -> dict:
@@ -246,14 +293,14 @@ class Tracer:
     def field(self, name: str) -> np.ndarray:
         which = FIELD_NAMES.index(name)
         nl = self.nz + 1 if which < 2 else self.nz
-        out = np.zeros((nl, self.ny, self.nx))
+        out = np.zeros((self.members, nl, self.ny, self.nx))
         self._check(_lib.gwam_get_field_host(self._h, which, out.ctypes.data_as(_vp)), "get_field_host")
-        return out
+        return out[0] if self.members == 1 else out
 
     def gamma2(self) -> np.ndarray:
-        out = np.zeros((self.nz, self.ny, self.nx))
+        out = np.zeros((self.members, self.nz, self.ny, self.nx))
         self._check(_lib.gwam_get_gamma2_host(self._h, out.ctypes.data_as(_vp)), "get_gamma2_host")
-        return out
+        return out[0] if self.members == 1 else out
 
     PHASES = ("advance", "rebin", "saturation", "projection", "grid")
 

@@ -39,9 +39,10 @@ P0 = 101325.0
 
 SEED_BASE = 2309_11257
 
-SPEC_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("pad_", np.int32), ("z_launch", np.float64),
+# laid out like the C struct of an explicit spectral launch (aligned: 72 bytes)
+SPEC_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("member", np.int32), ("z_launch", np.float64),
                        ("dz_launch", np.float64), ("theta", np.float64), ("c", np.float64),
-                       ("lambda_h", np.float64), ("flux", np.float64), ("spectral_frac", np.float64)])
+                       ("lambda_h", np.float64), ("flux", np.float64), ("spectral_frac", np.float64)], align=True)
 
 DEFAULT_PARAMS = dict(gamma_mode=1, saturation=1, smoothing=1, flux_form=0, splitting=1,
                       cap_per_column=4800, alpha_s=2.5, min_split_dz=1000.0)
@@ -250,3 +251,18 @@ def ensemble_members(grid: dict, members: int = 16, tag: int = 4):
     amps = g.uniform(30.0, 80.0, members)
     lats = g.uniform(30.0, 60.0, members)
     return [jet_background(grid, amp=float(a), lat_deg=float(p)) for a, p in zip(amps, lats)], amps, lats
+
+
+def ensemble_workload(members: int = 16, nx: int = 256, ny: int = 128, nz: int = 90):
+    """Batched ensemble: `members` spheres (jets U[30, 80] m/s at U[30, 60] deg), each with the
+    background source at 5 km and convective spectral launches at 10 km: lognormal(ln 16, 1) rays
+    per column, capped at 512 (uneven per-column counts)."""
+    grid = sphere_grid(nx=nx, ny=ny, nz=nz, dz=1000.0)
+    bgs, amps, lats = ensemble_members(grid, members)
+    specs = []
+    for m in range(members):
+        sp = convective_specs(grid, tag=400 + m, median=16.0, sigma=1.0, cap=512, z_launch=10e3)
+        sp["member"] = m
+        specs.append(sp)
+    return dict(name="ensemble", grid=grid, params=dict(DEFAULT_PARAMS), backgrounds=bgs, specs=specs,
+                source=background_source(), dt=180.0, members=members, amps=amps, lats=lats)

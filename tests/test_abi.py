@@ -62,9 +62,24 @@ def test_init_rejects_bad_arguments_before_touching_the_device(gw):
     assert lib.gwam_last_error(None) == b"null context"
 
 
-def test_struct_layouts_match_the_header(gw):
-    # sizes of the POD structs as the C compiler lays them out
-    assert C.sizeof(gw.Grid) == 4 * 4 + 7 * 8
-    assert C.sizeof(gw.Params) == 7 * 4 + 4 + 2 * 8 + 8
-    assert C.sizeof(gw.Spec) == 16 + 7 * 8
-    assert C.sizeof(gw.Stats) == 11 * 8 + 6 * 8
+def test_struct_layouts_match_the_header(gw, tmp_path):
+    """sizeof/offsetof of every POD struct as gcc lays out include/gwam.h, against the binding."""
+    structs = {"gwam_grid": gw.Grid, "gwam_params": gw.Params, "gwam_bg_source": gw.BgSource,
+               "gwam_spec": gw.Spec, "gwam_stats": gw.Stats, "gwam_ray_input": gw.RayInput}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gwam.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(out["%s.%s" % (cname, fname)]) == getattr(py, fname).offset, (cname, fname)
