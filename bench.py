@@ -37,6 +37,8 @@ WORKLOAD = "sphere 256x128x90, background source 983040 ray volumes, dt 180 s, F
 # divide, square root and trigonometric call as one operation.
 FLOPS_PER_RAY_STEP = 1460.0
 FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+# Precision form: algorithmic bytes of the ray step = the 64-byte ray record read and written once.
+BYTES_PER_RAY_STEP_FP32 = 128.0
 HBM_PEAK = None
 
 
@@ -159,7 +161,10 @@ def gpu_arm(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     w = synth.workload(args.workload)
-    grid, params = w["grid"], w["params"]
+    grid, params = w["grid"], dict(w["params"])
+    fp32 = args.workload == "sphere_fp32"
+    if fp32:
+        params["precision"] = 1
     nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
     T = gwam.Tracer(grid, params, max_rays=int(2.5 * 32 * nx * ny))
     bg_dev = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in w["background"]]
@@ -205,14 +210,23 @@ def gpu_arm(args, rank, world, local_rank):
         tot_rs = float(r.item())
     value = tot_rs / (ms_max / 1000.0)
 
-    # roofline of the dominant kernel (advance: FP64-pipe bound)
+    # roofline of the dominant kernel
     adv_ms = phases["advance"] / max(nprof, 1)
     rays_per_launch = ray_steps / args.steps
-    achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)",
-                "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
+    if fp32:
+        # precision form: the ray step reads and writes the 64-byte record
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        achieved = BYTES_PER_RAY_STEP_FP32 * rays_per_launch / (adv_ms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "kernel": "k_advance32 (FP32 RK3 ray step)", "achieved": achieved,
+                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                    "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
+    else:
+        achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "traffic": None, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)",
+                    "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
 
     # end to end through the public API with host buffers: each step uploads that step's
     # background from pinned host memory and reads du/dt, dv/dt back into pinned host memory
@@ -250,7 +264,7 @@ def gpu_arm(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "sphere" else args.workload, "rays_live_start": s0["n_live"], "rays_live_end": s1["n_live"],
                        "ray_steps_timed": ray_steps, "l2": "working set > L2 (ray state ~0.12-0.24 GB + "
                        "grid fields ~0.4 GB per step), no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -340,7 +354,7 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "sphere_half", "ensemble"],
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "sphere_half", "ensemble", "sphere_fp32"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
                          "ensemble: 16 members of the sphere with convective sources, graph-replayed steps")
     args = ap.parse_args()

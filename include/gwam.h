@@ -73,7 +73,9 @@ typedef struct {
 
 /* Method switches (App. B, Sec. 3c) and capacity. */
 typedef struct {
-    int precision;        /* 0: FP64 throughout */
+    int precision;        /* 0: FP64 throughout; 1: precision form -- ray kinematics in FP32 with
+                             positions as cell index + FP32 offsets, FP64 only for the saturation
+                             sums, the flux accumulation and the budget */
     int gamma_mode;       /* 0: Gamma = 0; 1: Gamma^2 = (d ln rho/dz)^2 / 4 (Sec. 2a) */
     int saturation;       /* spectral saturation of Sec. 3c on/off */
     int smoothing;        /* horizontal 1-2-1 flux smoothing (App. B.4 on a lat-lon grid) on/off */

@@ -32,8 +32,9 @@ static void dalloc(Context& c, T*& p, size_t count)
 
 static void free_all(Context& c)
 {
-    void* ptrs[] = {c.bg, c.rho, c.rho_inv, c.tables, c.bg_scratch, c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
-                    c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.ecap, c.cnt, c.off, c.off2,
+    void* ptrs[] = {c.bg, c.bg32, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.bg_scratch,
+                    c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
+                    c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
                     c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
                     c.flag_dev};
     for (void* p : ptrs)
@@ -91,7 +92,7 @@ using namespace gwam;
 
 extern "C" {
 
-const char* gwam_version(void) { return "gwam-gb300 0.1 (sm_103a, FP64 form)"; }
+const char* gwam_version(void) { return "gwam-gb300 0.2 (sm_103a; FP64 and FP32-kinematics forms)"; }
 
 int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, void* stream)
 {
@@ -104,7 +105,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
     if (!(grid->g > 0.0)) return GWAM_EINVAL;
     if ((int64_t)grid->nx * grid->ny * (grid->nz + 1) >= (int64_t)1 << 31) return GWAM_EINVAL;
     if (grid->nz > 192) return GWAM_EINVAL;   // column tiles of the transposing kernels live in shared memory
-    if (params->precision != 0) return GWAM_EINVAL;
+    if (params->precision != 0 && params->precision != 1) return GWAM_EINVAL;
     if (params->max_rays < 1 || params->max_rays >= ((int64_t)1 << 29)) return GWAM_EINVAL;
     if (!(params->alpha_s > 0.0) || !(params->min_split_dz >= 0.0)) return GWAM_EINVAL;
     if (params->flux_form != 0 && params->flux_form != 1) return GWAM_EINVAL;
@@ -192,11 +193,19 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.row_inv_cos = c.tables + G.ny;
             G.lev_inv_r = c.tables + 2 * G.ny;
         }
+        c.f32 = params->precision == 1;
         for (int b = 0; b < 2; ++b) {
-            dalloc(c, c.ray_mem[b], 7 * nr);
-            RaySoA& R = b == 0 ? c.A : c.B;
-            for (int q = 0; q < 7; ++q) R.a[q] = c.ray_mem[b] + q * nr;
+            if (c.f32) {
+                dalloc(c, c.ray32_mem[b], 4 * nr);
+                Ray32SoA& R = b == 0 ? c.A32 : c.B32;
+                for (int q = 0; q < 4; ++q) R.q[q] = c.ray32_mem[b] + q * nr;
+            } else {
+                dalloc(c, c.ray_mem[b], 7 * nr);
+                RaySoA& R = b == 0 ? c.A : c.B;
+                for (int q = 0; q < 7; ++q) R.a[q] = c.ray_mem[b] + q * nr;
+            }
         }
+        if (c.f32) dalloc(c, c.bg32, ncell);
         dalloc(c, c.info, nr);
         dalloc(c, c.ccell, nr);
         dalloc(c, c.cslot, nr);
@@ -207,6 +216,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         dalloc(c, c.pj, nr);
         dalloc(c, c.k2, nr);
         dalloc(c, c.kappa, nr);
+        dalloc(c, c.raycell, nr);
         dalloc(c, c.ecap, nr);
         dalloc(c, c.cnt, ncell + 1);
         dalloc(c, c.off, ncell + 1);
@@ -269,7 +279,10 @@ static int set_background_impl(gwam_ctx* ctx, int member, const double* u, const
     }
     const int m0 = member < 0 ? 0 : member, m1 = member < 0 ? c.G.members : member + 1;
     GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
-    for (int m = m0; m < m1; ++m) launch_set_background(c, m, src[0], src[1], src[2], src[3]);
+    for (int m = m0; m < m1; ++m) {
+        launch_set_background(c, m, src[0], src[1], src[2], src[3]);
+        if (c.f32) convert_background32(c, m);
+    }
     GWAM_CUDA(cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     GWAM_CUDA(cudaGetLastError());
@@ -464,10 +477,8 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
         if (e == cudaSuccess) {
             run_step(c, dt, dudt, dvdt);
             e = cudaStreamEndCapture(c.cap_stream, &graph);
-            // run_step swapped A and B while capturing: restore the parity of the live state
-            RaySoA t = c.A;
-            c.A = c.B;
-            c.B = t;
+            // run_step swapped the ray buffers while capturing: restore the live parity
+            swap_rays(c);
         }
         c.stream = user;
         c.prof = prof;
@@ -489,9 +500,7 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
         c.gdv[par] = dvdt;
     }
     GWAM_CUDA(cudaGraphLaunch(c.gexec[par], c.stream));
-    RaySoA t = c.A;
-    c.A = c.B;
-    c.B = t;
+    swap_rays(c);
     API_END
 }
 
@@ -586,7 +595,10 @@ int gwam_get_rays_host(gwam_ctx* ctx, double* state13, int64_t* ids, int32_t* ce
     GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * 13 * (size_t)n));
     GWAM_CUDA(cudaMalloc((void**)&tid, sizeof(long long) * (size_t)n));
     GWAM_CUDA(cudaMalloc((void**)&tcell, sizeof(int) * (size_t)n));
-    launch_gather_rays(c, tmp, tid, tcell, n);
+    if (c.f32)
+        launch_gather_rays32(c, tmp, tid, tcell, n);
+    else
+        launch_gather_rays(c, tmp, tid, tcell, n);
     for (int q = 0; q < 13 && state13; ++q)
         GWAM_CUDA(cudaMemcpyAsync(state13 + q * cap, tmp + q * n, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
                                   c.stream));
@@ -630,6 +642,7 @@ int gwam_get_field_host(gwam_ctx* ctx, int which, double* out_host)
 {
     API_BEGIN(ctx)
     if (which < 0 || which >= NFIELD || !out_host) return GWAM_EINVAL;
+    if (c.P.smoothing) smooth_field(c, which);
     const double* src = c.P.smoothing ? c.smooth[which] : c.field[which];
     const int nlev = which <= F_ZP ? c.G.nz + 1 : c.G.nz;
     double* tmp = nullptr;

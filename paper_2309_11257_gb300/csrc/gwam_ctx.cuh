@@ -62,8 +62,12 @@ struct Context {
     double* bg_scratch = nullptr;   // staging of caller fields ([nz][ny][nx], 4 fields)
 
     // ray volumes: A holds the canonical array between steps, B is the re-binned output
+    bool f32 = false;               // precision form: FP32 records and background
     RaySoA A{}, B{};
     double2* ray_mem[2] = {nullptr, nullptr};
+    Ray32SoA A32{}, B32{};
+    float4* ray32_mem[2] = {nullptr, nullptr};
+    Node32* bg32 = nullptr;
 
     // per-ray scratch
     int* info = nullptr;            // split code | children << 4 | status << 8
@@ -76,6 +80,7 @@ struct Context {
     double* pj = nullptr;           // saturation: P_j (incl. alpha_j)
     double* k2 = nullptr;           // saturation: K_j^2
     double* kappa = nullptr;        // saturation: kappa of the carrier cell, per ray
+    int* raycell = nullptr;         // global cell of every ray in the canonical array
     double* ecap = nullptr;         // cap: energies of the entries of over-full columns
 
     // per-cell scratch
@@ -125,7 +130,20 @@ struct Context {
     int tune_pending = 0;
     cudaEvent_t tune_ev[kTuneRing][6] = {};
 
-    int parity() const { return A.a[0] == ray_mem[0] ? 0 : 1; }
+    // exchange the canonical and the re-binned ray buffers of whichever form the context uses
+    void swap_rays_()
+    {
+        if (f32) {
+            Ray32SoA t = A32;
+            A32 = B32;
+            B32 = t;
+        } else {
+            RaySoA t = A;
+            A = B;
+            B = t;
+        }
+    }
+    int parity() const { return f32 ? (A32.q[0] == ray32_mem[0] ? 0 : 1) : (A.a[0] == ray_mem[0] ? 0 : 1); }
     int64_t field_len(int f) const { return (int64_t)G.ncol_all * (f <= F_ZP ? G.nz + 1 : G.nz); }
 };
 
@@ -137,6 +155,11 @@ void launch_background_source(Context& c, const gwam_bg_source& src);
 void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
 void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();
+void smooth_field(Context& c, int f);
+inline void swap_rays(Context& c) { c.swap_rays_(); }
+void run_step32(Context& c, double dt, double* du, double* dv);
+void convert_background32(Context& c, int member);
+void launch_gather_rays32(Context& c, double* state13, long long* ids, int* cells, int64_t n);
 void prof_mark(Context& c, int phase);
 void tune_mark(Context& c, int idx);
 void prof_harvest(Context& c);

@@ -119,6 +119,21 @@ struct __align__(128) Node {
     double d[4][3];    // d/dX, d/dY, d/dz of each
 };
 
+// FP32 background node of the precision form: the same 16 quantities in FP32 (64 bytes)
+struct __align__(64) Node32 {
+    float v[4];
+    float d[4][3];
+};
+
+// FP32 ray record of the precision form, 64 bytes as four float4 arrays:
+//   q[0] = (member-local cell as int bits, ox, oy, oz)    offsets in cell units, in [0, 1)
+//   q[1] = (k, l, m, N)
+//   q[2] = (eX, eY, eZ, Px)                               extents in coordinate units
+//   q[3] = (Py, Pz, id low 32 bits, id high 32 bits)
+struct Ray32SoA {
+    float4* q[4];
+};
+
 __host__ __device__ __forceinline__ int64_t node_index(const Grid& G, int i, int j, int k)
 {
     return ((int64_t)j * G.nx + i) * G.nz + k;

@@ -1,0 +1,433 @@
+// gwam_fp32.cu -- kernels and step of the precision form (FP32 kinematics, FP64 accumulation).
+// The re-binning (scans, cap bookkeeping, segment sort), smoothing and divergence are shared
+// with the FP64 form; only the kernels that touch ray state are specialised here.
+#include <algorithm>
+
+#include "gwam_common.cuh"
+#include "gwam_fp32.cuh"
+
+namespace gwam {
+
+__global__ void k_bg_to32(const Node* __restrict__ bg, Node32* __restrict__ bg32, int64_t n)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        Node32 o;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            o.v[f] = (float)bg[c].v[f];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) o.d[f][q] = (float)bg[c].d[f][q];
+        }
+        bg32[c] = o;
+    }
+}
+
+void convert_background32(Context& c, int member)
+{
+    const int64_t o = (int64_t)member * c.G.ncell;
+    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
+    k_bg_to32<<<blocks, kThreads, 0, c.stream>>>(c.bg + o, c.bg32 + o, c.G.ncell);
+}
+
+// RK3 advance in FP32 (the ray-step kernel of the precision form): state read and written in
+// place, exits, split decisions, child cells and slots as in k_advance.
+__global__ void __launch_bounds__(kThreads) k_advance32(Grid G, Params P, Ray32SoA A, const Node32* __restrict__ bg,
+                                                          Ctl* ctl, float dt, int* __restrict__ info,
+                                                          int4* __restrict__ ccell, int4* __restrict__ cslot,
+                                                          int* __restrict__ newid, int* __restrict__ cnt,
+                                                          double* __restrict__ partials, int pstride)
+{
+    const int n = ctl->n;
+    double w_exit = 0.0, w_inv = 0.0;
+    long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        S32 s;
+        load32(G, A, i, s);
+        const int mem = member_of(s.id);
+        rk3_32(G, bg + (int64_t)mem * G.ncell, s, dt);
+        const int st = renormalize32(G, s);
+        int code = 0, nch = 0;
+        int cc[4] = {-1, -1, -1, -1}, sl[4] = {0, 0, 0, 0};
+        if (st == 2) {
+            ++n_inv;
+            const double w = action32(s);
+            if (isfinite(w)) w_inv += w;
+        } else if (st == 1) {
+            ++n_exit;
+            w_exit += action32(s);
+        } else {
+            code = split_code32(G, P, s);
+            nch = num_children(code);
+            if (code & 1) ++n_sv;
+            if (code & 2) n_sh += (code & 1) ? 2 : 1;
+            for (int c = 0; c < nch; ++c) {
+                S32 ch;
+                if (make_child32(G, s, code, c, ch) != 0) {
+                    ++n_exit;
+                    w_exit += action32(ch);
+                } else {
+                    cc[c] = mem * G.ncell + cell32(G, ch);
+                    sl[c] = atomicAdd(&cnt[cc[c]], 1);
+                }
+            }
+            store32(G, A, i, s);
+        }
+        info[i] = code | (nch << 4) | (st << 8);
+        ccell[i] = make_int4(cc[0], cc[1], cc[2], cc[3]);
+        cslot[i] = make_int4(sl[0], sl[1], sl[2], sl[3]);
+        newid[i] = nch > 0 ? nch - 1 : 0;
+    }
+    const double we = block_sum(w_exit);
+    const double wi = block_sum(w_inv);
+    const long long ne = block_sum(n_exit), ni = block_sum(n_inv), nv = block_sum(n_sv), nh = block_sum(n_sh);
+    if (threadIdx.x == 0) {
+        partials[T_EXIT * pstride + blockIdx.x] = we;
+        partials[T_INVALID * pstride + blockIdx.x] = wi;
+        if (ne) atomicAdd((unsigned long long*)&ctl->n_exited, (unsigned long long)ne);
+        if (ni) atomicAdd((unsigned long long*)&ctl->n_invalid, (unsigned long long)ni);
+        if (nv) atomicAdd((unsigned long long*)&ctl->n_split_v, (unsigned long long)nv);
+        if (nh) atomicAdd((unsigned long long*)&ctl->n_split_h, (unsigned long long)nh);
+    }
+}
+
+__device__ __forceinline__ long long id32(const Ray32SoA& A, int64_t i)
+{
+    const float4 d = A.q[3][i];
+    return (long long)(((unsigned long long)(unsigned)__float_as_int(d.w) << 32) | (unsigned)__float_as_int(d.z));
+}
+
+__global__ void k_scatter32(Grid G, Ray32SoA A, Ctl* ctl, int64_t max_rays, const int* __restrict__ info,
+                            const int4* __restrict__ ccell, const int4* __restrict__ cslot,
+                            const int* __restrict__ newid, const int* __restrict__ off,
+                            long long* __restrict__ ent_id, int* __restrict__ ent_src)
+{
+    const int n = ctl->n;
+    const long long next = ctl->next_id;
+    const int total = off[G.ncell_all];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->n_children = total;
+        ctl->new_ids = newid[n];
+        if ((int64_t)total > max_rays) set_status(ctl, GWAM_ECAPACITY);
+    }
+    if ((int64_t)total > max_rays) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int nch = (info[i] >> 4) & 7;
+        if (!nch) continue;
+        const int4 cc = ccell[i], sl = cslot[i];
+        const int cs[4] = {cc.x, cc.y, cc.z, cc.w}, ss[4] = {sl.x, sl.y, sl.z, sl.w};
+        const long long pid = id32(A, i);
+        for (int c = 0; c < nch; ++c) {
+            if (cs[c] < 0) continue;
+            const int64_t pos = (int64_t)off[cs[c]] + ss[c];
+            if (pos >= max_rays) continue;
+            ent_id[pos] = c == 0 ? pid : with_member(member_of(pid), next + newid[i] + c - 1);
+            ent_src[pos] = i * 4 + c;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cap_apply32(Grid G, Params P, Ray32SoA A,
+                                                            const Node32* __restrict__ bg, Ctl* ctl,
+                                                            const int* __restrict__ info, const int* __restrict__ off,
+                                                            const int* __restrict__ overlist,
+                                                            const long long* __restrict__ ent_id, int* ent_src,
+                                                            double* ecap, int* cnt, double* __restrict__ partials,
+                                                            int pstride)
+{
+    double w_cap = 0.0;
+    long long n_cap = 0;
+    const int nover = ctl->status ? 0 : ctl->n_over;
+    for (int w = blockIdx.x; w < nover; w += gridDim.x) {
+        const int col = overlist[w];
+        const int a = off[col * G.nz], b = off[(col + 1) * G.nz];
+        const int count = b - a;
+        for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+            const int src = ent_src[e];
+            S32 s, ch;
+            load32(G, A, src >> 2, s);
+            make_child32(G, s, info[src >> 2] & 7, src & 3, ch);
+            Intr32 in;
+            intrinsic32(G, bg + (int64_t)member_of(s.id) * G.ncell, ch, in);
+            ecap[e] = (double)in.w * action32(ch);
+        }
+        __syncthreads();
+        for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
+            const double E = ecap[e];
+            const long long id = ent_id[e];
+            int rank = 0;
+            for (int q = a; q < b; ++q) {
+                const double Eq = ecap[q];
+                rank += (Eq < E) || (Eq == E && ent_id[q] > id);
+            }
+            if (rank < count - P.cap) {
+                const int src = ent_src[e];
+                S32 s, ch;
+                load32(G, A, src >> 2, s);
+                make_child32(G, s, info[src >> 2] & 7, src & 3, ch);
+                w_cap += action32(ch);
+                ++n_cap;
+                atomicSub(&cnt[member_of(s.id) * G.ncell + cell32(G, ch)], 1);
+                ent_src[e] = -1 - src;
+            }
+        }
+        __syncthreads();
+    }
+    const double wc = block_sum(w_cap);
+    const long long nc = block_sum(n_cap);
+    if (threadIdx.x == 0) {
+        partials[T_CAP * pstride + blockIdx.x] = wc;
+        if (nc) atomicAdd((unsigned long long*)&ctl->n_capped, (unsigned long long)nc);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ray32SoA A, Ray32SoA B,
+                                                              const Node32* __restrict__ bg, Ctl* ctl,
+                                                              const int* __restrict__ off2,
+                                                              const int* __restrict__ sorted_src,
+                                                              const int* __restrict__ info,
+                                                              const int* __restrict__ newid,
+                                                              double* __restrict__ pj, double* __restrict__ k2,
+                                                              int* __restrict__ raycell)
+{
+    if (ctl->status) return;
+    const int n_new = off2[G.ncell_all];
+    const int n_old = ctl->n;
+    const long long next = ctl->next_id;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_new; p += gridDim.x * blockDim.x) {
+        const int src = sorted_src[p];
+        const int i = src >> 2, c = src & 3;
+        if (src < 0 || i >= n_old) {
+            set_status(ctl, GWAM_ECUDA);
+            continue;
+        }
+        S32 s, ch;
+        load32(G, A, i, s);
+        make_child32(G, s, info[i] & 7, c, ch);
+        if (c != 0) ch.id = with_member(member_of(s.id), next + newid[i] + c - 1);
+        store32(G, B, p, ch);
+        raycell[p] = member_of(ch.id) * G.ncell + cell32(G, ch);
+        if (P.saturation) {
+            Intr32 in;
+            intrinsic32(G, bg + (int64_t)member_of(ch.id) * G.ncell, ch, in);
+            const double av = action32(ch) * inv_cell_volume(G, ch.j, ch.k);
+            pj[p] = (double)(in.m2 * in.kh2 * in.iw * in.iK2) * av;
+            k2[p] = (double)in.K2;
+        }
+    }
+}
+
+// Saturation N update and flux projection; per-ray terms in FP32, accumulated in FP64.
+__global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32SoA B, const Node32* __restrict__ bg,
+                                                          const Ctl* ctl, const int* __restrict__ off2,
+                                                          const double* __restrict__ kappa,
+                                                          const double* __restrict__ k2, double dt,
+                                                          double* __restrict__ fz_l, double* __restrict__ fz_p,
+                                                          double* __restrict__ f_ll, double* __restrict__ f_lp,
+                                                          double* __restrict__ f_pl, double* __restrict__ f_pp,
+                                                          double* __restrict__ e_l, double* __restrict__ e_p,
+                                                          double* __restrict__ wad, double* __restrict__ partials,
+                                                          int pstride)
+{
+    const int n = ctl->status ? 0 : off2[G.ncell_all];
+    double w_sat = 0.0, w_tot = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < n; p0 += stride) {
+        const int p = p0 + threadIdx.x;
+        const bool act = p < n;
+        int key = -1;
+        double hv[7] = {0, 0, 0, 0, 0, 0, 0};
+        float zl = 0.0f, zp = 0.0f, wh = 0.0f, lo = 0.0f, hi = 0.0f;
+        int col = 0, kk0 = 1, nkk = 0;
+        if (act) {
+            S32 s;
+            load32(G, B, p, s);
+            if (P.saturation) {
+                const double kap = kappa[p];
+                if (kap > 0.0) {
+                    const double fac = fmax(0.0, 1.0 - 2.0 * kap * k2[p] * dt);
+                    const double nold = s.n;
+                    s.n = (float)(nold * fac);
+                    w_sat += (nold - (double)s.n) * (double)s.p[0] * (double)s.p[1] * (double)s.p[2];
+                    float4 q1 = B.q[1][p];
+                    q1.w = s.n;
+                    B.q[1][p] = q1;
+                }
+            }
+            const double W = (double)s.n * (double)s.p[0] * (double)s.p[1] * (double)s.p[2];
+            w_tot += W;
+            const int mem = member_of(s.id);
+            Intr32 in;
+            intrinsic32(G, bg + (int64_t)mem * G.ncell, s, in);
+            col = mem * G.ncol + s.j * G.nx + s.i;
+            key = col * G.nz + s.k;
+            const float Vj = in.g.hX * s.e[0] * (G.geometry == 1 ? in.g.r : 1.0f) * s.e[1] * s.e[2];
+            const float A = (float)W * __frcp_rn(Vj);
+            const float aw = (float)(W * inv_cell_volume(G, s.j, s.k));
+            const float k = s.w[0], l = s.w[1], m = s.w[2];
+            const float mg2c = in.mg2 * in.c;
+            const float chx = k * mg2c, chy = l * mg2c, chr = -m * in.kh2 * in.c;
+            float t_ll, t_lp, t_pl, t_pp, el, ep;
+            if (P.flux_form == 0) {
+                // 1/(w^2 - f^2) = K^2 / (D k_h^2): the algebraically equal form without the
+                // cancellation that FP32 suffers for near-inertial waves
+                const float iden = in.K2 * __frcp_rn(in.D * in.kh2);
+                t_ll = (in.w2 * chx * k + in.f2 * chy * l) * iden;
+                t_lp = (in.w2 * chx * l - in.f2 * chy * k) * iden;
+                t_pl = (in.w2 * chy * k - in.f2 * chx * l) * iden;
+                t_pp = (in.w2 * chy * l + in.f2 * chx * k) * iden;
+                zl = in.w2 * chr * k * iden;
+                zp = in.w2 * chr * l * iden;
+                el = -in.f2 * in.n2 * chr * iden * k;
+                ep = -in.f2 * in.n2 * chr * iden * l;
+            } else {
+                t_ll = chx * k; t_lp = chx * l; t_pl = chy * k; t_pp = chy * l;
+                zl = chr * k; zp = chr * l;
+                el = 0.0f; ep = 0.0f;
+            }
+            hv[0] = (double)(aw * t_ll); hv[1] = (double)(aw * t_lp); hv[2] = (double)(aw * t_pl);
+            hv[3] = (double)(aw * t_pp); hv[4] = (double)(aw * el); hv[5] = (double)(aw * ep); hv[6] = (double)aw;
+            zl *= A;
+            zp *= A;
+            wh = in.g.cphi * s.e[0] * s.e[1] * (float)(G.row_inv_cos[s.j] * G.inv_dX * G.inv_dY);
+            const float zc = ((float)s.k + s.o[2]) * (float)G.dz;
+            lo = zc - 0.5f * s.e[2];
+            hi = zc + 0.5f * s.e[2];
+            kk0 = max(1, (int)floorf(lo * (float)G.inv_dz - 0.5f));
+            const int kk1 = min(G.nz - 1, (int)ceilf(hi * (float)G.inv_dz + 0.5f));
+            nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
+        }
+        if (warp_segment_reduce(key, hv) && key >= 0) {
+            atomicAdd(&f_ll[key], hv[0]);
+            atomicAdd(&f_lp[key], hv[1]);
+            atomicAdd(&f_pl[key], hv[2]);
+            atomicAdd(&f_pp[key], hv[3]);
+            atomicAdd(&e_l[key], hv[4]);
+            atomicAdd(&e_p[key], hv[5]);
+            atomicAdd(&wad[key], hv[6]);
+        }
+        int maxk = nkk;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) maxk = max(maxk, __shfl_xor_sync(0xffffffffu, maxk, o));
+        for (int o = 0; o < maxk; ++o) {
+            double zv[2] = {0.0, 0.0};
+            int zkey = -1;
+            if (o < nkk) {
+                const int kk = kk0 + o;
+                const float slo = ((float)kk - 0.5f) * (float)G.dz, shi = ((float)kk + 0.5f) * (float)G.dz;
+                const float ov = fminf(hi, shi) - fmaxf(lo, slo);
+                if (ov > 0.0f) {
+                    const float w = wh * ov * (float)G.inv_dz;
+                    zv[0] = (double)(w * zl);
+                    zv[1] = (double)(w * zp);
+                    zkey = col * (G.nz + 1) + kk;
+                }
+            }
+            if (warp_segment_reduce(zkey, zv) && zkey >= 0) {
+                atomicAdd(&fz_l[zkey], zv[0]);
+                atomicAdd(&fz_p[zkey], zv[1]);
+            }
+        }
+    }
+    const double ws = block_sum(w_sat);
+    const double wt = block_sum(w_tot);
+    if (threadIdx.x == 0) {
+        partials[T_SAT * pstride + blockIdx.x] = ws;
+        partials[T_TOTAL * pstride + blockIdx.x] = wt;
+    }
+}
+
+__global__ void k_gather_rays32(Grid G, Ray32SoA A, double* __restrict__ out, long long* __restrict__ ids,
+                                int* __restrict__ cells, int64_t n)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        S32 s;
+        load32(G, A, p, s);
+        double d[NSTATE];
+        to_double(G, s, d);
+        for (int q = 0; q < NSTATE; ++q) out[q * n + p] = d[q];
+        ids[p] = s.id;
+        cells[p] = member_of(s.id) * G.ncell + cell32(G, s);
+    }
+}
+
+void launch_gather_rays32(Context& c, double* state13, long long* ids, int* cells, int64_t n)
+{
+    const int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096);
+    k_gather_rays32<<<blocks, kThreads, 0, c.stream>>>(c.G, c.A32, state13, ids, cells, n);
+}
+
+// kernels shared with the FP64 step (gwam_step.cu)
+__global__ void k_step_begin(Ctl* ctl);
+__global__ void k_cap_find(Grid G, Params P, Ctl* ctl, const int* __restrict__ off, int* __restrict__ overlist);
+__global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
+                          const long long* __restrict__ ent_id, const int* __restrict__ ent_src,
+                          int* __restrict__ sorted_src, int* __restrict__ biglist);
+__global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
+                              const int* __restrict__ biglist, const long long* __restrict__ ent_id,
+                              const int* __restrict__ ent_src, int* __restrict__ sorted_src);
+__global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl);
+__global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+                            const int* __restrict__ raycell, const double* __restrict__ rho,
+                            const double* __restrict__ pj, const double* __restrict__ k2, double dt,
+                            double* __restrict__ kappa);
+void grid_phase(Context& c, double* du, double* dv, int mask);
+
+void run_step32(Context& c, double dt, double* du, double* dv)
+{
+    const Grid& G = c.G;
+    const Params& P = c.P;
+    cudaStream_t s = c.stream;
+    const int nb = c.grid_blocks;
+    const int cell_blocks = (int)std::min<int64_t>((G.ncell_all + kThreads - 1) / kThreads, 65535LL * 4);
+    const LaunchCfg& la = c.lcfg[0];
+    const LaunchCfg& lm = c.lcfg[1];
+    const LaunchCfg& lp = c.lcfg[2];
+    k_step_begin<<<1, 1, 0, s>>>(c.ctl);
+    cudaMemsetAsync(c.cnt, 0, sizeof(int) * (size_t)(G.ncell_all + 1), s);
+    cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, s);
+    prof_mark(c, 0);
+    tune_mark(c, 0);
+    k_advance32<<<la.blocks, la.threads, 0, s>>>(G, P, c.A32, c.bg32, c.ctl, (float)dt, c.info, c.ccell, c.cslot,
+                                                 c.newid, c.cnt, c.partials, c.max_blocks);
+    tune_mark(c, 1);
+    prof_mark(c, 1);
+    exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
+    exclusive_scan(c, c.cnt, c.off, G.ncell_all, nullptr);
+    k_scatter32<<<nb, kThreads, 0, s>>>(G, c.A32, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off,
+                                        c.ent_id, c.ent_src);
+    int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
+    const int* off2 = c.off;
+    if (P.cap > 0) {
+        k_cap_find<<<cell_blocks, kThreads, 0, s>>>(G, P, c.ctl, c.off, c.overlist);
+        k_cap_apply32<<<nb, kThreads, 0, s>>>(G, P, c.A32, c.bg32, c.ctl, c.info, c.off, c.overlist, c.ent_id,
+                                              c.ent_src, c.ecap, c.cnt, c.partials, c.max_blocks);
+        exclusive_scan(c, c.cnt, c.off2, G.ncell_all, nullptr);
+        off2 = c.off2;
+        mask |= 1 << T_CAP;
+    }
+    k_segsort<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.sorted_src, c.biglist);
+    k_segsort_big<<<nb, kThreads, 0, s>>>(c.ctl, c.off, off2, c.biglist, c.ent_id, c.ent_src, c.sorted_src);
+    k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
+    tune_mark(c, 2);
+    k_materialize32<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A32, c.B32, c.bg32, c.ctl, off2, c.sorted_src, c.info,
+                                                     c.newid, c.pj, c.k2, c.raycell);
+    tune_mark(c, 3);
+    prof_mark(c, 2);
+    if (P.saturation)
+        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa);
+    prof_mark(c, 3);
+    for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
+    tune_mark(c, 4);
+    k_project32<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B32, c.bg32, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL],
+                                                 c.field[F_ZP], c.field[F_LL], c.field[F_LP], c.field[F_PL],
+                                                 c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD],
+                                                 c.partials, c.max_blocks);
+    tune_mark(c, 5);
+    if (c.tune_active) ++c.tune_pending;
+    prof_mark(c, 4);
+    grid_phase(c, du, dv, mask);
+    prof_mark(c, 5);
+    swap_rays(c);
+}
+
+}  // namespace gwam

@@ -7,6 +7,7 @@
 //               filtered, m from the inverted Eq. dispersion, m < 0 (upward group velocity),
 //               A = F / (|k_h| ch_r).
 #include "gwam_common.cuh"
+#include "gwam_fp32.cuh"
 
 namespace gwam {
 
@@ -150,8 +151,8 @@ struct RayInputPtrs {
     const double* p[13];
 };
 
-__global__ void k_add_rays(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, RayInputPtrs in, int n_add, int pass,
-                           int* flags, double* partials, int pstride)
+__global__ void k_add_rays(Grid G, RaySoA A, Ray32SoA A32, bool f32, Ctl* ctl, int64_t max_rays, RayInputPtrs in,
+                           int n_add, int pass, int* flags, double* partials, int pstride)
 {
     const int n0 = ctl->n;
     const long long next = ctl->next_id;
@@ -178,8 +179,15 @@ __global__ void k_add_rays(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, RayInpu
                 set_status(ctl, GWAM_ECAPACITY);
                 continue;
             }
-            store_ray(A, pos, s, next + q);
-            w += ray_action(s);
+            if (f32) {
+                S32 r;
+                from_double(G, s, next + q, r);
+                store32(G, A32, pos, r);
+                w += (double)action32(r);
+            } else {
+                store_ray(A, pos, s, next + q);
+                w += ray_action(s);
+            }
         }
     }
     const double wb = block_sum(w);
@@ -200,8 +208,8 @@ void launch_add_rays(Context& c, const double* const in[13], int64_t n)
     RayInputPtrs d_in;
     for (int q = 0; q < 13; ++q) d_in.p[q] = in[q];
     cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream);
-    k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, c.max_rays, d_in, (int)n, 0, c.flag_dev,
-                                                         c.partials, c.max_blocks);
+    k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.A32, c.f32, c.ctl, c.max_rays, d_in, (int)n, 0,
+                                                         c.flag_dev, c.partials, c.max_blocks);
     cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
     cudaStreamSynchronize(c.stream);
     if (*c.flag_host) {
@@ -209,8 +217,8 @@ void launch_add_rays(Context& c, const double* const in[13], int64_t n)
         throw (int)GWAM_EINVAL;
     }
     cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, c.stream);
-    k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.ctl, c.max_rays, d_in, (int)n, 1, c.flag_dev,
-                                                         c.partials, c.max_blocks);
+    k_add_rays<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.G, c.A, c.A32, c.f32, c.ctl, c.max_rays, d_in, (int)n, 1,
+                                                         c.flag_dev, c.partials, c.max_blocks);
     finalize_tallies(c, 1 << T_LAUNCH, 0);
     k_append_close<<<1, 1, 0, c.stream>>>(c.ctl, c.max_rays, (int)n);
 }
@@ -311,7 +319,8 @@ __device__ __forceinline__ bool spec_bin(const gwam_spec& sp, Bin& b)
 
 // pass 0: flag[t] = launches?, count filtered bins; pass 1: write launched rays in order
 template <bool kSpec>
-__global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ctl* ctl, int64_t max_rays,
+__global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ray32SoA A32, bool f32, Ctl* ctl,
+                         int64_t max_rays,
                          gwam_bg_source src, const gwam_spec* __restrict__ specs, int total, int pass,
                          int* __restrict__ flag, double* __restrict__ partials, int pstride)
 {
@@ -336,8 +345,16 @@ __global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ctl* ctl
                 set_status(ctl, GWAM_ECAPACITY);
                 continue;
             }
-            store_ray(A, pos, s, with_member(b.member, next + flag[t]));
-            w += ray_action(s);
+            const long long id = with_member(b.member, next + flag[t]);
+            if (f32) {
+                S32 r;
+                from_double(G, s, id, r);
+                store32(G, A32, pos, r);
+                w += (double)action32(r);
+            } else {
+                store_ray(A, pos, s, id);
+                w += ray_action(s);
+            }
         }
     }
     const double wb = block_sum(w);
@@ -380,19 +397,19 @@ static void launch_common(Context& c, const gwam_bg_source* src, const gwam_spec
     if (src) s0 = *src;
     const int nb = c.grid_blocks;
     if (specs) {
-        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 0,
+        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 0,
                                                       flag, c.partials, c.max_blocks);
     } else {
-        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 0,
+        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 0,
                                                        flag, c.partials, c.max_blocks);
     }
     exclusive_scan(c, flag, flag, total, nullptr);
     cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, c.stream);
     if (specs) {
-        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 1,
+        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 1,
                                                       flag, c.partials, c.max_blocks);
     } else {
-        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.ctl, c.max_rays, s0, specs, (int)total, 1,
+        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 1,
                                                        flag, c.partials, c.max_blocks);
     }
     finalize_tallies(c, 1 << T_LAUNCH, 0);

@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
                                                             const int* __restrict__ sorted_src,
                                                             const int* __restrict__ info,
                                                             const int* __restrict__ newid, double* __restrict__ pj,
-                                                            double* __restrict__ k2)
+                                                            double* __restrict__ k2, int* __restrict__ raycell)
 {
     if (ctl->status) return;
     const int n_new = off2[G.ncell_all];
@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
         make_child(G, s, info[i] & 7, c, ch);
         const long long cid = c == 0 ? id : with_member(member_of(id), next + newid[i] + c - 1);
         store_ray(B, p, ch, cid);
+        raycell[p] = member_of(id) * G.ncell + cell_of(G, ch);
         if (P.saturation) {
             Geo g;
             Intr in;
@@ -412,22 +413,28 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
     }
 }
 
-// kappa = max(0, (P - rho/2) / (2 dt sum_j P_j K_j^2)) of every carrier cell (Eq. turbulent-diffusivity)
-__global__ void k_sat_kappa(Grid G, const Ctl* ctl, const int* __restrict__ off2, const double* __restrict__ rho,
+// kappa = max(0, (P - rho/2) / (2 dt sum_j P_j K_j^2)) of every carrier cell (Eq. turbulent-diffusivity).
+// Rays are in cell order, so each cell is a contiguous segment: the first ray of a segment sums it
+// in order (deterministic) and hands kappa to all of its rays.  Iterating rays, not cells, skips the
+// many empty cells.
+__global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+                            const int* __restrict__ raycell, const double* __restrict__ rho,
                             const double* __restrict__ pj, const double* __restrict__ k2, double dt,
                             double* __restrict__ kappa)
 {
     if (ctl->status) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell_all; c += gridDim.x * blockDim.x) {
-        const int a = off2[c], b = off2[c + 1];
-        if (a == b) continue;
+    const int n = off2[ncell_all];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int c = raycell[p];
+        if (p > 0 && raycell[p - 1] == c) continue;
+        const int b = off2[c + 1];
         double Pc = 0.0, Q = 0.0;
-        for (int p = a; p < b; ++p) {
-            Pc += pj[p];
-            Q += pj[p] * k2[p];
+        for (int q = p; q < b; ++q) {
+            Pc += pj[q];
+            Q += pj[q] * k2[q];
         }
         const double kap = Q > 0.0 ? fmax(0.0, (Pc - 0.5 * rho[c]) / (2.0 * dt * Q)) : 0.0;
-        for (int p = a; p < b; ++p) kappa[p] = kap;
+        for (int q = p; q < b; ++q) kappa[q] = kap;
     }
 }
 
@@ -589,6 +596,57 @@ __global__ void k_smooth(Grid G, const double* __restrict__ in, double* __restri
     }
 }
 
+struct FieldSet {
+    const double* in[NFIELD];
+    double* out[NFIELD];
+};
+
+// The same smoothing for several fields in one launch: block (32 levels, 8 columns) of one row;
+// blockIdx.z selects the field.  Neighbour offsets are formed once per thread.
+__global__ void __launch_bounds__(256) k_smooth_fields(Grid G, FieldSet fs)
+{
+    const int f = blockIdx.z;
+    const int nlev = f <= F_ZP ? G.nz + 1 : G.nz;
+    const int ntx = (G.nx + 7) / 8;
+    const int mem = blockIdx.y;
+    const int j = blockIdx.x / ntx;
+    const int i = (blockIdx.x % ntx) * 8 + threadIdx.y;
+    if (i >= G.nx) return;
+    const int im = i == 0 ? G.nx - 1 : i - 1, ip = i + 1 == G.nx ? 0 : i + 1;
+    int jm = j - 1, jp = j + 1;
+    if (G.geometry == 1) {
+        jm = jm < 0 ? 0 : jm;
+        jp = jp >= G.ny ? G.ny - 1 : jp;
+    } else {
+        jm = jm < 0 ? G.ny - 1 : jm;
+        jp = jp >= G.ny ? 0 : jp;
+    }
+    const int64_t base = (int64_t)mem * G.ncol;
+    const int64_t r0 = (base + (int64_t)jm * G.nx) * nlev, r1 = (base + (int64_t)j * G.nx) * nlev,
+                  r2 = (base + (int64_t)jp * G.nx) * nlev;
+    const int64_t cm = (int64_t)im * nlev, c0 = (int64_t)i * nlev, cp = (int64_t)ip * nlev;
+    const double* __restrict__ F = fs.in[f];
+    double* __restrict__ O = fs.out[f];
+    for (int lev = threadIdx.x; lev < nlev; lev += 32) {
+        const double a = F[r0 + cm + lev] + 2.0 * F[r0 + c0 + lev] + F[r0 + cp + lev];
+        const double b = F[r1 + cm + lev] + 2.0 * F[r1 + c0 + lev] + F[r1 + cp + lev];
+        const double c = F[r2 + cm + lev] + 2.0 * F[r2 + c0 + lev] + F[r2 + cp + lev];
+        O[r1 + c0 + lev] = (a + 2.0 * b + c) * (1.0 / 16.0);
+    }
+}
+
+// smooth fields 0 .. nf-1 in one launch
+void launch_smooth(Context& c, int nf)
+{
+    FieldSet fs;
+    for (int f = 0; f < NFIELD; ++f) {
+        fs.in[f] = c.field[f];
+        fs.out[f] = c.smooth[f];
+    }
+    const dim3 grid((unsigned)(((c.G.nx + 7) / 8) * c.G.ny), (unsigned)c.G.members, (unsigned)nf);
+    k_smooth_fields<<<grid, dim3(32, 8), 0, c.stream>>>(c.G, fs);
+}
+
 // du/dt = -(1/rho) [ (1/(r cos phi)) (d_lambda F^{ll} + d_phi (cos phi F^{pl})) + d_z F^z_l ] + E_l / (g rho),
 // dv/dt likewise (Eq. mean-flow-impact; centred differences, flux zero beyond the pole rows).
 // One block per (row, tile of TW columns); results transposed through shared memory into the
@@ -719,11 +777,13 @@ __global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl) { ctl->n_new = 
 
 // ============================================================================ orchestration
 
-static void swap_soa(Context& c)
+
+// smoothed copy of field f for a read (the step smooths only the fields the divergence needs)
+void smooth_field(Context& c, int f)
 {
-    RaySoA t = c.A;
-    c.A = c.B;
-    c.B = t;
+    const int nlev = f <= F_ZP ? c.G.nz + 1 : c.G.nz;
+    const int blocks = (int)std::min<int64_t>((c.field_len(f) + kThreads - 1) / kThreads, 8192);
+    k_smooth<<<blocks, kThreads, 0, c.stream>>>(c.G, c.field[f], c.smooth[f], nlev);
 }
 
 void finalize_tallies(Context& c, int mask, int mode)
@@ -767,8 +827,34 @@ void prof_harvest(Context& c)
     c.prof_pending = 0;
 }
 
+// smoothing, divergence into du/dt, dv/dt, and the budget fold (shared by both forms)
+void grid_phase(Context& c, double* du, double* dv, int mask)
+{
+    const Grid& G = c.G;
+    cudaStream_t s = c.stream;
+    double* const* fl = c.field;
+    double* out_u = du ? du : c.dudt_buf;
+    double* out_v = dv ? dv : c.dvdt_buf;
+    if (c.P.smoothing) {
+        // the 8 fields the divergence needs (the wave-action density is smoothed only when read)
+        launch_smooth(c, F_WAD);
+        fl = c.smooth;
+    }
+    const int TW = G.nz <= 96 ? 32 : 16;
+    const size_t shm = sizeof(double) * 2 * (size_t)TW * G.nz;
+    const int ntx = (G.nx + TW - 1) / TW;
+    k_divergence<<<ntx * G.ny * G.members, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP],
+                                                               fl[F_PL], fl[F_PP], fl[F_EL], fl[F_EP], c.rho_inv,
+                                                               out_u, out_v);
+    k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, c.max_blocks, mask, 1);
+}
+
 void run_step(Context& c, double dt, double* du, double* dv)
 {
+    if (c.f32) {
+        run_step32(c, dt, du, dv);
+        return;
+    }
     const Grid& G = c.G;
     const Params& P = c.P;
     cudaStream_t s = c.stream;
@@ -805,11 +891,11 @@ void run_step(Context& c, double dt, double* du, double* dv)
     k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
     tune_mark(c, 2);
     k_materialize<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A, c.B, c.bg, c.ctl, off2, c.sorted_src, c.info, c.newid,
-                                                   c.pj, c.k2);
+                                                   c.pj, c.k2, c.raycell);
     tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation)
-        k_sat_kappa<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, off2, c.rho, c.pj, c.k2, dt, c.kappa);
+        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa);
     prof_mark(c, 3);
     for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);
@@ -820,24 +906,9 @@ void run_step(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 5);
     if (c.tune_active) ++c.tune_pending;
     prof_mark(c, 4);
-    double* const* fl = c.field;
-    if (P.smoothing) {
-        for (int f = 0; f < NFIELD; ++f) {
-            const int nlev = f <= F_ZP ? G.nz + 1 : G.nz;
-            const int blocks = (int)std::min<int64_t>((c.field_len(f) + kThreads - 1) / kThreads, 8192);
-            k_smooth<<<blocks, kThreads, 0, s>>>(G, c.field[f], c.smooth[f], nlev);
-        }
-        fl = c.smooth;
-    }
-    const int TW = G.nz <= 96 ? 32 : 16;
-    const size_t shm = sizeof(double) * 2 * (size_t)TW * G.nz;
-    const int ntx = (G.nx + TW - 1) / TW;
-    k_divergence<<<ntx * G.ny * G.members, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP], fl[F_PL], fl[F_PP],
-                                                   fl[F_EL], fl[F_EP], c.rho_inv, du ? du : c.dudt_buf,
-                                                   dv ? dv : c.dvdt_buf);
-    k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, c.max_blocks, mask, 1);
+    grid_phase(c, du, dv, mask);
     prof_mark(c, 5);
-    swap_soa(c);
+    swap_rays(c);
 }
 
 }  // namespace gwam

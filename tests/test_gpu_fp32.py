@@ -1,0 +1,139 @@
+"""Precision form (FP32 kinematics, cell index + FP32 offset positions, FP64 accumulation) against
+the FP64 CPU oracle.  The errors are stated, not hidden: every output's error is printed, and the
+test holds them to the bounds the form is built for:
+  * ray state (rays present on both sides): normwise relative error <= 2e-5 per component;
+  * projected centre fields: |gpu - oracle| <= 1e-4 * S elementwise, S the oracle's sum of
+    contribution magnitudes (as in the FP64 parity tests);
+  * vertical fluxes and drag: |gpu - oracle| <= 1e-4 * S_col, S_col the largest S of the column.
+    A ray's share of a staggered cell is its vertical overlap with it; a position error of d moves
+    flux d/dz between neighbouring interfaces of the column, so a ray that just grazes an interface
+    (overlap of centimetres out of a kilometre) carries a large relative error there while the
+    column's flux is accurate -- the column scale measures that;
+  * integer bookkeeping: counts within 0.5 % (FP32 can move a ray across a threshold);
+  * budget terms: relative 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2309_11257_gb300 import synth
+from parity_util import scaled_error, state_errors
+
+pytestmark = pytest.mark.gpu
+
+STATE_TOL = 2e-5
+FIELD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def gw():
+    from paper_2309_11257_gb300 import build
+    build.build()
+    from paper_2309_11257_gb300 import gwam
+    return gwam
+
+
+def _run(gw, grid, params, bg, src, rays, steps, dt, specs=None):
+    import torch
+    T = gw.Tracer(grid, dict(params, precision=1), max_rays=3_000_000)
+    T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in bg])
+    O = oracle.Model(grid, params)
+    O.set_background(*bg)
+    if src:
+        T.launch_sources(src)
+        O.launch_background(src)
+    if specs is not None:
+        T.launch_spectral(specs)
+        O.launch_spectral(specs)
+    if rays:
+        T.add_rays(rays)
+        O.add_rays(rays)
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    du = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    for _ in range(steps):
+        T.step(dt, du, dv)
+        odu, odv = O.step(dt)
+    return T, O, du.cpu().numpy(), dv.cpu().numpy(), odu, odv
+
+
+def _report_and_check(T, O, grid, du, dv, odu, odv, label):
+    g, o = T.rays(), O.rays()
+    common, ig, io = np.intersect1d(g["id"], o["id"], return_indices=True)
+    assert len(common) >= 0.995 * len(o["id"])
+    errs = state_errors({n: g[n][ig] for n in oracle.STATE_NAMES}, {n: o[n][io] for n in oracle.STATE_NAMES}, grid)
+    su, sv = O.tendency_scale()
+    col = lambda S: np.broadcast_to(S.max(axis=0, keepdims=True), S.shape)
+    e_du, e_dv = scaled_error(du, odu, col(su)), scaled_error(dv, odv, col(sv))
+    l2 = np.linalg.norm(du - odu) / max(np.linalg.norm(odu), 1e-300)
+    field_errs = {}
+    for n in oracle.FIELD_NAMES:
+        S = O.field_abs(n)
+        field_errs[n] = scaled_error(T.field(n), O.field(n), col(S) if n.startswith("fz") else S)
+    gs, os_ = T.stats(), O.stats()
+    print("\n[%s] precision form vs FP64 oracle" % label)
+    print("  ray state normwise:", {k: "%.1e" % v for k, v in errs.items()})
+    print("  du/dt column-scaled %.2e (rel L2 %.2e), dv/dt column-scaled %.2e" % (e_du, l2, e_dv))
+    print("  fields scaled:", {k: "%.1e" % v for k, v in field_errs.items()})
+    print("  counts gpu/oracle:", {k: (gs[k], os_[k]) for k in ("n_live", "n_split_v", "n_split_h", "n_exited",
+                                                                "n_capped")})
+    assert max(errs.values()) <= STATE_TOL, errs
+    assert e_du <= FIELD_TOL and e_dv <= FIELD_TOL
+    assert max(field_errs.values()) <= FIELD_TOL, field_errs
+    for k in ("n_live", "n_launched", "n_filtered", "n_split_v", "n_split_h", "n_exited", "n_capped"):
+        assert abs(gs[k] - os_[k]) <= 0.005 * max(os_[k], 200), (k, gs[k], os_[k])
+    for k in ("w_total", "w_launched"):
+        assert abs(gs[k] - os_[k]) <= 1e-5 * abs(os_[k]), k
+
+
+def test_precision_form_small_sphere(gw):
+    grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+    bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+    rays = synth.sphere_rays(grid, 500, tag=71, z_lo=4e3, z_hi=20e3, ext_scale=2.5)
+    rays["n"] = rays["n"] * 30.0
+    out = _run(gw, grid, dict(synth.DEFAULT_PARAMS, cap_per_column=45), bg, synth.background_source(z_launch=2e3),
+               rays, 10, 300.0)
+    _report_and_check(*out[:2], grid, *out[2:], "sphere 40x20x24, 10 steps")
+
+
+def test_precision_form_fplane(gw):
+    grid = synth.fplane_grid(nx=24, ny=20, nz=40, dx=40e3, dy=30e3, dz=500.0)
+    bg = synth.perturbed(synth.uniform_background(grid, U=5.0), tag=21, rel=0.1)
+    rays = synth.fplane_rays(grid, 1500, tag=22, z_lo=3e3, z_hi=15e3, ext_z=1300.0)
+    rays["n"] = rays["n"] * 1e8
+    out = _run(gw, grid, dict(synth.DEFAULT_PARAMS, cap_per_column=12), bg, None, rays, 12, 240.0)
+    _report_and_check(*out[:2], grid, *out[2:], "f-plane 24x20x40, 12 steps")
+
+
+def test_precision_form_full_size_sphere(gw):
+    """The precision-form benchmark physics at the FP64 workload's size: launch and 2 steps."""
+    w = synth.workload("sphere")
+    out = _run(gw, w["grid"], w["params"], w["background"], w["source"], None, 2, w["dt"])
+    _report_and_check(*out[:2], w["grid"], *out[2:], "sphere 256x128x90, 2 steps")
+
+
+def test_precision_form_ensemble_and_graph(gw):
+    """Two members in the precision form: graph replay is bit-identical to eager steps, the budget
+    closes, the members stay independent."""
+    import torch
+    grid = synth.sphere_grid(nx=32, ny=16, nz=20, dz=1000.0)
+    outs = []
+    for graph in (False, True):
+        T = gw.Tracer(grid, dict(synth.DEFAULT_PARAMS, precision=1), max_rays=400000, members=2)
+        for m in range(2):
+            bg = synth.perturbed(synth.jet_background(grid, amp=30 + 30 * m, z_peak=12e3, z_width=5e3), tag=80 + m)
+            T.set_member_background(m, *[torch.from_numpy(a.copy()).cuda() for a in bg])
+        T.launch_sources(synth.background_source(z_launch=2e3))
+        du = torch.zeros((2, 20, 16, 32), dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(du)
+        for _ in range(6):
+            (T.step_graph if graph else T.step)(300.0, du, dv)
+        st = T.stats()
+        rhs = st["w_launched"] - st["w_saturated"] - st["w_exited"] - st["w_capped"] - st["w_invalid"]
+        assert abs(st["w_total"] - rhs) <= 1e-12 * st["w_total"]
+        r = T.rays()
+        assert set(np.unique(r["member"]).tolist()) == {0, 1}
+        assert np.isfinite(du.cpu().numpy()).all()
+        outs.append(r)
+    for n in ("id", "member", "cell") + tuple(oracle.STATE_NAMES):
+        np.testing.assert_array_equal(outs[0][n], outs[1][n])
