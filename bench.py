@@ -332,6 +332,133 @@ def ensemble_arm(args):
     return 0
 
 
+# Surrogate: algorithmic FLOPs of one column through the MLP 368 -> 4 x 512 (GELU) -> 180
+SUR_DIMS = (368, 512, 512, 512, 512, 180)
+SUR_FLOPS_PER_COLUMN = 2.0 * sum(a * b for a, b in zip(SUR_DIMS[:-1], SUR_DIMS[1:]))
+SUR_BATCH = 32768
+
+
+def surrogate_arm(args):
+    """Surrogate inference: one step = one pass over a batch of 32 768 columns (normalisation and
+    envelope test, 5 tensor-core GEMMs with fused bias/GELU, de-normalised drag scattered into the
+    [nz][ny][nx] outputs).  The drag error is stated from a surrogate trained first on ray-tracer
+    drag (8 members of a 64 x 32 x 90 sphere), measured on 2 held-out members."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2309_11257_gb300 import gwam, surrogate
+
+    t_start = time.perf_counter()
+    X, Y, info = surrogate.generate(members=8, nx=64, ny=32, nz=90, steps=60, avg=20, tag=1)
+    ncol = info["ncol"]
+    ntr = 6 * ncol
+    S = gwam.Surrogate(max_batch=SUR_BATCH, seed=1)
+    S.fit_normalization(X[:ntr], Y[:ntr], margin=0.05)
+    tsteps, tbatch = args.train_steps, 2048
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = surrogate.train(S, X[:ntr], Y[:ntr], steps=tsteps, batch=tbatch, lr=1e-3)
+    e1.record()
+    e1.synchronize()
+    train_cps = tsteps * tbatch / (e0.elapsed_time(e1) / 1000.0)
+    te = surrogate.drag_error(S, X[ntr:], Y[ntr:], 90)
+    ref = Y[ntr:].double()
+    base = float(torch.linalg.norm(ref - Y[:ntr].double().mean(dim=0)) / torch.linalg.norm(ref))
+    prep_s = time.perf_counter() - t_start
+
+    B = SUR_BATCH
+    idx = torch.arange(B, device="cuda") % X.shape[0]
+    Xb = X[idx].contiguous()
+    du = torch.zeros((90, B), dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    mask = torch.zeros(B, dtype=torch.int32, device="cuda")
+    nfb = torch.zeros(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        S.infer(Xb, du, dv, mask, nfb)
+    S.status()
+    S.profile(True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)                  # evict the batch from L2 between timed passes
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        S.infer(Xb, du, dv, mask, nfb)
+        b.record()
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    clocks = sampler.stop()
+    prof, passes = S.profile_read()
+    S.profile(False)
+    S.status()
+    value = B * args.steps / (tot / 1000.0)
+    gemm_ms = prof["gemm_ms"] / max(passes, 1)
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = SUR_FLOPS_PER_COLUMN * B / (gemm_ms / 1000.0) / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_gemm_bf16 (tcgen05, 5 launches per pass)", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured burst bf16 (MEASURED_PEAKS.json bf16_tflops)",
+                "gemm_ms_per_pass": gemm_ms, "pack_ms_per_pass": prof["pack_ms"] / max(passes, 1),
+                "flops_per_column": SUR_FLOPS_PER_COLUMN}
+
+    # end to end: features from pinned host memory, drag back to pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        Xh = Xb.cpu().pin_memory()
+        duh = torch.zeros((90, B), dtype=torch.float64).pin_memory()
+        dvh = torch.zeros_like(duh).pin_memory()
+        Xd = torch.empty_like(Xb)
+        ke = max(1, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            Xd.copy_(Xh, non_blocking=True)
+            S.infer(Xd, du, dv, mask, nfb)
+            duh.copy_(du, non_blocking=True)
+            dvh.copy_(dv, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e = {"value": B * ke / (t1 - t0), "unit": "columns/s", "h2d_bytes_per_step": B * 368 * 4,
+               "d2h_bytes_per_step": 2 * 90 * B * 8, "steps": ke}
+
+    cpu = None
+    if not args.no_cpu:
+        from oracle import mlp
+        p64 = [(W.astype(np.float64), b.astype(np.float64)) for W, b in S.params()]
+        xs = np.random.default_rng(0).standard_normal((4096, 368))
+        mlp.forward(p64, xs[:256])
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < 10.0:
+            mlp.forward(p64, xs)
+            reps += 1
+        dtc = time.perf_counter() - t0
+        cpu = {"value": 4096 * reps / dtc, "unit": "columns/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d FP64 forward passes of 4096 columns (%.1f s), numpy BLAS on all host cores" % (reps, dtc)}
+    line = {"metric": "surrogate columns/s", "value": value, "unit": "columns/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "surrogate MLP 368-4x512-180 GELU, batch %d columns" % B,
+                       "drag_rel_l2_heldout": te["rel_l2"], "drag_rel_l2_mean_baseline": base,
+                       "fallback_heldout": te["n_fallback"], "heldout_columns": int(Y.shape[0] - ntr),
+                       "train_columns": ntr, "train_steps": tsteps, "train_batch": tbatch,
+                       "train_columns_per_s": train_cps, "loss_history": hist,
+                       "tracer_columns_per_s": X.shape[0] / (info["tracer_ms_per_step"] / 1000.0),
+                       "prep_seconds": prep_s, "fallback_in_batch": int(nfb.item()),
+                       "l2": "256 MB buffer written between timed passes"},
+            "gpu_launches": args.steps * 6, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def launches_per_step(params) -> int:
     """Kernels of the library per gwam_step (memsets excluded)."""
     # begin, advance, 2 scans (3 kernels each), scatter, segsort x2, set_nnew, materialize, project,
@@ -354,9 +481,12 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "sphere_half", "ensemble", "sphere_fp32"],
+    ap.add_argument("--train-steps", type=int, default=1500, help="surrogate workload: training steps")
+    ap.add_argument("--workload", default="sphere",
+                    choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "surrogate"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
-                         "ensemble: 16 members of the sphere with convective sources, graph-replayed steps")
+                         "ensemble: 16 members of the sphere with convective sources, graph-replayed steps; "
+                         "surrogate: MLP inference over 32768 columns after training on tracer drag")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -365,6 +495,8 @@ def main():
         return reference_arm(args, rank, world)
     if args.workload == "ensemble":
         return ensemble_arm(args)
+    if args.workload == "surrogate":
+        return surrogate_arm(args)
     if world > 1:
         import torch
         import torch.distributed as dist

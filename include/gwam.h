@@ -233,6 +233,95 @@ int gwam_cell_offsets_noalloc(const int32_t *cells, int64_t n, int32_t ncell, in
  * rsqrt_out[i] ~ 1/sqrt(x[i]) for positive normal x.  Device pointers, n values; synchronises. */
 int gwam_selftest_math(const double *x, int64_t n, double *rcp_out, double *rsqrt_out, void *stream);
 
+/* Self-test of the surrogate's tensor-core GEMM (tcgen05 + TMA, sm_103a): C = act(A . B^T + bias)
+ * with A [M][K] and B [N][K] row-major BF16 device arrays (K contiguous, K a multiple of 64, base
+ * addresses 16-byte aligned), bias [N] FP32 or NULL, act = GELU(z) = z Phi(z) when gelu != 0, C
+ * [M][N] FP32, overwritten.  Products are exact, sums are FP32.  bn selects the tile width (0 = by
+ * N; else 64, 128, 192 or 256).  Synchronises `stream`.  Errors: GWAM_EINVAL (shape, alignment,
+ * tile), GWAM_ENOMEM, GWAM_ECUDA, GWAM_ETIMEOUT (a bounded device wait gave up). */
+int gwam_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int gelu, int bn,
+                   float *C, void *stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Column drag surrogate (not in the paper: an emulator of the ray tracer's column drag, with the
+ * tracer as fallback).  An MLP n_in -> n_hidden (x n_layers, GELU(z) = z Phi(z)) -> n_out with
+ * BF16 weights and activations on the tensor cores, FP32 accumulation, FP32 master weights and
+ * Adam moments (Kingma & Ba 2015).  Inputs are FP32 column features [n][n_in] (row-major, device),
+ * normalised per feature, x_hat = (x - mu) * (1 / sigma); targets FP32 [n][n_out] normalised the
+ * same way; the loss is the mean over rows and outputs of (y - t)^2 in normalised units.  A column
+ * is inside the envelope when lo[f] <= x_hat[f] <= hi[f] for every feature f (all finite); columns
+ * outside it are flagged for the ray tracer.  All work is enqueued on the stream given at creation.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct gwam_mlp gwam_mlp;
+typedef struct {
+    int n_in;        /* features per column (368 = u, v, N^2, ln rho on 90 levels + 8 source parameters) */
+    int n_hidden;    /* width of every hidden layer, a multiple of 64 (512) */
+    int n_layers;    /* hidden layers, 1..7 (4) */
+    int n_out;       /* outputs per column (180 = du/dt then dv/dt on nlev levels) */
+    int nlev;        /* levels of the drag output for gwam_mlp_infer (2 nlev = n_out), or 0 */
+    int max_batch;   /* rows per training step and per inference pass, a multiple of 128 */
+    uint64_t seed;   /* initial weights W ~ N(0, 1/n_in) from SplitMix64 + Box-Muller, b = 0 */
+    float beta1, beta2, eps;   /* Adam constants (0.9, 0.999, 1e-8) */
+} gwam_mlp_config;
+
+/* Create / destroy.  Allocates every buffer (weights, Adam state, activations of max_batch rows,
+ * split-K scratch) and the TMA tensor maps once.  GWAM_EINVAL, GWAM_ENOMEM, GWAM_ECUDA. */
+int gwam_mlp_create(gwam_mlp **out, const gwam_mlp_config *cfg, void *stream);
+void gwam_mlp_destroy(gwam_mlp *m);
+const char *gwam_mlp_last_error(const gwam_mlp *m);
+/* Normalisation and envelope from host arrays: x_mu, x_sigma, lo, hi [n_in]; y_mu, y_sigma [n_out];
+ * sigma > 0 and finite, else GWAM_EINVAL.  Synchronises. */
+int gwam_mlp_set_normalization_host(gwam_mlp *m, const float *x_mu, const float *x_sigma, const float *y_mu,
+                                    const float *y_sigma, const float *lo, const float *hi);
+/* Normalisation fitted to a device data set X [n][n_in], Y [n][n_out] (FP64 sums): mu, population
+ * sigma (1 for a constant feature); envelope = [min, max] of x_hat widened by margin * (max - min).
+ * stats_host (or NULL) receives 4 n_in + 2 n_out floats: x mu, x sigma, lo, hi, y mu, y sigma. */
+int gwam_mlp_fit_normalization(gwam_mlp *m, const float *X, const float *Y, int64_t n, float margin,
+                               float *stats_host);
+/* Parameters of weight layer 1..n_layers+1 from / to host: W [n_out_l][n_in_l] row-major, b [n_out_l].
+ * get: which = 0 the FP32 master weights, 1 the gradients of the last train step (either pointer
+ * may be NULL).  Synchronise. */
+int gwam_mlp_set_params_host(gwam_mlp *m, int layer, const float *W, const float *b);
+int gwam_mlp_get_params_host(gwam_mlp *m, int layer, int which, float *W, float *b);
+/* One training step on `batch` rows (a multiple of 64, <= max_batch) of the device data set X, Y
+ * of n rows: rows[] (device int32, batch entries in [0, n)) or, when rows is NULL, rows drawn by
+ * SplitMix64(seed + (r + 1) * 0x9E3779B97F4A7C15) mod n.  Forward, loss, backward and, when lr > 0,
+ * one Adam update with that learning rate (lr = 0: gradients only).  Asynchronous. */
+int gwam_mlp_train_step(gwam_mlp *m, const float *X, const float *Y, int64_t n, const int32_t *rows, int batch,
+                        uint64_t seed, float lr);
+/* Loss of the last train step (synchronises; returns a pending device error: GWAM_ETIMEOUT when a
+ * bounded wait in the GEMM gave up, GWAM_EINVAL for a row index outside the data set). */
+int gwam_mlp_last_loss_host(gwam_mlp *m, double *loss);
+/* Network outputs (normalised units) of the first `rows` rows of the last train step, [rows][n_out]. */
+int gwam_mlp_output_host(gwam_mlp *m, float *Y, int rows);
+/* Inference on ncol columns of features X [ncol][n_in]: for every column inside the envelope the
+ * de-normalised drag y * sigma + mu is written to dudt[k * ncol + c] and dvdt[k * ncol + c]
+ * (k < nlev, the [nz][ny][nx] layout with ncol = ny nx, FP64); fallback_mask[c] = 1 for columns
+ * outside the envelope (their drag entries are not written), else 0; *n_fallback (device int32) =
+ * their number.  Needs nlev >= 1 and n_out = 2 nlev.  Asynchronous. */
+int gwam_mlp_infer(gwam_mlp *m, const float *X, int64_t ncol, double *dudt, double *dvdt, int32_t *fallback_mask,
+                   int32_t *n_fallback);
+/* Inference timing with CUDA events on the surrogate's stream (for measurement tools; off by
+ * default): enable != 0 resets and starts it.  gwam_mlp_profile_read synchronises and returns the
+ * accumulated milliseconds of the input packing (ms_host[0]) and of the GEMM chain (ms_host[1]) and
+ * the number of timed passes (one per max_batch chunk). */
+int gwam_mlp_profile_enable(gwam_mlp *m, int enable);
+int gwam_mlp_profile_read(gwam_mlp *m, double *ms_host, int64_t *passes);
+/* Pending device status of the surrogate (synchronises). */
+int gwam_mlp_status(gwam_mlp *m);
+/* Fallback routing: copy the ray tracer's drag into the columns with mask[c] != 0 (device arrays,
+ * [nlev][ncol] FP64). */
+int gwam_mlp_merge_fallback(const int32_t *mask, int64_t ncol, int nlev, const double *dudt_tracer,
+                            const double *dvdt_tracer, double *dudt, double *dvdt, void *stream);
+/* Surrogate data: column features X [ncol][4 nz + n_src] (FP32) from [nz][ncol] FP64 device fields
+ * u, v, N^2, rho (features u, v, N^2, ln rho level by level, then the n_src source parameters from
+ * src[c * src_stride + j]; src_stride = 0 shares one set), and targets Y [ncol][2 nz] = scale *
+ * (du_sum, dv_sum). */
+int gwam_column_features(const double *u, const double *v, const double *n2, const double *rho, int nz,
+                         int64_t ncol, const float *src, int n_src, int src_stride, float *X, void *stream);
+int gwam_column_targets(const double *du_sum, const double *dv_sum, int nz, int64_t ncol, double scale, float *Y,
+                        void *stream);
+
 /* Per-phase device timing with CUDA events recorded on the context's stream around each phase
  * of gwam_step (for measurement tools; off by default).  enable != 0 resets and starts the
  * accumulation, 0 stops it.  Phases: 0 advance (RK3, exits, split decisions), 1 re-binning

@@ -77,6 +77,12 @@ class Stats(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class MlpConfig(C.Structure):
+    _fields_ = [("n_in", C.c_int), ("n_hidden", C.c_int), ("n_layers", C.c_int), ("n_out", C.c_int),
+                ("nlev", C.c_int), ("max_batch", C.c_int), ("seed", C.c_uint64), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 _vp = C.c_void_p
 _P = C.POINTER
 # name -> (restype, argtypes); every entry point declared in include/gwam.h
@@ -107,6 +113,24 @@ SIGNATURES = {
     "gwam_cell_offsets": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp, _vp]),
     "gwam_cell_offsets_noalloc": (C.c_int, [_vp, C.c_int64, C.c_int32, _vp, _vp]),
     "gwam_selftest_math": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
+    "gwam_gemm_bf16": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, _vp, _vp]),
+    "gwam_mlp_create": (C.c_int, [_P(_vp), _P(MlpConfig), _vp]),
+    "gwam_mlp_destroy": (None, [_vp]),
+    "gwam_mlp_last_error": (C.c_char_p, [_vp]),
+    "gwam_mlp_set_normalization_host": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "gwam_mlp_fit_normalization": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, _vp]),
+    "gwam_mlp_set_params_host": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "gwam_mlp_get_params_host": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
+    "gwam_mlp_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, C.c_int, C.c_uint64, C.c_float]),
+    "gwam_mlp_last_loss_host": (C.c_int, [_vp, _P(C.c_double)]),
+    "gwam_mlp_output_host": (C.c_int, [_vp, _vp, C.c_int]),
+    "gwam_mlp_infer": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
+    "gwam_mlp_status": (C.c_int, [_vp]),
+    "gwam_mlp_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "gwam_mlp_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
+    "gwam_mlp_merge_fallback": (C.c_int, [_vp, C.c_int64, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "gwam_column_features": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_int64, _vp, C.c_int, C.c_int, _vp, _vp]),
+    "gwam_column_targets": (C.c_int, [_vp, _vp, C.c_int, C.c_int64, C.c_double, _vp, _vp]),
     "gwam_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
     "gwam_last_error": (C.c_char_p, [_vp]),
@@ -315,3 +339,138 @@ class Tracer:
 
     def synchronize(self):
         self._check(_lib.gwam_synchronize(self._h), "synchronize")
+
+
+# ------------------------------------------------------------------ drag surrogate
+def _stream_ptr():
+    import torch
+    return _vp(torch.cuda.current_stream().cuda_stream)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Surrogate:
+    """The column drag surrogate (gwam_mlp_* in include/gwam.h).  Data sets and outputs are torch
+    CUDA tensors; the stream is torch's current stream at construction."""
+
+    def __init__(self, n_in=368, n_out=180, n_hidden=512, n_layers=4, nlev=90, max_batch=32768, seed=1,
+                 beta1=0.9, beta2=0.999, eps=1e-8):
+        self._h = _vp()
+        cfg = MlpConfig(n_in=n_in, n_hidden=n_hidden, n_layers=n_layers, n_out=n_out, nlev=nlev,
+                        max_batch=max_batch, seed=seed, beta1=beta1, beta2=beta2, eps=eps)
+        self._stream = _stream_ptr()
+        rc = _lib.gwam_mlp_create(C.byref(self._h), C.byref(cfg), self._stream)
+        if rc != GWAM_OK:
+            raise GwamError(rc, "gwam_mlp_create")
+        self.n_in, self.n_out, self.n_hidden, self.n_layers, self.nlev = n_in, n_out, n_hidden, n_layers, nlev
+        self.max_batch = max_batch
+        self.dims = (n_in,) + (n_hidden,) * n_layers + (n_out,)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and self._h.value:
+            _lib.gwam_mlp_destroy(self._h)
+            self._h = _vp()
+
+    def _check(self, rc, what):
+        if rc != GWAM_OK:
+            raise GwamError(rc, "%s: %s" % (what, _lib.gwam_mlp_last_error(self._h).decode()))
+
+    def set_normalization(self, x_mu, x_sigma, y_mu, y_sigma, lo, hi):
+        arrs = [_f32(a) for a in (x_mu, x_sigma, y_mu, y_sigma, lo, hi)]
+        self._check(_lib.gwam_mlp_set_normalization_host(self._h, *[a.ctypes.data_as(_vp) for a in arrs]),
+                    "set_normalization")
+
+    def fit_normalization(self, X, Y, margin=0.05):
+        st = np.zeros(4 * self.n_in + 2 * self.n_out, dtype=np.float32)
+        self._check(_lib.gwam_mlp_fit_normalization(self._h, _ptr(X), _ptr(Y), X.shape[0], float(margin),
+                                                    st.ctypes.data_as(_vp)), "fit_normalization")
+        ni, no = self.n_in, self.n_out
+        return {"x_mu": st[:ni], "x_sigma": st[ni:2 * ni], "lo": st[2 * ni:3 * ni], "hi": st[3 * ni:4 * ni],
+                "y_mu": st[4 * ni:4 * ni + no], "y_sigma": st[4 * ni + no:]}
+
+    def set_params(self, params):
+        for l, (W, b) in enumerate(params, start=1):
+            W, b = _f32(W), _f32(b)
+            self._check(_lib.gwam_mlp_set_params_host(self._h, l, W.ctypes.data_as(_vp), b.ctypes.data_as(_vp)),
+                        "set_params")
+
+    def _get(self, which):
+        out = []
+        for l in range(1, len(self.dims)):
+            W = np.zeros((self.dims[l], self.dims[l - 1]), dtype=np.float32)
+            b = np.zeros(self.dims[l], dtype=np.float32)
+            self._check(_lib.gwam_mlp_get_params_host(self._h, l, which, W.ctypes.data_as(_vp),
+                                                      b.ctypes.data_as(_vp)), "get_params")
+            out.append((W, b))
+        return out
+
+    def params(self):
+        return self._get(0)
+
+    def grads(self):
+        return self._get(1)
+
+    def train_step(self, X, Y, batch, seed=0, lr=1e-3, rows=None):
+        self._check(_lib.gwam_mlp_train_step(self._h, _ptr(X), _ptr(Y), X.shape[0],
+                                             _ptr(rows) if rows is not None else None, int(batch), int(seed),
+                                             float(lr)), "train_step")
+
+    def loss(self) -> float:
+        v = C.c_double()
+        self._check(_lib.gwam_mlp_last_loss_host(self._h, C.byref(v)), "last_loss")
+        return v.value
+
+    def output(self, rows):
+        out = np.zeros((rows, self.n_out), dtype=np.float32)
+        self._check(_lib.gwam_mlp_output_host(self._h, out.ctypes.data_as(_vp), int(rows)), "output")
+        return out
+
+    def infer(self, X, dudt, dvdt, mask, n_fallback):
+        """Drag of the in-envelope columns into dudt/dvdt ([nlev][ncol] float64 tensors); mask and
+        n_fallback (int32 tensors) receive the fallback flags and their count.  Asynchronous."""
+        self._check(_lib.gwam_mlp_infer(self._h, _ptr(X), X.shape[0], _ptr(dudt), _ptr(dvdt), _ptr(mask),
+                                        _ptr(n_fallback)), "infer")
+
+    def status(self):
+        self._check(_lib.gwam_mlp_status(self._h), "status")
+
+    def profile(self, enable=True):
+        self._check(_lib.gwam_mlp_profile_enable(self._h, 1 if enable else 0), "profile_enable")
+
+    def profile_read(self):
+        ms = np.zeros(2)
+        n = C.c_int64()
+        self._check(_lib.gwam_mlp_profile_read(self._h, ms.ctypes.data_as(_vp), C.byref(n)), "profile_read")
+        return {"pack_ms": ms[0], "gemm_ms": ms[1]}, n.value
+
+
+def merge_fallback(mask, du_tracer, dv_tracer, dudt, dvdt):
+    ncol = mask.shape[0]
+    nlev = dudt.numel() // ncol
+    rc = _lib.gwam_mlp_merge_fallback(_ptr(mask), ncol, nlev, _ptr(du_tracer), _ptr(dv_tracer), _ptr(dudt),
+                                      _ptr(dvdt), _stream_ptr())
+    if rc != GWAM_OK:
+        raise GwamError(rc, "merge_fallback")
+
+
+def column_features(u, v, n2, rho, src, out):
+    """Features [ncol][4 nz + n_src] of [nz][ny][nx] float64 tensors; src: float32 tensor [n_src]
+    (shared) or [ncol][n_src]."""
+    nz = u.shape[0]
+    ncol = u.numel() // nz
+    n_src = src.shape[-1]
+    stride = 0 if src.dim() == 1 else n_src
+    rc = _lib.gwam_column_features(_ptr(u), _ptr(v), _ptr(n2), _ptr(rho), nz, ncol, _ptr(src), n_src, stride,
+                                   _ptr(out), _stream_ptr())
+    if rc != GWAM_OK:
+        raise GwamError(rc, "column_features")
+
+
+def column_targets(du_sum, dv_sum, scale, out):
+    nz = du_sum.shape[0]
+    ncol = du_sum.numel() // nz
+    rc = _lib.gwam_column_targets(_ptr(du_sum), _ptr(dv_sum), nz, ncol, float(scale), _ptr(out), _stream_ptr())
+    if rc != GWAM_OK:
+        raise GwamError(rc, "column_targets")

@@ -65,7 +65,8 @@ def test_init_rejects_bad_arguments_before_touching_the_device(gw):
 def test_struct_layouts_match_the_header(gw, tmp_path):
     """sizeof/offsetof of every POD struct as gcc lays out include/gwam.h, against the binding."""
     structs = {"gwam_grid": gw.Grid, "gwam_params": gw.Params, "gwam_bg_source": gw.BgSource,
-               "gwam_spec": gw.Spec, "gwam_stats": gw.Stats, "gwam_ray_input": gw.RayInput}
+               "gwam_spec": gw.Spec, "gwam_stats": gw.Stats, "gwam_ray_input": gw.RayInput,
+               "gwam_mlp_config": gw.MlpConfig}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gwam.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
@@ -83,3 +84,20 @@ def test_struct_layouts_match_the_header(gw, tmp_path):
         assert int(out[cname]) == C.sizeof(py), cname
         for fname, _ in py._fields_:
             assert int(out["%s.%s" % (cname, fname)]) == getattr(py, fname).offset, (cname, fname)
+
+
+def test_surrogate_rejects_bad_configs_before_touching_the_device(gw):
+    lib = gw.lib()
+    h = C.c_void_p()
+    good = dict(n_in=368, n_hidden=512, n_layers=4, n_out=180, nlev=90, max_batch=1024, seed=1, beta1=0.9,
+                beta2=0.999, eps=1e-8)
+    for bad in (dict(n_hidden=500), dict(max_batch=1000), dict(n_layers=0), dict(nlev=91), dict(beta1=1.0),
+                dict(eps=0.0), dict(n_in=0)):
+        cfg = gw.MlpConfig(**dict(good, **bad))
+        assert lib.gwam_mlp_create(C.byref(h), C.byref(cfg), None) == gw.GWAM_EINVAL, bad
+        assert not h.value
+    assert lib.gwam_mlp_create(None, None, None) == gw.GWAM_EINVAL
+    assert lib.gwam_mlp_train_step(None, None, None, 0, None, 64, 0, 0.0) == gw.GWAM_EINVAL
+    assert lib.gwam_mlp_infer(None, None, 0, None, None, None, None) == gw.GWAM_EINVAL
+    assert lib.gwam_mlp_merge_fallback(None, 0, 0, None, None, None, None, None) == gw.GWAM_EINVAL
+    assert lib.gwam_gemm_bf16(None, None, 128, 64, 64, None, 0, 0, None, None) == gw.GWAM_EINVAL

@@ -1,0 +1,68 @@
+"""The surrogate's tcgen05/TMA BF16 GEMM against FP64 products of the same BF16 values.
+
+Products of BF16 numbers are exact in FP32; only the FP32 sums round, so every element must lie
+within 2e-5 * S of the FP64 result, S = sum_k |a_ik b_jk| (K <= 512: the worst case K 2^-24 is
+3e-5, the typical sqrt(K) 2^-24 is 1.3e-6).  A layout or descriptor mistake gives O(S) errors."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gw():
+    from paper_2309_11257_gb300 import build
+    build.build()
+    from paper_2309_11257_gb300 import gwam
+    return gwam
+
+
+def _gelu(z):
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+@pytest.mark.parametrize("M,N,K,bn,bias,gelu", [
+    (128, 64, 64, 64, False, False),
+    (300, 180, 384, 0, True, True),
+    (256, 512, 512, 0, True, False),
+    (1000, 256, 128, 256, True, True),
+    (129, 40, 192, 64, False, True),
+    (513, 192, 512, 192, True, False),
+    (2048, 512, 512, 128, False, False),
+])
+def test_gemm_matches_fp64(gw, M, N, K, bn, bias, gelu):
+    import torch
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = (torch.randn(N, K, generator=g) / 8).to(torch.bfloat16)
+    b = torch.randn(N, generator=g).float() if bias else None
+    Ad, Bd = A.cuda(), B.cuda()
+    bd = b.cuda() if bias else None
+    Cd = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    rc = gw.lib().gwam_gemm_bf16(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()), M, N, K,
+                                 C.c_void_p(bd.data_ptr() if bias else 0), int(gelu), bn,
+                                 C.c_void_p(Cd.data_ptr()), C.c_void_p(s.cuda_stream))
+    assert rc == 0
+    a, bb = A.double().numpy(), B.double().numpy()
+    z = a @ bb.T + (b.double().numpy() if bias else 0.0)
+    S = np.abs(a) @ np.abs(bb).T
+    ref = _gelu(z) if gelu else z
+    got = Cd.cpu().double().numpy()
+    err = np.abs(got - ref)
+    assert np.isfinite(got).all()
+    assert (err <= 2e-5 * S + 1e-6 * np.abs(ref)).all(), (err / (S + 1e-30)).max()
+
+
+def test_gemm_rejects_bad_shapes(gw):
+    import torch
+    A = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
+    Cd = torch.zeros(128, 64, device="cuda")
+    lib = gw.lib()
+    p = C.c_void_p(A.data_ptr())
+    assert lib.gwam_gemm_bf16(p, p, 128, 64, 60, None, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
+    assert lib.gwam_gemm_bf16(p, p, 128, 64, 64, None, 0, 96, C.c_void_p(Cd.data_ptr()), None) == -1
+    assert lib.gwam_gemm_bf16(p, p, 0, 64, 64, None, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
