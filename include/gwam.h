@@ -273,8 +273,10 @@ const char *gwam_mlp_last_error(const gwam_mlp *m);
  * sigma > 0 and finite, else GWAM_EINVAL.  Synchronises. */
 int gwam_mlp_set_normalization_host(gwam_mlp *m, const float *x_mu, const float *x_sigma, const float *y_mu,
                                     const float *y_sigma, const float *lo, const float *hi);
-/* Normalisation fitted to a device data set X [n][n_in], Y [n][n_out] (FP64 sums): mu, population
- * sigma (1 for a constant feature); envelope = [min, max] of x_hat widened by margin * (max - min).
+/* Normalisation fitted to a device data set X [n][n_in], Y [n][n_out] (FP64 sums): features get
+ * their mean and population sigma (1 for a constant feature); targets get their mean and one shared
+ * sigma, the RMS over outputs of their standard deviations (the loss is then proportional to the
+ * drag's own squared error); envelope = [min, max] of x_hat widened by margin * (max - min).
  * stats_host (or NULL) receives 4 n_in + 2 n_out floats: x mu, x sigma, lo, hi, y mu, y sigma. */
 int gwam_mlp_fit_normalization(gwam_mlp *m, const float *X, const float *Y, int64_t n, float margin,
                                float *stats_host);

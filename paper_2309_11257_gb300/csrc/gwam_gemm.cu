@@ -2,6 +2,8 @@
 // self-test entry point.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "gwam_gemm.cuh"
 
 namespace gwam {
@@ -10,7 +12,6 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;
-constexpr int kThreads = 128;
 constexpr uint32_t kABytes = kBM * kBK * 2;          // 16 KB per stage
 constexpr unsigned long long kWaitNs = 2000000000ull; // 2 s per wait
 
@@ -63,263 +64,416 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z)
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26 (absolute error
+// <= 1.5e-7): erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x),
+// x >= 0, odd in x.  Returns erf(x) and exp(-x^2) (fast reciprocal and exponential intrinsics).
+__device__ __forceinline__ float erf_as(float x, float& ex2)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float poly = fmaf(t, 1.061405429f, -1.453152027f);
+    poly = fmaf(t, poly, 1.421413741f);
+    poly = fmaf(t, poly, -0.284496736f);
+    poly = fmaf(t, poly, 0.254829592f);
+    ex2 = __expf(-ax * ax);
+    const float r = fmaf(-t * poly, ex2, 1.0f);
+    return copysignf(r, x);
 }
 
-// epilogue of 16 consecutive accumulator columns n = nb .. nb+15 of one row
-__device__ __forceinline__ void epi16(const GemmEpi& e, int row, int nb, const uint32_t (&r)[16], double& sq)
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2
+__device__ __forceinline__ float gelu(float z)
 {
-    float v[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-    const bool full = nb + 16 <= e.N;
+    float ex2;
+    const float er = erf_as(z * 0.70710678118654752f, ex2);
+    return 0.5f * z * (1.0f + er);
+}
+
+// GELU'(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi)
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    float ex2;
+    const float er = erf_as(z * 0.70710678118654752f, ex2);
+    return fmaf(z * 0.39894228040143268f, ex2, 0.5f * (1.0f + er));
+}
+
+// Epilogue of 32 consecutive accumulator columns n = nb .. nb+31 of one row.  Per-column
+// parameters arrive one per lane (lane j holds column nb + j) and are broadcast with shuffles, so
+// every lane of the warp must call this (rows >= M only skip the stores).  zz: the prefetched
+// pre-activations of EPI_BWD.
+__device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, float (&v)[32], const float* sbias,
+                                      float ps, float pm, const float (&zz)[32], int rowmask, double& sq)
+{
+    const bool live = row < e.M;
+    const bool full = nb + 32 <= e.N;
     if (e.mode == EPI_BWD) {
-        if (full && (e.ldz & 3) == 0) {
-            const float4* zp = reinterpret_cast<const float4*>(e.z + (size_t)row * e.ldz + nb);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 zz = zp[q];
-                v[4 * q] *= gelu_grad(zz.x);
-                v[4 * q + 1] *= gelu_grad(zz.y);
-                v[4 * q + 2] *= gelu_grad(zz.z);
-                v[4 * q + 3] *= gelu_grad(zz.w);
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (nb + j < e.N) v[j] *= gelu_grad(e.z[(size_t)row * e.ldz + nb + j]);
-        }
+        for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(zz[j]);
     } else {
         if (e.bias) {
+            // the tile's bias from shared memory (zero beyond N), broadcast to every lane
+            const float4* bp = reinterpret_cast<const float4*>(sbias + nb);
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (nb + j < e.N) v[j] += e.bias[nb + j];
+            for (int qq = 0; qq < 8; ++qq) {
+                const float4 b = bp[qq];
+                v[4 * qq] += b.x;
+                v[4 * qq + 1] += b.y;
+                v[4 * qq + 2] += b.z;
+                v[4 * qq + 3] += b.w;
+            }
         }
-        if (e.mode == EPI_STORE) {
-            if (e.z) {
+        if (e.mode == EPI_DRAG) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (nb + j < e.N) e.z[(size_t)row * e.ldz + nb + j] = v[j];
-            }
-            if (e.act) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = gelu(v[j]);
-            }
-        } else if (e.mode == EPI_LOSS) {
-            if (e.cf) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (nb + j < e.N) e.cf[(size_t)row * e.ldcf + nb + j] = v[j];
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 32; ++j) {
+                const float sj = __shfl_sync(0xffffffffu, ps, j), mj = __shfl_sync(0xffffffffu, pm, j);
                 const int n = nb + j;
-                const float d = n < e.n_true ? v[j] - e.tgt[(size_t)row * e.ldt + n] : 0.0f;
-                sq += (double)d * (double)d;
-                v[j] = e.gscale * d;
-            }
-        } else {  // EPI_DRAG
-            if (e.mask[row] == 0) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = nb + j;
-                    if (n < e.n_true) {
-                        const double y = (double)v[j] * (double)e.ysig[n] + (double)e.ymu[n];
-                        if (n < e.nlev) e.du[(size_t)n * e.ncol + row] = y;
-                        else e.dv[(size_t)(n - e.nlev) * e.ncol + row] = y;
-                    }
+                if (live && rowmask == 0 && n < e.n_true) {
+                    const double y = (double)v[j] * (double)sj + (double)mj;
+                    if (n < e.nlev) e.du[(size_t)n * e.ncol + row] = y;
+                    else e.dv[(size_t)(n - e.nlev) * e.ncol + row] = y;
                 }
             }
             return;
         }
+        if (!live) return;
+        if (e.mode == EPI_STORE) {
+            if (e.z) {
+                float* p = e.z + (size_t)row * e.ldz + nb;
+                if (full && (e.ldz & 3) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (nb + j < e.N) p[j] = v[j];
+                }
+            }
+            if (e.act) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = gelu(v[j]);
+            }
+        } else {  // EPI_LOSS
+            if (e.cf) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (nb + j < e.N) e.cf[(size_t)row * e.ldcf + nb + j] = v[j];
+            }
+            const float* tp = e.tgt + (size_t)row * e.ldt + nb;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float d = nb + j < e.n_true ? v[j] - tp[j] : 0.0f;
+                sq += (double)d * (double)d;
+                v[j] = e.gscale * d;
+            }
+        }
     }
+    if (!live) return;
     if (e.mode == EPI_STORE && e.cf) {
-        float* p = e.cf + (size_t)blockIdx.z * e.cf_slice + (size_t)row * e.ldcf + nb;
+        float* p = e.cf + (size_t)z * e.cf_slice + (size_t)row * e.ldcf + nb;
         if (full && (e.ldcf & 3) == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
+            for (int q = 0; q < 8; ++q)
                 reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
+            for (int j = 0; j < 32; ++j)
                 if (nb + j < e.N) p[j] = v[j];
         }
     }
     if (e.cb) {
         __nv_bfloat16* p = e.cb + (size_t)row * e.ldcb + nb;
         if (full && (e.ldcb & 7) == 0) {
-            uint32_t w[8];
+            uint32_t w[16];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 16; ++q) {
                 const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
                 w[q] = *reinterpret_cast<const uint32_t*>(&h);
             }
-            reinterpret_cast<uint4*>(p)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-            reinterpret_cast<uint4*>(p)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                reinterpret_cast<uint4*>(p)[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
+            for (int j = 0; j < 32; ++j)
                 if (nb + j < e.N) p[j] = __float2bfloat16_rn(v[j]);
         }
     }
     if (e.ct) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
+        for (int j = 0; j < 32; ++j)
             if (nb + j < e.N) e.ct[(size_t)(nb + j) * e.ldct + row] = __float2bfloat16_rn(v[j]);
     }
 }
 
-template <int BN, int ST>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, GemmEpi e)
+// Persistent, warp-specialised GEMM.  Warp 0 (one lane) streams the K blocks of every tile the
+// CTA owns through the shared-memory ring; warp 1 allocates TMEM and (one lane) issues the MMAs of
+// tile i into accumulator i % 2; warps 2 .. 2+EPW-1 drain accumulator (i % 2) while the MMAs of tile
+// i + 1 run into the other one.  Epilogue warp w reads TMEM lane quarter w % 4 and, with EPW / 4
+// warps per quarter, its share of the columns.  Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// over (k slice, m tile, n tile), n fastest.
+template <int BN, int ST, int EPW>
+__global__ void __launch_bounds__(64 + 32 * EPW, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, int ksplit,
+                GemmEpi e)
 {
     constexpr uint32_t kBBytes = BN * kBK * 2;
     constexpr uint32_t kStage = kABytes + kBBytes;   // a multiple of 1024
-    constexpr uint32_t kCols = BN <= 64 ? 64 : (BN <= 128 ? 128 : 256);
+    constexpr uint32_t kAccStride = BN <= 64 ? 64 : (BN <= 128 ? 128 : 256);
+    constexpr uint32_t kCols = 2 * kAccStride;
+    constexpr int kEpiThreads = 32 * EPW;
+    constexpr int kColsPerWarp = BN / (EPW / 4);
+    static_assert(kColsPerWarp % 32 == 0, "epilogue column share must be a multiple of 32");
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST], accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * kBM;
-    const int kb_total = K / kBK;
-    const int kb_per = kb_total / (int)gridDim.z;
-    const int kb0 = blockIdx.z * kb_per;
-    const int nk = kb_per;
+    const int n_tiles = (e.N + BN - 1) / BN, m_tiles = (e.M + kBM - 1) / kBM;
+    const int per_slice = n_tiles * m_tiles;
+    const int total = per_slice * ksplit;
+    const int nk = K / kBK / ksplit;
     const uint32_t base = (saddr(smem_raw) + 1023u) & ~1023u;
 
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
                      "r"(kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 32) {
+    if (tid == 0) {
         for (int s = 0; s < ST; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&full_bar[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&empty_bar[s])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&acc_bar)));
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&accf_bar[a])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(&acce_bar[a])), "r"(kEpiThreads));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&done_bar)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    // bias of all N columns in shared memory behind the stage ring, zero-padded to a multiple of 32
+    float* sbias = reinterpret_cast<float*>(smem_raw + (base - saddr(smem_raw)) + (size_t)ST * kStage);
+    if (e.bias) {
+        const int npad = (e.N + 31) & ~31;
+        for (int i = tid; i < npad; i += blockDim.x) sbias[i] = i < e.N ? e.bias[i] : 0.0f;
     }
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = tmem_slot;
     bool ok = true;
+    double sq = 0.0;
 
-    if (tid == 0) {
-        // TMA producer
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
-        int issued = 0;
-        for (int i = 0; i < nk; ++i) {
-            const int s = i % ST;
-            if (i >= ST && !mbar_wait(saddr(&empty_bar[s]), (uint32_t)((i / ST - 1) & 1))) {
-                ok = false;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+            int it = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                const int z = t / per_slice, r = t - z * per_slice;
+                const int m0 = (r / n_tiles) * kBM, n0 = (r % n_tiles) * BN;
+                for (int i = 0; i < nk; ++i, ++it) {
+                    const int s = it % ST;
+                    if (it >= ST && !mbar_wait(saddr(&empty_bar[s]), (uint32_t)((it / ST - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    if (abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = saddr(&full_bar[s]);
+                    const uint32_t dA = base + (uint32_t)s * kStage, dB = dA + kABytes;
+                    const int kx = (z * nk + i) * kBK;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage)
+                                 : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+                        "{%2, %3}], [%4];" ::"r"(dA),
+                        "l"(reinterpret_cast<uint64_t>(&ta)), "r"(kx), "r"(m0), "r"(fb)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, "
+                        "{%2, %3}], [%4];" ::"r"(dB),
+                        "l"(reinterpret_cast<uint64_t>(&tb)), "r"(kx), "r"(n0), "r"(fb)
+                        : "memory");
+                }
             }
-            const uint32_t fb = saddr(&full_bar[s]);
-            const uint32_t dA = base + (uint32_t)s * kStage, dB = dA + kABytes;
-            const int kx = (kb0 + i) * kBK;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage) : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];" ::"r"(dA),
-                "l"(reinterpret_cast<uint64_t>(&ta)), "r"(kx), "r"(m0), "r"(fb)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-                "[%4];" ::"r"(dB),
-                "l"(reinterpret_cast<uint64_t>(&tb)), "r"(kx), "r"(n0), "r"(fb)
-                : "memory");
-            ++issued;
+            if (!ok) abort_flag = 1;
+            // every issued copy has landed before the CTA may exit (immediate in the normal case)
+            for (int i = it > ST ? it - ST : 0; i < it; ++i)
+                if (!mbar_wait(saddr(&full_bar[i % ST]), (uint32_t)((i / ST) & 1))) ok = false;
         }
-        // every issued copy has landed before the CTA may exit (immediate in the normal case)
-        for (int i = issued > ST ? issued - ST : 0; i < issued; ++i)
-            if (!mbar_wait(saddr(&full_bar[i % ST]), (uint32_t)((i / ST) & 1))) ok = false;
-    } else if (tid == 32) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(kBM, BN);
-        for (int i = 0; i < nk; ++i) {
-            const int s = i % ST;
-            if (!mbar_wait(saddr(&full_bar[s]), (uint32_t)((i / ST) & 1))) {
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            constexpr uint32_t idesc = idesc_bf16(kBM, BN);
+            int it = 0, tl = 0;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
+                const int acc = tl & 1;
+                if (tl >= 2 && !mbar_wait(saddr(&acce_bar[acc]), (uint32_t)((tl / 2 - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_after();
+                const uint32_t d = tmem + (uint32_t)acc * kAccStride;
+                for (int i = 0; i < nk; ++i, ++it) {
+                    const int s = it % ST;
+                    if (abort_flag || !mbar_wait(saddr(&full_bar[s]), (uint32_t)((it / ST) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_after();
+                    const uint32_t a0 = base + (uint32_t)s * kStage, b0 = a0 + kABytes;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t ad = desc_sw128(a0 + 32u * kk), bd = desc_sw128(b0 + 32u * kk);
+                        const uint32_t accum = (i > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     saddr(&empty_bar[s]))
+                                 : "memory");
+                }
+                if (!ok) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 saddr(&accf_bar[acc]))
+                             : "memory");
+            }
+            if (!ok) abort_flag = 1;
+            // tracks every MMA issued above (also after a give-up): released TMEM is never written
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             saddr(&done_bar))
+                         : "memory");
+        }
+        __syncwarp();
+    } else {
+        // epilogue warps
+        constexpr int kChunks = kColsPerWarp / 32;
+        const int q = warp & 3, part = (warp - 2) >> 2;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int tl = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+            const int acc = tl & 1;
+            const int z = t / per_slice, r = t - z * per_slice;
+            const int m0 = (r / n_tiles) * kBM, n0 = (r % n_tiles) * BN;
+            const int row = m0 + q * 32 + lane;
+            const int cbeg = n0 + part * kColsPerWarp;
+            // de-normalisation of this warp's columns, one per lane, fetched before the wait
+            float ps[kChunks], pm[kChunks];
+#pragma unroll
+            for (int k = 0; k < kChunks; ++k) {
+                const int n = cbeg + 32 * k + lane;
+                ps[k] = (e.mode == EPI_DRAG && n < e.n_true) ? e.ysig[n] : 0.0f;
+                pm[k] = (e.mode == EPI_DRAG && n < e.n_true) ? e.ymu[n] : 0.0f;
+            }
+            const int rowmask = (e.mode == EPI_DRAG && row < e.M) ? e.mask[row] : 0;
+            const bool got = mbar_wait(saddr(&accf_bar[acc]), (uint32_t)((tl / 2) & 1));
+            if (!__all_sync(0xffffffffu, got) || abort_flag) {
                 ok = false;
                 break;
             }
             tc_after();
-            const uint32_t a0 = base + (uint32_t)s * kStage, b0 = a0 + kABytes;
+            const uint32_t tacc = tmem + lane_base + (uint32_t)acc * kAccStride + (uint32_t)(part * kColsPerWarp);
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-                const uint64_t ad = desc_sw128(a0 + 32u * kk), bd = desc_sw128(b0 + 32u * kk);
-                const uint32_t accum = (i > 0 || kk > 0) ? 1u : 0u;
+            for (int k = 0; k < kChunks; ++k) {
+                const int nb = cbeg + 32 * k;
+                if (nb >= e.N) break;
+                float zz[32];
+                if (e.mode == EPI_BWD) {
+                    // pre-activations in flight while the accumulator is read
+                    if (row < e.M && nb + 32 <= e.N && (e.ldz & 3) == 0) {
+                        const float4* zp = reinterpret_cast<const float4*>(e.z + (size_t)row * e.ldz + nb);
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            const float4 w = zp[qq];
+                            zz[4 * qq] = w.x;
+                            zz[4 * qq + 1] = w.y;
+                            zz[4 * qq + 2] = w.z;
+                            zz[4 * qq + 3] = w.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            zz[j] = (row < e.M && nb + j < e.N) ? e.z[(size_t)row * e.ldz + nb + j] : 0.0f;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) zz[j] = 0.0f;
+                }
+                uint32_t rr[32];
                 asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(accum)
-                    : "memory");
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]), "=r"(rr[6]),
+                      "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]), "=r"(rr[12]), "=r"(rr[13]),
+                      "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]), "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]),
+                      "=r"(rr[21]), "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]), "=r"(rr[27]),
+                      "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+                    : "r"(tacc + (uint32_t)(32 * k)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
+                epi32(e, z, row, nb, v, sbias, ps[k], pm[k], zz, rowmask, sq);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             saddr(&empty_bar[s]))
-                         : "memory");
+            tc_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&acce_bar[acc])) : "memory");
         }
-        // tracks every MMA issued above, also after a give-up
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         saddr(&acc_bar))
-                     : "memory");
-    }
-    __syncwarp();
-
-    bool acc_ok = mbar_wait(saddr(&acc_bar), 0u);
-    tc_after();
-    if (!__syncthreads_and(ok && acc_ok)) {
-        if (tid == 0 && e.err) atomicOr(e.err, 1);
-        // MMAs still in flight must finish before the TMEM is released: wait once more (bounded)
-        if (!acc_ok) acc_ok = mbar_wait(saddr(&acc_bar), 0u);
-    } else {
-        const int row = m0 + warp * 32 + lane;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-        double sq = 0.0;
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            if (n0 + c0 >= e.N) break;
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(tl + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < e.M) epi16(e, row, n0 + c0, r, sq);
-        }
+        if (!ok) abort_flag = 1;
         if (e.mode == EPI_LOSS) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0 && sq != 0.0) atomicAdd(e.loss, sq);
         }
     }
-    tc_before();
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+    // every MMA has finished before the TMEM is released (bounded wait; immediate normally)
+    const bool fin = mbar_wait(saddr(&done_bar), 0u);
+    if (!__syncthreads_and(ok && fin) && tid == 0 && e.err) atomicOr(e.err, 1);
+    tc_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
 }
 
 template <int BN, int ST>
 bool launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int ksplit, const GemmEpi& e, cudaStream_t s)
 {
-    constexpr size_t shm = (size_t)ST * (kABytes + BN * kBK * 2) + 1024;
+    constexpr int EPW = 8;
+    constexpr size_t kMaxShm = 232448 - 256;   // 227 KB opt-in per block, less the static part
+    const size_t shm = (size_t)ST * (kABytes + BN * kBK * 2) + 1024 + (e.bias ? (size_t)((e.N + 31) & ~31) * 4 : 0);
+    if (shm > kMaxShm) return false;
     int dev = 0;
     cudaGetDevice(&dev);
-    static unsigned long long configured = 0;  // one bit per device
-    if (dev < 64 && !(configured >> dev & 1ull)) {
-        if (cudaFuncSetAttribute(k_gemm_bf16<BN, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) !=
+    if (dev >= 64) return false;
+    // dynamic shared memory limit raised per device to the largest size launched so far (the
+    // opt-in limit counts the kernel's static shared memory too)
+    static size_t configured[64] = {};
+    static int sms[64] = {};
+    if (shm > configured[dev]) {
+        if (cudaFuncSetAttribute(k_gemm_bf16<BN, ST, EPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) !=
             cudaSuccess)
             return false;
-        configured |= 1ull << dev;
+        configured[dev] = shm;
+        sms[dev] = sm_count();
     }
-    const dim3 grid((unsigned)((e.N + BN - 1) / BN), (unsigned)((e.M + kBM - 1) / kBM), (unsigned)ksplit);
-    k_gemm_bf16<BN, ST><<<grid, kThreads, shm, s>>>(ta, tb, K, e);
+    const long long tiles = (long long)((e.N + BN - 1) / BN) * ((e.M + kBM - 1) / kBM) * ksplit;
+    const int grid = (int)std::min<long long>(tiles, sms[dev]);
+    k_gemm_bf16<BN, ST, EPW><<<grid, 64 + 32 * EPW, shm, s>>>(ta, tb, K, ksplit, e);
     return cudaPeekAtLastError() == cudaSuccess;
 }
 
@@ -360,7 +514,7 @@ int gemm_pick_bn(int M, int N)
     if (N <= 64) return 64;
     if (N <= 128) return 128;
     if (N <= 192) return 192;
-    return 128;
+    return 256;
 }
 
 bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int bn, int ksplit, const GemmEpi& e,
@@ -370,8 +524,8 @@ bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int b
     if (ksplit > 1 && e.mode != EPI_STORE) return false;
     if (bn == 0) bn = gemm_pick_bn(e.M, e.N);
     switch (bn) {
-    case 64: return launch<64, 4>(ta, tb, K, ksplit, e, s);
-    case 128: return launch<128, 3>(ta, tb, K, ksplit, e, s);
+    case 64: return launch<64, 8>(ta, tb, K, ksplit, e, s);
+    case 128: return launch<128, 6>(ta, tb, K, ksplit, e, s);
     case 192: return launch<192, 4>(ta, tb, K, ksplit, e, s);
     case 256: return launch<256, 4>(ta, tb, K, ksplit, e, s);
     default: return false;

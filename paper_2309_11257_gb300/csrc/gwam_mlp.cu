@@ -571,10 +571,15 @@ int gwam_mlp_fit_normalization(gwam_mlp* m, const float* X, const float* Y, int6
         lo[f] = (float)(a - margin * w);
         hi[f] = (float)(b + margin * w);
     }
+    // targets: per-output mean, one shared scale = the RMS of the per-output standard deviations,
+    // so the loss is proportional to the squared error of the drag itself (every level weighted by
+    // its physical size; an output that is always zero is not amplified)
+    double s2 = 0.0;
+    for (int o = 0; o < no; ++o) s2 += h[4 * (ni + o) + 1] * h[4 * (ni + o) + 1];
+    const double scale = s2 > 0 ? std::sqrt(s2 / no) : 1.0;
     for (int o = 0; o < no; ++o) {
-        const double* q = &h[4 * (ni + o)];
-        ym[o] = (float)q[0];
-        ys[o] = (float)(q[1] > 0 ? q[1] : 1.0);
+        ym[o] = (float)h[4 * (ni + o)];
+        ys[o] = (float)scale;
     }
     if (stats_host) {
         // mu, sigma, lo, hi of the features, then mu, sigma of the targets

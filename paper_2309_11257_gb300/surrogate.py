@@ -47,11 +47,12 @@ def _source_table(grid, src, specs, members):
     return out.reshape(members * ncol, N_SRC)
 
 
-def generate(members=8, nx=64, ny=32, nz=90, steps=60, avg=20, launch_every=20, tag=0, convection=True,
+def generate(members=16, nx=64, ny=32, nz=90, steps=120, avg=40, launch_every=5, tag=0, convection=True,
              src_overrides=None, max_rays=None, dt=180.0):
     """Run the FP64 tracer on `members` backgrounds and return (X, Y, info): features
     [members * nx * ny][4 nz + 8] and drag targets [members * nx * ny][2 nz] as float32 CUDA
-    tensors, member-major then column order (j, i)."""
+    tensors, member-major then column order (j, i).  The sources launch every `launch_every` steps
+    (a quasi-continuous source), so the averaged drag approaches the columns' steady response."""
     import torch
     g = synth.rng(5000 + tag)
     grid = synth.sphere_grid(nx=nx, ny=ny, nz=nz, dz=1000.0)
