@@ -236,11 +236,13 @@ int gwam_selftest_math(const double *x, int64_t n, double *rcp_out, double *rsqr
 /* Self-test of the surrogate's tensor-core GEMM (tcgen05 + TMA, sm_103a): C = act(A . B^T + bias)
  * with A [M][K] and B [N][K] row-major BF16 device arrays (K contiguous, K a multiple of 64, base
  * addresses 16-byte aligned), bias [N] FP32 or NULL, act = GELU(z) = z Phi(z) when gelu != 0, C
- * [M][N] FP32, overwritten.  Products are exact, sums are FP32.  bn selects the tile width (0 = by
- * N; else 64, 128, 192 or 256).  Synchronises `stream`.  Errors: GWAM_EINVAL (shape, alignment,
- * tile), GWAM_ENOMEM, GWAM_ECUDA, GWAM_ETIMEOUT (a bounded device wait gave up). */
+ * [M][N] overwritten: FP32 (out_bf16 = 0) or BF16 rounded to nearest (out_bf16 = 1; written through
+ * shared memory by TMA stores when N is a multiple of 8).  Products are exact, sums are FP32.  bn
+ * selects the tile width (0 = by N; else 64, 128, 192 or 256).  Synchronises `stream`.  Errors:
+ * GWAM_EINVAL (shape, alignment, tile), GWAM_ENOMEM, GWAM_ECUDA, GWAM_ETIMEOUT (a bounded device wait
+ * gave up). */
 int gwam_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int gelu, int bn,
-                   float *C, void *stream);
+                   int out_bf16, void *C, void *stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Column drag surrogate (not in the paper: an emulator of the ray tracer's column drag, with the

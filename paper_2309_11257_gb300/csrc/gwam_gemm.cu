@@ -64,36 +64,50 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// erf by Abramowitz & Stegun, Handbook of Mathematical Functions, formula 7.1.26 (absolute error
-// <= 1.5e-7): erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x),
-// x >= 0, odd in x.  Returns erf(x) and exp(-x^2) (fast reciprocal and exponential intrinsics).
-__device__ __forceinline__ float erf_as(float x, float& ex2)
+// Phi(z) = (1 + erf(z / sqrt 2)) / 2 with erf by Abramowitz & Stegun, Handbook of Mathematical
+// Functions, formula 7.1.26 (absolute error <= 1.5e-7): for x = |z| / sqrt 2 >= 0,
+// erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x).
+// erf_abs returns erf(|z| / sqrt 2) and exp(-z^2 / 2); 1/sqrt 2 is folded into p, and exp(-z^2/2)
+// = 2^(-z^2 log2(e) / 2).  Hardware reciprocal and base-2 exponential approximations (PTX
+// rcp.approx / ex2.approx, relative errors near 2^-23 and 2^-22).
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    const float ax = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float erf_abs(float z, float& e)
+{
+    const float t = rcp_approx(fmaf(0.23164189961f, fabsf(z), 1.0f));   // p / sqrt 2, p = 0.3275911
     float poly = fmaf(t, 1.061405429f, -1.453152027f);
     poly = fmaf(t, poly, 1.421413741f);
     poly = fmaf(t, poly, -0.284496736f);
     poly = fmaf(t, poly, 0.254829592f);
-    ex2 = __expf(-ax * ax);
-    const float r = fmaf(-t * poly, ex2, 1.0f);
-    return copysignf(r, x);
+    e = ex2_approx(z * z * -0.72134752044f);                             // -log2(e) / 2
+    return fmaf(-(t * poly), e, 1.0f);
 }
 
-// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2
+// GELU(z) = z Phi(z) = z / 2 + |z| erf(|z| / sqrt 2) / 2
 __device__ __forceinline__ float gelu(float z)
 {
-    float ex2;
-    const float er = erf_as(z * 0.70710678118654752f, ex2);
-    return 0.5f * z * (1.0f + er);
+    float e;
+    const float r = erf_abs(z, e);
+    const float h = 0.5f * z;
+    return fmaf(fabsf(h), r, h);
 }
 
 // GELU'(z) = Phi(z) + z phi(z), phi(z) = exp(-z^2 / 2) / sqrt(2 pi)
 __device__ __forceinline__ float gelu_grad(float z)
 {
-    float ex2;
-    const float er = erf_as(z * 0.70710678118654752f, ex2);
-    return fmaf(z * 0.39894228040143268f, ex2, 0.5f * (1.0f + er));
+    float e;
+    const float r = erf_abs(z, e);
+    return fmaf(z * 0.39894228040143268f, e, fmaf(0.5f, copysignf(r, z), 0.5f));
 }
 
 // Epilogue of 32 consecutive accumulator columns n = nb .. nb+31 of one row.  Per-column
@@ -101,7 +115,8 @@ __device__ __forceinline__ float gelu_grad(float z)
 // every lane of the warp must call this (rows >= M only skip the stores).  zz: the prefetched
 // pre-activations of EPI_BWD.
 __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, float (&v)[32], const float* sbias,
-                                      float ps, float pm, const float (&zz)[32], int rowmask, double& sq)
+                                      float ps, float pm, const float (&zz)[32], int rowmask, double& sq,
+                                      uint32_t stg, int cc0)
 {
     const bool live = row < e.M;
     const bool full = nb + 32 <= e.N;
@@ -180,7 +195,23 @@ __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, 
                 if (nb + j < e.N) p[j] = v[j];
         }
     }
-    if (e.cb) {
+    if (e.cb && stg) {
+        // this row's 64 bytes into the warp's 128-byte-swizzled staging box (16-byte chunk c of
+        // row r at r * 128 + ((c ^ (r % 8)) * 16)); a TMA store writes the box out
+        uint32_t w[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            w[q] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t a = stg + ((uint32_t)((cc0 + q) ^ (row & 7)) << 4);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[4 * q]), "r"(w[4 * q + 1]),
+                         "r"(w[4 * q + 2]), "r"(w[4 * q + 3])
+                         : "memory");
+        }
+    } else if (e.cb) {
         __nv_bfloat16* p = e.cb + (size_t)row * e.ldcb + nb;
         if (full && (e.ldcb & 7) == 0) {
             uint32_t w[16];
@@ -213,8 +244,8 @@ __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, 
 // over (k slice, m tile, n tile), n fastest.
 template <int BN, int ST, int EPW>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
-    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, int ksplit,
-                GemmEpi e)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                const __grid_constant__ CUtensorMap tc, int K, int ksplit, GemmEpi e)
 {
     constexpr uint32_t kBBytes = BN * kBK * 2;
     constexpr uint32_t kStage = kABytes + kBBytes;   // a multiple of 1024
@@ -222,7 +253,8 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     constexpr uint32_t kCols = 2 * kAccStride;
     constexpr int kEpiThreads = 32 * EPW;
     constexpr int kColsPerWarp = BN / (EPW / 4);
-    static_assert(kColsPerWarp % 32 == 0, "epilogue column share must be a multiple of 32");
+    static_assert(kColsPerWarp % 64 == 0, "epilogue column share must be a multiple of 64");
+    constexpr uint32_t kStgWarp = 32u * kColsPerWarp * 2u;   // BF16 staging of a warp's 32 rows
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST], accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_slot;
@@ -253,8 +285,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
-    // bias of all N columns in shared memory behind the stage ring, zero-padded to a multiple of 32
-    float* sbias = reinterpret_cast<float*>(smem_raw + (base - saddr(smem_raw)) + (size_t)ST * kStage);
+    // behind the stage ring: the epilogue warps' BF16 staging boxes (TMA-store mode), then the bias
+    // of all N columns, zero-padded to a multiple of 32
+    const uint32_t stg_base = base + (uint32_t)ST * kStage;
+    float* sbias = reinterpret_cast<float*>(smem_raw + (base - saddr(smem_raw)) + (size_t)ST * kStage +
+                                            (e.tstore ? (size_t)EPW * kStgWarp : 0));
     if (e.bias) {
         const int npad = (e.N + 31) & ~31;
         for (int i = tid; i < npad; i += blockDim.x) sbias[i] = i < e.N ? e.bias[i] : 0.0f;
@@ -382,6 +417,12 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 break;
             }
             tc_after();
+            const uint32_t stg_warp = stg_base + (uint32_t)(warp - 2) * kStgWarp;
+            if (e.tstore) {
+                // the previous tile's TMA store has finished reading this warp's staging boxes
+                if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                __syncwarp();
+            }
             const uint32_t tacc = tmem + lane_base + (uint32_t)acc * kAccStride + (uint32_t)(part * kColsPerWarp);
 #pragma unroll
             for (int k = 0; k < kChunks; ++k) {
@@ -423,11 +464,34 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
-                epi32(e, z, row, nb, v, sbias, ps[k], pm[k], zz, rowmask, sq);
+                const uint32_t stg =
+                    e.tstore ? stg_warp + (uint32_t)((32 * k) / 64) * 4096u + (uint32_t)lane * 128u : 0u;
+                epi32(e, z, row, nb, v, sbias, ps[k], pm[k], zz, rowmask, sq, stg, ((32 * k) % 64) / 8);
             }
             tc_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&acce_bar[acc])) : "memory");
+            if (e.tstore) {
+                // staging -> global by TMA (rows and columns outside the tensor are clipped)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+#pragma unroll
+                    for (int b = 0; b < kColsPerWarp / 64; ++b) {
+                        const int x = cbeg + 64 * b;
+                        if (x < e.N)
+                            asm volatile(
+                                "cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                    reinterpret_cast<uint64_t>(&tc)),
+                                "r"(x), "r"(m0 + q * 32), "r"(stg_warp + (uint32_t)b * 4096u)
+                                : "memory");
+                    }
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+            }
         }
+        // this warp's TMA stores have completed before the CTA exits
+        if (e.tstore && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
         if (!ok) abort_flag = 1;
         if (e.mode == EPI_LOSS) {
 #pragma unroll
@@ -450,12 +514,14 @@ int sm_count()
     return n > 0 ? n : 1;
 }
 
-template <int BN, int ST>
-bool launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int ksplit, const GemmEpi& e, cudaStream_t s)
+template <int BN, int ST, int EPW>
+bool launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int K, int ksplit, const GemmEpi& e,
+            cudaStream_t s)
 {
-    constexpr int EPW = 8;
     constexpr size_t kMaxShm = 232448 - 256;   // 227 KB opt-in per block, less the static part
-    const size_t shm = (size_t)ST * (kABytes + BN * kBK * 2) + 1024 + (e.bias ? (size_t)((e.N + 31) & ~31) * 4 : 0);
+    constexpr size_t kStg = (size_t)32 * BN / (EPW / 4) * 2 * EPW;
+    const size_t shm = (size_t)ST * (kABytes + BN * kBK * 2) + 1024 + (e.tstore ? kStg : 0) +
+                       (e.bias ? (size_t)((e.N + 31) & ~31) * 4 : 0);
     if (shm > kMaxShm) return false;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -473,7 +539,7 @@ bool launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int ksplit, con
     }
     const long long tiles = (long long)((e.N + BN - 1) / BN) * ((e.M + kBM - 1) / kBM) * ksplit;
     const int grid = (int)std::min<long long>(tiles, sms[dev]);
-    k_gemm_bf16<BN, ST, EPW><<<grid, 64 + 32 * EPW, shm, s>>>(ta, tb, K, ksplit, e);
+    k_gemm_bf16<BN, ST, EPW><<<grid, 64 + 32 * EPW, shm, s>>>(ta, tb, tc, K, ksplit, e);
     return cudaPeekAtLastError() == cudaSuccess;
 }
 
@@ -517,17 +583,22 @@ int gemm_pick_bn(int M, int N)
     return 256;
 }
 
-bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int bn, int ksplit, const GemmEpi& e,
-                      cudaStream_t s)
+bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap* tc, int K, int bn, int ksplit,
+                      const GemmEpi& e_in, cudaStream_t s)
 {
-    if (e.M < 1 || e.N < 1 || K < kBK || K % kBK || ksplit < 1 || (K / kBK) % ksplit || ksplit > 65535) return false;
-    if (ksplit > 1 && e.mode != EPI_STORE) return false;
+    if (e_in.M < 1 || e_in.N < 1 || K < kBK || K % kBK || ksplit < 1 || (K / kBK) % ksplit || ksplit > 65535)
+        return false;
+    if (ksplit > 1 && e_in.mode != EPI_STORE) return false;
+    GemmEpi e = e_in;
+    e.tstore = (tc && e.cb) ? 1 : 0;
+    static const CUtensorMap none{};
+    const CUtensorMap& tcm = e.tstore ? *tc : none;
     if (bn == 0) bn = gemm_pick_bn(e.M, e.N);
     switch (bn) {
-    case 64: return launch<64, 8>(ta, tb, K, ksplit, e, s);
-    case 128: return launch<128, 6>(ta, tb, K, ksplit, e, s);
-    case 192: return launch<192, 4>(ta, tb, K, ksplit, e, s);
-    case 256: return launch<256, 4>(ta, tb, K, ksplit, e, s);
+    case 64: return launch<64, 8, 4>(ta, tb, tcm, K, ksplit, e, s);
+    case 128: return launch<128, 5, 8>(ta, tb, tcm, K, ksplit, e, s);
+    case 192: return launch<192, 4, 12>(ta, tb, tcm, K, ksplit, e, s);
+    case 256: return launch<256, 3, 16>(ta, tb, tcm, K, ksplit, e, s);
     default: return false;
     }
 }
@@ -535,19 +606,21 @@ bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int b
 }  // namespace gwam
 
 // Self-test entry point (declared in gwam.h): C = act(A . B^T + bias) with BF16 A [M][K] and
-// B [N][K], FP32 C [M][N]; bn = 0 picks the tile width.
+// B [N][K]; C FP32 [M][N], or BF16 [M][N] (written by TMA stores when N is a multiple of 8);
+// bn = 0 picks the tile width.
 extern "C" int gwam_gemm_bf16(const void* A, const void* B, int M, int N, int K, const float* bias, int gelu, int bn,
-                              float* C, void* stream)
+                              int out_bf16, void* C, void* stream)
 {
     if (!A || !B || !C || M < 1 || N < 1 || K < 64 || K % 64 || (bn != 0 && bn != 64 && bn != 128 && bn != 192 &&
                                                                   bn != 256))
         return -1;
     cudaStream_t s = (cudaStream_t)stream;
     const int use_bn = bn ? bn : gwam::gemm_pick_bn(M, N);
-    CUtensorMap ta, tb;
+    CUtensorMap ta, tb, tc;
     if (!gwam::make_tmap_bf16(&ta, A, (uint64_t)M, (uint64_t)K, (uint64_t)K, 128) ||
         !gwam::make_tmap_bf16(&tb, B, (uint64_t)N, (uint64_t)K, (uint64_t)K, (uint32_t)use_bn))
         return -1;
+    const bool have_tc = out_bf16 && N % 8 == 0 && gwam::make_tmap_bf16(&tc, C, (uint64_t)M, (uint64_t)N, (uint64_t)N, 32);
     int* err = nullptr;
     if (cudaMallocAsync((void**)&err, sizeof(int), s) != cudaSuccess) return -2;
     cudaMemsetAsync(err, 0, sizeof(int), s);
@@ -557,10 +630,15 @@ extern "C" int gwam_gemm_bf16(const void* A, const void* B, int M, int N, int K,
     e.M = M;
     e.N = N;
     e.bias = bias;
-    e.cf = C;
-    e.ldcf = N;
+    if (out_bf16) {
+        e.cb = (__nv_bfloat16*)C;
+        e.ldcb = N;
+    } else {
+        e.cf = (float*)C;
+        e.ldcf = N;
+    }
     e.err = err;
-    const bool launched = gwam::gemm_bf16_launch(ta, tb, K, use_bn, 1, e, s);
+    const bool launched = gwam::gemm_bf16_launch(ta, tb, have_tc ? &tc : nullptr, K, use_bn, 1, e, s);
     int h = 0;
     cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(err, s);

@@ -56,6 +56,7 @@ struct GemmEpi {
     double* dv;
     int ncol, nlev;
     int* err;                 // bit 0 set when a bounded wait gave up
+    int tstore;               // set by gemm_bf16_launch: cb is written through an output tensor map
 };
 
 // 2-D BF16 tensor map of a row-major [rows][cols] matrix with leading dimension ld (elements),
@@ -64,10 +65,12 @@ bool make_tmap_bf16(CUtensorMap* map, const void* base, uint64_t rows, uint64_t 
                     uint32_t box_rows);
 
 // Launch: A described by ta (box rows 128), B by tb (box rows bn); K a multiple of 64, split into
-// ksplit slices along K (blockIdx.z; K / 64 must be divisible by ksplit).  bn = 0 picks the tile
-// width from N.  Returns false on an unsupported shape.
-bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, int K, int bn, int ksplit, const GemmEpi& e,
-                      cudaStream_t s);
+// ksplit slices along K (K / 64 must be divisible by ksplit).  tc (or null): tensor map of the BF16
+// output cb (box 64 columns x 32 rows) -- the epilogue then stages each warp's rows in shared memory
+// and writes them with TMA stores.  bn = 0 picks the tile width from N.  false on an unsupported
+// shape.
+bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap* tc, int K, int bn, int ksplit,
+                      const GemmEpi& e, cudaStream_t s);
 
 // The tile width gemm_bf16_launch uses for N when bn = 0 (the caller builds tb with this box).
 int gemm_pick_bn(int M, int N);

@@ -282,6 +282,7 @@ struct gwam_mlp {
     bool has_norm = false;
     int last_batch = 0;
     CUtensorMap tf_a[kMaxL + 1], tf_b[kMaxL + 1], tx_a[kMaxL + 1], tx_b[kMaxL + 1], tw_a[kMaxL + 1], tw_b[kMaxL + 1];
+    CUtensorMap to_act[kMaxL + 1], to_dz[kMaxL + 1];   // BF16 outputs written by TMA stores
     int bn_f[kMaxL + 1] = {}, bn_x[kMaxL + 1] = {}, bn_w[kMaxL + 1] = {};
     std::vector<void*> allocs;
     std::string last_error;
@@ -383,10 +384,11 @@ int check_err(gwam_mlp* m)
     return GWAM_OK;
 }
 
-bool gemm(gwam_mlp* m, const CUtensorMap& ta, const CUtensorMap& tb, int K, int bn, int ks, gwam::GemmEpi e)
+bool gemm(gwam_mlp* m, const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap* tc, int K, int bn, int ks,
+          gwam::GemmEpi e)
 {
     e.err = m->err;
-    return gwam::gemm_bf16_launch(ta, tb, K, bn, ks, e, m->s);
+    return gwam::gemm_bf16_launch(ta, tb, tc, K, bn, ks, e, m->s);
 }
 
 // forward through every layer for B rows of act[0]; last layer per `last`
@@ -407,13 +409,14 @@ bool forward(gwam_mlp* m, int B, bool train, const gwam::GemmEpi& last)
             e.ct = m->actT[l];
             e.ldct = m->max_batch;
         }
-        if (!gemm(m, m->tf_a[l], m->tf_b[l], m->D[l - 1], m->bn_f[l], 1, e)) return false;
+        if (!gemm(m, m->tf_a[l], m->tf_b[l], &m->to_act[l], m->D[l - 1], m->bn_f[l], 1, e)) return false;
     }
     gwam::GemmEpi e = last;
     e.M = B;
     e.N = m->D[m->nl];
     e.bias = m->b[m->nl];
-    return gemm(m, m->tf_a[m->nl], m->tf_b[m->nl], m->D[m->nl - 1], m->bn_f[m->nl], 1, e);
+    return gemm(m, m->tf_a[m->nl], m->tf_b[m->nl], e.cb ? &m->to_dz[m->nl] : nullptr, m->D[m->nl - 1],
+                m->bn_f[m->nl], 1, e);
 }
 
 }  // namespace
@@ -480,7 +483,9 @@ int gwam_mlp_create(gwam_mlp** out, const gwam_mlp_config* cfg, void* stream)
              gwam::make_tmap_bf16(&m->tx_a[l], m->dz[l], Bm, Do, Do, 128) &&
              gwam::make_tmap_bf16(&m->tx_b[l], m->WbT[l], Di, Do, Do, m->bn_x[l]) &&
              gwam::make_tmap_bf16(&m->tw_a[l], m->dzT[l], Do, Bm, Bm, 128) &&
-             gwam::make_tmap_bf16(&m->tw_b[l], m->actT[l - 1], Di, Bm, Bm, m->bn_w[l]);
+             gwam::make_tmap_bf16(&m->tw_b[l], m->actT[l - 1], Di, Bm, Bm, m->bn_w[l]) &&
+             gwam::make_tmap_bf16(&m->to_dz[l], m->dz[l], Bm, Do, Do, 32) &&
+             (l == m->nl || gwam::make_tmap_bf16(&m->to_act[l], m->act[l], Bm, Do, Do, 32));
     }
     if (!ok) {
         gwam_mlp_destroy(m);
@@ -661,7 +666,7 @@ int gwam_mlp_train_step(gwam_mlp* m, const float* X, const float* Y, int64_t n, 
         e.cf = m->partial;
         e.ldcf = m->D[l - 1];
         e.cf_slice = (long long)m->D[l] * m->D[l - 1];
-        ok = gemm(m, m->tw_a[l], m->tw_b[l], B, m->bn_w[l], S, e);
+        ok = gemm(m, m->tw_a[l], m->tw_b[l], nullptr, B, m->bn_w[l], S, e);
         k_rowsum<<<m->D[l], 256, 0, m->s>>>(m->dzT[l], m->max_batch, B, m->D[l], m->db_raw[l]);
         // input gradient of the layer below, times GELU'(Z_{l-1})
         if (l > 1 && ok) {
@@ -675,7 +680,7 @@ int gwam_mlp_train_step(gwam_mlp* m, const float* X, const float* Y, int64_t n, 
             x.ldcb = m->D[l - 1];
             x.ct = m->dzT[l - 1];
             x.ldct = m->max_batch;
-            ok = gemm(m, m->tx_a[l], m->tx_b[l], m->D[l], m->bn_x[l], 1, x);
+            ok = gemm(m, m->tx_a[l], m->tx_b[l], &m->to_dz[l - 1], m->D[l], m->bn_x[l], 1, x);
         }
         // Adam (or gradients only when lr = 0)
         if (ok) {

@@ -100,4 +100,4 @@ def test_surrogate_rejects_bad_configs_before_touching_the_device(gw):
     assert lib.gwam_mlp_train_step(None, None, None, 0, None, 64, 0, 0.0) == gw.GWAM_EINVAL
     assert lib.gwam_mlp_infer(None, None, 0, None, None, None, None) == gw.GWAM_EINVAL
     assert lib.gwam_mlp_merge_fallback(None, 0, 0, None, None, None, None, None) == gw.GWAM_EINVAL
-    assert lib.gwam_gemm_bf16(None, None, 128, 64, 64, None, 0, 0, None, None) == gw.GWAM_EINVAL
+    assert lib.gwam_gemm_bf16(None, None, 128, 64, 64, None, 0, 0, 0, None, None) == gw.GWAM_EINVAL

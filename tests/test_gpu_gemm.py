@@ -24,7 +24,7 @@ def _gelu(z):
     return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
 
 
-@pytest.mark.parametrize("M,N,K,bn,bias,gelu", [
+CASES = [
     (128, 64, 64, 64, False, False),
     (300, 180, 384, 0, True, True),
     (256, 512, 512, 0, True, False),
@@ -32,7 +32,10 @@ def _gelu(z):
     (129, 40, 192, 64, False, True),
     (513, 192, 512, 192, True, False),
     (2048, 512, 512, 128, False, False),
-])
+]
+
+
+@pytest.mark.parametrize("M,N,K,bn,bias,gelu", CASES)
 def test_gemm_matches_fp64(gw, M, N, K, bn, bias, gelu):
     import torch
     g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
@@ -44,7 +47,7 @@ def test_gemm_matches_fp64(gw, M, N, K, bn, bias, gelu):
     Cd = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream()
     rc = gw.lib().gwam_gemm_bf16(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()), M, N, K,
-                                 C.c_void_p(bd.data_ptr() if bias else 0), int(gelu), bn,
+                                 C.c_void_p(bd.data_ptr() if bias else 0), int(gelu), bn, 0,
                                  C.c_void_p(Cd.data_ptr()), C.c_void_p(s.cuda_stream))
     assert rc == 0
     a, bb = A.double().numpy(), B.double().numpy()
@@ -57,12 +60,33 @@ def test_gemm_matches_fp64(gw, M, N, K, bn, bias, gelu):
     assert (err <= 2e-5 * S + 1e-6 * np.abs(ref)).all(), (err / (S + 1e-30)).max()
 
 
+@pytest.mark.parametrize("M,N,K,bn,bias,gelu", CASES)
+def test_gemm_bf16_output_through_tma_store(gw, M, N, K, bn, bias, gelu):
+    """BF16 output (TMA stores from swizzled shared memory when N % 8 == 0): the FP32 result of the
+    same kernel rounded to BF16, bit for bit."""
+    import torch
+    g = torch.Generator().manual_seed(M * 5 + N + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = (torch.randn(N, K, generator=g) / 8).to(torch.bfloat16).cuda()
+    b = torch.randn(N, generator=g).float().cuda() if bias else None
+    Cf = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    Cb = torch.full((M, N), float("nan"), dtype=torch.bfloat16, device="cuda")
+    s = torch.cuda.current_stream()
+    lib = gw.lib()
+    args = (C.c_void_p(A.data_ptr()), C.c_void_p(B.data_ptr()), M, N, K, C.c_void_p(b.data_ptr() if bias else 0),
+            int(gelu), bn)
+    assert lib.gwam_gemm_bf16(*args, 0, C.c_void_p(Cf.data_ptr()), C.c_void_p(s.cuda_stream)) == 0
+    assert lib.gwam_gemm_bf16(*args, 1, C.c_void_p(Cb.data_ptr()), C.c_void_p(s.cuda_stream)) == 0
+    ref = Cf.to(torch.bfloat16)
+    assert torch.equal(Cb.view(torch.int16), ref.view(torch.int16))
+
+
 def test_gemm_rejects_bad_shapes(gw):
     import torch
     A = torch.zeros(128, 64, dtype=torch.bfloat16, device="cuda")
     Cd = torch.zeros(128, 64, device="cuda")
     lib = gw.lib()
     p = C.c_void_p(A.data_ptr())
-    assert lib.gwam_gemm_bf16(p, p, 128, 64, 60, None, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
-    assert lib.gwam_gemm_bf16(p, p, 128, 64, 64, None, 0, 96, C.c_void_p(Cd.data_ptr()), None) == -1
-    assert lib.gwam_gemm_bf16(p, p, 0, 64, 64, None, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
+    assert lib.gwam_gemm_bf16(p, p, 128, 64, 60, None, 0, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
+    assert lib.gwam_gemm_bf16(p, p, 128, 64, 64, None, 0, 96, 0, C.c_void_p(Cd.data_ptr()), None) == -1
+    assert lib.gwam_gemm_bf16(p, p, 0, 64, 64, None, 0, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
