@@ -165,7 +165,7 @@ def gpu_arm(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     w = synth.workload(args.workload)
     grid, params = w["grid"], dict(w["params"])
-    fp32 = args.workload == "sphere_fp32"
+    fp32 = args.workload in ("sphere_fp32", "sphere_half_fp32")
     if fp32:
         params["precision"] = 1
     nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
@@ -498,7 +498,7 @@ def main():
     ap.add_argument("--train-steps", type=int, default=800,
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
-                    choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "surrogate"],
+                    choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
                          "ensemble: 16 members of the sphere with convective sources, graph-replayed steps; "
                          "surrogate: MLP inference over 32768 columns after training on tracer drag")

@@ -42,7 +42,10 @@ static void free_all(Context& c)
     for (int f = 0; f < NFIELD; ++f) {
         if (c.field[f]) cudaFree(c.field[f]);
         if (c.smooth[f]) cudaFree(c.smooth[f]);
+        if (c.nar32[f]) cudaFree(c.nar32[f]);
+        if (c.sm32[f]) cudaFree(c.sm32[f]);
     }
+    if (c.rho_inv32) cudaFree(c.rho_inv32);
     for (int q = 0; q < Context::kRing; ++q)
         for (int p = 0; p <= Context::kPhases; ++p)
             if (c.prof_ev[q][p]) cudaEventDestroy(c.prof_ev[q][p]);
@@ -226,6 +229,13 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         const size_t scan_blocks = (std::max(nr, ncell) + 2047) / 2048 + 2;
         dalloc(c, c.scan_tmp, scan_blocks + 1);
         c.scan_tmp_cap = (int64_t)scan_blocks + 1;
+        if (c.f32) {
+            for (int f = 0; f < NFIELD; ++f) {
+                dalloc(c, c.nar32[f], (size_t)c.field_len(f));
+                dalloc(c, c.sm32[f], (size_t)c.field_len(f));
+            }
+            dalloc(c, c.rho_inv32, ncell);
+        }
         for (int f = 0; f < NFIELD; ++f) {
             dalloc(c, c.field[f], (size_t)c.field_len(f));
             dalloc(c, c.smooth[f], (size_t)c.field_len(f));
@@ -642,7 +652,10 @@ int gwam_get_field_host(gwam_ctx* ctx, int which, double* out_host)
 {
     API_BEGIN(ctx)
     if (which < 0 || which >= NFIELD || !out_host) return GWAM_EINVAL;
-    if (c.P.smoothing) smooth_field(c, which);
+    if (c.P.smoothing) {
+        if (c.f32) smooth_field32(c, which);
+        else smooth_field(c, which);
+    }
     const double* src = c.P.smoothing ? c.smooth[which] : c.field[which];
     const int nlev = which <= F_ZP ? c.G.nz + 1 : c.G.nz;
     double* tmp = nullptr;

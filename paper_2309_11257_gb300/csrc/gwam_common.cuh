@@ -44,6 +44,9 @@ __device__ __forceinline__ bool warp_segment_reduce(int key, double (&v)[NV])
     const int next = __shfl_down_sync(0xffffffffu, key, 1);
     const bool head = (lane == 0) || (prev != key);
     const unsigned heads = __ballot_sync(0xffffffffu, head);
+    // every lane its own run (the usual case once ray volumes spread): nothing to combine, and
+    // no FP64 additions spent on it
+    if (heads == 0xffffffffu) return true;
     const unsigned upto = heads & (0xffffffffu >> (31 - lane));
     const int start = 31 - __clz(upto);
 #pragma unroll

@@ -95,6 +95,11 @@ struct Context {
     // grid fields (column-major; interface fields [col][nz+1])
     double* field[NFIELD] = {};
     double* smooth[NFIELD] = {};
+    // precision form: FP32 copies of the projected fields (narrowed once per step), their smoothed
+    // versions and 1 / rho (narrowed when the background is set)
+    float* nar32[NFIELD] = {};
+    float* sm32[NFIELD] = {};
+    float* rho_inv32 = nullptr;
     double* dudt_buf = nullptr;     // [nz][ny][nx]
     double* dvdt_buf = nullptr;
 
@@ -156,6 +161,7 @@ void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
 void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();
 void smooth_field(Context& c, int f);
+void smooth_field32(Context& c, int f);
 inline void swap_rays(Context& c) { c.swap_rays_(); }
 void run_step32(Context& c, double dt, double* du, double* dv);
 void convert_background32(Context& c, int member);

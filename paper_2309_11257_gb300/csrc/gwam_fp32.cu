@@ -22,11 +22,224 @@ __global__ void k_bg_to32(const Node* __restrict__ bg, Node32* __restrict__ bg32
     }
 }
 
+// FP64 -> FP32, round to nearest, for up to NFIELD arrays in one launch (blockIdx.y = array)
+struct NarrowSet {
+    const double* in[NFIELD];
+    float* out[NFIELD];
+    int64_t n[NFIELD];
+};
+
+__global__ void k_narrow(NarrowSet s)
+{
+    const int f = blockIdx.y;
+    const int64_t n = s.n[f];
+    const double* __restrict__ in = s.in[f];
+    float* __restrict__ out = s.out[f];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
 void convert_background32(Context& c, int member)
 {
     const int64_t o = (int64_t)member * c.G.ncell;
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
     k_bg_to32<<<blocks, kThreads, 0, c.stream>>>(c.bg + o, c.bg32 + o, c.G.ncell);
+    NarrowSet ns{};
+    ns.in[0] = c.rho_inv + o;
+    ns.out[0] = c.rho_inv32 + o;
+    ns.n[0] = c.G.ncell;
+    k_narrow<<<dim3((unsigned)blocks, 1), kThreads, 0, c.stream>>>(ns);
+}
+
+// ---------------------------------------------------------------------------- FP32 grid phase
+// The precision form keeps the projection sums (and the saturation sums and the budget) in FP64;
+// smoothing and divergence run in FP32: GB300's FP64 rate is 1/64 of its FP32 rate, and these
+// stencils would otherwise be bound by it.  The projected FP64 fields are narrowed once, smoothed
+// and differenced in FP32, and du/dt, dv/dt widened to the caller's FP64 on the way out.
+
+struct FieldSet32 {
+    const float* in[NFIELD];
+    float* out[NFIELD];
+};
+
+// separable 1-2-1 x 1-2-1 smoothing (periodic in lambda, edge row reused at the poles), as
+// k_smooth_fields: block (32 levels, 8 columns) of one row, blockIdx.z = field
+__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, int f0)
+{
+    const int f = f0 + blockIdx.z;
+    const int nlev = f <= F_ZP ? G.nz + 1 : G.nz;
+    const int ntx = (G.nx + 7) / 8;
+    const int mem = blockIdx.y;
+    const int j = blockIdx.x / ntx;
+    const int i = (blockIdx.x % ntx) * 8 + threadIdx.y;
+    if (i >= G.nx) return;
+    const int im = i == 0 ? G.nx - 1 : i - 1, ip = i + 1 == G.nx ? 0 : i + 1;
+    int jm = j - 1, jp = j + 1;
+    if (G.geometry == 1) {
+        jm = jm < 0 ? 0 : jm;
+        jp = jp >= G.ny ? G.ny - 1 : jp;
+    } else {
+        jm = jm < 0 ? G.ny - 1 : jm;
+        jp = jp >= G.ny ? 0 : jp;
+    }
+    const int64_t base = (int64_t)mem * G.ncol;
+    const int64_t r0 = (base + (int64_t)jm * G.nx) * nlev, r1 = (base + (int64_t)j * G.nx) * nlev,
+                  r2 = (base + (int64_t)jp * G.nx) * nlev;
+    const int64_t cm = (int64_t)im * nlev, c0 = (int64_t)i * nlev, cp = (int64_t)ip * nlev;
+    const float* __restrict__ F = fs.in[f];
+    float* __restrict__ O = fs.out[f];
+    for (int lev = threadIdx.x; lev < nlev; lev += 32) {
+        const float a = F[r0 + cm + lev] + 2.0f * F[r0 + c0 + lev] + F[r0 + cp + lev];
+        const float b = F[r1 + cm + lev] + 2.0f * F[r1 + c0 + lev] + F[r1 + cp + lev];
+        const float cc = F[r2 + cm + lev] + 2.0f * F[r2 + c0 + lev] + F[r2 + cp + lev];
+        O[r1 + c0 + lev] = (a + 2.0f * b + cc) * 0.0625f;
+    }
+}
+
+// divergence (Eq. mean-flow-impact) in FP32, as k_divergence: one block per (row, tile of TW
+// columns), results transposed through shared memory into the caller's [nz][ny][nx] FP64 layout
+__global__ void k_divergence32(Grid G, int TW, const float* __restrict__ fzl, const float* __restrict__ fzp,
+                               const float* __restrict__ fll, const float* __restrict__ flp,
+                               const float* __restrict__ fpl, const float* __restrict__ fpp,
+                               const float* __restrict__ el, const float* __restrict__ ep,
+                               const float* __restrict__ rho_inv, double* __restrict__ du, double* __restrict__ dv)
+{
+    extern __shared__ float tile32[];
+    float* tu = tile32;
+    float* tv = tile32 + (size_t)TW * G.nz;
+    float* lev32 = tile32 + 2 * (size_t)TW * G.nz;   // 1 / (a + z_k) per level
+    for (int k = threadIdx.x; k < G.nz; k += blockDim.x) lev32[k] = (float)G.lev_inv_r[k];
+    __syncthreads();
+    const int ntx = (G.nx + TW - 1) / TW;
+    const int mem = blockIdx.x / (ntx * G.ny);
+    const int bl = blockIdx.x - mem * ntx * G.ny;
+    const int j = bl / ntx;
+    const int i0 = (bl % ntx) * TW;
+    {
+        const int64_t oc = (int64_t)mem * G.ncell, oz = (int64_t)mem * G.ncol * (G.nz + 1);
+        fzl += oz; fzp += oz;
+        fll += oc; flp += oc; fpl += oc; fpp += oc; el += oc; ep += oc; rho_inv += oc;
+        if (du) du += oc;
+        if (dv) dv += oc;
+    }
+    const int nz = G.nz;
+    const int n = TW * nz;
+    const float h2x = (float)(0.5 * G.inv_dX), h2y = (float)(0.5 * G.inv_dY), idz = (float)G.inv_dz,
+                ig = (float)G.inv_g;
+    float rcp_cos = 1.0f, cn = 0.0f, cs = 0.0f;
+    if (G.geometry == 1) {
+        rcp_cos = (float)G.row_inv_cos[j];
+        if (j + 1 < G.ny) cn = (float)G.row_cos[j + 1];
+        if (j - 1 >= 0) cs = (float)G.row_cos[j - 1];
+    }
+    const int jn = G.geometry == 1 ? j + 1 : wrap_int(j + 1, G.ny);
+    const int js = G.geometry == 1 ? j - 1 : wrap_int(j - 1, G.ny);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int k = t % nz, ii = t / nz;
+        const int i = i0 + ii;
+        if (i >= G.nx) continue;
+        const int ie = i + 1 == G.nx ? 0 : i + 1, iw = i == 0 ? G.nx - 1 : i - 1;
+        const int64_t c = ((int64_t)j * G.nx + i) * nz + k;
+        const int64_t ce = ((int64_t)j * G.nx + ie) * nz + k;
+        const int64_t cw = ((int64_t)j * G.nx + iw) * nz + k;
+        const int64_t zc = ((int64_t)j * G.nx + i) * (nz + 1) + k;
+        float pl_n = 0.0f, pl_s = 0.0f, pp_n = 0.0f, pp_s = 0.0f;
+        if (jn >= 0 && jn < G.ny) {
+            const int64_t cc = ((int64_t)jn * G.nx + i) * nz + k;
+            pl_n = fpl[cc];
+            pp_n = fpp[cc];
+        }
+        if (js >= 0 && js < G.ny) {
+            const int64_t cc = ((int64_t)js * G.nx + i) * nz + k;
+            pl_s = fpl[cc];
+            pp_s = fpp[cc];
+        }
+        const float ri = rho_inv[c];
+        float div_u, div_v;
+        const float dzl = (fzl[zc + 1] - fzl[zc]) * idz;
+        const float dzp = (fzp[zc + 1] - fzp[zc]) * idz;
+        if (G.geometry == 1) {
+            const float mh = rcp_cos * lev32[k];
+            div_u = ((fll[ce] - fll[cw]) * h2x + (cn * pl_n - cs * pl_s) * h2y) * mh + dzl;
+            div_v = ((flp[ce] - flp[cw]) * h2x + (cn * pp_n - cs * pp_s) * h2y) * mh + dzp;
+        } else {
+            div_u = (fll[ce] - fll[cw]) * h2x + (pl_n - pl_s) * h2y + dzl;
+            div_v = (flp[ce] - flp[cw]) * h2x + (pp_n - pp_s) * h2y + dzp;
+        }
+        tu[k * TW + ii] = (el[c] * ig - div_u) * ri;
+        tv[k * TW + ii] = (ep[c] * ig - div_v) * ri;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const int ii = t % TW, k = t / TW;
+        const int i = i0 + ii;
+        if (i >= G.nx) continue;
+        const int64_t o = ((int64_t)k * G.ny + j) * G.nx + i;
+        if (du) du[o] = (double)tu[k * TW + ii];
+        if (dv) dv[o] = (double)tv[k * TW + ii];
+    }
+}
+
+__global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+static void narrow_fields(Context& c, int f0, int f1)
+{
+    NarrowSet ns{};
+    int64_t nmax = 0;
+    for (int f = f0; f < f1; ++f) {
+        ns.in[f - f0] = c.field[f];
+        ns.out[f - f0] = c.nar32[f];
+        ns.n[f - f0] = c.field_len(f);
+        nmax = std::max(nmax, c.field_len(f));
+    }
+    const int blocks = (int)std::min<int64_t>((nmax + kThreads - 1) / kThreads, 2 * 152 * 8 / (f1 - f0) + 1);
+    k_narrow<<<dim3((unsigned)blocks, (unsigned)(f1 - f0)), kThreads, 0, c.stream>>>(ns);
+}
+
+static void smooth32(Context& c, int f0, int f1)
+{
+    FieldSet32 fs{};
+    for (int f = 0; f < NFIELD; ++f) {
+        fs.in[f] = c.nar32[f];
+        fs.out[f] = c.sm32[f];
+    }
+    const dim3 grid((unsigned)(((c.G.nx + 7) / 8) * c.G.ny), (unsigned)c.G.members, (unsigned)(f1 - f0));
+    k_smooth_fields32<<<grid, dim3(32, 8), 0, c.stream>>>(c.G, fs, f0);
+}
+
+void smooth_field32(Context& c, int f)
+{
+    narrow_fields(c, f, f + 1);
+    smooth32(c, f, f + 1);
+    // widened into the FP64 smoothed copy the field readers use
+    const int blocks = (int)std::min<int64_t>((c.field_len(f) + kThreads - 1) / kThreads, 8192);
+    k_widen<<<blocks, kThreads, 0, c.stream>>>(c.sm32[f], c.smooth[f], c.field_len(f));
+}
+
+static void grid_phase32(Context& c, double* du, double* dv, int mask)
+{
+    const Grid& G = c.G;
+    cudaStream_t s = c.stream;
+    double* out_u = du ? du : c.dudt_buf;
+    double* out_v = dv ? dv : c.dvdt_buf;
+    narrow_fields(c, 0, F_WAD);
+    float* const* fl = c.nar32;
+    if (c.P.smoothing) {
+        smooth32(c, 0, F_WAD);
+        fl = c.sm32;
+    }
+    const int TW = G.nz <= 96 ? 32 : 16;
+    const size_t shm = sizeof(float) * (2 * (size_t)TW * G.nz + G.nz);
+    if (shm > 48 * 1024) cudaFuncSetAttribute(k_divergence32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    const int ntx = (G.nx + TW - 1) / TW;
+    k_divergence32<<<ntx * G.ny * G.members, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP],
+                                                                 fl[F_PL], fl[F_PP], fl[F_EL], fl[F_EP], c.rho_inv32,
+                                                                 out_u, out_v);
+    finalize_tallies(c, mask, 1);
 }
 
 // RK3 advance in FP32 (the ray-step kernel of the precision form): state read and written in
@@ -425,7 +638,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 5);
     if (c.tune_active) ++c.tune_pending;
     prof_mark(c, 4);
-    grid_phase(c, du, dv, mask);
+    grid_phase32(c, du, dv, mask);
     prof_mark(c, 5);
     swap_rays(c);
 }
