@@ -233,6 +233,13 @@ int gwam_cell_offsets_noalloc(const int32_t *cells, int64_t n, int32_t ncell, in
  * rsqrt_out[i] ~ 1/sqrt(x[i]) for positive normal x.  Device pointers, n values; synchronises. */
 int gwam_selftest_math(const double *x, int64_t n, double *rcp_out, double *rsqrt_out, void *stream);
 
+/* Self-test of the precision form's FP64-free helpers: widened[i] = x[i] as a double by integer
+ * re-biasing (must equal the hardware float -> double conversion bit for bit, subnormals, zeros,
+ * infinities and NaN classes included); action[i] (or NULL) = x[i] x[i+1] x[i+2] x[i+3] (indices
+ * mod n) formed in double-float arithmetic on the FP32 pipes and returned as a double.  Device
+ * pointers; synchronises `stream`. */
+int gwam_selftest_widen(const float *x, int64_t n, double *widened, double *action, void *stream);
+
 /* Self-test of the surrogate's tensor-core GEMM (tcgen05 + TMA, sm_103a): C = act(A . B^T + bias)
  * with A [M][K] and B [N][K] row-major BF16 device arrays (K contiguous, K a multiple of 64, base
  * addresses 16-byte aligned), bias [N] FP32 or NULL, act = GELU(z) = z Phi(z) when gelu != 0, C

@@ -32,7 +32,7 @@ static void dalloc(Context& c, T*& p, size_t count)
 
 static void free_all(Context& c)
 {
-    void* ptrs[] = {c.bg, c.bg32, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.bg_scratch,
+    void* ptrs[] = {c.bg, c.bg32, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.bg_scratch,
                     c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
                     c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
                     c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
@@ -159,6 +159,16 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         G.inv_nx = 1.0 / G.nx;
         G.inv_ny = 1.0 / G.ny;
         G.inv_g = 1.0 / G.g;
+        G.f_dX = (float)G.dX;
+        G.f_dY = (float)G.dY;
+        G.f_dz = (float)G.dz;
+        G.f_y0 = (float)G.y0;
+        G.f_radius = (float)G.radius;
+        G.f_omega = (float)G.omega;
+        G.f_f0 = (float)G.f0;
+        G.f_inv_dX = (float)G.inv_dX;
+        G.f_inv_dY = (float)G.inv_dY;
+        G.f_inv_dz = (float)G.inv_dz;
         Params& P = c.P;
         P.gamma_mode = params->gamma_mode;
         P.saturation = params->saturation;
@@ -167,6 +177,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         P.splitting = params->splitting;
         P.cap = params->cap_per_column;
         P.alpha_s = params->alpha_s;
+        P.f_alpha_s = (float)params->alpha_s;
         P.min_split_dz = params->min_split_dz;
         c.max_rays = params->max_rays;
         // persistent grids: multiples of the SM count; the three heavy ray kernels are autotunable
@@ -195,6 +206,22 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.row_cos = c.tables;
             G.row_inv_cos = c.tables + G.ny;
             G.lev_inv_r = c.tables + 2 * G.ny;
+            std::vector<float> t32(2 * (size_t)G.ny + (size_t)G.ny * G.nz);
+            for (int j = 0; j < G.ny; ++j) {
+                t32[j] = (float)tab[j];
+                t32[G.ny + j] = (float)(tab[G.ny + j] * G.inv_dX * G.inv_dY);
+                for (int k = 0; k < G.nz; ++k) {
+                    const double ir = tab[2 * G.ny + k];
+                    const double iv = G.geometry == 1 ? ir * ir * tab[G.ny + j] * G.inv_dX * G.inv_dY * G.inv_dz
+                                                      : G.inv_dX * G.inv_dY * G.inv_dz;
+                    t32[2 * (size_t)G.ny + (size_t)j * G.nz + k] = (float)iv;
+                }
+            }
+            dalloc(c, c.tables32, t32.size());
+            GWAM_CUDA(cudaMemcpy(c.tables32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+            G.row_cos32 = c.tables32;
+            G.whf32 = c.tables32 + G.ny;
+            G.ivol32 = c.tables32 + 2 * G.ny;
         }
         c.f32 = params->precision == 1;
         for (int b = 0; b < 2; ++b) {

@@ -59,6 +59,7 @@ struct Context {
     double* rho = nullptr;          // rho per node
     double* rho_inv = nullptr;      // 1 / rho per node
     double* tables = nullptr;       // row_cos[ny], row_inv_cos[ny], lev_inv_r[nz]
+    float* tables32 = nullptr;      // row_cos32[ny], whf32[ny], ivol32[ny * nz]
     double* bg_scratch = nullptr;   // staging of caller fields ([nz][ny][nx], 4 fields)
 
     // ray volumes: A holds the canonical array between steps, B is the re-binned output

@@ -66,11 +66,17 @@ struct Grid {
     const double* row_cos;      // cos(phi_j) of every row centre (sphere), 1 on the f-plane
     const double* row_inv_cos;  // 1 / row_cos
     const double* lev_inv_r;    // 1 / (a + z_k) of every level centre (sphere), 1 on the f-plane
+    // FP32 copies for the precision form (a float <- double conversion runs at the FP64 rate)
+    float f_dX, f_dY, f_dz, f_y0, f_radius, f_omega, f_f0, f_inv_dX, f_inv_dY, f_inv_dz;
+    const float* row_cos32;     // [ny]
+    const float* ivol32;        // [ny * nz]: 1 / cell volume of row j, level k
+    const float* whf32;         // [ny]: row_inv_cos * inv_dX * inv_dY (solid-angle share per unit extent)
 };
 
 struct Params {
     int gamma_mode, saturation, smoothing, flux_form, splitting, cap;
     double alpha_s, min_split_dz;
+    float f_alpha_s;
 };
 
 // Ray-volume state, structure of arrays of double2 (16-byte vector loads):

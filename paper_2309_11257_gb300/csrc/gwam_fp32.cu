@@ -422,9 +422,10 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
         if (P.saturation) {
             Intr32 in;
             intrinsic32(G, bg + (int64_t)member_of(ch.id) * G.ncell, ch, in);
-            const double av = action32(ch) * inv_cell_volume(G, ch.j, ch.k);
-            pj[p] = (double)(in.m2 * in.kh2 * in.iw * in.iK2) * av;
-            k2[p] = (double)in.K2;
+            // P_j alpha_j = m^2 k_h^2 / (w K^2) N Px Py Pz / V_c in double-float, one FP64 add at the end
+            const DF av = df_mul(action_df(ch), G.ivol32[ch.j * G.nz + ch.k]);
+            pj[p] = df_to_double(df_mul(av, in.m2 * in.kh2 * in.iw * in.iK2));
+            k2[p] = widen(in.K2);
         }
     }
 }
@@ -441,8 +442,12 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
                                                           double* __restrict__ wad, double* __restrict__ partials,
                                                           int pstride)
 {
+    // FP64 work is kept out of the per-ray path (GB300's FP64 rate is 1/72 of FP32): the action
+    // and the budget terms in double-float, float -> double by integer widening, FP64 only in the
+    // grid atomics (L2) and one addition per thread for the budget
     const int n = ctl->status ? 0 : off2[G.ncell_all];
-    double w_sat = 0.0, w_tot = 0.0;
+    DF w_sat{0.0f, 0.0f}, w_tot{0.0f, 0.0f};
+    const float dtf = (float)dt;
     const int stride = gridDim.x * blockDim.x;
     for (int p0 = blockIdx.x * blockDim.x; p0 < n; p0 += stride) {
         const int p = p0 + threadIdx.x;
@@ -455,27 +460,29 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
             S32 s;
             load32(G, B, p, s);
             if (P.saturation) {
-                const double kap = kappa[p];
-                if (kap > 0.0) {
-                    const double fac = fmax(0.0, 1.0 - 2.0 * kap * k2[p] * dt);
-                    const double nold = s.n;
-                    s.n = (float)(nold * fac);
-                    w_sat += (nold - (double)s.n) * (double)s.p[0] * (double)s.p[1] * (double)s.p[2];
+                const double kapd = kappa[p];
+                if (__double_as_longlong(kapd) > 0) {   // kappa >= 0, so positive bits <=> kappa > 0
+                    const float kap = __double2float_rn(kapd), kk2 = __double2float_rn(k2[p]);
+                    const float fac = fmaxf(0.0f, 1.0f - 2.0f * kap * kk2 * dtf);
+                    const float nold = s.n;
+                    s.n = nold * fac;
+                    w_sat = df_add(w_sat, df_mul(df_mul(df_mul(df_diff(nold, s.n), s.p[0]), s.p[1]), s.p[2]));
                     float4 q1 = B.q[1][p];
                     q1.w = s.n;
                     B.q[1][p] = q1;
                 }
             }
-            const double W = (double)s.n * (double)s.p[0] * (double)s.p[1] * (double)s.p[2];
-            w_tot += W;
+            const DF Wd = action_df(s);
+            w_tot = df_add(w_tot, Wd);
+            const float W = __fadd_rn(Wd.hi, Wd.lo);
             const int mem = member_of(s.id);
             Intr32 in;
             intrinsic32(G, bg + (int64_t)mem * G.ncell, s, in);
             col = mem * G.ncol + s.j * G.nx + s.i;
             key = col * G.nz + s.k;
             const float Vj = in.g.hX * s.e[0] * (G.geometry == 1 ? in.g.r : 1.0f) * s.e[1] * s.e[2];
-            const float A = (float)W * __frcp_rn(Vj);
-            const float aw = (float)(W * inv_cell_volume(G, s.j, s.k));
+            const float A = W * __frcp_rn(Vj);
+            const float aw = W * G.ivol32[s.j * G.nz + s.k];
             const float k = s.w[0], l = s.w[1], m = s.w[2];
             const float mg2c = in.mg2 * in.c;
             const float chx = k * mg2c, chy = l * mg2c, chr = -m * in.kh2 * in.c;
@@ -497,16 +504,16 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
                 zl = chr * k; zp = chr * l;
                 el = 0.0f; ep = 0.0f;
             }
-            hv[0] = (double)(aw * t_ll); hv[1] = (double)(aw * t_lp); hv[2] = (double)(aw * t_pl);
-            hv[3] = (double)(aw * t_pp); hv[4] = (double)(aw * el); hv[5] = (double)(aw * ep); hv[6] = (double)aw;
+            hv[0] = widen(aw * t_ll); hv[1] = widen(aw * t_lp); hv[2] = widen(aw * t_pl);
+            hv[3] = widen(aw * t_pp); hv[4] = widen(aw * el); hv[5] = widen(aw * ep); hv[6] = widen(aw);
             zl *= A;
             zp *= A;
-            wh = in.g.cphi * s.e[0] * s.e[1] * (float)(G.row_inv_cos[s.j] * G.inv_dX * G.inv_dY);
-            const float zc = ((float)s.k + s.o[2]) * (float)G.dz;
+            wh = in.g.cphi * s.e[0] * s.e[1] * G.whf32[s.j];
+            const float zc = ((float)s.k + s.o[2]) * G.f_dz;
             lo = zc - 0.5f * s.e[2];
             hi = zc + 0.5f * s.e[2];
-            kk0 = max(1, (int)floorf(lo * (float)G.inv_dz - 0.5f));
-            const int kk1 = min(G.nz - 1, (int)ceilf(hi * (float)G.inv_dz + 0.5f));
+            kk0 = max(1, (int)floorf(lo * G.f_inv_dz - 0.5f));
+            const int kk1 = min(G.nz - 1, (int)ceilf(hi * G.f_inv_dz + 0.5f));
             nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
         }
         if (warp_segment_reduce(key, hv) && key >= 0) {
@@ -526,12 +533,12 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
             int zkey = -1;
             if (o < nkk) {
                 const int kk = kk0 + o;
-                const float slo = ((float)kk - 0.5f) * (float)G.dz, shi = ((float)kk + 0.5f) * (float)G.dz;
+                const float slo = ((float)kk - 0.5f) * G.f_dz, shi = ((float)kk + 0.5f) * G.f_dz;
                 const float ov = fminf(hi, shi) - fmaxf(lo, slo);
                 if (ov > 0.0f) {
-                    const float w = wh * ov * (float)G.inv_dz;
-                    zv[0] = (double)(w * zl);
-                    zv[1] = (double)(w * zp);
+                    const float w = wh * ov * G.f_inv_dz;
+                    zv[0] = widen(w * zl);
+                    zv[1] = widen(w * zp);
                     zkey = col * (G.nz + 1) + kk;
                 }
             }
@@ -541,8 +548,8 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
             }
         }
     }
-    const double ws = block_sum(w_sat);
-    const double wt = block_sum(w_tot);
+    const double ws = block_sum(df_to_double(w_sat));
+    const double wt = block_sum(df_to_double(w_tot));
     if (threadIdx.x == 0) {
         partials[T_SAT * pstride + blockIdx.x] = ws;
         partials[T_TOTAL * pstride + blockIdx.x] = wt;

@@ -50,6 +50,71 @@ __device__ __forceinline__ double action32(const S32& s)
     return (double)s.n * (double)s.p[0] * (double)s.p[1] * (double)s.p[2];
 }
 
+// Exact float -> double with integer operations only (on GB300 the conversion instruction runs at
+// the FP64 rate): sign kept, exponent re-biased from 127 to 1023, the 23 mantissa bits moved to the
+// top of the 52-bit field; subnormal floats are normalised first; infinities and NaNs keep their
+// class.
+__device__ __forceinline__ double widen(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t sign = u & 0x80000000u;
+    uint32_t ex = (u >> 23) & 0xFFu, man = u & 0x7FFFFFu;
+    if (ex == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | (man >> 3)), (int)(man << 29));
+    if (ex == 0u) {
+        if (man == 0u) return __hiloint2double((int)sign, 0);
+        const int sh = __clz((int)man) - 8;   // moves the leading one to bit 23
+        man = (man << sh) & 0x7FFFFFu;
+        ex = 1u - (uint32_t)sh;               // wraps below zero; the re-bias brings it back
+    }
+    return __hiloint2double((int)(sign | ((ex + 896u) << 20) | (man >> 3)), (int)(man << 29));
+}
+
+// Double-float values hi + lo (|lo| <= ulp(hi) / 2) on the FP32 pipes, about 48 significant bits:
+// products by TwoProduct (an FMA gives the exact rounding error), sums by TwoSum (Dekker 1971,
+// Knuth); every operation is an explicitly rounded intrinsic, never contracted or reordered.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_mul(DF x, float b)
+{
+    const float p = __fmul_rn(x.hi, b);
+    const float e = __fmaf_rn(x.lo, b, __fmaf_rn(x.hi, b, -p));
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb)), __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// a - b exactly as a double-float
+__device__ __forceinline__ DF df_diff(float a, float b)
+{
+    const float s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb))};
+}
+
+__device__ __forceinline__ double df_to_double(DF x) { return widen(x.hi) + widen(x.lo); }
+
+// N Px Py Pz as a double-float (relative error about 2^-47)
+__device__ __forceinline__ DF action_df(const S32& s)
+{
+    return df_mul(df_mul(df_prod(s.n, s.p[0]), s.p[1]), s.p[2]);
+}
+
 // ------------------------------------------------------------------------------ gather
 
 struct Bg32 {
@@ -132,9 +197,9 @@ struct Geo32 {
 __device__ __forceinline__ void geo32(const Grid& G, const S32& s, const float o[3], Geo32& g)
 {
     if (G.geometry == 1) {
-        const float phi = (float)G.y0 + ((float)s.j + o[1]) * (float)G.dY;
+        const float phi = G.f_y0 + ((float)s.j + o[1]) * G.f_dY;
         sincosf(phi, &g.sphi, &g.cphi);
-        g.r = (float)G.radius + ((float)s.k + o[2]) * (float)G.dz;
+        g.r = G.f_radius + ((float)s.k + o[2]) * G.f_dz;
         g.ir = __frcp_rn(g.r);
         const float ic = __frcp_rn(g.cphi);
         g.hX = g.r * g.cphi;
@@ -149,12 +214,12 @@ __device__ __forceinline__ void geo32(const Grid& G, const S32& s, const float o
 __device__ __forceinline__ void coriolis32(const Grid& G, const Geo32& g, float& f2, float& df2)
 {
     if (G.geometry == 1) {
-        const float om = (float)G.omega;
+        const float om = G.f_omega;
         const float f = 2.0f * om * g.sphi;
         f2 = f * f;
         df2 = 8.0f * om * om * g.sphi * g.cphi;
     } else {
-        f2 = (float)(G.f0 * G.f0);
+        f2 = G.f_f0 * G.f_f0;
         df2 = 0.0f;
     }
 }
@@ -213,7 +278,7 @@ __device__ __forceinline__ void rhs32(const Grid& G, const Node32* __restrict__ 
         F[5] = -Gq[2];
     }
     // face group velocities -> coordinate rates -> cell units
-    const float scale[3] = {g.ihX * (float)G.inv_dX, g.ir * (float)G.inv_dY, (float)G.inv_dz};
+    const float scale[3] = {g.ihX * G.f_inv_dX, g.ir * G.f_inv_dY, G.f_inv_dz};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         float vel[2];
@@ -301,10 +366,10 @@ __device__ __forceinline__ int split_code32(const Grid& G, const Params& P, cons
     int code = 0;
     if (s.e[2] > fmaxf((float)(P.alpha_s * G.dz), (float)P.min_split_dz)) code |= 1;
     float xlen, ylen, thr, area, athr;
-    const float a = (float)P.alpha_s, dX = (float)G.dX, dY = (float)G.dY;
+    const float a = P.f_alpha_s, dX = G.f_dX, dY = G.f_dY;
     if (G.geometry == 1) {
-        const float cj = (float)G.row_cos[s.j];
-        const float cp = cosf((float)G.y0 + ((float)s.j + s.o[1]) * dY);
+        const float cj = G.row_cos32[s.j];
+        const float cp = cosf(G.f_y0 + ((float)s.j + s.o[1]) * dY);
         xlen = cp * s.e[0];
         ylen = s.e[1];
         thr = a * sqrtf(cj * dX * dY);
@@ -327,7 +392,7 @@ __device__ __forceinline__ int make_child32(const Grid& G, const S32& p, int cod
     s = p;
     if (!code) return 0;
     const int nv = (code & 1) ? 2 : 1;
-    const float inv[3] = {(float)G.inv_dX, (float)G.inv_dY, (float)G.inv_dz};
+    const float inv[3] = {G.f_inv_dX, G.f_inv_dY, G.f_inv_dz};
     if (code & 1) {
         const bool plus = (c % nv) == 1;
         s.o[2] += (plus ? 0.25f : -0.25f) * s.e[2] * inv[2];

@@ -1,5 +1,6 @@
 // gwam_io.cu -- copies of device state into caller layouts (results, diagnostics, tests).
 #include "gwam_common.cuh"
+#include "gwam_fp32.cuh"
 
 namespace gwam {
 
@@ -69,7 +70,35 @@ __global__ void k_selftest_math(const double* __restrict__ x, int64_t n, double*
     }
 }
 
+__global__ void k_selftest_widen(const float* __restrict__ x, int64_t n, double* __restrict__ w,
+                                 double* __restrict__ prod)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        w[i] = widen(x[i]);
+        if (prod) {
+            // the double-float product chain of N Px Py Pz on (x_i, x_{i+1}, x_{i+2}, x_{i+3})
+            S32 s{};
+            s.n = x[i];
+            s.p[0] = x[(i + 1) % n];
+            s.p[1] = x[(i + 2) % n];
+            s.p[2] = x[(i + 3) % n];
+            prod[i] = df_to_double(action_df(s));
+        }
+    }
+}
+
 }  // namespace gwam
+
+extern "C" int gwam_selftest_widen(const float* x, int64_t n, double* widened, double* action, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !widened))) return GWAM_EINVAL;
+    if (n == 0) return GWAM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>((n + gwam::kThreads - 1) / gwam::kThreads, 4096);
+    gwam::k_selftest_widen<<<blocks, gwam::kThreads, 0, s>>>(x, n, widened, action);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GWAM_ECUDA;
+    return GWAM_OK;
+}
 
 extern "C" int gwam_selftest_math(const double* x, int64_t n, double* rcp_out, double* rsqrt_out, void* stream)
 {

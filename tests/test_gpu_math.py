@@ -29,3 +29,42 @@ def test_rcp_and_rsqrt_within_two_ulp():
         ulp = np.abs(got - ref) / np.spacing(np.abs(ref))
         assert np.all(np.isfinite(got))
         assert ulp.max() <= 2.0, ulp.max()
+
+
+def test_integer_widening_and_double_float_action():
+    """float -> double by integer re-biasing equals the hardware conversion bit for bit; the
+    double-float product of four floats is within 2^-46 of the exact (FP64-evaluated) product."""
+    import torch
+    from paper_2309_11257_gb300 import build
+    build.build()
+    from paper_2309_11257_gb300 import gwam
+    rng = np.random.default_rng(2)
+    special = np.array([0.0, -0.0, 1.0, -1.0, np.inf, -np.inf, np.nan, 1e-45, -1e-45, 1.17549435e-38,
+                        1.1754942e-38, 3.4028235e38, -3.4028235e38, 5.877472e-39, 2.0 ** -149, 2.0 ** -126],
+                       dtype=np.float32)
+    bits = rng.integers(0, 2 ** 32, size=200_000, dtype=np.uint64).astype(np.uint32).view(np.float32)
+    mags = (10.0 ** rng.uniform(-30, 30, 100_000) * rng.choice([-1, 1], 100_000)).astype(np.float32)
+    x = np.concatenate([special, bits, mags])
+    xd = torch.from_numpy(x).cuda()
+    w = torch.empty(len(x), dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    assert gwam.lib().gwam_selftest_widen(C.c_void_p(xd.data_ptr()), len(x), C.c_void_p(w.data_ptr()), None,
+                                          C.c_void_p(s.cuda_stream)) == 0
+    ref = xd.double().cpu().numpy().view(np.uint64)
+    got = w.cpu().numpy().view(np.uint64)
+    nan = np.isnan(x)
+    np.testing.assert_array_equal(got[~nan], ref[~nan])
+    assert np.isnan(w.cpu().numpy()[nan]).all()
+    # double-float action on positive, moderate values (the ray-volume range)
+    y = (10.0 ** rng.uniform(-7, 7, 50_000)).astype(np.float32)   # products stay normal in FP32
+    yd = torch.from_numpy(y).cuda()
+    w2 = torch.empty(len(y), dtype=torch.float64, device="cuda")
+    a = torch.empty_like(w2)
+    assert gwam.lib().gwam_selftest_widen(C.c_void_p(yd.data_ptr()), len(y), C.c_void_p(w2.data_ptr()),
+                                          C.c_void_p(a.data_ptr()), C.c_void_p(s.cuda_stream)) == 0
+    yy = y.astype(np.float64)
+    n = len(y)
+    idx = np.arange(n)
+    exact = yy * yy[(idx + 1) % n] * yy[(idx + 2) % n] * yy[(idx + 3) % n]
+    rel = np.abs(a.cpu().numpy() - exact) / exact
+    assert rel.max() <= 2.0 ** -46, rel.max()
