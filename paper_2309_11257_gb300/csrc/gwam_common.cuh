@@ -60,6 +60,21 @@ __device__ __forceinline__ bool warp_segment_reduce(int key, double (&v)[NV])
     return (lane == 31) || (next != key);
 }
 
+// True when this lane's run of equal keys touches neither lane 0 nor lane 31: with the ray array
+// sorted by key and a warp holding 32 consecutive entries, no other warp holds that key, so the
+// run's sum may be stored instead of added atomically (fewer L2 atomics, and deterministic).
+__device__ __forceinline__ bool warp_run_interior(int key)
+{
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    const unsigned tails = __ballot_sync(0xffffffffu, lane == 31 || next != key);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    const int end = __ffs(tails & (0xffffffffu << lane)) - 1;
+    return start > 0 && end < 31;
+}
+
 __device__ __forceinline__ void set_status(Ctl* ctl, int code)
 {
     atomicCAS(&ctl->status, 0, code);

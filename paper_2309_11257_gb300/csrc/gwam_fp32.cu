@@ -186,6 +186,34 @@ __global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, 
         out[i] = (double)in[i];
 }
 
+// Saturation (Sec. 3c, Eq. turbulent-diffusivity) of the precision form: per carrier cell the
+// sums P_c = sum P_j alpha_j and Q_c = sum P_j alpha_j K_j^2 in FP64 (segment head over the
+// cell's run of the canonical array), the threshold difference P_c - rho/2 in FP64, then
+// kappa = (P_c - rho/2) / (2 dt Q_c) in FP32 for every ray of the cell.
+__global__ void k_sat_kappa32(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+                              const int* __restrict__ raycell, const double* __restrict__ rho,
+                              const double* __restrict__ pj, const float* __restrict__ k2, float dt,
+                              float* __restrict__ kappa)
+{
+    if (ctl->status) return;
+    const int n = off2[ncell_all];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int c = raycell[p];
+        if (p > 0 && raycell[p - 1] == c) continue;
+        const int b = off2[c + 1];
+        double Pc = 0.0, Q = 0.0;
+        for (int q = p; q < b; ++q) {
+            const double v = pj[q];
+            Pc += v;
+            Q = fma(v, widen(k2[q]), Q);
+        }
+        const double d = fma(-0.5, rho[c], Pc);
+        float kap = 0.0f;
+        if (d > 0.0 && Q > 0.0) kap = __fdiv_rn(__double2float_rn(d), 2.0f * dt * __double2float_rn(Q));
+        for (int q = p; q < b; ++q) kappa[q] = kap;
+    }
+}
+
 static void narrow_fields(Context& c, int f0, int f1)
 {
     NarrowSet ns{};
@@ -399,7 +427,7 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
                                                               const int* __restrict__ sorted_src,
                                                               const int* __restrict__ info,
                                                               const int* __restrict__ newid,
-                                                              double* __restrict__ pj, double* __restrict__ k2,
+                                                              double* __restrict__ pj, float* __restrict__ k2,
                                                               int* __restrict__ raycell)
 {
     if (ctl->status) return;
@@ -425,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
             // P_j alpha_j = m^2 k_h^2 / (w K^2) N Px Py Pz / V_c in double-float, one FP64 add at the end
             const DF av = df_mul(action_df(ch), G.ivol32[ch.j * G.nz + ch.k]);
             pj[p] = df_to_double(df_mul(av, in.m2 * in.kh2 * in.iw * in.iK2));
-            k2[p] = widen(in.K2);
+            k2[p] = in.K2;
         }
     }
 }
@@ -433,8 +461,8 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
 // Saturation N update and flux projection; per-ray terms in FP32, accumulated in FP64.
 __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32SoA B, const Node32* __restrict__ bg,
                                                           const Ctl* ctl, const int* __restrict__ off2,
-                                                          const double* __restrict__ kappa,
-                                                          const double* __restrict__ k2, double dt,
+                                                          const float* __restrict__ kappa,
+                                                          const float* __restrict__ k2, double dt,
                                                           double* __restrict__ fz_l, double* __restrict__ fz_p,
                                                           double* __restrict__ f_ll, double* __restrict__ f_lp,
                                                           double* __restrict__ f_pl, double* __restrict__ f_pp,
@@ -460,10 +488,9 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
             S32 s;
             load32(G, B, p, s);
             if (P.saturation) {
-                const double kapd = kappa[p];
-                if (__double_as_longlong(kapd) > 0) {   // kappa >= 0, so positive bits <=> kappa > 0
-                    const float kap = __double2float_rn(kapd), kk2 = __double2float_rn(k2[p]);
-                    const float fac = fmaxf(0.0f, 1.0f - 2.0f * kap * kk2 * dtf);
+                const float kap = kappa[p];
+                if (kap > 0.0f) {
+                    const float fac = fmaxf(0.0f, 1.0f - 2.0f * kap * k2[p] * dtf);
                     const float nold = s.n;
                     s.n = nold * fac;
                     w_sat = df_add(w_sat, df_mul(df_mul(df_mul(df_diff(nold, s.n), s.p[0]), s.p[1]), s.p[2]));
@@ -516,14 +543,26 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
             const int kk1 = min(G.nz - 1, (int)ceilf(hi * G.f_inv_dz + 0.5f));
             nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
         }
+        const bool own = warp_run_interior(key);
         if (warp_segment_reduce(key, hv) && key >= 0) {
-            atomicAdd(&f_ll[key], hv[0]);
-            atomicAdd(&f_lp[key], hv[1]);
-            atomicAdd(&f_pl[key], hv[2]);
-            atomicAdd(&f_pp[key], hv[3]);
-            atomicAdd(&e_l[key], hv[4]);
-            atomicAdd(&e_p[key], hv[5]);
-            atomicAdd(&wad[key], hv[6]);
+            if (own) {
+                // the whole cell is this run: store its sum (fields were zeroed before the launch)
+                f_ll[key] = hv[0];
+                f_lp[key] = hv[1];
+                f_pl[key] = hv[2];
+                f_pp[key] = hv[3];
+                e_l[key] = hv[4];
+                e_p[key] = hv[5];
+                wad[key] = hv[6];
+            } else {
+                atomicAdd(&f_ll[key], hv[0]);
+                atomicAdd(&f_lp[key], hv[1]);
+                atomicAdd(&f_pl[key], hv[2]);
+                atomicAdd(&f_pp[key], hv[3]);
+                atomicAdd(&e_l[key], hv[4]);
+                atomicAdd(&e_p[key], hv[5]);
+                atomicAdd(&wad[key], hv[6]);
+            }
         }
         int maxk = nkk;
 #pragma unroll
@@ -630,15 +669,18 @@ void run_step32(Context& c, double dt, double* du, double* dv)
     k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
     tune_mark(c, 2);
     k_materialize32<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A32, c.B32, c.bg32, c.ctl, off2, c.sorted_src, c.info,
-                                                     c.newid, c.pj, c.k2, c.raycell);
+                                                     c.newid, c.pj, reinterpret_cast<float*>(c.k2), c.raycell);
     tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation)
-        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa);
+        k_sat_kappa32<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj,
+                                              reinterpret_cast<const float*>(c.k2), (float)dt,
+                                              reinterpret_cast<float*>(c.kappa));
     prof_mark(c, 3);
     for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);
-    k_project32<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B32, c.bg32, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL],
+    k_project32<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B32, c.bg32, c.ctl, off2, reinterpret_cast<const float*>(c.kappa),
+                                                 reinterpret_cast<const float*>(c.k2), dt, c.field[F_ZL],
                                                  c.field[F_ZP], c.field[F_LL], c.field[F_LP], c.field[F_PL],
                                                  c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD],
                                                  c.partials, c.max_blocks);

@@ -416,7 +416,8 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
 // kappa = max(0, (P - rho/2) / (2 dt sum_j P_j K_j^2)) of every carrier cell (Eq. turbulent-diffusivity).
 // Rays are in cell order, so each cell is a contiguous segment: the first ray of a segment sums it
 // in order (deterministic) and hands kappa to all of its rays.  Iterating rays, not cells, skips the
-// many empty cells.
+// many empty cells.  (A warp-parallel segmented sum was measured slower on GB300: it spends about
+// five FP64 additions per lane where this loop spends two per ray.)
 __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
                             const int* __restrict__ raycell, const double* __restrict__ rho,
                             const double* __restrict__ pj, const double* __restrict__ k2, double dt,
@@ -433,7 +434,9 @@ __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int nc
             Pc += pj[q];
             Q += pj[q] * k2[q];
         }
-        const double kap = Q > 0.0 ? fmax(0.0, (Pc - 0.5 * rho[c]) / (2.0 * dt * Q)) : 0.0;
+        // Newton-refined reciprocal instead of an IEEE division (<= 2 ulp; FP64 division is a long
+        // instruction sequence at GB300's FP64 rate)
+        const double kap = Q > 0.0 ? fmax(0.0, (Pc - 0.5 * rho[c]) * rcp_nr(2.0 * dt * Q)) : 0.0;
         for (int q = p; q < b; ++q) kappa[q] = kap;
     }
 }
@@ -525,14 +528,26 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
             nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
         }
         // centre fields: warp-segmented reduction over runs of equal cells, one atomic per run
+        const bool own = warp_run_interior(key);
         if (warp_segment_reduce(key, hv) && key >= 0) {
-            atomicAdd(&f_ll[key], hv[0]);
-            atomicAdd(&f_lp[key], hv[1]);
-            atomicAdd(&f_pl[key], hv[2]);
-            atomicAdd(&f_pp[key], hv[3]);
-            atomicAdd(&e_l[key], hv[4]);
-            atomicAdd(&e_p[key], hv[5]);
-            atomicAdd(&wad[key], hv[6]);
+            if (own) {
+                // the whole cell is this run: store its sum (fields were zeroed before the launch)
+                f_ll[key] = hv[0];
+                f_lp[key] = hv[1];
+                f_pl[key] = hv[2];
+                f_pp[key] = hv[3];
+                e_l[key] = hv[4];
+                e_p[key] = hv[5];
+                wad[key] = hv[6];
+            } else {
+                atomicAdd(&f_ll[key], hv[0]);
+                atomicAdd(&f_lp[key], hv[1]);
+                atomicAdd(&f_pl[key], hv[2]);
+                atomicAdd(&f_pp[key], hv[3]);
+                atomicAdd(&e_l[key], hv[4]);
+                atomicAdd(&e_p[key], hv[5]);
+                atomicAdd(&wad[key], hv[6]);
+            }
         }
         // interface fields
         int maxk = nkk;
