@@ -239,6 +239,9 @@ int gwam_selftest_math(const double *x, int64_t n, double *rcp_out, double *rsqr
  * mod n) formed in double-float arithmetic on the FP32 pipes and returned as a double.  Device
  * pointers; synchronises `stream`. */
 int gwam_selftest_widen(const float *x, int64_t n, double *widened, double *action, void *stream);
+/* Self-test of the integer double -> float narrowing (round to nearest even): out[i] must equal the
+ * hardware conversion bit for bit (subnormal results, overflow to infinity, NaN classes included). */
+int gwam_selftest_narrow(const double *x, int64_t n, float *out, void *stream);
 
 /* Self-test of the surrogate's tensor-core GEMM (tcgen05 + TMA, sm_103a): C = act(A . B^T + bias)
  * with A [M][K] and B [N][K] row-major BF16 device arrays (K contiguous, K a multiple of 64, base

@@ -36,7 +36,7 @@ __global__ void k_narrow(NarrowSet s)
     const double* __restrict__ in = s.in[f];
     float* __restrict__ out = s.out[f];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = __double2float_rn(in[i]);
+        out[i] = narrow(in[i]);
 }
 
 void convert_background32(Context& c, int member)
@@ -86,13 +86,29 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     const int64_t r0 = (base + (int64_t)jm * G.nx) * nlev, r1 = (base + (int64_t)j * G.nx) * nlev,
                   r2 = (base + (int64_t)jp * G.nx) * nlev;
     const int64_t cm = (int64_t)im * nlev, c0 = (int64_t)i * nlev, cp = (int64_t)ip * nlev;
+    const int tx = threadIdx.x;
     const float* __restrict__ F = fs.in[f];
-    float* __restrict__ O = fs.out[f];
-    for (int lev = threadIdx.x; lev < nlev; lev += 32) {
-        const float a = F[r0 + cm + lev] + 2.0f * F[r0 + c0 + lev] + F[r0 + cp + lev];
-        const float b = F[r1 + cm + lev] + 2.0f * F[r1 + c0 + lev] + F[r1 + cp + lev];
-        const float cc = F[r2 + cm + lev] + 2.0f * F[r2 + c0 + lev] + F[r2 + cp + lev];
-        O[r1 + c0 + lev] = (a + 2.0f * b + cc) * 0.0625f;
+    const float* p00 = F + r0 + cm + tx, *p01 = F + r0 + c0 + tx, *p02 = F + r0 + cp + tx;
+    const float* p10 = F + r1 + cm + tx, *p11 = F + r1 + c0 + tx, *p12 = F + r1 + cp + tx;
+    const float* p20 = F + r2 + cm + tx, *p21 = F + r2 + c0 + tx, *p22 = F + r2 + cp + tx;
+    float* __restrict__ O = fs.out[f] + r1 + c0 + tx;
+    // level groups of 32 at constant offsets from nine row/column pointers (no index arithmetic
+    // per load: the kernel was issue-bound on 64-bit address computation)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        if (tx + 32 * g < nlev) {
+            const int o = 32 * g;
+            const float a = p00[o] + 2.0f * p01[o] + p02[o];
+            const float b = p10[o] + 2.0f * p11[o] + p12[o];
+            const float cc = p20[o] + 2.0f * p21[o] + p22[o];
+            O[o] = (a + 2.0f * b + cc) * 0.0625f;
+        }
+    }
+    for (int o = 128; tx + o < nlev; o += 32) {
+        const float a = p00[o] + 2.0f * p01[o] + p02[o];
+        const float b = p10[o] + 2.0f * p11[o] + p12[o];
+        const float cc = p20[o] + 2.0f * p21[o] + p22[o];
+        O[o] = (a + 2.0f * b + cc) * 0.0625f;
     }
 }
 
@@ -481,7 +497,7 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
         const int p = p0 + threadIdx.x;
         const bool act = p < n;
         int key = -1;
-        double hv[7] = {0, 0, 0, 0, 0, 0, 0};
+        DF hv[7] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
         float zl = 0.0f, zp = 0.0f, wh = 0.0f, lo = 0.0f, hi = 0.0f;
         int col = 0, kk0 = 1, nkk = 0;
         if (act) {
@@ -531,8 +547,8 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
                 zl = chr * k; zp = chr * l;
                 el = 0.0f; ep = 0.0f;
             }
-            hv[0] = widen(aw * t_ll); hv[1] = widen(aw * t_lp); hv[2] = widen(aw * t_pl);
-            hv[3] = widen(aw * t_pp); hv[4] = widen(aw * el); hv[5] = widen(aw * ep); hv[6] = widen(aw);
+            hv[0].hi = aw * t_ll; hv[1].hi = aw * t_lp; hv[2].hi = aw * t_pl;
+            hv[3].hi = aw * t_pp; hv[4].hi = aw * el; hv[5].hi = aw * ep; hv[6].hi = aw;
             zl *= A;
             zp *= A;
             wh = in.g.cphi * s.e[0] * s.e[1] * G.whf32[s.j];
@@ -544,31 +560,21 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
             nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
         }
         const bool own = warp_run_interior(key);
-        if (warp_segment_reduce(key, hv) && key >= 0) {
-            if (own) {
+        if (warp_segment_reduce_df(key, hv) && key >= 0) {
+            double* const dst[7] = {f_ll, f_lp, f_pl, f_pp, e_l, e_p, wad};
+#pragma unroll
+            for (int q = 0; q < 7; ++q) {
+                const double v = df_to_double(hv[q]);
                 // the whole cell is this run: store its sum (fields were zeroed before the launch)
-                f_ll[key] = hv[0];
-                f_lp[key] = hv[1];
-                f_pl[key] = hv[2];
-                f_pp[key] = hv[3];
-                e_l[key] = hv[4];
-                e_p[key] = hv[5];
-                wad[key] = hv[6];
-            } else {
-                atomicAdd(&f_ll[key], hv[0]);
-                atomicAdd(&f_lp[key], hv[1]);
-                atomicAdd(&f_pl[key], hv[2]);
-                atomicAdd(&f_pp[key], hv[3]);
-                atomicAdd(&e_l[key], hv[4]);
-                atomicAdd(&e_p[key], hv[5]);
-                atomicAdd(&wad[key], hv[6]);
+                if (own) dst[q][key] = v;
+                else atomicAdd(&dst[q][key], v);
             }
         }
         int maxk = nkk;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) maxk = max(maxk, __shfl_xor_sync(0xffffffffu, maxk, o));
         for (int o = 0; o < maxk; ++o) {
-            double zv[2] = {0.0, 0.0};
+            DF zv[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
             int zkey = -1;
             if (o < nkk) {
                 const int kk = kk0 + o;
@@ -576,14 +582,14 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
                 const float ov = fminf(hi, shi) - fmaxf(lo, slo);
                 if (ov > 0.0f) {
                     const float w = wh * ov * G.f_inv_dz;
-                    zv[0] = widen(w * zl);
-                    zv[1] = widen(w * zp);
+                    zv[0].hi = w * zl;
+                    zv[1].hi = w * zp;
                     zkey = col * (G.nz + 1) + kk;
                 }
             }
-            if (warp_segment_reduce(zkey, zv) && zkey >= 0) {
-                atomicAdd(&fz_l[zkey], zv[0]);
-                atomicAdd(&fz_p[zkey], zv[1]);
+            if (warp_segment_reduce_df(zkey, zv) && zkey >= 0) {
+                atomicAdd(&fz_l[zkey], df_to_double(zv[0]));
+                atomicAdd(&fz_p[zkey], df_to_double(zv[1]));
             }
         }
     }

@@ -87,7 +87,24 @@ __global__ void k_selftest_widen(const float* __restrict__ x, int64_t n, double*
     }
 }
 
+__global__ void k_selftest_narrow(const double* __restrict__ x, int64_t n, float* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = narrow(x[i]);
+}
+
 }  // namespace gwam
+
+extern "C" int gwam_selftest_narrow(const double* x, int64_t n, float* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) return GWAM_EINVAL;
+    if (n == 0) return GWAM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>((n + gwam::kThreads - 1) / gwam::kThreads, 4096);
+    gwam::k_selftest_narrow<<<blocks, gwam::kThreads, 0, s>>>(x, n, out);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GWAM_ECUDA;
+    return GWAM_OK;
+}
 
 extern "C" int gwam_selftest_widen(const float* x, int64_t n, double* widened, double* action, void* stream)
 {

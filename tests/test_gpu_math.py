@@ -68,3 +68,35 @@ def test_integer_widening_and_double_float_action():
     exact = yy * yy[(idx + 1) % n] * yy[(idx + 2) % n] * yy[(idx + 3) % n]
     rel = np.abs(a.cpu().numpy() - exact) / exact
     assert rel.max() <= 2.0 ** -46, rel.max()
+
+
+def test_integer_narrowing_matches_the_hardware_conversion():
+    """double -> float by integer rounding (nearest even) equals the hardware conversion bit for
+    bit: random bit patterns, the float range edges, subnormal results, ties, overflow."""
+    import torch
+    from paper_2309_11257_gb300 import build
+    build.build()
+    from paper_2309_11257_gb300 import gwam
+    rng = np.random.default_rng(3)
+    bits = rng.integers(0, 2 ** 63, size=300_000, dtype=np.uint64) | \
+        (rng.integers(0, 2, size=300_000, dtype=np.uint64) << np.uint64(63))
+    x = bits.view(np.float64)
+    mags = 10.0 ** rng.uniform(-50, 45, 200_000) * rng.choice([-1, 1], 200_000)
+    f32 = np.finfo(np.float32)
+    special = np.array([0.0, -0.0, 1.0, np.inf, -np.inf, np.nan, float(f32.max), float(f32.max) * (1 + 2 ** -25),
+                        float(f32.max) * (1 + 2 ** -23), float(f32.tiny), float(f32.tiny) / 3, 2.0 ** -149,
+                        2.0 ** -150, 2.0 ** -150 * 1.0000001, 3 * 2.0 ** -151, 1.0 + 2 ** -24, 1.0 + 3 * 2 ** -24,
+                        5e-324, -5e-324, 1e-320])
+    # exact ties at every float exponent: 1 + 2^-24 scaled
+    ties = (1.0 + 2.0 ** -24) * 2.0 ** rng.integers(-149, 127, 20_000).astype(np.float64)
+    allx = np.concatenate([special, x, mags, ties])
+    xd = torch.from_numpy(allx).cuda()
+    out = torch.empty(len(allx), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    assert gwam.lib().gwam_selftest_narrow(C.c_void_p(xd.data_ptr()), len(allx), C.c_void_p(out.data_ptr()),
+                                           C.c_void_p(s.cuda_stream)) == 0
+    ref = xd.float().cpu().numpy()
+    got = out.cpu().numpy()
+    nan = np.isnan(allx)
+    np.testing.assert_array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
+    assert np.isnan(got[nan]).all()
