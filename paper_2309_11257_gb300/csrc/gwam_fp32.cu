@@ -62,18 +62,31 @@ struct FieldSet32 {
     float* out[NFIELD];
 };
 
-// separable 1-2-1 x 1-2-1 smoothing (periodic in lambda, edge row reused at the poles), as
-// k_smooth_fields: block (32 levels, 8 columns) of one row, blockIdx.z = field
-__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, int f0)
+// separable 1-2-1 x 1-2-1 smoothing (periodic in lambda, edge row reused at the poles).  A warp
+// owns 32 consecutive levels of one row over a run of kSpan columns and slides a 3 x 3 window along
+// the row: each new column costs 3 loads (rows j-1, j, j+1) instead of 9, the column sums of the
+// previous two columns are kept in registers.  Warp item = (field, member, row, level group, span).
+constexpr int kSpan = 64;
+__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, int f0, int nf)
 {
-    const int f = f0 + blockIdx.z;
+    const int lane = threadIdx.x & 31;
+    const int nlg = (G.nz + 1 + 31) / 32;                   // level groups (interface fields have nz + 1)
+    const int nsp = (G.nx + kSpan - 1) / kSpan;
+    const long long per_field = (long long)G.members * G.ny * nlg * nsp;
+    const long long items = per_field * nf;
+    const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (w >= items) return;
+    const int f = f0 + (int)(w / per_field);
+    long long r = w % per_field;
+    const int sp = (int)(r % nsp);
+    r /= nsp;
+    const int lg = (int)(r % nlg);
+    r /= nlg;
+    const int j = (int)(r % G.ny);
+    const int mem = (int)(r / G.ny);
     const int nlev = f <= F_ZP ? G.nz + 1 : G.nz;
-    const int ntx = (G.nx + 7) / 8;
-    const int mem = blockIdx.y;
-    const int j = blockIdx.x / ntx;
-    const int i = (blockIdx.x % ntx) * 8 + threadIdx.y;
-    if (i >= G.nx) return;
-    const int im = i == 0 ? G.nx - 1 : i - 1, ip = i + 1 == G.nx ? 0 : i + 1;
+    const int lev = lg * 32 + lane;
+    if (lg * 32 >= nlev) return;
     int jm = j - 1, jp = j + 1;
     if (G.geometry == 1) {
         jm = jm < 0 ? 0 : jm;
@@ -82,33 +95,26 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
         jm = jm < 0 ? G.ny - 1 : jm;
         jp = jp >= G.ny ? 0 : jp;
     }
+    const bool live = lev < nlev;
     const int64_t base = (int64_t)mem * G.ncol;
-    const int64_t r0 = (base + (int64_t)jm * G.nx) * nlev, r1 = (base + (int64_t)j * G.nx) * nlev,
-                  r2 = (base + (int64_t)jp * G.nx) * nlev;
-    const int64_t cm = (int64_t)im * nlev, c0 = (int64_t)i * nlev, cp = (int64_t)ip * nlev;
-    const int tx = threadIdx.x;
     const float* __restrict__ F = fs.in[f];
-    const float* p00 = F + r0 + cm + tx, *p01 = F + r0 + c0 + tx, *p02 = F + r0 + cp + tx;
-    const float* p10 = F + r1 + cm + tx, *p11 = F + r1 + c0 + tx, *p12 = F + r1 + cp + tx;
-    const float* p20 = F + r2 + cm + tx, *p21 = F + r2 + c0 + tx, *p22 = F + r2 + cp + tx;
-    float* __restrict__ O = fs.out[f] + r1 + c0 + tx;
-    // level groups of 32 at constant offsets from nine row/column pointers (no index arithmetic
-    // per load: the kernel was issue-bound on 64-bit address computation)
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        if (tx + 32 * g < nlev) {
-            const int o = 32 * g;
-            const float a = p00[o] + 2.0f * p01[o] + p02[o];
-            const float b = p10[o] + 2.0f * p11[o] + p12[o];
-            const float cc = p20[o] + 2.0f * p21[o] + p22[o];
-            O[o] = (a + 2.0f * b + cc) * 0.0625f;
-        }
-    }
-    for (int o = 128; tx + o < nlev; o += 32) {
-        const float a = p00[o] + 2.0f * p01[o] + p02[o];
-        const float b = p10[o] + 2.0f * p11[o] + p12[o];
-        const float cc = p20[o] + 2.0f * p21[o] + p22[o];
-        O[o] = (a + 2.0f * b + cc) * 0.0625f;
+    const float* R0 = F + (base + (int64_t)jm * G.nx) * nlev + lev;
+    const float* R1 = F + (base + (int64_t)j * G.nx) * nlev + lev;
+    const float* R2 = F + (base + (int64_t)jp * G.nx) * nlev + lev;
+    float* O = fs.out[f] + (base + (int64_t)j * G.nx) * nlev + lev;
+    const int i0 = sp * kSpan, i1 = min(G.nx, i0 + kSpan);
+    // vertical 1-2-1 column sums at columns i0 - 1 and i0
+    auto colsum = [&](int i) -> float {
+        const int64_t o = (int64_t)i * nlev;
+        return live ? R0[o] + 2.0f * R1[o] + R2[o] : 0.0f;
+    };
+    float cm = colsum(i0 == 0 ? G.nx - 1 : i0 - 1);
+    float c0 = colsum(i0);
+    for (int i = i0; i < i1; ++i) {
+        const float cp = colsum(i + 1 == G.nx ? 0 : i + 1);
+        if (live) O[(int64_t)i * nlev] = (cm + 2.0f * c0 + cp) * 0.0625f;
+        cm = c0;
+        c0 = cp;
     }
 }
 
@@ -251,8 +257,9 @@ static void smooth32(Context& c, int f0, int f1)
         fs.in[f] = c.nar32[f];
         fs.out[f] = c.sm32[f];
     }
-    const dim3 grid((unsigned)(((c.G.nx + 7) / 8) * c.G.ny), (unsigned)c.G.members, (unsigned)(f1 - f0));
-    k_smooth_fields32<<<grid, dim3(32, 8), 0, c.stream>>>(c.G, fs, f0);
+    const long long warps = (long long)(f1 - f0) * c.G.members * c.G.ny * ((c.G.nz + 1 + 31) / 32) *
+                            ((c.G.nx + kSpan - 1) / kSpan);
+    k_smooth_fields32<<<(unsigned)((warps + 7) / 8), 256, 0, c.stream>>>(c.G, fs, f0, f1 - f0);
 }
 
 void smooth_field32(Context& c, int f)

@@ -74,7 +74,7 @@ __device__ __forceinline__ double widen(float x)
 // a float subnormal) and rounded on the dropped bits; a carry out of the significand moves into
 // the exponent, an exponent beyond the float range gives infinity, infinities and NaNs keep their
 // class.
-__device__ __forceinline__ float narrow(double x)
+__device__ __forceinline__ float narrow_general(double x)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
@@ -93,6 +93,21 @@ __device__ __forceinline__ float narrow(double x)
     uint32_t r = E > 0 ? ((uint32_t)E << 23) + (uint32_t)(q - (1ull << 23)) : (uint32_t)q;
     if (r > 0x7F800000u) r = 0x7F800000u;
     return __uint_as_float(sign | r);
+}
+
+// Fast path of narrow for the usual case -- the result is a normal float or rounds up to infinity
+// -- with 32-bit operations on the two words of the double; everything else takes narrow_general.
+__device__ __forceinline__ float narrow(double x)
+{
+    const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+    const uint32_t e = (hw >> 20) & 0x7FFu;
+    if (e - 897u < 254u) {                      // float exponent 1 .. 254
+        uint32_t r = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
+        const uint32_t rem = lw & 0x1FFFFFFFu;  // the 29 dropped bits
+        r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+        return __uint_as_float((hw & 0x80000000u) | r);
+    }
+    return narrow_general(x);
 }
 
 // Double-float values hi + lo (|lo| <= ulp(hi) / 2) on the FP32 pipes, about 48 significant bits:
