@@ -32,7 +32,8 @@ static void dalloc(Context& c, T*& p, size_t count)
 
 static void free_all(Context& c)
 {
-    void* ptrs[] = {c.bg, c.bg32, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.bg_scratch,
+    void* ptrs[] = {c.bg, c.bg32, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.tables_df,
+                    c.bg_scratch,
                     c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
                     c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
                     c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
@@ -217,6 +218,13 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
                     t32[2 * (size_t)G.ny + (size_t)j * G.nz + k] = (float)iv;
                 }
             }
+            std::vector<float2> tdf(tab.size());
+            for (size_t q = 0; q < tab.size(); ++q) {
+                const float hi = (float)tab[q];
+                tdf[q] = make_float2(hi, (float)(tab[q] - (double)hi));
+            }
+            dalloc(c, c.tables_df, tdf.size());
+            GWAM_CUDA(cudaMemcpy(c.tables_df, tdf.data(), sizeof(float2) * tdf.size(), cudaMemcpyHostToDevice));
             dalloc(c, c.tables32, t32.size());
             GWAM_CUDA(cudaMemcpy(c.tables32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
             G.row_cos32 = c.tables32;

@@ -60,6 +60,7 @@ struct Context {
     double* rho_inv = nullptr;      // 1 / rho per node
     double* tables = nullptr;       // row_cos[ny], row_inv_cos[ny], lev_inv_r[nz]
     float* tables32 = nullptr;      // row_cos32[ny], whf32[ny], ivol32[ny * nz]
+    float2* tables_df = nullptr;    // row_cos, row_inv_cos [ny], lev_inv_r [nz] as double-float pairs
     double* bg_scratch = nullptr;   // staging of caller fields ([nz][ny][nx], 4 fields)
 
     // ray volumes: A holds the canonical array between steps, B is the re-binned output
@@ -163,6 +164,7 @@ void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();
 void smooth_field(Context& c, int f);
 void smooth_field32(Context& c, int f);
+void grid_phase_df(Context& c, double* du, double* dv, int mask);
 inline void swap_rays(Context& c) { c.swap_rays_(); }
 void run_step32(Context& c, double dt, double* du, double* dv);
 void convert_background32(Context& c, int member);

@@ -35,8 +35,17 @@ __global__ void k_narrow(NarrowSet s)
     const int64_t n = s.n[f];
     const double* __restrict__ in = s.in[f];
     float* __restrict__ out = s.out[f];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = narrow(in[i]);
+    // four elements per thread and pass, all loads issued first (bytes in flight)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+        const double a = in[i], b = in[i + stride], c = in[i + 2 * stride], d = in[i + 3 * stride];
+        out[i] = narrow(a);
+        out[i + stride] = narrow(b);
+        out[i + 2 * stride] = narrow(c);
+        out[i + 3 * stride] = narrow(d);
+    }
+    for (; i < n; i += stride) out[i] = narrow(in[i]);
 }
 
 void convert_background32(Context& c, int member)
@@ -110,7 +119,25 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     };
     float cm = colsum(i0 == 0 ? G.nx - 1 : i0 - 1);
     float c0 = colsum(i0);
-    for (int i = i0; i < i1; ++i) {
+    int i = i0;
+    // four columns per pass with their twelve loads issued together
+    for (; i + 4 <= i1; i += 4) {
+        float c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ii = i + 1 + q;
+            c[q] = colsum(ii >= G.nx ? ii - G.nx : ii);
+        }
+        if (live) {
+            O[(int64_t)i * nlev] = (cm + 2.0f * c0 + c[0]) * 0.0625f;
+            O[(int64_t)(i + 1) * nlev] = (c0 + 2.0f * c[0] + c[1]) * 0.0625f;
+            O[(int64_t)(i + 2) * nlev] = (c[0] + 2.0f * c[1] + c[2]) * 0.0625f;
+            O[(int64_t)(i + 3) * nlev] = (c[1] + 2.0f * c[2] + c[3]) * 0.0625f;
+        }
+        cm = c[2];
+        c0 = c[3];
+    }
+    for (; i < i1; ++i) {
         const float cp = colsum(i + 1 == G.nx ? 0 : i + 1);
         if (live) O[(int64_t)i * nlev] = (cm + 2.0f * c0 + cp) * 0.0625f;
         cm = c0;

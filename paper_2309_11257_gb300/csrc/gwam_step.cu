@@ -921,7 +921,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 5);
     if (c.tune_active) ++c.tune_pending;
     prof_mark(c, 4);
-    grid_phase(c, du, dv, mask);
+    grid_phase_df(c, du, dv, mask);
     prof_mark(c, 5);
     swap_rays(c);
 }
