@@ -42,7 +42,7 @@ BYTES_PER_RAY_STEP_FP32 = 128.0
 HBM_PEAK = None
 # DRAM bytes per k_advance launch from the ncu capture in profiles/k_advance_sphere_half_fp64.md
 # (38.9 MB for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
-ADV_TRAFFIC_BYTES_PER_RAY = 38.86e6 / 253952
+ADV_TRAFFIC_BYTES_PER_RAY = None   # re-captured after the double-float gather (kernel changed)
 
 
 def measured_peaks():
@@ -228,7 +228,7 @@ def gpu_arm(args, rank, world, local_rank):
         achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
         roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "traffic": ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch,
+                    "traffic": ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch if ADV_TRAFFIC_BYTES_PER_RAY else None,
                     "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere, scaled by rays",
                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)",
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}

@@ -32,7 +32,7 @@ static void dalloc(Context& c, T*& p, size_t count)
 
 static void free_all(Context& c)
 {
-    void* ptrs[] = {c.bg, c.bg32, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.tables_df,
+    void* ptrs[] = {c.bg, c.bg32, c.bgdf, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.tables_df,
                     c.bg_scratch,
                     c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
                     c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
@@ -244,6 +244,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             }
         }
         if (c.f32) dalloc(c, c.bg32, ncell);
+        else dalloc(c, c.bgdf, ncell);
         dalloc(c, c.info, nr);
         dalloc(c, c.ccell, nr);
         dalloc(c, c.cslot, nr);
@@ -327,6 +328,7 @@ static int set_background_impl(gwam_ctx* ctx, int member, const double* u, const
     for (int m = m0; m < m1; ++m) {
         launch_set_background(c, m, src[0], src[1], src[2], src[3]);
         if (c.f32) convert_background32(c, m);
+        else convert_background_df(c, m);
     }
     GWAM_CUDA(cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));

@@ -70,6 +70,7 @@ struct Context {
     Ray32SoA A32{}, B32{};
     float4* ray32_mem[2] = {nullptr, nullptr};
     Node32* bg32 = nullptr;
+    NodeDF* bgdf = nullptr;         // FP64 form: the background as double-float pairs (per-step gathers)
 
     // per-ray scratch
     int* info = nullptr;            // split code | children << 4 | status << 8
@@ -168,6 +169,7 @@ void grid_phase_df(Context& c, double* du, double* dv, int mask);
 inline void swap_rays(Context& c) { c.swap_rays_(); }
 void run_step32(Context& c, double dt, double* du, double* dv);
 void convert_background32(Context& c, int member);
+void convert_background_df(Context& c, int member);
 void launch_gather_rays32(Context& c, double* state13, long long* ids, int* cells, int64_t n);
 void prof_mark(Context& c, int phase);
 void tune_mark(Context& c, int idx);

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "gwam_df.cuh"
+
 namespace gwam {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -183,6 +185,36 @@ __device__ __forceinline__ void bracket_clamped(double s, int n, int& q0, int& q
     }
 }
 
+// The background node as 16 double-float pairs (hi, lo), in the order of Node's 16 doubles: the
+// per-step gathers of the FP64 form run on the FP32 pipes (compensated sums), with about 48
+// significant bits.  Filled from the FP64 nodes whenever the background is set.
+struct __align__(128) NodeDF {
+    float4 q[8];   // q[e] = (hi, lo) of value 2e, then (hi, lo) of value 2e + 1
+};
+
+// s + c += (wh + wl) (vh + vl): TwoProduct of the high parts, TwoSum into s, all lower-order terms
+// into the compensation c
+__device__ __forceinline__ void df_acc(float vh, float vl, float wh, float wl, float& s, float& c)
+{
+    const float p = __fmul_rn(wh, vh);
+    const float e = __fmaf_rn(wh, vh, -p);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(wh, vl, __fmaf_rn(wl, vh, e))));
+}
+
+__device__ __forceinline__ void accumulate_node_df(const NodeDF* __restrict__ p, DF w, float (&s)[16], float (&c)[16])
+{
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float4 a = __ldg(p->q + e);
+        df_acc(a.x, a.y, w.hi, w.lo, s[2 * e], c[2 * e]);
+        df_acc(a.z, a.w, w.hi, w.lo, s[2 * e + 1], c[2 * e + 1]);
+    }
+}
+
 __device__ __forceinline__ void accumulate_node(const Node* __restrict__ p, double w, double* acc)
 {
     const double2* q = reinterpret_cast<const double2*>(p);
@@ -195,7 +227,8 @@ __device__ __forceinline__ void accumulate_node(const Node* __restrict__ p, doub
 }
 
 // Trilinear interpolation of the node values and node gradients to (X, Y, Z).
-__device__ __forceinline__ void gather(const Grid& G, const Node* __restrict__ bg, double X, double Y, double Z, Bg& b)
+__device__ __forceinline__ void gather_fp64(const Grid& G, const Node* __restrict__ bg, double X, double Y, double Z,
+                                            Bg& b)
 {
     int i0, i1, j0, j1, k0, k1;
     double tx, ty, tz;
@@ -225,6 +258,46 @@ __device__ __forceinline__ void gather(const Grid& G, const Node* __restrict__ b
         b.v[f] = acc[f];
 #pragma unroll
         for (int q = 0; q < 3; ++q) b.d[f][q] = acc[4 + 3 * f + q];
+    }
+}
+
+// Trilinear interpolation of the node values and node gradients to (X, Y, Z), as gather_fp64, with
+// the weights and the 8-corner sums in double-float (about 2^-47 relative to the sum of |terms|);
+// only the bracketing (3 axes) and the 16 results use FP64 operations.
+__device__ __forceinline__ void gather(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
+                                       Bg& b)
+{
+    int i0, i1, j0, j1, k0, k1;
+    double tx, ty, tz;
+    bracket_periodic(X * G.inv_dX - 0.5, G.nx, G.inv_nx, i0, i1, tx);
+    if (G.geometry == 1) bracket_clamped((Y - G.y0) * G.inv_dY - 0.5, G.ny, j0, j1, ty);
+    else bracket_periodic(Y * G.inv_dY - 0.5, G.ny, G.inv_ny, j0, j1, ty);
+    bracket_clamped(Z * G.inv_dz - 0.5, G.nz, k0, k1, tz);
+    const DF one{1.0f, 0.0f};
+    const DF Tx = df_split(tx), Ty = df_split(ty), Tz = df_split(tz);
+    const DF Ux = df_add(one, {-Tx.hi, -Tx.lo}), Uy = df_add(one, {-Ty.hi, -Ty.lo}), Uz = df_add(one, {-Tz.hi, -Tz.lo});
+    const DF w00 = df_mul2(Ux, Uy), w10 = df_mul2(Tx, Uy), w01 = df_mul2(Ux, Ty), w11 = df_mul2(Tx, Ty);
+    float s[16], c[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s[q] = c[q] = 0.0f;
+    const int dk = k1 - k0;
+    const NodeDF* c00 = bg + node_index(G, i0, j0, k0);
+    const NodeDF* c10 = bg + node_index(G, i1, j0, k0);
+    const NodeDF* c01 = bg + node_index(G, i0, j1, k0);
+    const NodeDF* c11 = bg + node_index(G, i1, j1, k0);
+    accumulate_node_df(c00, df_mul2(w00, Uz), s, c);
+    accumulate_node_df(c00 + dk, df_mul2(w00, Tz), s, c);
+    accumulate_node_df(c10, df_mul2(w10, Uz), s, c);
+    accumulate_node_df(c10 + dk, df_mul2(w10, Tz), s, c);
+    accumulate_node_df(c01, df_mul2(w01, Uz), s, c);
+    accumulate_node_df(c01 + dk, df_mul2(w01, Tz), s, c);
+    accumulate_node_df(c11, df_mul2(w11, Uz), s, c);
+    accumulate_node_df(c11 + dk, df_mul2(w11, Tz), s, c);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        b.v[f] = widen(s[f]) + widen(c[f]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) b.d[f][q] = widen(s[4 + 3 * f + q]) + widen(c[4 + 3 * f + q]);
     }
 }
 
@@ -288,7 +361,7 @@ __device__ __forceinline__ void geometry_at(const Grid& G, double Y, double Z, G
 // opposing face group velocities, the extents with their difference (Sec. 3b, App. B.1); the
 // wavenumber follows Eq. eikonal-sphere:1-3 (sphere) or kdot = -grad Omega (f-plane) with the
 // centre values.
-__device__ __forceinline__ void ray_rhs(const Grid& G, const Node* __restrict__ bg, const double y[9], double F[9])
+__device__ __forceinline__ void ray_rhs(const Grid& G, const NodeDF* __restrict__ bg, const double y[9], double F[9])
 {
     const double k = y[3], l = y[4], m = y[5];
     Bg b;
@@ -348,7 +421,7 @@ __device__ __forceinline__ void ray_rhs(const Grid& G, const Node* __restrict__ 
 }
 
 // Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.
-__device__ __forceinline__ void rk3(const Grid& G, const Node* __restrict__ bg, double s[NSTATE], double dt)
+__device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt)
 {
     const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
     const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
@@ -500,7 +573,7 @@ struct Intr {
     double kh2, m2, mg2, K2, iK2, D, w, iw, w2, c, f2, n2;
 };
 
-__device__ __forceinline__ void intrinsic_at(const Grid& G, const Node* __restrict__ bg, const double s[NSTATE],
+__device__ __forceinline__ void intrinsic_at(const Grid& G, const NodeDF* __restrict__ bg, const double s[NSTATE],
                                              Geo& g, Intr& in)
 {
     Bg b;

@@ -1,0 +1,158 @@
+// gwam_df.cuh -- FP64-free building blocks for GB300, whose FP64 rate is 1/72 of its FP32 rate:
+// exact float <-> double conversions by integer operations and double-float ("DF") arithmetic,
+// hi + lo pairs of FP32 values carrying about 48 significant bits on the FP32 pipes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gwam {
+
+// Exact float -> double with integer operations only (on GB300 the conversion instruction runs at
+// the FP64 rate): sign kept, exponent re-biased from 127 to 1023, the 23 mantissa bits moved to the
+// top of the 52-bit field; subnormal floats are normalised first; infinities and NaNs keep their
+// class.
+__device__ __forceinline__ double widen(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t sign = u & 0x80000000u;
+    uint32_t ex = (u >> 23) & 0xFFu, man = u & 0x7FFFFFu;
+    if (ex == 0xFFu) return __hiloint2double((int)(sign | 0x7FF00000u | (man >> 3)), (int)(man << 29));
+    if (ex == 0u) {
+        if (man == 0u) return __hiloint2double((int)sign, 0);
+        const int sh = __clz((int)man) - 8;   // moves the leading one to bit 23
+        man = (man << sh) & 0x7FFFFFu;
+        ex = 1u - (uint32_t)sh;               // wraps below zero; the re-bias brings it back
+    }
+    return __hiloint2double((int)(sign | ((ex + 896u) << 20) | (man >> 3)), (int)(man << 29));
+}
+
+// double -> float, round to nearest even, with integer operations only (the conversion instruction
+// runs at the FP64 rate on GB300).  The 53-bit significand is shifted right to 24 bits (fewer for
+// a float subnormal) and rounded on the dropped bits; a carry out of the significand moves into
+// the exponent, an exponent beyond the float range gives infinity, infinities and NaNs keep their
+// class.
+__device__ __forceinline__ float narrow_general(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u | (uint32_t)(m >> 29) : 0u));
+    const int E = e - 896;                       // float biased exponent (1023 - 127)
+    if (E >= 255) return __uint_as_float(sign | 0x7F800000u);
+    const int shift = E > 0 ? 29 : 30 - E;       // significand bits dropped
+    if (shift > 60) return __uint_as_float(sign);
+    const unsigned long long mm = m | (e ? (1ull << 52) : 0ull);
+    const unsigned long long keep = mm >> shift;
+    const unsigned long long rem = mm & ((1ull << shift) - 1ull);
+    const unsigned long long half = 1ull << (shift - 1);
+    const unsigned long long q = keep + ((rem > half || (rem == half && (keep & 1ull))) ? 1ull : 0ull);
+    uint32_t r = E > 0 ? ((uint32_t)E << 23) + (uint32_t)(q - (1ull << 23)) : (uint32_t)q;
+    if (r > 0x7F800000u) r = 0x7F800000u;
+    return __uint_as_float(sign | r);
+}
+
+// Fast path of narrow for the usual case -- the result is a normal float or rounds up to infinity
+// -- with 32-bit operations on the two words of the double; everything else takes narrow_general.
+__device__ __forceinline__ float narrow(double x)
+{
+    const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+    const uint32_t e = (hw >> 20) & 0x7FFu;
+    if (e - 897u < 254u) {                      // float exponent 1 .. 254
+        uint32_t r = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
+        const uint32_t rem = lw & 0x1FFFFFFFu;  // the 29 dropped bits
+        r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+        return __uint_as_float((hw & 0x80000000u) | r);
+    }
+    return narrow_general(x);
+}
+
+// Double-float values hi + lo (|lo| <= ulp(hi) / 2) on the FP32 pipes, about 48 significant bits:
+// products by TwoProduct (an FMA gives the exact rounding error), sums by TwoSum (Dekker 1971,
+// Knuth); every operation is an explicitly rounded intrinsic, never contracted or reordered.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ DF df_mul(DF x, float b)
+{
+    const float p = __fmul_rn(x.hi, b);
+    const float e = __fmaf_rn(x.lo, b, __fmaf_rn(x.hi, b, -p));
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb)), __fadd_rn(a.lo, b.lo));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// a - b exactly as a double-float
+__device__ __forceinline__ DF df_diff(float a, float b)
+{
+    const float s = __fsub_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb))};
+}
+
+// hi + lo as a double (exact: lo's bits lie below hi's); a value that is one float needs no FP64 add
+__device__ __forceinline__ double df_to_double(DF x)
+{
+    return x.lo == 0.0f ? widen(x.hi) : widen(x.hi) + widen(x.lo);
+}
+
+// Segmented inclusive sum over runs of equal keys in a warp (as warp_segment_reduce) in
+// double-float: the FP32 pipes do the additions, the last lane of each run holds the run's sum.
+// Returns true on the last lane of a run.
+template <int NV>
+__device__ __forceinline__ bool warp_segment_reduce_df(int key, DF (&v)[NV])
+{
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const int next = __shfl_down_sync(0xffffffffu, key, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+    if (heads == 0xffffffffu) return true;
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            DF o;
+            o.hi = __shfl_up_sync(0xffffffffu, v[q].hi, d);
+            o.lo = __shfl_up_sync(0xffffffffu, v[q].lo, d);
+            if (lane - d >= start) v[q] = df_add(v[q], o);
+        }
+    }
+    return lane == 31 || next != key;
+}
+
+
+__device__ __forceinline__ DF df_mul2(DF a, DF b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float s = __fadd_rn(p, e);
+    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+
+// x = hi + lo to about 48 bits (one FP64 subtraction)
+__device__ __forceinline__ DF df_split(double x)
+{
+    const float hi = narrow(x);
+    return {hi, narrow(x - widen(hi))};
+}
+
+}  // namespace gwam

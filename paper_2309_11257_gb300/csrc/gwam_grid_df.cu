@@ -14,22 +14,6 @@ namespace gwam {
 
 namespace {
 
-__device__ __forceinline__ DF df_split(double x)
-{
-    const float hi = narrow(x);
-    return {hi, narrow(x - widen(hi))};
-}
-
-__device__ __forceinline__ DF df_mul2(DF a, DF b)
-{
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = __fmaf_rn(a.hi, b.hi, -p);
-    e = __fmaf_rn(a.hi, b.lo, e);
-    e = __fmaf_rn(a.lo, b.hi, e);
-    const float s = __fadd_rn(p, e);
-    return {s, __fsub_rn(e, __fsub_rn(s, p))};
-}
-
 __device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
 // multiplication by a power of two (exact)
@@ -88,12 +72,31 @@ __global__ void __launch_bounds__(256) k_smooth_df(Grid G, FieldSetDF fs, int f0
     const int i0 = sp * kSpanDF, i1 = min(G.nx, i0 + kSpanDF);
     DF cm = colsum(i0 == 0 ? G.nx - 1 : i0 - 1);
     DF c0 = colsum(i0);
-    for (int i = i0; i < i1; ++i) {
-        const DF cp = colsum(i + 1 == G.nx ? 0 : i + 1);
-        if (live) {
-            const DF s = df_pow2(df_add(df_add(cm, df_pow2(c0, 2.0f)), cp), 0.0625f);
-            O[(int64_t)i * nlev] = make_float2(s.hi, s.lo);
+    auto out = [&](int i, DF a, DF b, DF c) {
+        const DF s = df_pow2(df_add(df_add(a, df_pow2(b, 2.0f)), c), 0.0625f);
+        O[(int64_t)i * nlev] = make_float2(s.hi, s.lo);
+    };
+    int i = i0;
+    // four columns per pass, their twelve loads issued together
+    for (; i + 4 <= i1; i += 4) {
+        DF c[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int ii = i + 1 + q;
+            c[q] = colsum(ii >= G.nx ? ii - G.nx : ii);
         }
+        if (live) {
+            out(i, cm, c0, c[0]);
+            out(i + 1, c0, c[0], c[1]);
+            out(i + 2, c[0], c[1], c[2]);
+            out(i + 3, c[1], c[2], c[3]);
+        }
+        cm = c[2];
+        c0 = c[3];
+    }
+    for (; i < i1; ++i) {
+        const DF cp = colsum(i + 1 == G.nx ? 0 : i + 1);
+        if (live) out(i, cm, c0, cp);
         cm = c0;
         c0 = cp;
     }
@@ -227,7 +230,28 @@ void split_fields_df(Context& c, const double* const* in, float2* const* out, in
                                                                               c.field_len(F_LL), nf);
 }
 
+__global__ void k_bg_to_df(const Node* __restrict__ bg, NodeDF* __restrict__ out, int64_t n)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double* v = reinterpret_cast<const double*>(bg + c);
+        NodeDF o;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const DF a = df_split(v[2 * e]), b = df_split(v[2 * e + 1]);
+            o.q[e] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
+        out[c] = o;
+    }
+}
+
 }  // namespace
+
+void convert_background_df(Context& c, int member)
+{
+    const int64_t o = (int64_t)member * c.G.ncell;
+    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
+    k_bg_to_df<<<blocks, kThreads, 0, c.stream>>>(c.bg + o, c.bgdf + o, c.G.ncell);
+}
 
 void grid_phase_df(Context& c, double* du, double* dv, int mask)
 {

@@ -256,7 +256,7 @@ __device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict
     const double Y = row_lat(G, b.j);
     const double Z = b.z_launch + 0.5 * b.dz_launch;
     Bg bk;
-    gather(G, bg, X, Y, Z, bk);
+    gather_fp64(G, bg, X, Y, Z, bk);
     Geo g;
     geometry_at(G, Y, Z, g);
     double f2, df2;

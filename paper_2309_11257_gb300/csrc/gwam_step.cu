@@ -145,7 +145,7 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 
 // ============================================================================ advance
 
-__global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A, const Node* __restrict__ bg,
+__global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
                                                         Ctl* ctl, double dt, int* __restrict__ info,
                                                         int4* __restrict__ ccell, int4* __restrict__ cslot,
                                                         int* __restrict__ newid, int* __restrict__ cnt,
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A
         long long id;
         load_ray(A, i, s, id);
         const int mem = member_of(id);
-        const Node* bgm = bg + (int64_t)mem * G.ncell;
+        const NodeDF* bgm = bg + (int64_t)mem * G.ncell;
         rk3(G, bgm, s, dt);
         wrap_position(G, s);
         const int st = ray_status(G, s);
@@ -252,7 +252,7 @@ __global__ void k_cap_find(Grid G, Params P, Ctl* ctl, const int* __restrict__ o
 
 // Remove the lowest-energy ray volumes of each over-full column (energy w_hat * N Px Py Pz;
 // ties: the larger id goes first).  One block per column, rank by counting.
-__global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA A, const Node* __restrict__ bg,
+__global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
                                                           Ctl* ctl, const int* __restrict__ info,
                                                           const int* __restrict__ off,
                                                           const int* __restrict__ overlist,
@@ -375,7 +375,7 @@ __global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* 
 // per-ray saturation terms P_j = m^2 k_h^2 / (w K^2) A_j alpha_j (with A_j alpha_j = N Px Py Pz / V_c)
 // and K_j^2 (Eq. instability-threshold).
 __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RaySoA A, RaySoA B,
-                                                            const Node* __restrict__ bg, Ctl* ctl,
+                                                            const NodeDF* __restrict__ bg, Ctl* ctl,
                                                             const int* __restrict__ off2,
                                                             const int* __restrict__ sorted_src,
                                                             const int* __restrict__ info,
@@ -449,7 +449,7 @@ __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int nc
 //   pseudomomentum form (App. A): T^{ab} = ch_a k_b A
 // Centre fields: cell averages over the ray volumes whose carrier is in the cell, weight V_j/V_c.
 // Interface fields (z = kk dz, 1 <= kk < nz): staggered-cell overlap, weight w_h * overlap / dz.
-__global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B, const Node* __restrict__ bg,
+__global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B, const NodeDF* __restrict__ bg,
                                                         const Ctl* ctl, const int* __restrict__ off2,
                                                         const double* __restrict__ kappa,
                                                         const double* __restrict__ k2, double dt,
@@ -883,7 +883,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, s);
     prof_mark(c, 0);
     tune_mark(c, 0);
-    k_advance<<<la.blocks, la.threads, 0, s>>>(G, P, c.A, c.bg, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
+    k_advance<<<la.blocks, la.threads, 0, s>>>(G, P, c.A, c.bgdf, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
                                                c.partials, c.max_blocks);
     tune_mark(c, 1);
     prof_mark(c, 1);
@@ -895,7 +895,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     const int* off2 = c.off;
     if (P.cap > 0) {
         k_cap_find<<<cell_blocks, kThreads, 0, s>>>(G, P, c.ctl, c.off, c.overlist);
-        k_cap_apply<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bg, c.ctl, c.info, c.off, c.overlist, c.ent_id, c.ent_src,
+        k_cap_apply<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bgdf, c.ctl, c.info, c.off, c.overlist, c.ent_id, c.ent_src,
                                             c.ecap, c.cnt, c.partials, c.max_blocks);
         exclusive_scan(c, c.cnt, c.off2, G.ncell_all, nullptr);
         off2 = c.off2;
@@ -905,7 +905,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     k_segsort_big<<<nb, kThreads, 0, s>>>(c.ctl, c.off, off2, c.biglist, c.ent_id, c.ent_src, c.sorted_src);
     k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
     tune_mark(c, 2);
-    k_materialize<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A, c.B, c.bg, c.ctl, off2, c.sorted_src, c.info, c.newid,
+    k_materialize<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A, c.B, c.bgdf, c.ctl, off2, c.sorted_src, c.info, c.newid,
                                                    c.pj, c.k2, c.raycell);
     tune_mark(c, 3);
     prof_mark(c, 2);
@@ -914,7 +914,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     prof_mark(c, 3);
     for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);
-    k_project<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B, c.bg, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL],
+    k_project<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B, c.bgdf, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL],
                                                c.field[F_ZP], c.field[F_LL], c.field[F_LP], c.field[F_PL],
                                                c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD],
                                                c.partials, c.max_blocks);
