@@ -264,7 +264,8 @@ class Model:
         return out
 
     def field_abs(self, name: str) -> np.ndarray:
-        """Sum of |contribution| of a projected field (the scale of its rounding error)."""
+        """Sum of |contribution| of a projected field (the scale of its rounding error), each
+        contribution taken with the ray volume's wave action before the step's saturation."""
         which = FIELD_NAMES.index(name)
         nl = self.nz + 1 if which < 2 else self.nz
         out = np.zeros((nl, self.ny, self.nx))

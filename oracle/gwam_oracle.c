@@ -60,6 +60,9 @@ struct orc_model {
     double *fz[2];                       /* vertical fluxes at level interfaces [nz+1][ny][nx] */
     double *hf[NFIELD_H];                /* F_ll F_lp F_pl F_pp E_l E_p wave-action density [nz][ny][nx] */
     double *fzabs[2], *hfabs[NFIELD_H];  /* sums of |contribution| of the same fields (error scales) */
+    double *n_scale;                     /* per ray: wave-action density before this step's saturation */
+    int64_t n_scale_cap;
+    int n_scale_valid;                   /* set by apply_saturation, consumed by project */
 };
 
 /* ------------------------------------------------------------------ geometry */
@@ -413,6 +416,7 @@ void orc_destroy(orc_model *m)
         for (int q = 0; q < 3; ++q) free(m->grad[f][q]);
     free_fields(m);
     free_rays(m);
+    free(m->n_scale);
     free(m);
 }
 
@@ -878,6 +882,14 @@ int orc_cell_pq(const orc_model *m, double *p_cells, double *q_cells)
  * contained in"), rho at the cell centre, and the factor is clamped at 0 (not in the paper). */
 static void apply_saturation(orc_model *m, double dt)
 {
+    if (m->n > m->n_scale_cap) {
+        free(m->n_scale);
+        m->n_scale = malloc(sizeof(double) * (size_t)m->n);
+        m->n_scale_cap = m->n_scale ? m->n : 0;
+    }
+    m->n_scale_valid = m->n_scale != NULL;
+    if (m->n_scale_valid)
+        for (int64_t q = 0; q < m->n; ++q) m->n_scale[q] = fabs(m->s[SN][q]);
     int64_t a = 0;
     while (a < m->n) {
         int32_t cell = m->cell[a];
@@ -921,6 +933,39 @@ static void apply_saturation(orc_model *m, double dt)
  *   (f/g) e_r x <u'b'> = -(1 / (g rho)) f^2 N^2 ch_r / (w^2 - f^2) k_h A
  * (accumulated here without the 1/(g rho) factor, applied with the cell density later).
  * Pseudomomentum form (App. A): T^{ab} = ch_a k_b A, no elastic term. */
+/* the eight flux values of one ray volume with wave action A (all linear in A):
+ * out = {T_ll, T_lp, T_pl, T_pp, E_l, E_p, Z_l, Z_p} */
+static void ray_fluxes(const orc_model *m, const disp_t *d, double f2, double n2, double kk, double ll, double A,
+                       double out[8])
+{
+    const double *ch = d->ch;
+    if (m->P.flux_form == 0) {
+        double den = d->w2 - f2;
+        out[0] = (d->w2 * ch[0] * kk + f2 * ch[1] * ll) / den * A;
+        out[1] = (d->w2 * ch[0] * ll - f2 * ch[1] * kk) / den * A;
+        out[2] = (d->w2 * ch[1] * kk - f2 * ch[0] * ll) / den * A;
+        out[3] = (d->w2 * ch[1] * ll + f2 * ch[0] * kk) / den * A;
+        out[4] = -f2 * n2 * ch[2] / den * kk * A;
+        out[5] = -f2 * n2 * ch[2] / den * ll * A;
+        out[6] = d->w2 * ch[2] * kk / den * A;
+        out[7] = d->w2 * ch[2] * ll / den * A;
+    } else {
+        out[0] = ch[0] * kk * A;
+        out[1] = ch[0] * ll * A;
+        out[2] = ch[1] * kk * A;
+        out[3] = ch[1] * ll * A;
+        out[4] = 0.0;
+        out[5] = 0.0;
+        out[6] = ch[2] * kk * A;
+        out[7] = ch[2] * ll * A;
+    }
+}
+
+/* Error scales (hfabs, fzabs): sums of |contribution| with the wave action a ray volume had before
+ * this step's saturation.  The saturation factor 1 - 2 kappa K^2 dt is a difference of terms of
+ * size 1, so its rounding error is of order the unit roundoff relative to 1, not to the factor;
+ * a nearly fully damped ray volume therefore carries an error proportional to its action before
+ * the damping, and the scale follows that. */
 static void project(orc_model *m)
 {
     long nx = m->G.nx, ny = m->G.ny, nz = m->G.nz;
@@ -943,29 +988,12 @@ static void project(orc_model *m)
         ray_disp(m, s, &d, &f2, &n2);
         spectral_extents(m, s, &dk, &dl, &dm);
         double A = s[SN] * dk * dl * dm;
-        double kk = s[SK], ll = s[SL];
-        const double *ch = d.ch;
-        double t_ll, t_lp, t_pl, t_pp, e_l, e_p, z_l, z_p;
-        if (m->P.flux_form == 0) {
-            double den = d.w2 - f2;
-            t_ll = (d.w2 * ch[0] * kk + f2 * ch[1] * ll) / den * A;
-            t_lp = (d.w2 * ch[0] * ll - f2 * ch[1] * kk) / den * A;
-            t_pl = (d.w2 * ch[1] * kk - f2 * ch[0] * ll) / den * A;
-            t_pp = (d.w2 * ch[1] * ll + f2 * ch[0] * kk) / den * A;
-            z_l = d.w2 * ch[2] * kk / den * A;
-            z_p = d.w2 * ch[2] * ll / den * A;
-            e_l = -f2 * n2 * ch[2] / den * kk * A;
-            e_p = -f2 * n2 * ch[2] / den * ll * A;
-        } else {
-            t_ll = ch[0] * kk * A;
-            t_lp = ch[0] * ll * A;
-            t_pl = ch[1] * kk * A;
-            t_pp = ch[1] * ll * A;
-            z_l = ch[2] * kk * A;
-            z_p = ch[2] * ll * A;
-            e_l = 0.0;
-            e_p = 0.0;
-        }
+        double A_scale = (m->n_scale_valid ? m->n_scale[q] : fabs(s[SN])) * dk * dl * dm;
+        double fl[8], fa[8];
+        ray_fluxes(m, &d, f2, n2, s[SK], s[SL], A, fl);
+        ray_fluxes(m, &d, f2, n2, s[SK], s[SL], A_scale, fa);
+        double t_ll = fl[0], t_lp = fl[1], t_pl = fl[2], t_pp = fl[3], e_l = fl[4], e_p = fl[5];
+        double z_l = fl[6], z_p = fl[7];
         /* horizontal fluxes: cell average over the ray volumes whose carrier lies in the cell,
          * each weighted by its share alpha_j = V_j / V_c of the cell volume */
         double alpha = physical_volume(m, s) / cell_volume(m, j, k);
@@ -977,7 +1005,7 @@ static void project(orc_model *m)
         m->hf[4][c] += alpha * e_l;
         m->hf[5][c] += alpha * e_p;
         m->hf[6][c] += alpha * A;
-        double hv[NFIELD_H] = {t_ll, t_lp, t_pl, t_pp, e_l, e_p, A};
+        double hv[NFIELD_H] = {fa[0], fa[1], fa[2], fa[3], fa[4], fa[5], A_scale};
         for (int f = 0; f < NFIELD_H; ++f) m->hfabs[f][c] += fabs(alpha * hv[f]);
         /* vertical fluxes at the cell interfaces z = kk dz, 1 <= kk <= nz-1: integrate over the
          * staggered cell [(kk - 1/2) dz, (kk + 1/2) dz] of the carrier column; the weight is the
@@ -997,10 +1025,11 @@ static void project(orc_model *m)
             size_t ci = ((size_t)kk2 * ny + (size_t)j) * nx + (size_t)i;
             m->fz[0][ci] += w * z_l;
             m->fz[1][ci] += w * z_p;
-            m->fzabs[0][ci] += fabs(w * z_l);
-            m->fzabs[1][ci] += fabs(w * z_p);
+            m->fzabs[0][ci] += fabs(w * fa[6]);
+            m->fzabs[1][ci] += fabs(w * fa[7]);
         }
     }
+    m->n_scale_valid = 0;
 }
 
 /* Reading of App. B.4 for a lat-lon grid: separable 1-2-1 x 1-2-1 weights (4 centre, 2 edge,

@@ -104,7 +104,8 @@ void orc_get_stats(const orc_model *m, orc_stats *out);
 /* grid fields of the last step: which = 0..8 ->
  * Fz_lambda, Fz_phi ([nz+1][ny][nx]), F_ll, F_lp, F_pl, F_pp, E_l, E_p, wave-action density ([nz][ny][nx]) */
 int orc_get_field(const orc_model *m, int which, double *out);
-/* error scales: sums of |contribution| of a field, and the tendency formula applied to them */
+/* error scales: sums of |contribution| of a field (each with the ray volume's wave action before the
+ * step's saturation), and the tendency formula applied to them */
 int orc_get_field_abs(const orc_model *m, int which, double *out);
 int orc_tendency_scale(const orc_model *m, double *du_scale, double *dv_scale);
 /* Gamma^2 node field [nz][ny][nx] */

@@ -7,7 +7,10 @@ Tolerances (FP64 path):
     modulo their period;
   * du/dt, dv/dt and the grid fields, which are sums over ray volumes: elementwise
     |gpu - oracle| <= 1e-9 * S, with S the oracle's sum of the magnitudes of the contributions
-    (pushed through the divergence for the tendencies).  Sums whose contributions cancel (opposite
+    (pushed through the divergence for the tendencies), each taken with the ray volume's wave
+    action before this step's saturation: the damping factor 1 - 2 kappa K^2 dt is a difference
+    of terms of size 1, so a nearly fully damped ray volume carries an error of the unit roundoff
+    times its undamped contribution.  Sums whose contributions cancel (opposite
     azimuths) carry only rounding noise relative to their own size, so a plain relative error of
     the result would measure summation order, not parity;
   * budget terms: relative 1e-9.

@@ -33,9 +33,9 @@ MUTATIONS = {
     "threshold_integrand": ("*pj = s[SM] * s[SM] * d.kh2 / (d.w * d.K2) * A * alpha;",
                             "*pj = s[SM] * s[SM] * d.kh2 / (d.w * d.K2 * d.K2) * A * alpha;"),
     # projection and tendencies
-    "coriolis_flux_sign": ("t_ll = (d.w2 * ch[0] * kk + f2 * ch[1] * ll) / den * A;",
-                           "t_ll = (d.w2 * ch[0] * kk - f2 * ch[1] * ll) / den * A;"),
-    "elastic_sign": ("e_l = -f2 * n2 * ch[2] / den * kk * A;", "e_l = f2 * n2 * ch[2] / den * kk * A;"),
+    "coriolis_flux_sign": ("out[0] = (d->w2 * ch[0] * kk + f2 * ch[1] * ll) / den * A;",
+                           "out[0] = (d->w2 * ch[0] * kk - f2 * ch[1] * ll) / den * A;"),
+    "elastic_sign": ("out[4] = -f2 * n2 * ch[2] / den * kk * A;", "out[4] = f2 * n2 * ch[2] / den * kk * A;"),
     "vertical_overlap": ("double w = w_h * ov / dz;", "double w = w_h * ov / s[SEZ];"),
     "volume_share": ("double alpha = physical_volume(m, s) / cell_volume(m, j, k);\n        size_t c",
                      "double alpha = 1.0;\n        size_t c"),
