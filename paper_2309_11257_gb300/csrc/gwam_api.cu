@@ -194,11 +194,12 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         dalloc(c, c.rho_inv, ncell);
         {
             // row and level tables (host-computed once)
-            std::vector<double> tab(2 * (size_t)G.ny + G.nz);
+            std::vector<double> tab(3 * (size_t)G.ny + G.nz);
             for (int j = 0; j < G.ny; ++j) {
                 const double phi = G.y0 + (j + 0.5) * G.dY;
                 tab[j] = G.geometry == 1 ? cos(phi) : 1.0;
                 tab[G.ny + j] = 1.0 / tab[j];
+                tab[2 * (size_t)G.ny + G.nz + j] = phi;   // row-centre latitude
             }
             for (int k = 0; k < G.nz; ++k)
                 tab[2 * G.ny + k] = G.geometry == 1 ? 1.0 / (G.radius + (k + 0.5) * G.dz) : 1.0;
@@ -207,6 +208,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.row_cos = c.tables;
             G.row_inv_cos = c.tables + G.ny;
             G.lev_inv_r = c.tables + 2 * G.ny;
+            G.row_lat = c.tables + 2 * G.ny + G.nz;
             std::vector<float> t32(2 * (size_t)G.ny + (size_t)G.ny * G.nz);
             for (int j = 0; j < G.ny; ++j) {
                 t32[j] = (float)tab[j];
@@ -218,13 +220,26 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
                     t32[2 * (size_t)G.ny + (size_t)j * G.nz + k] = (float)iv;
                 }
             }
-            std::vector<float2> tdf(tab.size());
-            for (size_t q = 0; q < tab.size(); ++q) {
-                const float hi = (float)tab[q];
-                tdf[q] = make_float2(hi, (float)(tab[q] - (double)hi));
+            // double-float tables: row_cos, row_inv_cos [ny], lev_inv_r [nz], then (sin, cos) of every
+            // row centre [ny][2]
+            auto split = [](double x) {
+                const float hi = (float)x;
+                return make_float2(hi, (float)(x - (double)hi));
+            };
+            std::vector<float2> tdf(4 * (size_t)G.ny + G.nz);
+            for (int q = 0; q < 2 * G.ny + G.nz; ++q) tdf[q] = split(tab[q]);
+            for (int j = 0; j < G.ny; ++j) {
+                const double phi = tab[2 * (size_t)G.ny + G.nz + j];
+                tdf[2 * (size_t)G.ny + G.nz + 2 * j] = split(G.geometry == 1 ? sin(phi) : 0.0);
+                tdf[2 * (size_t)G.ny + G.nz + 2 * j + 1] = split(G.geometry == 1 ? cos(phi) : 1.0);
             }
             dalloc(c, c.tables_df, tdf.size());
             GWAM_CUDA(cudaMemcpy(c.tables_df, tdf.data(), sizeof(float2) * tdf.size(), cudaMemcpyHostToDevice));
+            G.row_sc_df = c.tables_df + 2 * G.ny + G.nz;
+            G.df_radius = split(G.radius);
+            G.df_2omega = split(2.0 * G.omega);
+            G.df_8omega2 = split(8.0 * G.omega * G.omega);
+            G.df_f0sq = split(G.f0 * G.f0);
             dalloc(c, c.tables32, t32.size());
             GWAM_CUDA(cudaMemcpy(c.tables32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
             G.row_cos32 = c.tables32;

@@ -73,6 +73,10 @@ struct Grid {
     const float* row_cos32;     // [ny]
     const float* ivol32;        // [ny * nz]: 1 / cell volume of row j, level k
     const float* whf32;         // [ny]: row_inv_cos * inv_dX * inv_dY (solid-angle share per unit extent)
+    // double-float constants and row tables of the FP64 form's ray equations
+    float2 df_radius, df_2omega, df_8omega2, df_f0sq;
+    const float2* row_sc_df;    // [ny][2]: sin, cos of every row centre (sphere)
+    const double* row_lat;      // [ny]: latitude of every row centre
 };
 
 struct Params {
@@ -301,6 +305,49 @@ __device__ __forceinline__ void gather(const Grid& G, const NodeDF* __restrict__
     }
 }
 
+struct BgDF {
+    DF v[4];
+    DF d[4][3];
+};
+
+// gather with double-float results (no conversion back to FP64)
+__device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
+                                          BgDF& b)
+{
+    int i0, i1, j0, j1, k0, k1;
+    double tx, ty, tz;
+    bracket_periodic(X * G.inv_dX - 0.5, G.nx, G.inv_nx, i0, i1, tx);
+    if (G.geometry == 1) bracket_clamped((Y - G.y0) * G.inv_dY - 0.5, G.ny, j0, j1, ty);
+    else bracket_periodic(Y * G.inv_dY - 0.5, G.ny, G.inv_ny, j0, j1, ty);
+    bracket_clamped(Z * G.inv_dz - 0.5, G.nz, k0, k1, tz);
+    const DF one{1.0f, 0.0f};
+    const DF Tx = df_split(tx), Ty = df_split(ty), Tz = df_split(tz);
+    const DF Ux = df_sub(one, Tx), Uy = df_sub(one, Ty), Uz = df_sub(one, Tz);
+    const DF w00 = df_mul2(Ux, Uy), w10 = df_mul2(Tx, Uy), w01 = df_mul2(Ux, Ty), w11 = df_mul2(Tx, Ty);
+    float s[16], c[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s[q] = c[q] = 0.0f;
+    const int dk = k1 - k0;
+    const NodeDF* c00 = bg + node_index(G, i0, j0, k0);
+    const NodeDF* c10 = bg + node_index(G, i1, j0, k0);
+    const NodeDF* c01 = bg + node_index(G, i0, j1, k0);
+    const NodeDF* c11 = bg + node_index(G, i1, j1, k0);
+    accumulate_node_df(c00, df_mul2(w00, Uz), s, c);
+    accumulate_node_df(c00 + dk, df_mul2(w00, Tz), s, c);
+    accumulate_node_df(c10, df_mul2(w10, Uz), s, c);
+    accumulate_node_df(c10 + dk, df_mul2(w10, Tz), s, c);
+    accumulate_node_df(c01, df_mul2(w01, Uz), s, c);
+    accumulate_node_df(c01 + dk, df_mul2(w01, Tz), s, c);
+    accumulate_node_df(c11, df_mul2(w11, Uz), s, c);
+    accumulate_node_df(c11 + dk, df_mul2(w11, Tz), s, c);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        b.v[f] = df_norm(s[f], c[f]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) b.d[f][q] = df_norm(s[4 + 3 * f + q], c[4 + 3 * f + q]);
+    }
+}
+
 // f^2 and d(f^2)/dphi (f = 2 Omega sin phi on the sphere, f0 on the f-plane)
 __device__ __forceinline__ void coriolis(const Grid& G, double sphi, double cphi, double& f2, double& df2)
 {
@@ -420,6 +467,142 @@ __device__ __forceinline__ void ray_rhs(const Grid& G, const NodeDF* __restrict_
     }
 }
 
+// ------------------------------------------------------------ the ray equations in double-float
+// The same formulas as dispersion / geometry_at / coriolis / ray_rhs above, evaluated in
+// double-float on the FP32 pipes (GB300's FP64 rate is 1/72 of its FP32 rate): the state enters
+// as FP64 and is split (one FP64 subtraction per component), the nine rates leave as FP64.  Every
+// intermediate carries about 48 significant bits, the reciprocal and reciprocal square root one
+// Newton step in DF from the FP32 hardware approximations (~2^-45).
+
+struct DispDF {
+    DF K2, iK2, D, w2, iw, c;
+};
+
+__device__ __forceinline__ void dispersion_df(DF kh2, DF mg2, DF n2, DF f2, DispDF& d)
+{
+    d.K2 = df_add(kh2, mg2);
+    d.D = df_sub(n2, f2);
+    d.iK2 = df_rcp(d.K2);
+    d.w2 = df_mul2(df_add(df_mul2(f2, mg2), df_mul2(n2, kh2)), d.iK2);
+    d.iw = df_rsqrt(d.w2);
+    d.c = df_mul2(df_mul2(d.D, df_mul2(d.iK2, d.iK2)), d.iw);
+}
+
+struct GeoDF {
+    DF ir, ihX, sphi, cphi, tphi;
+};
+
+// sin and cos of the latitude from the row-centre table and the offset d from the centre
+// (|d| <= half a row): sin(p0 + d) = s0 cos d + c0 sin d, cos(p0 + d) = c0 cos d - s0 sin d, with
+// sin d and cos d from their Taylor series -- the terms up to d^3 and d^4 in DF, the smaller ones
+// (below 3e-8 for rows of up to 9 degrees) in FP32, truncated after d^7 and d^8
+__device__ __forceinline__ void geometry_df(const Grid& G, double Y, double Z, GeoDF& g)
+{
+    if (G.geometry == 1) {
+        int j = (int)floor((Y - G.y0) * G.inv_dY);
+        j = j < 0 ? 0 : (j >= G.ny ? G.ny - 1 : j);
+        const DF d = df_split(Y - G.row_lat[j]);
+        const DF dd = df_mul2(d, d);
+        constexpr DF sixth{1.0f / 6.0f, (float)(1.0 / 6.0 - (double)(1.0f / 6.0f))};
+        constexpr DF twentyfourth{1.0f / 24.0f, (float)(1.0 / 24.0 - (double)(1.0f / 24.0f))};
+        const float d2 = dd.hi;
+        const float d4 = d2 * d2;
+        const DF sind = df_add(df_sub(d, df_mul2(df_mul2(dd, d), sixth)),
+                               df_f(d.hi * d4 * (1.0f / 120.0f - d2 * (1.0f / 5040.0f))));
+        const DF cosd = df_sub(df_add(df_sub(df_f(1.0f), df_pow2(dd, 0.5f)), df_mul2(df_mul2(dd, dd), twentyfourth)),
+                               df_f(d4 * d2 * (1.0f / 720.0f - d2 * (1.0f / 40320.0f))));
+        const float2 sc0 = G.row_sc_df[2 * j], sc1 = G.row_sc_df[2 * j + 1];
+        const DF s0{sc0.x, sc0.y}, c0{sc1.x, sc1.y};
+        g.sphi = df_add(df_mul2(s0, cosd), df_mul2(c0, sind));
+        g.cphi = df_sub(df_mul2(c0, cosd), df_mul2(s0, sind));
+        const DF r = df_add(DF{G.df_radius.x, G.df_radius.y}, df_split(Z));
+        g.ir = df_rcp(r);
+        const DF ic = df_rcp(g.cphi);
+        g.ihX = df_mul2(g.ir, ic);
+        g.tphi = df_mul2(g.sphi, ic);
+    } else {
+        g.sphi = df_f(0.0f);
+        g.cphi = df_f(1.0f);
+        g.tphi = df_f(0.0f);
+        g.ir = df_f(1.0f);
+        g.ihX = df_f(1.0f);
+    }
+}
+
+__device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restrict__ bg, const double y[9], double F[9])
+{
+    BgDF b;
+    gather_df(G, bg, y[0], y[1], y[2], b);
+    GeoDF g;
+    geometry_df(G, y[1], y[2], g);
+    DF f2, df2;
+    if (G.geometry == 1) {
+        const DF f = df_mul2(DF{G.df_2omega.x, G.df_2omega.y}, g.sphi);
+        f2 = df_mul2(f, f);
+        df2 = df_mul2(df_mul2(DF{G.df_8omega2.x, G.df_8omega2.y}, g.sphi), g.cphi);
+    } else {
+        f2 = DF{G.df_f0sq.x, G.df_f0sq.y};
+        df2 = df_f(0.0f);
+    }
+    const DF k = df_split(y[3]), l = df_split(y[4]), m = df_split(y[5]);
+    const DF U = b.v[0], V = b.v[1], N2 = b.v[2], G2 = b.v[3];
+    const DF kh2 = df_add(df_mul2(k, k), df_mul2(l, l)), m2 = df_mul2(m, m);
+    const DF mg2 = df_add(m2, G2);
+    DispDF d;
+    dispersion_df(kh2, mg2, N2, f2, d);
+    const DF mg2c = df_mul2(mg2, d.c);
+    const DF cgx = df_add(df_mul2(k, mg2c), U);
+    const DF cgy = df_add(df_mul2(l, mg2c), V);
+    const DF cgz = df_neg(df_mul2(df_mul2(m, kh2), d.c));
+    const DF hwK = df_pow2(df_mul2(d.iw, d.iK2), 0.5f);   // 1 / (2 w K^2)
+    const DF aN = df_mul2(kh2, hwK);
+    const DF aG = df_mul2(df_mul2(aN, d.D), d.iK2);
+    const DF aF = df_mul2(mg2, hwK);
+    DF Gq[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        Gq[q] = df_sub(df_add(df_add(df_mul2(k, b.d[0][q]), df_mul2(l, b.d[1][q])), df_mul2(aN, b.d[2][q])),
+                       df_mul2(aG, b.d[3][q]));
+    Gq[1] = df_add(Gq[1], df_mul2(aF, df2));
+    DF R[9];
+    if (G.geometry == 1) {
+        const DF ir = g.ir;
+        R[3] = df_add(df_neg(df_mul2(Gq[0], g.ihX)), df_mul2(df_mul2(k, ir), df_sub(df_mul2(g.tphi, cgy), cgz)));
+        R[4] = df_sub(df_neg(df_mul2(Gq[1], ir)), df_mul2(ir, df_add(df_mul2(l, cgz), df_mul2(df_mul2(k, g.tphi), cgx))));
+        R[5] = df_add(df_neg(Gq[2]), df_mul2(ir, df_add(df_mul2(k, cgx), df_mul2(l, cgy))));
+    } else {
+        R[3] = df_neg(Gq[0]);
+        R[4] = df_neg(Gq[1]);
+        R[5] = df_neg(Gq[2]);
+    }
+    // faces: first-order Taylor values along the face's own axis
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const DF ext = df_split(y[6 + q]);
+        DF vel[2];
+#pragma unroll
+        for (int sd = 0; sd < 2; ++sd) {
+            const DF h = df_pow2(ext, sd == 0 ? 0.5f : -0.5f);
+            const DF N2f = df_add(N2, df_mul2(b.d[2][q], h));
+            const DF G2f = df_add(G2, df_mul2(b.d[3][q], h));
+            const DF f2f = (q == 1) ? df_add(f2, df_mul2(df2, h)) : f2;
+            const DF mg2f = df_add(m2, G2f);
+            DispDF e;
+            dispersion_df(kh2, mg2f, N2f, f2f, e);
+            if (q == 0)
+                vel[sd] = df_mul2(df_add(df_add(df_mul2(df_mul2(k, mg2f), e.c), U), df_mul2(b.d[0][0], h)), g.ihX);
+            else if (q == 1)
+                vel[sd] = df_mul2(df_add(df_add(df_mul2(df_mul2(l, mg2f), e.c), V), df_mul2(b.d[1][1], h)), g.ir);
+            else
+                vel[sd] = df_neg(df_mul2(df_mul2(m, kh2), e.c));
+        }
+        R[q] = df_pow2(df_add(vel[0], vel[1]), 0.5f);
+        R[6 + q] = df_sub(vel[0], vel[1]);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c] = df_to_double(R[c]);
+}
+
 // Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.
 __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt)
 {
@@ -431,7 +614,7 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
 #pragma unroll 1
     for (int st = 0; st < 3; ++st) {
         double F[9];
-        ray_rhs(G, bg, s, F);
+        ray_rhs_df(G, bg, s, F);
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
             q[c] = A[st] * q[c] + dt * F[c];

@@ -148,6 +148,40 @@ __device__ __forceinline__ DF df_mul2(DF a, DF b)
     return {s, __fsub_rn(e, __fsub_rn(s, p))};
 }
 
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+// multiplication by a power of two (exact)
+__device__ __forceinline__ DF df_pow2(DF a, float s) { return {a.hi * s, a.lo * s}; }
+__device__ __forceinline__ DF df_f(float a) { return {a, 0.0f}; }
+
+// renormalise an unevaluated sum s + c into a DF pair (TwoSum)
+__device__ __forceinline__ DF df_norm(float s, float c)
+{
+    const float h = __fadd_rn(s, c);
+    const float bb = __fsub_rn(h, s);
+    return {h, __fadd_rn(__fsub_rn(s, __fsub_rn(h, bb)), __fsub_rn(c, bb))};
+}
+
+// 1 / x: the FP32 hardware approximation (about 23 correct bits) refined by one Newton step
+// y <- y + y (1 - x y) in DF, which squares the relative error to about 2^-45
+__device__ __forceinline__ DF df_rcp(DF x)
+{
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x.hi));
+    const DF e = df_sub(df_f(1.0f), df_mul(x, r0));
+    return df_add(df_f(r0), df_mul(e, r0));
+}
+
+// 1 / sqrt(x): the FP32 hardware approximation refined by one Newton step
+// y <- y + y (1 - x y^2) / 2 in DF (relative error about 2^-45, as df_rcp)
+__device__ __forceinline__ DF df_rsqrt(DF x)
+{
+    float r0;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(x.hi));
+    const DF e = df_sub(df_f(1.0f), df_mul2(x, df_prod(r0, r0)));
+    return df_add(df_f(r0), df_pow2(df_mul(e, r0), 0.5f));
+}
+
 // x = hi + lo to about 48 bits (one FP64 subtraction)
 __device__ __forceinline__ DF df_split(double x)
 {

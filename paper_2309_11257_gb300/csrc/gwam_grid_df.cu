@@ -14,10 +14,6 @@ namespace gwam {
 
 namespace {
 
-__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
-// multiplication by a power of two (exact)
-__device__ __forceinline__ DF df_pow2(DF a, float s) { return {a.hi * s, a.lo * s}; }
 __device__ __forceinline__ DF df_load(const float2* p) { const float2 v = *p; return {v.x, v.y}; }
 
 struct FieldSetDF {
