@@ -221,12 +221,23 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
                 }
             }
             // double-float tables: row_cos, row_inv_cos [ny], lev_inv_r [nz], then (sin, cos) of every
-            // row centre [ny][2]
+            // row centre [ny][2], the horizontal share per unit extent [ny] and the inverse cell
+            // volumes [ny][nz]
             auto split = [](double x) {
                 const float hi = (float)x;
                 return make_float2(hi, (float)(x - (double)hi));
             };
-            std::vector<float2> tdf(4 * (size_t)G.ny + G.nz);
+            const size_t o_whf = 4 * (size_t)G.ny + G.nz, o_ivol = o_whf + G.ny;
+            std::vector<float2> tdf(o_ivol + (size_t)G.ny * G.nz);
+            for (int j = 0; j < G.ny; ++j) {
+                tdf[o_whf + j] = split(tab[G.ny + j] * G.inv_dX * G.inv_dY);
+                for (int k = 0; k < G.nz; ++k) {
+                    const double ir = tab[2 * G.ny + k];
+                    tdf[o_ivol + (size_t)j * G.nz + k] =
+                        split(G.geometry == 1 ? ir * ir * tab[G.ny + j] * G.inv_dX * G.inv_dY * G.inv_dz
+                                              : G.inv_dX * G.inv_dY * G.inv_dz);
+                }
+            }
             for (int q = 0; q < 2 * G.ny + G.nz; ++q) tdf[q] = split(tab[q]);
             for (int j = 0; j < G.ny; ++j) {
                 const double phi = tab[2 * (size_t)G.ny + G.nz + j];
@@ -236,6 +247,8 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             dalloc(c, c.tables_df, tdf.size());
             GWAM_CUDA(cudaMemcpy(c.tables_df, tdf.data(), sizeof(float2) * tdf.size(), cudaMemcpyHostToDevice));
             G.row_sc_df = c.tables_df + 2 * G.ny + G.nz;
+            G.whf_df = c.tables_df + o_whf;
+            G.ivol_df = c.tables_df + o_ivol;
             G.df_radius = split(G.radius);
             G.df_2omega = split(2.0 * G.omega);
             G.df_8omega2 = split(8.0 * G.omega * G.omega);

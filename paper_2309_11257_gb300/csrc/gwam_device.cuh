@@ -77,6 +77,8 @@ struct Grid {
     float2 df_radius, df_2omega, df_8omega2, df_f0sq;
     const float2* row_sc_df;    // [ny][2]: sin, cos of every row centre (sphere)
     const double* row_lat;      // [ny]: latitude of every row centre
+    const float2* whf_df;       // [ny]: row_inv_cos * inv_dX * inv_dY
+    const float2* ivol_df;      // [ny * nz]: 1 / cell volume of row j, level k
 };
 
 struct Params {
@@ -310,9 +312,11 @@ struct BgDF {
     DF d[4][3];
 };
 
-// gather with double-float results (no conversion back to FP64)
-__device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
-                                          BgDF& b)
+// Trilinear sums of the node quantities held in the float4 elements [E0, E1) of every NodeDF
+// (element e holds quantities 2e and 2e + 1), as unevaluated hi + compensation pairs.
+template <int E0, int E1>
+__device__ __forceinline__ void gather_df_sums(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y,
+                                               double Z, float (&s)[2 * (E1 - E0)], float (&c)[2 * (E1 - E0)])
 {
     int i0, i1, j0, j1, k0, k1;
     double tx, ty, tz;
@@ -324,28 +328,47 @@ __device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restric
     const DF Tx = df_split(tx), Ty = df_split(ty), Tz = df_split(tz);
     const DF Ux = df_sub(one, Tx), Uy = df_sub(one, Ty), Uz = df_sub(one, Tz);
     const DF w00 = df_mul2(Ux, Uy), w10 = df_mul2(Tx, Uy), w01 = df_mul2(Ux, Ty), w11 = df_mul2(Tx, Ty);
-    float s[16], c[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) s[q] = c[q] = 0.0f;
+    for (int q = 0; q < 2 * (E1 - E0); ++q) s[q] = c[q] = 0.0f;
     const int dk = k1 - k0;
-    const NodeDF* c00 = bg + node_index(G, i0, j0, k0);
-    const NodeDF* c10 = bg + node_index(G, i1, j0, k0);
-    const NodeDF* c01 = bg + node_index(G, i0, j1, k0);
-    const NodeDF* c11 = bg + node_index(G, i1, j1, k0);
-    accumulate_node_df(c00, df_mul2(w00, Uz), s, c);
-    accumulate_node_df(c00 + dk, df_mul2(w00, Tz), s, c);
-    accumulate_node_df(c10, df_mul2(w10, Uz), s, c);
-    accumulate_node_df(c10 + dk, df_mul2(w10, Tz), s, c);
-    accumulate_node_df(c01, df_mul2(w01, Uz), s, c);
-    accumulate_node_df(c01 + dk, df_mul2(w01, Tz), s, c);
-    accumulate_node_df(c11, df_mul2(w11, Uz), s, c);
-    accumulate_node_df(c11 + dk, df_mul2(w11, Tz), s, c);
+    const NodeDF* corner[4] = {bg + node_index(G, i0, j0, k0), bg + node_index(G, i1, j0, k0),
+                               bg + node_index(G, i0, j1, k0), bg + node_index(G, i1, j1, k0)};
+    const DF wc[4] = {w00, w10, w01, w11};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const NodeDF* p = corner[q >> 1] + ((q & 1) ? dk : 0);
+        const DF w = df_mul2(wc[q >> 1], (q & 1) ? Tz : Uz);
+#pragma unroll
+        for (int e = E0; e < E1; ++e) {
+            const float4 a = __ldg(p->q + e);
+            df_acc(a.x, a.y, w.hi, w.lo, s[2 * (e - E0)], c[2 * (e - E0)]);
+            df_acc(a.z, a.w, w.hi, w.lo, s[2 * (e - E0) + 1], c[2 * (e - E0) + 1]);
+        }
+    }
+}
+
+// gather with double-float results (no conversion back to FP64)
+__device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
+                                          BgDF& b)
+{
+    float s[16], c[16];
+    gather_df_sums<0, 8>(G, bg, X, Y, Z, s, c);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         b.v[f] = df_norm(s[f], c[f]);
 #pragma unroll
         for (int q = 0; q < 3; ++q) b.d[f][q] = df_norm(s[4 + 3 * f + q], c[4 + 3 * f + q]);
     }
+}
+
+// N^2 and Gamma^2 alone (the second float4 of each node): what the intrinsic quantities need
+__device__ __forceinline__ void gather_n2g2_df(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y,
+                                               double Z, DF& n2, DF& g2)
+{
+    float s[2], c[2];
+    gather_df_sums<1, 2>(G, bg, X, Y, Z, s, c);
+    n2 = df_norm(s[0], c[0]);
+    g2 = df_norm(s[1], c[1]);
 }
 
 // f^2 and d(f^2)/dphi (f = 2 Omega sin phi on the sphere, f0 on the f-plane)
@@ -496,25 +519,30 @@ struct GeoDF {
 // (|d| <= half a row): sin(p0 + d) = s0 cos d + c0 sin d, cos(p0 + d) = c0 cos d - s0 sin d, with
 // sin d and cos d from their Taylor series -- the terms up to d^3 and d^4 in DF, the smaller ones
 // (below 3e-8 for rows of up to 9 degrees) in FP32, truncated after d^7 and d^8
+__device__ __forceinline__ void lat_sincos_df(const Grid& G, double Y, DF& sphi, DF& cphi)
+{
+    int j = (int)floor((Y - G.y0) * G.inv_dY);
+    j = j < 0 ? 0 : (j >= G.ny ? G.ny - 1 : j);
+    const DF d = df_split(Y - G.row_lat[j]);
+    const DF dd = df_mul2(d, d);
+    constexpr DF sixth{1.0f / 6.0f, (float)(1.0 / 6.0 - (double)(1.0f / 6.0f))};
+    constexpr DF twentyfourth{1.0f / 24.0f, (float)(1.0 / 24.0 - (double)(1.0f / 24.0f))};
+    const float d2 = dd.hi;
+    const float d4 = d2 * d2;
+    const DF sind = df_add(df_sub(d, df_mul2(df_mul2(dd, d), sixth)),
+                           df_f(d.hi * d4 * (1.0f / 120.0f - d2 * (1.0f / 5040.0f))));
+    const DF cosd = df_sub(df_add(df_sub(df_f(1.0f), df_pow2(dd, 0.5f)), df_mul2(df_mul2(dd, dd), twentyfourth)),
+                           df_f(d4 * d2 * (1.0f / 720.0f - d2 * (1.0f / 40320.0f))));
+    const float2 sc0 = G.row_sc_df[2 * j], sc1 = G.row_sc_df[2 * j + 1];
+    const DF s0{sc0.x, sc0.y}, c0{sc1.x, sc1.y};
+    sphi = df_add(df_mul2(s0, cosd), df_mul2(c0, sind));
+    cphi = df_sub(df_mul2(c0, cosd), df_mul2(s0, sind));
+}
+
 __device__ __forceinline__ void geometry_df(const Grid& G, double Y, double Z, GeoDF& g)
 {
     if (G.geometry == 1) {
-        int j = (int)floor((Y - G.y0) * G.inv_dY);
-        j = j < 0 ? 0 : (j >= G.ny ? G.ny - 1 : j);
-        const DF d = df_split(Y - G.row_lat[j]);
-        const DF dd = df_mul2(d, d);
-        constexpr DF sixth{1.0f / 6.0f, (float)(1.0 / 6.0 - (double)(1.0f / 6.0f))};
-        constexpr DF twentyfourth{1.0f / 24.0f, (float)(1.0 / 24.0 - (double)(1.0f / 24.0f))};
-        const float d2 = dd.hi;
-        const float d4 = d2 * d2;
-        const DF sind = df_add(df_sub(d, df_mul2(df_mul2(dd, d), sixth)),
-                               df_f(d.hi * d4 * (1.0f / 120.0f - d2 * (1.0f / 5040.0f))));
-        const DF cosd = df_sub(df_add(df_sub(df_f(1.0f), df_pow2(dd, 0.5f)), df_mul2(df_mul2(dd, dd), twentyfourth)),
-                               df_f(d4 * d2 * (1.0f / 720.0f - d2 * (1.0f / 40320.0f))));
-        const float2 sc0 = G.row_sc_df[2 * j], sc1 = G.row_sc_df[2 * j + 1];
-        const DF s0{sc0.x, sc0.y}, c0{sc1.x, sc1.y};
-        g.sphi = df_add(df_mul2(s0, cosd), df_mul2(c0, sind));
-        g.cphi = df_sub(df_mul2(c0, cosd), df_mul2(s0, sind));
+        lat_sincos_df(G, Y, g.sphi, g.cphi);
         const DF r = df_add(DF{G.df_radius.x, G.df_radius.y}, df_split(Z));
         g.ir = df_rcp(r);
         const DF ic = df_rcp(g.cphi);
@@ -601,6 +629,36 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) F[c] = df_to_double(R[c]);
+}
+
+// Intrinsic quantities of a ray volume at its carrier position in double-float (the FP64 form's
+// saturation and projection): wavenumbers, f^2, N^2 and the dispersion terms, from N^2 and Gamma^2
+// interpolated alone.
+struct IntrDF {
+    DF k, l, m, kh2, m2, mg2, f2, n2;
+    DispDF d;
+};
+
+__device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __restrict__ bg, const double s[NSTATE],
+                                             IntrDF& in)
+{
+    DF g2;
+    gather_n2g2_df(G, bg, s[SX], s[SY], s[SZ], in.n2, g2);
+    if (G.geometry == 1) {
+        DF sphi, cphi;
+        lat_sincos_df(G, s[SY], sphi, cphi);
+        const DF f = df_mul2(DF{G.df_2omega.x, G.df_2omega.y}, sphi);
+        in.f2 = df_mul2(f, f);
+    } else {
+        in.f2 = DF{G.df_f0sq.x, G.df_f0sq.y};
+    }
+    in.k = df_split(s[SK]);
+    in.l = df_split(s[SL]);
+    in.m = df_split(s[SM]);
+    in.kh2 = df_add(df_mul2(in.k, in.k), df_mul2(in.l, in.l));
+    in.m2 = df_mul2(in.m, in.m);
+    in.mg2 = df_add(in.m2, g2);
+    dispersion_df(in.kh2, in.mg2, in.n2, in.f2, in.d);
 }
 
 // Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.

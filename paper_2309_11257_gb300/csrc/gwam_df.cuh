@@ -182,6 +182,20 @@ __device__ __forceinline__ DF df_rsqrt(DF x)
     return df_add(df_f(r0), df_pow2(df_mul(e, r0), 0.5f));
 }
 
+// floor and ceil of hi + lo (a normalised pair: lo only matters when hi is an integer)
+__device__ __forceinline__ float df_floor(DF x)
+{
+    const float f = floorf(x.hi);
+    return (f == x.hi && x.lo < 0.0f) ? f - 1.0f : f;
+}
+__device__ __forceinline__ float df_ceil(DF x)
+{
+    const float f = ceilf(x.hi);
+    return (f == x.hi && x.lo > 0.0f) ? f + 1.0f : f;
+}
+// a < b for normalised pairs
+__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
 // x = hi + lo to about 48 bits (one FP64 subtraction)
 __device__ __forceinline__ DF df_split(double x)
 {

@@ -145,7 +145,7 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 
 // ============================================================================ advance
 
-__global__ void __launch_bounds__(kThreads) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
+__global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
                                                         Ctl* ctl, double dt, int* __restrict__ info,
                                                         int4* __restrict__ ccell, int4* __restrict__ cslot,
                                                         int* __restrict__ newid, int* __restrict__ cnt,
@@ -401,14 +401,14 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
         store_ray(B, p, ch, cid);
         raycell[p] = member_of(id) * G.ncell + cell_of(G, ch);
         if (P.saturation) {
-            Geo g;
-            Intr in;
-            intrinsic_at(G, bg + (int64_t)member_of(id) * G.ncell, ch, g, in);
+            IntrDF in;
+            intrinsic_df(G, bg + (int64_t)member_of(id) * G.ncell, ch, in);
             int ci, cj, ck;
             cell_ijk(G, ch, ci, cj, ck);
-            const double av = ray_action(ch) * inv_cell_volume(G, cj, ck);
-            pj[p] = in.m2 * in.kh2 * in.iw * in.iK2 * av;
-            k2[p] = in.K2;
+            const float2 iv = G.ivol_df[cj * G.nz + ck];
+            const DF av = df_mul2(df_split(ray_action(ch)), DF{iv.x, iv.y});
+            pj[p] = df_to_double(df_mul2(df_mul2(df_mul2(in.m2, in.kh2), df_mul2(in.d.iw, in.d.iK2)), av));
+            k2[p] = df_to_double(in.d.K2);
         }
     }
 }
@@ -467,8 +467,10 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
         const int p = p0 + threadIdx.x;
         const bool act = p < n;
         int key = -1;
-        double hv[7] = {0, 0, 0, 0, 0, 0, 0};
-        double zl = 0.0, zp = 0.0, wh = 0.0, lo = 0.0, hi = 0.0;
+        DF hv[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) hv[q] = df_f(0.0f);
+        DF zl = df_f(0.0f), zp = df_f(0.0f), lo = df_f(0.0f), hi = df_f(0.0f);
         int col = 0, kk0 = 1, nkk = 0;
         if (act) {
             double s[NSTATE];
@@ -487,66 +489,90 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
             const double W = ray_action(s);
             w_tot += W;
             const int mem = member_of(id);
-            Geo g;
-            Intr in;
-            intrinsic_at(G, bg + (int64_t)mem * G.ncell, s, g, in);
+            IntrDF in;
+            intrinsic_df(G, bg + (int64_t)mem * G.ncell, s, in);
             int ci, cj, ck;
             cell_ijk(G, s, ci, cj, ck);
             col = mem * G.ncol + cj * G.nx + ci;
             key = col * G.nz + ck;
-            const double Vj = ray_volume(G, s, g);
-            const double A = W * rcp_nr(Vj);               // N dk dl dm
-            const double aw = W * inv_cell_volume(G, cj, ck);   // alpha_j A_j with alpha_j = V_j / V_c
-            const double k = s[SK], l = s[SL], m = s[SM];
-            const double mg2c = in.mg2 * in.c;             // (m^2 + Gamma^2) D / (w K^4)
-            const double chx = k * mg2c, chy = l * mg2c, chr = -m * in.kh2 * in.c;
-            double t_ll, t_lp, t_pl, t_pp, el, ep;
+            const DF Wd = df_split(W);
+            const float2 iv = G.ivol_df[cj * G.nz + ck];
+            const DF aw = df_mul2(Wd, DF{iv.x, iv.y});            // alpha_j A_j = W / V_c
+            const DF mg2c = df_mul2(in.mg2, in.d.c);              // (m^2 + Gamma^2) D / (w K^4)
+            const DF chx = df_mul2(in.k, mg2c), chy = df_mul2(in.l, mg2c);
+            const DF chr = df_neg(df_mul2(df_mul2(in.m, in.kh2), in.d.c));
+            DF t_ll, t_lp, t_pl, t_pp, el, ep, zc;
             if (P.flux_form == 0) {
-                const double iden = rcp_nr(in.w2 - in.f2);
-                t_ll = (in.w2 * chx * k + in.f2 * chy * l) * iden;
-                t_lp = (in.w2 * chx * l - in.f2 * chy * k) * iden;
-                t_pl = (in.w2 * chy * k - in.f2 * chx * l) * iden;
-                t_pp = (in.w2 * chy * l + in.f2 * chx * k) * iden;
-                zl = in.w2 * chr * k * iden;
-                zp = in.w2 * chr * l * iden;
-                el = -in.f2 * in.n2 * chr * iden * k;
-                ep = -in.f2 * in.n2 * chr * iden * l;
+                // 1 / (w^2 - f^2) as K^2 / ((N^2 - f^2) k_h^2): the same quantity without the cancellation
+                const DF iden = df_mul2(in.d.K2, df_rcp(df_mul2(in.d.D, in.kh2)));
+                const DF w2x = df_mul2(in.d.w2, chx), w2y = df_mul2(in.d.w2, chy);
+                const DF f2x = df_mul2(in.f2, chx), f2y = df_mul2(in.f2, chy);
+                t_ll = df_mul2(df_add(df_mul2(w2x, in.k), df_mul2(f2y, in.l)), iden);
+                t_lp = df_mul2(df_sub(df_mul2(w2x, in.l), df_mul2(f2y, in.k)), iden);
+                t_pl = df_mul2(df_sub(df_mul2(w2y, in.k), df_mul2(f2x, in.l)), iden);
+                t_pp = df_mul2(df_add(df_mul2(w2y, in.l), df_mul2(f2x, in.k)), iden);
+                zc = df_mul2(df_mul2(in.d.w2, chr), iden);
+                const DF ec = df_neg(df_mul2(df_mul2(df_mul2(in.f2, in.n2), chr), iden));
+                el = df_mul2(ec, in.k);
+                ep = df_mul2(ec, in.l);
             } else {
-                t_ll = chx * k; t_lp = chx * l; t_pl = chy * k; t_pp = chy * l;
-                zl = chr * k; zp = chr * l;
-                el = 0.0; ep = 0.0;
+                t_ll = df_mul2(chx, in.k);
+                t_lp = df_mul2(chx, in.l);
+                t_pl = df_mul2(chy, in.k);
+                t_pp = df_mul2(chy, in.l);
+                zc = chr;
+                el = df_f(0.0f);
+                ep = df_f(0.0f);
             }
-            hv[0] = aw * t_ll; hv[1] = aw * t_lp; hv[2] = aw * t_pl; hv[3] = aw * t_pp;
-            hv[4] = aw * el; hv[5] = aw * ep; hv[6] = aw;
-            zl *= A;
-            zp *= A;
-            wh = g.cphi * s[SEX] * s[SEY] * G.row_inv_cos[cj] * G.inv_dX * G.inv_dY;
-            lo = s[SZ] - 0.5 * s[SEZ];
-            hi = s[SZ] + 0.5 * s[SEZ];
-            kk0 = max(1, (int)floor(lo * G.inv_dz - 0.5));
-            const int kk1 = min(G.nz - 1, (int)ceil(hi * G.inv_dz + 0.5));
+            hv[0] = df_mul2(aw, t_ll);
+            hv[1] = df_mul2(aw, t_lp);
+            hv[2] = df_mul2(aw, t_pl);
+            hv[3] = df_mul2(aw, t_pp);
+            hv[4] = df_mul2(aw, el);
+            hv[5] = df_mul2(aw, ep);
+            hv[6] = aw;
+            // vertical fluxes: w_h A = W whf / (r^2 ez) -- the cos(phi) ex ey of the horizontal share
+            // and of the ray volume cancel; the overlaps are taken in units of dz
+            const DF ez = df_split(s[SEZ]);
+            DF r2e = ez;
+            if (G.geometry == 1) {
+                const DF r = df_add(DF{G.df_radius.x, G.df_radius.y}, df_split(s[SZ]));
+                r2e = df_mul2(df_mul2(r, r), ez);
+            }
+            const float2 wf = G.whf_df[cj];
+            const DF zcA = df_mul2(zc, df_mul2(df_mul2(Wd, DF{wf.x, wf.y}), df_rcp(r2e)));
+            zl = df_mul2(zcA, in.k);
+            zp = df_mul2(zcA, in.l);
+            const DF u = df_split(s[SZ] * G.inv_dz), e = df_pow2(df_split(s[SEZ] * G.inv_dz), 0.5f);
+            lo = df_sub(u, e);
+            hi = df_add(u, e);
+            kk0 = max(1, (int)df_floor(df_sub(lo, df_f(0.5f))));
+            const int kk1 = min(G.nz - 1, (int)df_ceil(df_add(hi, df_f(0.5f))));
             nkk = kk1 >= kk0 ? kk1 - kk0 + 1 : 0;
         }
         // centre fields: warp-segmented reduction over runs of equal cells, one atomic per run
         const bool own = warp_run_interior(key);
-        if (warp_segment_reduce(key, hv) && key >= 0) {
+        if (warp_segment_reduce_df(key, hv) && key >= 0) {
+            double v[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) v[q] = df_to_double(hv[q]);
             if (own) {
                 // the whole cell is this run: store its sum (fields were zeroed before the launch)
-                f_ll[key] = hv[0];
-                f_lp[key] = hv[1];
-                f_pl[key] = hv[2];
-                f_pp[key] = hv[3];
-                e_l[key] = hv[4];
-                e_p[key] = hv[5];
-                wad[key] = hv[6];
+                f_ll[key] = v[0];
+                f_lp[key] = v[1];
+                f_pl[key] = v[2];
+                f_pp[key] = v[3];
+                e_l[key] = v[4];
+                e_p[key] = v[5];
+                wad[key] = v[6];
             } else {
-                atomicAdd(&f_ll[key], hv[0]);
-                atomicAdd(&f_lp[key], hv[1]);
-                atomicAdd(&f_pl[key], hv[2]);
-                atomicAdd(&f_pp[key], hv[3]);
-                atomicAdd(&e_l[key], hv[4]);
-                atomicAdd(&e_p[key], hv[5]);
-                atomicAdd(&wad[key], hv[6]);
+                atomicAdd(&f_ll[key], v[0]);
+                atomicAdd(&f_lp[key], v[1]);
+                atomicAdd(&f_pl[key], v[2]);
+                atomicAdd(&f_pp[key], v[3]);
+                atomicAdd(&e_l[key], v[4]);
+                atomicAdd(&e_p[key], v[5]);
+                atomicAdd(&wad[key], v[6]);
             }
         }
         // interface fields
@@ -554,22 +580,21 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) maxk = max(maxk, __shfl_xor_sync(0xffffffffu, maxk, o));
         for (int o = 0; o < maxk; ++o) {
-            double zv[2] = {0.0, 0.0};
+            DF zv[2] = {df_f(0.0f), df_f(0.0f)};
             int zkey = -1;
             if (o < nkk) {
                 const int kk = kk0 + o;
-                const double slo = (kk - 0.5) * G.dz, shi = (kk + 0.5) * G.dz;
-                const double ov = fmin(hi, shi) - fmax(lo, slo);
-                if (ov > 0.0) {
-                    const double w = wh * ov * G.inv_dz;
-                    zv[0] = w * zl;
-                    zv[1] = w * zp;
+                const DF slo = df_f((float)kk - 0.5f), shi = df_f((float)kk + 0.5f);
+                const DF ov = df_sub(df_less(hi, shi) ? hi : shi, df_less(lo, slo) ? slo : lo);
+                if (ov.hi > 0.0f) {
+                    zv[0] = df_mul2(ov, zl);
+                    zv[1] = df_mul2(ov, zp);
                     zkey = col * (G.nz + 1) + kk;
                 }
             }
-            if (warp_segment_reduce(zkey, zv) && zkey >= 0) {
-                atomicAdd(&fz_l[zkey], zv[0]);
-                atomicAdd(&fz_p[zkey], zv[1]);
+            if (warp_segment_reduce_df(zkey, zv) && zkey >= 0) {
+                atomicAdd(&fz_l[zkey], df_to_double(zv[0]));
+                atomicAdd(&fz_p[zkey], df_to_double(zv[1]));
             }
         }
     }
