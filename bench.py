@@ -36,7 +36,11 @@ WORKLOAD = "sphere 256x128x90, background source 983040 ray volumes, dt 180 s, F
 # gradients, plus exits and split decisions), counted from the formulas with every add, multiply,
 # divide, square root and trigonometric call as one operation.
 FLOPS_PER_RAY_STEP = 1460.0
-FP64_PEAK_TFLOPS = 1.25          # nominal GB300 FP64 rate (no measured FP64 peak is provided)
+# Peak rate of FP64-precision operations on GB300 (one operation per add or multiply): the kernel
+# runs them as double-float pairs on the FP32 pipes (152 SMs x 128 lanes x 2.07 GHz = 40.3 T FP32
+# instructions/s; a double-float add takes 11 FP32 instructions, a multiply 7, 9 on average ->
+# 4.48 T/s) besides the FP64 pipe (2 per clock per SM -> 0.63 T/s); together 5.1 T/s.
+FP64_EQ_PEAK_TOPS = 152 * 128 * 2.07e9 / 9.0 / 1e12 + 152 * 2 * 2.07e9 / 1e12
 # Precision form: algorithmic bytes of the ray step = the 64-byte ray record read and written once.
 BYTES_PER_RAY_STEP_FP32 = 128.0
 HBM_PEAK = None
@@ -227,10 +231,12 @@ def gpu_arm(args, rank, world, local_rank):
     else:
         achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
         roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak": FP64_EQ_PEAK_TOPS, "unit": "TFLOP/s", "frac": achieved / FP64_EQ_PEAK_TOPS,
                     "traffic": ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch if ADV_TRAFFIC_BYTES_PER_RAY else None,
                     "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere, scaled by rays",
-                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak on this pool)",
+                    "peak_source": "derived from unit counts and the 2.07 GHz clock: FP64-precision operations "
+                                   "as double-float on the FP32 pipes (4.48 T/s) plus the FP64 pipe (0.63 T/s)",
+                    "flops_per_ray_step": FLOPS_PER_RAY_STEP,
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
 
     # end to end through the public API with host buffers: each step uploads that step's

@@ -194,13 +194,24 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         dalloc(c, c.rho_inv, ncell);
         {
             // row and level tables (host-computed once)
-            std::vector<double> tab(3 * (size_t)G.ny + G.nz);
+            // split thresholds per row (App. B.3) after the row-centre latitudes: alpha_s sqrt(cos dX dY),
+            // alpha_s cos dX dY (cos = 1 on the f-plane), evaluated left to right as the oracle does
+            const size_t o_thr = 3 * (size_t)G.ny + G.nz;
+            std::vector<double> tab(o_thr + 2 * (size_t)G.ny);
             for (int j = 0; j < G.ny; ++j) {
                 const double phi = G.y0 + (j + 0.5) * G.dY;
                 tab[j] = G.geometry == 1 ? cos(phi) : 1.0;
                 tab[G.ny + j] = 1.0 / tab[j];
                 tab[2 * (size_t)G.ny + G.nz + j] = phi;   // row-centre latitude
+                if (G.geometry == 1) {
+                    tab[o_thr + 2 * j] = P.alpha_s * sqrt(tab[j] * G.dX * G.dY);
+                    tab[o_thr + 2 * j + 1] = P.alpha_s * tab[j] * G.dX * G.dY;
+                } else {
+                    tab[o_thr + 2 * j] = P.alpha_s * sqrt(G.dX * G.dY);
+                    tab[o_thr + 2 * j + 1] = P.alpha_s * G.dX * G.dY;
+                }
             }
+            G.split_hthr = fmax(P.alpha_s * G.dz, P.min_split_dz);
             for (int k = 0; k < G.nz; ++k)
                 tab[2 * G.ny + k] = G.geometry == 1 ? 1.0 / (G.radius + (k + 0.5) * G.dz) : 1.0;
             dalloc(c, c.tables, tab.size());
@@ -209,6 +220,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.row_inv_cos = c.tables + G.ny;
             G.lev_inv_r = c.tables + 2 * G.ny;
             G.row_lat = c.tables + 2 * G.ny + G.nz;
+            G.split_thr = c.tables + o_thr;
             std::vector<float> t32(2 * (size_t)G.ny + (size_t)G.ny * G.nz);
             for (int j = 0; j < G.ny; ++j) {
                 t32[j] = (float)tab[j];
@@ -227,8 +239,9 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
                 const float hi = (float)x;
                 return make_float2(hi, (float)(x - (double)hi));
             };
-            const size_t o_whf = 4 * (size_t)G.ny + G.nz, o_ivol = o_whf + G.ny;
-            std::vector<float2> tdf(o_ivol + (size_t)G.ny * G.nz);
+            const size_t o_whf = 4 * (size_t)G.ny + G.nz, o_ivol = o_whf + G.ny, o_lat = o_ivol + (size_t)G.ny * G.nz;
+            std::vector<float2> tdf(o_lat + G.ny);
+            for (int j = 0; j < G.ny; ++j) tdf[o_lat + j] = split(tab[2 * (size_t)G.ny + G.nz + j]);
             for (int j = 0; j < G.ny; ++j) {
                 tdf[o_whf + j] = split(tab[G.ny + j] * G.inv_dX * G.inv_dY);
                 for (int k = 0; k < G.nz; ++k) {
@@ -249,6 +262,11 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.row_sc_df = c.tables_df + 2 * G.ny + G.nz;
             G.whf_df = c.tables_df + o_whf;
             G.ivol_df = c.tables_df + o_ivol;
+            G.row_lat_df = c.tables_df + o_lat;
+            G.df_inv_dX = split(G.inv_dX);
+            G.df_inv_dY = split(G.inv_dY);
+            G.df_inv_dz = split(G.inv_dz);
+            G.df_y0 = split(G.y0);
             G.df_radius = split(G.radius);
             G.df_2omega = split(2.0 * G.omega);
             G.df_8omega2 = split(8.0 * G.omega * G.omega);

@@ -79,6 +79,12 @@ struct Grid {
     const double* row_lat;      // [ny]: latitude of every row centre
     const float2* whf_df;       // [ny]: row_inv_cos * inv_dX * inv_dY
     const float2* ivol_df;      // [ny * nz]: 1 / cell volume of row j, level k
+    const float2* row_lat_df;   // [ny]: latitude of every row centre
+    float2 df_inv_dX, df_inv_dY, df_inv_dz, df_y0;
+    // split thresholds (App. B.3), computed on the host in the order the device used to:
+    // split_thr[2 j] = alpha_s sqrt(cos(phi_j) dX dY), split_thr[2 j + 1] = alpha_s cos(phi_j) dX dY
+    const double* split_thr;
+    double split_hthr;          // max(alpha_s dz, min_split_dz)
 };
 
 struct Params {
@@ -312,20 +318,62 @@ struct BgDF {
     DF d[4][3];
 };
 
+// Bracketing in node units on double-float coordinates (FP32 pipes only): u = node coordinate,
+// q0 = floor(u) (wrapped or clamped), t = u - floor(u).  A non-finite u maps to node 0.
+__device__ __forceinline__ int wrap_fast(int i, int n)
+{
+    if ((unsigned)i < (unsigned)n) return i;
+    if (i < 0 && i >= -n) return i + n;
+    return wrap_int(i, n);
+}
+
+__device__ __forceinline__ void bracket_periodic_df(DF u, int n, int& q0, int& q1, DF& t)
+{
+    float fl = df_floor(u);
+    if (!(fabsf(fl) < 1e9f)) {
+        fl = 0.0f;
+        u = df_f(0.0f);
+    }
+    t = df_sub(u, df_f(fl));
+    q0 = wrap_fast((int)fl, n);
+    q1 = q0 + 1 == n ? 0 : q0 + 1;
+}
+
+__device__ __forceinline__ void bracket_clamped_df(DF u, int n, int& q0, int& q1, DF& t)
+{
+    float fl = df_floor(u);
+    if (!(fabsf(fl) < 1e9f)) {
+        fl = 0.0f;
+        u = df_f(0.0f);
+    }
+    const int q = (int)fl;
+    if (q < 0) {
+        q0 = 0; q1 = 1; t = df_f(0.0f);
+    } else if (q >= n - 1) {
+        q0 = n - 2; q1 = n - 1; t = df_f(1.0f);
+    } else {
+        q0 = q; q1 = q + 1; t = df_sub(u, df_f(fl));
+    }
+}
+
 // Trilinear sums of the node quantities held in the float4 elements [E0, E1) of every NodeDF
-// (element e holds quantities 2e and 2e + 1), as unevaluated hi + compensation pairs.
+// (element e holds quantities 2e and 2e + 1), as unevaluated hi + compensation pairs, at the
+// double-float position (X, Y, Z).
 template <int E0, int E1>
-__device__ __forceinline__ void gather_df_sums(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y,
-                                               double Z, float (&s)[2 * (E1 - E0)], float (&c)[2 * (E1 - E0)])
+__device__ __forceinline__ void gather_df_sums(const Grid& G, const NodeDF* __restrict__ bg, DF X, DF Y, DF Z,
+                                               float (&s)[2 * (E1 - E0)], float (&c)[2 * (E1 - E0)])
 {
     int i0, i1, j0, j1, k0, k1;
-    double tx, ty, tz;
-    bracket_periodic(X * G.inv_dX - 0.5, G.nx, G.inv_nx, i0, i1, tx);
-    if (G.geometry == 1) bracket_clamped((Y - G.y0) * G.inv_dY - 0.5, G.ny, j0, j1, ty);
-    else bracket_periodic(Y * G.inv_dY - 0.5, G.ny, G.inv_ny, j0, j1, ty);
-    bracket_clamped(Z * G.inv_dz - 0.5, G.nz, k0, k1, tz);
+    DF Tx, Ty, Tz;
+    const DF half = df_f(0.5f);
+    bracket_periodic_df(df_sub(df_mul2(X, DF{G.df_inv_dX.x, G.df_inv_dX.y}), half), G.nx, i0, i1, Tx);
+    if (G.geometry == 1)
+        bracket_clamped_df(df_sub(df_mul2(df_sub(Y, DF{G.df_y0.x, G.df_y0.y}), DF{G.df_inv_dY.x, G.df_inv_dY.y}), half),
+                           G.ny, j0, j1, Ty);
+    else
+        bracket_periodic_df(df_sub(df_mul2(Y, DF{G.df_inv_dY.x, G.df_inv_dY.y}), half), G.ny, j0, j1, Ty);
+    bracket_clamped_df(df_sub(df_mul2(Z, DF{G.df_inv_dz.x, G.df_inv_dz.y}), half), G.nz, k0, k1, Tz);
     const DF one{1.0f, 0.0f};
-    const DF Tx = df_split(tx), Ty = df_split(ty), Tz = df_split(tz);
     const DF Ux = df_sub(one, Tx), Uy = df_sub(one, Ty), Uz = df_sub(one, Tz);
     const DF w00 = df_mul2(Ux, Uy), w10 = df_mul2(Tx, Uy), w01 = df_mul2(Ux, Ty), w11 = df_mul2(Tx, Ty);
 #pragma unroll
@@ -348,8 +396,7 @@ __device__ __forceinline__ void gather_df_sums(const Grid& G, const NodeDF* __re
 }
 
 // gather with double-float results (no conversion back to FP64)
-__device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
-                                          BgDF& b)
+__device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restrict__ bg, DF X, DF Y, DF Z, BgDF& b)
 {
     float s[16], c[16];
     gather_df_sums<0, 8>(G, bg, X, Y, Z, s, c);
@@ -362,8 +409,8 @@ __device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restric
 }
 
 // N^2 and Gamma^2 alone (the second float4 of each node): what the intrinsic quantities need
-__device__ __forceinline__ void gather_n2g2_df(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y,
-                                               double Z, DF& n2, DF& g2)
+__device__ __forceinline__ void gather_n2g2_df(const Grid& G, const NodeDF* __restrict__ bg, DF X, DF Y, DF Z,
+                                               DF& n2, DF& g2)
 {
     float s[2], c[2];
     gather_df_sums<1, 2>(G, bg, X, Y, Z, s, c);
@@ -519,11 +566,13 @@ struct GeoDF {
 // (|d| <= half a row): sin(p0 + d) = s0 cos d + c0 sin d, cos(p0 + d) = c0 cos d - s0 sin d, with
 // sin d and cos d from their Taylor series -- the terms up to d^3 and d^4 in DF, the smaller ones
 // (below 3e-8 for rows of up to 9 degrees) in FP32, truncated after d^7 and d^8
-__device__ __forceinline__ void lat_sincos_df(const Grid& G, double Y, DF& sphi, DF& cphi)
+__device__ __forceinline__ void lat_sincos_df(const Grid& G, DF Y, DF& sphi, DF& cphi)
 {
-    int j = (int)floor((Y - G.y0) * G.inv_dY);
-    j = j < 0 ? 0 : (j >= G.ny ? G.ny - 1 : j);
-    const DF d = df_split(Y - G.row_lat[j]);
+    // the row only selects the expansion point: a neighbouring row near a boundary is as good
+    const float fj = df_floor(df_mul2(df_sub(Y, DF{G.df_y0.x, G.df_y0.y}), DF{G.df_inv_dY.x, G.df_inv_dY.y}));
+    const int j = fj < 0.0f ? 0 : (fj >= (float)(G.ny - 1) ? G.ny - 1 : (int)fj);
+    const float2 rl = G.row_lat_df[j];
+    const DF d = df_sub(Y, DF{rl.x, rl.y});
     const DF dd = df_mul2(d, d);
     constexpr DF sixth{1.0f / 6.0f, (float)(1.0 / 6.0 - (double)(1.0f / 6.0f))};
     constexpr DF twentyfourth{1.0f / 24.0f, (float)(1.0 / 24.0 - (double)(1.0f / 24.0f))};
@@ -539,11 +588,11 @@ __device__ __forceinline__ void lat_sincos_df(const Grid& G, double Y, DF& sphi,
     cphi = df_sub(df_mul2(c0, cosd), df_mul2(s0, sind));
 }
 
-__device__ __forceinline__ void geometry_df(const Grid& G, double Y, double Z, GeoDF& g)
+__device__ __forceinline__ void geometry_df(const Grid& G, DF Y, DF Z, GeoDF& g)
 {
     if (G.geometry == 1) {
         lat_sincos_df(G, Y, g.sphi, g.cphi);
-        const DF r = df_add(DF{G.df_radius.x, G.df_radius.y}, df_split(Z));
+        const DF r = df_add(DF{G.df_radius.x, G.df_radius.y}, Z);
         g.ir = df_rcp(r);
         const DF ic = df_rcp(g.cphi);
         g.ihX = df_mul2(g.ir, ic);
@@ -557,7 +606,7 @@ __device__ __forceinline__ void geometry_df(const Grid& G, double Y, double Z, G
     }
 }
 
-__device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restrict__ bg, const double y[9], double F[9])
+__device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restrict__ bg, const DF y[9], DF R[9])
 {
     BgDF b;
     gather_df(G, bg, y[0], y[1], y[2], b);
@@ -572,7 +621,7 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
         f2 = DF{G.df_f0sq.x, G.df_f0sq.y};
         df2 = df_f(0.0f);
     }
-    const DF k = df_split(y[3]), l = df_split(y[4]), m = df_split(y[5]);
+    const DF k = y[3], l = y[4], m = y[5];
     const DF U = b.v[0], V = b.v[1], N2 = b.v[2], G2 = b.v[3];
     const DF kh2 = df_add(df_mul2(k, k), df_mul2(l, l)), m2 = df_mul2(m, m);
     const DF mg2 = df_add(m2, G2);
@@ -592,7 +641,6 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
         Gq[q] = df_sub(df_add(df_add(df_mul2(k, b.d[0][q]), df_mul2(l, b.d[1][q])), df_mul2(aN, b.d[2][q])),
                        df_mul2(aG, b.d[3][q]));
     Gq[1] = df_add(Gq[1], df_mul2(aF, df2));
-    DF R[9];
     if (G.geometry == 1) {
         const DF ir = g.ir;
         R[3] = df_add(df_neg(df_mul2(Gq[0], g.ihX)), df_mul2(df_mul2(k, ir), df_sub(df_mul2(g.tphi, cgy), cgz)));
@@ -606,7 +654,7 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
     // faces: first-order Taylor values along the face's own axis
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const DF ext = df_split(y[6 + q]);
+        const DF ext = y[6 + q];
         DF vel[2];
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {
@@ -627,8 +675,6 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
         R[q] = df_pow2(df_add(vel[0], vel[1]), 0.5f);
         R[6 + q] = df_sub(vel[0], vel[1]);
     }
-#pragma unroll
-    for (int c = 0; c < 9; ++c) F[c] = df_to_double(R[c]);
 }
 
 // Intrinsic quantities of a ray volume at its carrier position in double-float (the FP64 form's
@@ -643,10 +689,11 @@ __device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __rest
                                              IntrDF& in)
 {
     DF g2;
-    gather_n2g2_df(G, bg, s[SX], s[SY], s[SZ], in.n2, g2);
+    const DF Y = df_split(s[SY]);
+    gather_n2g2_df(G, bg, df_split(s[SX]), Y, df_split(s[SZ]), in.n2, g2);
     if (G.geometry == 1) {
         DF sphi, cphi;
-        lat_sincos_df(G, s[SY], sphi, cphi);
+        lat_sincos_df(G, Y, sphi, cphi);
         const DF f = df_mul2(DF{G.df_2omega.x, G.df_2omega.y}, sphi);
         in.f2 = df_mul2(f, f);
     } else {
@@ -661,24 +708,43 @@ __device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __rest
     dispersion_df(in.kh2, in.mg2, in.n2, in.f2, in.d);
 }
 
-// Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.
-__device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt)
+// Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.  The rates
+// and the low-storage register q are double-float; the state advances in FP64 (s += B q rounded
+// once per stage) and, for the next evaluation, in a double-float copy updated by the same B q.
+// The FP64 state waits in shared memory during the stages (sh: this thread's first slot, slots
+// kThreads apart), which keeps it out of the registers the ray equations need.
+__device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt,
+                                    double* sh)
 {
-    const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
-    const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
-    double q[9];
+    constexpr DF A1{-5.0f / 9.0f, (float)(-5.0 / 9.0 - (double)(-5.0f / 9.0f))};
+    constexpr DF A2{-153.0f / 128.0f, 0.0f};
+    constexpr DF B0{1.0f / 3.0f, (float)(1.0 / 3.0 - (double)(1.0f / 3.0f))};
+    constexpr DF B1{15.0f / 16.0f, 0.0f};
+    constexpr DF B2{8.0f / 15.0f, (float)(8.0 / 15.0 - (double)(8.0f / 15.0f))};
+    const DF dtd = df_split(dt);
+    DF y[9], q[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) q[c] = 0.0;
+    for (int c = 0; c < 9; ++c) {
+        y[c] = df_split(s[c]);
+        q[c] = df_f(0.0f);
+        sh[c * kThreads] = s[c];
+    }
 #pragma unroll 1
     for (int st = 0; st < 3; ++st) {
-        double F[9];
-        ray_rhs_df(G, bg, s, F);
+        DF F[9];
+        ray_rhs_df(G, bg, y, F);
+        const DF a = st == 1 ? A1 : A2;
+        const DF b = st == 0 ? B0 : (st == 1 ? B1 : B2);
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            q[c] = A[st] * q[c] + dt * F[c];
-            s[c] += B[st] * q[c];
+            q[c] = st == 0 ? df_mul2(dtd, F[c]) : df_add(df_mul2(a, q[c]), df_mul2(dtd, F[c]));
+            const DF bq = df_mul2(b, q[c]);
+            sh[c * kThreads] += df_to_double(bq);
+            y[c] = df_add(y[c], bq);
         }
     }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) s[c] = sh[c * kThreads];
 }
 
 // ---------------------------------------------------------------------------- bookkeeping
@@ -706,10 +772,11 @@ __device__ __forceinline__ double ray_action(const double s[NSTATE])
 // 0 inside, 1 left the domain, 2 not a valid ray volume
 __device__ __forceinline__ int ray_status(const Grid& G, const double s[NSTATE])
 {
-    bool finite = true;
+    // finiteness from the exponent bits (integer pipe): all ones means infinity or NaN
+    unsigned allf = 0u;
 #pragma unroll
-    for (int c = 0; c < NSTATE; ++c) finite = finite && isfinite(s[c]);
-    if (!finite) return 2;
+    for (int c = 0; c < NSTATE; ++c) allf |= ((((unsigned)__double2hiint(s[c]) >> 20) & 0x7FFu) + 1u) & 0x800u;
+    if (allf) return 2;
     if (!(s[SEX] > 0.0 && s[SEY] > 0.0 && s[SEZ] > 0.0)) return 2;
     if (!(s[SZ] >= 0.0 && s[SZ] < G.ztop)) return 1;
     if (G.geometry == 1 && !(fabs(s[SY]) <= G.phimax)) return 1;
@@ -740,24 +807,25 @@ __device__ __forceinline__ int split_code(const Grid& G, const Params& P, const 
 {
     if (!P.splitting) return 0;
     int code = 0;
-    if (s[SEZ] > fmax(P.alpha_s * G.dz, P.min_split_dz)) code |= 1;
+    if (s[SEZ] > G.split_hthr) code |= 1;
     double xlen, ylen, thr, area, athr;
     if (G.geometry == 1) {
         int i, j, k;
         cell_ijk(G, s, i, j, k);
-        const double cj = G.row_cos[j];
-        const double cp = cos(s[SY]);
+        DF sphi, cphi;
+        lat_sincos_df(G, df_split(s[SY]), sphi, cphi);
+        const double cp = df_to_double(cphi);
         xlen = cp * s[SEX];
         ylen = s[SEY];
-        thr = P.alpha_s * sqrt(cj * G.dX * G.dY);
+        thr = G.split_thr[2 * j];
         area = cp * s[SEX] * s[SEY];
-        athr = P.alpha_s * cj * G.dX * G.dY;
+        athr = G.split_thr[2 * j + 1];
     } else {
         xlen = s[SEX];
         ylen = s[SEY];
-        thr = P.alpha_s * sqrt(G.dX * G.dY);
+        thr = G.split_thr[0];
         area = s[SEX] * s[SEY];
-        athr = P.alpha_s * G.dX * G.dY;
+        athr = G.split_thr[1];
     }
     if (xlen > thr || ylen > thr || area > athr) code |= (xlen >= ylen) ? 2 : 6;
     return code;

@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
                                                         int* __restrict__ newid, int* __restrict__ cnt,
                                                         double* __restrict__ partials, int pstride)
 {
+    __shared__ double sh_state[9 * kThreads];
     const int n = ctl->n;
     double w_exit = 0.0, w_inv = 0.0;
     long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
         load_ray(A, i, s, id);
         const int mem = member_of(id);
         const NodeDF* bgm = bg + (int64_t)mem * G.ncell;
-        rk3(G, bgm, s, dt);
+        rk3(G, bgm, s, dt, sh_state + threadIdx.x);
         wrap_position(G, s);
         const int st = ray_status(G, s);
         int code = 0, nch = 0;
