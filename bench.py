@@ -44,9 +44,10 @@ FP64_EQ_PEAK_TOPS = 152 * 128 * 2.07e9 / 9.0 / 1e12 + 152 * 2 * 2.07e9 / 1e12
 # Precision form: algorithmic bytes of the ray step = the 64-byte ray record read and written once.
 BYTES_PER_RAY_STEP_FP32 = 128.0
 HBM_PEAK = None
-# DRAM bytes per k_advance launch from the ncu capture in profiles/k_advance_sphere_half_fp64.md
-# (38.9 MB for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
-ADV_TRAFFIC_BYTES_PER_RAY = None   # re-captured after the double-float gather (kernel changed)
+# DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 40.0 MB, k_advance32:
+# 20.6 MB, each for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
+ADV_TRAFFIC_BYTES_PER_RAY = 157.4
+ADV32_TRAFFIC_BYTES_PER_RAY = 81.0
 
 
 def measured_peaks():
@@ -225,7 +226,9 @@ def gpu_arm(args, rank, world, local_rank):
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
         achieved = BYTES_PER_RAY_STEP_FP32 * rays_per_launch / (adv_ms / 1000.0) / 1e9
         roofline = {"bound": "hbm", "kernel": "k_advance32 (FP32 RK3 ray step)", "achieved": achieved,
-                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": ADV32_TRAFFIC_BYTES_PER_RAY * rays_per_launch,
+                    "traffic_source": "ncu dram bytes of k_advance32 on the 128x64 sphere, scaled by rays",
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
     else:
