@@ -374,7 +374,6 @@ static int set_background_impl(gwam_ctx* ctx, int member, const double* u, const
     for (int m = m0; m < m1; ++m) {
         launch_set_background(c, m, src[0], src[1], src[2], src[3]);
         if (c.f32) convert_background32(c, m);
-        else convert_background_df(c, m);
     }
     GWAM_CUDA(cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));

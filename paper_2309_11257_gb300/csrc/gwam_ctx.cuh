@@ -169,7 +169,6 @@ void grid_phase_df(Context& c, double* du, double* dv, int mask);
 inline void swap_rays(Context& c) { c.swap_rays_(); }
 void run_step32(Context& c, double dt, double* du, double* dv);
 void convert_background32(Context& c, int member);
-void convert_background_df(Context& c, int member);
 void launch_gather_rays32(Context& c, double* state13, long long* ids, int* cells, int64_t n);
 void prof_mark(Context& c, int phase);
 void tune_mark(Context& c, int idx);

@@ -8,20 +8,6 @@
 
 namespace gwam {
 
-__global__ void k_bg_to32(const Node* __restrict__ bg, Node32* __restrict__ bg32, int64_t n)
-{
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        Node32 o;
-#pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            o.v[f] = (float)bg[c].v[f];
-#pragma unroll
-            for (int q = 0; q < 3; ++q) o.d[f][q] = (float)bg[c].d[f][q];
-        }
-        bg32[c] = o;
-    }
-}
-
 // FP64 -> FP32, round to nearest, for up to NFIELD arrays in one launch (blockIdx.y = array)
 struct NarrowSet {
     const double* in[NFIELD];
@@ -48,11 +34,11 @@ __global__ void k_narrow(NarrowSet s)
     for (; i < n; i += stride) out[i] = narrow(in[i]);
 }
 
+// the FP32 nodes themselves are written by the node-gradient pass; here 1/rho is narrowed
 void convert_background32(Context& c, int member)
 {
     const int64_t o = (int64_t)member * c.G.ncell;
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
-    k_bg_to32<<<blocks, kThreads, 0, c.stream>>>(c.bg + o, c.bg32 + o, c.G.ncell);
     NarrowSet ns{};
     ns.in[0] = c.rho_inv + o;
     ns.out[0] = c.rho_inv32 + o;

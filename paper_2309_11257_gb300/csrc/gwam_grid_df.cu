@@ -226,28 +226,7 @@ void split_fields_df(Context& c, const double* const* in, float2* const* out, in
                                                                               c.field_len(F_LL), nf);
 }
 
-__global__ void k_bg_to_df(const Node* __restrict__ bg, NodeDF* __restrict__ out, int64_t n)
-{
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
-        const double* v = reinterpret_cast<const double*>(bg + c);
-        NodeDF o;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const DF a = df_split(v[2 * e]), b = df_split(v[2 * e + 1]);
-            o.q[e] = make_float4(a.hi, a.lo, b.hi, b.lo);
-        }
-        out[c] = o;
-    }
-}
-
 }  // namespace
-
-void convert_background_df(Context& c, int member)
-{
-    const int64_t o = (int64_t)member * c.G.ncell;
-    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
-    k_bg_to_df<<<blocks, kThreads, 0, c.stream>>>(c.bg + o, c.bgdf + o, c.G.ncell);
-}
 
 void grid_phase_df(Context& c, double* du, double* dv, int mask)
 {

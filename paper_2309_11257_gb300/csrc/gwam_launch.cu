@@ -13,15 +13,23 @@ namespace gwam {
 
 enum { BG_NONFINITE = 1, BG_RHO = 2, BG_N2F2 = 4 };
 
+// exponent bits all ones: infinity or NaN (integer pipe)
+__device__ __forceinline__ bool nonfinite_bits(double x)
+{
+    return ((((unsigned)__double2hiint(x) >> 20) & 0x7FFu) == 0x7FFu);
+}
+
 // caller [nz][ny][nx] -> column-major node values (U, V, N^2, Gamma^2) and rho, transposed through
-// shared memory (32 columns of a row per block); Gamma^2 = (d ln rho / dz)^2 / 4 by centred
-// differences of ln rho (one-sided at the bottom and top)
+// shared memory (kBgTile columns of a row per block).  Gamma^2 = (d ln rho / dz)^2 / 4 by centred
+// differences of ln rho (one-sided at the bottom and top); ln rho is taken once per node, in the
+// loading pass, and 1/rho by the Newton reciprocal.
+constexpr int kBgTile = 16;
 __global__ void k_set_background(Grid G, int gamma_mode, const double* __restrict__ u, const double* __restrict__ v,
                                  const double* __restrict__ n2, const double* __restrict__ rho, Node* __restrict__ bg,
                                  double* __restrict__ rho_c, double* __restrict__ rho_inv, int* flags)
 {
-    extern __shared__ double sh[];   // 4 fields x nz x 32
-    const int TW = 32;
+    extern __shared__ double sh[];   // 5 arrays x nz x kBgTile: U, V, N^2, rho, ln rho
+    const int TW = kBgTile;
     const int nz = G.nz;
     const int ntx = (G.nx + TW - 1) / TW;
     const int j = blockIdx.x / ntx, i0 = (blockIdx.x % ntx) * TW;
@@ -29,6 +37,7 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
     double* sv = sh + nz * TW;
     double* sn = sh + 2 * nz * TW;
     double* sr = sh + 3 * nz * TW;
+    double* sl = sh + 4 * nz * TW;
     int bad = 0;
     for (int t = threadIdx.x; t < nz * TW; t += blockDim.x) {
         const int ii = t % TW, k = t / TW, i = i0 + ii;
@@ -39,8 +48,9 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
         sv[k * TW + ii] = b;
         sn[k * TW + ii] = c;
         sr[k * TW + ii] = d;
-        if (!(isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d))) bad |= BG_NONFINITE;
+        if (nonfinite_bits(a) || nonfinite_bits(b) || nonfinite_bits(c) || nonfinite_bits(d)) bad |= BG_NONFINITE;
         else if (!(d > 0.0)) bad |= BG_RHO;
+        sl[k * TW + ii] = (gamma_mode && d > 0.0) ? log(d) : 0.0;
     }
     __syncthreads();
     double f2 = G.f0 * G.f0;
@@ -48,81 +58,102 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
         const double f = 2.0 * G.omega * sin(row_lat(G, j));
         f2 = f * f;
     }
+    const double h1 = G.inv_dz, h2 = 0.5 * G.inv_dz;
     for (int t = threadIdx.x; t < nz * TW; t += blockDim.x) {
         const int k = t % nz, ii = t / nz, i = i0 + ii;
         if (i >= G.nx) continue;
         double g2 = 0.0;
         if (gamma_mode) {
             double dl;
-            if (k == 0) dl = (log(sr[1 * TW + ii]) - log(sr[ii])) / G.dz;
-            else if (k == nz - 1) dl = (log(sr[(nz - 1) * TW + ii]) - log(sr[(nz - 2) * TW + ii])) / G.dz;
-            else dl = (log(sr[(k + 1) * TW + ii]) - log(sr[(k - 1) * TW + ii])) / (2.0 * G.dz);
+            if (k == 0) dl = (sl[1 * TW + ii] - sl[ii]) * h1;
+            else if (k == nz - 1) dl = (sl[(nz - 1) * TW + ii] - sl[(nz - 2) * TW + ii]) * h1;
+            else dl = (sl[(k + 1) * TW + ii] - sl[(k - 1) * TW + ii]) * h2;
             g2 = 0.25 * dl * dl;
         }
         const double nn = sn[k * TW + ii];
         if (!(nn > f2)) bad |= BG_N2F2;
         const int64_t c = node_index(G, i, j, k);
-        Node& nd = bg[c];
-        nd.v[0] = su[k * TW + ii];
-        nd.v[1] = sv[k * TW + ii];
-        nd.v[2] = nn;
-        nd.v[3] = g2;
-        rho_c[c] = sr[k * TW + ii];
-        rho_inv[c] = 1.0 / sr[k * TW + ii];
+        double4* nv = reinterpret_cast<double4*>(bg[c].v);
+        *nv = make_double4(su[k * TW + ii], sv[k * TW + ii], nn, g2);
+        const double r = sr[k * TW + ii];
+        rho_c[c] = r;
+        rho_inv[c] = r > 0.0 ? rcp_nr(r) : 0.0;
     }
     if (bad) atomicOr(flags, bad);
 }
 
-// node gradients by centred differences: periodic in x (and y on the f-plane), one-sided at the
-// pole rows and at the bottom and top levels
-__global__ void k_node_gradients(Grid G, Node* __restrict__ bg)
+// Node gradients by centred differences: periodic in x (and y on the f-plane), one-sided at the
+// pole rows and at the bottom and top levels.  The same pass writes the per-step gather copies of
+// the node: double-float pairs (FP64 form, bgdf) or FP32 (precision form, bg32), whichever is given.
+__global__ void k_node_gradients(Grid G, Node* __restrict__ bg, NodeDF* __restrict__ bgdf, Node32* __restrict__ bg32)
 {
     const int64_t total = (int64_t)G.ncell;
+    const double sx = 0.5 * G.inv_dX;
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(c % G.nz);
         const int col = (int)(c / G.nz);
         const int i = col % G.nx, j = col / G.nx;
-        const Node* e = bg + node_index(G, wrap_int(i + 1, G.nx), j, k);
-        const Node* w = bg + node_index(G, wrap_int(i - 1, G.nx), j, k);
+        const Node* e = bg + node_index(G, i + 1 == G.nx ? 0 : i + 1, j, k);
+        const Node* w = bg + node_index(G, i == 0 ? G.nx - 1 : i - 1, j, k);
         const Node *nn, *ss;
         double sy;
         if (G.geometry == 0) {
-            nn = bg + node_index(G, i, wrap_int(j + 1, G.ny), k);
-            ss = bg + node_index(G, i, wrap_int(j - 1, G.ny), k);
-            sy = 1.0 / (2.0 * G.dY);
+            nn = bg + node_index(G, i, j + 1 == G.ny ? 0 : j + 1, k);
+            ss = bg + node_index(G, i, j == 0 ? G.ny - 1 : j - 1, k);
+            sy = 0.5 * G.inv_dY;
         } else if (j == 0) {
             nn = bg + node_index(G, i, 1, k);
             ss = bg + node_index(G, i, 0, k);
-            sy = 1.0 / G.dY;
+            sy = G.inv_dY;
         } else if (j == G.ny - 1) {
             nn = bg + node_index(G, i, G.ny - 1, k);
             ss = bg + node_index(G, i, G.ny - 2, k);
-            sy = 1.0 / G.dY;
+            sy = G.inv_dY;
         } else {
             nn = bg + node_index(G, i, j + 1, k);
             ss = bg + node_index(G, i, j - 1, k);
-            sy = 1.0 / (2.0 * G.dY);
+            sy = 0.5 * G.inv_dY;
         }
         const Node *up, *dn;
         double sz;
         if (k == 0) {
-            up = bg + c + 1; dn = bg + c; sz = 1.0 / G.dz;
+            up = bg + c + 1; dn = bg + c; sz = G.inv_dz;
         } else if (k == G.nz - 1) {
-            up = bg + c; dn = bg + c - 1; sz = 1.0 / G.dz;
+            up = bg + c; dn = bg + c - 1; sz = G.inv_dz;
         } else {
-            up = bg + c + 1; dn = bg + c - 1; sz = 1.0 / (2.0 * G.dz);
+            up = bg + c + 1; dn = bg + c - 1; sz = 0.5 * G.inv_dz;
         }
-        double d[4][3];
+        auto vals = [](const Node* p) { return *reinterpret_cast<const double4*>(p->v); };
+        const double4 ve = vals(e), vw = vals(w), vn = vals(nn), vs = vals(ss), vu = vals(up), vd = vals(dn),
+                      vc = vals(bg + c);
+        const double q[16] = {vc.x, vc.y, vc.z, vc.w,
+                              (ve.x - vw.x) * sx, (vn.x - vs.x) * sy, (vu.x - vd.x) * sz,
+                              (ve.y - vw.y) * sx, (vn.y - vs.y) * sy, (vu.y - vd.y) * sz,
+                              (ve.z - vw.z) * sx, (vn.z - vs.z) * sy, (vu.z - vd.z) * sz,
+                              (ve.w - vw.w) * sx, (vn.w - vs.w) * sy, (vu.w - vd.w) * sz};
+        double4* gd = reinterpret_cast<double4*>(bg[c].d[0]);
+        gd[0] = make_double4(q[4], q[5], q[6], q[7]);
+        gd[1] = make_double4(q[8], q[9], q[10], q[11]);
+        gd[2] = make_double4(q[12], q[13], q[14], q[15]);
+        if (bgdf) {
+            NodeDF o;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            d[f][0] = (e->v[f] - w->v[f]) / (2.0 * G.dX);
-            d[f][1] = (nn->v[f] - ss->v[f]) * sy;
-            d[f][2] = (up->v[f] - dn->v[f]) * sz;
+            for (int el = 0; el < 8; ++el) {
+                const DF a = df_split(q[2 * el]), b = df_split(q[2 * el + 1]);
+                o.q[el] = make_float4(a.hi, a.lo, b.hi, b.lo);
+            }
+            bgdf[c] = o;
         }
+        if (bg32) {
+            Node32 o;
 #pragma unroll
-        for (int f = 0; f < 4; ++f)
+            for (int f = 0; f < 4; ++f) {
+                o.v[f] = narrow(q[f]);
 #pragma unroll
-            for (int q = 0; q < 3; ++q) bg[c].d[f][q] = d[f][q];
+                for (int d = 0; d < 3; ++d) o.d[f][d] = narrow(q[4 + 3 * f + d]);
+            }
+            bg32[c] = o;
+        }
     }
 }
 
@@ -134,14 +165,15 @@ void configure_launch_kernels()
 void launch_set_background(Context& c, int member, const double* u, const double* v, const double* n2,
                            const double* rho)
 {
-    const int TW = 32;
+    const int TW = kBgTile;
     const int ntx = (c.G.nx + TW - 1) / TW;
-    const size_t shm = sizeof(double) * 4 * (size_t)c.G.nz * TW;
+    const size_t shm = sizeof(double) * 5 * (size_t)c.G.nz * TW;
     const int64_t o = (int64_t)member * c.G.ncell;
     k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg + o,
                                                                 c.rho + o, c.rho_inv + o, c.flag_dev);
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
-    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o);
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.f32 ? nullptr : c.bgdf + o,
+                                                        c.f32 ? c.bg32 + o : nullptr);
 }
 
 // ----------------------------------------------------------------------------- explicit rays
