@@ -242,6 +242,11 @@ int gwam_selftest_widen(const float *x, int64_t n, double *widened, double *acti
 /* Self-test of the integer double -> float narrowing (round to nearest even): out[i] must equal the
  * hardware conversion bit for bit (subnormal results, overflow to infinity, NaN classes included). */
 int gwam_selftest_narrow(const double *x, int64_t n, float *out, void *stream);
+/* Self-test of the double-float logarithm of a ratio that forms Gamma^2 = (d ln rho / dz)^2 / 4 from
+ * centred differences of ln rho (Sec. 2a; the differences are taken as ln(rho_up / rho_down)):
+ * out[i] = ln(a[i] / b[i]) for positive normal doubles a, b, relative error about 2^-45 (exactly 0
+ * when a == b).  Device pointers; synchronises `stream`. */
+int gwam_selftest_logratio(const double *a, const double *b, int64_t n, double *out, void *stream);
 
 /* Self-test of the surrogate's tensor-core GEMM (tcgen05 + TMA, sm_103a): C = act(A . B^T + bias)
  * with A [M][K] and B [N][K] row-major BF16 device arrays (K contiguous, K a multiple of 64, base

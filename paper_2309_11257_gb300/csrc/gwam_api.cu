@@ -196,13 +196,15 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             // row and level tables (host-computed once)
             // split thresholds per row (App. B.3) after the row-centre latitudes: alpha_s sqrt(cos dX dY),
             // alpha_s cos dX dY (cos = 1 on the f-plane), evaluated left to right as the oracle does
-            const size_t o_thr = 3 * (size_t)G.ny + G.nz;
-            std::vector<double> tab(o_thr + 2 * (size_t)G.ny);
+            const size_t o_thr = 3 * (size_t)G.ny + G.nz, o_f2 = o_thr + 2 * (size_t)G.ny;
+            std::vector<double> tab(o_f2 + G.ny);
             for (int j = 0; j < G.ny; ++j) {
                 const double phi = G.y0 + (j + 0.5) * G.dY;
                 tab[j] = G.geometry == 1 ? cos(phi) : 1.0;
                 tab[G.ny + j] = 1.0 / tab[j];
                 tab[2 * (size_t)G.ny + G.nz + j] = phi;   // row-centre latitude
+                const double f = G.geometry == 1 ? 2.0 * G.omega * sin(phi) : G.f0;
+                tab[o_f2 + j] = f * f;
                 if (G.geometry == 1) {
                     tab[o_thr + 2 * j] = P.alpha_s * sqrt(tab[j] * G.dX * G.dY);
                     tab[o_thr + 2 * j + 1] = P.alpha_s * tab[j] * G.dX * G.dY;
@@ -221,6 +223,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.lev_inv_r = c.tables + 2 * G.ny;
             G.row_lat = c.tables + 2 * G.ny + G.nz;
             G.split_thr = c.tables + o_thr;
+            G.row_f2 = c.tables + o_f2;
             std::vector<float> t32(2 * (size_t)G.ny + (size_t)G.ny * G.nz);
             for (int j = 0; j < G.ny; ++j) {
                 t32[j] = (float)tab[j];

@@ -85,6 +85,7 @@ struct Grid {
     // split_thr[2 j] = alpha_s sqrt(cos(phi_j) dX dY), split_thr[2 j + 1] = alpha_s cos(phi_j) dX dY
     const double* split_thr;
     double split_hthr;          // max(alpha_s dz, min_split_dz)
+    const double* row_f2;       // [ny]: f^2 of every row centre (f0^2 on the f-plane)
 };
 
 struct Params {
@@ -132,11 +133,11 @@ __device__ __forceinline__ void store_ray(const RaySoA& R, int64_t i, const doub
 }
 
 // Background nodes at cell centres, column-major: node (i, j, k) at (j*nx + i)*nz + k.
-// Each node holds U, V, N^2, Gamma^2 and their gradients along X, Y, z (centred differences),
-// 128 bytes: the quantities the ray equations interpolate (Sec. 3b, App. B.1).
-struct __align__(128) Node {
+// The FP64 node holds U, V, N^2, Gamma^2 (32 bytes); the per-step gathers of the ray equations read
+// the copies that also carry the node gradients (NodeDF of the FP64 form, Node32 of the precision
+// form), written when the background is set (Sec. 3b, App. B.1).
+struct __align__(32) Node {
     double v[4];       // U, V, N^2, Gamma^2
-    double d[4][3];    // d/dX, d/dY, d/dz of each
 };
 
 // FP32 background node of the precision form: the same 16 quantities in FP32 (64 bytes)
@@ -227,20 +228,9 @@ __device__ __forceinline__ void accumulate_node_df(const NodeDF* __restrict__ p,
     }
 }
 
-__device__ __forceinline__ void accumulate_node(const Node* __restrict__ p, double w, double* acc)
-{
-    const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const double2 a = __ldg(q + e);
-        acc[2 * e] += w * a.x;
-        acc[2 * e + 1] += w * a.y;
-    }
-}
-
-// Trilinear interpolation of the node values and node gradients to (X, Y, Z).
-__device__ __forceinline__ void gather_fp64(const Grid& G, const Node* __restrict__ bg, double X, double Y, double Z,
-                                            Bg& b)
+// Trilinear interpolation of the FP64 node values (U, V, N^2, Gamma^2) to (X, Y, Z).
+__device__ __forceinline__ void gather_values_fp64(const Grid& G, const Node* __restrict__ bg, double X, double Y,
+                                                   double Z, double v[4])
 {
     int i0, i1, j0, j1, k0, k1;
     double tx, ty, tz;
@@ -248,68 +238,23 @@ __device__ __forceinline__ void gather_fp64(const Grid& G, const Node* __restric
     if (G.geometry == 1) bracket_clamped((Y - G.y0) * G.inv_dY - 0.5, G.ny, j0, j1, ty);
     else bracket_periodic(Y * G.inv_dY - 0.5, G.ny, G.inv_ny, j0, j1, ty);
     bracket_clamped(Z * G.inv_dz - 0.5, G.nz, k0, k1, tz);
-    double acc[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = 0.0;
     const double ux = 1.0 - tx, uy = 1.0 - ty, uz = 1.0 - tz;
     const int dk = k1 - k0;
-    const Node* c00 = bg + node_index(G, i0, j0, k0);
-    const Node* c10 = bg + node_index(G, i1, j0, k0);
-    const Node* c01 = bg + node_index(G, i0, j1, k0);
-    const Node* c11 = bg + node_index(G, i1, j1, k0);
-    accumulate_node(c00, ux * uy * uz, acc);
-    accumulate_node(c00 + dk, ux * uy * tz, acc);
-    accumulate_node(c10, tx * uy * uz, acc);
-    accumulate_node(c10 + dk, tx * uy * tz, acc);
-    accumulate_node(c01, ux * ty * uz, acc);
-    accumulate_node(c01 + dk, ux * ty * tz, acc);
-    accumulate_node(c11, tx * ty * uz, acc);
-    accumulate_node(c11 + dk, tx * ty * tz, acc);
+    const Node* cn[4] = {bg + node_index(G, i0, j0, k0), bg + node_index(G, i1, j0, k0),
+                         bg + node_index(G, i0, j1, k0), bg + node_index(G, i1, j1, k0)};
+    const double wc[4] = {ux * uy, tx * uy, ux * ty, tx * ty};
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        b.v[f] = acc[f];
+    for (int f = 0; f < 4; ++f) v[f] = 0.0;
 #pragma unroll
-        for (int q = 0; q < 3; ++q) b.d[f][q] = acc[4 + 3 * f + q];
-    }
-}
-
-// Trilinear interpolation of the node values and node gradients to (X, Y, Z), as gather_fp64, with
-// the weights and the 8-corner sums in double-float (about 2^-47 relative to the sum of |terms|);
-// only the bracketing (3 axes) and the 16 results use FP64 operations.
-__device__ __forceinline__ void gather(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
-                                       Bg& b)
-{
-    int i0, i1, j0, j1, k0, k1;
-    double tx, ty, tz;
-    bracket_periodic(X * G.inv_dX - 0.5, G.nx, G.inv_nx, i0, i1, tx);
-    if (G.geometry == 1) bracket_clamped((Y - G.y0) * G.inv_dY - 0.5, G.ny, j0, j1, ty);
-    else bracket_periodic(Y * G.inv_dY - 0.5, G.ny, G.inv_ny, j0, j1, ty);
-    bracket_clamped(Z * G.inv_dz - 0.5, G.nz, k0, k1, tz);
-    const DF one{1.0f, 0.0f};
-    const DF Tx = df_split(tx), Ty = df_split(ty), Tz = df_split(tz);
-    const DF Ux = df_add(one, {-Tx.hi, -Tx.lo}), Uy = df_add(one, {-Ty.hi, -Ty.lo}), Uz = df_add(one, {-Tz.hi, -Tz.lo});
-    const DF w00 = df_mul2(Ux, Uy), w10 = df_mul2(Tx, Uy), w01 = df_mul2(Ux, Ty), w11 = df_mul2(Tx, Ty);
-    float s[16], c[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) s[q] = c[q] = 0.0f;
-    const int dk = k1 - k0;
-    const NodeDF* c00 = bg + node_index(G, i0, j0, k0);
-    const NodeDF* c10 = bg + node_index(G, i1, j0, k0);
-    const NodeDF* c01 = bg + node_index(G, i0, j1, k0);
-    const NodeDF* c11 = bg + node_index(G, i1, j1, k0);
-    accumulate_node_df(c00, df_mul2(w00, Uz), s, c);
-    accumulate_node_df(c00 + dk, df_mul2(w00, Tz), s, c);
-    accumulate_node_df(c10, df_mul2(w10, Uz), s, c);
-    accumulate_node_df(c10 + dk, df_mul2(w10, Tz), s, c);
-    accumulate_node_df(c01, df_mul2(w01, Uz), s, c);
-    accumulate_node_df(c01 + dk, df_mul2(w01, Tz), s, c);
-    accumulate_node_df(c11, df_mul2(w11, Uz), s, c);
-    accumulate_node_df(c11 + dk, df_mul2(w11, Tz), s, c);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        b.v[f] = widen(s[f]) + widen(c[f]);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) b.d[f][q] = widen(s[4 + 3 * f + q]) + widen(c[4 + 3 * f + q]);
+    for (int q = 0; q < 8; ++q) {
+        const Node* p = cn[q >> 1] + ((q & 1) ? dk : 0);
+        const double w = wc[q >> 1] * ((q & 1) ? tz : uz);
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p->v));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p->v) + 1);
+        v[0] += w * a.x;
+        v[1] += w * a.y;
+        v[2] += w * b.x;
+        v[3] += w * b.y;
     }
 }
 
@@ -405,6 +350,20 @@ __device__ __forceinline__ void gather_df(const Grid& G, const NodeDF* __restric
         b.v[f] = df_norm(s[f], c[f]);
 #pragma unroll
         for (int q = 0; q < 3; ++q) b.d[f][q] = df_norm(s[4 + 3 * f + q], c[4 + 3 * f + q]);
+    }
+}
+
+// gather with FP64 results from the double-float nodes (saturation and cap paths of the FP64 form)
+__device__ __forceinline__ void gather(const Grid& G, const NodeDF* __restrict__ bg, double X, double Y, double Z,
+                                       Bg& b)
+{
+    float s[16], c[16];
+    gather_df_sums<0, 8>(G, bg, df_split(X), df_split(Y), df_split(Z), s, c);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        b.v[f] = widen(s[f]) + widen(c[f]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) b.d[f][q] = widen(s[4 + 3 * f + q]) + widen(c[4 + 3 * f + q]);
     }
 }
 

@@ -203,4 +203,53 @@ __device__ __forceinline__ DF df_split(double x)
     return {hi, narrow(x - widen(hi))};
 }
 
+// ln(a / b) for positive normal doubles, in double-float on the FP32 pipes.  a = 2^ea ma and
+// b = 2^eb mb with ma, mb in [1, 2) (exponent fields set by integer operations); mb is doubled when
+// ma / mb >= sqrt(2) and ma when ma / mb < sqrt(1/2), so that ma / mb lies in [sqrt(1/2), sqrt(2))
+// and a / b = 2^e ma / mb.
+// Then ln(ma / mb) = 2 atanh(s), s = (ma - mb) / (ma + mb), |s| < 0.172 (the difference is exact
+// in FP64: ma and mb lie within a factor of two), from the series
+// ln = 2 s (1 + s^2/3 + s^4/5 + ...) (Abramowitz & Stegun 4.1.27): the terms to s^8/9 in DF,
+// s^10/11 ... s^20/21 in FP32 (each below 2e-9 of the sum), truncated after s^20/21 (the next term is
+// below 1e-18); e ln 2 with ln 2 as a DF constant.  Relative error about 2^-45: logarithms of
+// ratios near one keep their relative precision.
+__device__ __forceinline__ DF df_log_ratio(double a, double b)
+{
+    const int ha = __double2hiint(a), hb = __double2hiint(b);
+    int e = ((ha >> 20) & 0x7FF) - ((hb >> 20) & 0x7FF);
+    double ma = __hiloint2double((ha & 0x800FFFFF) | 0x3FF00000, __double2loint(a));
+    double mb = __hiloint2double((hb & 0x800FFFFF) | 0x3FF00000, __double2loint(b));
+    // ma / mb in (1/2, 2): the leading mantissa bits decide (either side of a boundary is accurate)
+    const float fa = __int_as_float(((ha & 0x000FFFFF) << 3) | 0x3F800000);
+    const float fb = __int_as_float(((hb & 0x000FFFFF) << 3) | 0x3F800000);
+    if (fa >= 1.41421356f * fb) {
+        mb = __hiloint2double(__double2hiint(mb) + 0x00100000, __double2loint(mb));   // 2 mb
+        e += 1;
+    } else if (fa * 1.41421356f < fb) {
+        ma = __hiloint2double(__double2hiint(ma) + 0x00100000, __double2loint(ma));   // 2 ma
+        e -= 1;
+    }
+    const DF num = df_split(ma - mb), den = df_split(ma + mb);
+    float d0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(d0) : "f"(den.hi));
+    const DF id1 = df_add(df_f(d0), df_mul(df_sub(df_f(1.0f), df_mul(den, d0)), d0));
+    const DF id = df_add(id1, df_mul2(df_sub(df_f(1.0f), df_mul2(den, id1)), id1));
+    const DF t = df_mul2(num, id);
+    const DF t2 = df_mul2(t, t);
+    const float z = t2.hi;
+    const float tail = 1.0f / 11.0f + z * (1.0f / 13.0f + z * (1.0f / 15.0f + z * (1.0f / 17.0f + z * (1.0f / 19.0f + z * (1.0f / 21.0f)))));
+    constexpr DF c3{1.0f / 3.0f, (float)(1.0 / 3.0 - (double)(1.0f / 3.0f))};
+    constexpr DF c5{1.0f / 5.0f, (float)(1.0 / 5.0 - (double)(1.0f / 5.0f))};
+    constexpr DF c7{1.0f / 7.0f, (float)(1.0 / 7.0 - (double)(1.0f / 7.0f))};
+    constexpr DF c9{1.0f / 9.0f, (float)(1.0 / 9.0 - (double)(1.0f / 9.0f))};
+    constexpr DF ln2{0.693147182f, (float)(0.69314718055994530942 - (double)0.693147182f)};
+    DF p = df_add(c9, df_mul(t2, tail));
+    p = df_add(c7, df_mul2(t2, p));
+    p = df_add(c5, df_mul2(t2, p));
+    p = df_add(c3, df_mul2(t2, p));
+    p = df_add(df_f(1.0f), df_mul2(t2, p));
+    const DF lnm = df_mul2(df_pow2(t, 2.0f), p);
+    return df_add(df_mul(ln2, (float)e), lnm);
+}
+
 }  // namespace gwam

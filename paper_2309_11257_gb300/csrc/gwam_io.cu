@@ -93,7 +93,25 @@ __global__ void k_selftest_narrow(const double* __restrict__ x, int64_t n, float
         out[i] = narrow(x[i]);
 }
 
+__global__ void k_selftest_logratio(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                                    double* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = df_to_double(df_log_ratio(a[i], b[i]));
+}
+
 }  // namespace gwam
+
+extern "C" int gwam_selftest_logratio(const double* a, const double* b, int64_t n, double* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!a || !b || !out))) return GWAM_EINVAL;
+    if (n == 0) return GWAM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>((n + gwam::kThreads - 1) / gwam::kThreads, 4096);
+    gwam::k_selftest_logratio<<<blocks, gwam::kThreads, 0, s>>>(a, b, n, out);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GWAM_ECUDA;
+    return GWAM_OK;
+}
 
 extern "C" int gwam_selftest_narrow(const double* x, int64_t n, float* out, void* stream)
 {

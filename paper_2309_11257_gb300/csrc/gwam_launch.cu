@@ -21,14 +21,15 @@ __device__ __forceinline__ bool nonfinite_bits(double x)
 
 // caller [nz][ny][nx] -> column-major node values (U, V, N^2, Gamma^2) and rho, transposed through
 // shared memory (kBgTile columns of a row per block).  Gamma^2 = (d ln rho / dz)^2 / 4 by centred
-// differences of ln rho (one-sided at the bottom and top); ln rho is taken once per node, in the
-// loading pass, and 1/rho by the Newton reciprocal.
+// differences of ln rho (one-sided at the bottom and top), each difference taken as the logarithm of
+// the density ratio in double-float (df_log_ratio); 1/rho by the Newton reciprocal; f^2 of the row
+// from the host table.
 constexpr int kBgTile = 16;
 __global__ void k_set_background(Grid G, int gamma_mode, const double* __restrict__ u, const double* __restrict__ v,
                                  const double* __restrict__ n2, const double* __restrict__ rho, Node* __restrict__ bg,
                                  double* __restrict__ rho_c, double* __restrict__ rho_inv, int* flags)
 {
-    extern __shared__ double sh[];   // 5 arrays x nz x kBgTile: U, V, N^2, rho, ln rho
+    extern __shared__ double sh[];   // 4 arrays x nz x kBgTile: U, V, N^2, rho
     const int TW = kBgTile;
     const int nz = G.nz;
     const int ntx = (G.nx + TW - 1) / TW;
@@ -37,7 +38,6 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
     double* sv = sh + nz * TW;
     double* sn = sh + 2 * nz * TW;
     double* sr = sh + 3 * nz * TW;
-    double* sl = sh + 4 * nz * TW;
     int bad = 0;
     for (int t = threadIdx.x; t < nz * TW; t += blockDim.x) {
         const int ii = t % TW, k = t / TW, i = i0 + ii;
@@ -49,35 +49,33 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
         sn[k * TW + ii] = c;
         sr[k * TW + ii] = d;
         if (nonfinite_bits(a) || nonfinite_bits(b) || nonfinite_bits(c) || nonfinite_bits(d)) bad |= BG_NONFINITE;
-        else if (!(d > 0.0)) bad |= BG_RHO;
-        sl[k * TW + ii] = (gamma_mode && d > 0.0) ? log(d) : 0.0;
+        else if (__double_as_longlong(d) <= 0) bad |= BG_RHO;   // rho <= 0 (or -0)
     }
     __syncthreads();
-    double f2 = G.f0 * G.f0;
-    if (G.geometry == 1) {
-        const double f = 2.0 * G.omega * sin(row_lat(G, j));
-        f2 = f * f;
-    }
-    const double h1 = G.inv_dz, h2 = 0.5 * G.inv_dz;
+    const double f2 = G.row_f2[j];
+    const DF h1{G.df_inv_dz.x, G.df_inv_dz.y};
+    const DF h2 = df_pow2(h1, 0.5f);
     for (int t = threadIdx.x; t < nz * TW; t += blockDim.x) {
         const int k = t % nz, ii = t / nz, i = i0 + ii;
         if (i >= G.nx) continue;
+        const double r = sr[k * TW + ii];
+        const bool rok = __double_as_longlong(r) > 0 && !nonfinite_bits(r);
         double g2 = 0.0;
         if (gamma_mode) {
-            double dl;
-            if (k == 0) dl = (sl[1 * TW + ii] - sl[ii]) * h1;
-            else if (k == nz - 1) dl = (sl[(nz - 1) * TW + ii] - sl[(nz - 2) * TW + ii]) * h1;
-            else dl = (sl[(k + 1) * TW + ii] - sl[(k - 1) * TW + ii]) * h2;
-            g2 = 0.25 * dl * dl;
+            const int ku = k == nz - 1 ? k : k + 1, kd = k == 0 ? 0 : k - 1;
+            const double ru = sr[ku * TW + ii], rd = sr[kd * TW + ii];
+            if (rok && __double_as_longlong(ru) > 0 && __double_as_longlong(rd) > 0 && !nonfinite_bits(ru) &&
+                !nonfinite_bits(rd)) {
+                const DF dl = df_mul2(df_log_ratio(ru, rd), (k == 0 || k == nz - 1) ? h1 : h2);
+                g2 = df_to_double(df_pow2(df_mul2(dl, dl), 0.25f));
+            }
         }
         const double nn = sn[k * TW + ii];
         if (!(nn > f2)) bad |= BG_N2F2;
         const int64_t c = node_index(G, i, j, k);
-        double4* nv = reinterpret_cast<double4*>(bg[c].v);
-        *nv = make_double4(su[k * TW + ii], sv[k * TW + ii], nn, g2);
-        const double r = sr[k * TW + ii];
+        *reinterpret_cast<double4*>(bg[c].v) = make_double4(su[k * TW + ii], sv[k * TW + ii], nn, g2);
         rho_c[c] = r;
-        rho_inv[c] = r > 0.0 ? rcp_nr(r) : 0.0;
+        rho_inv[c] = rok ? rcp_nr(r) : 0.0;
     }
     if (bad) atomicOr(flags, bad);
 }
@@ -88,7 +86,8 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
 __global__ void k_node_gradients(Grid G, Node* __restrict__ bg, NodeDF* __restrict__ bgdf, Node32* __restrict__ bg32)
 {
     const int64_t total = (int64_t)G.ncell;
-    const double sx = 0.5 * G.inv_dX;
+    const DF idx{G.df_inv_dX.x, G.df_inv_dX.y}, idy{G.df_inv_dY.x, G.df_inv_dY.y}, idz{G.df_inv_dz.x, G.df_inv_dz.y};
+    const DF sx = df_pow2(idx, 0.5f);
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < total; c += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(c % G.nz);
         const int col = (int)(c / G.nz);
@@ -96,61 +95,63 @@ __global__ void k_node_gradients(Grid G, Node* __restrict__ bg, NodeDF* __restri
         const Node* e = bg + node_index(G, i + 1 == G.nx ? 0 : i + 1, j, k);
         const Node* w = bg + node_index(G, i == 0 ? G.nx - 1 : i - 1, j, k);
         const Node *nn, *ss;
-        double sy;
+        DF sy;
         if (G.geometry == 0) {
             nn = bg + node_index(G, i, j + 1 == G.ny ? 0 : j + 1, k);
             ss = bg + node_index(G, i, j == 0 ? G.ny - 1 : j - 1, k);
-            sy = 0.5 * G.inv_dY;
+            sy = df_pow2(idy, 0.5f);
         } else if (j == 0) {
             nn = bg + node_index(G, i, 1, k);
             ss = bg + node_index(G, i, 0, k);
-            sy = G.inv_dY;
+            sy = idy;
         } else if (j == G.ny - 1) {
             nn = bg + node_index(G, i, G.ny - 1, k);
             ss = bg + node_index(G, i, G.ny - 2, k);
-            sy = G.inv_dY;
+            sy = idy;
         } else {
             nn = bg + node_index(G, i, j + 1, k);
             ss = bg + node_index(G, i, j - 1, k);
-            sy = 0.5 * G.inv_dY;
+            sy = df_pow2(idy, 0.5f);
         }
         const Node *up, *dn;
-        double sz;
+        DF sz;
         if (k == 0) {
-            up = bg + c + 1; dn = bg + c; sz = G.inv_dz;
+            up = bg + c + 1; dn = bg + c; sz = idz;
         } else if (k == G.nz - 1) {
-            up = bg + c; dn = bg + c - 1; sz = G.inv_dz;
+            up = bg + c; dn = bg + c - 1; sz = idz;
         } else {
-            up = bg + c + 1; dn = bg + c - 1; sz = 0.5 * G.inv_dz;
+            up = bg + c + 1; dn = bg + c - 1; sz = df_pow2(idz, 0.5f);
         }
         auto vals = [](const Node* p) { return *reinterpret_cast<const double4*>(p->v); };
         const double4 ve = vals(e), vw = vals(w), vn = vals(nn), vs = vals(ss), vu = vals(up), vd = vals(dn),
                       vc = vals(bg + c);
-        const double q[16] = {vc.x, vc.y, vc.z, vc.w,
-                              (ve.x - vw.x) * sx, (vn.x - vs.x) * sy, (vu.x - vd.x) * sz,
-                              (ve.y - vw.y) * sx, (vn.y - vs.y) * sy, (vu.y - vd.y) * sz,
-                              (ve.z - vw.z) * sx, (vn.z - vs.z) * sy, (vu.z - vd.z) * sz,
-                              (ve.w - vw.w) * sx, (vn.w - vs.w) * sy, (vu.w - vd.w) * sz};
-        double4* gd = reinterpret_cast<double4*>(bg[c].d[0]);
-        gd[0] = make_double4(q[4], q[5], q[6], q[7]);
-        gd[1] = make_double4(q[8], q[9], q[10], q[11]);
-        gd[2] = make_double4(q[12], q[13], q[14], q[15]);
+        // differences in FP64 (one rounding), scaled in double-float by the spacing reciprocals
+        const double dx[4] = {ve.x - vw.x, ve.y - vw.y, ve.z - vw.z, ve.w - vw.w};
+        const double dy[4] = {vn.x - vs.x, vn.y - vs.y, vn.z - vs.z, vn.w - vs.w};
+        const double dz[4] = {vu.x - vd.x, vu.y - vd.y, vu.z - vd.z, vu.w - vd.w};
+        const double val[4] = {vc.x, vc.y, vc.z, vc.w};
+        DF q[16];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            q[f] = df_split(val[f]);
+            q[4 + 3 * f] = df_mul2(df_split(dx[f]), sx);
+            q[5 + 3 * f] = df_mul2(df_split(dy[f]), sy);
+            q[6 + 3 * f] = df_mul2(df_split(dz[f]), sz);
+        }
         if (bgdf) {
             NodeDF o;
 #pragma unroll
-            for (int el = 0; el < 8; ++el) {
-                const DF a = df_split(q[2 * el]), b = df_split(q[2 * el + 1]);
-                o.q[el] = make_float4(a.hi, a.lo, b.hi, b.lo);
-            }
+            for (int el = 0; el < 8; ++el) o.q[el] = make_float4(q[2 * el].hi, q[2 * el].lo, q[2 * el + 1].hi, q[2 * el + 1].lo);
             bgdf[c] = o;
         }
         if (bg32) {
+            // the FP32 node: each quantity rounded once to nearest (hi + lo rounded as a pair)
             Node32 o;
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
-                o.v[f] = narrow(q[f]);
+                o.v[f] = narrow(val[f]);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) o.d[f][d] = narrow(q[4 + 3 * f + d]);
+                for (int d = 0; d < 3; ++d) o.d[f][d] = __fadd_rn(q[4 + 3 * f + d].hi, q[4 + 3 * f + d].lo);
             }
             bg32[c] = o;
         }
@@ -167,7 +168,7 @@ void launch_set_background(Context& c, int member, const double* u, const double
 {
     const int TW = kBgTile;
     const int ntx = (c.G.nx + TW - 1) / TW;
-    const size_t shm = sizeof(double) * 5 * (size_t)c.G.nz * TW;
+    const size_t shm = sizeof(double) * 4 * (size_t)c.G.nz * TW;
     const int64_t o = (int64_t)member * c.G.ncell;
     k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg + o,
                                                                 c.rho + o, c.rho_inv + o, c.flag_dev);
@@ -288,7 +289,7 @@ __device__ __forceinline__ int make_launch(const Grid& G, const Node* __restrict
     const double Y = row_lat(G, b.j);
     const double Z = b.z_launch + 0.5 * b.dz_launch;
     Bg bk;
-    gather_fp64(G, bg, X, Y, Z, bk);
+    gather_values_fp64(G, bg, X, Y, Z, bk.v);
     Geo g;
     geometry_at(G, Y, Z, g);
     double f2, df2;

@@ -115,6 +115,7 @@ SIGNATURES = {
     "gwam_selftest_math": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_selftest_widen": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_selftest_narrow": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+    "gwam_selftest_logratio": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "gwam_gemm_bf16": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "gwam_mlp_create": (C.c_int, [_P(_vp), _P(MlpConfig), _vp]),
     "gwam_mlp_destroy": (None, [_vp]),

@@ -100,3 +100,33 @@ def test_integer_narrowing_matches_the_hardware_conversion():
     nan = np.isnan(allx)
     np.testing.assert_array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
     assert np.isnan(got[nan]).all()
+
+
+def test_double_float_log_ratio():
+    """ln(a/b) in double-float (atanh series after range reduction, as used for the Gamma^2
+    differences) against numpy's FP64 logarithms: ratios across 70 decades, near 1, exactly 1 and
+    at powers of two; relative error within 2^-44 (exactly 0 for a == b)."""
+    import torch
+    from paper_2309_11257_gb300 import build
+    build.build()
+    from paper_2309_11257_gb300 import gwam
+    rng = np.random.default_rng(8)
+    b = 10.0 ** rng.uniform(-30, 30, 200_000)
+    r = np.concatenate([10.0 ** rng.uniform(-35, 35, 100_000), np.exp(rng.uniform(-0.5, 0.5, 80_000)),
+                        1.0 + rng.uniform(-1e-9, 1e-9, 10_000), 2.0 ** rng.integers(-100, 100, 9_998).astype(float),
+                        np.array([1.0, np.sqrt(2.0)])])
+    a = b * r
+    ad, bd = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    out = torch.empty(len(a), dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    assert gwam.lib().gwam_selftest_logratio(C.c_void_p(ad.data_ptr()), C.c_void_p(bd.data_ptr()), len(a),
+                                             C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream)) == 0
+    # FP64 reference: log1p of the exact difference over b near 1 (Sterbenz), log of the quotient
+    # elsewhere; both within a few 2^-53 of |ln(a/b)|
+    near = np.abs(a / b - 1.0) < 0.5
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ref = np.where(near, np.log1p((a - b) / b), np.log(a / np.where(near, 1.0, b)))
+    got = out.cpu().numpy()
+    tol = 2.0 ** -44 * np.abs(ref)
+    err = np.abs(got - ref)
+    assert np.all(err <= tol), (err / tol).max()

@@ -122,6 +122,23 @@ def test_sphere_parity_with_launches_caps_and_exits(gw):
     assert st["n_exited"] > 0 and st["n_capped"] > 0 and st["n_split_h"] > 0 and st["w_saturated"] > 0
 
 
+@pytest.mark.parametrize("geometry", ["sphere", "fplane"])
+def test_gamma2_matches_the_oracle(gw, geometry):
+    """Gamma^2 = (d ln rho / dz)^2 / 4 (Sec. 2a reading): the device forms the centred differences as
+    logarithms of density ratios in double-float; the oracle differences FP64 logarithms.  Same
+    nodes, relative 1e-12 (the ratio form is the better conditioned of the two)."""
+    if geometry == "sphere":
+        grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+        bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+    else:
+        w = synth.workload("fplane")
+        grid, bg = w["grid"], synth.perturbed(w["background"], tag=44)
+    T, O = _pair(gw, grid, dict(synth.DEFAULT_PARAMS), bg, 1000)
+    g, o = T.gamma2(), O.gamma2()
+    assert g.shape == o.shape
+    np.testing.assert_allclose(g, o, rtol=1e-12, atol=0)
+
+
 def test_spectral_launch_parity(gw):
     """Explicit spectral launches (convective-like source) incl. filtered bins."""
     grid = synth.sphere_grid(nx=36, ny=18, nz=30, dz=1000.0)
