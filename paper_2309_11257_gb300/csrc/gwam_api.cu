@@ -80,6 +80,25 @@ static void h2d(Context& c, void* dst, const void* src, size_t bytes)
     GWAM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c.stream));
 }
 
+// Device address of a page-locked, device-mapped host buffer [p, p + bytes) (kernels then read or
+// write it directly over the host link, without a staging copy), or null when any part of it is
+// pageable or unmapped.
+static void* mapped_host(const void* p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    const char* q = static_cast<const char*>(p);
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess || cudaPointerGetAttributes(&b, q + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
 }  // namespace gwam
 
 using namespace gwam;
@@ -368,9 +387,20 @@ static int set_background_impl(gwam_ctx* ctx, int member, const double* u, const
     const size_t nc = (size_t)c.G.ncell;
     const double* src[4] = {u, v, n2, rho};
     if (host) {
-        if (!c.bg_scratch) dalloc(c, c.bg_scratch, 4 * nc);
-        for (int q = 0; q < 4; ++q) h2d(c, c.bg_scratch + q * nc, src[q], sizeof(double) * nc);
-        for (int q = 0; q < 4; ++q) src[q] = c.bg_scratch + q * nc;
+        // page-locked caller buffers are read by the set-up kernel directly; pageable ones are staged
+        const double* mapped[4];
+        bool all = true;
+        for (int q = 0; q < 4; ++q) {
+            mapped[q] = static_cast<const double*>(mapped_host(src[q], sizeof(double) * nc));
+            all = all && mapped[q];
+        }
+        if (all) {
+            for (int q = 0; q < 4; ++q) src[q] = mapped[q];
+        } else {
+            if (!c.bg_scratch) dalloc(c, c.bg_scratch, 4 * nc);
+            for (int q = 0; q < 4; ++q) h2d(c, c.bg_scratch + q * nc, src[q], sizeof(double) * nc);
+            for (int q = 0; q < 4; ++q) src[q] = c.bg_scratch + q * nc;
+        }
     }
     const int m0 = member < 0 ? 0 : member, m1 = member < 0 ? c.G.members : member + 1;
     GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
@@ -537,10 +567,17 @@ int gwam_step_host(gwam_ctx* ctx, double dt, double* dudt_host, double* dvdt_hos
         c.err = "gwam_step_host: no background";
         return GWAM_ESTATE;
     }
-    run_step(c, dt, nullptr, nullptr);
     const size_t bytes = sizeof(double) * (size_t)c.G.ncell_all;
-    if (dudt_host) GWAM_CUDA(cudaMemcpyAsync(dudt_host, c.dudt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
-    if (dvdt_host) GWAM_CUDA(cudaMemcpyAsync(dvdt_host, c.dvdt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
+    // page-locked caller buffers receive du/dt, dv/dt straight from the divergence kernel
+    double* du_map = static_cast<double*>(mapped_host(dudt_host, bytes));
+    double* dv_map = static_cast<double*>(mapped_host(dvdt_host, bytes));
+    if (du_map && dv_map) {
+        run_step(c, dt, du_map, dv_map);
+    } else {
+        run_step(c, dt, nullptr, nullptr);
+        if (dudt_host) GWAM_CUDA(cudaMemcpyAsync(dudt_host, c.dudt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
+        if (dvdt_host) GWAM_CUDA(cudaMemcpyAsync(dvdt_host, c.dvdt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
+    }
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     GWAM_CUDA(cudaGetLastError());
     API_END

@@ -278,22 +278,31 @@ def test_edge_cases(gw):
 
 
 def test_host_entry_points_match_device_ones(gw):
-    """gwam_set_background_host / gwam_step_host (host buffers) give the device-path results."""
+    """gwam_set_background_host / gwam_step_host give the device-path results, both with pageable
+    host buffers (staged copies) and with page-locked ones (read and written by the kernels
+    directly)."""
     import torch
     w = synth.workload("fplane")
     grid, params = w["grid"], w["params"]
     rays = synth.fplane_rays(grid, 300, tag=12)
     outs = []
-    for host in (False, True):
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    for mode in ("device", "pageable", "pinned"):
+        host = mode != "device"
         T = gw.Tracer(grid, params, max_rays=4096)
-        if host:
+        if mode == "pageable":
             T.set_background(*w["background"])
+        elif mode == "pinned":
+            T.set_background(*[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in w["background"]])
         else:
             T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in w["background"]])
         T.add_rays(rays)
-        shape = (grid["nz"], grid["ny"], grid["nx"])
         if host:
-            du, dv = np.zeros(shape), np.zeros(shape)
+            if mode == "pinned":
+                du = torch.full(shape, np.nan, dtype=torch.float64).pin_memory().numpy()
+                dv = torch.full(shape, np.nan, dtype=torch.float64).pin_memory().numpy()
+            else:
+                du, dv = np.zeros(shape), np.zeros(shape)
             for _ in range(3):
                 T.step_host(300.0, du, dv)
         else:
@@ -302,7 +311,9 @@ def test_host_entry_points_match_device_ones(gw):
             for _ in range(3):
                 T.step(300.0, dud, dvd)
             du, dv = dud.cpu().numpy(), dvd.cpu().numpy()
-        outs.append((T.rays(), du, dv))
-    for n in oracle.STATE_NAMES:
-        np.testing.assert_array_equal(outs[0][0][n], outs[1][0][n])
-    assert level_error(outs[1][1], outs[0][1]) <= 1e-12
+        outs.append((T.rays(), np.array(du), np.array(dv)))
+    for o in outs[1:]:
+        for n in oracle.STATE_NAMES:
+            np.testing.assert_array_equal(outs[0][0][n], o[0][n])
+        assert level_error(o[1], outs[0][1]) <= 1e-12
+        assert level_error(o[2], outs[0][2]) <= 1e-12
