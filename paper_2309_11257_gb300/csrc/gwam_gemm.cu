@@ -114,13 +114,14 @@ __device__ __forceinline__ float gelu_grad(float z)
 // parameters arrive one per lane (lane j holds column nb + j) and are broadcast with shuffles, so
 // every lane of the warp must call this (rows >= M only skip the stores).  zz: the prefetched
 // pre-activations of EPI_BWD.
+template <int MODE>
 __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, float (&v)[32], const float* sbias,
                                       float ps, float pm, const float (&zz)[32], int rowmask, double& sq,
                                       uint32_t stg, int cc0)
 {
     const bool live = row < e.M;
     const bool full = nb + 32 <= e.N;
-    if (e.mode == EPI_BWD) {
+    if (MODE == EPI_BWD) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(zz[j]);
     } else {
@@ -136,7 +137,7 @@ __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, 
                 v[4 * qq + 3] += b.w;
             }
         }
-        if (e.mode == EPI_DRAG) {
+        if (MODE == EPI_DRAG) {
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const float sj = __shfl_sync(0xffffffffu, ps, j), mj = __shfl_sync(0xffffffffu, pm, j);
@@ -150,7 +151,7 @@ __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, 
             return;
         }
         if (!live) return;
-        if (e.mode == EPI_STORE) {
+        if (MODE == EPI_STORE) {
             if (e.z) {
                 float* p = e.z + (size_t)row * e.ldz + nb;
                 if (full && (e.ldz & 3) == 0) {
@@ -183,7 +184,7 @@ __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, 
         }
     }
     if (!live) return;
-    if (e.mode == EPI_STORE && e.cf) {
+    if (MODE == EPI_STORE && e.cf) {
         float* p = e.cf + (size_t)z * e.cf_slice + (size_t)row * e.ldcf + nb;
         if (full && (e.ldcf & 3) == 0) {
 #pragma unroll
@@ -242,7 +243,7 @@ __device__ __forceinline__ void epi32(const GemmEpi& e, int z, int row, int nb, 
 // i + 1 run into the other one.  Epilogue warp w reads TMEM lane quarter w % 4 and, with EPW / 4
 // warps per quarter, its share of the columns.  Tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
 // over (k slice, m tile, n tile), n fastest.
-template <int BN, int ST, int EPW>
+template <int BN, int ST, int EPW, int MODE>
 __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                 const __grid_constant__ CUtensorMap tc, int K, int ksplit, GemmEpi e)
@@ -407,10 +408,10 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
 #pragma unroll
             for (int k = 0; k < kChunks; ++k) {
                 const int n = cbeg + 32 * k + lane;
-                ps[k] = (e.mode == EPI_DRAG && n < e.n_true) ? e.ysig[n] : 0.0f;
-                pm[k] = (e.mode == EPI_DRAG && n < e.n_true) ? e.ymu[n] : 0.0f;
+                ps[k] = (MODE == EPI_DRAG && n < e.n_true) ? e.ysig[n] : 0.0f;
+                pm[k] = (MODE == EPI_DRAG && n < e.n_true) ? e.ymu[n] : 0.0f;
             }
-            const int rowmask = (e.mode == EPI_DRAG && row < e.M) ? e.mask[row] : 0;
+            const int rowmask = (MODE == EPI_DRAG && row < e.M) ? e.mask[row] : 0;
             const bool got = mbar_wait(saddr(&accf_bar[acc]), (uint32_t)((tl / 2) & 1));
             if (!__all_sync(0xffffffffu, got) || abort_flag) {
                 ok = false;
@@ -429,7 +430,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 const int nb = cbeg + 32 * k;
                 if (nb >= e.N) break;
                 float zz[32];
-                if (e.mode == EPI_BWD) {
+                if (MODE == EPI_BWD) {
                     // pre-activations in flight while the accumulator is read
                     if (row < e.M && nb + 32 <= e.N && (e.ldz & 3) == 0) {
                         const float4* zp = reinterpret_cast<const float4*>(e.z + (size_t)row * e.ldz + nb);
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(rr[j]);
                 const uint32_t stg =
                     e.tstore ? stg_warp + (uint32_t)((32 * k) / 64) * 4096u + (uint32_t)lane * 128u : 0u;
-                epi32(e, z, row, nb, v, sbias, ps[k], pm[k], zz, rowmask, sq, stg, ((32 * k) % 64) / 8);
+                epi32<MODE>(e, z, row, nb, v, sbias, ps[k], pm[k], zz, rowmask, sq, stg, ((32 * k) % 64) / 8);
             }
             tc_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(&acce_bar[acc])) : "memory");
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         if (e.tstore && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
         __syncwarp();
         if (!ok) abort_flag = 1;
-        if (e.mode == EPI_LOSS) {
+        if (MODE == EPI_LOSS) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
             if (lane == 0 && sq != 0.0) atomicAdd(e.loss, sq);
@@ -514,9 +515,9 @@ int sm_count()
     return n > 0 ? n : 1;
 }
 
-template <int BN, int ST, int EPW>
-bool launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int K, int ksplit, const GemmEpi& e,
-            cudaStream_t s)
+template <int BN, int ST, int EPW, int MODE>
+bool launch_mode(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int K, int ksplit,
+                 const GemmEpi& e, cudaStream_t s)
 {
     constexpr size_t kMaxShm = 232448 - 256;   // 227 KB opt-in per block, less the static part
     constexpr size_t kStg = (size_t)32 * BN / (EPW / 4) * 2 * EPW;
@@ -531,7 +532,7 @@ bool launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
     static size_t configured[64] = {};
     static int sms[64] = {};
     if (shm > configured[dev]) {
-        if (cudaFuncSetAttribute(k_gemm_bf16<BN, ST, EPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) !=
+        if (cudaFuncSetAttribute(k_gemm_bf16<BN, ST, EPW, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) !=
             cudaSuccess)
             return false;
         configured[dev] = shm;
@@ -539,8 +540,23 @@ bool launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc,
     }
     const long long tiles = (long long)((e.N + BN - 1) / BN) * ((e.M + kBM - 1) / kBM) * ksplit;
     const int grid = (int)std::min<long long>(tiles, sms[dev]);
-    k_gemm_bf16<BN, ST, EPW><<<grid, 64 + 32 * EPW, shm, s>>>(ta, tb, tc, K, ksplit, e);
+    k_gemm_bf16<BN, ST, EPW, MODE><<<grid, 64 + 32 * EPW, shm, s>>>(ta, tb, tc, K, ksplit, e);
     return cudaPeekAtLastError() == cudaSuccess;
+}
+
+// one kernel per epilogue mode: each holds only its own epilogue code (a smaller instruction
+// footprint for the epilogue warps, whose instruction fetch otherwise stalls them)
+template <int BN, int ST, int EPW>
+bool launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int K, int ksplit, const GemmEpi& e,
+            cudaStream_t s)
+{
+    switch (e.mode) {
+    case EPI_STORE: return launch_mode<BN, ST, EPW, EPI_STORE>(ta, tb, tc, K, ksplit, e, s);
+    case EPI_BWD: return launch_mode<BN, ST, EPW, EPI_BWD>(ta, tb, tc, K, ksplit, e, s);
+    case EPI_LOSS: return launch_mode<BN, ST, EPW, EPI_LOSS>(ta, tb, tc, K, ksplit, e, s);
+    case EPI_DRAG: return launch_mode<BN, ST, EPW, EPI_DRAG>(ta, tb, tc, K, ksplit, e, s);
+    default: return false;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
