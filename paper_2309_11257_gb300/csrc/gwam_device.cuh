@@ -792,11 +792,12 @@ __device__ __forceinline__ int split_code(const Grid& G, const Params& P, const 
 
 __device__ __forceinline__ int num_children(int code) { return ((code & 1) ? 2 : 1) * ((code & 2) ? 2 : 1); }
 
-__device__ __forceinline__ void halve(double s[NSTATE], int axis, bool plus)
+// one axis of a split: the half at +-1/4 of the extent, half the extent and half the product
+__device__ __forceinline__ void halve(double& x, double& ext, double& P, bool plus)
 {
-    s[SX + axis] += (plus ? 0.25 : -0.25) * s[SEX + axis];
-    s[SEX + axis] *= 0.5;
-    s[SPX + axis] *= 0.5;
+    x += (plus ? 0.25 : -0.25) * ext;
+    ext *= 0.5;
+    P *= 0.5;
 }
 
 // Child c of a split parent: children are ordered (lower, upper) x (minus, plus) with the
@@ -806,8 +807,12 @@ __device__ __forceinline__ void make_child(const Grid& G, const double p[NSTATE]
 #pragma unroll
     for (int q = 0; q < NSTATE; ++q) s[q] = p[q];
     const int nv = (code & 1) ? 2 : 1;
-    if (code & 1) halve(s, 2, (c % nv) == 1);
-    if (code & 2) halve(s, (code & 4) ? 1 : 0, (c / nv) == 1);
+    if (code & 1) halve(s[SZ], s[SEZ], s[SPZ], (c % nv) == 1);
+    if (code & 2) {
+        const bool plus = (c / nv) == 1;
+        if (code & 4) halve(s[SY], s[SEY], s[SPY], plus);
+        else halve(s[SX], s[SEX], s[SPX], plus);
+    }
     if (code) wrap_position(G, s);
 }
 

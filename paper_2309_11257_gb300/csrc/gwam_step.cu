@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
             nch = num_children(code);
             if (code & 1) ++n_sv;
             if (code & 2) n_sh += (code & 1) ? 2 : 1;
-            for (int c = 0; c < nch; ++c) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c >= nch) break;
                 double ch[NSTATE];
                 make_child(G, s, code, c, ch);
                 if (ray_status(G, ch) != 0) {
