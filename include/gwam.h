@@ -203,6 +203,17 @@ int gwam_get_field_host(gwam_ctx *ctx, int which, double *out_host);
 int gwam_get_gamma2_host(gwam_ctx *ctx, double *out_host);
 int gwam_synchronize(gwam_ctx *ctx);
 
+/* Checkpoint and resume (an operation of this library, not of the paper).  gwam_save writes the
+ * complete state that the next step depends on -- the ray volumes in canonical order, ids,
+ * counters, budget terms and the background (FP64 nodes and rho; the derived arrays are rebuilt
+ * on load) -- to a binary file in host byte order; gwam_load reads it into a context created with the same grid,
+ * parameters, members and precision (GWAM_EINVAL otherwise, or for a missing or truncated file;
+ * GWAM_ECAPACITY if the file holds more ray volumes than this context's max_rays).  A step after
+ * gwam_load gives bit for bit the results the saved context's next step gives.  The grid fields of
+ * the last step (gwam_get_field_host) are not part of the checkpoint.  Both synchronise. */
+int gwam_save(gwam_ctx *ctx, const char *path);
+int gwam_load(gwam_ctx *ctx, const char *path);
+
 /* Per-cell segment offsets of a ray array ordered by cell (the parent-cell storage of App. B.2):
  * offsets[c] = number of entries of cells[] smaller than c, offsets[ncell] = n, so the entries of
  * cell c are [offsets[c], offsets[c+1]) when cells[] is sorted.  cells: n int32 device values in

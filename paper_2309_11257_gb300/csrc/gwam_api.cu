@@ -1,5 +1,6 @@
 // gwam_api.cu -- the extern "C" entry points declared in include/gwam.h.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -801,6 +802,189 @@ int gwam_get_gamma2_host(gwam_ctx* ctx, double* out_host)
                               c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     cudaFree(tmp);
+    API_END
+}
+
+// ------------------------------------------------------------------------------ checkpoints
+// File layout: CkptHeader, one byte per member (background set), the ray arrays of the canonical
+// order (FP64 form: 7 x n double2; precision form: 4 x n float4), then, when a background is set,
+// the FP64 nodes [members * ncell] and rho [members * ncell].  Host byte order.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t precision, geometry, nx, ny, nz, members;
+    int32_t gamma_mode, saturation, smoothing, flux_form, splitting, cap;
+    double dX, dY, dz, radius, omega, f0, g, alpha_s, min_split_dz;
+    int64_t n;
+    int32_t have_bg, pad;
+    Ctl ctl;
+    DevBudget budget;
+};
+constexpr char kCkptMagic[8] = {'G', 'W', 'A', 'M', 'C', 'K', 'P', '1'};
+
+void fill_header(const Context& c, CkptHeader& h)
+{
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.header_bytes = sizeof(CkptHeader);
+    h.precision = c.f32 ? 1 : 0;
+    h.geometry = c.G.geometry;
+    h.nx = c.G.nx;
+    h.ny = c.G.ny;
+    h.nz = c.G.nz;
+    h.members = c.G.members;
+    h.gamma_mode = c.P.gamma_mode;
+    h.saturation = c.P.saturation;
+    h.smoothing = c.P.smoothing;
+    h.flux_form = c.P.flux_form;
+    h.splitting = c.P.splitting;
+    h.cap = c.P.cap;
+    h.dX = c.G.dX;
+    h.dY = c.G.dY;
+    h.dz = c.G.dz;
+    h.radius = c.G.radius;
+    h.omega = c.G.omega;
+    h.f0 = c.G.f0;
+    h.g = c.G.g;
+    h.alpha_s = c.P.alpha_s;
+    h.min_split_dz = c.P.min_split_dz;
+}
+
+// the configuration fields of two headers agree (everything but the state)
+bool same_config(const CkptHeader& a, const CkptHeader& b)
+{
+    return memcmp(a.magic, b.magic, 8) == 0 && a.version == b.version && a.header_bytes == b.header_bytes &&
+           a.precision == b.precision && a.geometry == b.geometry && a.nx == b.nx && a.ny == b.ny && a.nz == b.nz &&
+           a.members == b.members && a.gamma_mode == b.gamma_mode && a.saturation == b.saturation &&
+           a.smoothing == b.smoothing && a.flux_form == b.flux_form && a.splitting == b.splitting &&
+           a.cap == b.cap && a.dX == b.dX && a.dY == b.dY && a.dz == b.dz && a.radius == b.radius &&
+           a.omega == b.omega && a.f0 == b.f0 && a.g == b.g && a.alpha_s == b.alpha_s &&
+           a.min_split_dz == b.min_split_dz;
+}
+
+struct FileCloser {
+    FILE* f;
+    ~FileCloser()
+    {
+        if (f) fclose(f);
+    }
+};
+}  // namespace
+
+int gwam_save(gwam_ctx* ctx, const char* path)
+{
+    API_BEGIN(ctx)
+    if (!path) return GWAM_EINVAL;
+    check_pending(c);
+    CkptHeader h;
+    fill_header(c, h);
+    h.n = c.ctl_host->n;
+    h.have_bg = c.have_bg ? 1 : 0;
+    h.ctl = *c.ctl_host;
+    h.budget = *c.budget_host;
+    const size_t n = (size_t)h.n;
+    const size_t nc = (size_t)c.G.ncell_all;
+    // device -> host first, so that a failed copy leaves no partial file
+    std::vector<unsigned char> rays(n * (c.f32 ? 4 * sizeof(float4) : 7 * sizeof(double2)));
+    for (int q = 0; q < (c.f32 ? 4 : 7) && n; ++q) {
+        const size_t bytes = n * (c.f32 ? sizeof(float4) : sizeof(double2));
+        const void* src = c.f32 ? (const void*)c.A32.q[q] : (const void*)c.A.a[q];
+        GWAM_CUDA(cudaMemcpyAsync(rays.data() + q * bytes, src, bytes, cudaMemcpyDeviceToHost, c.stream));
+    }
+    std::vector<Node> nodes;
+    std::vector<double> rho;
+    if (h.have_bg) {
+        nodes.resize(nc);
+        rho.resize(nc);
+        GWAM_CUDA(cudaMemcpyAsync(nodes.data(), c.bg, sizeof(Node) * nc, cudaMemcpyDeviceToHost, c.stream));
+        GWAM_CUDA(cudaMemcpyAsync(rho.data(), c.rho, sizeof(double) * nc, cudaMemcpyDeviceToHost, c.stream));
+    }
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    std::vector<unsigned char> flags(c.G.members);
+    for (int m = 0; m < c.G.members; ++m) flags[m] = c.member_bg[m] ? 1 : 0;
+    FileCloser fc{fopen(path, "wb")};
+    if (!fc.f) {
+        c.err = "gwam_save: cannot open the file for writing";
+        return GWAM_EINVAL;
+    }
+    bool ok = fwrite(&h, sizeof(h), 1, fc.f) == 1 && fwrite(flags.data(), 1, flags.size(), fc.f) == flags.size() &&
+              (rays.empty() || fwrite(rays.data(), 1, rays.size(), fc.f) == rays.size());
+    if (ok && h.have_bg)
+        ok = fwrite(nodes.data(), sizeof(Node), nc, fc.f) == nc && fwrite(rho.data(), sizeof(double), nc, fc.f) == nc;
+    if (!ok) {
+        c.err = "gwam_save: write failed";
+        return GWAM_EINVAL;
+    }
+    API_END
+}
+
+int gwam_load(gwam_ctx* ctx, const char* path)
+{
+    API_BEGIN(ctx)
+    if (!path) return GWAM_EINVAL;
+    check_pending(c);
+    FileCloser fc{fopen(path, "rb")};
+    if (!fc.f) {
+        c.err = "gwam_load: cannot open the file";
+        return GWAM_EINVAL;
+    }
+    CkptHeader h, mine;
+    fill_header(c, mine);
+    if (fread(&h, sizeof(h), 1, fc.f) != 1 || !same_config(h, mine)) {
+        c.err = "gwam_load: not a checkpoint of this grid, parameters and precision";
+        return GWAM_EINVAL;
+    }
+    if (h.n < 0 || h.n > c.max_rays || h.ctl.n != h.n || h.ctl.status != 0) {
+        c.err = "gwam_load: ray count beyond max_rays or inconsistent header";
+        return h.n > c.max_rays ? GWAM_ECAPACITY : GWAM_EINVAL;
+    }
+    const size_t n = (size_t)h.n;
+    const size_t nc = (size_t)c.G.ncell_all;
+    std::vector<unsigned char> flags(c.G.members);
+    std::vector<unsigned char> rays(n * (c.f32 ? 4 * sizeof(float4) : 7 * sizeof(double2)));
+    bool ok = fread(flags.data(), 1, flags.size(), fc.f) == flags.size() &&
+              (rays.empty() || fread(rays.data(), 1, rays.size(), fc.f) == rays.size());
+    std::vector<Node> nodes;
+    std::vector<double> rho;
+    if (ok && h.have_bg) {
+        nodes.resize(nc);
+        rho.resize(nc);
+        ok = fread(nodes.data(), sizeof(Node), nc, fc.f) == nc && fread(rho.data(), sizeof(double), nc, fc.f) == nc;
+    }
+    if (!ok) {
+        c.err = "gwam_load: truncated checkpoint";
+        return GWAM_EINVAL;
+    }
+    for (int q = 0; q < (c.f32 ? 4 : 7) && n; ++q) {
+        const size_t bytes = n * (c.f32 ? sizeof(float4) : sizeof(double2));
+        void* dst = c.f32 ? (void*)c.A32.q[q] : (void*)c.A.a[q];
+        GWAM_CUDA(cudaMemcpyAsync(dst, rays.data() + q * bytes, bytes, cudaMemcpyHostToDevice, c.stream));
+    }
+    *c.ctl_host = h.ctl;
+    *c.budget_host = h.budget;
+    GWAM_CUDA(cudaMemcpyAsync(c.ctl, c.ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c.stream));
+    GWAM_CUDA(cudaMemcpyAsync(c.budget, c.budget_host, sizeof(DevBudget), cudaMemcpyHostToDevice, c.stream));
+    if (h.have_bg) {
+        GWAM_CUDA(cudaMemcpyAsync(c.bg, nodes.data(), sizeof(Node) * nc, cudaMemcpyHostToDevice, c.stream));
+        GWAM_CUDA(cudaMemcpyAsync(c.rho, rho.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, c.stream));
+        for (int m = 0; m < c.G.members; ++m)
+            if (flags[m]) {
+                restore_background(c, m);
+                if (c.f32) convert_background32(c, m);
+            }
+    }
+    for (int m = 0; m < c.G.members; ++m) c.member_bg[m] = h.have_bg && flags[m];
+    c.have_bg = h.have_bg != 0;
+    for (int m = 0; m < c.G.members; ++m) c.have_bg = c.have_bg && c.member_bg[m];
+    for (int q = 0; q < 2; ++q)
+        if (c.gexec[q]) {
+            cudaGraphExecDestroy(c.gexec[q]);
+            c.gexec[q] = nullptr;
+        }
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
     API_END
 }
 

@@ -156,6 +156,8 @@ struct Context {
 };
 
 // kernels, launched from the host side (gwam_step.cu / gwam_launch.cu)
+// derived background arrays (1/rho, gradients, gather copies) from restored nodes and rho
+void restore_background(Context& c, int member);
 void launch_set_background(Context& c, int member, const double* u, const double* v, const double* n2,
                            const double* rho);
 void launch_add_rays(Context& c, const double* const in[13], int64_t n);

@@ -177,6 +177,24 @@ void launch_set_background(Context& c, int member, const double* u, const double
                                                         c.f32 ? c.bg32 + o : nullptr);
 }
 
+// 1/rho of restored nodes (checkpoint load), by the Newton reciprocal as in k_set_background
+__global__ void k_rho_inv(const double* __restrict__ rho, double* __restrict__ rho_inv, int64_t n)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+        const double r = rho[c];
+        rho_inv[c] = (__double_as_longlong(r) > 0 && !nonfinite_bits(r)) ? rcp_nr(r) : 0.0;
+    }
+}
+
+void restore_background(Context& c, int member)
+{
+    const int64_t o = (int64_t)member * c.G.ncell;
+    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
+    k_rho_inv<<<blocks, kThreads, 0, c.stream>>>(c.rho + o, c.rho_inv + o, c.G.ncell);
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.f32 ? nullptr : c.bgdf + o,
+                                                        c.f32 ? c.bg32 + o : nullptr);
+}
+
 // ----------------------------------------------------------------------------- explicit rays
 
 // pass 0 validates, pass 1 writes at n + q with id next_id + q

@@ -116,6 +116,8 @@ SIGNATURES = {
     "gwam_selftest_widen": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_selftest_narrow": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "gwam_selftest_logratio": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
+    "gwam_save": (C.c_int, [_vp, C.c_char_p]),
+    "gwam_load": (C.c_int, [_vp, C.c_char_p]),
     "gwam_gemm_bf16": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "gwam_mlp_create": (C.c_int, [_P(_vp), _P(MlpConfig), _vp]),
     "gwam_mlp_destroy": (None, [_vp]),
@@ -290,6 +292,15 @@ class Tracer:
         """Step with host (numpy, ideally pinned) output buffers; synchronising."""
         self._check(_lib.gwam_step_host(self._h, float(dt), dudt.ctypes.data_as(_vp), dvdt.ctypes.data_as(_vp)),
                     "step_host")
+
+    # -------------------------------------------------------------- checkpoints
+    def save(self, path: str):
+        """Write the complete step state (rays, ids, counters, budget, background) to `path`."""
+        self._check(_lib.gwam_save(self._h, os.fsencode(path)), "save")
+
+    def load(self, path: str):
+        """Read a checkpoint written by a tracer of the same grid, parameters and precision."""
+        self._check(_lib.gwam_load(self._h, os.fsencode(path)), "load")
 
     # -------------------------------------------------------------- outputs
     def num_rays(self) -> int:
