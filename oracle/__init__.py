@@ -50,7 +50,7 @@ class Grid(C.Structure):
 class Params(C.Structure):
     _fields_ = [("gamma_mode", C.c_int), ("saturation", C.c_int), ("smoothing", C.c_int),
                 ("flux_form", C.c_int), ("splitting", C.c_int), ("cap_per_column", C.c_int),
-                ("alpha_s", C.c_double), ("min_split_dz", C.c_double)]
+                ("alpha_s", C.c_double), ("min_split_dz", C.c_double), ("columnar", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -252,7 +252,13 @@ void orc_rhs(const orc_model *m, const double *y, double *F)
              + d.kh2 / (2.0 * d.w * d.K2) * (dN2[q] - d.D / d.K2 * dG2[q])
              + d.mg2 / (2.0 * d.w * d.K2) * df2v[q];
     }
-    if (is_sphere(m)) {
+    if (m->P.columnar) {
+        /* single-column approximation (MS-GWaM-1D, Sec. 1): horizontal gradients of the resolved
+         * flow are neglected, so k and l stay fixed and m follows the vertical gradient alone */
+        F[3] = 0.0;
+        F[4] = 0.0;
+        F[5] = -G[2];
+    } else if (is_sphere(m)) {
         double tphi = tan(Y);
         F[3] = -G[0] / hX - k * cg[2] / r + k * tphi * cg[1] / r;   /* Eq. eikonal-sphere:1 */
         F[4] = -G[1] / r - l * cg[2] / r - k * tphi * cg[0] / r;    /* Eq. eikonal-sphere:2 */
@@ -264,6 +270,12 @@ void orc_rhs(const orc_model *m, const double *y, double *F)
     }
 
     for (int q = 0; q < 3; ++q) {
+        if (m->P.columnar && q < 2) {
+            /* no horizontal propagation or advection: position and horizontal extents fixed */
+            F[q] = 0.0;
+            F[6 + q] = 0.0;
+            continue;
+        }
         double vel[2];
         for (int side = 0; side < 2; ++side) {
             double h = (side == 0 ? 0.5 : -0.5) * ext[q];
@@ -1123,6 +1135,11 @@ int orc_divergence(const orc_model *m, const double *fz_l, const double *fz_p,
                     div_v = (f_lp[ce] - f_lp[cw]) / (2.0 * dX) + (f_pp[cn] - f_pp[cs]) / (2.0 * dY)
                           + (fz_top_p - fz_bot_p) / dz;
                 }
+                if (m->P.columnar) {
+                    /* horizontally homogeneous column: the vertical flux divergence alone */
+                    div_u = (fz_top_l - fz_bot_l) / dz;
+                    div_v = (fz_top_p - fz_bot_p) / dz;
+                }
                 dudt[c] = -div_u / rho + e_l[c] / (m->G.g * rho);
                 dvdt[c] = -div_v / rho + e_p[c] / (m->G.g * rho);
             }
@@ -1158,8 +1175,9 @@ int orc_tendency_scale(const orc_model *m, double *du_s, double *dv_s)
                 for (int q = 0; q < 2; ++q) {
                     double yn = (jn >= 0 && jn < ny) ? A[q][1][node(m, k, jn, i)] : 0.0;
                     double ys = (js >= 0 && js < ny) ? A[q][1][node(m, k, js, i)] : 0.0;
-                    double v = (A[q][0][ce] + A[q][0][cw]) / (2.0 * dX * hx) + (cn * yn + cs * ys) / (2.0 * dY * hy)
-                             + (A[q][2][((size_t)(k + 1) * ny + j) * nx + i] + A[q][2][((size_t)k * ny + j) * nx + i]) / dz;
+                    double v = (A[q][2][((size_t)(k + 1) * ny + j) * nx + i] + A[q][2][((size_t)k * ny + j) * nx + i]) / dz;
+                    if (!m->P.columnar)
+                        v += (A[q][0][ce] + A[q][0][cw]) / (2.0 * dX * hx) + (cn * yn + cs * ys) / (2.0 * dY * hy);
                     v = v / m->rho[c] + A[q][3][c] / (m->G.g * m->rho[c]);
                     (q == 0 ? du_s : dv_s)[c] = v;
                 }

@@ -49,6 +49,8 @@ typedef struct {
     int cap_per_column;     /* max rays per column (Sec. B.5); <= 0 disables */
     double alpha_s;         /* splitting scale factor (2.5 in App. B.3) */
     double min_split_dz;    /* minimum vertical split threshold (1 km in App. B.3) */
+    int columnar;           /* 1: single-column mode of MS-GWaM-1D (Sec. 1) -- no horizontal propagation,
+                               advection or refraction; drag from the vertical flux divergence */
 } orc_params;
 
 typedef struct {

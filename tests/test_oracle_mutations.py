@@ -43,6 +43,11 @@ MUTATIONS = {
                        "double dp_u = (pl_n - pl_s) / (2.0 * dY);"),
     # bookkeeping
     "split_id_reuse": ("oid[1] = m->next_id++;", "oid[1] = m->next_id;"),
+    # columnar mode (single-column approximation)
+    "columnar_metric_term": ("        F[5] = -G[2];\n    } else if (is_sphere(m)) {",
+                             "        F[5] = -G[2] + k * cg[0] / r;\n    } else if (is_sphere(m)) {"),
+    "columnar_horizontal_divergence": ("                    div_u = (fz_top_l - fz_bot_l) / dz;\n",
+                                       "                    div_u = div_u;\n"),
 }
 
 

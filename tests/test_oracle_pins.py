@@ -793,3 +793,71 @@ def test_exits_at_top_and_budget_closure():
     # canonical order: ascending (cell, id)
     key = r["cell"].astype(np.int64) * (1 << 40) + r["id"]
     assert np.all(np.diff(key) > 0)
+
+
+# ------------------------------------------------------------------ columnar mode (MS-GWaM-1D, Sec. 1)
+
+def test_columnar_mode_freezes_horizontal_state_and_follows_vertical_hamiltonian():
+    """Single-column approximation: horizontal gradients of the resolved flow neglected and no
+    horizontal propagation or advection (Sec. 1).  Then lambda, phi, k, l and the horizontal
+    extents stay fixed, while m obeys Hamilton's equation for the vertical coordinate alone,
+    dm/dt = -dOmega/dz (no metric terms: the ray does not move over the sphere), and z moves with
+    the vertical group velocity -- checked by finite differences of Omega."""
+    grid = synth.sphere_grid(nx=64, ny=40, nz=30, dz=1000.0)
+    M = model(grid, dict(columnar=1), _sphere_linear_bg(grid))
+    g = np.random.default_rng(41)
+    dlam, dphi = 2 * math.pi / 64, math.pi / 40
+    for _ in range(20):
+        lam = (g.integers(2, 60) + g.uniform(0.6, 1.4)) * dlam
+        phi = -0.5 * math.pi + (g.integers(6, 32) + g.uniform(0.6, 1.4)) * dphi
+        z = (g.integers(3, 25) + g.uniform(0.6, 1.4)) * 1000.0
+        k, l = 2 * math.pi / 3e5 * g.normal(size=2)
+        m = -2 * math.pi / 4e3
+        F = M.rhs([lam, phi, z, k, l, m, 0.0, 0.0, 0.0])
+        assert F[0] == 0.0 and F[1] == 0.0 and F[3] == 0.0 and F[4] == 0.0 and F[6] == 0.0 and F[7] == 0.0
+        dOdz = fd(lambda t: M.omega(lam, phi, t, k, l, m), z, 0.05)
+        dOdm = fd(lambda t: M.omega(lam, phi, z, k, l, t), m, 1e-6 * abs(m))
+        assert abs(F[5] + dOdz) <= 1e-5 * abs(dOdz), (F[5], -dOdz)
+        assert abs(F[2] - dOdm) <= 1e-5 * abs(dOdm), (F[2], dOdm)
+    # a full RK3 step keeps the horizontal components bit for bit
+    y0 = [3 * dlam + 0.3 * dlam, 0.2, 12e3, 2e-5, -1e-5, -1.5e-3, 0.05, 0.04, 800.0]
+    y1 = M.rk3(y0, 300.0)
+    for c in (0, 1, 3, 4, 6, 7):
+        assert y1[c] == y0[c]
+    assert y1[2] != y0[2] and y1[5] != y0[5]
+
+
+def test_columnar_mode_equals_3d_in_a_horizontally_uniform_fplane():
+    """Where the single-column assumption holds exactly (f-plane, horizontally uniform
+    background), the vertical part of the 3-D ray equations (z, m, dZ rates) is the columnar one."""
+    w = synth.workload("fplane")
+    grid = w["grid"]
+    g = np.random.default_rng(43)
+    M1 = model(grid, dict(columnar=1), w["background"])
+    M3 = model(grid, dict(columnar=0), w["background"])
+    for _ in range(20):
+        y = [g.uniform(0, 16 * grid["dx"]), g.uniform(0, 16 * grid["dy"]), g.uniform(2e3, 30e3),
+             g.normal() * 2e-5, g.normal() * 2e-5, -g.uniform(6e-4, 6e-3), 5e4, 5e4, 500.0]
+        F1, F3 = M1.rhs(y), M3.rhs(y)
+        for c in (2, 5, 8):
+            assert abs(F1[c] - F3[c]) <= 1e-13 * abs(F3[c]) + 1e-300, (c, F1[c], F3[c])
+
+
+def test_columnar_divergence_keeps_only_the_vertical_flux_and_elastic_terms():
+    """Horizontally homogeneous column: the horizontal flux divergence drops out of Eq.
+    mean-flow-impact; the vertical flux divergence and the elastic term remain."""
+    grid = synth.sphere_grid(nx=16, ny=8, nz=10, dz=1000.0)
+    bg = _sphere_bg(grid)
+    M = model(grid, dict(columnar=1), bg)
+    g = np.random.default_rng(47)
+    nz, ny, nx = 10, 8, 16
+    f = {n: g.normal(size=(nz, ny, nx)) for n in oracle.FIELD_NAMES[2:8]}
+    f["fz_l"] = g.normal(size=(nz + 1, ny, nx))
+    f["fz_p"] = g.normal(size=(nz + 1, ny, nx))
+    du, dv = M.divergence(f)
+    rho = bg[3]
+    gr = grid["g"]
+    exp_u = -(f["fz_l"][1:] - f["fz_l"][:-1]) / 1000.0 / rho + f["e_l"] / (gr * rho)
+    exp_v = -(f["fz_p"][1:] - f["fz_p"][:-1]) / 1000.0 / rho + f["e_p"] / (gr * rho)
+    np.testing.assert_allclose(du, exp_u, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(dv, exp_v, rtol=1e-12, atol=0)
