@@ -87,6 +87,11 @@ typedef struct {
     int64_t max_rays;     /* capacity: live ray volumes plus split children of one step (all members) */
     int members;          /* ensemble members: independent backgrounds and ray populations advanced
                              together (0 or 1: a single member; at most 255) */
+    int columnar;         /* 1: single-column mode of MS-GWaM-1D (the single-column approximation of
+                             Sec. 1): no horizontal propagation, advection or refraction -- position,
+                             horizontal wavenumber and horizontal extents fixed, dm/dt = -dOmega/dz --
+                             and du/dt, dv/dt from the vertical flux divergence and the elastic term
+                             only; 0: the 3-D model */
 } gwam_params;
 
 /* Background source of Sec. 3c: alpha(phi) profile, F_sol = alpha(phi) F_s + alpha(-phi) F_w,

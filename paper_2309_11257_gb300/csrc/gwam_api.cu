@@ -130,6 +130,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
     if ((int64_t)grid->nx * grid->ny * (grid->nz + 1) >= (int64_t)1 << 31) return GWAM_EINVAL;
     if (grid->nz > 192) return GWAM_EINVAL;   // column tiles of the transposing kernels live in shared memory
     if (params->precision != 0 && params->precision != 1) return GWAM_EINVAL;
+    if (params->columnar != 0 && params->columnar != 1) return GWAM_EINVAL;
     if (params->max_rays < 1 || params->max_rays >= ((int64_t)1 << 29)) return GWAM_EINVAL;
     if (!(params->alpha_s > 0.0) || !(params->min_split_dz >= 0.0)) return GWAM_EINVAL;
     if (params->flux_form != 0 && params->flux_form != 1) return GWAM_EINVAL;
@@ -196,6 +197,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         P.smoothing = params->smoothing;
         P.flux_form = params->flux_form;
         P.splitting = params->splitting;
+        G.columnar = params->columnar;
         P.cap = params->cap_per_column;
         P.alpha_s = params->alpha_s;
         P.f_alpha_s = (float)params->alpha_s;
@@ -814,7 +816,7 @@ struct CkptHeader {
     char magic[8];
     uint32_t version, header_bytes;
     int32_t precision, geometry, nx, ny, nz, members;
-    int32_t gamma_mode, saturation, smoothing, flux_form, splitting, cap;
+    int32_t gamma_mode, saturation, smoothing, flux_form, splitting, cap, columnar, pad0;
     double dX, dY, dz, radius, omega, f0, g, alpha_s, min_split_dz;
     int64_t n;
     int32_t have_bg, pad;
@@ -841,6 +843,7 @@ void fill_header(const Context& c, CkptHeader& h)
     h.flux_form = c.P.flux_form;
     h.splitting = c.P.splitting;
     h.cap = c.P.cap;
+    h.columnar = c.G.columnar;
     h.dX = c.G.dX;
     h.dY = c.G.dY;
     h.dz = c.G.dz;
@@ -859,7 +862,7 @@ bool same_config(const CkptHeader& a, const CkptHeader& b)
            a.precision == b.precision && a.geometry == b.geometry && a.nx == b.nx && a.ny == b.ny && a.nz == b.nz &&
            a.members == b.members && a.gamma_mode == b.gamma_mode && a.saturation == b.saturation &&
            a.smoothing == b.smoothing && a.flux_form == b.flux_form && a.splitting == b.splitting &&
-           a.cap == b.cap && a.dX == b.dX && a.dY == b.dY && a.dz == b.dz && a.radius == b.radius &&
+           a.cap == b.cap && a.columnar == b.columnar && a.dX == b.dX && a.dY == b.dY && a.dz == b.dz && a.radius == b.radius &&
            a.omega == b.omega && a.f0 == b.f0 && a.g == b.g && a.alpha_s == b.alpha_s &&
            a.min_split_dz == b.min_split_dz;
 }

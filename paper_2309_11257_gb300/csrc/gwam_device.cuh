@@ -53,6 +53,7 @@ __device__ __forceinline__ double rsqrt_nr(double x)
 // Grid geometry as the kernels see it (derived once on the host).
 struct Grid {
     int geometry;          // 0 f-plane, 1 sphere
+    int columnar;          // single-column mode (no horizontal propagation, advection or refraction)
     int nx, ny, nz;
     int ncol, ncell;       // per member: nx*ny, nx*ny*nz
     int members;           // ensemble members (independent backgrounds and ray populations)
@@ -600,7 +601,12 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
         Gq[q] = df_sub(df_add(df_add(df_mul2(k, b.d[0][q]), df_mul2(l, b.d[1][q])), df_mul2(aN, b.d[2][q])),
                        df_mul2(aG, b.d[3][q]));
     Gq[1] = df_add(Gq[1], df_mul2(aF, df2));
-    if (G.geometry == 1) {
+    if (G.columnar) {
+        // single-column mode: k and l fixed, m by the vertical gradient of Omega alone
+        R[3] = df_f(0.0f);
+        R[4] = df_f(0.0f);
+        R[5] = df_neg(Gq[2]);
+    } else if (G.geometry == 1) {
         const DF ir = g.ir;
         R[3] = df_add(df_neg(df_mul2(Gq[0], g.ihX)), df_mul2(df_mul2(k, ir), df_sub(df_mul2(g.tphi, cgy), cgz)));
         R[4] = df_sub(df_neg(df_mul2(Gq[1], ir)), df_mul2(ir, df_add(df_mul2(l, cgz), df_mul2(df_mul2(k, g.tphi), cgx))));
@@ -613,6 +619,12 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
     // faces: first-order Taylor values along the face's own axis
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
+        if (G.columnar && q < 2) {
+            // no horizontal propagation or advection
+            R[q] = df_f(0.0f);
+            R[6 + q] = df_f(0.0f);
+            continue;
+        }
         const DF ext = y[6 + q];
         DF vel[2];
 #pragma unroll

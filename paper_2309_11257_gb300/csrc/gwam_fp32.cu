@@ -131,8 +131,11 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     }
 }
 
-// divergence (Eq. mean-flow-impact) in FP32, as k_divergence: one block per (row, tile of TW
-// columns), results transposed through shared memory into the caller's [nz][ny][nx] FP64 layout
+// divergence (Eq. mean-flow-impact) in FP32:
+//   du/dt = -(1/rho) [ (1/(r cos phi)) (d_lambda F^{ll} + d_phi (cos phi F^{pl})) + d_z F^z_l ] + E_l / (g rho),
+// dv/dt likewise (centred differences, flux zero beyond the pole rows; in the columnar mode the
+// vertical term alone).  One block per (row, tile of TW columns), results transposed through shared
+// memory into the caller's [nz][ny][nx] FP64 layout
 __global__ void k_divergence32(Grid G, int TW, const float* __restrict__ fzl, const float* __restrict__ fzp,
                                const float* __restrict__ fll, const float* __restrict__ flp,
                                const float* __restrict__ fpl, const float* __restrict__ fpp,
@@ -200,6 +203,11 @@ __global__ void k_divergence32(Grid G, int TW, const float* __restrict__ fzl, co
         } else {
             div_u = (fll[ce] - fll[cw]) * h2x + (pl_n - pl_s) * h2y + dzl;
             div_v = (flp[ce] - flp[cw]) * h2x + (pp_n - pp_s) * h2y + dzp;
+        }
+        if (G.columnar) {
+            // horizontally homogeneous column: the vertical flux divergence alone
+            div_u = dzl;
+            div_v = dzp;
         }
         tu[k * TW + ii] = (el[c] * ig - div_u) * ri;
         tv[k * TW + ii] = (ep[c] * ig - div_v) * ri;
@@ -655,7 +663,6 @@ __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int nc
                             const int* __restrict__ raycell, const double* __restrict__ rho,
                             const double* __restrict__ pj, const double* __restrict__ k2, double dt,
                             double* __restrict__ kappa);
-void grid_phase(Context& c, double* du, double* dv, int mask);
 
 void run_step32(Context& c, double dt, double* du, double* dv)
 {

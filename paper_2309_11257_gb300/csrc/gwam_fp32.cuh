@@ -209,7 +209,12 @@ __device__ __forceinline__ void rhs32(const Grid& G, const Node32* __restrict__ 
 #pragma unroll
     for (int q = 0; q < 3; ++q) Gq[q] = k * b.d[0][q] + l * b.d[1][q] + aN * b.d[2][q] - aG * b.d[3][q];
     Gq[1] += aF * df2;
-    if (G.geometry == 1) {
+    if (G.columnar) {
+        // single-column mode: k and l fixed, m by the vertical gradient of Omega alone
+        F[3] = 0.0f;
+        F[4] = 0.0f;
+        F[5] = -Gq[2];
+    } else if (G.geometry == 1) {
         F[3] = -Gq[0] * g.ihX + k * g.ir * (g.tphi * cgy - cgz);
         F[4] = -Gq[1] * g.ir - g.ir * (l * cgz + k * g.tphi * cgx);
         F[5] = -Gq[2] + g.ir * (k * cgx + l * cgy);
@@ -222,6 +227,12 @@ __device__ __forceinline__ void rhs32(const Grid& G, const Node32* __restrict__ 
     const float scale[3] = {g.ihX * G.f_inv_dX, g.ir * G.f_inv_dY, G.f_inv_dz};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
+        if (G.columnar && q < 2) {
+            // no horizontal propagation or advection
+            F[q] = 0.0f;
+            F[6 + q] = 0.0f;
+            continue;
+        }
         float vel[2];
 #pragma unroll
         for (int sd = 0; sd < 2; ++sd) {

@@ -97,9 +97,11 @@ __global__ void __launch_bounds__(256) k_smooth_df(Grid G, FieldSetDF fs, int f0
     }
 }
 
-// Divergence (Eq. mean-flow-impact) of the smoothed double-float fields, as k_divergence: one block
-// per (row, tile of TW columns), results transposed through shared memory into [nz][ny][nx]; only
-// the final du/dt, dv/dt are formed in FP64.
+// Divergence (Eq. mean-flow-impact) of the smoothed double-float fields,
+//   du/dt = -(1/rho) [ (1/(r cos phi)) (d_lambda F^{ll} + d_phi (cos phi F^{pl})) + d_z F^z_l ] + E_l / (g rho),
+// dv/dt likewise (centred differences, flux zero beyond the pole rows; in the columnar mode the
+// vertical term alone): one block per (row, tile of TW columns), results transposed through shared
+// memory into [nz][ny][nx]; only the final du/dt, dv/dt are formed in FP64.
 struct DivConsts {
     DF h2x, h2y, idz, ig;
 };
@@ -179,6 +181,11 @@ __global__ void k_divergence_df(Grid G, int TW, DivConsts K, const float2* __res
             div_v = df_add(df_add(df_mul2(df_sub(df_load(&flp[ce]), df_load(&flp[cw])), K.h2x),
                                   df_mul2(df_sub(pp_n, pp_s), K.h2y)),
                            dzp);
+        }
+        if (G.columnar) {
+            // horizontally homogeneous column: the vertical flux divergence alone
+            div_u = dzl;
+            div_v = dzp;
         }
         const DF ru = df_mul2(df_sub(df_mul2(df_load(&el[c]), K.ig), div_u), ri);
         const DF rv = df_mul2(df_sub(df_mul2(df_load(&ep[c]), K.ig), div_v), ri);

@@ -690,89 +690,6 @@ void launch_smooth(Context& c, int nf)
     k_smooth_fields<<<grid, dim3(32, 8), 0, c.stream>>>(c.G, fs);
 }
 
-// du/dt = -(1/rho) [ (1/(r cos phi)) (d_lambda F^{ll} + d_phi (cos phi F^{pl})) + d_z F^z_l ] + E_l / (g rho),
-// dv/dt likewise (Eq. mean-flow-impact; centred differences, flux zero beyond the pole rows).
-// One block per (row, tile of TW columns); results transposed through shared memory into the
-// caller's [nz][ny][nx] layout.
-__global__ void k_divergence(Grid G, int TW, const double* __restrict__ fzl, const double* __restrict__ fzp,
-                             const double* __restrict__ fll, const double* __restrict__ flp,
-                             const double* __restrict__ fpl, const double* __restrict__ fpp,
-                             const double* __restrict__ el, const double* __restrict__ ep,
-                             const double* __restrict__ rho_inv, double* __restrict__ du, double* __restrict__ dv)
-{
-    extern __shared__ double tile[];
-    double* tu = tile;
-    double* tv = tile + (size_t)TW * G.nz;
-    const int ntx = (G.nx + TW - 1) / TW;
-    const int mem = blockIdx.x / (ntx * G.ny);
-    const int bl = blockIdx.x - mem * ntx * G.ny;
-    const int j = bl / ntx;
-    const int i0 = (bl % ntx) * TW;
-    {
-        // this member's planes
-        const int64_t oc = (int64_t)mem * G.ncell, oz = (int64_t)mem * G.ncol * (G.nz + 1);
-        fzl += oz; fzp += oz;
-        fll += oc; flp += oc; fpl += oc; fpp += oc; el += oc; ep += oc; rho_inv += oc;
-        if (du) du += oc;
-        if (dv) dv += oc;
-    }
-    const int nz = G.nz;
-    const int n = TW * nz;
-    const double h2x = 0.5 * G.inv_dX, h2y = 0.5 * G.inv_dY;
-    double rcp_cos = 1.0, cn = 0.0, cs = 0.0;
-    if (G.geometry == 1) {
-        rcp_cos = G.row_inv_cos[j];
-        if (j + 1 < G.ny) cn = G.row_cos[j + 1];
-        if (j - 1 >= 0) cs = G.row_cos[j - 1];
-    }
-    const int jn = G.geometry == 1 ? j + 1 : wrap_int(j + 1, G.ny);
-    const int js = G.geometry == 1 ? j - 1 : wrap_int(j - 1, G.ny);
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int k = t % nz, ii = t / nz;
-        const int i = i0 + ii;
-        if (i >= G.nx) continue;
-        const int ie = i + 1 == G.nx ? 0 : i + 1, iw = i == 0 ? G.nx - 1 : i - 1;
-        const int64_t c = ((int64_t)j * G.nx + i) * nz + k;
-        const int64_t ce = ((int64_t)j * G.nx + ie) * nz + k;
-        const int64_t cw = ((int64_t)j * G.nx + iw) * nz + k;
-        const int64_t zc = ((int64_t)j * G.nx + i) * (nz + 1) + k;
-        double pl_n = 0.0, pl_s = 0.0, pp_n = 0.0, pp_s = 0.0;
-        if (jn >= 0 && jn < G.ny) {
-            const int64_t cc = ((int64_t)jn * G.nx + i) * nz + k;
-            pl_n = fpl[cc];
-            pp_n = fpp[cc];
-        }
-        if (js >= 0 && js < G.ny) {
-            const int64_t cc = ((int64_t)js * G.nx + i) * nz + k;
-            pl_s = fpl[cc];
-            pp_s = fpp[cc];
-        }
-        const double ri = rho_inv[c];
-        double div_u, div_v;
-        const double dzl = (fzl[zc + 1] - fzl[zc]) * G.inv_dz;
-        const double dzp = (fzp[zc + 1] - fzp[zc]) * G.inv_dz;
-        if (G.geometry == 1) {
-            const double mh = rcp_cos * G.lev_inv_r[k];
-            div_u = ((fll[ce] - fll[cw]) * h2x + (cn * pl_n - cs * pl_s) * h2y) * mh + dzl;
-            div_v = ((flp[ce] - flp[cw]) * h2x + (cn * pp_n - cs * pp_s) * h2y) * mh + dzp;
-        } else {
-            div_u = (fll[ce] - fll[cw]) * h2x + (pl_n - pl_s) * h2y + dzl;
-            div_v = (flp[ce] - flp[cw]) * h2x + (pp_n - pp_s) * h2y + dzp;
-        }
-        tu[k * TW + ii] = (el[c] * G.inv_g - div_u) * ri;
-        tv[k * TW + ii] = (ep[c] * G.inv_g - div_v) * ri;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int ii = t % TW, k = t / TW;
-        const int i = i0 + ii;
-        if (i >= G.nx) continue;
-        const int64_t o = ((int64_t)k * G.ny + j) * G.nx + i;
-        if (du) du[o] = tu[k * TW + ii];
-        if (dv) dv[o] = tv[k * TW + ii];
-    }
-}
-
 // ============================================================================ budget, control
 
 // Fold the per-block partials of the slots in `mask` (block order: deterministic) into the
@@ -843,7 +760,6 @@ void configure_launch_kernels();
 
 void configure_kernels()
 {
-    cudaFuncSetAttribute(k_divergence, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
     configure_launch_kernels();
 }
 
@@ -868,28 +784,6 @@ void prof_harvest(Context& c)
     }
     c.prof_steps += c.prof_pending;
     c.prof_pending = 0;
-}
-
-// smoothing, divergence into du/dt, dv/dt, and the budget fold (shared by both forms)
-void grid_phase(Context& c, double* du, double* dv, int mask)
-{
-    const Grid& G = c.G;
-    cudaStream_t s = c.stream;
-    double* const* fl = c.field;
-    double* out_u = du ? du : c.dudt_buf;
-    double* out_v = dv ? dv : c.dvdt_buf;
-    if (c.P.smoothing) {
-        // the 8 fields the divergence needs (the wave-action density is smoothed only when read)
-        launch_smooth(c, F_WAD);
-        fl = c.smooth;
-    }
-    const int TW = G.nz <= 96 ? 32 : 16;
-    const size_t shm = sizeof(double) * 2 * (size_t)TW * G.nz;
-    const int ntx = (G.nx + TW - 1) / TW;
-    k_divergence<<<ntx * G.ny * G.members, kThreads, shm, s>>>(G, TW, fl[F_ZL], fl[F_ZP], fl[F_LL], fl[F_LP],
-                                                               fl[F_PL], fl[F_PP], fl[F_EL], fl[F_EP], c.rho_inv,
-                                                               out_u, out_v);
-    k_finalize<<<1, kThreads, 0, s>>>(c.ctl, c.budget, c.partials, c.max_blocks, mask, 1);
 }
 
 void run_step(Context& c, double dt, double* du, double* dv)

@@ -46,7 +46,7 @@ class Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("gamma_mode", C.c_int), ("saturation", C.c_int), ("smoothing", C.c_int),
                 ("flux_form", C.c_int), ("splitting", C.c_int), ("cap_per_column", C.c_int),
                 ("alpha_s", C.c_double), ("min_split_dz", C.c_double), ("max_rays", C.c_int64),
-                ("members", C.c_int)]
+                ("members", C.c_int), ("columnar", C.c_int)]
 
 
 class BgSource(C.Structure):

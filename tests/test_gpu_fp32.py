@@ -8,7 +8,10 @@ test holds them to the bounds the form is built for:
     A ray's share of a staggered cell is its vertical overlap with it; a position error of d moves
     flux d/dz between neighbouring interfaces of the column, so a ray that just grazes an interface
     (overlap of centimetres out of a kilometre) carries a large relative error there while the
-    column's flux is accurate -- the column scale measures that;
+    column's flux is accurate -- the column scale measures that.  The elastic terms E ~ f^2 are
+    held the same way: near the equator the relative error of f^2 is the FP32 position resolution
+    (about 1e-8 rad) over phi, so a ray within 1e-4 rad of the equator carries a 1e-4 relative
+    error in its (vanishing) elastic contribution;
   * integer bookkeeping: counts within 0.5 % (FP32 can move a ray across a threshold);
   * budget terms: relative 1e-5.
 """
@@ -69,7 +72,10 @@ def _report_and_check(T, O, grid, du, dv, odu, odv, label):
     field_errs = {}
     for n in oracle.FIELD_NAMES:
         S = O.field_abs(n)
-        field_errs[n] = scaled_error(T.field(n), O.field(n), col(S) if n.startswith("fz") else S)
+        # vertical fluxes and elastic terms by the column's largest S: a ray grazing an interface
+        # carries a large relative error in that interface's share, and E is proportional to f^2,
+        # whose relative error near the equator is the FP32 position resolution (1e-8 rad) over phi
+        field_errs[n] = scaled_error(T.field(n), O.field(n), col(S) if n.startswith(("fz", "e_")) else S)
     gs, os_ = T.stats(), O.stats()
     print("\n[%s] precision form vs FP64 oracle" % label)
     print("  ray state normwise:", {k: "%.1e" % v for k, v in errs.items()})
@@ -103,6 +109,17 @@ def test_precision_form_fplane(gw):
     rays["n"] = rays["n"] * 1e8
     out = _run(gw, grid, dict(synth.DEFAULT_PARAMS, cap_per_column=12), bg, None, rays, 12, 240.0)
     _report_and_check(*out[:2], grid, *out[2:], "f-plane 24x20x40, 12 steps")
+
+
+def test_precision_form_columnar_sphere(gw):
+    """The columnar (single-column) mode in the precision form: same bars as the 3-D form."""
+    grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+    bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+    rays = synth.sphere_rays(grid, 500, tag=71, z_lo=4e3, z_hi=20e3, ext_scale=2.5)
+    rays["n"] = rays["n"] * 30.0
+    out = _run(gw, grid, dict(synth.DEFAULT_PARAMS, cap_per_column=45, columnar=1), bg,
+               synth.background_source(z_launch=2e3), rays, 10, 300.0)
+    _report_and_check(*out[:2], grid, *out[2:], "columnar sphere 40x20x24, 10 steps")
 
 
 def test_precision_form_full_size_sphere(gw):

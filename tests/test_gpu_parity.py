@@ -139,6 +139,38 @@ def test_gamma2_matches_the_oracle(gw, geometry):
     np.testing.assert_allclose(g, o, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("geometry", ["sphere", "fplane"])
+def test_columnar_mode_parity(gw, geometry):
+    """Single-column mode (MS-GWaM-1D): the same parity bars as the 3-D model, and the horizontal
+    position, wavenumber and extents of every ray volume exactly as launched."""
+    if geometry == "sphere":
+        grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+        bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+        rays = synth.sphere_rays(grid, 777, tag=32, z_lo=4e3, z_hi=20e3, ext_scale=1.0)
+        dt = 300.0
+    else:
+        grid = synth.fplane_grid(nx=24, ny=20, nz=40, dx=40e3, dy=30e3, dz=500.0)
+        bg = synth.perturbed(synth.uniform_background(grid, U=5.0), tag=21, rel=0.1)
+        rays = synth.fplane_rays(grid, 1500, tag=22, z_lo=3e3, z_hi=15e3, ext_z=1300.0)
+        dt = 240.0
+    rays["n"] = rays["n"] * 30.0
+    params = dict(synth.DEFAULT_PARAMS, cap_per_column=45, columnar=1)
+    T, O = _pair(gw, grid, params, bg, 200000)
+    T.add_rays(rays)
+    O.add_rays(rays)
+    r0 = T.rays()
+    for s in range(8):
+        du, dv, odu, odv = _step_both(T, O, dt, grid["nz"], grid["ny"], grid["nx"])
+        if s % 3 == 2 or s == 7:
+            _compare_all(T, O, grid, du, dv, odu, odv)
+    r1 = T.rays()
+    assert T.stats()["n_split_h"] == 0
+    common, i0, i1 = np.intersect1d(r0["id"], r1["id"], return_indices=True)
+    assert len(common) > 0.5 * len(r0["id"])
+    for n in ("x", "y", "k", "l", "ex", "ey"):   # vertical splits move z, ez, pz only
+        np.testing.assert_array_equal(r1[n][i1], r0[n][i0])
+
+
 def test_spectral_launch_parity(gw):
     """Explicit spectral launches (convective-like source) incl. filtered bins."""
     grid = synth.sphere_grid(nx=36, ny=18, nz=30, dz=1000.0)
