@@ -115,12 +115,12 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------- oracle arm
 
-def oracle_throughput(steps: int, warmup: int):
+def oracle_throughput(steps: int, warmup: int, workload: str = "sphere"):
     """FP64 CPU oracle on the same workload: launch (untimed), `warmup` untimed steps, then
     `steps` timed steps; returns ray-volume steps/s and the timed sample."""
     import oracle
     from paper_2309_11257_gb300 import synth
-    w = synth.workload("sphere")
+    w = synth.workload(workload)
     M = oracle.Model(w["grid"], w["params"])
     M.set_background(*w["background"])
     M.launch_background(w["source"])
@@ -270,7 +270,7 @@ def gpu_arm(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cval, sample = oracle_throughput(2, 0)
+        cval, sample = oracle_throughput(2, 0, "sphere_columnar" if args.workload == "sphere_columnar" else "sphere")
         cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "2 oracle steps right after the launch of the full workload (%d ray-volume steps, "
                          "%.1f s), single thread" % (sample["ray_steps"], sample["seconds"])}
@@ -507,8 +507,10 @@ def main():
     ap.add_argument("--train-steps", type=int, default=800,
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
-                    choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate"],
+                    choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate",
+                             "sphere_columnar"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
+                         "sphere_columnar: the sphere in the single-column (MS-GWaM-1D) mode; "
                          "ensemble: 16 members of the sphere with convective sources, graph-replayed steps; "
                          "surrogate: MLP inference over 32768 columns after training on tracer drag")
     args = ap.parse_args()

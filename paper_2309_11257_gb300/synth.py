@@ -237,11 +237,12 @@ def workload(name: str) -> dict:
         params = dict(DEFAULT_PARAMS, saturation=0, smoothing=0)
         return dict(name=name, grid=grid, params=params, background=uniform_background(grid),
                     rays=fplane_rays(grid, 4096, tag=1), source=None, dt=300.0, steps=100)
-    if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32"):
+    if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32", "sphere_columnar"):
         nx, ny = {"sphere": (256, 128), "sphere_fp32": (512, 256), "sphere_half": (128, 64),
-                  "sphere_half_fp32": (128, 64)}[name]
+                  "sphere_half_fp32": (128, 64), "sphere_columnar": (256, 128)}[name]
         grid = sphere_grid(nx=nx, ny=ny, nz=90, dz=1000.0)
-        return dict(name=name, grid=grid, params=dict(DEFAULT_PARAMS), background=jet_background(grid),
+        params = dict(DEFAULT_PARAMS, columnar=1 if name == "sphere_columnar" else 0)
+        return dict(name=name, grid=grid, params=params, background=jet_background(grid),
                     rays=None, source=background_source(), dt=180.0, steps=200)
     raise KeyError(name)
 
