@@ -98,6 +98,9 @@ def _declare(lib):
     lib.orc_get_gamma2.argtypes = [C.c_void_p, _D]
     lib.orc_get_field_abs.argtypes = [C.c_void_p, C.c_int, _D]
     lib.orc_tendency_scale.argtypes = [C.c_void_p, _D, _D]
+    lib.orc_set_theta.argtypes = [C.c_void_p, _D]
+    lib.orc_theta_tendency.argtypes = [C.c_void_p, _D, _D]
+    lib.orc_theta_divergence.argtypes = [C.c_void_p, _D, _D, _D]
     lib.orc_gather.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, _D]
     lib.orc_dispersion.argtypes = [C.c_double] * 6 + [_D]
     lib.orc_rhs.argtypes = [C.c_void_p, _D, _D]
@@ -137,6 +140,8 @@ def _f64(a) -> np.ndarray:
 
 
 FIELD_NAMES = ("fz_l", "fz_p", "f_ll", "f_lp", "f_pl", "f_pp", "e_l", "e_p", "wad")
+THETA_FIELD_NAMES = ("t_l", "t_p")          # potential-temperature flux integrals (Eq. fluxes:temperature)
+ALL_FIELD_NAMES = FIELD_NAMES + THETA_FIELD_NAMES
 
 
 def _struct(cls, d: dict):
@@ -257,7 +262,7 @@ class Model:
         return s.as_dict()
 
     def field(self, name: str) -> np.ndarray:
-        which = FIELD_NAMES.index(name)
+        which = ALL_FIELD_NAMES.index(name)
         nl = self.nz + 1 if which < 2 else self.nz
         out = np.zeros((nl, self.ny, self.nx))
         self._lib.orc_get_field(self._h, which, _dp(out))
@@ -266,11 +271,33 @@ class Model:
     def field_abs(self, name: str) -> np.ndarray:
         """Sum of |contribution| of a projected field (the scale of its rounding error), each
         contribution taken with the ray volume's wave action before the step's saturation."""
-        which = FIELD_NAMES.index(name)
+        which = ALL_FIELD_NAMES.index(name)
         nl = self.nz + 1 if which < 2 else self.nz
         out = np.zeros((nl, self.ny, self.nx))
         self._lib.orc_get_field_abs(self._h, which, _dp(out))
         return out
+
+    def set_theta(self, theta):
+        """Reference potential temperature [nz][ny][nx] (positive)."""
+        t = _f64(theta)
+        if self._lib.orc_set_theta(self._h, _dp(t)) != 0:
+            raise ValueError("oracle rejected theta")
+
+    def theta_divergence(self, tl, tp):
+        """d theta/dt of given integrals T_l, T_p [nz][ny][nx]."""
+        out = np.zeros((self.nz, self.ny, self.nx))
+        if self._lib.orc_theta_divergence(self._h, _dp(_f64(tl)), _dp(_f64(tp)), _dp(out)) != 0:
+            raise ValueError("no theta set")
+        return out
+
+    def theta_tendency(self):
+        """(d theta/dt of the last step, its error scale), [nz][ny][nx] each."""
+        shape = (self.nz, self.ny, self.nx)
+        out = np.zeros(shape)
+        sc = np.zeros(shape)
+        if self._lib.orc_theta_tendency(self._h, _dp(out), _dp(sc)) != 0:
+            raise ValueError("no theta set")
+        return out, sc
 
     def tendency_scale(self):
         """Error scales of du/dt and dv/dt of the last step (magnitudes through the divergence)."""

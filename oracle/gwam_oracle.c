@@ -43,7 +43,7 @@
 #endif
 
 enum { SX, SY, SZ, SK, SL, SM, SEX, SEY, SEZ, SPX, SPY, SPZ, SN, NSTATE };
-enum { NFIELD_H = 7 };
+enum { NFIELD_H = 9 };
 
 struct orc_model {
     orc_grid G;
@@ -58,7 +58,9 @@ struct orc_model {
     int64_t next_id;
     orc_stats st;
     double *fz[2];                       /* vertical fluxes at level interfaces [nz+1][ny][nx] */
-    double *hf[NFIELD_H];                /* F_ll F_lp F_pl F_pp E_l E_p wave-action density [nz][ny][nx] */
+    double *hf[NFIELD_H];                /* F_ll F_lp F_pl F_pp E_l E_p wave-action density, and the
+                                            potential-temperature flux integrals T_l T_p [nz][ny][nx] */
+    double *theta;                       /* reference potential temperature [nz][ny][nx], or NULL */
     double *fzabs[2], *hfabs[NFIELD_H];  /* sums of |contribution| of the same fields (error scales) */
     double *n_scale;                     /* per ray: wave-action density before this step's saturation */
     int64_t n_scale_cap;
@@ -429,6 +431,7 @@ void orc_destroy(orc_model *m)
     free_fields(m);
     free_rays(m);
     free(m->n_scale);
+    free(m->theta);
     free(m);
 }
 
@@ -945,14 +948,19 @@ static void apply_saturation(orc_model *m, double dt)
  *   (f/g) e_r x <u'b'> = -(1 / (g rho)) f^2 N^2 ch_r / (w^2 - f^2) k_h A
  * (accumulated here without the 1/(g rho) factor, applied with the cell density later).
  * Pseudomomentum form (App. A): T^{ab} = ch_a k_b A, no elastic term. */
-/* the eight flux values of one ray volume with wave action A (all linear in A):
- * out = {T_ll, T_lp, T_pl, T_pp, E_l, E_p, Z_l, Z_p} */
-static void ray_fluxes(const orc_model *m, const disp_t *d, double f2, double n2, double kk, double ll, double A,
-                       double out[8])
+/* the ten flux values of one ray volume with wave action A (all linear in A):
+ * out = {T_ll, T_lp, T_pl, T_pp, E_l, E_p, Z_l, Z_p, Th_l, Th_p}; the last two are the integrand of
+ * Eq. fluxes:temperature without its theta-bar / (g rho-bar) factor (applied with the cell values):
+ *   <u'theta'> (g rho / theta) = ch_r f N^2 / (w^2 - f^2) (e_r x k_h) A,  e_r x k_h = (-l, k),
+ * f the signed Coriolis parameter at the ray; zero in the pseudomomentum form (App. A). */
+static void ray_fluxes(const orc_model *m, const disp_t *d, double f, double f2, double n2, double kk, double ll,
+                       double A, double out[10])
 {
     const double *ch = d->ch;
     if (m->P.flux_form == 0) {
         double den = d->w2 - f2;
+        out[8] = -f * n2 * ch[2] / den * ll * A;
+        out[9] = f * n2 * ch[2] / den * kk * A;
         out[0] = (d->w2 * ch[0] * kk + f2 * ch[1] * ll) / den * A;
         out[1] = (d->w2 * ch[0] * ll - f2 * ch[1] * kk) / den * A;
         out[2] = (d->w2 * ch[1] * kk - f2 * ch[0] * ll) / den * A;
@@ -970,6 +978,8 @@ static void ray_fluxes(const orc_model *m, const disp_t *d, double f2, double n2
         out[5] = 0.0;
         out[6] = ch[2] * kk * A;
         out[7] = ch[2] * ll * A;
+        out[8] = 0.0;
+        out[9] = 0.0;
     }
 }
 
@@ -1001,9 +1011,10 @@ static void project(orc_model *m)
         spectral_extents(m, s, &dk, &dl, &dm);
         double A = s[SN] * dk * dl * dm;
         double A_scale = (m->n_scale_valid ? m->n_scale[q] : fabs(s[SN])) * dk * dl * dm;
-        double fl[8], fa[8];
-        ray_fluxes(m, &d, f2, n2, s[SK], s[SL], A, fl);
-        ray_fluxes(m, &d, f2, n2, s[SK], s[SL], A_scale, fa);
+        double fl[10], fa[10];
+        const double fsgn = is_sphere(m) ? 2.0 * m->G.omega * sin(s[SY]) : m->G.f0;
+        ray_fluxes(m, &d, fsgn, f2, n2, s[SK], s[SL], A, fl);
+        ray_fluxes(m, &d, fsgn, f2, n2, s[SK], s[SL], A_scale, fa);
         double t_ll = fl[0], t_lp = fl[1], t_pl = fl[2], t_pp = fl[3], e_l = fl[4], e_p = fl[5];
         double z_l = fl[6], z_p = fl[7];
         /* horizontal fluxes: cell average over the ray volumes whose carrier lies in the cell,
@@ -1017,7 +1028,9 @@ static void project(orc_model *m)
         m->hf[4][c] += alpha * e_l;
         m->hf[5][c] += alpha * e_p;
         m->hf[6][c] += alpha * A;
-        double hv[NFIELD_H] = {fa[0], fa[1], fa[2], fa[3], fa[4], fa[5], A_scale};
+        m->hf[7][c] += alpha * fl[8];
+        m->hf[8][c] += alpha * fl[9];
+        double hv[NFIELD_H] = {fa[0], fa[1], fa[2], fa[3], fa[4], fa[5], A_scale, fa[8], fa[9]};
         for (int f = 0; f < NFIELD_H; ++f) m->hfabs[f][c] += fabs(alpha * hv[f]);
         /* vertical fluxes at the cell interfaces z = kk dz, 1 <= kk <= nz-1: integrate over the
          * staggered cell [(kk - 1/2) dz, (kk + 1/2) dz] of the carrier column; the weight is the
@@ -1198,6 +1211,73 @@ int orc_get_field_abs(const orc_model *m, int which, double *out)
         return 0;
     }
     return -1;
+}
+
+/* reference potential temperature theta-bar at the nodes, C-order [nz][ny][nx] (positive) */
+int orc_set_theta(orc_model *m, const double *theta)
+{
+    size_t nc = (size_t)m->G.nx * m->G.ny * m->G.nz;
+    for (size_t q = 0; q < nc; ++q)
+        if (!(theta[q] > 0.0) || !isfinite(theta[q])) return -1;
+    if (!m->theta) m->theta = malloc(nc * sizeof(double));
+    memcpy(m->theta, theta, nc * sizeof(double));
+    return 0;
+}
+
+/* Eq. mean-flow-impact-t: d theta / dt = -div <u'theta'>, <u'theta'> horizontal (along e_r x k_h)
+ * and equal to theta-bar / (g rho-bar) times the projected integrals T_l, T_p of each cell (Eq.
+ * fluxes:temperature).  The horizontal divergence as in orc_divergence: centred differences,
+ * (1/(r cos phi)) [d/dlambda Th_l + d/dphi (cos phi Th_p)], flux zero beyond the pole rows; zero in
+ * the columnar mode.  With mag != 0 every difference becomes a sum of magnitudes (error scale). */
+static void theta_div(const orc_model *m, const double *tl, const double *tp, double *out, int mag)
+{
+    long nx = m->G.nx, ny = m->G.ny, nz = m->G.nz;
+    double dX = cell_x(m), dY = cell_y(m), dz = m->G.dz;
+    double sg = mag ? -1.0 : 1.0;     /* (east - sg west): a difference, or a sum of magnitudes */
+    for (long k = 0; k < nz; ++k)
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                size_t c = node(m, k, j, i);
+                if (m->P.columnar) {
+                    out[c] = 0.0;
+                    continue;
+                }
+#define THF(arr, cc) ((arr)[cc] * m->theta[cc] / (m->G.g * m->rho[cc]))
+                size_t ce = node(m, k, j, wrap_index(i + 1, nx)), cw = node(m, k, j, wrap_index(i - 1, nx));
+                double div;
+                if (is_sphere(m)) {
+                    double r = m->G.radius + (k + 0.5) * dz;
+                    double cphi = cos(row_lat(m, j));
+                    double yn = 0.0, ys = 0.0;
+                    if (j + 1 < ny) yn = cos(row_lat(m, j + 1)) * THF(tp, node(m, k, j + 1, i));
+                    if (j - 1 >= 0) ys = cos(row_lat(m, j - 1)) * THF(tp, node(m, k, j - 1, i));
+                    double dl = (THF(tl, ce) - sg * THF(tl, cw)) / (2.0 * dX);
+                    double dp = (yn - sg * ys) / (2.0 * dY);
+                    div = (dl + dp) / (r * cphi);
+                } else {
+                    size_t cn = node(m, k, wrap_index(j + 1, ny), i), cs = node(m, k, wrap_index(j - 1, ny), i);
+                    div = (THF(tl, ce) - sg * THF(tl, cw)) / (2.0 * dX) + (THF(tp, cn) - sg * THF(tp, cs)) / (2.0 * dY);
+                }
+#undef THF
+                out[c] = mag ? div : -div;
+            }
+}
+
+/* the potential-temperature tendency of given integrals T_l, T_p (C-order [nz][ny][nx]) */
+int orc_theta_divergence(const orc_model *m, const double *tl, const double *tp, double *out)
+{
+    if (!m->theta) return -1;
+    theta_div(m, tl, tp, out, 0);
+    return 0;
+}
+
+/* the tendency of the last step's (smoothed) integrals, and its error scale (may be NULL) */
+int orc_theta_tendency(const orc_model *m, double *out, double *scale)
+{
+    if (!m->theta) return -1;
+    theta_div(m, m->hf[7], m->hf[8], out, 0);
+    if (scale) theta_div(m, m->hfabs[7], m->hfabs[8], scale, 1);
+    return 0;
 }
 
 int orc_get_field(const orc_model *m, int which, double *out)

@@ -103,13 +103,21 @@ int64_t orc_num_rays(const orc_model *m);
 /* state: 13 arrays of n in the order x y z k l m dX dY dZ Px Py Pz N (array order) */
 int orc_get_rays(const orc_model *m, double *state13, int64_t *ids, int32_t *cells);
 void orc_get_stats(const orc_model *m, orc_stats *out);
-/* grid fields of the last step: which = 0..8 ->
- * Fz_lambda, Fz_phi ([nz+1][ny][nx]), F_ll, F_lp, F_pl, F_pp, E_l, E_p, wave-action density ([nz][ny][nx]) */
+/* grid fields of the last step: which = 0..10 ->
+ * Fz_lambda, Fz_phi ([nz+1][ny][nx]), F_ll, F_lp, F_pl, F_pp, E_l, E_p, wave-action density, and the
+ * potential-temperature flux integrals T_l, T_p of Eq. fluxes:temperature without theta-bar / (g rho-bar)
+ * ([nz][ny][nx]) */
 int orc_get_field(const orc_model *m, int which, double *out);
 /* error scales: sums of |contribution| of a field (each with the ray volume's wave action before the
  * step's saturation), and the tendency formula applied to them */
 int orc_get_field_abs(const orc_model *m, int which, double *out);
 int orc_tendency_scale(const orc_model *m, double *du_scale, double *dv_scale);
+/* reference potential temperature [nz][ny][nx] (positive; -1 otherwise) and the potential-temperature
+ * tendency of the last step (Eq. mean-flow-impact-t) with its error scale (scale may be NULL) */
+int orc_set_theta(orc_model *m, const double *theta);
+int orc_theta_tendency(const orc_model *m, double *out, double *scale);
+/* the same divergence of given integrals T_l, T_p (C-order [nz][ny][nx]) */
+int orc_theta_divergence(const orc_model *m, const double *tl, const double *tp, double *out);
 /* Gamma^2 node field [nz][ny][nx] */
 int orc_get_gamma2(const orc_model *m, double *out);
 

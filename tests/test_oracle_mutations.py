@@ -43,6 +43,11 @@ MUTATIONS = {
                        "double dp_u = (pl_n - pl_s) / (2.0 * dY);"),
     # bookkeeping
     "split_id_reuse": ("oid[1] = m->next_id++;", "oid[1] = m->next_id;"),
+    # potential-temperature flux and tendency
+    "theta_flux_sign": ("out[8] = -f * n2 * ch[2] / den * ll * A;", "out[8] = f * n2 * ch[2] / den * ll * A;"),
+    "theta_flux_component": ("out[9] = f * n2 * ch[2] / den * kk * A;", "out[9] = f * n2 * ch[2] / den * ll * A;"),
+    "theta_div_cos": ("if (j + 1 < ny) yn = cos(row_lat(m, j + 1)) * THF(tp, node(m, k, j + 1, i));",
+                      "if (j + 1 < ny) yn = THF(tp, node(m, k, j + 1, i));"),
     # columnar mode (single-column approximation)
     "columnar_metric_term": ("        F[5] = -G[2];\n    } else if (is_sphere(m)) {",
                              "        F[5] = -G[2] + k * cg[0] / r;\n    } else if (is_sphere(m)) {"),

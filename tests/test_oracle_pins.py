@@ -639,6 +639,12 @@ def test_fluxes_follow_plane_wave_polarization():
         ub = np.array([mo["ub"], mo["vb"]])
         e0 = f0 * np.array([-ub[1], ub[0]]) * rho
         np.testing.assert_allclose(E, scale * (R @ e0), rtol=1e-10, atol=1e-12 * abs(scale * e0).max())
+        # potential-temperature flux (Eq. fluxes:temperature) with theta' = theta-bar b' / g: the
+        # projected integrals are g rho <u'theta'> / theta-bar = rho <u'b'>, a vector along e_r x k_h
+        Th = np.array([M.field("t_l")[c], M.field("t_p")[c]])
+        np.testing.assert_allclose(Th, scale * (R @ (rho * ub)), rtol=1e-10, atol=1e-12 * abs(scale * ub).max())
+        # and Eq. fluxes:buoyancy: the elastic term is f e_r x of it
+        np.testing.assert_allclose(E, f0 * np.array([-Th[1], Th[0]]), rtol=1e-12)
         # vertical flux of horizontal momentum: rho <w'u'> over the interfaces it covers
         fz = np.array([M.field("fz_l")[:, 4, 3].sum(), M.field("fz_p")[:, 4, 3].sum()])
         wu = R @ np.array([mo["wu"], mo["wv"]])
@@ -861,3 +867,35 @@ def test_columnar_divergence_keeps_only_the_vertical_flux_and_elastic_terms():
     exp_v = -(f["fz_p"][1:] - f["fz_p"][:-1]) / 1000.0 / rho + f["e_p"] / (gr * rho)
     np.testing.assert_allclose(du, exp_u, rtol=1e-12, atol=0)
     np.testing.assert_allclose(dv, exp_v, rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------------------------ potential temperature (Eq. mean-flow-impact-t)
+
+def test_theta_tendency_closed_forms():
+    """d theta/dt = -div <u'theta'> with <u'theta'> = theta-bar/(g rho-bar) T: a sinusoid in x has
+    the closed-form centred difference; uniform T contributes nothing; on the sphere T_phi ~ 1/cos
+    phi (flux form) gives zero; the columnar mode drops the horizontal divergence."""
+    grid = synth.fplane_grid(nx=16, ny=8, nz=10, dz=500.0)
+    bg = synth.uniform_background(grid)
+    M = model(grid, None, bg)
+    rho = bg[3]
+    M.set_theta(grid["g"] * rho)               # theta-bar / (g rho-bar) = 1
+    x, y, z = synth.node_coords(grid)
+    Lx = 16 * grid["dx"]
+    kx = 2 * math.pi / Lx
+    tl = np.broadcast_to(np.sin(kx * x)[None, None, :], (10, 8, 16)).copy()
+    tp = np.full((10, 8, 16), 3.0)
+    out = M.theta_divergence(tl, tp)
+    expect = -(np.cos(kx * x) * math.sin(kx * grid["dx"]) / grid["dx"])[None, None, :]
+    np.testing.assert_allclose(out, np.broadcast_to(expect, out.shape), rtol=1e-10, atol=1e-18)
+    Mc = model(grid, dict(columnar=1), bg)
+    Mc.set_theta(grid["g"] * rho)
+    assert np.all(Mc.theta_divergence(tl, tp) == 0.0)
+    sg = synth.sphere_grid(nx=16, ny=10, nz=6, dz=1000.0)
+    sbg = _sphere_bg(sg)
+    Ms = model(sg, None, sbg)
+    Ms.set_theta(sg["g"] * sbg[3])
+    _, phi, _ = synth.node_coords(sg)
+    tp_s = np.broadcast_to((1.0 / np.cos(phi))[None, :, None], (6, 10, 16)).copy()
+    out = Ms.theta_divergence(np.zeros((6, 10, 16)), tp_s)
+    np.testing.assert_allclose(out[:, 1:-1, :], 0.0, atol=1e-20)
