@@ -92,6 +92,9 @@ typedef struct {
                              horizontal wavenumber and horizontal extents fixed, dm/dt = -dOmega/dz --
                              and du/dt, dv/dt from the vertical flux divergence and the elastic term
                              only; 0: the 3-D model */
+    int theta_flux;       /* 1: also project the potential-temperature flux of Eq. fluxes:temperature
+                             (fields 9, 10 of gwam_get_field_host) for gwam_get_theta_tendency_host;
+                             FP64 form only (GWAM_EINVAL with precision 1) */
 } gwam_params;
 
 /* Background source of Sec. 3c: alpha(phi) profile, F_sol = alpha(phi) F_s + alpha(-phi) F_w,
@@ -201,9 +204,19 @@ int gwam_get_rays_host(gwam_ctx *ctx, double *state13_host, int64_t *ids_host, i
 /* Counters and budget (synchronising; returns a pending device status). */
 int gwam_get_stats(gwam_ctx *ctx, gwam_stats *out);
 /* Grid field of the last step into host memory, [members] outermost: 0 Fz_lambda, 1 Fz_phi
- * ([nz+1][ny][nx]), 2 F_ll, 3 F_lp, 4 F_pl, 5 F_pp, 6 E_lambda, 7 E_phi, 8 wave-action density ([nz][ny][nx]);
- * fluxes after smoothing when it is on; E_* without the 1/(g rho) factor. */
+ * ([nz+1][ny][nx]), 2 F_ll, 3 F_lp, 4 F_pl, 5 F_pp, 6 E_lambda, 7 E_phi, 8 wave-action density, 9 T_lambda,
+ * 10 T_phi ([nz][ny][nx]; 9 and 10 only with theta_flux = 1: g rho-bar <u'theta'> / theta-bar of Eq.
+ * fluxes:temperature); fluxes after smoothing when it is on; E_* without the 1/(g rho) factor. */
 int gwam_get_field_host(gwam_ctx *ctx, int which, double *out_host);
+/* Reference potential temperature theta-bar of Eq. fluxes:temperature: device array
+ * [members][nz][ny][nx], copied; GWAM_ENUMERIC unless every value is positive and finite. */
+int gwam_set_theta(gwam_ctx *ctx, const double *theta);
+/* Potential-temperature tendency of the last step (Eq. mean-flow-impact-t), d theta/dt =
+ * -div <u'theta'> with <u'theta'> = theta-bar / (g rho-bar) times the projected integrals of fields
+ * 9, 10 (smoothed when smoothing is on), horizontal centred differences as in the momentum
+ * divergence, zero in the columnar mode; into host memory [members][nz][ny][nx].  Needs
+ * theta_flux = 1, gwam_set_theta and a background (GWAM_ESTATE otherwise).  Synchronises. */
+int gwam_get_theta_tendency_host(gwam_ctx *ctx, double *out_host);
 /* Gamma^2 node field [members][nz][ny][nx] into host memory. */
 int gwam_get_gamma2_host(gwam_ctx *ctx, double *out_host);
 int gwam_synchronize(gwam_ctx *ctx);

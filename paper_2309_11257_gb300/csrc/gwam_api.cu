@@ -34,7 +34,7 @@ static void dalloc(Context& c, T*& p, size_t count)
 static void free_all(Context& c)
 {
     void* ptrs[] = {c.bg, c.bg32, c.bgdf, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.tables_df,
-                    c.bg_scratch,
+                    c.bg_scratch, c.theta,
                     c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
                     c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
                     c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
@@ -131,6 +131,8 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
     if (grid->nz > 192) return GWAM_EINVAL;   // column tiles of the transposing kernels live in shared memory
     if (params->precision != 0 && params->precision != 1) return GWAM_EINVAL;
     if (params->columnar != 0 && params->columnar != 1) return GWAM_EINVAL;
+    if (params->theta_flux != 0 && params->theta_flux != 1) return GWAM_EINVAL;
+    if (params->theta_flux && params->precision == 1) return GWAM_EINVAL;
     if (params->max_rays < 1 || params->max_rays >= ((int64_t)1 << 29)) return GWAM_EINVAL;
     if (!(params->alpha_s > 0.0) || !(params->min_split_dz >= 0.0)) return GWAM_EINVAL;
     if (params->flux_form != 0 && params->flux_form != 1) return GWAM_EINVAL;
@@ -198,6 +200,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         P.flux_form = params->flux_form;
         P.splitting = params->splitting;
         G.columnar = params->columnar;
+        P.theta_flux = params->theta_flux;
         P.cap = params->cap_per_column;
         P.alpha_s = params->alpha_s;
         P.f_alpha_s = (float)params->alpha_s;
@@ -296,6 +299,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
             G.df_2omega = split(2.0 * G.omega);
             G.df_8omega2 = split(8.0 * G.omega * G.omega);
             G.df_f0sq = split(G.f0 * G.f0);
+            G.df_f0 = split(G.f0);
             dalloc(c, c.tables32, t32.size());
             GWAM_CUDA(cudaMemcpy(c.tables32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
             G.row_cos32 = c.tables32;
@@ -793,6 +797,52 @@ int gwam_get_field_host(gwam_ctx* ctx, int which, double* out_host)
     API_END
 }
 
+int gwam_set_theta(gwam_ctx* ctx, const double* theta)
+{
+    API_BEGIN(ctx)
+    if (!theta) return GWAM_EINVAL;
+    if (!c.theta) dalloc(c, c.theta, (size_t)c.G.ncell_all);
+    GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
+    launch_set_theta(c, theta);
+    GWAM_CUDA(cudaMemcpyAsync(c.flag_host, c.flag_dev, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
+    if (*c.flag_host) {
+        c.err = "gwam_set_theta: theta must be positive and finite";
+        cudaFree(c.theta);
+        c.theta = nullptr;
+        return GWAM_ENUMERIC;
+    }
+    API_END
+}
+
+int gwam_get_theta_tendency_host(gwam_ctx* ctx, double* out_host)
+{
+    API_BEGIN(ctx)
+    if (!out_host) return GWAM_EINVAL;
+    if (!c.P.theta_flux || !c.theta || !c.have_bg) {
+        c.err = "gwam_get_theta_tendency_host: needs theta_flux = 1, gwam_set_theta and a background";
+        return GWAM_ESTATE;
+    }
+    check_pending(c);
+    const double* tl = c.field[F_TL];
+    const double* tp = c.field[F_TP];
+    if (c.P.smoothing) {
+        smooth_field(c, F_TL);
+        smooth_field(c, F_TP);
+        tl = c.smooth[F_TL];
+        tp = c.smooth[F_TP];
+    }
+    double* tmp = nullptr;
+    GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(double) * (size_t)c.G.ncell_all));
+    launch_theta_div(c, tl, tp, tmp);
+    GWAM_CUDA(cudaMemcpyAsync(out_host, tmp, sizeof(double) * (size_t)c.G.ncell_all, cudaMemcpyDeviceToHost,
+                              c.stream));
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    cudaFree(tmp);
+    API_END
+}
+
 int gwam_get_gamma2_host(gwam_ctx* ctx, double* out_host)
 {
     API_BEGIN(ctx)
@@ -816,7 +866,7 @@ struct CkptHeader {
     char magic[8];
     uint32_t version, header_bytes;
     int32_t precision, geometry, nx, ny, nz, members;
-    int32_t gamma_mode, saturation, smoothing, flux_form, splitting, cap, columnar, pad0;
+    int32_t gamma_mode, saturation, smoothing, flux_form, splitting, cap, columnar, theta_flux;
     double dX, dY, dz, radius, omega, f0, g, alpha_s, min_split_dz;
     int64_t n;
     int32_t have_bg, pad;
@@ -844,6 +894,7 @@ void fill_header(const Context& c, CkptHeader& h)
     h.splitting = c.P.splitting;
     h.cap = c.P.cap;
     h.columnar = c.G.columnar;
+    h.theta_flux = c.P.theta_flux;
     h.dX = c.G.dX;
     h.dY = c.G.dY;
     h.dz = c.G.dz;
@@ -862,7 +913,7 @@ bool same_config(const CkptHeader& a, const CkptHeader& b)
            a.precision == b.precision && a.geometry == b.geometry && a.nx == b.nx && a.ny == b.ny && a.nz == b.nz &&
            a.members == b.members && a.gamma_mode == b.gamma_mode && a.saturation == b.saturation &&
            a.smoothing == b.smoothing && a.flux_form == b.flux_form && a.splitting == b.splitting &&
-           a.cap == b.cap && a.columnar == b.columnar && a.dX == b.dX && a.dY == b.dY && a.dz == b.dz && a.radius == b.radius &&
+           a.cap == b.cap && a.columnar == b.columnar && a.theta_flux == b.theta_flux && a.dX == b.dX && a.dY == b.dY && a.dz == b.dz && a.radius == b.radius &&
            a.omega == b.omega && a.f0 == b.f0 && a.g == b.g && a.alpha_s == b.alpha_s &&
            a.min_split_dz == b.min_split_dz;
 }

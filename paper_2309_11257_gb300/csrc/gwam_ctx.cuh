@@ -35,7 +35,8 @@ struct DevBudget {
     double w_total, w_launched, w_saturated, w_exited, w_capped, w_invalid;
 };
 
-enum FieldId { F_ZL, F_ZP, F_LL, F_LP, F_PL, F_PP, F_EL, F_EP, F_WAD, NFIELD };
+// F_TL, F_TP: the potential-temperature flux integrals (projected only with Params.theta_flux)
+enum FieldId { F_ZL, F_ZP, F_LL, F_LP, F_PL, F_PP, F_EL, F_EP, F_WAD, F_TL, F_TP, NFIELD };
 
 struct LaunchCfg {
     int threads, blocks;
@@ -58,6 +59,7 @@ struct Context {
     Node* bg = nullptr;          // U V N2 G2 per node
     double* rho = nullptr;          // rho per node
     double* rho_inv = nullptr;      // 1 / rho per node
+    double* theta = nullptr;        // reference potential temperature per node (gwam_set_theta)
     double* tables = nullptr;       // row_cos[ny], row_inv_cos[ny], lev_inv_r[nz]
     float* tables32 = nullptr;      // row_cos32[ny], whf32[ny], ivol32[ny * nz]
     float2* tables_df = nullptr;    // row_cos, row_inv_cos [ny], lev_inv_r [nz] as double-float pairs
@@ -156,6 +158,10 @@ struct Context {
 };
 
 // kernels, launched from the host side (gwam_step.cu / gwam_launch.cu)
+// reference potential temperature (caller layout -> column-major) and the theta tendency of the
+// last step's T fields into the caller layout
+void launch_set_theta(Context& c, const double* theta);
+void launch_theta_div(Context& c, const double* tl, const double* tp, double* out);
 // derived background arrays (1/rho, gradients, gather copies) from restored nodes and rho
 void restore_background(Context& c, int member);
 void launch_set_background(Context& c, int member, const double* u, const double* v, const double* n2,

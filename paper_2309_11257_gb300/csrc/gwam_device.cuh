@@ -75,7 +75,7 @@ struct Grid {
     const float* ivol32;        // [ny * nz]: 1 / cell volume of row j, level k
     const float* whf32;         // [ny]: row_inv_cos * inv_dX * inv_dY (solid-angle share per unit extent)
     // double-float constants and row tables of the FP64 form's ray equations
-    float2 df_radius, df_2omega, df_8omega2, df_f0sq;
+    float2 df_radius, df_2omega, df_8omega2, df_f0sq, df_f0;
     const float2* row_sc_df;    // [ny][2]: sin, cos of every row centre (sphere)
     const double* row_lat;      // [ny]: latitude of every row centre
     const float2* whf_df;       // [ny]: row_inv_cos * inv_dX * inv_dY
@@ -90,7 +90,7 @@ struct Grid {
 };
 
 struct Params {
-    int gamma_mode, saturation, smoothing, flux_form, splitting, cap;
+    int gamma_mode, saturation, smoothing, flux_form, splitting, cap, theta_flux;
     double alpha_s, min_split_dz;
     float f_alpha_s;
 };
@@ -652,7 +652,7 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
 // saturation and projection): wavenumbers, f^2, N^2 and the dispersion terms, from N^2 and Gamma^2
 // interpolated alone.
 struct IntrDF {
-    DF k, l, m, kh2, m2, mg2, f2, n2;
+    DF k, l, m, kh2, m2, mg2, f, f2, n2;   // f: the signed Coriolis parameter at the ray
     DispDF d;
 };
 
@@ -665,9 +665,10 @@ __device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __rest
     if (G.geometry == 1) {
         DF sphi, cphi;
         lat_sincos_df(G, Y, sphi, cphi);
-        const DF f = df_mul2(DF{G.df_2omega.x, G.df_2omega.y}, sphi);
-        in.f2 = df_mul2(f, f);
+        in.f = df_mul2(DF{G.df_2omega.x, G.df_2omega.y}, sphi);
+        in.f2 = df_mul2(in.f, in.f);
     } else {
+        in.f = DF{G.df_f0.x, G.df_f0.y};
         in.f2 = DF{G.df_f0sq.x, G.df_f0sq.y};
     }
     in.k = df_split(s[SK]);

@@ -710,7 +710,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
                                               reinterpret_cast<const float*>(c.k2), (float)dt,
                                               reinterpret_cast<float*>(c.kappa));
     prof_mark(c, 3);
-    for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
+    for (int f = 0; f < F_TL; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);
     k_project32<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B32, c.bg32, c.ctl, off2, reinterpret_cast<const float*>(c.kappa),
                                                  reinterpret_cast<const float*>(c.k2), dt, c.field[F_ZL],

@@ -195,6 +195,71 @@ void restore_background(Context& c, int member)
                                                         c.f32 ? c.bg32 + o : nullptr);
 }
 
+// caller [members][nz][ny][nx] -> column-major reference potential temperature; flags values that
+// are not positive and finite
+__global__ void k_set_theta(Grid G, const double* __restrict__ theta, double* __restrict__ out, int* flags)
+{
+    const int64_t total = (int64_t)G.ncell_all;
+    int bad = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t mem = t / G.ncell, r = t - mem * G.ncell;
+        const int i = (int)(r % G.nx), j = (int)((r / G.nx) % G.ny), k = (int)(r / G.ncol);
+        const double v = theta[t];
+        if (!(v > 0.0) || nonfinite_bits(v)) bad = 1;
+        out[mem * G.ncell + node_index(G, i, j, k)] = v;
+    }
+    if (bad) atomicOr(flags, BG_NONFINITE);
+}
+
+void launch_set_theta(Context& c, const double* theta)
+{
+    const int blocks = (int)std::min<int64_t>((c.G.ncell_all + kThreads - 1) / kThreads, 16384);
+    k_set_theta<<<blocks, kThreads, 0, c.stream>>>(c.G, theta, c.theta, c.flag_dev);
+}
+
+// Eq. mean-flow-impact-t: d theta/dt = -div <u'theta'>, <u'theta'> = theta-bar / (g rho-bar) T per cell
+// from the (smoothed) integrals T_l, T_p; horizontal centred differences as in the momentum
+// divergence (flux zero beyond the pole rows), zero in the columnar mode.  Output in the caller's
+// [members][nz][ny][nx].  FP64: an on-demand diagnostic, not a per-step kernel.
+__global__ void k_theta_div(Grid G, const double* __restrict__ tl, const double* __restrict__ tp,
+                            const double* __restrict__ theta, const double* __restrict__ rho_inv,
+                            double* __restrict__ out)
+{
+    const int64_t total = (int64_t)G.ncell_all;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t mem = t / G.ncell, r = t - mem * G.ncell;
+        const int i = (int)(r % G.nx), j = (int)((r / G.nx) % G.ny), k = (int)(r / G.ncol);
+        if (G.columnar) {
+            out[t] = 0.0;
+            continue;
+        }
+        const int64_t o = mem * G.ncell;
+        auto thf = [&](const double* a, int ii, int jj) {
+            const int64_t c = o + node_index(G, ii, jj, k);
+            return a[c] * theta[c] * rho_inv[c] * G.inv_g;
+        };
+        const int ie = i + 1 == G.nx ? 0 : i + 1, iw = i == 0 ? G.nx - 1 : i - 1;
+        double div;
+        if (G.geometry == 1) {
+            const double yn = j + 1 < G.ny ? G.row_cos[j + 1] * thf(tp, i, j + 1) : 0.0;
+            const double ys = j - 1 >= 0 ? G.row_cos[j - 1] * thf(tp, i, j - 1) : 0.0;
+            const double dl = (thf(tl, ie, j) - thf(tl, iw, j)) * (0.5 * G.inv_dX);
+            const double dp = (yn - ys) * (0.5 * G.inv_dY);
+            div = (dl + dp) * G.row_inv_cos[j] * G.lev_inv_r[k];
+        } else {
+            const int jn = j + 1 == G.ny ? 0 : j + 1, js = j == 0 ? G.ny - 1 : j - 1;
+            div = (thf(tl, ie, j) - thf(tl, iw, j)) * (0.5 * G.inv_dX) + (thf(tp, i, jn) - thf(tp, i, js)) * (0.5 * G.inv_dY);
+        }
+        out[t] = -div;
+    }
+}
+
+void launch_theta_div(Context& c, const double* tl, const double* tp, double* out)
+{
+    const int blocks = (int)std::min<int64_t>((c.G.ncell_all + kThreads - 1) / kThreads, 16384);
+    k_theta_div<<<blocks, kThreads, 0, c.stream>>>(c.G, tl, tp, c.theta, c.rho_inv, out);
+}
+
 // ----------------------------------------------------------------------------- explicit rays
 
 // pass 0 validates, pass 1 writes at n + q with id next_id + q

@@ -452,6 +452,7 @@ __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int nc
 //   pseudomomentum form (App. A): T^{ab} = ch_a k_b A
 // Centre fields: cell averages over the ray volumes whose carrier is in the cell, weight V_j/V_c.
 // Interface fields (z = kk dz, 1 <= kk < nz): staggered-cell overlap, weight w_h * overlap / dz.
+template <bool THETA>
 __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B, const NodeDF* __restrict__ bg,
                                                         const Ctl* ctl, const int* __restrict__ off2,
                                                         const double* __restrict__ kappa,
@@ -460,9 +461,11 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                                                         double* __restrict__ f_ll, double* __restrict__ f_lp,
                                                         double* __restrict__ f_pl, double* __restrict__ f_pp,
                                                         double* __restrict__ e_l, double* __restrict__ e_p,
-                                                        double* __restrict__ wad, double* __restrict__ partials,
+                                                        double* __restrict__ wad, double* __restrict__ f_tl,
+                                                        double* __restrict__ f_tp, double* __restrict__ partials,
                                                         int pstride)
 {
+    constexpr int NH = THETA ? 9 : 7;   // centre fields of the segmented sums
     const int n = ctl->status ? 0 : off2[G.ncell_all];
     double w_sat = 0.0, w_tot = 0.0;
     const int stride = gridDim.x * blockDim.x;
@@ -470,9 +473,9 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
         const int p = p0 + threadIdx.x;
         const bool act = p < n;
         int key = -1;
-        DF hv[7];
+        DF hv[NH];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) hv[q] = df_f(0.0f);
+        for (int q = 0; q < NH; ++q) hv[q] = df_f(0.0f);
         DF zl = df_f(0.0f), zp = df_f(0.0f), lo = df_f(0.0f), hi = df_f(0.0f);
         int col = 0, kk0 = 1, nkk = 0;
         if (act) {
@@ -518,6 +521,12 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                 const DF ec = df_neg(df_mul2(df_mul2(df_mul2(in.f2, in.n2), chr), iden));
                 el = df_mul2(ec, in.k);
                 ep = df_mul2(ec, in.l);
+                if (THETA) {
+                    // Eq. fluxes:temperature without theta-bar / (g rho-bar): ch_r f N^2 / (w^2 - f^2) (e_r x k_h)
+                    const DF tc = df_mul2(df_mul2(df_mul2(in.f, in.n2), chr), iden);
+                    hv[7 % NH] = df_mul2(aw, df_neg(df_mul2(tc, in.l)));
+                    hv[8 % NH] = df_mul2(aw, df_mul2(tc, in.k));
+                }
             } else {
                 t_ll = df_mul2(chx, in.k);
                 t_lp = df_mul2(chx, in.l);
@@ -556,9 +565,9 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
         // centre fields: warp-segmented reduction over runs of equal cells, one atomic per run
         const bool own = warp_run_interior(key);
         if (warp_segment_reduce_df(key, hv) && key >= 0) {
-            double v[7];
+            double v[NH];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) v[q] = df_to_double(hv[q]);
+            for (int q = 0; q < NH; ++q) v[q] = df_to_double(hv[q]);
             if (own) {
                 // the whole cell is this run: store its sum (fields were zeroed before the launch)
                 f_ll[key] = v[0];
@@ -568,6 +577,10 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                 e_l[key] = v[4];
                 e_p[key] = v[5];
                 wad[key] = v[6];
+                if (THETA) {
+                    f_tl[key] = v[7 % NH];
+                    f_tp[key] = v[8 % NH];
+                }
             } else {
                 atomicAdd(&f_ll[key], v[0]);
                 atomicAdd(&f_lp[key], v[1]);
@@ -576,6 +589,10 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
                 atomicAdd(&e_l[key], v[4]);
                 atomicAdd(&e_p[key], v[5]);
                 atomicAdd(&wad[key], v[6]);
+                if (THETA) {
+                    atomicAdd(&f_tl[key], v[7 % NH]);
+                    atomicAdd(&f_tp[key], v[8 % NH]);
+                }
             }
         }
         // interface fields
@@ -834,12 +851,20 @@ void run_step(Context& c, double dt, double* du, double* dv)
     if (P.saturation)
         k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa);
     prof_mark(c, 3);
-    for (int f = 0; f < NFIELD; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
+    for (int f = 0; f < (P.theta_flux ? NFIELD : F_TL); ++f)
+        cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);
-    k_project<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B, c.bgdf, c.ctl, off2, c.kappa, c.k2, dt, c.field[F_ZL],
-                                               c.field[F_ZP], c.field[F_LL], c.field[F_LP], c.field[F_PL],
-                                               c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD],
-                                               c.partials, c.max_blocks);
+    if (P.theta_flux)
+        k_project<true><<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B, c.bgdf, c.ctl, off2, c.kappa, c.k2, dt,
+                                                         c.field[F_ZL], c.field[F_ZP], c.field[F_LL], c.field[F_LP],
+                                                         c.field[F_PL], c.field[F_PP], c.field[F_EL], c.field[F_EP],
+                                                         c.field[F_WAD], c.field[F_TL], c.field[F_TP], c.partials,
+                                                         c.max_blocks);
+    else
+        k_project<false><<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B, c.bgdf, c.ctl, off2, c.kappa, c.k2, dt,
+                                                          c.field[F_ZL], c.field[F_ZP], c.field[F_LL], c.field[F_LP],
+                                                          c.field[F_PL], c.field[F_PP], c.field[F_EL], c.field[F_EP],
+                                                          c.field[F_WAD], nullptr, nullptr, c.partials, c.max_blocks);
     tune_mark(c, 5);
     if (c.tune_active) ++c.tune_pending;
     prof_mark(c, 4);

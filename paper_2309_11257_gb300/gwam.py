@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "GWAM_OK", -1: "GWAM_EINVAL", -2: "GWAM_ENOMEM", -3: "GWAM_EC
                 -5: "GWAM_ECUDA", -6: "GWAM_ETIMEOUT", -7: "GWAM_ESTATE"}
 STATE_NAMES = ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "px", "py", "pz", "n")
 MEMBER_SHIFT = 56     # ray ids carry the ensemble member in their top 8 bits
-FIELD_NAMES = ("fz_l", "fz_p", "f_ll", "f_lp", "f_pl", "f_pp", "e_l", "e_p", "wad")
+FIELD_NAMES = ("fz_l", "fz_p", "f_ll", "f_lp", "f_pl", "f_pp", "e_l", "e_p", "wad", "t_l", "t_p")
 
 
 class GwamError(RuntimeError):
@@ -46,7 +46,7 @@ class Params(C.Structure):
     _fields_ = [("precision", C.c_int), ("gamma_mode", C.c_int), ("saturation", C.c_int), ("smoothing", C.c_int),
                 ("flux_form", C.c_int), ("splitting", C.c_int), ("cap_per_column", C.c_int),
                 ("alpha_s", C.c_double), ("min_split_dz", C.c_double), ("max_rays", C.c_int64),
-                ("members", C.c_int), ("columnar", C.c_int)]
+                ("members", C.c_int), ("columnar", C.c_int), ("theta_flux", C.c_int)]
 
 
 class BgSource(C.Structure):
@@ -117,6 +117,8 @@ SIGNATURES = {
     "gwam_selftest_narrow": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "gwam_selftest_logratio": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "gwam_save": (C.c_int, [_vp, C.c_char_p]),
+    "gwam_set_theta": (C.c_int, [_vp, _vp]),
+    "gwam_get_theta_tendency_host": (C.c_int, [_vp, _vp]),
     "gwam_load": (C.c_int, [_vp, C.c_char_p]),
     "gwam_gemm_bf16": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
     "gwam_mlp_create": (C.c_int, [_P(_vp), _P(MlpConfig), _vp]),
@@ -292,6 +294,17 @@ class Tracer:
         """Step with host (numpy, ideally pinned) output buffers; synchronising."""
         self._check(_lib.gwam_step_host(self._h, float(dt), dudt.ctypes.data_as(_vp), dvdt.ctypes.data_as(_vp)),
                     "step_host")
+
+    # -------------------------------------------------------------- potential temperature
+    def set_theta(self, theta):
+        """Reference potential temperature: a float64 CUDA tensor [members][nz][ny][nx] (or [nz][ny][nx])."""
+        self._check(_lib.gwam_set_theta(self._h, _ptr(theta)), "set_theta")
+
+    def theta_tendency(self) -> np.ndarray:
+        """d theta/dt of the last step (needs theta_flux = 1 and set_theta)."""
+        out = np.zeros((self.members, self.nz, self.ny, self.nx))
+        self._check(_lib.gwam_get_theta_tendency_host(self._h, out.ctypes.data_as(_vp)), "get_theta_tendency_host")
+        return out[0] if self.members == 1 else out
 
     # -------------------------------------------------------------- checkpoints
     def save(self, path: str):

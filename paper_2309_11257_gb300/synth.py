@@ -45,7 +45,8 @@ SPEC_DTYPE = np.dtype([("i", np.int32), ("j", np.int32), ("member", np.int32), (
                        ("lambda_h", np.float64), ("flux", np.float64), ("spectral_frac", np.float64)], align=True)
 
 DEFAULT_PARAMS = dict(gamma_mode=1, saturation=1, smoothing=1, flux_form=0, splitting=1,
-                      cap_per_column=4800, alpha_s=2.5, min_split_dz=1000.0, columnar=0)
+                      cap_per_column=4800, alpha_s=2.5, min_split_dz=1000.0, columnar=0,
+                      theta_flux=0)
 
 
 def rng(tag: int) -> np.random.Generator:

@@ -171,6 +171,48 @@ def test_columnar_mode_parity(gw, geometry):
         np.testing.assert_array_equal(r1[n][i1], r0[n][i0])
 
 
+@pytest.mark.parametrize("geometry", ["sphere", "fplane"])
+def test_theta_flux_and_tendency_parity(gw, geometry):
+    """Potential-temperature flux integrals (Eq. fluxes:temperature) and d theta/dt (Eq.
+    mean-flow-impact-t) against the oracle, scaled as the other projected fields; the momentum
+    path is unchanged by projecting them."""
+    import torch
+    if geometry == "sphere":
+        grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+        bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+        rays = synth.sphere_rays(grid, 777, tag=32, z_lo=4e3, z_hi=20e3, ext_scale=3.0)
+        dt = 300.0
+    else:
+        grid = synth.fplane_grid(nx=24, ny=20, nz=40, dx=40e3, dy=30e3, dz=500.0)
+        bg = synth.perturbed(synth.uniform_background(grid, U=5.0), tag=21, rel=0.1)
+        rays = synth.fplane_rays(grid, 1500, tag=22, z_lo=3e3, z_hi=15e3, ext_z=1300.0)
+        dt = 240.0
+    rays["n"] = rays["n"] * 30.0
+    _, _, z = synth.node_coords(grid)
+    theta = 240.0 * np.exp(bg[2] * z[:, None, None] / grid["g"])      # d ln theta/dz = N^2 / g
+    params = dict(synth.DEFAULT_PARAMS, cap_per_column=45, theta_flux=1)
+    T, O = _pair(gw, grid, params, bg, 200000)
+    T0, _ = _pair(gw, grid, dict(params, theta_flux=0), bg, 200000)
+    T.set_theta(torch.from_numpy(np.ascontiguousarray(theta)).cuda())
+    O.set_theta(theta)
+    for X in (T, O, T0):
+        X.add_rays(rays)
+    for s in range(6):
+        du, dv, odu, odv = _step_both(T, O, dt, grid["nz"], grid["ny"], grid["nx"])
+        T0.step(dt, *[torch.zeros((grid["nz"], grid["ny"], grid["nx"]), dtype=torch.float64, device="cuda")
+                      for _ in range(2)])
+        if s % 2 == 1:
+            _compare_all(T, O, grid, du, dv, odu, odv)
+            for name in oracle.THETA_FIELD_NAMES:
+                assert_fields_match(T.field(name), O.field(name), O.field_abs(name), name=name)
+            th, sc = O.theta_tendency()
+            assert_fields_match(T.theta_tendency(), th, sc, name="dtheta/dt")
+            assert np.abs(th).max() > 0.0
+    r, r0 = T.rays(), T0.rays()
+    for n in oracle.STATE_NAMES:
+        np.testing.assert_array_equal(r[n], r0[n])
+
+
 def test_spectral_launch_parity(gw):
     """Explicit spectral launches (convective-like source) incl. filtered bins."""
     grid = synth.sphere_grid(nx=36, ny=18, nz=30, dz=1000.0)
