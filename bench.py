@@ -180,8 +180,18 @@ def gpu_arm(args, rank, world, local_rank):
     T.launch_sources(w["source"])
     du = torch.zeros((nz, ny, nx), dtype=torch.float64, device=dev)
     dv = torch.zeros_like(du)
-    for _ in range(args.warmup):
+    coupled = w.get("coupled", False)
+
+    def one_step():
         T.step(w["dt"], du, dv)
+        if coupled:
+            # online coupling: the host model advances u, v by the drag and hands the background back
+            bg_dev[0].add_(du, alpha=w["dt"])
+            bg_dev[1].add_(dv, alpha=w["dt"])
+            T.set_background(*bg_dev)
+
+    for _ in range(args.warmup):
+        one_step()
     T.profile(True)
     s0 = T.stats()
     sampler = ClockSampler(local_rank)
@@ -195,7 +205,7 @@ def gpu_arm(args, rank, world, local_rank):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        T.step(w["dt"], du, dv)
+        one_step()
     e1.record(stream)
     e1.synchronize()
     torch.cuda.synchronize()
@@ -288,7 +298,7 @@ def gpu_arm(args, rank, world, local_rank):
             "e2e": e2e,
             "clocks": clocks,
         }
-        line["gpu_launches"] = args.steps * launches_per_step(params)
+        line["gpu_launches"] = args.steps * (launches_per_step(params) + (2 if coupled else 0))
         print(json.dumps(line), flush=True)
     return 0
 
@@ -508,9 +518,11 @@ def main():
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
                     choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate",
-                             "sphere_columnar"],
+                             "sphere_columnar", "sphere_coupled"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
                          "sphere_columnar: the sphere in the single-column (MS-GWaM-1D) mode; "
+                         "sphere_coupled: the sphere with u, v advanced by the drag after every step "
+                         "(add on the device, then gwam_set_background, inside the timed region); "
                          "ensemble: 16 members of the sphere with convective sources, graph-replayed steps; "
                          "surrogate: MLP inference over 32768 columns after training on tracer drag")
     args = ap.parse_args()

@@ -115,6 +115,23 @@ def jet_background(grid: dict, amp=60.0, lat_deg=45.0, width_deg=10.0, z_peak=60
     return u, v, n2, rho
 
 
+def channel_jet_background(grid: dict, amp=40.0, width=400e3, z_peak=35e3, z_width=12e3, N=0.02,
+                           T=240.0):
+    """f-plane zonal jet U = A exp(-((y - y_c)/w)^2) exp(-((z - z_j)/h)^2) centred in the box (y_c = L_y/2),
+    V = 0, constant N, isothermal density (the jet-refraction run on the f-plane)."""
+    nx, ny, nz = grid["nx"], grid["ny"], grid["nz"]
+    _, y, z = node_coords(grid)
+    yc = 0.5 * ny * grid["dy"]
+    shape = (nz, ny, nx)
+    prof = amp * np.exp(-((y - yc) / width) ** 2)
+    u = np.broadcast_to(np.exp(-((z - z_peak) / z_width) ** 2)[:, None, None] * prof[None, :, None], shape).copy()
+    v = np.zeros(shape)
+    n2 = np.full(shape, float(N) ** 2)
+    _, H, rho0 = isothermal(T)
+    rho = np.broadcast_to((rho0 * np.exp(-z / H))[:, None, None], shape).copy()
+    return u, v, n2, rho
+
+
 def perturbed(fields, tag: int, rel=0.05):
     """Background plus a smooth seeded perturbation in all three directions (parity tests)."""
     g = rng(tag)
@@ -229,6 +246,36 @@ def convective_specs(grid: dict, tag: int, median=16.0, sigma=1.0, cap=512, z_la
     return out
 
 
+def uniform_specs(grid: dict, n_az=8, c_list=(5.0, 5.0 * 10 ** (1 / 3), 5.0 * 10 ** (2 / 3), 50.0),
+                  flux=1e-3, z_launch=5e3, dz_launch=1e3, lambda_h=100e3, frac=0.1, lat_max_deg=85.0):
+    """Explicit spectral launches, the same in every column: n_az azimuths (even) times the phase
+    speeds in c_list, each ray carrying flux / (n_az len(c_list)).
+
+    The azimuths are +-(a + 1/2) 2 pi / n_az, a = 0 .. n_az/2 - 1: mirror pairs (theta, -theta) are
+    exact (l = |k_h| sin(theta) flips sign with no rounding difference), so a background without
+    meridional structure sees no net meridional flux; and no azimuth lies on an axis, where a
+    wavenumber component would be rounding noise (cos(pi/2) is not 0 in floating point).
+    """
+    nx, ny = grid["nx"], grid["ny"]
+    _, phi, _ = node_coords(grid)
+    rows = np.nonzero(np.abs(np.degrees(phi)) <= lat_max_deg)[0] if grid["geometry"] == 1 else np.arange(ny)
+    per = n_az * len(c_list)
+    ncol = len(rows) * nx
+    half = (np.arange(n_az // 2) + 0.5) * (2.0 * math.pi / n_az)
+    theta = np.concatenate([half, -half])
+    out = np.zeros(ncol * per, dtype=SPEC_DTYPE)
+    out["j"] = np.repeat(rows, nx * per)
+    out["i"] = np.tile(np.repeat(np.arange(nx), per), len(rows))
+    out["theta"] = np.tile(np.repeat(theta, len(c_list)), ncol)
+    out["c"] = np.tile(np.asarray(c_list, dtype=np.float64), ncol * n_az)
+    out["z_launch"] = z_launch
+    out["dz_launch"] = dz_launch
+    out["lambda_h"] = lambda_h
+    out["flux"] = flux / per
+    out["spectral_frac"] = frac
+    return out
+
+
 # ---------------------------------------------------------------- named workloads
 
 def workload(name: str) -> dict:
@@ -238,13 +285,15 @@ def workload(name: str) -> dict:
         params = dict(DEFAULT_PARAMS, saturation=0, smoothing=0)
         return dict(name=name, grid=grid, params=params, background=uniform_background(grid),
                     rays=fplane_rays(grid, 4096, tag=1), source=None, dt=300.0, steps=100)
-    if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32", "sphere_columnar"):
+    if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32", "sphere_columnar", "sphere_coupled"):
         nx, ny = {"sphere": (256, 128), "sphere_fp32": (512, 256), "sphere_half": (128, 64),
-                  "sphere_half_fp32": (128, 64), "sphere_columnar": (256, 128)}[name]
+                  "sphere_half_fp32": (128, 64), "sphere_columnar": (256, 128), "sphere_coupled": (256, 128)}[name]
         grid = sphere_grid(nx=nx, ny=ny, nz=90, dz=1000.0)
         params = dict(DEFAULT_PARAMS, columnar=1 if name == "sphere_columnar" else 0)
+        # sphere_coupled: the background is advanced by the drag after every step (online coupling)
         return dict(name=name, grid=grid, params=params, background=jet_background(grid),
-                    rays=None, source=background_source(), dt=180.0, steps=200)
+                    rays=None, source=background_source(), dt=180.0, steps=200,
+                    coupled=name == "sphere_coupled")
     raise KeyError(name)
 
 
