@@ -88,6 +88,8 @@ def _declare(lib):
     lib.orc_add_rays.argtypes = [C.c_void_p, C.c_int64] + [_D] * 13
     lib.orc_launch_background.argtypes = [C.c_void_p, _P(BgSource)]
     lib.orc_launch_spectral.argtypes = [C.c_void_p, C.c_int64, _P(Spec)]
+    lib.orc_launch_ghost.argtypes = [C.c_void_p, _P(BgSource), C.c_double]
+    lib.orc_launch_ghost_spectral.argtypes = [C.c_void_p, C.c_int64, _P(Spec), C.c_double]
     lib.orc_step.argtypes = [C.c_void_p, C.c_double, _D, _D]
     lib.orc_diagnose.argtypes = [C.c_void_p, _D, _D]
     lib.orc_num_rays.restype = C.c_int64
@@ -207,16 +209,32 @@ class Model:
         if self._lib.orc_launch_background(self._h, C.byref(s)) != 0:
             raise ValueError("launch rejected")
 
-    def launch_spectral(self, specs: np.ndarray):
-        """specs: structured array with fields of Spec (see synth.SPEC_DTYPE)."""
+    @staticmethod
+    def _specs(specs: np.ndarray):
         n = len(specs)
         arr = (Spec * max(n, 1))()
         for q in range(n):
             for name, _ in Spec._fields_:
                 if name in specs.dtype.names:
                     setattr(arr[q], name, specs[name][q].item())
+        return n, arr
+
+    def launch_spectral(self, specs: np.ndarray):
+        """specs: structured array with fields of Spec (see synth.SPEC_DTYPE)."""
+        n, arr = self._specs(specs)
         if self._lib.orc_launch_spectral(self._h, n, arr) != 0:
             raise ValueError("spectral launch rejected")
+
+    def launch_ghost(self, src: dict, dt: float):
+        """Ghost-layer emission of the background source over one launch interval dt."""
+        s = _struct(BgSource, src)
+        if self._lib.orc_launch_ghost(self._h, C.byref(s), float(dt)) != 0:
+            raise ValueError("ghost launch rejected")
+
+    def launch_ghost_spectral(self, specs: np.ndarray, dt: float):
+        n, arr = self._specs(specs)
+        if self._lib.orc_launch_ghost_spectral(self._h, n, arr, float(dt)) != 0:
+            raise ValueError("ghost spectral launch rejected")
 
     # -- step
     def step(self, dt: float, want_tendencies: bool = True):

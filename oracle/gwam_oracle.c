@@ -229,7 +229,7 @@ double orc_omega(const orc_model *m, double X, double Y, double Z, double k, dou
  *  - group velocities at the six face centres from first-order Taylor values
  *    chi_face = chi + grad chi . (r_face - r) (App. B.1); the face mean advances the
  *    carrier, the face difference is the extent rate (Sec. 3b, App. B.1). */
-void orc_rhs(const orc_model *m, const double *y, double *F)
+static void rhs_mode(const orc_model *m, const double *y, double *F, int columnar)
 {
     double X = y[0], Y = y[1], Z = y[2], k = y[3], l = y[4], mm = y[5];
     double ext[3] = {y[6], y[7], y[8]};
@@ -254,7 +254,7 @@ void orc_rhs(const orc_model *m, const double *y, double *F)
              + d.kh2 / (2.0 * d.w * d.K2) * (dN2[q] - d.D / d.K2 * dG2[q])
              + d.mg2 / (2.0 * d.w * d.K2) * df2v[q];
     }
-    if (m->P.columnar) {
+    if (columnar) {
         /* single-column approximation (MS-GWaM-1D, Sec. 1): horizontal gradients of the resolved
          * flow are neglected, so k and l stay fixed and m follows the vertical gradient alone */
         F[3] = 0.0;
@@ -272,7 +272,7 @@ void orc_rhs(const orc_model *m, const double *y, double *F)
     }
 
     for (int q = 0; q < 3; ++q) {
-        if (m->P.columnar && q < 2) {
+        if (columnar && q < 2) {
             /* no horizontal propagation or advection: position and horizontal extents fixed */
             F[q] = 0.0;
             F[6 + q] = 0.0;
@@ -297,18 +297,29 @@ void orc_rhs(const orc_model *m, const double *y, double *F)
     }
 }
 
+void orc_rhs(const orc_model *m, const double *y, double *F)
+{
+    rhs_mode(m, y, F, m->P.columnar);
+}
+
 /* Williamson (1980) low-storage third-order Runge-Kutta, background frozen over the step
- * (App. B.2; the coefficients are the published ones of that scheme). */
-void orc_rk3(const orc_model *m, double *y, double dt)
+ * (App. B.2; the coefficients are the published ones of that scheme).  columnar != 0 integrates
+ * the single-column form whatever the model's mode (the ghost layer of the launch). */
+static void rk3_mode(const orc_model *m, double *y, double dt, int columnar)
 {
     static const double A[3] = {0.0, -5.0 / 9.0, -153.0 / 128.0};
     static const double B[3] = {1.0 / 3.0, 15.0 / 16.0, 8.0 / 15.0};
     double q[9] = {0}, F[9];
     for (int s = 0; s < 3; ++s) {
-        orc_rhs(m, y, F);
+        rhs_mode(m, y, F, columnar);
         for (int c = 0; c < 9; ++c) q[c] = A[s] * q[c] + dt * F[c];
         for (int c = 0; c < 9; ++c) y[c] += B[s] * q[c];
     }
+}
+
+void orc_rk3(const orc_model *m, double *y, double dt)
+{
+    rk3_mode(m, y, dt, m->P.columnar);
 }
 
 static void wrap_position(const orc_model *m, double *s)
@@ -583,8 +594,8 @@ double orc_fam(double p, double tau, double f_s, double f_w)
  * w = |k_h| c - k.U must satisfy |f| < w < N, and m follows from inverting Eq. dispersion,
  * m^2 = k_h^2 (N^2 - w^2) / (w^2 - f^2) - Gamma^2, with m < 0 (upward group velocity).
  * The bin carries the pseudomomentum flux F = |k_h| ch_r A through the launch level. */
-static int launch_one(orc_model *m, long i, long j, double z_launch, double dz_launch, double theta,
-                      double c, double lambda_h, double flux, double frac)
+static int launch_state(orc_model *m, long i, long j, double z_launch, double dz_launch, double theta,
+                        double c, double lambda_h, double flux, double frac, double *s)
 {
     double X = (i + 0.5) * cell_x(m);
     double Y = row_lat(m, j);
@@ -610,20 +621,70 @@ static int launch_one(orc_model *m, long i, long j, double z_launch, double dz_l
     dispersion(k, l, mm, N2, G2, f2, &d);
     double A = flux / (kh * d.ch[2]);
     double dk = frac * kh, dl = frac * kh, dm = frac * fabs(mm);
-    double s[NSTATE];
     make_ray(m, X, Y, Z, k, l, mm, cell_x(m), cell_y(m), dz_launch, dk, dl, dm, A / (dk * dl * dm), s);
     if (ray_status(m, s) != 0) {
         m->st.n_filtered++;
         return 0;
     }
+    return 1;
+}
+
+static void activate(orc_model *m, const double *s)
+{
     append_ray(m, s, m->next_id++);
     m->st.n_launched++;
     m->st.w_launched += ray_action(s);
     m->st.w_total += ray_action(s);
+}
+
+static int launch_one(orc_model *m, long i, long j, double z_launch, double dz_launch, double theta,
+                      double c, double lambda_h, double flux, double frac)
+{
+    double s[NSTATE];
+    if (!launch_state(m, i, j, z_launch, dz_launch, theta, c, lambda_h, flux, frac, s)) return 0;
+    activate(m, s);
     return 1;
 }
 
-int orc_launch_background(orc_model *m, const orc_bg_source *src)
+/* Ghost-layer launch (Sec. 3c): a ghost ray volume fills the launch layer [z_launch, z_launch +
+ * dz_launch] in the launch state of the bin and propagates vertically only (the single-column
+ * equations) over one launch interval dt.  The part of it above the layer top is separated and
+ * activated: same N, wavevector and horizontal extents, vertical extent from the layer top (or its
+ * own bottom, if it left the layer whole) to its top, and the vertical phase-space product in
+ * proportion, P_z = P_z,ghost * extent / dZ_ghost.  A ghost volume reflected within the layer
+ * (m no longer negative: downward group velocity) is discarded and counted as filtered. */
+static int ghost_one(orc_model *m, long i, long j, double z_launch, double dz_launch, double theta,
+                     double c, double lambda_h, double flux, double frac, double dt)
+{
+    double s[NSTATE];
+    if (!launch_state(m, i, j, z_launch, dz_launch, theta, c, lambda_h, flux, frac, s)) return 0;
+    double y[9];
+    memcpy(y, s, sizeof(y));
+    rk3_mode(m, y, dt, 1);
+    if (!(y[SM] < 0.0)) {
+        m->st.n_filtered++;
+        return 0;
+    }
+    double layer_top = z_launch + dz_launch;
+    double top = y[SZ] + 0.5 * y[SEZ], bot = y[SZ] - 0.5 * y[SEZ];
+    if (!(top > layer_top)) return 0;                  /* nothing has left the layer */
+    double lo = bot > layer_top ? bot : layer_top;
+    double e[NSTATE];
+    memcpy(e, s, sizeof(e));
+    e[SM] = y[SM];
+    e[SZ] = 0.5 * (lo + top);
+    e[SEZ] = top - lo;
+    e[SPZ] = s[SPZ] * e[SEZ] / y[SEZ];
+    if (ray_status(m, e) != 0) {
+        m->st.n_filtered++;
+        return 0;
+    }
+    activate(m, e);
+    return 1;
+}
+
+/* dt > 0: ghost-layer emission over one launch interval; dt == 0: activate the launch states */
+static int launch_background_dt(orc_model *m, const orc_bg_source *src, double dt)
 {
     if (!is_sphere(m) || !m->have_bg) return -1;
     if (src->n_az < 1 || src->n_c < 1) return -1;
@@ -639,9 +700,41 @@ int orc_launch_background(orc_model *m, const orc_bg_source *src)
                     double theta = 2.0 * M_PI * a / src->n_az;
                     double c = src->n_c == 1 ? src->c_min
                              : src->c_min * pow(src->c_max / src->c_min, (double)q / (src->n_c - 1));
-                    launch_one(m, i, j, src->z_launch, src->dz_launch, theta, c, src->lambda_h, fbin,
-                               src->spectral_frac);
+                    if (dt > 0.0)
+                        ghost_one(m, i, j, src->z_launch, src->dz_launch, theta, c, src->lambda_h, fbin,
+                                  src->spectral_frac, dt);
+                    else
+                        launch_one(m, i, j, src->z_launch, src->dz_launch, theta, c, src->lambda_h, fbin,
+                                   src->spectral_frac);
                 }
+    }
+    m->st.n_live = m->n;
+    return 0;
+}
+
+int orc_launch_background(orc_model *m, const orc_bg_source *src)
+{
+    return launch_background_dt(m, src, 0.0);
+}
+
+int orc_launch_ghost(orc_model *m, const orc_bg_source *src, double dt)
+{
+    if (!(dt > 0.0)) return -1;
+    return launch_background_dt(m, src, dt);
+}
+
+static int launch_spectral_dt(orc_model *m, int64_t n, const orc_spec *sp, double dt)
+{
+    if (!m->have_bg) return -1;
+    for (int64_t q = 0; q < n; ++q)
+        if (sp[q].i < 0 || sp[q].i >= m->G.nx || sp[q].j < 0 || sp[q].j >= m->G.ny) return -1;
+    for (int64_t q = 0; q < n; ++q) {
+        if (dt > 0.0)
+            ghost_one(m, sp[q].i, sp[q].j, sp[q].z_launch, sp[q].dz_launch, sp[q].theta, sp[q].c,
+                      sp[q].lambda_h, sp[q].flux, sp[q].spectral_frac, dt);
+        else
+            launch_one(m, sp[q].i, sp[q].j, sp[q].z_launch, sp[q].dz_launch, sp[q].theta, sp[q].c,
+                       sp[q].lambda_h, sp[q].flux, sp[q].spectral_frac);
     }
     m->st.n_live = m->n;
     return 0;
@@ -649,14 +742,13 @@ int orc_launch_background(orc_model *m, const orc_bg_source *src)
 
 int orc_launch_spectral(orc_model *m, int64_t n, const orc_spec *sp)
 {
-    if (!m->have_bg) return -1;
-    for (int64_t q = 0; q < n; ++q) {
-        if (sp[q].i < 0 || sp[q].i >= m->G.nx || sp[q].j < 0 || sp[q].j >= m->G.ny) return -1;
-        launch_one(m, sp[q].i, sp[q].j, sp[q].z_launch, sp[q].dz_launch, sp[q].theta, sp[q].c,
-                   sp[q].lambda_h, sp[q].flux, sp[q].spectral_frac);
-    }
-    m->st.n_live = m->n;
-    return 0;
+    return launch_spectral_dt(m, n, sp, 0.0);
+}
+
+int orc_launch_ghost_spectral(orc_model *m, int64_t n, const orc_spec *sp, double dt)
+{
+    if (!(dt > 0.0)) return -1;
+    return launch_spectral_dt(m, n, sp, dt);
 }
 
 /* ------------------------------------------------------------------ splitting (App. B.3) */

@@ -94,6 +94,11 @@ int orc_add_rays(orc_model *m, int64_t n, const double *x, const double *y, cons
                  const double *dk, const double *dl, const double *dm, const double *nn);
 int orc_launch_background(orc_model *m, const orc_bg_source *src);
 int orc_launch_spectral(orc_model *m, int64_t n, const orc_spec *specs);
+/* ghost-layer launch over one launch interval dt > 0 (Sec. 3c): per bin, the part of a layer-filling
+ * ghost ray volume that propagated (vertically only) out of the launch layer is activated; ghost
+ * volumes reflected within the layer are discarded (counted as filtered) */
+int orc_launch_ghost(orc_model *m, const orc_bg_source *src, double dt);
+int orc_launch_ghost_spectral(orc_model *m, int64_t n, const orc_spec *specs, double dt);
 /* one full step; dudt/dvdt C-order [nz][ny][nx] (may be NULL) */
 int orc_step(orc_model *m, double dt, double *dudt, double *dvdt);
 

@@ -53,6 +53,12 @@ MUTATIONS = {
                              "        F[5] = -G[2] + k * cg[0] / r;\n    } else if (is_sphere(m)) {"),
     "columnar_horizontal_divergence": ("                    div_u = (fz_top_l - fz_bot_l) / dz;\n",
                                        "                    div_u = div_u;\n"),
+    # ghost-layer launch
+    "ghost_pz_unscaled": ("e[SPZ] = s[SPZ] * e[SEZ] / y[SEZ];", "e[SPZ] = s[SPZ];"),
+    "ghost_propagates_in_3d": ("rk3_mode(m, y, dt, 1);", "rk3_mode(m, y, dt, m->P.columnar);"),
+    "ghost_keeps_reflected": ("    if (!(y[SM] < 0.0)) {\n        m->st.n_filtered++;",
+                              "    if (0) {\n        m->st.n_filtered++;"),
+    "ghost_extent_from_bottom": ("double lo = bot > layer_top ? bot : layer_top;", "double lo = bot;"),
 }
 
 

@@ -899,3 +899,151 @@ def test_theta_tendency_closed_forms():
     tp_s = np.broadcast_to((1.0 / np.cos(phi))[None, :, None], (6, 10, 16)).copy()
     out = Ms.theta_divergence(np.zeros((6, 10, 16)), tp_s)
     np.testing.assert_allclose(out[:, 1:-1, :], 0.0, atol=1e-20)
+
+
+# ------------------------------------------------------------------ ghost-layer launch (Sec. 3c)
+
+def _spec(i, j, theta, c, flux, z_launch=5e3, dz_launch=1e3, lambda_h=100e3):
+    s = np.zeros(1, dtype=synth.SPEC_DTYPE)
+    s["i"], s["j"], s["theta"], s["c"], s["flux"] = i, j, theta, c, flux
+    s["z_launch"], s["dz_launch"], s["lambda_h"], s["spectral_frac"] = z_launch, dz_launch, lambda_h, 0.1
+    return s
+
+
+def test_ghost_emission_carries_the_source_flux_per_interval():
+    """Uniform f-plane: the emitted part of each bin is the slab its wave action crossed the layer top
+    in dt, so its action is the pseudomomentum flux times dt times the column area over |k_h|
+    (A = F / (|k_h| c_r) and an extent c_r dt), whatever c_r is.  The ghost propagates vertically
+    only: position, horizontal wavenumber, extents and N stay those of the launch state, and the
+    emitted slab starts at the layer top."""
+    grid = synth.fplane_grid(nx=3, ny=2, nz=40, dx=50e3, dy=40e3, dz=500.0, f0=1e-4)
+    bg = synth.uniform_background(grid, U=5.0, V=-2.0)
+    params = dict(saturation=0, smoothing=0)
+    specs = synth.uniform_specs(grid, flux=2e-3)
+    kh = 2.0 * math.pi / 100e3
+    dt = 60.0
+    G = model(grid, params, bg)
+    G.launch_ghost_spectral(specs, dt)
+    L = model(grid, params, bg)
+    L.launch_spectral(specs)
+    g, s = G.rays(), L.rays()
+    # the bins the wind filters at launch (w_hat <= |f|) are filtered here too; every other bin emits
+    assert len(g["id"]) == len(s["id"]) and len(g["id"]) > 0.8 * len(specs)
+    W = g["n"] * g["px"] * g["py"] * g["pz"]
+    np.testing.assert_allclose(W, 2e-3 / 32 * dt * grid["dx"] * grid["dy"] / kh, rtol=1e-12)
+    for n in ("x", "y", "k", "l", "m", "ex", "ey", "px", "py", "n"):
+        np.testing.assert_array_equal(g[n], s[n])
+    assert np.all(g["ez"] < s["ez"])
+    np.testing.assert_allclose(g["z"] - 0.5 * g["ez"], 6e3, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(g["pz"] / g["ez"], s["pz"] / s["ez"], rtol=1e-13)   # same dm
+    st = G.stats()
+    assert st["n_launched"] == len(s["id"]) and st["n_filtered"] == len(specs) - len(s["id"])
+    assert st["w_launched"] == pytest.approx(W.sum(), rel=1e-13)
+
+
+def test_ghost_emission_on_the_sphere_follows_the_source_profile():
+    """Background source at rest on the sphere: per row the emitted action is F_am(phi) dt A_c / |k_h|
+    (A_c the column area at the launch height, F_am of Sec. 3c) -- the rate the source prescribes."""
+    grid = synth.sphere_grid(nx=8, ny=36, nz=30, dz=500.0)
+    n2c, H, rho0 = synth.isothermal()
+    shape = (30, 36, 8)
+    _, phi, z = synth.node_coords(grid)
+    bg = (np.zeros(shape), np.zeros(shape), np.full(shape, n2c),
+          np.broadcast_to((rho0 * np.exp(-z / H))[:, None, None], shape).copy())
+    src = synth.background_source(launch_zero_flux=0)
+    kh = 2.0 * math.pi / src["lambda_h"]
+    dt = 60.0
+    G = model(grid, dict(saturation=0, smoothing=0), bg)
+    G.launch_ghost(src, dt)
+    r = G.rays()
+    W = r["n"] * r["px"] * r["py"] * r["pz"]
+    rows = 0
+    for j in range(36):
+        pdeg = math.degrees(phi[j])
+        F = oracle.fam(pdeg, src["tau"], src["f_s"], src["f_w"])
+        sel = np.abs(r["y"] - phi[j]) < 1e-12
+        if F == 0.0 or abs(pdeg) > src["phi_max_deg"]:
+            assert not sel.any()
+            continue
+        rows += 1
+        assert sel.sum() == 8 * src["n_az"] * src["n_c"]
+        area = (synth.EARTH_RADIUS + 5.5e3) ** 2 * math.cos(phi[j]) * (2 * math.pi / 8) * (math.pi / 36)
+        assert W[sel].sum() == pytest.approx(F * dt * area / kh * 8, rel=1e-12)
+    assert rows == 26
+
+
+def test_ghost_volume_that_left_the_layer_whole_is_emitted_whole():
+    """A launch interval longer than the layer's crossing time emits the whole ghost volume: the launch
+    state moved up by c_r dt with its action (less than the flux times dt)."""
+    grid = synth.fplane_grid(nx=2, ny=2, nz=80, dx=50e3, dy=50e3, dz=500.0, f0=1e-4)
+    bg = synth.uniform_background(grid, U=0.0)
+    params = dict(saturation=0, smoothing=0)
+    sp = _spec(0, 0, 0.0, 50.0, 1e-3)
+    kh = 2.0 * math.pi / 100e3
+    L = model(grid, params, bg)
+    L.launch_spectral(sp)
+    s = L.rays()
+    c_r = None
+    for dt in (60.0, 600.0):
+        G = model(grid, params, bg)
+        G.launch_ghost_spectral(sp, dt)
+        g = G.rays()
+        W = g["n"][0] * g["px"][0] * g["py"][0] * g["pz"][0]
+        if dt == 60.0:
+            c_r = g["ez"][0] / dt                      # the part above the top: c_r dt
+            assert W == pytest.approx(1e-3 * dt * 2.5e9 / kh, rel=1e-12)
+        else:
+            assert c_r * dt > 1e3
+            assert g["ez"][0] == pytest.approx(1e3, rel=1e-13)
+            assert g["z"][0] == pytest.approx(5.5e3 + c_r * dt, rel=1e-12)
+            assert W == pytest.approx(s["n"][0] * s["px"][0] * s["py"][0] * s["pz"][0], rel=1e-13)
+            assert W < 1e-3 * dt * 2.5e9 / kh
+
+
+def test_ghost_reflected_within_the_layer_is_discarded():
+    """N^2 falling with height: a bin launched with w_hat just below N at the layer centre meets its
+    turning level (N(z) = w_hat) within the layer after |m| / (dm/dt) ~ a second, dm/dt = -d w_hat/dz
+    = k_h^2 / (2 w_hat K^2) |dN^2/dz| (Gamma = 0): it turns downward and is discarded.  A slower bin,
+    whose turning level is far above, is emitted."""
+    grid = synth.fplane_grid(nx=2, ny=2, nz=40, dx=50e3, dy=50e3, dz=500.0, f0=1e-4)
+    u, v, n2, rho = synth.uniform_background(grid, U=0.0)
+    _, _, z = synth.node_coords(grid)
+    N2c, Hn = 4e-4, 4e3
+    n2 = np.broadcast_to((N2c * np.exp(-(z - 5.5e3) / Hn))[:, None, None], n2.shape).copy()
+    params = dict(saturation=0, smoothing=0, gamma_mode=0)
+    kh = 2.0 * math.pi / 100e3
+    dt = 60.0
+    for frac, reflects in ((0.999, True), (0.99, True), (0.1, False)):
+        w = frac * math.sqrt(N2c)
+        c = w / kh
+        m0 = -kh * math.sqrt((N2c - w * w) / (w * w - 1e-8))
+        mdot = kh * kh / (2.0 * w * (kh * kh + m0 * m0)) * N2c / Hn
+        assert (abs(m0) / mdot < 0.1 * dt) == reflects
+        G = model(grid, params, (u, v, n2, rho))
+        G.launch_ghost_spectral(_spec(0, 0, 0.0, c, 1e-3), dt)
+        st = G.stats()
+        assert (st["n_launched"], st["n_filtered"]) == ((0, 1) if reflects else (1, 0))
+
+
+def test_ghost_launching_every_interval_gives_the_steady_source_flux():
+    """Emitting every interval and stepping, the emitted slabs tile the column above the layer without
+    gap or overlap (uniform medium), so the projected vertical pseudomomentum flux (App. A form) at
+    every interface inside the filled region is the source flux exactly."""
+    grid = synth.fplane_grid(nx=2, ny=2, nz=60, dx=50e3, dy=50e3, dz=500.0, f0=1e-4)
+    bg = synth.uniform_background(grid, U=0.0)
+    params = dict(saturation=0, smoothing=0, flux_form=1)
+    sp = np.concatenate([_spec(i, j, 0.0, 23.2, 1e-3) for j in range(2) for i in range(2)])
+    G = model(grid, params, bg)
+    dt, n = 120.0, 30
+    for _ in range(n):
+        G.launch_ghost_spectral(sp, dt)
+        G.step(dt, want_tendencies=False)
+    r = G.rays()
+    delta = r["ez"].max()
+    assert np.allclose(r["ez"], delta, rtol=1e-12) and len(r["z"]) == 4 * n
+    fz = G.field("fz_l")
+    zi = np.arange(grid["nz"] + 1) * grid["dz"]
+    inside = (zi - 0.5 * grid["dz"] > 6e3 + delta) & (zi + 0.5 * grid["dz"] < 6e3 + (n + 1) * delta)
+    assert inside.sum() >= 8
+    np.testing.assert_allclose(fz[inside], 1e-3, rtol=1e-12)
+    np.testing.assert_array_equal(G.field("fz_p")[inside], 0.0)
