@@ -165,9 +165,27 @@ int gwam_add_rays_host(gwam_ctx *ctx, const gwam_ray_input *rays, int64_t n);
  * in member order, column order (j, then i) and bin order (azimuth, then phase speed).  Bins with w_hat outside
  * (|f|, N) or m^2 <= 0 are counted in n_filtered.  Stream-ordered (no host sync). */
 int gwam_launch_sources(gwam_ctx *ctx, const gwam_bg_source *src);
-/* Explicit spectral launches, in array order; `specs` device pointer / host pointer. */
+/* Explicit spectral launches, in array order; `specs` device pointer / host pointer.  A spec whose
+ * column or member lies outside the grid: GWAM_EINVAL (host specs, nothing launched) or, for device
+ * specs, the context status GWAM_EINVAL reported by the next synchronising call. */
 int gwam_launch_spectral(gwam_ctx *ctx, const gwam_spec *specs, int64_t n);
 int gwam_launch_spectral_host(gwam_ctx *ctx, const gwam_spec *specs, int64_t n);
+
+/* Ghost-layer launch over one launch interval dt > 0 (Sec. 3c: the source layer within which ray
+ * volumes propagate vertically only; each interval the part that left it is activated, volumes
+ * reflected inside are discarded).  Per bin (same bins, order and filtering as gwam_launch_sources /
+ * gwam_launch_spectral) a ghost ray volume in the launch state fills the layer [z_launch, z_launch +
+ * dz_launch] and is advanced over dt by the single-column equations (k, l, horizontal position and
+ * extents fixed).  If its m is no longer negative it is discarded (counted in n_filtered);
+ * otherwise the part above the layer top -- from the top (or the ghost's own bottom, if it left
+ * whole) to the ghost's top, with the ghost's m, N, horizontal extents and P_z in proportion to
+ * the extent -- is appended as a new ray volume (n_launched, w_launched); a bin from which
+ * nothing has left the layer appends nothing.  Called once per model step before gwam_step, this
+ * emits the source flux every interval.  FP64 form only (precision 1: GWAM_EINVAL); dt not > 0 or
+ * not finite: GWAM_EINVAL.  Stream-ordered like the launches above. */
+int gwam_launch_ghost(gwam_ctx *ctx, const gwam_bg_source *src, double dt);
+int gwam_launch_ghost_spectral(gwam_ctx *ctx, const gwam_spec *specs, int64_t n, double dt);
+int gwam_launch_ghost_spectral_host(gwam_ctx *ctx, const gwam_spec *specs, int64_t n, double dt);
 
 /* One full step of dt seconds (dt > 0): RK3 ray propagation (App. B.2), exits, splitting
  * (App. B.3), re-binning by cell, per-column cap (App. B.5), saturation (Sec. 3c), flux

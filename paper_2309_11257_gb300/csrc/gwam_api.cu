@@ -489,7 +489,8 @@ static int add_rays_impl(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n, bool
 int gwam_add_rays(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n) { return add_rays_impl(ctx, r, n, false); }
 int gwam_add_rays_host(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n) { return add_rays_impl(ctx, r, n, true); }
 
-int gwam_launch_sources(gwam_ctx* ctx, const gwam_bg_source* src)
+// ghost_dt > 0: ghost-layer emission over one launch interval (FP64 form only)
+static int launch_sources_impl(gwam_ctx* ctx, const gwam_bg_source* src, double ghost_dt)
 {
     API_BEGIN(ctx)
     if (!src) return GWAM_EINVAL;
@@ -500,12 +501,34 @@ int gwam_launch_sources(gwam_ctx* ctx, const gwam_bg_source* src)
     if (c.G.geometry != 1 || src->n_az < 1 || src->n_c < 1 || src->n_az * src->n_c > 1024) return GWAM_EINVAL;
     if (!(src->lambda_h > 0.0) || !(src->dz_launch > 0.0) || !(src->c_min > 0.0) || !(src->c_max > 0.0))
         return GWAM_EINVAL;
-    launch_background_source(c, *src);
+    if (ghost_dt > 0.0)
+        launch_ghost_source(c, *src, ghost_dt);
+    else
+        launch_background_source(c, *src);
     GWAM_CUDA(cudaGetLastError());
     API_END
 }
 
-static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n, bool host)
+static int check_ghost(gwam_ctx* ctx, double dt)
+{
+    if (!ctx) return GWAM_EINVAL;
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    if (ctx->c.f32) {
+        ctx->c.err = "gwam_launch_ghost: the ghost layer is built in the FP64 form only";
+        return GWAM_EINVAL;
+    }
+    return GWAM_OK;
+}
+
+int gwam_launch_sources(gwam_ctx* ctx, const gwam_bg_source* src) { return launch_sources_impl(ctx, src, 0.0); }
+
+int gwam_launch_ghost(gwam_ctx* ctx, const gwam_bg_source* src, double dt)
+{
+    const int rc = check_ghost(ctx, dt);
+    return rc ? rc : launch_sources_impl(ctx, src, dt);
+}
+
+static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n, bool host, double ghost_dt = 0.0)
 {
     API_BEGIN(ctx)
     if (n < 0 || (n > 0 && !specs)) return GWAM_EINVAL;
@@ -530,7 +553,10 @@ static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n
     }
     int rc = GWAM_OK;
     try {
-        launch_spectral(c, d, n);
+        if (ghost_dt > 0.0)
+            launch_ghost_spectral(c, d, n, ghost_dt);
+        else
+            launch_spectral(c, d, n);
         GWAM_CUDA(cudaGetLastError());
     } catch (int code) {
         rc = code;
@@ -551,6 +577,18 @@ int gwam_launch_spectral(gwam_ctx* ctx, const gwam_spec* specs, int64_t n)
 int gwam_launch_spectral_host(gwam_ctx* ctx, const gwam_spec* specs, int64_t n)
 {
     return launch_spectral_impl(ctx, specs, n, true);
+}
+
+int gwam_launch_ghost_spectral(gwam_ctx* ctx, const gwam_spec* specs, int64_t n, double dt)
+{
+    const int rc = check_ghost(ctx, dt);
+    return rc ? rc : launch_spectral_impl(ctx, specs, n, false, dt);
+}
+
+int gwam_launch_ghost_spectral_host(gwam_ctx* ctx, const gwam_spec* specs, int64_t n, double dt)
+{
+    const int rc = check_ghost(ctx, dt);
+    return rc ? rc : launch_spectral_impl(ctx, specs, n, true, dt);
 }
 
 int gwam_step(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)

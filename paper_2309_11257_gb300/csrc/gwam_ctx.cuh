@@ -169,6 +169,8 @@ void launch_set_background(Context& c, int member, const double* u, const double
 void launch_add_rays(Context& c, const double* const in[13], int64_t n);
 void launch_background_source(Context& c, const gwam_bg_source& src);
 void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
+void launch_ghost_source(Context& c, const gwam_bg_source& src, double dt);
+void launch_ghost_spectral(Context& c, const gwam_spec* specs, int64_t n, double dt);
 void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();
 void smooth_field(Context& c, int f);

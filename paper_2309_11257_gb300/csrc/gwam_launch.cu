@@ -425,33 +425,71 @@ __device__ __forceinline__ bool source_bin(const Grid& G, const gwam_bg_source& 
     return true;
 }
 
-__device__ __forceinline__ bool spec_bin(const gwam_spec& sp, Bin& b)
+__device__ __forceinline__ bool spec_bin(const Grid& G, Ctl* ctl, const gwam_spec& sp, Bin& b)
 {
+    // device-resident specs are not seen by the host: a column or member outside the grid is an
+    // input error (status GWAM_EINVAL, read at the next synchronising call), never an index
+    if (sp.i < 0 || sp.i >= G.nx || sp.j < 0 || sp.j >= G.ny || sp.member < 0 || sp.member >= G.members) {
+        set_status(ctl, GWAM_EINVAL);
+        return false;
+    }
     b.i = sp.i; b.j = sp.j; b.member = sp.member;
     b.z_launch = sp.z_launch; b.dz_launch = sp.dz_launch; b.theta = sp.theta; b.c = sp.c;
     b.lambda_h = sp.lambda_h; b.flux = sp.flux; b.frac = sp.spectral_frac;
     return true;
 }
 
-// pass 0: flag[t] = launches?, count filtered bins; pass 1: write launched rays in order
-template <bool kSpec>
-__global__ void k_launch(Grid G, const Node* __restrict__ bg, RaySoA A, Ray32SoA A32, bool f32, Ctl* ctl,
-                         int64_t max_rays,
-                         gwam_bg_source src, const gwam_spec* __restrict__ specs, int total, int pass,
-                         int* __restrict__ flag, double* __restrict__ partials, int pstride)
+// Ghost-layer emission (Sec. 3c): the launch state s fills the layer [z_launch, z_launch + dz_launch]
+// and propagates vertically only over the launch interval dt (single-column RK3: G.columnar is set
+// on the grid this kernel is given).  Returns 1 with s = the part above the layer top (vertical
+// extent from the layer top, or the ghost's own bottom if it left whole, to its top; P_z in
+// proportion; the ghost's m), 0 when the ghost was reflected in the layer (m no longer negative) or
+// the part lies outside the domain, 2 when nothing has left the layer.
+__device__ __forceinline__ int ghost_emit(const Grid& G, const NodeDF* __restrict__ bgdf, const Bin& b, double dt,
+                                          double s[NSTATE], double* sh)
 {
+    double y[NSTATE];
+#pragma unroll
+    for (int c = 0; c < NSTATE; ++c) y[c] = s[c];
+    rk3(G, bgdf + (int64_t)b.member * G.ncell, y, dt, sh);
+    if (!(y[SM] < 0.0)) return 0;
+    const double layer_top = b.z_launch + b.dz_launch;
+    const double top = y[SZ] + 0.5 * y[SEZ], bot = y[SZ] - 0.5 * y[SEZ];
+    if (!(top > layer_top)) return 2;
+    const double lo = bot > layer_top ? bot : layer_top;
+    s[SM] = y[SM];
+    s[SZ] = 0.5 * (lo + top);
+    s[SEZ] = top - lo;
+    s[SPZ] = s[SPZ] * s[SEZ] / y[SEZ];   // once per emitted ray: IEEE division is fine here
+    return ray_status(G, s) == 0 ? 1 : 0;
+}
+
+// pass 0: flag[t] = launches?, count filtered bins; pass 1: write launched rays in order.
+// kGhost: emit what left the ghost layer over ghost_dt instead of the launch state itself.
+template <bool kSpec, bool kGhost>
+__global__ void k_launch(Grid G, const Node* __restrict__ bg, const NodeDF* __restrict__ bgdf, RaySoA A,
+                         Ray32SoA A32, bool f32, Ctl* ctl, int64_t max_rays,
+                         gwam_bg_source src, const gwam_spec* __restrict__ specs, int total, double ghost_dt,
+                         int pass, int* __restrict__ flag, double* __restrict__ partials, int pstride)
+{
+    __shared__ double sh_state[kGhost ? 9 * kThreads : 1];
     const int n0 = ctl->n;
     const long long next = ctl->next_id;
     double w = 0.0;
     long long filtered = 0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         Bin b;
-        bool eligible = kSpec ? spec_bin(specs[t], b) : source_bin(G, src, t, b);
+        bool eligible = kSpec ? spec_bin(G, ctl, specs[t], b) : source_bin(G, src, t, b);
         double s[NSTATE];
         int ok = 0;
         if (eligible) {
             ok = make_launch(G, bg, b, s);
-            if (!ok) ++filtered;
+            if (kGhost && ok) {
+                const int e = ghost_emit(G, bgdf, b, ghost_dt, s, sh_state + threadIdx.x);
+                ok = e == 1;
+                if (e == 2) eligible = false;      // nothing left the layer: neither launched nor filtered
+            }
+            if (eligible && !ok) ++filtered;
         }
         if (pass == 0) {
             flag[t] = ok;
@@ -505,29 +543,43 @@ static int* launch_scratch(Context& c, int64_t need)
     return c.newid;
 }
 
-static void launch_common(Context& c, const gwam_bg_source* src, const gwam_spec* specs, int64_t total)
+static void launch_pass(Context& c, const Grid& G, const gwam_bg_source& s0, const gwam_spec* specs, int total,
+                        double ghost_dt, int pass, int* flag)
+{
+    const int nb = c.grid_blocks;
+    const bool ghost = ghost_dt > 0.0;
+    if (specs && ghost)
+        k_launch<true, true><<<nb, kThreads, 0, c.stream>>>(G, c.bg, c.bgdf, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0,
+                                                            specs, total, ghost_dt, pass, flag, c.partials,
+                                                            c.max_blocks);
+    else if (specs)
+        k_launch<true, false><<<nb, kThreads, 0, c.stream>>>(G, c.bg, c.bgdf, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0,
+                                                             specs, total, ghost_dt, pass, flag, c.partials,
+                                                             c.max_blocks);
+    else if (ghost)
+        k_launch<false, true><<<nb, kThreads, 0, c.stream>>>(G, c.bg, c.bgdf, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0,
+                                                             specs, total, ghost_dt, pass, flag, c.partials,
+                                                             c.max_blocks);
+    else
+        k_launch<false, false><<<nb, kThreads, 0, c.stream>>>(G, c.bg, c.bgdf, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0,
+                                                              specs, total, ghost_dt, pass, flag, c.partials,
+                                                              c.max_blocks);
+}
+
+static void launch_common(Context& c, const gwam_bg_source* src, const gwam_spec* specs, int64_t total,
+                          double ghost_dt = 0.0)
 {
     if (total <= 0) return;
     int* flag = launch_scratch(c, total);
     gwam_bg_source s0{};
     if (src) s0 = *src;
-    const int nb = c.grid_blocks;
-    if (specs) {
-        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 0,
-                                                      flag, c.partials, c.max_blocks);
-    } else {
-        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 0,
-                                                       flag, c.partials, c.max_blocks);
-    }
+    // the ghost layer propagates vertically only: the single-column equations on this grid copy
+    Grid G = c.G;
+    if (ghost_dt > 0.0) G.columnar = 1;
+    launch_pass(c, G, s0, specs, (int)total, ghost_dt, 0, flag);
     exclusive_scan(c, flag, flag, total, nullptr);
     cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, c.stream);
-    if (specs) {
-        k_launch<true><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 1,
-                                                      flag, c.partials, c.max_blocks);
-    } else {
-        k_launch<false><<<nb, kThreads, 0, c.stream>>>(c.G, c.bg, c.A, c.A32, c.f32, c.ctl, c.max_rays, s0, specs, (int)total, 1,
-                                                       flag, c.partials, c.max_blocks);
-    }
+    launch_pass(c, G, s0, specs, (int)total, ghost_dt, 1, flag);
     finalize_tallies(c, 1 << T_LAUNCH, 0);
     k_launch_close<<<1, 1, 0, c.stream>>>(c.ctl, c.max_rays, flag, (int)total);
     if (flag != c.newid) cudaFreeAsync(flag, c.stream);
@@ -540,5 +592,16 @@ void launch_background_source(Context& c, const gwam_bg_source& src)
 }
 
 void launch_spectral(Context& c, const gwam_spec* specs, int64_t n) { launch_common(c, nullptr, specs, n); }
+
+void launch_ghost_source(Context& c, const gwam_bg_source& src, double dt)
+{
+    const int64_t total = (int64_t)c.G.ncol_all * src.n_az * src.n_c;
+    launch_common(c, &src, nullptr, total, dt);
+}
+
+void launch_ghost_spectral(Context& c, const gwam_spec* specs, int64_t n, double dt)
+{
+    launch_common(c, nullptr, specs, n, dt);
+}
 
 }  // namespace gwam

@@ -98,6 +98,9 @@ SIGNATURES = {
     "gwam_launch_sources": (C.c_int, [_vp, _P(BgSource)]),
     "gwam_launch_spectral": (C.c_int, [_vp, _vp, C.c_int64]),
     "gwam_launch_spectral_host": (C.c_int, [_vp, _vp, C.c_int64]),
+    "gwam_launch_ghost": (C.c_int, [_vp, _P(BgSource), C.c_double]),
+    "gwam_launch_ghost_spectral": (C.c_int, [_vp, _vp, C.c_int64, C.c_double]),
+    "gwam_launch_ghost_spectral_host": (C.c_int, [_vp, _vp, C.c_int64, C.c_double]),
     "gwam_step": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "gwam_step_host": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "gwam_step_graph": (C.c_int, [_vp, C.c_double, _vp, _vp]),
@@ -248,13 +251,28 @@ class Tracer:
         s = _struct(BgSource, src)
         self._check(_lib.gwam_launch_sources(self._h, C.byref(s)), "launch_sources")
 
-    def launch_spectral(self, specs: np.ndarray):
-        """specs: numpy structured array laid out like gwam_spec (synth.SPEC_DTYPE, host memory)."""
+    @staticmethod
+    def _specs(specs: np.ndarray) -> np.ndarray:
         specs = np.ascontiguousarray(specs)
         assert specs.dtype.itemsize == C.sizeof(Spec) and all(
             specs.dtype.fields[n][1] == getattr(Spec, n).offset for n, _ in Spec._fields_), "spec layout"
+        return specs
+
+    def launch_spectral(self, specs: np.ndarray):
+        """specs: numpy structured array laid out like gwam_spec (synth.SPEC_DTYPE, host memory)."""
+        specs = self._specs(specs)
         self._check(_lib.gwam_launch_spectral_host(self._h, specs.ctypes.data_as(_vp), len(specs)),
                     "launch_spectral_host")
+
+    def launch_ghost(self, src: dict, dt: float):
+        """Ghost-layer emission of the background source over one launch interval dt (FP64 form)."""
+        s = _struct(BgSource, src)
+        self._check(_lib.gwam_launch_ghost(self._h, C.byref(s), float(dt)), "launch_ghost")
+
+    def launch_ghost_spectral(self, specs: np.ndarray, dt: float):
+        specs = self._specs(specs)
+        self._check(_lib.gwam_launch_ghost_spectral_host(self._h, specs.ctypes.data_as(_vp), len(specs),
+                                                          float(dt)), "launch_ghost_spectral_host")
 
     # -------------------------------------------------------------- step
     def step(self, dt: float, dudt=None, dvdt=None):
