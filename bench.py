@@ -174,15 +174,22 @@ def gpu_arm(args, rank, world, local_rank):
     if fp32:
         params["precision"] = 1
     nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
-    T = gwam.Tracer(grid, params, max_rays=int(2.5 * 32 * nx * ny))
+    ghost = w.get("ghost", False)
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
+    # ghost-layer emission adds up to one ray volume per bin and step
+    cap_rays = 32 * nx * ny * (args.warmup + args.steps + e2e_steps + 2) if ghost else 2.5 * 32 * nx * ny
+    T = gwam.Tracer(grid, params, max_rays=int(cap_rays))
     bg_dev = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in w["background"]]
     T.set_background(*bg_dev)
-    T.launch_sources(w["source"])
+    if not ghost:
+        T.launch_sources(w["source"])
     du = torch.zeros((nz, ny, nx), dtype=torch.float64, device=dev)
     dv = torch.zeros_like(du)
     coupled = w.get("coupled", False)
 
     def one_step():
+        if ghost:
+            T.launch_ghost(w["source"], w["dt"])
         T.step(w["dt"], du, dv)
         if coupled:
             # online coupling: the host model advances u, v by the drag and hands the background back
@@ -259,7 +266,7 @@ def gpu_arm(args, rank, world, local_rank):
         bg_host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in w["background"]]
         du_h = torch.zeros((nz, ny, nx), dtype=torch.float64).pin_memory().numpy()
         dv_h = torch.zeros((nz, ny, nx), dtype=torch.float64).pin_memory().numpy()
-        ke = max(1, min(args.steps, 10))
+        ke = e2e_steps
         T.set_background(*bg_host)
         T.step_host(w["dt"], du_h, dv_h)
         a0 = T.stats()["ray_steps"]
@@ -267,6 +274,8 @@ def gpu_arm(args, rank, world, local_rank):
         t0 = time.perf_counter()
         for _ in range(ke):
             T.set_background(*bg_host)
+            if ghost:
+                T.launch_ghost(w["source"], w["dt"])
             T.step_host(w["dt"], du_h, dv_h)
         t1 = time.perf_counter()
         rs = T.stats()["ray_steps"] - a0
@@ -298,7 +307,8 @@ def gpu_arm(args, rank, world, local_rank):
             "e2e": e2e,
             "clocks": clocks,
         }
-        line["gpu_launches"] = args.steps * (launches_per_step(params) + (2 if coupled else 0))
+        # coupling: set-up + gradients; ghost launch: 2 launch passes, 3 scan kernels, tallies, close
+        line["gpu_launches"] = args.steps * (launches_per_step(params) + (2 if coupled else 0) + (7 if ghost else 0))
         print(json.dumps(line), flush=True)
     return 0
 
@@ -518,11 +528,13 @@ def main():
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
                     choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate",
-                             "sphere_columnar", "sphere_coupled"],
+                             "sphere_columnar", "sphere_coupled", "sphere_ghost"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
                          "sphere_columnar: the sphere in the single-column (MS-GWaM-1D) mode; "
                          "sphere_coupled: the sphere with u, v advanced by the drag after every step "
                          "(add on the device, then gwam_set_background, inside the timed region); "
+                         "sphere_ghost: the source emitted through the ghost layer before every 60 s step, "
+                         "from no rays (the count grows by up to 0.98 M per step); "
                          "ensemble: 16 members of the sphere with convective sources, graph-replayed steps; "
                          "surrogate: MLP inference over 32768 columns after training on tracer drag")
     args = ap.parse_args()

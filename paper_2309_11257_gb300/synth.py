@@ -285,6 +285,12 @@ def workload(name: str) -> dict:
         params = dict(DEFAULT_PARAMS, saturation=0, smoothing=0)
         return dict(name=name, grid=grid, params=params, background=uniform_background(grid),
                     rays=fplane_rays(grid, 4096, tag=1), source=None, dt=300.0, steps=100)
+    if name == "sphere_ghost":
+        # the background source emitted through the ghost layer every 60 s interval (the paper's model
+        # step), starting from no rays
+        grid = sphere_grid(nx=256, ny=128, nz=90, dz=1000.0)
+        return dict(name=name, grid=grid, params=dict(DEFAULT_PARAMS), background=jet_background(grid),
+                    rays=None, source=background_source(), dt=60.0, steps=200, ghost=True)
     if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32", "sphere_columnar", "sphere_coupled"):
         nx, ny = {"sphere": (256, 128), "sphere_fp32": (512, 256), "sphere_half": (128, 64),
                   "sphere_half_fp32": (128, 64), "sphere_columnar": (256, 128), "sphere_coupled": (256, 128)}[name]
