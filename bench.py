@@ -510,7 +510,7 @@ def launches_per_step(params) -> int:
     if params.get("cap_per_column", 0) > 0:
         n += 2 + 3                                   # cap find/apply + scan
     if params.get("saturation", 0):
-        n += 1
+        n += 2                                       # short runs, long runs (one per lane)
     if params.get("smoothing", 0):
         n += 9
     return n

@@ -233,10 +233,30 @@ __global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, 
 // sums P_c = sum P_j alpha_j and Q_c = sum P_j alpha_j K_j^2 in FP64 (segment head over the
 // cell's run of the canonical array), the threshold difference P_c - rho/2 in FP64, then
 // kappa = (P_c - rho/2) / (2 dt Q_c) in FP32 for every ray of the cell.
-__global__ void k_sat_kappa32(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+__device__ __forceinline__ void sat_run32(int p, int b, int c, const double* __restrict__ rho,
+                                          const double* __restrict__ pj, const float* __restrict__ k2, float dt,
+                                          float* __restrict__ kappa)
+{
+    double Pc = 0.0, Q = 0.0;
+    for (int q = p; q < b; ++q) {
+        const double v = pj[q];
+        Pc += v;
+        Q = fma(v, widen(k2[q]), Q);
+    }
+    const double d = fma(-0.5, rho[c], Pc);
+    float kap = 0.0f;
+    if (d > 0.0 && Q > 0.0) kap = __fdiv_rn(__double2float_rn(d), 2.0f * dt * __double2float_rn(Q));
+    for (int q = p; q < b; ++q) kappa[q] = kap;
+}
+
+// as k_sat_kappa / k_sat_kappa_long of the FP64 form: short runs by their head, runs longer than
+// kSatRun32 one per lane from a list
+constexpr int kSatRun32 = 16;
+
+__global__ void k_sat_kappa32(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
                               const int* __restrict__ raycell, const double* __restrict__ rho,
                               const double* __restrict__ pj, const float* __restrict__ k2, float dt,
-                              float* __restrict__ kappa)
+                              float* __restrict__ kappa, int* __restrict__ longlist)
 {
     if (ctl->status) return;
     const int n = off2[ncell_all];
@@ -244,16 +264,21 @@ __global__ void k_sat_kappa32(const Ctl* ctl, const int* __restrict__ off2, int 
         const int c = raycell[p];
         if (p > 0 && raycell[p - 1] == c) continue;
         const int b = off2[c + 1];
-        double Pc = 0.0, Q = 0.0;
-        for (int q = p; q < b; ++q) {
-            const double v = pj[q];
-            Pc += v;
-            Q = fma(v, widen(k2[q]), Q);
-        }
-        const double d = fma(-0.5, rho[c], Pc);
-        float kap = 0.0f;
-        if (d > 0.0 && Q > 0.0) kap = __fdiv_rn(__double2float_rn(d), 2.0f * dt * __double2float_rn(Q));
-        for (int q = p; q < b; ++q) kappa[q] = kap;
+        if (b - p > kSatRun32)
+            longlist[atomicAdd(&ctl->n_big, 1)] = c;
+        else
+            sat_run32(p, b, c, rho, pj, k2, dt, kappa);
+    }
+}
+
+__global__ void k_sat_kappa32_long(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ longlist,
+                                   const double* __restrict__ rho, const double* __restrict__ pj,
+                                   const float* __restrict__ k2, float dt, float* __restrict__ kappa)
+{
+    const int nl = ctl->status ? 0 : ctl->n_big;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += gridDim.x * blockDim.x) {
+        const int c = longlist[t];
+        sat_run32(off2[c], off2[c + 1], c, rho, pj, k2, dt, kappa);
     }
 }
 
@@ -705,10 +730,14 @@ void run_step32(Context& c, double dt, double* du, double* dv)
                                                      c.newid, c.pj, reinterpret_cast<float*>(c.k2), c.raycell);
     tune_mark(c, 3);
     prof_mark(c, 2);
-    if (P.saturation)
+    if (P.saturation) {
         k_sat_kappa32<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj,
                                               reinterpret_cast<const float*>(c.k2), (float)dt,
-                                              reinterpret_cast<float*>(c.kappa));
+                                              reinterpret_cast<float*>(c.kappa), c.biglist);
+        k_sat_kappa32_long<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj,
+                                                   reinterpret_cast<const float*>(c.k2), (float)dt,
+                                                   reinterpret_cast<float*>(c.kappa));
+    }
     prof_mark(c, 3);
     for (int f = 0; f < F_TL; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);

@@ -417,14 +417,35 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
 }
 
 // kappa = max(0, (P - rho/2) / (2 dt sum_j P_j K_j^2)) of every carrier cell (Eq. turbulent-diffusivity).
-// Rays are in cell order, so each cell is a contiguous segment: the first ray of a segment sums it
-// in order (deterministic) and hands kappa to all of its rays.  Iterating rays, not cells, skips the
-// many empty cells.  (A warp-parallel segmented sum was measured slower on GB300: it spends about
-// five FP64 additions per lane where this loop spends two per ray.)
-__global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+// Rays are in cell order, so each cell is a contiguous run; a run is summed left to right by one
+// thread (deterministic, and the order the factor max(0, 1 - 2 kappa K^2 dt) is computed in: where it
+// is of the size of the rounding error, the order decides whether it clamps to zero).  Iterating
+// rays, not cells, skips the many empty cells.  The head of a short run sums it in place; a run longer
+// than kSatRun is appended to a list that k_sat_kappa_long sums with one run per lane, so the FP64
+// additions of 32 long runs share one warp instruction instead of one lane of 32 each.
+constexpr int kSatRun = 16;
+
+__device__ __forceinline__ void sat_run(int p, int b, int c, const double* __restrict__ rho,
+                                        const double* __restrict__ pj, const double* __restrict__ k2, double dt,
+                                        double* __restrict__ kappa)
+{
+    double Pc = 0.0, Q = 0.0;
+    for (int q = p; q < b; ++q) {
+        Pc += pj[q];
+        Q += pj[q] * k2[q];
+    }
+    // Newton-refined reciprocal instead of an IEEE division (<= 2 ulp; FP64 division is a long
+    // instruction sequence at GB300's FP64 rate)
+    const double kap = Q > 0.0 ? fmax(0.0, (Pc - 0.5 * rho[c]) * rcp_nr(2.0 * dt * Q)) : 0.0;
+    for (int q = p; q < b; ++q) kappa[q] = kap;
+}
+
+// long runs go to longlist (cell ids), counted in ctl->n_big (reset by k_set_nnew once the segment
+// sort is done)
+__global__ void k_sat_kappa(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
                             const int* __restrict__ raycell, const double* __restrict__ rho,
                             const double* __restrict__ pj, const double* __restrict__ k2, double dt,
-                            double* __restrict__ kappa)
+                            double* __restrict__ kappa, int* __restrict__ longlist)
 {
     if (ctl->status) return;
     const int n = off2[ncell_all];
@@ -432,15 +453,21 @@ __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int nc
         const int c = raycell[p];
         if (p > 0 && raycell[p - 1] == c) continue;
         const int b = off2[c + 1];
-        double Pc = 0.0, Q = 0.0;
-        for (int q = p; q < b; ++q) {
-            Pc += pj[q];
-            Q += pj[q] * k2[q];
-        }
-        // Newton-refined reciprocal instead of an IEEE division (<= 2 ulp; FP64 division is a long
-        // instruction sequence at GB300's FP64 rate)
-        const double kap = Q > 0.0 ? fmax(0.0, (Pc - 0.5 * rho[c]) * rcp_nr(2.0 * dt * Q)) : 0.0;
-        for (int q = p; q < b; ++q) kappa[q] = kap;
+        if (b - p > kSatRun)
+            longlist[atomicAdd(&ctl->n_big, 1)] = c;
+        else
+            sat_run(p, b, c, rho, pj, k2, dt, kappa);
+    }
+}
+
+__global__ void k_sat_kappa_long(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ longlist,
+                                 const double* __restrict__ rho, const double* __restrict__ pj,
+                                 const double* __restrict__ k2, double dt, double* __restrict__ kappa)
+{
+    const int nl = ctl->status ? 0 : ctl->n_big;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += gridDim.x * blockDim.x) {
+        const int c = longlist[t];
+        sat_run(off2[c], off2[c + 1], c, rho, pj, k2, dt, kappa);
     }
 }
 
@@ -750,7 +777,12 @@ __global__ void k_step_begin(Ctl* ctl)
     ctl->ray_steps += ctl->n;
 }
 
-__global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl) { ctl->n_new = off2[ncell]; }
+// also frees the long-segment counter of the segment sort for the saturation's long-run list
+__global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl)
+{
+    ctl->n_new = off2[ncell];
+    ctl->n_big = 0;
+}
 
 // ============================================================================ orchestration
 
@@ -848,8 +880,11 @@ void run_step(Context& c, double dt, double* du, double* dv)
                                                    c.pj, c.k2, c.raycell);
     tune_mark(c, 3);
     prof_mark(c, 2);
-    if (P.saturation)
-        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa);
+    if (P.saturation) {
+        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa,
+                                            c.biglist);
+        k_sat_kappa_long<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj, c.k2, dt, c.kappa);
+    }
     prof_mark(c, 3);
     for (int f = 0; f < (P.theta_flux ? NFIELD : F_TL); ++f)
         cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
