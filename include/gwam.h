@@ -289,6 +289,11 @@ int gwam_selftest_widen(const float *x, int64_t n, double *widened, double *acti
 /* Self-test of the integer double -> float narrowing (round to nearest even): out[i] must equal the
  * hardware conversion bit for bit (subnormal results, overflow to infinity, NaN classes included). */
 int gwam_selftest_narrow(const double *x, int64_t n, float *out, void *stream);
+/* Self-test of the double-float split of the FP64 form: hi[i] = x[i] rounded to FP32 and lo[i] =
+ * (x[i] - hi[i]) rounded to FP32 (round to nearest even both), bit for bit, whichever of its two
+ * paths (integer-only for 2^-74 <= |x| < 2^127, one FP64 subtraction otherwise) x[i] takes.  Device
+ * pointers, n values; synchronises `stream`. */
+int gwam_selftest_split(const double *x, int64_t n, float *hi, float *lo, void *stream);
 /* Self-test of the double-float logarithm of a ratio that forms Gamma^2 = (d ln rho / dz)^2 / 4 from
  * centred differences of ln rho (Sec. 2a; the differences are taken as ln(rho_up / rho_down)):
  * out[i] = ln(a[i] / b[i]) for positive normal doubles a, b, relative error about 2^-45 (exactly 0

@@ -196,9 +196,26 @@ __device__ __forceinline__ float df_ceil(DF x)
 // a < b for normalised pairs
 __device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
-// x = hi + lo to about 48 bits (one FP64 subtraction)
+// x = hi + lo to about 48 bits: hi = x rounded to FP32, lo = (x - hi) rounded to FP32.  For
+// 2^-74 <= |x| < 2^127 (hi a finite normal float, lo normal or zero) with integer operations and one
+// int -> float conversion, no FP64 instruction: x - hi is the 29 bits narrow dropped, less 2^29 when
+// it rounded up, in units of 2^(e - 1075); that integer rounded to FP32 and scaled by the power of
+// two is RN(x - hi) exactly.  Other x: narrow(x - widen(hi)) (one FP64 subtraction), the same values.
 __device__ __forceinline__ DF df_split(double x)
 {
+    const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
+    const uint32_t e = (hw >> 20) & 0x7FFu;
+    if (e - 949u < 201u) {
+        uint32_t r = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
+        const uint32_t rem = lw & 0x1FFFFFFFu;   // the 29 dropped bits
+        const bool up = rem > 0x10000000u || (rem == 0x10000000u && (r & 1u));
+        r += up ? 1u : 0u;
+        const uint32_t sign = hw & 0x80000000u;
+        int res = up ? (int)rem - (1 << 29) : (int)rem;   // |res| <= 2^28
+        if (sign) res = -res;
+        const float scale = __uint_as_float((e - 948u) << 23);   // 2^(e - 1075), a normal float
+        return {__uint_as_float(sign | r), __fmul_rn(__int2float_rn(res), scale)};
+    }
     const float hi = narrow(x);
     return {hi, narrow(x - widen(hi))};
 }

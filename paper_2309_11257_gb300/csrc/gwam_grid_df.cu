@@ -25,9 +25,9 @@ struct FieldSetDF {
 // consecutive levels of kRowsDF rows over kSpanDF columns.  For every column it loads and splits the
 // kRowsDF + 2 values of its rows and their two neighbours once (2 loads and splits per output
 // instead of 3 for two rows: measured faster than 1, 4 or 8 rows), forms the vertical 1-2-1 sums
-// of its rows, and slides a window of three such sums along the row.  Warp item = (field, member,
-// row group, level group, span).
-constexpr int kSpanDF = 32;
+// of its rows, and slides a window of three such sums along the row (spans of 16 columns: measured
+// faster than 8 or 32).  Warp item = (field, member, row group, level group, span).
+constexpr int kSpanDF = 16;
 constexpr int kRowsDF = 2;
 __global__ void __launch_bounds__(256) k_smooth_df(Grid G, FieldSetDF fs, int f0, int nf)
 {

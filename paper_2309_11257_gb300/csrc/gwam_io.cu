@@ -93,6 +93,16 @@ __global__ void k_selftest_narrow(const double* __restrict__ x, int64_t n, float
         out[i] = narrow(x[i]);
 }
 
+__global__ void k_selftest_split(const double* __restrict__ x, int64_t n, float* __restrict__ hi,
+                                 float* __restrict__ lo)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const DF d = df_split(x[i]);
+        hi[i] = d.hi;
+        lo[i] = d.lo;
+    }
+}
+
 __global__ void k_selftest_logratio(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
                                     double* __restrict__ out)
 {
@@ -109,6 +119,17 @@ extern "C" int gwam_selftest_logratio(const double* a, const double* b, int64_t 
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks = (int)std::min<int64_t>((n + gwam::kThreads - 1) / gwam::kThreads, 4096);
     gwam::k_selftest_logratio<<<blocks, gwam::kThreads, 0, s>>>(a, b, n, out);
+    if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GWAM_ECUDA;
+    return GWAM_OK;
+}
+
+extern "C" int gwam_selftest_split(const double* x, int64_t n, float* hi, float* lo, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !hi || !lo))) return GWAM_EINVAL;
+    if (n == 0) return GWAM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (int)std::min<int64_t>((n + gwam::kThreads - 1) / gwam::kThreads, 4096);
+    gwam::k_selftest_split<<<blocks, gwam::kThreads, 0, s>>>(x, n, hi, lo);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GWAM_ECUDA;
     return GWAM_OK;
 }

@@ -118,6 +118,7 @@ SIGNATURES = {
     "gwam_selftest_math": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_selftest_widen": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_selftest_narrow": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+    "gwam_selftest_split": (C.c_int, [_vp, C.c_int64, _vp, _vp, _vp]),
     "gwam_selftest_logratio": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "gwam_save": (C.c_int, [_vp, C.c_char_p]),
     "gwam_set_theta": (C.c_int, [_vp, _vp]),

@@ -102,6 +102,37 @@ def test_integer_narrowing_matches_the_hardware_conversion():
     assert np.isnan(got[nan]).all()
 
 
+def test_double_float_split_is_exact():
+    """The split x = hi + lo of the FP64 form: hi = RN32(x), lo = RN32(x - hi) bit for bit, over 100
+    decades, at rounding ties (x = float + half an ulp, both ways of even), at the ends of the
+    integer-only range (2^-74, 2^127) and outside it (tiny, subnormal, huge, zero, infinities)."""
+    import torch
+    from paper_2309_11257_gb300 import build
+    build.build()
+    from paper_2309_11257_gb300 import gwam
+    rng = np.random.default_rng(12)
+    h = rng.uniform(1.0, 2.0, 20_000).astype(np.float32).astype(np.float64)
+    half_ulp = np.spacing(h.astype(np.float32)).astype(np.float64) / 2
+    x = np.concatenate([rng.normal(size=200_000) * 10.0 ** rng.uniform(-50, 50, 200_000),
+                        h + half_ulp, -(h + half_ulp), h - half_ulp / 2,
+                        2.0 ** -74 * rng.uniform(1, 2, 1000), 2.0 ** 126 * rng.uniform(1, 1.9999, 1000),
+                        2.0 ** rng.integers(-140, 140, 1000).astype(float),
+                        np.array([0.0, -0.0, 5e-324, 1e-310, 1e300, -1e300, np.inf, -np.inf])])
+    xd = torch.from_numpy(x).cuda()
+    hi = torch.empty(len(x), dtype=torch.float32, device="cuda")
+    lo = torch.empty_like(hi)
+    s = torch.cuda.current_stream()
+    assert gwam.lib().gwam_selftest_split(C.c_void_p(xd.data_ptr()), len(x), C.c_void_p(hi.data_ptr()),
+                                          C.c_void_p(lo.data_ptr()), C.c_void_p(s.cuda_stream)) == 0
+    with np.errstate(over="ignore", invalid="ignore"):
+        rhi = x.astype(np.float32)
+        rlo = (x - rhi.astype(np.float64)).astype(np.float32)
+    ghi, glo = hi.cpu().numpy(), lo.cpu().numpy()
+    fin = np.isfinite(rhi)
+    np.testing.assert_array_equal(ghi.view(np.uint32), rhi.view(np.uint32))
+    np.testing.assert_array_equal(glo[fin].view(np.uint32), rlo[fin].view(np.uint32))
+
+
 def test_double_float_log_ratio():
     """ln(a/b) in double-float (atanh series after range reduction, as used for the Gamma^2
     differences) against numpy's FP64 logarithms: ratios across 70 decades, near 1, exactly 1 and
