@@ -200,11 +200,17 @@ __device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.h
 // 2^-74 <= |x| < 2^127 (hi a finite normal float, lo normal or zero) with integer operations and one
 // int -> float conversion, no FP64 instruction: x - hi is the 29 bits narrow dropped, less 2^29 when
 // it rounded up, in units of 2^(e - 1075); that integer rounded to FP32 and scaled by the power of
-// two is RN(x - hi) exactly.  Other x: narrow(x - widen(hi)) (one FP64 subtraction), the same values.
+// two is RN(x - hi) exactly.  Zeros and FP64 subnormals (e = 0; the empty cells of a projected
+// field) round to hi = +-0 and lo = x rounded, +-0 likewise (+0 for a zero x).  Other x:
+// narrow(x - widen(hi)) (one FP64 subtraction), the same values.
 __device__ __forceinline__ DF df_split(double x)
 {
     const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
     const uint32_t e = (hw >> 20) & 0x7FFu;
+    if (e == 0u) {
+        const uint32_t sign = hw & 0x80000000u;
+        return {__uint_as_float(sign), __uint_as_float(((hw & 0xFFFFFu) | lw) ? sign : 0u)};
+    }
     if (e - 949u < 201u) {
         uint32_t r = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
         const uint32_t rem = lw & 0x1FFFFFFFu;   // the 29 dropped bits

@@ -249,35 +249,14 @@ __device__ __forceinline__ void sat_run32(int p, int b, int c, const double* __r
     for (int q = p; q < b; ++q) kappa[q] = kap;
 }
 
-// as k_sat_kappa / k_sat_kappa_long of the FP64 form: short runs by their head, runs longer than
-// kSatRun32 one per lane from a list
-constexpr int kSatRun32 = 16;
-
-__global__ void k_sat_kappa32(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
-                              const int* __restrict__ raycell, const double* __restrict__ rho,
-                              const double* __restrict__ pj, const float* __restrict__ k2, float dt,
-                              float* __restrict__ kappa, int* __restrict__ longlist)
-{
-    if (ctl->status) return;
-    const int n = off2[ncell_all];
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int c = raycell[p];
-        if (p > 0 && raycell[p - 1] == c) continue;
-        const int b = off2[c + 1];
-        if (b - p > kSatRun32)
-            longlist[atomicAdd(&ctl->n_big, 1)] = c;
-        else
-            sat_run32(p, b, c, rho, pj, k2, dt, kappa);
-    }
-}
-
-__global__ void k_sat_kappa32_long(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ longlist,
-                                   const double* __restrict__ rho, const double* __restrict__ pj,
-                                   const float* __restrict__ k2, float dt, float* __restrict__ kappa)
+// the listed runs (k_sat_heads of the FP64 form lists them), one per lane
+__global__ void k_sat_kappa32(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ runlist,
+                              const double* __restrict__ rho, const double* __restrict__ pj,
+                              const float* __restrict__ k2, float dt, float* __restrict__ kappa)
 {
     const int nl = ctl->status ? 0 : ctl->n_big;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += gridDim.x * blockDim.x) {
-        const int c = longlist[t];
+        const int c = runlist[t];
         sat_run32(off2[c], off2[c + 1], c, rho, pj, k2, dt, kappa);
     }
 }
@@ -684,10 +663,8 @@ __global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* 
                               const int* __restrict__ biglist, const long long* __restrict__ ent_id,
                               const int* __restrict__ ent_src, int* __restrict__ sorted_src);
 __global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl);
-__global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, int ncell_all,
-                            const int* __restrict__ raycell, const double* __restrict__ rho,
-                            const double* __restrict__ pj, const double* __restrict__ k2, double dt,
-                            double* __restrict__ kappa);
+__global__ void k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all, const int* __restrict__ raycell,
+                            int* __restrict__ runlist);
 
 void run_step32(Context& c, double dt, double* du, double* dv)
 {
@@ -731,12 +708,10 @@ void run_step32(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation) {
-        k_sat_kappa32<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj,
+        k_sat_heads<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.biglist);
+        k_sat_kappa32<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj,
                                               reinterpret_cast<const float*>(c.k2), (float)dt,
-                                              reinterpret_cast<float*>(c.kappa), c.biglist);
-        k_sat_kappa32_long<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj,
-                                                   reinterpret_cast<const float*>(c.k2), (float)dt,
-                                                   reinterpret_cast<float*>(c.kappa));
+                                              reinterpret_cast<float*>(c.kappa));
     }
     prof_mark(c, 3);
     for (int f = 0; f < F_TL; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);

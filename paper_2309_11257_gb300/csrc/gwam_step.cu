@@ -419,11 +419,34 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
 // kappa = max(0, (P - rho/2) / (2 dt sum_j P_j K_j^2)) of every carrier cell (Eq. turbulent-diffusivity).
 // Rays are in cell order, so each cell is a contiguous run; a run is summed left to right by one
 // thread (deterministic, and the order the factor max(0, 1 - 2 kappa K^2 dt) is computed in: where it
-// is of the size of the rounding error, the order decides whether it clamps to zero).  Iterating
-// rays, not cells, skips the many empty cells.  The head of a short run sums it in place; a run longer
-// than kSatRun is appended to a list that k_sat_kappa_long sums with one run per lane, so the FP64
-// additions of 32 long runs share one warp instruction instead of one lane of 32 each.
-constexpr int kSatRun = 16;
+// is of the size of the rounding error, the order decides whether it clamps to zero).  k_sat_heads
+// lists the cell of every run (one warp-aggregated atomic per warp; iterating rays, not cells, skips
+// the many empty cells) and k_sat_kappa sums the listed runs one per lane: the FP64 additions of 32
+// runs share one warp instruction, where a thread per ray left all but the runs' first lanes idle.
+// The list order varies from run to run; every run's sum does not.
+__global__ void k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all, const int* __restrict__ raycell,
+                            int* __restrict__ runlist)
+{
+    if (ctl->status) return;
+    const int n = off2[ncell_all];
+    const int lane = threadIdx.x & 31;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < n; p0 += gridDim.x * blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        int c = -1;
+        bool head = false;
+        if (p < n) {
+            c = raycell[p];
+            head = p == 0 || raycell[p - 1] != c;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, head);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(&ctl->n_big, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (head) runlist[base + __popc(m & ((1u << lane) - 1u))] = c;
+    }
+}
 
 __device__ __forceinline__ void sat_run(int p, int b, int c, const double* __restrict__ rho,
                                         const double* __restrict__ pj, const double* __restrict__ k2, double dt,
@@ -440,33 +463,14 @@ __device__ __forceinline__ void sat_run(int p, int b, int c, const double* __res
     for (int q = p; q < b; ++q) kappa[q] = kap;
 }
 
-// long runs go to longlist (cell ids), counted in ctl->n_big (reset by k_set_nnew once the segment
-// sort is done)
-__global__ void k_sat_kappa(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
-                            const int* __restrict__ raycell, const double* __restrict__ rho,
-                            const double* __restrict__ pj, const double* __restrict__ k2, double dt,
-                            double* __restrict__ kappa, int* __restrict__ longlist)
-{
-    if (ctl->status) return;
-    const int n = off2[ncell_all];
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const int c = raycell[p];
-        if (p > 0 && raycell[p - 1] == c) continue;
-        const int b = off2[c + 1];
-        if (b - p > kSatRun)
-            longlist[atomicAdd(&ctl->n_big, 1)] = c;
-        else
-            sat_run(p, b, c, rho, pj, k2, dt, kappa);
-    }
-}
-
-__global__ void k_sat_kappa_long(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ longlist,
-                                 const double* __restrict__ rho, const double* __restrict__ pj,
-                                 const double* __restrict__ k2, double dt, double* __restrict__ kappa)
+// the listed runs, counted in ctl->n_big (reset by k_set_nnew once the segment sort is done)
+__global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ runlist,
+                            const double* __restrict__ rho, const double* __restrict__ pj,
+                            const double* __restrict__ k2, double dt, double* __restrict__ kappa)
 {
     const int nl = ctl->status ? 0 : ctl->n_big;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nl; t += gridDim.x * blockDim.x) {
-        const int c = longlist[t];
+        const int c = runlist[t];
         sat_run(off2[c], off2[c + 1], c, rho, pj, k2, dt, kappa);
     }
 }
@@ -777,7 +781,7 @@ __global__ void k_step_begin(Ctl* ctl)
     ctl->ray_steps += ctl->n;
 }
 
-// also frees the long-segment counter of the segment sort for the saturation's long-run list
+// also frees the long-segment counter of the segment sort for the saturation's run list
 __global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl)
 {
     ctl->n_new = off2[ncell];
@@ -881,9 +885,8 @@ void run_step(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation) {
-        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.rho, c.pj, c.k2, dt, c.kappa,
-                                            c.biglist);
-        k_sat_kappa_long<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj, c.k2, dt, c.kappa);
+        k_sat_heads<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.biglist);
+        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj, c.k2, dt, c.kappa);
     }
     prof_mark(c, 3);
     for (int f = 0; f < (P.theta_flux ? NFIELD : F_TL); ++f)
