@@ -44,9 +44,9 @@ FP64_EQ_PEAK_TOPS = 152 * 128 * 2.07e9 / 9.0 / 1e12 + 152 * 2 * 2.07e9 / 1e12
 # Precision form: algorithmic bytes of the ray step = the 64-byte ray record read and written once.
 BYTES_PER_RAY_STEP_FP32 = 128.0
 HBM_PEAK = None
-# DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 38.7 MB, k_advance32:
+# DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 39.8 MB, k_advance32:
 # 20.8 MB, each for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
-ADV_TRAFFIC_BYTES_PER_RAY = 152.2
+ADV_TRAFFIC_BYTES_PER_RAY = 156.7
 ADV32_TRAFFIC_BYTES_PER_RAY = 81.7
 
 
