@@ -663,8 +663,8 @@ __global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* 
                               const int* __restrict__ biglist, const long long* __restrict__ ent_id,
                               const int* __restrict__ ent_src, int* __restrict__ sorted_src);
 __global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl);
-__global__ void k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all, const int* __restrict__ raycell,
-                            int* __restrict__ runlist);
+__global__ void __launch_bounds__(kThreads) k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+                                                          const int* __restrict__ raycell, int* __restrict__ runlist);
 
 void run_step32(Context& c, double dt, double* du, double* dv)
 {

@@ -420,16 +420,19 @@ __global__ void __launch_bounds__(kThreads) k_materialize(Grid G, Params P, RayS
 // Rays are in cell order, so each cell is a contiguous run; a run is summed left to right by one
 // thread (deterministic, and the order the factor max(0, 1 - 2 kappa K^2 dt) is computed in: where it
 // is of the size of the rounding error, the order decides whether it clamps to zero).  k_sat_heads
-// lists the cell of every run (one warp-aggregated atomic per warp; iterating rays, not cells, skips
-// the many empty cells) and k_sat_kappa sums the listed runs one per lane: the FP64 additions of 32
+// lists the cell of every run (one atomic per block and pass, the counts of its warps aggregated in
+// shared memory: a single counter under one atomic per warp serialised; iterating rays, not cells,
+// skips the many empty cells) and k_sat_kappa sums the listed runs one per lane: the FP64 additions of 32
 // runs share one warp instruction, where a thread per ray left all but the runs' first lanes idle.
 // The list order varies from run to run; every run's sum does not.
-__global__ void k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all, const int* __restrict__ raycell,
-                            int* __restrict__ runlist)
+__global__ void __launch_bounds__(kThreads) k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
+                                                          const int* __restrict__ raycell, int* __restrict__ runlist)
 {
+    __shared__ int wcount[kThreads / 32], wbase[kThreads / 32];
     if (ctl->status) return;
     const int n = off2[ncell_all];
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // one atomic per block and pass: the block's warps take consecutive slices of the list
     for (int p0 = blockIdx.x * blockDim.x; p0 < n; p0 += gridDim.x * blockDim.x) {
         const int p = p0 + threadIdx.x;
         int c = -1;
@@ -439,12 +442,19 @@ __global__ void k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_al
             head = p == 0 || raycell[p - 1] != c;
         }
         const unsigned m = __ballot_sync(0xffffffffu, head);
-        if (!m) continue;
-        const int leader = __ffs(m) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(&ctl->n_big, __popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (head) runlist[base + __popc(m & ((1u << lane) - 1u))] = c;
+        if (lane == 0) wcount[warp] = __popc(m);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                wbase[w] = tot;
+                tot += wcount[w];
+            }
+            const int b = tot ? atomicAdd(&ctl->n_big, tot) : 0;
+            for (int w = 0; w < kThreads / 32; ++w) wbase[w] += b;
+        }
+        __syncthreads();
+        if (head) runlist[wbase[warp] + __popc(m & ((1u << lane) - 1u))] = c;
     }
 }
 
