@@ -193,6 +193,20 @@ int gwam_launch_ghost_spectral_host(gwam_ctx *ctx, const gwam_spec *specs, int64
  * dudt, dvdt ([members][nz][ny][nx] device buffers, may be NULL), wave-action budget (Sec. 4).
  * Stream-ordered: no host synchronisation. */
 int gwam_step(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
+
+/* Asynchronous host entry points: the host-link copies run on two copy streams of the context (one
+ * per direction) and overlap the steps; neither call waits for the device.  gwam_set_background_host_async copies the
+ * four page-locked caller fields into one of two device staging slots and sets every member's
+ * background from it (as gwam_set_background); an invalid value (as there) becomes the sticky
+ * context status GWAM_ENUMERIC, reported by the next synchronising call, and the steps in between
+ * do nothing.  gwam_step_host_async runs gwam_step into one of two device output slots and copies
+ * du/dt, dv/dt into the page-locked caller buffers (either may be NULL).  The caller keeps the input
+ * fields unchanged and reads the outputs only after a synchronising call (gwam_synchronize,
+ * gwam_get_stats, ...); buffers that are not page-locked: GWAM_EINVAL. */
+int gwam_set_background_host_async(gwam_ctx *ctx, const double *u, const double *v, const double *n2,
+                                   const double *rho);
+int gwam_step_host_async(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
+
 /* The same step replayed from a CUDA graph: the first call for a given (dt, dudt, dvdt) captures the
  * step's kernels (two graphs, one per ray-buffer parity) on an internal stream; later calls launch
  * the graph on the context's stream -- one launch per step.  Launches and backgrounds may change

@@ -57,6 +57,15 @@ static void free_all(Context& c)
     for (int q = 0; q < 2; ++q)
         if (c.gexec[q]) cudaGraphExecDestroy(c.gexec[q]);
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+    for (int q = 0; q < 2; ++q) {
+        if (c.bg_stage[q]) cudaFree(c.bg_stage[q]);
+        if (c.d_out[q]) cudaFree(c.d_out[q]);
+        cudaEvent_t* evs[] = {&c.ev_up[q], &c.ev_free[q], &c.ev_dready[q], &c.ev_d2h[q]};
+        for (cudaEvent_t* e : evs)
+            if (*e) cudaEventDestroy(*e);
+    }
+    if (c.up_stream) cudaStreamDestroy(c.up_stream);
+    if (c.down_stream) cudaStreamDestroy(c.down_stream);
     if (c.ctl_host) cudaFreeHost(c.ctl_host);
     if (c.budget_host) cudaFreeHost(c.budget_host);
     if (c.flag_host) cudaFreeHost(c.flag_host);
@@ -64,6 +73,9 @@ static void free_all(Context& c)
 
 static void check_pending(Context& c)
 {
+    // asynchronous host copies
+    if (c.up_stream) GWAM_CUDA(cudaStreamSynchronize(c.up_stream));
+    if (c.down_stream) GWAM_CUDA(cudaStreamSynchronize(c.down_stream));
     GWAM_CUDA(cudaMemcpyAsync(c.ctl_host, c.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaMemcpyAsync(c.budget_host, c.budget, sizeof(DevBudget), cudaMemcpyDeviceToHost, c.stream));
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
@@ -624,6 +636,98 @@ int gwam_step_host(gwam_ctx* ctx, double dt, double* dudt_host, double* dvdt_hos
         if (dvdt_host) GWAM_CUDA(cudaMemcpyAsync(dvdt_host, c.dvdt_buf, bytes, cudaMemcpyDeviceToHost, c.stream));
     }
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
+    API_END
+}
+
+// ---------------------------------------------------------------- asynchronous host entry points
+
+// page-locked host memory [p, p + bytes) (cudaHostAlloc / cudaHostRegister)
+static bool page_locked(const void* p, size_t bytes)
+{
+    if (!p) return false;
+    const char* q = static_cast<const char*>(p);
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess || cudaPointerGetAttributes(&b, q + bytes - 1) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && b.type == cudaMemoryTypeHost;
+}
+
+static void async_setup(Context& c)
+{
+    if (c.up_stream) return;
+    GWAM_CUDA(cudaStreamCreateWithFlags(&c.up_stream, cudaStreamNonBlocking));
+    GWAM_CUDA(cudaStreamCreateWithFlags(&c.down_stream, cudaStreamNonBlocking));
+    for (int q = 0; q < 2; ++q) {
+        dalloc(c, c.bg_stage[q], 4 * (size_t)c.G.ncell);
+        dalloc(c, c.d_out[q], 2 * (size_t)c.G.ncell_all);
+        cudaEvent_t* evs[] = {&c.ev_up[q], &c.ev_free[q], &c.ev_dready[q], &c.ev_d2h[q]};
+        for (cudaEvent_t* e : evs) GWAM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+}
+
+int gwam_set_background_host_async(gwam_ctx* ctx, const double* u, const double* v, const double* n2,
+                                   const double* rho)
+{
+    API_BEGIN(ctx)
+    const size_t nc = (size_t)c.G.ncell, bytes = sizeof(double) * nc;
+    const double* src[4] = {u, v, n2, rho};
+    for (int q = 0; q < 4; ++q)
+        if (!page_locked(src[q], bytes)) {
+            c.err = "gwam_set_background_host_async: the fields must be page-locked host memory";
+            return GWAM_EINVAL;
+        }
+    async_setup(c);
+    const int k = c.stage_k;
+    c.stage_k ^= 1;
+    double* st = c.bg_stage[k];
+    // the copies wait until the set-up kernel two calls back has read this slot
+    GWAM_CUDA(cudaStreamWaitEvent(c.up_stream, c.ev_free[k], 0));
+    for (int q = 0; q < 4; ++q)
+        GWAM_CUDA(cudaMemcpyAsync(st + q * nc, src[q], bytes, cudaMemcpyHostToDevice, c.up_stream));
+    GWAM_CUDA(cudaEventRecord(c.ev_up[k], c.up_stream));
+    GWAM_CUDA(cudaStreamWaitEvent(c.stream, c.ev_up[k], 0));
+    GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
+    for (int m = 0; m < c.G.members; ++m) {
+        launch_set_background(c, m, st, st + nc, st + 2 * nc, st + 3 * nc);
+        if (c.f32) convert_background32(c, m);
+    }
+    GWAM_CUDA(cudaEventRecord(c.ev_free[k], c.stream));
+    launch_flag_to_status(c);
+    GWAM_CUDA(cudaGetLastError());
+    for (int m = 0; m < c.G.members; ++m) c.member_bg[m] = true;
+    c.have_bg = true;
+    API_END
+}
+
+int gwam_step_host_async(gwam_ctx* ctx, double dt, double* dudt_host, double* dvdt_host)
+{
+    API_BEGIN(ctx)
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_step_host_async: no background";
+        return GWAM_ESTATE;
+    }
+    const size_t n = (size_t)c.G.ncell_all, bytes = sizeof(double) * n;
+    if ((dudt_host && !page_locked(dudt_host, bytes)) || (dvdt_host && !page_locked(dvdt_host, bytes))) {
+        c.err = "gwam_step_host_async: du/dt, dv/dt must be page-locked host memory";
+        return GWAM_EINVAL;
+    }
+    async_setup(c);
+    const int k = c.out_k;
+    c.out_k ^= 1;
+    double* du = c.d_out[k];
+    double* dv = du + n;
+    // this slot's previous copies to the host (two calls back) must be done before it is rewritten
+    GWAM_CUDA(cudaStreamWaitEvent(c.stream, c.ev_d2h[k], 0));
+    run_step(c, dt, du, dv);
+    GWAM_CUDA(cudaEventRecord(c.ev_dready[k], c.stream));
+    GWAM_CUDA(cudaStreamWaitEvent(c.down_stream, c.ev_dready[k], 0));
+    if (dudt_host) GWAM_CUDA(cudaMemcpyAsync(dudt_host, du, bytes, cudaMemcpyDeviceToHost, c.down_stream));
+    if (dvdt_host) GWAM_CUDA(cudaMemcpyAsync(dvdt_host, dv, bytes, cudaMemcpyDeviceToHost, c.down_stream));
+    GWAM_CUDA(cudaEventRecord(c.ev_d2h[k], c.down_stream));
     GWAM_CUDA(cudaGetLastError());
     API_END
 }

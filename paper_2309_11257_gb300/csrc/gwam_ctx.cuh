@@ -126,6 +126,16 @@ struct Context {
     int64_t prof_steps = 0;
     double prof_ms[kPhases] = {};
 
+    // asynchronous host entry points: one stream for uploads and one for downloads over the host
+    // link (a single in-order copy stream would hold the next upload behind the download that waits
+    // for the current step), two device staging slots for the background and two for du/dt, dv/dt,
+    // with events ordering slot reuse
+    cudaStream_t up_stream = nullptr, down_stream = nullptr;
+    double* bg_stage[2] = {nullptr, nullptr};   // [4][ncell] each
+    double* d_out[2] = {nullptr, nullptr};      // [2][ncell_all] each: du/dt then dv/dt
+    cudaEvent_t ev_up[2] = {}, ev_free[2] = {}, ev_dready[2] = {}, ev_d2h[2] = {};
+    int stage_k = 0, out_k = 0;
+
     // CUDA graphs of the step, one per ray-buffer parity, keyed by (dt, dudt, dvdt)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -170,6 +180,7 @@ void launch_add_rays(Context& c, const double* const in[13], int64_t n);
 void launch_background_source(Context& c, const gwam_bg_source& src);
 void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
 void launch_ghost_source(Context& c, const gwam_bg_source& src, double dt);
+void launch_flag_to_status(Context& c);
 void launch_ghost_spectral(Context& c, const gwam_spec* specs, int64_t n, double dt);
 void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();

@@ -177,6 +177,15 @@ void launch_set_background(Context& c, int member, const double* u, const double
                                                         c.f32 ? c.bg32 + o : nullptr);
 }
 
+// asynchronous background: an invalid value becomes the sticky context status (GWAM_ENUMERIC),
+// reported by the next synchronising call; the steps in between do nothing
+__global__ void k_flag_to_status(const int* flag, Ctl* ctl)
+{
+    if (*flag) set_status(ctl, GWAM_ENUMERIC);
+}
+
+void launch_flag_to_status(Context& c) { k_flag_to_status<<<1, 1, 0, c.stream>>>(c.flag_dev, c.ctl); }
+
 // 1/rho of restored nodes (checkpoint load), by the Newton reciprocal as in k_set_background
 __global__ void k_rho_inv(const double* __restrict__ rho, double* __restrict__ rho_inv, int64_t n)
 {

@@ -104,6 +104,8 @@ SIGNATURES = {
     "gwam_step": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "gwam_step_host": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "gwam_step_graph": (C.c_int, [_vp, C.c_double, _vp, _vp]),
+    "gwam_set_background_host_async": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "gwam_step_host_async": (C.c_int, [_vp, C.c_double, _vp, _vp]),
     "gwam_set_launch_config": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "gwam_get_launch_config": (C.c_int, [_vp, C.c_int, _P(C.c_int), _P(C.c_int)]),
     "gwam_autotune": (C.c_int, [_vp, C.c_double, C.c_int, _vp, _vp]),
@@ -315,6 +317,18 @@ class Tracer:
                     "step_host")
 
     # -------------------------------------------------------------- potential temperature
+    def set_background_async(self, u, v, n2, rho):
+        """Page-locked numpy arrays [nz][ny][nx]: copied on the context's upload stream, set up without
+        waiting (keep them unchanged until the next synchronising call)."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, n2, rho)]
+        self._check(_lib.gwam_set_background_host_async(self._h, *[a.ctypes.data_as(_vp) for a in arrs]),
+                    "set_background_host_async")
+
+    def step_host_async(self, dt: float, dudt: np.ndarray, dvdt: np.ndarray):
+        """Page-locked numpy outputs, valid after the next synchronising call."""
+        self._check(_lib.gwam_step_host_async(self._h, float(dt), dudt.ctypes.data_as(_vp),
+                                              dvdt.ctypes.data_as(_vp)), "step_host_async")
+
     def set_theta(self, theta):
         """Reference potential temperature: a float64 CUDA tensor [members][nz][ny][nx] (or [nz][ny][nx])."""
         self._check(_lib.gwam_set_theta(self._h, _ptr(theta)), "set_theta")

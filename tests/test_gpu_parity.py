@@ -354,24 +354,35 @@ def test_edge_cases(gw):
 def test_host_entry_points_match_device_ones(gw):
     """gwam_set_background_host / gwam_step_host give the device-path results, both with pageable
     host buffers (staged copies) and with page-locked ones (read and written by the kernels
-    directly)."""
+    directly); so do the asynchronous entry points (copies on the copy stream, the background set
+    before every step so both staging slots are reused)."""
     import torch
     w = synth.workload("fplane")
     grid, params = w["grid"], w["params"]
     rays = synth.fplane_rays(grid, 300, tag=12)
     outs = []
     shape = (grid["nz"], grid["ny"], grid["nx"])
-    for mode in ("device", "pageable", "pinned"):
+    for mode in ("device", "pageable", "pinned", "async"):
         host = mode != "device"
         T = gw.Tracer(grid, params, max_rays=4096)
-        if mode == "pageable":
+        pinned_bg = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in w["background"]]
+        if mode == "async":
+            T.set_background_async(*pinned_bg)
+        elif mode == "pageable":
             T.set_background(*w["background"])
         elif mode == "pinned":
             T.set_background(*[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in w["background"]])
         else:
             T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in w["background"]])
         T.add_rays(rays)
-        if host:
+        if mode == "async":
+            du = torch.full(shape, np.nan, dtype=torch.float64).pin_memory().numpy()
+            dv = torch.full(shape, np.nan, dtype=torch.float64).pin_memory().numpy()
+            for _ in range(3):
+                T.set_background_async(*pinned_bg)
+                T.step_host_async(300.0, du, dv)
+            T.synchronize()
+        elif host:
             if mode == "pinned":
                 du = torch.full(shape, np.nan, dtype=torch.float64).pin_memory().numpy()
                 dv = torch.full(shape, np.nan, dtype=torch.float64).pin_memory().numpy()
@@ -391,3 +402,32 @@ def test_host_entry_points_match_device_ones(gw):
             np.testing.assert_array_equal(outs[0][0][n], o[0][n])
         assert level_error(o[1], outs[0][1]) <= 1e-12
         assert level_error(o[2], outs[0][2]) <= 1e-12
+
+
+def test_async_host_entry_points_reject_and_report(gw):
+    """Pageable buffers are refused (GWAM_EINVAL) by the asynchronous entry points; an invalid
+    background (N^2 <= f^2) set asynchronously is reported by the next synchronising call."""
+    import torch
+    w = synth.workload("fplane")
+    grid, params = w["grid"], w["params"]
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    T = gw.Tracer(grid, params, max_rays=4096)
+    with pytest.raises(gw.GwamError):
+        T.set_background_async(*w["background"])
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in w["background"]]
+    T.set_background_async(*pinned)
+    T.add_rays(synth.fplane_rays(grid, 100, tag=13))
+    with pytest.raises(gw.GwamError):
+        T.step_host_async(300.0, np.zeros(shape), np.zeros(shape))
+    du = torch.zeros(shape, dtype=torch.float64).pin_memory().numpy()
+    dv = torch.zeros(shape, dtype=torch.float64).pin_memory().numpy()
+    T.step_host_async(300.0, du, dv)
+    T.synchronize()
+    bad = [a.copy() for a in pinned]
+    bad[2][3, 2, 1] = 0.0        # N^2 <= f^2 at one node
+    bad = [torch.from_numpy(a).pin_memory().numpy() for a in bad]
+    T.set_background_async(*bad)
+    T.step_host_async(300.0, du, dv)
+    with pytest.raises(gw.GwamError) as e:
+        T.synchronize()
+    assert e.value.code == -4          # GWAM_ENUMERIC
