@@ -58,16 +58,20 @@ struct FieldSet32 {
 };
 
 // separable 1-2-1 x 1-2-1 smoothing (periodic in lambda, edge row reused at the poles).  A warp
-// owns 32 consecutive levels of one row over a run of kSpan columns and slides a 3 x 3 window along
-// the row: each new column costs 3 loads (rows j-1, j, j+1) instead of 9, the column sums of the
-// previous two columns are kept in registers.  Warp item = (field, member, row, level group, span).
-constexpr int kSpan = 64;
+// owns 32 consecutive levels of kRows32 rows over a run of kSpan columns and slides a 3 x 3 window
+// along the rows: each new column costs kRows32 + 2 loads (the rows and their two neighbours) for
+// kRows32 outputs, and the column sums of the previous two columns stay in registers (two rows over
+// spans of 32 columns: measured faster than one row, or spans of 16 or 64).  Warp item = (field,
+// member, row group, level group, span).
+constexpr int kSpan = 32;
+constexpr int kRows32 = 2;
 __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, int f0, int nf)
 {
     const int lane = threadIdx.x & 31;
     const int nlg = (G.nz + 1 + 31) / 32;                   // level groups (interface fields have nz + 1)
     const int nsp = (G.nx + kSpan - 1) / kSpan;
-    const long long per_field = (long long)G.members * G.ny * nlg * nsp;
+    const int nrg = (G.ny + kRows32 - 1) / kRows32;
+    const long long per_field = (long long)G.members * nrg * nlg * nsp;
     const long long items = per_field * nf;
     const long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (w >= items) return;
@@ -77,57 +81,72 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     r /= nsp;
     const int lg = (int)(r % nlg);
     r /= nlg;
-    const int j = (int)(r % G.ny);
-    const int mem = (int)(r / G.ny);
+    const int rg = (int)(r % nrg);
+    const int mem = (int)(r / nrg);
     const int nlev = f <= F_ZP ? G.nz + 1 : G.nz;
     const int lev = lg * 32 + lane;
     if (lg * 32 >= nlev) return;
-    int jm = j - 1, jp = j + 1;
-    if (G.geometry == 1) {
-        jm = jm < 0 ? 0 : jm;
-        jp = jp >= G.ny ? G.ny - 1 : jp;
-    } else {
-        jm = jm < 0 ? G.ny - 1 : jm;
-        jp = jp >= G.ny ? 0 : jp;
-    }
     const bool live = lev < nlev;
+    const int j0 = rg * kRows32;
+    const int nrow = min(kRows32, G.ny - j0);
     const int64_t base = (int64_t)mem * G.ncol;
     const float* __restrict__ F = fs.in[f];
-    const float* R0 = F + (base + (int64_t)jm * G.nx) * nlev + lev;
-    const float* R1 = F + (base + (int64_t)j * G.nx) * nlev + lev;
-    const float* R2 = F + (base + (int64_t)jp * G.nx) * nlev + lev;
-    float* O = fs.out[f] + (base + (int64_t)j * G.nx) * nlev + lev;
-    const int i0 = sp * kSpan, i1 = min(G.nx, i0 + kSpan);
-    // vertical 1-2-1 column sums at columns i0 - 1 and i0
-    auto colsum = [&](int i) -> float {
-        const int64_t o = (int64_t)i * nlev;
-        return live ? R0[o] + 2.0f * R1[o] + R2[o] : 0.0f;
-    };
-    float cm = colsum(i0 == 0 ? G.nx - 1 : i0 - 1);
-    float c0 = colsum(i0);
-    int i = i0;
-    // four columns per pass with their twelve loads issued together
-    for (; i + 4 <= i1; i += 4) {
-        float c[4];
+    // source rows j0 - 1 .. j0 + kRows32 (clamped at the poles, wrapped on the f-plane)
+    const float* src[kRows32 + 2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int ii = i + 1 + q;
-            c[q] = colsum(ii >= G.nx ? ii - G.nx : ii);
-        }
+    for (int q = 0; q < kRows32 + 2; ++q) {
+        int jj = j0 - 1 + q;
+        if (G.geometry == 1) jj = jj < 0 ? 0 : (jj >= G.ny ? G.ny - 1 : jj);
+        else jj = jj < 0 ? jj + G.ny : (jj >= G.ny ? jj - G.ny : jj);
+        src[q] = F + (base + (int64_t)jj * G.nx) * nlev + lev;
+    }
+    float* O = fs.out[f] + (base + (int64_t)j0 * G.nx) * nlev + lev;
+    const int64_t orow = (int64_t)G.nx * nlev;
+    // vertical 1-2-1 column sums of the kRows32 rows at column i
+    auto colsums = [&](int i, float (&cs)[kRows32]) {
+        float v[kRows32 + 2];
+        const int64_t o = (int64_t)i * nlev;
+#pragma unroll
+        for (int q = 0; q < kRows32 + 2; ++q) v[q] = live ? src[q][o] : 0.0f;
+#pragma unroll
+        for (int q = 0; q < kRows32; ++q) cs[q] = v[q] + 2.0f * v[q + 1] + v[q + 2];
+    };
+    const int i0 = sp * kSpan, i1 = min(G.nx, i0 + kSpan);
+    float cm[kRows32], c0[kRows32], cp[kRows32], cq[kRows32];
+    colsums(i0 == 0 ? G.nx - 1 : i0 - 1, cm);
+    colsums(i0, c0);
+    int i = i0;
+    // two columns per pass with their loads issued together
+    for (; i + 2 <= i1; i += 2) {
+        colsums(i + 1 == G.nx ? 0 : i + 1, cp);
+        colsums(i + 2 >= G.nx ? i + 2 - G.nx : i + 2, cq);
         if (live) {
-            O[(int64_t)i * nlev] = (cm + 2.0f * c0 + c[0]) * 0.0625f;
-            O[(int64_t)(i + 1) * nlev] = (c0 + 2.0f * c[0] + c[1]) * 0.0625f;
-            O[(int64_t)(i + 2) * nlev] = (c[0] + 2.0f * c[1] + c[2]) * 0.0625f;
-            O[(int64_t)(i + 3) * nlev] = (c[1] + 2.0f * c[2] + c[3]) * 0.0625f;
+#pragma unroll
+            for (int q = 0; q < kRows32; ++q) {
+                if (q < nrow) {
+                    O[q * orow + (int64_t)i * nlev] = (cm[q] + 2.0f * c0[q] + cp[q]) * 0.0625f;
+                    O[q * orow + (int64_t)(i + 1) * nlev] = (c0[q] + 2.0f * cp[q] + cq[q]) * 0.0625f;
+                }
+            }
         }
-        cm = c[2];
-        c0 = c[3];
+#pragma unroll
+        for (int q = 0; q < kRows32; ++q) {
+            cm[q] = cp[q];
+            c0[q] = cq[q];
+        }
     }
     for (; i < i1; ++i) {
-        const float cp = colsum(i + 1 == G.nx ? 0 : i + 1);
-        if (live) O[(int64_t)i * nlev] = (cm + 2.0f * c0 + cp) * 0.0625f;
-        cm = c0;
-        c0 = cp;
+        colsums(i + 1 == G.nx ? 0 : i + 1, cp);
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < kRows32; ++q)
+                if (q < nrow) O[q * orow + (int64_t)i * nlev] = (cm[q] + 2.0f * c0[q] + cp[q]) * 0.0625f;
+        }
+#pragma unroll
+        for (int q = 0; q < kRows32; ++q) {
+            cm[q] = c0[q];
+            c0[q] = cp[q];
+        }
     }
 }
 
@@ -282,8 +301,8 @@ static void smooth32(Context& c, int f0, int f1)
         fs.in[f] = c.nar32[f];
         fs.out[f] = c.sm32[f];
     }
-    const long long warps = (long long)(f1 - f0) * c.G.members * c.G.ny * ((c.G.nz + 1 + 31) / 32) *
-                            ((c.G.nx + kSpan - 1) / kSpan);
+    const long long warps = (long long)(f1 - f0) * c.G.members * ((c.G.ny + kRows32 - 1) / kRows32) *
+                            ((c.G.nz + 1 + 31) / 32) * ((c.G.nx + kSpan - 1) / kSpan);
     k_smooth_fields32<<<(unsigned)((warps + 7) / 8), 256, 0, c.stream>>>(c.G, fs, f0, f1 - f0);
 }
 
