@@ -181,7 +181,9 @@ int gwam_launch_spectral_host(gwam_ctx *ctx, const gwam_spec *specs, int64_t n);
  * whole) to the ghost's top, with the ghost's m, N, horizontal extents and P_z in proportion to
  * the extent -- is appended as a new ray volume (n_launched, w_launched); a bin from which
  * nothing has left the layer appends nothing.  Called once per model step before gwam_step, this
- * emits the source flux every interval.  FP64 form only (precision 1: GWAM_EINVAL); dt not > 0 or
+ * emits the source flux every interval.  The ghost is integrated in the FP64 form's double-float
+ * arithmetic in both forms: a precision-form context allocates double-float background nodes
+ * (128 B per node) at its first ghost-layer launch and keeps them set from then on.  dt not > 0 or
  * not finite: GWAM_EINVAL.  Stream-ordered like the launches above. */
 int gwam_launch_ghost(gwam_ctx *ctx, const gwam_bg_source *src, double dt);
 int gwam_launch_ghost_spectral(gwam_ctx *ctx, const gwam_spec *specs, int64_t n, double dt);

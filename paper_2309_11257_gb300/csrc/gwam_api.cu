@@ -501,7 +501,23 @@ static int add_rays_impl(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n, bool
 int gwam_add_rays(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n) { return add_rays_impl(ctx, r, n, false); }
 int gwam_add_rays_host(gwam_ctx* ctx, const gwam_ray_input* r, int64_t n) { return add_rays_impl(ctx, r, n, true); }
 
-// ghost_dt > 0: ghost-layer emission over one launch interval (FP64 form only)
+static int check_ghost(gwam_ctx* ctx, double dt)
+{
+    if (!ctx) return GWAM_EINVAL;
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    return GWAM_OK;
+}
+
+// the ghost volume is integrated by the FP64 form's double-float RK3: a precision-form context keeps
+// double-float nodes too from its first ghost-layer launch on (set-up writes them from then on)
+static void ensure_bgdf(Context& c)
+{
+    if (c.bgdf) return;
+    dalloc(c, c.bgdf, (size_t)c.G.ncell_all);
+    for (int m = 0; m < c.G.members; ++m) node_gradients_df(c, m);
+}
+
+// ghost_dt > 0: ghost-layer emission over one launch interval
 static int launch_sources_impl(gwam_ctx* ctx, const gwam_bg_source* src, double ghost_dt)
 {
     API_BEGIN(ctx)
@@ -513,23 +529,14 @@ static int launch_sources_impl(gwam_ctx* ctx, const gwam_bg_source* src, double 
     if (c.G.geometry != 1 || src->n_az < 1 || src->n_c < 1 || src->n_az * src->n_c > 1024) return GWAM_EINVAL;
     if (!(src->lambda_h > 0.0) || !(src->dz_launch > 0.0) || !(src->c_min > 0.0) || !(src->c_max > 0.0))
         return GWAM_EINVAL;
-    if (ghost_dt > 0.0)
+    if (ghost_dt > 0.0) {
+        ensure_bgdf(c);
         launch_ghost_source(c, *src, ghost_dt);
-    else
+    } else {
         launch_background_source(c, *src);
+    }
     GWAM_CUDA(cudaGetLastError());
     API_END
-}
-
-static int check_ghost(gwam_ctx* ctx, double dt)
-{
-    if (!ctx) return GWAM_EINVAL;
-    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
-    if (ctx->c.f32) {
-        ctx->c.err = "gwam_launch_ghost: the ghost layer is built in the FP64 form only";
-        return GWAM_EINVAL;
-    }
-    return GWAM_OK;
 }
 
 int gwam_launch_sources(gwam_ctx* ctx, const gwam_bg_source* src) { return launch_sources_impl(ctx, src, 0.0); }
@@ -565,10 +572,12 @@ static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n
     }
     int rc = GWAM_OK;
     try {
-        if (ghost_dt > 0.0)
+        if (ghost_dt > 0.0) {
+            ensure_bgdf(c);
             launch_ghost_spectral(c, d, n, ghost_dt);
-        else
+        } else {
             launch_spectral(c, d, n);
+        }
         GWAM_CUDA(cudaGetLastError());
     } catch (int code) {
         rc = code;

@@ -72,7 +72,8 @@ struct Context {
     Ray32SoA A32{}, B32{};
     float4* ray32_mem[2] = {nullptr, nullptr};
     Node32* bg32 = nullptr;
-    NodeDF* bgdf = nullptr;         // FP64 form: the background as double-float pairs (per-step gathers)
+    NodeDF* bgdf = nullptr;         // FP64 form: the background as double-float pairs (per-step gathers);
+                                    // precision form: allocated by its first ghost-layer launch
 
     // per-ray scratch
     int* info = nullptr;            // split code | children << 4 | status << 8
@@ -181,6 +182,7 @@ void launch_background_source(Context& c, const gwam_bg_source& src);
 void launch_spectral(Context& c, const gwam_spec* specs, int64_t n);
 void launch_ghost_source(Context& c, const gwam_bg_source& src, double dt);
 void launch_flag_to_status(Context& c);
+void node_gradients_df(Context& c, int member);
 void launch_ghost_spectral(Context& c, const gwam_spec* specs, int64_t n, double dt);
 void run_step(Context& c, double dt, double* du, double* dv);
 void configure_kernels();

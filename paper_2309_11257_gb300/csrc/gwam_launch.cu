@@ -173,8 +173,17 @@ void launch_set_background(Context& c, int member, const double* u, const double
     k_set_background<<<ntx * c.G.ny, kThreads, shm, c.stream>>>(c.G, c.P.gamma_mode, u, v, n2, rho, c.bg + o,
                                                                 c.rho + o, c.rho_inv + o, c.flag_dev);
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
-    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.f32 ? nullptr : c.bgdf + o,
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.bgdf ? c.bgdf + o : nullptr,
                                                         c.f32 ? c.bg32 + o : nullptr);
+}
+
+// double-float nodes of a precision-form context (its ghost-layer launch integrates the ghost in the
+// FP64 form's double-float RK3): from the FP64 node values already set
+void node_gradients_df(Context& c, int member)
+{
+    const int64_t o = (int64_t)member * c.G.ncell;
+    const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.bgdf + o, nullptr);
 }
 
 // asynchronous background: an invalid value becomes the sticky context status (GWAM_ENUMERIC),
@@ -200,7 +209,7 @@ void restore_background(Context& c, int member)
     const int64_t o = (int64_t)member * c.G.ncell;
     const int blocks = (int)std::min<int64_t>((c.G.ncell + kThreads - 1) / kThreads, 16384);
     k_rho_inv<<<blocks, kThreads, 0, c.stream>>>(c.rho + o, c.rho_inv + o, c.G.ncell);
-    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.f32 ? nullptr : c.bgdf + o,
+    k_node_gradients<<<blocks, kThreads, 0, c.stream>>>(c.G, c.bg + o, c.bgdf ? c.bgdf + o : nullptr,
                                                         c.f32 ? c.bg32 + o : nullptr);
 }
 

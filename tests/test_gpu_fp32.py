@@ -122,6 +122,31 @@ def test_precision_form_columnar_sphere(gw):
     _report_and_check(*out[:2], grid, *out[2:], "columnar sphere 40x20x24, 10 steps")
 
 
+def test_precision_form_ghost_layer_launch(gw):
+    """Ghost-layer emission every interval in the precision form (the ghost integrated in double-float
+    on nodes the context allocates at its first ghost launch): sheared f-plane, 8 cycles, then the
+    bars above against the FP64 oracle running the same cycles."""
+    import torch
+    grid = synth.fplane_grid(nx=12, ny=10, nz=40, dx=40e3, dy=30e3, dz=500.0)
+    bg = synth.perturbed(synth.uniform_background(grid, U=8.0, V=-3.0), tag=61, rel=0.1)
+    params = dict(synth.DEFAULT_PARAMS, cap_per_column=60)
+    specs = synth.uniform_specs(grid, flux=4e-3, z_launch=3e3)
+    T = gw.Tracer(grid, dict(params, precision=1), max_rays=400000)
+    T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in bg])
+    O = oracle.Model(grid, params)
+    O.set_background(*bg)
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    du = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    for _ in range(8):
+        T.launch_ghost_spectral(specs, 240.0)
+        O.launch_ghost_spectral(specs, 240.0)
+        T.step(240.0, du, dv)
+        odu, odv = O.step(240.0)
+    assert T.stats()["n_launched"] > 7 * 0.8 * len(specs)
+    _report_and_check(T, O, grid, du.cpu().numpy(), dv.cpu().numpy(), odu, odv, "ghost f-plane 12x10x40, 8 cycles")
+
+
 def test_precision_form_full_size_sphere(gw):
     """The precision-form benchmark physics at the FP64 workload's size: launch and 2 steps."""
     w = synth.workload("sphere")

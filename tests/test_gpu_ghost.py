@@ -141,11 +141,6 @@ def test_ghost_launch_rejects(gw):
         with pytest.raises(gw.GwamError):
             T.launch_ghost_spectral(specs, dt)
     assert T.num_rays() == 0
-    import torch
-    T32 = gw.Tracer(grid, dict(synth.DEFAULT_PARAMS, precision=1), max_rays=10000)
-    T32.set_background(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in bg])
-    with pytest.raises(gw.GwamError):
-        T32.launch_ghost_spectral(specs, 60.0)
     bad = specs[:4].copy()
     bad["i"][2] = grid["nx"]
     with pytest.raises(gw.GwamError):
