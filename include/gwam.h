@@ -93,8 +93,8 @@ typedef struct {
                              and du/dt, dv/dt from the vertical flux divergence and the elastic term
                              only; 0: the 3-D model */
     int theta_flux;       /* 1: also project the potential-temperature flux of Eq. fluxes:temperature
-                             (fields 9, 10 of gwam_get_field_host) for gwam_get_theta_tendency_host;
-                             FP64 form only (GWAM_EINVAL with precision 1) */
+                             (fields 9, 10 of gwam_get_field_host) for gwam_get_theta_tendency_host,
+                             in either form (FP64 sums; FP32 integrands in the precision form) */
 } gwam_params;
 
 /* Background source of Sec. 3c: alpha(phi) profile, F_sol = alpha(phi) F_s + alpha(-phi) F_w,

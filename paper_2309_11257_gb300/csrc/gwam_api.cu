@@ -144,7 +144,6 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
     if (params->precision != 0 && params->precision != 1) return GWAM_EINVAL;
     if (params->columnar != 0 && params->columnar != 1) return GWAM_EINVAL;
     if (params->theta_flux != 0 && params->theta_flux != 1) return GWAM_EINVAL;
-    if (params->theta_flux && params->precision == 1) return GWAM_EINVAL;
     if (params->max_rays < 1 || params->max_rays >= ((int64_t)1 << 29)) return GWAM_EINVAL;
     if (!(params->alpha_s > 0.0) || !(params->min_split_dz >= 0.0)) return GWAM_EINVAL;
     if (params->flux_form != 0 && params->flux_form != 1) return GWAM_EINVAL;

@@ -526,6 +526,8 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
 }
 
 // Saturation N update and flux projection; per-ray terms in FP32, accumulated in FP64.
+// THETA: also the potential-temperature flux integrals of Eq. fluxes:temperature (fields F_TL, F_TP)
+template <bool THETA>
 __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32SoA B, const Node32* __restrict__ bg,
                                                           const Ctl* ctl, const int* __restrict__ off2,
                                                           const float* __restrict__ kappa,
@@ -534,9 +536,11 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
                                                           double* __restrict__ f_ll, double* __restrict__ f_lp,
                                                           double* __restrict__ f_pl, double* __restrict__ f_pp,
                                                           double* __restrict__ e_l, double* __restrict__ e_p,
-                                                          double* __restrict__ wad, double* __restrict__ partials,
+                                                          double* __restrict__ wad, double* __restrict__ f_tl,
+                                                          double* __restrict__ f_tp, double* __restrict__ partials,
                                                           int pstride)
 {
+    constexpr int NH = THETA ? 9 : 7;   // centre fields of the segmented sums
     // FP64 work is kept out of the per-ray path (GB300's FP64 rate is 1/72 of FP32): the action
     // and the budget terms in double-float, float -> double by integer widening, FP64 only in the
     // grid atomics (L2) and one addition per thread for the budget
@@ -548,7 +552,9 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
         const int p = p0 + threadIdx.x;
         const bool act = p < n;
         int key = -1;
-        DF hv[7] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+        DF hv[NH];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) hv[q] = {0.0f, 0.0f};
         float zl = 0.0f, zp = 0.0f, wh = 0.0f, lo = 0.0f, hi = 0.0f;
         int col = 0, kk0 = 1, nkk = 0;
         if (act) {
@@ -593,6 +599,14 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
                 zp = in.w2 * chr * l * iden;
                 el = -in.f2 * in.n2 * chr * iden * k;
                 ep = -in.f2 * in.n2 * chr * iden * l;
+                if (THETA) {
+                    // Eq. fluxes:temperature without theta-bar / (g rho-bar): ch_r f N^2 / (w^2 - f^2)
+                    // (e_r x k_h), f signed at the ray
+                    const float f = G.geometry == 1 ? 2.0f * G.f_omega * in.g.sphi : G.f_f0;
+                    const float tc = f * in.n2 * chr * iden;
+                    hv[7 % NH].hi = aw * -(tc * l);
+                    hv[8 % NH].hi = aw * (tc * k);
+                }
             } else {
                 t_ll = chx * k; t_lp = chx * l; t_pl = chy * k; t_pp = chy * l;
                 zl = chr * k; zp = chr * l;
@@ -612,9 +626,9 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
         }
         const bool own = warp_run_interior(key);
         if (warp_segment_reduce_df(key, hv) && key >= 0) {
-            double* const dst[7] = {f_ll, f_lp, f_pl, f_pp, e_l, e_p, wad};
+            double* const dst[9] = {f_ll, f_lp, f_pl, f_pp, e_l, e_p, wad, f_tl, f_tp};
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
+            for (int q = 0; q < NH; ++q) {
                 const double v = df_to_double(hv[q]);
                 // the whole cell is this run: store its sum (fields were zeroed before the launch)
                 if (own) dst[q][key] = v;
@@ -733,13 +747,21 @@ void run_step32(Context& c, double dt, double* du, double* dv)
                                               reinterpret_cast<float*>(c.kappa));
     }
     prof_mark(c, 3);
-    for (int f = 0; f < F_TL; ++f) cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
+    for (int f = 0; f < (P.theta_flux ? NFIELD : F_TL); ++f)
+        cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
     tune_mark(c, 4);
-    k_project32<<<lp.blocks, lp.threads, 0, s>>>(G, P, c.B32, c.bg32, c.ctl, off2, reinterpret_cast<const float*>(c.kappa),
-                                                 reinterpret_cast<const float*>(c.k2), dt, c.field[F_ZL],
-                                                 c.field[F_ZP], c.field[F_LL], c.field[F_LP], c.field[F_PL],
-                                                 c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD],
-                                                 c.partials, c.max_blocks);
+    if (P.theta_flux)
+        k_project32<true><<<lp.blocks, lp.threads, 0, s>>>(
+            G, P, c.B32, c.bg32, c.ctl, off2, reinterpret_cast<const float*>(c.kappa),
+            reinterpret_cast<const float*>(c.k2), dt, c.field[F_ZL], c.field[F_ZP], c.field[F_LL], c.field[F_LP],
+            c.field[F_PL], c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD], c.field[F_TL], c.field[F_TP],
+            c.partials, c.max_blocks);
+    else
+        k_project32<false><<<lp.blocks, lp.threads, 0, s>>>(
+            G, P, c.B32, c.bg32, c.ctl, off2, reinterpret_cast<const float*>(c.kappa),
+            reinterpret_cast<const float*>(c.k2), dt, c.field[F_ZL], c.field[F_ZP], c.field[F_LL], c.field[F_LP],
+            c.field[F_PL], c.field[F_PP], c.field[F_EL], c.field[F_EP], c.field[F_WAD], nullptr, nullptr,
+            c.partials, c.max_blocks);
     tune_mark(c, 5);
     if (c.tune_active) ++c.tune_pending;
     prof_mark(c, 4);

@@ -147,6 +147,51 @@ def test_precision_form_ghost_layer_launch(gw):
     _report_and_check(T, O, grid, du.cpu().numpy(), dv.cpu().numpy(), odu, odv, "ghost f-plane 12x10x40, 8 cycles")
 
 
+@pytest.mark.parametrize("geometry", ["sphere", "fplane"])
+def test_precision_form_theta_flux(gw, geometry):
+    """Potential-temperature flux integrals (Eq. fluxes:temperature) and d theta/dt (Eq.
+    mean-flow-impact-t) in the precision form: the field bar above, by the column's largest
+    contribution sum like the elastic terms (f^2 and f share the FP32 latitude resolution), and
+    the tendency by the same column scale of its error scale."""
+    import torch
+    if geometry == "sphere":
+        grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+        bg = synth.perturbed(synth.jet_background(grid, z_peak=15e3, z_width=6e3), tag=31)
+        rays = synth.sphere_rays(grid, 777, tag=32, z_lo=4e3, z_hi=20e3, ext_scale=3.0)
+        dt = 300.0
+    else:
+        grid = synth.fplane_grid(nx=24, ny=20, nz=40, dx=40e3, dy=30e3, dz=500.0)
+        bg = synth.perturbed(synth.uniform_background(grid, U=5.0), tag=21, rel=0.1)
+        rays = synth.fplane_rays(grid, 1500, tag=22, z_lo=3e3, z_hi=15e3, ext_z=1300.0)
+        dt = 240.0
+    rays["n"] = rays["n"] * 30.0
+    _, _, z = synth.node_coords(grid)
+    theta = 240.0 * np.exp(bg[2] * z[:, None, None] / grid["g"])      # d ln theta/dz = N^2 / g
+    params = dict(synth.DEFAULT_PARAMS, cap_per_column=45, theta_flux=1)
+    T = gw.Tracer(grid, dict(params, precision=1), max_rays=200000)
+    T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in bg])
+    T.set_theta(torch.from_numpy(np.ascontiguousarray(theta)).cuda())
+    O = oracle.Model(grid, params)
+    O.set_background(*bg)
+    O.set_theta(theta)
+    T.add_rays(rays)
+    O.add_rays(rays)
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    du = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    for _ in range(6):
+        T.step(dt, du, dv)
+        odu, odv = O.step(dt)
+    _report_and_check(T, O, grid, du.cpu().numpy(), dv.cpu().numpy(), odu, odv, "theta " + geometry)
+    col = lambda S: np.broadcast_to(S.max(axis=0, keepdims=True), S.shape)
+    errs = {n: scaled_error(T.field(n), O.field(n), col(O.field_abs(n))) for n in oracle.THETA_FIELD_NAMES}
+    th, sc = O.theta_tendency()
+    errs["dtheta/dt"] = scaled_error(T.theta_tendency(), th, col(sc))
+    print("  theta fields and tendency:", {k: "%.1e" % v for k, v in errs.items()})
+    assert np.abs(th).max() > 0.0
+    assert max(errs.values()) <= FIELD_TOL, errs
+
+
 def test_precision_form_full_size_sphere(gw):
     """The precision-form benchmark physics at the FP64 workload's size: launch and 2 steps."""
     w = synth.workload("sphere")
