@@ -187,10 +187,18 @@ def gpu_arm(args, rank, world, local_rank):
     dv = torch.zeros_like(du)
     coupled = w.get("coupled", False)
 
-    def one_step():
+    # timed steps replay the step's CUDA graph (gwam_step_graph; --eager: gwam_step); the per-phase
+    # times of the roofline are the CUDA events the graphs carry at the phase boundaries (those of
+    # the last replays inside the timed region), or, eager, the profiled steps of the timed region
+    use_graph = not args.eager
+
+    def one_step(graph=use_graph):
         if ghost:
             T.launch_ghost(w["source"], w["dt"])
-        T.step(w["dt"], du, dv)
+        if graph:
+            T.step_graph(w["dt"], du, dv)
+        else:
+            T.step(w["dt"], du, dv)
         if coupled:
             # online coupling: the host model advances u, v by the drag and hands the background back
             bg_dev[0].add_(du, alpha=w["dt"])
@@ -199,7 +207,8 @@ def gpu_arm(args, rank, world, local_rank):
 
     for _ in range(args.warmup):
         one_step()
-    T.profile(True)
+    if not use_graph:
+        T.profile(True)
     s0 = T.stats()
     sampler = ClockSampler(local_rank)
     sampler.start()
@@ -221,9 +230,15 @@ def gpu_arm(args, rank, world, local_rank):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     s1 = T.stats()
-    phases, nprof = T.profile_read()
-    T.profile(False)
+    if use_graph:
+        phases, ngraphs = T.graph_profile_read()   # already averaged over the graphs' last replays
+        assert ngraphs > 0
+        nprof = 1
+    else:
+        phases, nprof = T.profile_read()
+        T.profile(False)
     ray_steps = s1["ray_steps"] - s0["ray_steps"]
+    rays_per_launch = ray_steps / args.steps
     tot_rs = ray_steps
     ms_max = ms
     if world > 1:
@@ -235,9 +250,8 @@ def gpu_arm(args, rank, world, local_rank):
         tot_rs = float(r.item())
     value = tot_rs / (ms_max / 1000.0)
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (its launches in the profiled eager steps)
     adv_ms = phases["advance"] / max(nprof, 1)
-    rays_per_launch = ray_steps / args.steps
     if fp32:
         # precision form: the ray step reads and writes the 64-byte record
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
@@ -302,7 +316,9 @@ def gpu_arm(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "sphere" else args.workload, "rays_live_start": s0["n_live"], "rays_live_end": s1["n_live"],
-                       "ray_steps_timed": ray_steps, "l2": "working set > L2 (ray state ~0.12-0.24 GB + "
+                       "ray_steps_timed": ray_steps,
+                       "step_call": "gwam_step_graph (one CUDA graph launch per step)" if use_graph else "gwam_step",
+                       "l2": "working set > L2 (ray state ~0.12-0.24 GB + "
                        "grid fields ~0.4 GB per step), no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
             "gpu_launches": None,
             "roofline": roofline,
@@ -527,6 +543,7 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="time gwam_step calls instead of graph replays")
     ap.add_argument("--train-steps", type=int, default=800,
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",

@@ -417,6 +417,11 @@ int gwam_column_targets(const double *du_sum, const double *dv_sum, int nz, int6
  * milliseconds per phase (ms_host[5]) and the number of profiled steps. */
 int gwam_profile_enable(gwam_ctx *ctx, int enable);
 int gwam_profile_read(gwam_ctx *ctx, double *ms_host, int64_t *steps);
+/* The same five phase times for graph replays (gwam_step_graph): each step graph carries event nodes
+ * at the phase boundaries, overwritten by every replay; this call synchronises and returns the
+ * phase times of the last replay of each of the two graphs (one per ray-buffer parity), averaged,
+ * in ms_host[5], and in *replays how many graphs contributed (0 before the first replay). */
+int gwam_graph_profile_read(gwam_ctx *ctx, double *ms_host, int *replays);
 /* Human-readable description of the last error on this context (never NULL). */
 const char *gwam_last_error(const gwam_ctx *ctx);
 /* Library version string. */

@@ -56,6 +56,9 @@ static void free_all(Context& c)
             if (c.tune_ev[q][p]) cudaEventDestroy(c.tune_ev[q][p]);
     for (int q = 0; q < 2; ++q)
         if (c.gexec[q]) cudaGraphExecDestroy(c.gexec[q]);
+    for (int q = 0; q < 2; ++q)
+        for (int p = 0; p <= Context::kPhases; ++p)
+            if (c.gprof_ev[q][p]) cudaEventDestroy(c.gprof_ev[q][p]);
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     for (int q = 0; q < 2; ++q) {
         if (c.bg_stage[q]) cudaFree(c.bg_stage[q]);
@@ -754,11 +757,17 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
             GWAM_CUDA(cudaGraphExecDestroy(c.gexec[par]));
             c.gexec[par] = nullptr;
         }
-        // capture one step on the internal stream; the ray buffers are swapped back afterwards
+        // capture one step on the internal stream; the ray buffers are swapped back afterwards.  The
+        // phase boundaries become event nodes of the graph (gwam_graph_profile_read)
         GWAM_CUDA(cudaStreamSynchronize(c.stream));
+        if (!c.gprof_ev[par][0])
+            for (int p = 0; p <= Context::kPhases; ++p) GWAM_CUDA(cudaEventCreate(&c.gprof_ev[par][p]));
         const bool prof = c.prof, tune = c.tune_active;
         c.prof = false;
         c.tune_active = false;
+        c.gcap_prof = true;
+        c.gcap_par = par;
+        c.glaunched[par] = false;
         cudaStream_t user = c.stream;
         c.stream = c.cap_stream;
         cudaGraph_t graph = nullptr;
@@ -772,6 +781,7 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
         c.stream = user;
         c.prof = prof;
         c.tune_active = tune;
+        c.gcap_prof = false;
         if (e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             c.err = std::string("graph capture: ") + cudaGetErrorString(e);
@@ -789,6 +799,7 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
         c.gdv[par] = dvdt;
     }
     GWAM_CUDA(cudaGraphLaunch(c.gexec[par], c.stream));
+    c.glaunched[par] = true;
     swap_rays(c);
     API_END
 }
@@ -1221,6 +1232,27 @@ int gwam_profile_read(gwam_ctx* ctx, double* ms_host, int64_t* steps)
     prof_harvest(c);
     for (int p = 0; p < Context::kPhases; ++p) ms_host[p] = c.prof_ms[p];
     *steps = c.prof_steps;
+    API_END
+}
+
+int gwam_graph_profile_read(gwam_ctx* ctx, double* ms_host, int* replays)
+{
+    API_BEGIN(ctx)
+    if (!ms_host || !replays) return GWAM_EINVAL;
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    for (int p = 0; p < Context::kPhases; ++p) ms_host[p] = 0.0;
+    int n = 0;
+    for (int par = 0; par < 2; ++par) {
+        if (!c.glaunched[par] || !c.gprof_ev[par][0]) continue;
+        for (int p = 0; p < Context::kPhases; ++p) {
+            float ms = 0.0f;
+            GWAM_CUDA(cudaEventElapsedTime(&ms, c.gprof_ev[par][p], c.gprof_ev[par][p + 1]));
+            ms_host[p] += ms;
+        }
+        ++n;
+    }
+    for (int p = 0; p < Context::kPhases; ++p) ms_host[p] = n ? ms_host[p] / n : 0.0;
+    *replays = n;
     API_END
 }
 

@@ -123,6 +123,12 @@ struct Context {
     static constexpr int kRing = 128;
     bool prof = false;
     cudaEvent_t prof_ev[kRing][kPhases + 1] = {};
+    // the same phase boundaries recorded by the step graphs themselves (one set per ray-buffer
+    // parity; each replay overwrites its set), read by gwam_graph_profile_read
+    cudaEvent_t gprof_ev[2][kPhases + 1] = {};
+    bool gcap_prof = false;     // capturing: prof_mark records into gprof_ev[gcap_par]
+    int gcap_par = 0;
+    bool glaunched[2] = {false, false};
     int prof_pending = 0;
     int64_t prof_steps = 0;
     double prof_ms[kPhases] = {};

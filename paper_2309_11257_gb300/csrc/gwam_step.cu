@@ -829,6 +829,11 @@ void configure_kernels()
 // event `phase` of the current profiled step (phase 0 = step start, kPhases = step end)
 void prof_mark(Context& c, int phase)
 {
+    if (c.gcap_prof) {
+        // an event-record node of the graph (a plain record under capture would only order streams)
+        cudaEventRecordWithFlags(c.gprof_ev[c.gcap_par][phase], c.stream, cudaEventRecordExternal);
+        return;
+    }
     if (!c.prof) return;
     if (phase == 0 && c.prof_pending == Context::kRing) prof_harvest(c);
     cudaEventRecord(c.prof_ev[c.prof_pending][phase], c.stream);

@@ -146,6 +146,7 @@ SIGNATURES = {
     "gwam_column_targets": (C.c_int, [_vp, _vp, C.c_int, C.c_int64, C.c_double, _vp, _vp]),
     "gwam_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
+    "gwam_graph_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int)]),
     "gwam_last_error": (C.c_char_p, [_vp]),
     "gwam_version": (C.c_char_p, []),
 }
@@ -395,6 +396,13 @@ class Tracer:
         ms = np.zeros(5)
         n = C.c_int64()
         self._check(_lib.gwam_profile_read(self._h, ms.ctypes.data_as(_vp), C.byref(n)), "profile_read")
+        return dict(zip(self.PHASES, ms.tolist())), n.value
+
+    def graph_profile_read(self):
+        """Phase times (ms) of the last replay of each step graph, averaged; and how many graphs."""
+        ms = np.zeros(5)
+        n = C.c_int()
+        self._check(_lib.gwam_graph_profile_read(self._h, ms.ctypes.data_as(_vp), C.byref(n)), "graph_profile_read")
         return dict(zip(self.PHASES, ms.tolist())), n.value
 
     def synchronize(self):

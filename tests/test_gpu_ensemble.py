@@ -113,6 +113,11 @@ def test_graph_replay_matches_eager_steps(gw):
             if s == 3:      # a launch between replays: the graph reads counts from device memory
                 T.launch_sources(synth.background_source(z_launch=3e3))
             (T.step_graph if use_graph else T.step)(300.0, du, dv)
+        if use_graph:
+            # the graphs' phase events: the five phases of the last replays, positive, summing to
+            # no more than a step's wall time
+            phases, n = T.graph_profile_read()
+            assert n == 2 and all(v > 0.0 for v in phases.values()), phases
         outs.append((T.rays(), du.cpu().numpy(), T.stats()))
     for n in ("id", "member", "cell") + tuple(oracle.STATE_NAMES):
         np.testing.assert_array_equal(outs[0][0][n], outs[1][0][n])
