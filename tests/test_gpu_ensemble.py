@@ -114,8 +114,7 @@ def test_graph_replay_matches_eager_steps(gw):
                 T.launch_sources(synth.background_source(z_launch=3e3))
             (T.step_graph if use_graph else T.step)(300.0, du, dv)
         if use_graph:
-            # the graphs' phase events: the five phases of the last replays, positive, summing to
-            # no more than a step's wall time
+            # the graphs' phase events: the five phase times of the last replays, all positive
             phases, n = T.graph_profile_read()
             assert n == 2 and all(v > 0.0 for v in phases.values()), phases
         outs.append((T.rays(), du.cpu().numpy(), T.stats()))
