@@ -239,6 +239,9 @@ def gpu_arm(args, rank, world, local_rank):
         T.profile(False)
     ray_steps = s1["ray_steps"] - s0["ray_steps"]
     rays_per_launch = ray_steps / args.steps
+    if use_graph and ghost:
+        # the graphs' phase times are those of the last steps; the population grows every step
+        rays_per_launch = s1["n_live"]
     tot_rs = ray_steps
     ms_max = ms
     if world > 1:
