@@ -201,7 +201,8 @@ int gwam_step(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
  * four page-locked caller fields into one of two device staging slots and sets every member's
  * background from it (as gwam_set_background); an invalid value (as there) becomes the sticky
  * context status GWAM_ENUMERIC, reported by the next synchronising call, and the steps in between
- * do nothing.  gwam_step_host_async runs gwam_step into one of two device output slots and copies
+ * do nothing.  gwam_step_host_async runs the step (as gwam_step_graph: one graph per output slot,
+ * the slots alternating with the ray buffers) into one of two device output slots and copies
  * du/dt, dv/dt into the page-locked caller buffers (either may be NULL).  The caller keeps the input
  * fields unchanged and reads the outputs only after a synchronising call (gwam_synchronize,
  * gwam_get_stats, ...); buffers that are not page-locked: GWAM_EINVAL. */

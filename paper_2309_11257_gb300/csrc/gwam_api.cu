@@ -651,6 +651,8 @@ int gwam_step_host(gwam_ctx* ctx, double dt, double* dudt_host, double* dvdt_hos
     API_END
 }
 
+static void graph_step(Context& c, double dt, double* dudt, double* dvdt);
+
 // ---------------------------------------------------------------- asynchronous host entry points
 
 // page-locked host memory [p, p + bytes) (cudaHostAlloc / cudaHostRegister)
@@ -733,7 +735,7 @@ int gwam_step_host_async(gwam_ctx* ctx, double dt, double* dudt_host, double* dv
     double* dv = du + n;
     // this slot's previous copies to the host (two calls back) must be done before it is rewritten
     GWAM_CUDA(cudaStreamWaitEvent(c.stream, c.ev_d2h[k], 0));
-    run_step(c, dt, du, dv);
+    graph_step(c, dt, du, dv);   // the slots alternate with the ray-buffer parity: one graph each
     GWAM_CUDA(cudaEventRecord(c.ev_dready[k], c.stream));
     GWAM_CUDA(cudaStreamWaitEvent(c.down_stream, c.ev_dready[k], 0));
     if (dudt_host) GWAM_CUDA(cudaMemcpyAsync(dudt_host, du, bytes, cudaMemcpyDeviceToHost, c.down_stream));
@@ -743,14 +745,10 @@ int gwam_step_host_async(gwam_ctx* ctx, double dt, double* dudt_host, double* dv
     API_END
 }
 
-int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
+// one step as a replay of the step's CUDA graph for (dt, dudt, dvdt), captured on first use per
+// ray-buffer parity; throws (int) status on failure
+static void graph_step(Context& c, double dt, double* dudt, double* dvdt)
 {
-    API_BEGIN(ctx)
-    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
-    if (!c.have_bg) {
-        c.err = "gwam_step_graph: no background";
-        return GWAM_ESTATE;
-    }
     const int par = c.parity();
     if (!c.gexec[par] || c.gdt[par] != dt || c.gdu[par] != dudt || c.gdv[par] != dvdt) {
         if (c.gexec[par]) {
@@ -785,14 +783,14 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
         if (e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
             c.err = std::string("graph capture: ") + cudaGetErrorString(e);
-            return GWAM_ECUDA;
+            throw (int)GWAM_ECUDA;
         }
         e = cudaGraphInstantiate(&c.gexec[par], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             c.gexec[par] = nullptr;
             c.err = std::string("graph instantiate: ") + cudaGetErrorString(e);
-            return GWAM_ECUDA;
+            throw (int)GWAM_ECUDA;
         }
         c.gdt[par] = dt;
         c.gdu[par] = dudt;
@@ -801,6 +799,17 @@ int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
     GWAM_CUDA(cudaGraphLaunch(c.gexec[par], c.stream));
     c.glaunched[par] = true;
     swap_rays(c);
+}
+
+int gwam_step_graph(gwam_ctx* ctx, double dt, double* dudt, double* dvdt)
+{
+    API_BEGIN(ctx)
+    if (!(dt > 0.0) || !isfinite(dt)) return GWAM_EINVAL;
+    if (!c.have_bg) {
+        c.err = "gwam_step_graph: no background";
+        return GWAM_ESTATE;
+    }
+    graph_step(c, dt, dudt, dvdt);
     API_END
 }
 
