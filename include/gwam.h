@@ -213,8 +213,9 @@ int gwam_step_host_async(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
 /* The same step replayed from a CUDA graph: the first call for a given (dt, dudt, dvdt) captures the
  * step's kernels (two graphs, one per ray-buffer parity) on an internal stream; later calls launch
  * the graph on the context's stream -- one launch per step.  Launches and backgrounds may change
- * between calls (the kernels read counts from device memory).  Per-phase profiling is not recorded
- * inside graphs. */
+ * between calls (the kernels read counts from device memory).  The graphs carry event nodes at the
+ * phase boundaries instead of the per-phase profiling of gwam_profile_enable
+ * (gwam_graph_profile_read). */
 int gwam_step_graph(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
 /* The same with host output buffers (copied back and synchronised). */
 int gwam_step_host(gwam_ctx *ctx, double dt, double *dudt_host, double *dvdt_host);

@@ -38,7 +38,7 @@ static void free_all(Context& c)
                     c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
                     c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
                     c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
-                    c.flag_dev};
+                    c.flag_dev, c.spec_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int f = 0; f < NFIELD; ++f) {
@@ -560,7 +560,6 @@ static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n
     if (n == 0) return GWAM_OK;
     if (n >= ((int64_t)1 << 30)) return GWAM_EINVAL;
     const gwam_spec* d = specs;
-    gwam_spec* tmp = nullptr;
     if (host) {
         for (int64_t q = 0; q < n; ++q) {
             const gwam_spec& s = specs[q];
@@ -568,27 +567,26 @@ static int launch_spectral_impl(gwam_ctx* ctx, const gwam_spec* specs, int64_t n
                 !(s.lambda_h > 0.0) || !(s.dz_launch > 0.0))
                 return GWAM_EINVAL;
         }
-        GWAM_CUDA(cudaMalloc((void**)&tmp, sizeof(gwam_spec) * (size_t)n));
-        h2d(c, tmp, specs, sizeof(gwam_spec) * (size_t)n);
-        d = tmp;
-    }
-    int rc = GWAM_OK;
-    try {
-        if (ghost_dt > 0.0) {
-            ensure_bgdf(c);
-            launch_ghost_spectral(c, d, n, ghost_dt);
-        } else {
-            launch_spectral(c, d, n);
+        // a device copy kept between calls (per-step ghost launches from host specs do not allocate
+        // or wait): the copy is ordered on the stream after the kernels that read the previous one
+        if (n > c.spec_cap) {
+            GWAM_CUDA(cudaStreamSynchronize(c.stream));
+            if (c.spec_buf) GWAM_CUDA(cudaFree(c.spec_buf));
+            c.spec_buf = nullptr;
+            c.spec_cap = 0;
+            GWAM_CUDA(cudaMalloc((void**)&c.spec_buf, sizeof(gwam_spec) * (size_t)n));
+            c.spec_cap = n;
         }
-        GWAM_CUDA(cudaGetLastError());
-    } catch (int code) {
-        rc = code;
+        h2d(c, c.spec_buf, specs, sizeof(gwam_spec) * (size_t)n);
+        d = c.spec_buf;
     }
-    if (tmp) {
-        cudaStreamSynchronize(c.stream);
-        cudaFree(tmp);
+    if (ghost_dt > 0.0) {
+        ensure_bgdf(c);
+        launch_ghost_spectral(c, d, n, ghost_dt);
+    } else {
+        launch_spectral(c, d, n);
     }
-    if (rc) return rc;
+    GWAM_CUDA(cudaGetLastError());
     API_END
 }
 

@@ -64,6 +64,8 @@ struct Context {
     float* tables32 = nullptr;      // row_cos32[ny], whf32[ny], ivol32[ny * nz]
     float2* tables_df = nullptr;    // row_cos, row_inv_cos [ny], lev_inv_r [nz] as double-float pairs
     double* bg_scratch = nullptr;   // staging of caller fields ([nz][ny][nx], 4 fields)
+    gwam_spec* spec_buf = nullptr;  // device copy of host spectral launches (grown, kept)
+    int64_t spec_cap = 0;
 
     // ray volumes: A holds the canonical array between steps, B is the re-binned output
     bool f32 = false;               // precision form: FP32 records and background
