@@ -183,6 +183,8 @@ def gpu_arm(args, rank, world, local_rank):
     T.set_background(*bg_dev)
     if not ghost:
         T.launch_sources(w["source"])
+    if params.get("theta_flux"):
+        T.set_theta(torch.from_numpy(synth.isothermal_theta(grid)).to(dev))
     du = torch.zeros((nz, ny, nx), dtype=torch.float64, device=dev)
     dv = torch.zeros_like(du)
     coupled = w.get("coupled", False)
@@ -551,11 +553,12 @@ def main():
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
                     choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate",
-                             "sphere_columnar", "sphere_coupled", "sphere_ghost"],
+                             "sphere_columnar", "sphere_coupled", "sphere_ghost", "sphere_theta"],
                     help="sphere_half: the same physics on 128 x 64 columns (profiling captures); "
                          "sphere_columnar: the sphere in the single-column (MS-GWaM-1D) mode; "
                          "sphere_coupled: the sphere with u, v advanced by the drag after every step "
                          "(add on the device, then gwam_set_background, inside the timed region); "
+                         "sphere_theta: the sphere with the potential-temperature flux projected too; "
                          "sphere_ghost: the source emitted through the ghost layer before every 60 s step, "
                          "from no rays (the count grows by up to 0.98 M per step); "
                          "ensemble: 16 members of the sphere with convective sources, graph-replayed steps; "

@@ -291,16 +291,28 @@ def workload(name: str) -> dict:
         grid = sphere_grid(nx=256, ny=128, nz=90, dz=1000.0)
         return dict(name=name, grid=grid, params=dict(DEFAULT_PARAMS), background=jet_background(grid),
                     rays=None, source=background_source(), dt=60.0, steps=200, ghost=True)
-    if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32", "sphere_columnar", "sphere_coupled"):
+    if name in ("sphere", "sphere_fp32", "sphere_half", "sphere_half_fp32", "sphere_columnar", "sphere_coupled",
+                "sphere_theta"):
         nx, ny = {"sphere": (256, 128), "sphere_fp32": (512, 256), "sphere_half": (128, 64),
-                  "sphere_half_fp32": (128, 64), "sphere_columnar": (256, 128), "sphere_coupled": (256, 128)}[name]
+                  "sphere_half_fp32": (128, 64), "sphere_columnar": (256, 128), "sphere_coupled": (256, 128),
+                  "sphere_theta": (256, 128)}[name]
         grid = sphere_grid(nx=nx, ny=ny, nz=90, dz=1000.0)
-        params = dict(DEFAULT_PARAMS, columnar=1 if name == "sphere_columnar" else 0)
+        # sphere_theta: the potential-temperature flux integrals projected as well (theta_flux)
+        params = dict(DEFAULT_PARAMS, columnar=1 if name == "sphere_columnar" else 0,
+                      theta_flux=1 if name == "sphere_theta" else 0)
         # sphere_coupled: the background is advanced by the drag after every step (online coupling)
         return dict(name=name, grid=grid, params=params, background=jet_background(grid),
                     rays=None, source=background_source(), dt=180.0, steps=200,
                     coupled=name == "sphere_coupled")
     raise KeyError(name)
+
+
+def isothermal_theta(grid: dict, T=240.0):
+    """Reference potential temperature of the isothermal atmosphere: d ln theta / dz = N^2 / g."""
+    n2c, _, _ = isothermal(T)
+    _, _, z = node_coords(grid)
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    return np.broadcast_to((T * np.exp(n2c * z / GRAVITY))[:, None, None], shape).copy()
 
 
 def ensemble_members(grid: dict, members: int = 16, tag: int = 4):
