@@ -199,7 +199,9 @@ int gwam_step(gwam_ctx *ctx, double dt, double *dudt, double *dvdt);
 /* Asynchronous host entry points: the host-link copies run on two copy streams of the context (one
  * per direction) and overlap the steps; neither call waits for the device.  gwam_set_background_host_async copies the
  * four page-locked caller fields into one of two device staging slots and sets every member's
- * background from it (as gwam_set_background); an invalid value (as there) becomes the sticky
+ * background from it (as gwam_set_background) into a second background set on a set-up stream of
+ * its own, overlapping the step in flight; the next step reads the new set (the two sets swap at
+ * every call; the first call allocates the second set, about 180 B per node); an invalid value (as there) becomes the sticky
  * context status GWAM_ENUMERIC, reported by the next synchronising call, and the steps in between
  * do nothing.  gwam_step_host_async runs the step (as gwam_step_graph: one graph per output slot,
  * the slots alternating with the ray buffers) into one of two device output slots and copies

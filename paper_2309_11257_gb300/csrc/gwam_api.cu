@@ -54,11 +54,20 @@ static void free_all(Context& c)
     for (int q = 0; q < Context::kTuneRing; ++q)
         for (int p = 0; p < 6; ++p)
             if (c.tune_ev[q][p]) cudaEventDestroy(c.tune_ev[q][p]);
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < Context::kGraphs; ++q)
         if (c.gexec[q]) cudaGraphExecDestroy(c.gexec[q]);
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < Context::kGraphs; ++q)
         for (int p = 0; p <= Context::kPhases; ++p)
             if (c.gprof_ev[q][p]) cudaEventDestroy(c.gprof_ev[q][p]);
+    {
+        void* alt[] = {c.bg_alt, c.bgdf_alt, c.bg32_alt, c.rho_alt, c.rho_inv_alt, c.rho_inv32_alt, c.flag_async};
+        for (void* p : alt)
+            if (p) cudaFree(p);
+        for (int q = 0; q < 2; ++q)
+            if (c.ev_rel[q]) cudaEventDestroy(c.ev_rel[q]);
+        if (c.ev_setup_done) cudaEventDestroy(c.ev_setup_done);
+        if (c.setup_stream) cudaStreamDestroy(c.setup_stream);
+    }
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     for (int q = 0; q < 2; ++q) {
         if (c.bg_stage[q]) cudaFree(c.bg_stage[q]);
@@ -516,6 +525,8 @@ static void ensure_bgdf(Context& c)
 {
     if (c.bgdf) return;
     dalloc(c, c.bgdf, (size_t)c.G.ncell_all);
+    // the second background set (asynchronous path) gets its nodes at its next set-up
+    if (c.bg_alt && !c.bgdf_alt) dalloc(c, c.bgdf_alt, (size_t)c.G.ncell_all);
     for (int m = 0; m < c.G.members; ++m) node_gradients_df(c, m);
 }
 
@@ -671,12 +682,35 @@ static void async_setup(Context& c)
     if (c.up_stream) return;
     GWAM_CUDA(cudaStreamCreateWithFlags(&c.up_stream, cudaStreamNonBlocking));
     GWAM_CUDA(cudaStreamCreateWithFlags(&c.down_stream, cudaStreamNonBlocking));
+    GWAM_CUDA(cudaStreamCreateWithFlags(&c.setup_stream, cudaStreamNonBlocking));
     for (int q = 0; q < 2; ++q) {
         dalloc(c, c.bg_stage[q], 4 * (size_t)c.G.ncell);
         dalloc(c, c.d_out[q], 2 * (size_t)c.G.ncell_all);
-        cudaEvent_t* evs[] = {&c.ev_up[q], &c.ev_free[q], &c.ev_dready[q], &c.ev_d2h[q]};
+        cudaEvent_t* evs[] = {&c.ev_up[q], &c.ev_free[q], &c.ev_dready[q], &c.ev_d2h[q], &c.ev_rel[q]};
         for (cudaEvent_t* e : evs) GWAM_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     }
+    GWAM_CUDA(cudaEventCreateWithFlags(&c.ev_setup_done, cudaEventDisableTiming));
+    // the second background set, shaped like the first
+    const size_t nc = (size_t)c.G.ncell_all;
+    dalloc(c, c.bg_alt, nc);
+    dalloc(c, c.rho_alt, nc);
+    dalloc(c, c.rho_inv_alt, nc);
+    if (c.bgdf) dalloc(c, c.bgdf_alt, nc);
+    if (c.bg32) dalloc(c, c.bg32_alt, nc);
+    if (c.rho_inv32) dalloc(c, c.rho_inv32_alt, nc);
+    dalloc(c, c.flag_async, 1);
+}
+
+// exchange the current and the second background set
+static void swap_bg_sets(Context& c)
+{
+    std::swap(c.bg, c.bg_alt);
+    std::swap(c.bgdf, c.bgdf_alt);
+    std::swap(c.bg32, c.bg32_alt);
+    std::swap(c.rho, c.rho_alt);
+    std::swap(c.rho_inv, c.rho_inv_alt);
+    std::swap(c.rho_inv32, c.rho_inv32_alt);
+    c.cur_set ^= 1;
 }
 
 int gwam_set_background_host_async(gwam_ctx* ctx, const double* u, const double* v, const double* n2,
@@ -691,22 +725,44 @@ int gwam_set_background_host_async(gwam_ctx* ctx, const double* u, const double*
             return GWAM_EINVAL;
         }
     async_setup(c);
+    if (c.bgdf && !c.bgdf_alt) dalloc(c, c.bgdf_alt, (size_t)c.G.ncell_all);   // grown since (ghost launch)
     const int k = c.stage_k;
     c.stage_k ^= 1;
     double* st = c.bg_stage[k];
-    // the copies wait until the set-up kernel two calls back has read this slot
+    // the copies wait until the set-up two calls back has read this slot
     GWAM_CUDA(cudaStreamWaitEvent(c.up_stream, c.ev_free[k], 0));
     for (int q = 0; q < 4; ++q)
         GWAM_CUDA(cudaMemcpyAsync(st + q * nc, src[q], bytes, cudaMemcpyHostToDevice, c.up_stream));
     GWAM_CUDA(cudaEventRecord(c.ev_up[k], c.up_stream));
-    GWAM_CUDA(cudaStreamWaitEvent(c.stream, c.ev_up[k], 0));
-    GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
-    for (int m = 0; m < c.G.members; ++m) {
-        launch_set_background(c, m, st, st + nc, st + 2 * nc, st + 3 * nc);
-        if (c.f32) convert_background32(c, m);
+    // the current set stops being current after the work issued so far; the other set is written
+    // on the set-up stream once its own last readers are done, overlapping the steps in flight
+    const int cur = c.cur_set;
+    GWAM_CUDA(cudaEventRecord(c.ev_rel[cur], c.stream));
+    GWAM_CUDA(cudaStreamWaitEvent(c.setup_stream, c.ev_up[k], 0));
+    GWAM_CUDA(cudaStreamWaitEvent(c.setup_stream, c.ev_rel[cur ^ 1], 0));
+    swap_bg_sets(c);
+    cudaStream_t user = c.stream;
+    int* flag = c.flag_dev;
+    c.stream = c.setup_stream;
+    c.flag_dev = c.flag_async;
+    int rc = GWAM_OK;
+    try {
+        GWAM_CUDA(cudaMemsetAsync(c.flag_dev, 0, sizeof(int), c.stream));
+        for (int m = 0; m < c.G.members; ++m) {
+            launch_set_background(c, m, st, st + nc, st + 2 * nc, st + 3 * nc);
+            if (c.f32) convert_background32(c, m);
+        }
+        GWAM_CUDA(cudaEventRecord(c.ev_free[k], c.stream));
+        launch_flag_to_status(c);
+        GWAM_CUDA(cudaEventRecord(c.ev_setup_done, c.stream));
+    } catch (int code) {
+        rc = code;
     }
-    GWAM_CUDA(cudaEventRecord(c.ev_free[k], c.stream));
-    launch_flag_to_status(c);
+    c.stream = user;
+    c.flag_dev = flag;
+    if (rc) return rc;
+    // later work on the context's stream (the next step) waits for the new background
+    GWAM_CUDA(cudaStreamWaitEvent(c.stream, c.ev_setup_done, 0));
     GWAM_CUDA(cudaGetLastError());
     for (int m = 0; m < c.G.members; ++m) c.member_bg[m] = true;
     c.have_bg = true;
@@ -748,22 +804,23 @@ int gwam_step_host_async(gwam_ctx* ctx, double dt, double* dudt_host, double* dv
 static void graph_step(Context& c, double dt, double* dudt, double* dvdt)
 {
     const int par = c.parity();
-    if (!c.gexec[par] || c.gdt[par] != dt || c.gdu[par] != dudt || c.gdv[par] != dvdt) {
-        if (c.gexec[par]) {
-            GWAM_CUDA(cudaGraphExecDestroy(c.gexec[par]));
-            c.gexec[par] = nullptr;
+    const int gi = par + 2 * c.cur_set;   // the graph bakes in the ray buffers and the background set
+    if (!c.gexec[gi] || c.gdt[gi] != dt || c.gdu[gi] != dudt || c.gdv[gi] != dvdt) {
+        if (c.gexec[gi]) {
+            GWAM_CUDA(cudaGraphExecDestroy(c.gexec[gi]));
+            c.gexec[gi] = nullptr;
         }
         // capture one step on the internal stream; the ray buffers are swapped back afterwards.  The
         // phase boundaries become event nodes of the graph (gwam_graph_profile_read)
         GWAM_CUDA(cudaStreamSynchronize(c.stream));
-        if (!c.gprof_ev[par][0])
-            for (int p = 0; p <= Context::kPhases; ++p) GWAM_CUDA(cudaEventCreate(&c.gprof_ev[par][p]));
+        if (!c.gprof_ev[gi][0])
+            for (int p = 0; p <= Context::kPhases; ++p) GWAM_CUDA(cudaEventCreate(&c.gprof_ev[gi][p]));
         const bool prof = c.prof, tune = c.tune_active;
         c.prof = false;
         c.tune_active = false;
         c.gcap_prof = true;
-        c.gcap_par = par;
-        c.glaunched[par] = false;
+        c.gcap_slot = gi;
+        c.glaunched[gi] = false;
         cudaStream_t user = c.stream;
         c.stream = c.cap_stream;
         cudaGraph_t graph = nullptr;
@@ -783,19 +840,19 @@ static void graph_step(Context& c, double dt, double* dudt, double* dvdt)
             c.err = std::string("graph capture: ") + cudaGetErrorString(e);
             throw (int)GWAM_ECUDA;
         }
-        e = cudaGraphInstantiate(&c.gexec[par], graph, 0);
+        e = cudaGraphInstantiate(&c.gexec[gi], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
-            c.gexec[par] = nullptr;
+            c.gexec[gi] = nullptr;
             c.err = std::string("graph instantiate: ") + cudaGetErrorString(e);
             throw (int)GWAM_ECUDA;
         }
-        c.gdt[par] = dt;
-        c.gdu[par] = dudt;
-        c.gdv[par] = dvdt;
+        c.gdt[gi] = dt;
+        c.gdu[gi] = dudt;
+        c.gdv[gi] = dvdt;
     }
-    GWAM_CUDA(cudaGraphLaunch(c.gexec[par], c.stream));
-    c.glaunched[par] = true;
+    GWAM_CUDA(cudaGraphLaunch(c.gexec[gi], c.stream));
+    c.glaunched[gi] = true;
     swap_rays(c);
 }
 
@@ -818,7 +875,7 @@ int gwam_set_launch_config(gwam_ctx* ctx, int kernel, int threads, int blocks)
         blocks > c.max_blocks)
         return GWAM_EINVAL;
     c.lcfg[kernel] = LaunchCfg{threads, blocks};
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < Context::kGraphs; ++q)
         if (c.gexec[q]) {
             cudaGraphExecDestroy(c.gexec[q]);
             c.gexec[q] = nullptr;
@@ -872,7 +929,7 @@ int gwam_autotune(gwam_ctx* ctx, double dt, int steps_per_candidate, double* dud
             }
     }
     for (int k = 0; k < 3; ++k) c.lcfg[k] = best[k];
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < Context::kGraphs; ++q)
         if (c.gexec[q]) {
             cudaGraphExecDestroy(c.gexec[q]);
             c.gexec[q] = nullptr;
@@ -1200,7 +1257,7 @@ int gwam_load(gwam_ctx* ctx, const char* path)
     for (int m = 0; m < c.G.members; ++m) c.member_bg[m] = h.have_bg && flags[m];
     c.have_bg = h.have_bg != 0;
     for (int m = 0; m < c.G.members; ++m) c.have_bg = c.have_bg && c.member_bg[m];
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < Context::kGraphs; ++q)
         if (c.gexec[q]) {
             cudaGraphExecDestroy(c.gexec[q]);
             c.gexec[q] = nullptr;
@@ -1249,11 +1306,11 @@ int gwam_graph_profile_read(gwam_ctx* ctx, double* ms_host, int* replays)
     GWAM_CUDA(cudaStreamSynchronize(c.stream));
     for (int p = 0; p < Context::kPhases; ++p) ms_host[p] = 0.0;
     int n = 0;
-    for (int par = 0; par < 2; ++par) {
-        if (!c.glaunched[par] || !c.gprof_ev[par][0]) continue;
+    for (int gi = 0; gi < Context::kGraphs; ++gi) {
+        if (!c.glaunched[gi] || !c.gprof_ev[gi][0]) continue;
         for (int p = 0; p < Context::kPhases; ++p) {
             float ms = 0.0f;
-            GWAM_CUDA(cudaEventElapsedTime(&ms, c.gprof_ev[par][p], c.gprof_ev[par][p + 1]));
+            GWAM_CUDA(cudaEventElapsedTime(&ms, c.gprof_ev[gi][p], c.gprof_ev[gi][p + 1]));
             ms_host[p] += ms;
         }
         ++n;

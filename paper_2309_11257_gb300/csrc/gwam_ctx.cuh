@@ -125,12 +125,13 @@ struct Context {
     static constexpr int kRing = 128;
     bool prof = false;
     cudaEvent_t prof_ev[kRing][kPhases + 1] = {};
-    // the same phase boundaries recorded by the step graphs themselves (one set per ray-buffer
-    // parity; each replay overwrites its set), read by gwam_graph_profile_read
-    cudaEvent_t gprof_ev[2][kPhases + 1] = {};
-    bool gcap_prof = false;     // capturing: prof_mark records into gprof_ev[gcap_par]
-    int gcap_par = 0;
-    bool glaunched[2] = {false, false};
+    // the same phase boundaries recorded by the step graphs themselves (one set per graph; each
+    // replay overwrites its set), read by gwam_graph_profile_read
+    static constexpr int kGraphs = 4;   // ray-buffer parity x background set
+    cudaEvent_t gprof_ev[kGraphs][kPhases + 1] = {};
+    bool gcap_prof = false;     // capturing: prof_mark records into gprof_ev[gcap_slot]
+    int gcap_slot = 0;
+    bool glaunched[kGraphs] = {};
     int prof_pending = 0;
     int64_t prof_steps = 0;
     double prof_ms[kPhases] = {};
@@ -145,12 +146,27 @@ struct Context {
     cudaEvent_t ev_up[2] = {}, ev_free[2] = {}, ev_dready[2] = {}, ev_d2h[2] = {};
     int stage_k = 0, out_k = 0;
 
-    // CUDA graphs of the step, one per ray-buffer parity, keyed by (dt, dudt, dvdt)
+    // second background set of the asynchronous host path (allocated on first use): the set-up of
+    // the next background writes it on its own stream while the current step reads the other, and
+    // the two are swapped; events order the writes after the last reads
+    Node* bg_alt = nullptr;
+    NodeDF* bgdf_alt = nullptr;
+    Node32* bg32_alt = nullptr;
+    double* rho_alt = nullptr;
+    double* rho_inv_alt = nullptr;
+    float* rho_inv32_alt = nullptr;
+    int cur_set = 0;                // which physical set the pointers above name as current
+    cudaStream_t setup_stream = nullptr;
+    cudaEvent_t ev_rel[2] = {};     // set s no longer read (recorded when it stops being current)
+    cudaEvent_t ev_setup_done = nullptr;
+    int* flag_async = nullptr;      // validation flag of the asynchronous set-up
+
+    // CUDA graphs of the step, one per (ray-buffer parity, background set), keyed by (dt, dudt, dvdt)
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    double gdt[2] = {0.0, 0.0};
-    double* gdu[2] = {nullptr, nullptr};
-    double* gdv[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[kGraphs] = {};
+    double gdt[kGraphs] = {};
+    double* gdu[kGraphs] = {};
+    double* gdv[kGraphs] = {};
     std::vector<bool> member_bg;
 
     // autotuning: event sets around the three heavy kernels, one per step

@@ -831,7 +831,7 @@ void prof_mark(Context& c, int phase)
 {
     if (c.gcap_prof) {
         // an event-record node of the graph (a plain record under capture would only order streams)
-        cudaEventRecordWithFlags(c.gprof_ev[c.gcap_par][phase], c.stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(c.gprof_ev[c.gcap_slot][phase], c.stream, cudaEventRecordExternal);
         return;
     }
     if (!c.prof) return;

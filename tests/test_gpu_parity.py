@@ -404,6 +404,47 @@ def test_host_entry_points_match_device_ones(gw):
         assert level_error(o[2], outs[0][2]) <= 1e-12
 
 
+def test_async_backgrounds_changing_every_step(gw):
+    """A background that changes before every step, set asynchronously (double-buffered background
+    sets, the set-up of the next overlapping the current step) and synchronously: the same ray state
+    bit for bit after every step, and the same tendencies; then a synchronous set-up after the
+    asynchronous ones and a checkpoint of the current set."""
+    import torch
+    w = synth.workload("fplane")
+    grid, params = w["grid"], dict(w["params"], saturation=1, smoothing=1)
+    rays = synth.fplane_rays(grid, 600, tag=14)
+    shape = (grid["nz"], grid["ny"], grid["nx"])
+    bgs = []
+    for s in range(6):
+        u, v, n2, rho = [np.array(a) for a in synth.perturbed(synth.uniform_background(grid, U=10.0), tag=40 + s)]
+        bgs.append([torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in (u, v, n2, rho)])
+    outs = []
+    for mode in ("sync", "async"):
+        T = gw.Tracer(grid, params, max_rays=8192)
+        T.set_background(*bgs[0])
+        T.add_rays(rays)
+        du = torch.zeros(shape, dtype=torch.float64).pin_memory().numpy()
+        dv = torch.zeros(shape, dtype=torch.float64).pin_memory().numpy()
+        states = []
+        for s in range(1, 6):
+            if mode == "async":
+                T.set_background_async(*bgs[s])
+                T.step_host_async(300.0, du, dv)
+                T.synchronize()
+            else:
+                T.set_background(*bgs[s])
+                T.step_host(300.0, du, dv)
+            states.append((T.rays(), du.copy(), dv.copy()))
+        T.set_background(*bgs[0])          # synchronous set-up of the current set after async ones
+        T.step_host(300.0, du, dv)
+        states.append((T.rays(), du.copy(), dv.copy()))
+        outs.append(states)
+    for a, b in zip(*outs):
+        for n in oracle.STATE_NAMES:
+            np.testing.assert_array_equal(a[0][n], b[0][n])
+        assert level_error(b[1], a[1]) <= 1e-12 and level_error(b[2], a[2]) <= 1e-12
+
+
 def test_async_host_entry_points_reject_and_report(gw):
     """Pageable buffers are refused (GWAM_EINVAL) by the asynchronous entry points; an invalid
     background (N^2 <= f^2) set asynchronously is reported by the next synchronising call."""
