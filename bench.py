@@ -157,6 +157,20 @@ def reference_arm(args, rank, world):
 
 # ------------------------------------------------------------------------------------- GPU arm
 
+def whole_job(ms, units, extra_sum, dev, world):
+    """Whole-job figures of N replicas (one per rank, exchanging nothing else): the slowest rank's
+    time, and the units and `extra_sum` (e.g. an end-to-end rate) summed over the ranks."""
+    if world <= 1:
+        return ms, units, extra_sum
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units), float(extra_sum)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u[0].item()), float(u[1].item())
+
+
 def gpu_arm(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -244,15 +258,7 @@ def gpu_arm(args, rank, world, local_rank):
     if use_graph and ghost:
         # the graphs' phase times are those of the last steps; the population grows every step
         rays_per_launch = s1["n_live"]
-    tot_rs = ray_steps
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        r = torch.tensor([float(ray_steps)], dtype=torch.float64, device=dev)
-        dist.all_reduce(r, op=dist.ReduceOp.SUM)
-        tot_rs = float(r.item())
+    ms_max, tot_rs, _ = whole_job(ms, ray_steps, 0.0, dev, world)
     value = tot_rs / (ms_max / 1000.0)
 
     # roofline of the dominant kernel (its launches in the profiled eager steps)
@@ -308,10 +314,7 @@ def gpu_arm(args, rank, world, local_rank):
         t1 = time.perf_counter()
         rs = T.stats()["ray_steps"] - a0
         e2e_val = rs / (t1 - t0)
-        if world > 1:
-            r = torch.tensor([e2e_val], dtype=torch.float64, device=dev)
-            dist.all_reduce(r, op=dist.ReduceOp.SUM)
-            e2e_val = float(r.item())
+        _, _, e2e_val = whole_job(0.0, 0, e2e_val, dev, world)
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 4 * 8 * nz * ny * nx,
                "d2h_bytes_per_step": 2 * 8 * nz * ny * nx, "steps": ke}
 
