@@ -289,7 +289,15 @@ int gwam_cell_offsets(const int32_t *cells, int64_t n, int32_t ncell, int32_t *o
  * loads the library until the process exits).
  *   - ncell must not exceed GWAM_NOALLOC_MAX_CELLS, else GWAM_ECAPACITY and nothing is done.
  *   - The first call on a device, with that device current, looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and remembers it; make that first call before any stream capture.
+ *     With lazy module loading (the CUDA default since 12.2) the array and the kernels are loaded
+ *     onto the device at that first call, not when the library is loaded: make the first call
+ *     before the host model reserves its device memory, or load modules eagerly
+ *     (CUDA_MODULE_LOADING=EAGER) so the array is placed when the library loads.
+ *   - The remembered address belongs to the device's context: after cudaDeviceReset it is stale,
+ *     so do not call this entry point in a process that has reset the device.
+ *   - Errors that the caller's own earlier work left pending are neither reported by this call
+ *     nor cleared by it (each launch's own status is checked).
  *   - All calls share the one array: calls that overlap on the GPU (concurrent streams, threads or
  *     processes sharing a context) race with each other; serialise them. */
 #define GWAM_NOALLOC_MAX_CELLS 16775168
