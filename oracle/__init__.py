@@ -6,8 +6,9 @@ library under ``paper_2309_11257_gb300`` never imports it, and this package
 imports nothing from the library: the two share no code.
 
 The arithmetic lives in ``gwam_oracle.c`` (plain C, FP64, no FMA contraction,
-single threaded); this module compiles it with gcc on first use and wraps it
-with ctypes.  Grid fields are numpy arrays in C order ``[nz][ny][nx]``.
+single threaded unless set_threads asks for more: the per-ray loops then run
+under OpenMP with bit-identical results); this module compiles it with gcc on
+first use and wraps it with ctypes.  Grid fields are numpy arrays in C order ``[nz][ny][nx]``.
 """
 from __future__ import annotations
 
@@ -30,13 +31,15 @@ STATE_NAMES = ("x", "y", "z", "k", "l", "m", "ex", "ey", "ez", "px", "py", "pz",
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared library (gcc, -O2, no FP contraction)."""
+    """Compile the oracle shared library (gcc, -O2, no FP contraction; OpenMP for the optional
+    threaded per-ray loops, left out if the compiler lacks it)."""
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+        r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(base + ["-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -96,6 +99,9 @@ def _declare(lib):
     lib.orc_num_rays.argtypes = [C.c_void_p]
     lib.orc_get_rays.argtypes = [C.c_void_p, _D, _P(C.c_int64), _P(C.c_int32)]
     lib.orc_get_stats.argtypes = [C.c_void_p, _P(Stats)]
+    lib.orc_get_action_scale.argtypes = [C.c_void_p, _D]
+    lib.orc_set_threads.restype = C.c_int
+    lib.orc_set_threads.argtypes = [C.c_void_p, C.c_int]
     lib.orc_get_field.argtypes = [C.c_void_p, C.c_int, _D]
     lib.orc_get_gamma2.argtypes = [C.c_void_p, _D]
     lib.orc_get_field_abs.argtypes = [C.c_void_p, C.c_int, _D]
@@ -190,6 +196,11 @@ class Model:
             self._h = None
 
     # -- inputs
+    def set_threads(self, n: int) -> int:
+        """Threads for the independent per-ray loops (results identical for any count); returns
+        the count in effect."""
+        return int(self._lib.orc_set_threads(self._h, int(n)))
+
     def set_background(self, u, v, n2, rho):
         arrs = [_f64(a).reshape(self.nz, self.ny, self.nx) for a in (u, v, n2, rho)]
         rc = self._lib.orc_set_background(self._h, *[_dp(a) for a in arrs])
@@ -272,6 +283,10 @@ class Model:
         out = {name: st[q].copy() for q, name in enumerate(STATE_NAMES)}
         out["id"] = ids
         out["cell"] = cells
+        # scale of the rounding error of N: its value before the last step's saturation
+        out["n_scale"] = np.zeros(n)
+        if n:
+            self._lib.orc_get_action_scale(self._h, _dp(out["n_scale"]))
         return out
 
     def stats(self) -> dict:
@@ -288,7 +303,8 @@ class Model:
 
     def field_abs(self, name: str) -> np.ndarray:
         """Sum of |contribution| of a projected field (the scale of its rounding error), each
-        contribution taken with the ray volume's wave action before the step's saturation."""
+        contribution taken with the ray volume's wave action before the step's saturation and with
+        the wavenumber and group-velocity components replaced by the magnitudes of their vectors."""
         which = ALL_FIELD_NAMES.index(name)
         nl = self.nz + 1 if which < 2 else self.nz
         out = np.zeros((nl, self.ny, self.nx))

@@ -26,11 +26,18 @@
  *   tendencies ................................................ Eq. mean-flow-impact
  *   wave-action budget ........................................ Sec. 4, Eq. wave-action-budget
  *
+ * Threads (orc_set_threads, default 1): the independent per-ray work -- the RK3 advance, and the
+ * per-ray integrands of saturation and projection -- may run in parallel (OpenMP); every sum,
+ * every bookkeeping decision and every id is still taken one ray at a time in array order, so the
+ * results are bit-identical for any thread count.  This exists only to time the oracle on all host
+ * cores.
+ *
  * Where the paper is silent the code states the reading it takes ("Reading:").
- * Parity unpinned (self-consistent readings with no number in the paper to pin):
- * the lat-lon smoothing stencil, the omitted curvature terms of the tensor
- * divergence, the edge clamps of the gather, the boundary exits and the
- * tie-break of the cap.
+ * Readings with no number in the paper (the lat-lon smoothing stencil, the edge
+ * gradients and clamps of the gather, the boundary exits, the tie-break of the
+ * cap) are pinned to what the reading itself fixes.  Parity unpinned: the
+ * omitted curvature terms of the tensor divergence (the paper gives no
+ * discrete form to pin the omission against).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -65,7 +72,16 @@ struct orc_model {
     double *n_scale;                     /* per ray: wave-action density before this step's saturation */
     int64_t n_scale_cap;
     int n_scale_valid;                   /* set by apply_saturation, consumed by project */
+    int n_scale_current;                 /* n_scale belongs to the current ray array (the last step's
+                                            saturation; cleared when rays are added or reordered) */
+    int threads;                         /* threads for the per-ray loops (<= 1: serial) */
 };
+
+#ifdef _OPENMP
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static) num_threads(m->threads) if(m->threads > 1)")
+#else
+#define ORC_PARALLEL_FOR
+#endif
 
 /* ------------------------------------------------------------------ geometry */
 
@@ -523,6 +539,7 @@ static void reserve(orc_model *m, int64_t need)
 
 static void append_ray(orc_model *m, const double *s, int64_t id)
 {
+    m->n_scale_current = 0;
     reserve(m, m->n + 1);
     for (int c = 0; c < NSTATE; ++c) m->s[c][m->n] = s[c];
     m->id[m->n] = id;
@@ -834,6 +851,7 @@ static int cmp_key(const void *a, const void *b)
 static void sort_rays(orc_model *m)
 {
     int64_t n = m->n;
+    m->n_scale_current = 0;
     key_t_ *key = malloc(sizeof(key_t_) * (size_t)(n ? n : 1));
     for (int64_t q = 0; q < n; ++q) {
         double s[NSTATE];
@@ -997,6 +1015,19 @@ static void apply_saturation(orc_model *m, double dt)
     m->n_scale_valid = m->n_scale != NULL;
     if (m->n_scale_valid)
         for (int64_t q = 0; q < m->n; ++q) m->n_scale[q] = fabs(m->s[SN][q]);
+    m->n_scale_current = m->n_scale_valid;
+    /* per-ray P_j and K_j^2 (independent per ray; the rays of a cell share its j, k) */
+    int64_t nr = m->n;
+    double *PJ = malloc(sizeof(double) * (size_t)(nr ? nr : 1));
+    double *KJ = malloc(sizeof(double) * (size_t)(nr ? nr : 1));
+    ORC_PARALLEL_FOR
+    for (int64_t q = 0; q < nr; ++q) {
+        double s[NSTATE];
+        long i, j, k;
+        load_ray(m, q, s);
+        cell_ijk(m, s, &i, &j, &k);
+        ray_p(m, s, j, k, &PJ[q], &KJ[q]);
+    }
     int64_t a = 0;
     while (a < m->n) {
         int32_t cell = m->cell[a];
@@ -1008,19 +1039,16 @@ static void apply_saturation(orc_model *m, double dt)
         cell_ijk(m, s0, &i, &j, &k);
         double P = 0.0, Q = 0.0;
         for (int64_t q = a; q < b; ++q) {
-            double s[NSTATE], pj, K2;
-            load_ray(m, q, s);
-            ray_p(m, s, j, k, &pj, &K2);
-            P += pj;
-            Q += pj * K2;
+            P += PJ[q];
+            Q += PJ[q] * KJ[q];
         }
         double rho = m->rho[node(m, k, j, i)];
         double kappa = Q > 0.0 ? fmax(0.0, (P - 0.5 * rho) / (2.0 * dt * Q)) : 0.0;
         if (kappa > 0.0) {
             for (int64_t q = a; q < b; ++q) {
-                double s[NSTATE], pj, K2;
+                double s[NSTATE];
                 load_ray(m, q, s);
-                ray_p(m, s, j, k, &pj, &K2);
+                double K2 = KJ[q];
                 double fac = fmax(0.0, 1.0 - 2.0 * kappa * K2 * dt);
                 double nold = s[SN];
                 m->s[SN][q] = nold * fac;
@@ -1029,6 +1057,8 @@ static void apply_saturation(orc_model *m, double dt)
         }
         a = b;
     }
+    free(PJ);
+    free(KJ);
 }
 
 /* ------------------------------------------------------------------ projection (Sec. 2b, Sec. 3b) */
@@ -1075,6 +1105,32 @@ static void ray_fluxes(const orc_model *m, const disp_t *d, double f, double f2,
     }
 }
 
+/* Error scales of the ten flux values of one ray volume (same order as ray_fluxes, all >= 0): each
+ * integrand with the horizontal wavenumber and group-velocity components replaced by the magnitudes
+ * |k_h| and |ch_h| of their vectors, and ch_r by |ch_r|.  The integrands of Eq. fluxes:momentum and
+ * Eq. fluxes:temperature are tensors and vectors built from k_h and ch_h; a component of those
+ * vectors carries a rounding error relative to the vector's magnitude, not to itself (a wave vector
+ * along one axis has a rounding-level component along the other, e.g. cos(pi/2) |k_h|), so the scale
+ * of an integrand is the one that does not depend on the orientation of the wave vector. */
+static void ray_flux_scales(const orc_model *m, const disp_t *d, double f, double f2, double n2, double kh,
+                            double A, double out[10])
+{
+    const double chh = hypot(d->ch[0], d->ch[1]), chr = fabs(d->ch[2]);
+    if (m->P.flux_form == 0) {
+        double den = d->w2 - f2;
+        double t = (d->w2 + f2) * chh * kh / den * A;
+        out[0] = out[1] = out[2] = out[3] = t;
+        out[4] = out[5] = f2 * n2 * chr / den * kh * A;
+        out[6] = out[7] = d->w2 * chr * kh / den * A;
+        out[8] = out[9] = fabs(f) * n2 * chr / den * kh * A;
+    } else {
+        out[0] = out[1] = out[2] = out[3] = chh * kh * A;
+        out[4] = out[5] = 0.0;
+        out[6] = out[7] = chr * kh * A;
+        out[8] = out[9] = 0.0;
+    }
+}
+
 /* Error scales (hfabs, fzabs): sums of |contribution| with the wave action a ray volume had before
  * this step's saturation.  The saturation factor 1 - 2 kappa K^2 dt is a difference of terms of
  * size 1, so its rounding error is of order the unit roundoff relative to 1, not to the factor;
@@ -1093,59 +1149,69 @@ static void project(orc_model *m)
         memset(m->hfabs[f], 0, nc * sizeof(double));
     }
     double dz = m->G.dz;
-    for (int64_t q = 0; q < m->n; ++q) {
+    /* per-ray integrands (independent per ray), then the sums in array order */
+    typedef struct { double fl[10], fa[10], A, A_scale, alpha, w_h, lo, hi; long i, j, k; } ray_proj_t;
+    int64_t nr = m->n;
+    ray_proj_t *RP = malloc(sizeof(ray_proj_t) * (size_t)(nr ? nr : 1));
+    ORC_PARALLEL_FOR
+    for (int64_t q = 0; q < nr; ++q) {
+        ray_proj_t *rp = &RP[q];
         double s[NSTATE], f2, n2, dk, dl, dm;
-        long i, j, k;
         disp_t d;
         load_ray(m, q, s);
-        cell_ijk(m, s, &i, &j, &k);
+        cell_ijk(m, s, &rp->i, &rp->j, &rp->k);
         ray_disp(m, s, &d, &f2, &n2);
         spectral_extents(m, s, &dk, &dl, &dm);
-        double A = s[SN] * dk * dl * dm;
-        double A_scale = (m->n_scale_valid ? m->n_scale[q] : fabs(s[SN])) * dk * dl * dm;
-        double fl[10], fa[10];
+        rp->A = s[SN] * dk * dl * dm;
+        rp->A_scale = (m->n_scale_valid ? m->n_scale[q] : fabs(s[SN])) * dk * dl * dm;
         const double fsgn = is_sphere(m) ? 2.0 * m->G.omega * sin(s[SY]) : m->G.f0;
-        ray_fluxes(m, &d, fsgn, f2, n2, s[SK], s[SL], A, fl);
-        ray_fluxes(m, &d, fsgn, f2, n2, s[SK], s[SL], A_scale, fa);
-        double t_ll = fl[0], t_lp = fl[1], t_pl = fl[2], t_pp = fl[3], e_l = fl[4], e_p = fl[5];
-        double z_l = fl[6], z_p = fl[7];
+        ray_fluxes(m, &d, fsgn, f2, n2, s[SK], s[SL], rp->A, rp->fl);
+        ray_flux_scales(m, &d, fsgn, f2, n2, hypot(s[SK], s[SL]), rp->A_scale, rp->fa);
         /* horizontal fluxes: cell average over the ray volumes whose carrier lies in the cell,
          * each weighted by its share alpha_j = V_j / V_c of the cell volume */
-        double alpha = physical_volume(m, s) / cell_volume(m, j, k);
+        rp->alpha = physical_volume(m, s) / cell_volume(m, rp->j, rp->k);
+        /* horizontal share of the column: solid angle of the ray volume over that of the cell */
+        if (is_sphere(m))
+            rp->w_h = cos(s[SY]) * s[SEX] * s[SEY] / (cos(row_lat(m, rp->j)) * cell_x(m) * cell_y(m));
+        else
+            rp->w_h = s[SEX] * s[SEY] / (m->G.dx * m->G.dy);
+        rp->lo = s[SZ] - 0.5 * s[SEZ];
+        rp->hi = s[SZ] + 0.5 * s[SEZ];
+    }
+    for (int64_t q = 0; q < nr; ++q) {
+        const ray_proj_t *rp = &RP[q];
+        const double *fl = rp->fl, *fa = rp->fa;
+        long i = rp->i, j = rp->j, k = rp->k;
+        double alpha = rp->alpha, A = rp->A;
         size_t c = node(m, k, j, i);
-        m->hf[0][c] += alpha * t_ll;
-        m->hf[1][c] += alpha * t_lp;
-        m->hf[2][c] += alpha * t_pl;
-        m->hf[3][c] += alpha * t_pp;
-        m->hf[4][c] += alpha * e_l;
-        m->hf[5][c] += alpha * e_p;
+        m->hf[0][c] += alpha * fl[0];
+        m->hf[1][c] += alpha * fl[1];
+        m->hf[2][c] += alpha * fl[2];
+        m->hf[3][c] += alpha * fl[3];
+        m->hf[4][c] += alpha * fl[4];
+        m->hf[5][c] += alpha * fl[5];
         m->hf[6][c] += alpha * A;
         m->hf[7][c] += alpha * fl[8];
         m->hf[8][c] += alpha * fl[9];
-        double hv[NFIELD_H] = {fa[0], fa[1], fa[2], fa[3], fa[4], fa[5], A_scale, fa[8], fa[9]};
+        double hv[NFIELD_H] = {fa[0], fa[1], fa[2], fa[3], fa[4], fa[5], rp->A_scale, fa[8], fa[9]};
         for (int f = 0; f < NFIELD_H; ++f) m->hfabs[f][c] += fabs(alpha * hv[f]);
         /* vertical fluxes at the cell interfaces z = kk dz, 1 <= kk <= nz-1: integrate over the
          * staggered cell [(kk - 1/2) dz, (kk + 1/2) dz] of the carrier column; the weight is the
          * horizontal share times the vertical overlap share.  Reading: F^z = 0 at z = 0, z_top. */
-        /* horizontal share of the column: solid angle of the ray volume over that of the cell */
-        double w_h;
-        if (is_sphere(m))
-            w_h = cos(s[SY]) * s[SEX] * s[SEY] / (cos(row_lat(m, j)) * cell_x(m) * cell_y(m));
-        else
-            w_h = s[SEX] * s[SEY] / (m->G.dx * m->G.dy);
-        double lo = s[SZ] - 0.5 * s[SEZ], hi = s[SZ] + 0.5 * s[SEZ];
+        double w_h = rp->w_h, lo = rp->lo, hi = rp->hi;
         for (long kk2 = 1; kk2 < nz; ++kk2) {
             double slo = (kk2 - 0.5) * dz, shi = (kk2 + 0.5) * dz;
             double ov = fmin(hi, shi) - fmax(lo, slo);
             if (!(ov > 0.0)) continue;
             double w = w_h * ov / dz;
             size_t ci = ((size_t)kk2 * ny + (size_t)j) * nx + (size_t)i;
-            m->fz[0][ci] += w * z_l;
-            m->fz[1][ci] += w * z_p;
+            m->fz[0][ci] += w * fl[6];
+            m->fz[1][ci] += w * fl[7];
             m->fzabs[0][ci] += fabs(w * fa[6]);
             m->fzabs[1][ci] += fabs(w * fa[7]);
         }
     }
+    free(RP);
     m->n_scale_valid = 0;
 }
 
@@ -1155,9 +1221,12 @@ static void project(orc_model *m)
 int orc_smooth(const orc_model *m, double *fld, int nlev)
 {
     long nx = m->G.nx, ny = m->G.ny;
-    double *tmp = malloc(sizeof(double) * (size_t)nx * ny);
+    /* levels are independent */
+    double *tmpall = malloc(sizeof(double) * (size_t)nx * ny * (size_t)(nlev > 0 ? nlev : 1));
+    ORC_PARALLEL_FOR
     for (int lev = 0; lev < nlev; ++lev) {
         double *F = fld + (size_t)lev * nx * ny;
+        double *tmp = tmpall + (size_t)lev * nx * ny;
         for (long j = 0; j < ny; ++j)
             for (long i = 0; i < nx; ++i) {
                 double acc = 0.0;
@@ -1173,7 +1242,7 @@ int orc_smooth(const orc_model *m, double *fld, int nlev)
             }
         memcpy(F, tmp, sizeof(double) * (size_t)nx * ny);
     }
-    free(tmp);
+    free(tmpall);
     return 0;
 }
 
@@ -1200,6 +1269,7 @@ int orc_divergence(const orc_model *m, const double *fz_l, const double *fz_p,
 {
     long nx = m->G.nx, ny = m->G.ny, nz = m->G.nz;
     double dX = cell_x(m), dY = cell_y(m), dz = m->G.dz;
+    ORC_PARALLEL_FOR
     for (long k = 0; k < nz; ++k)
         for (long j = 0; j < ny; ++j)
             for (long i = 0; i < nx; ++i) {
@@ -1397,10 +1467,17 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
     int64_t ncap = 4 * n + 1, nn = 0;
     for (int c = 0; c < NSTATE; ++c) ns[c] = malloc(sizeof(double) * (size_t)ncap);
     int64_t *nid = malloc(sizeof(int64_t) * (size_t)ncap);
+    /* the advance of each ray volume is independent of the others */
+    double *adv = malloc(sizeof(double) * NSTATE * (size_t)(n ? n : 1));
+    ORC_PARALLEL_FOR
+    for (int64_t q = 0; q < n; ++q) {
+        double *sq = adv + (size_t)q * NSTATE;
+        load_ray(m, q, sq);
+        orc_advance_ray(m, sq, dt);
+    }
     for (int64_t q = 0; q < n; ++q) {
         double s[NSTATE];
-        load_ray(m, q, s);
-        orc_advance_ray(m, s, dt);
+        memcpy(s, adv + (size_t)q * NSTATE, sizeof(s));
         int st = ray_status(m, s);
         if (st == 2) {
             m->st.n_invalid++;
@@ -1426,6 +1503,7 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
             ++nn;
         }
     }
+    free(adv);
     m->n = 0;
     reserve(m, nn);
     for (int c = 0; c < NSTATE; ++c) {
@@ -1490,6 +1568,27 @@ int orc_get_rays(const orc_model *m, double *state, int64_t *ids, int32_t *cells
             cells[q] = cell_of(m, s);
         }
     return 0;
+}
+
+/* Per ray volume of the current array: its wave-action density before the last step's saturation
+ * (the scale of the damped density's rounding error, see project), or |N| when the array changed
+ * since that saturation or none ran. */
+int orc_get_action_scale(const orc_model *m, double *out)
+{
+    for (int64_t q = 0; q < m->n; ++q)
+        out[q] = (m->n_scale_current && m->n_scale) ? m->n_scale[q] : fabs(m->s[SN][q]);
+    return 0;
+}
+
+int orc_set_threads(orc_model *m, int threads)
+{
+    m->threads = threads > 1 ? threads : 1;
+#ifdef _OPENMP
+    return m->threads;
+#else
+    m->threads = 1;
+    return 1;
+#endif
 }
 
 void orc_get_stats(const orc_model *m, orc_stats *out)

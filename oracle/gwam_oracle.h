@@ -108,6 +108,11 @@ int64_t orc_num_rays(const orc_model *m);
 /* state: 13 arrays of n in the order x y z k l m dX dY dZ Px Py Pz N (array order) */
 int orc_get_rays(const orc_model *m, double *state13, int64_t *ids, int32_t *cells);
 void orc_get_stats(const orc_model *m, orc_stats *out);
+/* threads for the independent per-ray loops (results bit-identical for any count; returns the count
+ * in effect: 1 when built without OpenMP) */
+int orc_set_threads(orc_model *m, int threads);
+/* per ray volume: the wave-action density before the last step's saturation, or |N| (n values) */
+int orc_get_action_scale(const orc_model *m, double *out);
 /* grid fields of the last step: which = 0..10 ->
  * Fz_lambda, Fz_phi ([nz+1][ny][nx]), F_ll, F_lp, F_pl, F_pp, E_l, E_p, wave-action density, and the
  * potential-temperature flux integrals T_l, T_p of Eq. fluxes:temperature without theta-bar / (g rho-bar)

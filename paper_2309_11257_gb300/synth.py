@@ -247,22 +247,28 @@ def convective_specs(grid: dict, tag: int, median=16.0, sigma=1.0, cap=512, z_la
 
 
 def uniform_specs(grid: dict, n_az=8, c_list=(5.0, 5.0 * 10 ** (1 / 3), 5.0 * 10 ** (2 / 3), 50.0),
-                  flux=1e-3, z_launch=5e3, dz_launch=1e3, lambda_h=100e3, frac=0.1, lat_max_deg=85.0):
+                  flux=1e-3, z_launch=5e3, dz_launch=1e3, lambda_h=100e3, frac=0.1, lat_max_deg=85.0,
+                  azimuths="half_bin"):
     """Explicit spectral launches, the same in every column: n_az azimuths (even) times the phase
     speeds in c_list, each ray carrying flux / (n_az len(c_list)).
 
-    The azimuths are +-(a + 1/2) 2 pi / n_az, a = 0 .. n_az/2 - 1: mirror pairs (theta, -theta) are
-    exact (l = |k_h| sin(theta) flips sign with no rounding difference), so a background without
+    azimuths="half_bin": +-(a + 1/2) 2 pi / n_az, a = 0 .. n_az/2 - 1: mirror pairs (theta, -theta)
+    are exact (l = |k_h| sin(theta) flips sign with no rounding difference), so a background without
     meridional structure sees no net meridional flux; and no azimuth lies on an axis, where a
     wavenumber component would be rounding noise (cos(pi/2) is not 0 in floating point).
+    azimuths="axis": a 2 pi / n_az, a = 0 .. n_az - 1, the azimuths of the background source (four of
+    them on the axes).
     """
     nx, ny = grid["nx"], grid["ny"]
     _, phi, _ = node_coords(grid)
     rows = np.nonzero(np.abs(np.degrees(phi)) <= lat_max_deg)[0] if grid["geometry"] == 1 else np.arange(ny)
     per = n_az * len(c_list)
     ncol = len(rows) * nx
-    half = (np.arange(n_az // 2) + 0.5) * (2.0 * math.pi / n_az)
-    theta = np.concatenate([half, -half])
+    if azimuths == "axis":
+        theta = np.arange(n_az) * (2.0 * math.pi / n_az)
+    else:
+        half = (np.arange(n_az // 2) + 0.5) * (2.0 * math.pi / n_az)
+        theta = np.concatenate([half, -half])
     out = np.zeros(ncol * per, dtype=SPEC_DTYPE)
     out["j"] = np.repeat(rows, nx * per)
     out["i"] = np.tile(np.repeat(np.arange(nx), per), len(rows))

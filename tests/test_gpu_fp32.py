@@ -1,7 +1,9 @@
 """Precision form (FP32 kinematics, cell index + FP32 offset positions, FP64 accumulation) against
 the FP64 CPU oracle.  The errors are stated, not hidden: every output's error is printed, and the
 test holds them to the bounds the form is built for:
-  * ray state (rays present on both sides): normwise relative error <= 2e-5 per component;
+  * ray state (rays present on both sides): normwise relative error <= 2e-5 per component, and
+    per ray against each ray's own scale (as in the FP64 parity tests) <= 1e-4 (measured: at most
+    2.7e-5, N after strong saturation on the f-plane, 1.5e-6 otherwise);
   * projected centre fields: |gpu - oracle| <= 1e-4 * S elementwise, S the oracle's sum of
     contribution magnitudes (as in the FP64 parity tests);
   * vertical fluxes and drag: |gpu - oracle| <= 1e-4 * S_col, S_col the largest S of the column.
@@ -25,6 +27,7 @@ from parity_util import scaled_error, state_errors
 pytestmark = pytest.mark.gpu
 
 STATE_TOL = 2e-5
+STATE_TOL_PER_RAY = 1e-4
 FIELD_TOL = 1e-4
 
 
@@ -64,7 +67,10 @@ def _report_and_check(T, O, grid, du, dv, odu, odv, label):
     g, o = T.rays(), O.rays()
     common, ig, io = np.intersect1d(g["id"], o["id"], return_indices=True)
     assert len(common) >= 0.995 * len(o["id"])
-    errs = state_errors({n: g[n][ig] for n in oracle.STATE_NAMES}, {n: o[n][io] for n in oracle.STATE_NAMES}, grid)
+    gsel = {n: g[n][ig] for n in oracle.STATE_NAMES}
+    osel = {n: o[n][io] for n in oracle.STATE_NAMES + ("n_scale",)}
+    errs = state_errors(gsel, osel, grid, mode="normwise")
+    errs_ray = state_errors(gsel, osel, grid, mode="per_ray")
     su, sv = O.tendency_scale()
     col = lambda S: np.broadcast_to(S.max(axis=0, keepdims=True), S.shape)
     e_du, e_dv = scaled_error(du, odu, col(su)), scaled_error(dv, odv, col(sv))
@@ -79,11 +85,13 @@ def _report_and_check(T, O, grid, du, dv, odu, odv, label):
     gs, os_ = T.stats(), O.stats()
     print("\n[%s] precision form vs FP64 oracle" % label)
     print("  ray state normwise:", {k: "%.1e" % v for k, v in errs.items()})
+    print("  ray state per ray:", {k: "%.1e" % v for k, v in errs_ray.items()})
     print("  du/dt column-scaled %.2e (rel L2 %.2e), dv/dt column-scaled %.2e" % (e_du, l2, e_dv))
     print("  fields scaled:", {k: "%.1e" % v for k, v in field_errs.items()})
     print("  counts gpu/oracle:", {k: (gs[k], os_[k]) for k in ("n_live", "n_split_v", "n_split_h", "n_exited",
                                                                 "n_capped")})
     assert max(errs.values()) <= STATE_TOL, errs
+    assert max(errs_ray.values()) <= STATE_TOL_PER_RAY, errs_ray
     assert e_du <= FIELD_TOL and e_dv <= FIELD_TOL
     assert max(field_errs.values()) <= FIELD_TOL, field_errs
     for k in ("n_live", "n_launched", "n_filtered", "n_split_v", "n_split_h", "n_exited", "n_capped"):

@@ -12,8 +12,8 @@ import pytest
 
 import oracle
 from paper_2309_11257_gb300 import synth
-from parity_util import (RTOL, assert_fields_match, assert_rays_match, assert_stats_match, level_error,
-                         state_errors)
+from parity_util import (RTOL, assert_fields_match, assert_level_errors, assert_rays_match, assert_stats_match,
+                         level_error, state_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -47,13 +47,18 @@ def _step_both(T, O, dt, nz, ny, nx):
     return du.cpu().numpy(), dv.cpu().numpy(), odu, odv
 
 
-def _compare_all(T, O, grid, du=None, dv=None, odu=None, odv=None, fields=True):
+def _compare_all(T, O, grid, du=None, dv=None, odu=None, odv=None, fields=True, report=None):
     errs = assert_rays_match(T.rays(), O.rays(), grid)
     assert_stats_match(T.stats(), O.stats())
     if du is not None:
         su, sv = O.tendency_scale()
-        assert_fields_match(du, odu, su, name="dudt")
-        assert_fields_match(dv, odv, sv, name="dvdt")
+        eu = assert_fields_match(du, odu, su, name="dudt")
+        ev = assert_fields_match(dv, odv, sv, name="dvdt")
+        # beside the elementwise bar: the plain per-level relative drag error
+        lu = assert_level_errors(du, odu, su, name="dudt")
+        lv = assert_level_errors(dv, odv, sv, name="dvdt")
+        if report is not None:
+            report.append(dict(state=errs, dudt_scaled=eu, dvdt_scaled=ev, dudt_level=lu, dvdt_level=lv))
     if fields:
         for name in oracle.FIELD_NAMES:
             assert_fields_match(T.field(name), O.field(name), O.field_abs(name), name=name)
@@ -65,14 +70,18 @@ def test_fplane_workload_parity(gw):
     w = synth.workload("fplane")
     grid, params = w["grid"], w["params"]
     rays = synth.fplane_rays(grid, 1000, tag=11)
+    # and ray volumes just below the top (32 km), so that some leave the domain (exit path)
+    top = synth.fplane_rays(grid, 100, tag=13, z_lo=29.5e3, z_hi=31.5e3)
     T, O = _pair(gw, grid, params, w["background"], 8192)
-    T.add_rays(rays)
-    O.add_rays(rays)
+    for r in (rays, top):
+        T.add_rays(r)
+        O.add_rays(r)
     _compare_all(T, O, grid, fields=False)
     for s in range(20):
         du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
         if s % 5 == 4:
             _compare_all(T, O, grid, du, dv, odu, odv)
+    assert O.stats()["n_exited"] > 0
 
 
 @pytest.mark.parametrize("variant", ["direct", "pseudomomentum_gamma0"])
@@ -240,6 +249,29 @@ def test_full_size_sphere_launch_and_step(gw):
     _compare_all(T, O, grid, fields=False)
     du, dv, odu, odv = _step_both(T, O, w["dt"], grid["nz"], grid["ny"], grid["nx"])
     _compare_all(T, O, grid, du, dv, odu, odv)
+
+
+def test_sphere_200_steps_compared_every_25(gw):
+    """The benchmark's physics over its whole 200-step run (saturation aloft, splits at altitude,
+    exits through the top) on a 64 x 32 x 90 sphere: the same jets, background source (61 440 ray
+    volumes) and dt of 180 s, compared in full every 25 steps (ids, cells, counters, ray state per
+    ray, tendencies elementwise and per level, every projected field)."""
+    w = synth.workload("sphere")
+    grid = synth.sphere_grid(nx=64, ny=32, nz=90, dz=1000.0)
+    T, O = _pair(gw, grid, w["params"], synth.jet_background(grid), 400_000)
+    T.launch_sources(w["source"])
+    O.launch_background(w["source"])
+    report = []
+    for s in range(200):
+        du, dv, odu, odv = _step_both(T, O, w["dt"], grid["nz"], grid["ny"], grid["nx"])
+        if s % 25 == 24:
+            _compare_all(T, O, grid, du, dv, odu, odv, report=report)
+    for q, r in enumerate(report):
+        print("step %d: state %s; dudt %.2e dvdt %.2e of S; per-level %s %s" % (
+            25 * (q + 1), {k: "%.1e" % v for k, v in r["state"].items()}, r["dudt_scaled"], r["dvdt_scaled"],
+            r["dudt_level"], r["dvdt_level"]))
+    st = O.stats()
+    assert st["n_exited"] > 0 and st["n_split_v"] + st["n_split_h"] > 0 and st["w_saturated"] > 0
 
 
 def test_full_size_sampled_rays_over_several_steps(gw):

@@ -37,8 +37,7 @@ MUTATIONS = {
                            "out[0] = (d->w2 * ch[0] * kk - f2 * ch[1] * ll) / den * A;"),
     "elastic_sign": ("out[4] = -f2 * n2 * ch[2] / den * kk * A;", "out[4] = f2 * n2 * ch[2] / den * kk * A;"),
     "vertical_overlap": ("double w = w_h * ov / dz;", "double w = w_h * ov / s[SEZ];"),
-    "volume_share": ("double alpha = physical_volume(m, s) / cell_volume(m, j, k);\n        size_t c",
-                     "double alpha = 1.0;\n        size_t c"),
+    "volume_share": ("rp->alpha = physical_volume(m, s) / cell_volume(m, rp->j, rp->k);", "rp->alpha = 1.0;"),
     "divergence_cos": ("double dp_u = (cn * pl_n - cs * pl_s) / (2.0 * dY);",
                        "double dp_u = (pl_n - pl_s) / (2.0 * dY);"),
     # bookkeeping
@@ -53,6 +52,21 @@ MUTATIONS = {
                              "        F[5] = -G[2] + k * cg[0] / r;\n    } else if (is_sphere(m)) {"),
     "columnar_horizontal_divergence": ("                    div_u = (fz_top_l - fz_bot_l) / dz;\n",
                                        "                    div_u = div_u;\n"),
+    # smoothing (App. B.4 reading), edge gradients and values (App. B.1 reading), cap ties, exits
+    "smooth_box_weights": ("double w = (di == 0 ? 2.0 : 1.0) * (dj == 0 ? 2.0 : 1.0);", "double w = 16.0 / 9.0;"),
+    "smooth_x_only": ("double w = (di == 0 ? 2.0 : 1.0) * (dj == 0 ? 2.0 : 1.0);",
+                      "double w = (di == 0 ? 2.0 : 1.0) * (dj == 0 ? 4.0 : 0.0);"),
+    "smooth_pole_mirror": ("if (is_sphere(m)) jj = clampl(jj, 0, ny - 1);",
+                           "if (is_sphere(m)) jj = jj < 0 ? 1 : (jj > ny - 1 ? ny - 2 : jj);"),
+    "pole_gradient_halved": ("m->grad[f][1][c] = (A[node(m, k, 1, i)] - A[node(m, k, 0, i)]) / dY;",
+                             "m->grad[f][1][c] = (A[node(m, k, 1, i)] - A[node(m, k, 0, i)]) / (2.0 * dY);"),
+    "top_gradient_halved": ("m->grad[f][2][c] = (A[node(m, nz - 1, j, i)] - A[node(m, nz - 2, j, i)]) / dz;",
+                            "m->grad[f][2][c] = (A[node(m, nz - 1, j, i)] - A[node(m, nz - 2, j, i)]) / (2.0 * dz);"),
+    "edge_value_extrapolated": ("*q0 = n - 2; *q1 = n - 1; *t = 1.0;",
+                                "*q0 = n - 2; *q1 = n - 1; *t = s - (double)(n - 2);"),
+    "cap_tie_smaller_id_removed": ("if (x->id != y->id) return x->id > y->id ? -1 : 1;",
+                                   "if (x->id != y->id) return x->id < y->id ? -1 : 1;"),
+    "exit_at_the_pole": ("double phimax = 0.5 * M_PI - 0.5 * cell_y(m);", "double phimax = 0.5 * M_PI;"),
     # ghost-layer launch
     "ghost_pz_unscaled": ("e[SPZ] = s[SPZ] * e[SEZ] / y[SEZ];", "e[SPZ] = s[SPZ];"),
     "ghost_propagates_in_3d": ("rk3_mode(m, y, dt, 1);", "rk3_mode(m, y, dt, m->P.columnar);"),
