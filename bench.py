@@ -9,6 +9,10 @@ speeds per column (983 040 ray volumes), dt = 180 s, FP64.  Synthetic inputs, se
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+The workload runs 200 steps; after the launch, 100 untimed lead-in steps (--lead-in) put the W
+warm-up and K timed steps into the run's steady part (waves aloft, saturation, exits through the
+top); the line also reports the whole 200-step run's rate (config.run) and the live ray counts.
+
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs its own replica of the
 workload on its own GPU (the replicas exchange nothing); value = all ranks' ray-volume steps
 divided by the slowest rank's time.  --impl reference times the FP64 CPU oracle instead.
@@ -43,6 +47,16 @@ FLOPS_PER_RAY_STEP = 1460.0
 FP64_EQ_PEAK_TOPS = 152 * 128 * 2.07e9 / 9.0 / 1e12 + 152 * 2 * 2.07e9 / 1e12
 # Precision form: algorithmic bytes of the ray step = the 64-byte ray record read and written once.
 BYTES_PER_RAY_STEP_FP32 = 128.0
+# FP64 form, HBM view of the ray step: the 112-byte ray state read and written once (224 B) plus the
+# background it gathers, <= 4 fields x 8 B per touched cell (about 96 B per ray volume at ~1 M rays).
+BYTES_PER_RAY_STEP_FP64 = 224.0 + 96.0
+# Whole step, algorithmic bytes: the ray state (224 B per ray volume, 128 B in the precision form) and,
+# per grid cell, the background read (4 x 8 B), the two saturation sums written and read (32 B), the
+# 8 flux fields and the wave-action diagnostic written once and read once by the stencils (144 B) and
+# the two tendencies written (16 B): 224 B per cell.
+BYTES_PER_CELL_STEP = 224.0
+# Representative window: the workloads run 200 steps; the timed steps follow an untimed lead-in.
+RUN_STEPS = 200
 HBM_PEAK = None
 # DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 39.8 MB, k_advance32:
 # 20.8 MB, each for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
@@ -115,13 +129,37 @@ class ClockSampler:
 
 # ------------------------------------------------------------------------------------- oracle arm
 
-def oracle_throughput(steps: int, warmup: int, workload: str = "sphere"):
+def host_cpu():
+    """Host core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for ln in open("/proc/cpuinfo"):
+                if ln.lower().startswith(("model name", "cpu part")):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def oracle_throughput(steps: int, warmup: int, workload: str = "sphere", threads: int = 0):
     """FP64 CPU oracle on the same workload: launch (untimed), `warmup` untimed steps, then
-    `steps` timed steps; returns ray-volume steps/s and the timed sample."""
+    `steps` timed steps, its per-ray loops on `threads` host threads (0: all cores); returns
+    ray-volume steps/s, the timed sample and the threads used."""
     import oracle
     from paper_2309_11257_gb300 import synth
     w = synth.workload(workload)
     M = oracle.Model(w["grid"], w["params"])
+    used = M.set_threads(threads or (os.cpu_count() or 1))
     M.set_background(*w["background"])
     M.launch_background(w["source"])
     for _ in range(warmup):
@@ -132,23 +170,27 @@ def oracle_throughput(steps: int, warmup: int, workload: str = "sphere"):
         ray_steps += M.n_rays
         M.step(w["dt"])
     dt = time.perf_counter() - t0
-    return ray_steps / dt, dict(steps=steps, warmup=warmup, ray_steps=ray_steps, seconds=dt)
+    return ray_steps / dt, dict(steps=steps, warmup=warmup, ray_steps=ray_steps, seconds=dt, threads=used)
 
 
 def reference_arm(args, rank, world):
+    """The FP64 CPU oracle on the GPU arm's workload: the launch, W untimed steps, then exactly K
+    timed steps of the whole workload, the oracle's per-ray loops on all host cores."""
     if rank != 0:
         return 0
-    steps = max(1, min(args.steps, 4))
-    warm = min(args.warmup, 1)
+    steps = max(1, args.steps)
+    warm = max(0, args.warmup)
     value, sample = oracle_throughput(steps, warm)
+    ncpu, cpu_model = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sample["seconds"] / steps,
+        "steps": steps, "warmup": warm, "ms_per_step": 1000.0 * sample["seconds"] / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d timed oracle steps (after %d untimed) of the full workload, single thread"
-                                   % (steps, warm)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["threads"], "kind": "oracle",
+                         "cpu_model": cpu_model, "host_cores": ncpu,
+                         "sample": "%d timed oracle steps (after the launch and %d untimed) of the full workload, "
+                                   "%d threads" % (steps, warm, sample["threads"])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -189,9 +231,12 @@ def gpu_arm(args, rank, world, local_rank):
         params["precision"] = 1
     nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
     ghost = w.get("ghost", False)
-    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
+    e2e_steps = 0 if args.no_e2e else max(10, args.e2e_steps)
+    # untimed lead-in so that the timed window lies in the steady part of the 200-step run (the ghost
+    # workload starts from no rays and grows every step: no lead-in)
+    lead_in = 0 if ghost else (RUN_STEPS // 2 if args.lead_in < 0 else args.lead_in)
     # ghost-layer emission adds up to one ray volume per bin and step
-    cap_rays = 32 * nx * ny * (args.warmup + args.steps + e2e_steps + 2) if ghost else 2.5 * 32 * nx * ny
+    cap_rays = 32 * nx * ny * (args.warmup + args.steps + e2e_steps + 5) if ghost else 2.5 * 32 * nx * ny
     T = gwam.Tracer(grid, params, max_rays=int(cap_rays))
     bg_dev = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in w["background"]]
     T.set_background(*bg_dev)
@@ -221,8 +266,16 @@ def gpu_arm(args, rank, world, local_rank):
             bg_dev[1].add_(dv, alpha=w["dt"])
             T.set_background(*bg_dev)
 
-    for _ in range(args.warmup):
+    # lead-in and warm-up, timed separately for the whole-run figure (not the reported value)
+    run_ms = 0.0
+    run_rs0 = T.stats()["ray_steps"]
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(torch.cuda.current_stream())
+    for _ in range(lead_in + args.warmup):
         one_step()
+    eb.record(torch.cuda.current_stream())
+    eb.synchronize()
+    run_ms += ea.elapsed_time(eb)
     if not use_graph:
         T.profile(True)
     s0 = T.stats()
@@ -246,6 +299,7 @@ def gpu_arm(args, rank, world, local_rank):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     s1 = T.stats()
+    run_ms += ms
     if use_graph:
         phases, ngraphs = T.graph_profile_read()   # already averaged over the graphs' last replays
         assert ngraphs > 0
@@ -260,9 +314,38 @@ def gpu_arm(args, rank, world, local_rank):
         rays_per_launch = s1["n_live"]
     ms_max, tot_rs, _ = whole_job(ms, ray_steps, 0.0, dev, world)
     value = tot_rs / (ms_max / 1000.0)
+    step_window = [lead_in + args.warmup + 1, lead_in + args.warmup + args.steps]
+
+    # the rest of the 200-step run (not part of the value): whole-run ray-volume steps/s
+    rest = RUN_STEPS - (lead_in + args.warmup + args.steps) if not ghost else 0
+    if rest > 0:
+        ea.record(torch.cuda.current_stream())
+        for _ in range(rest):
+            one_step()
+        eb.record(torch.cuda.current_stream())
+        eb.synchronize()
+        run_ms += ea.elapsed_time(eb)
+    s_run = T.stats()
+    whole_run = None
+    if not ghost:
+        whole_run = {"steps": s_run["n_steps"], "value": (s_run["ray_steps"] - run_rs0) / (run_ms / 1000.0),
+                     "unit": UNIT, "rays_live_end": s_run["n_live"],
+                     "note": "every step of the run after the launch (first graph captures included), "
+                             "CUDA events; not the reported value"}
 
     # roofline of the dominant kernel (its launches in the profiled eager steps)
     adv_ms = phases["advance"] / max(nprof, 1)
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    ncell = nx * ny * nz
+    ray_bytes = BYTES_PER_RAY_STEP_FP32 if fp32 else BYTES_PER_RAY_STEP_FP64
+    step_bytes = (BYTES_PER_RAY_STEP_FP32 if fp32 else 224.0) * rays_per_launch + BYTES_PER_CELL_STEP * ncell
+    step_ms = ms_max / args.steps
+    hbm_view = {"peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel_bytes_per_ray_step": ray_bytes,
+                "kernel_gbs": ray_bytes * rays_per_launch / (adv_ms / 1000.0) / 1e9,
+                "kernel_frac": ray_bytes * rays_per_launch / (adv_ms / 1000.0) / 1e9 / hbm_peak,
+                "step_bytes": step_bytes, "step_gbs": step_bytes / (step_ms / 1000.0) / 1e9,
+                "step_frac": step_bytes / (step_ms / 1000.0) / 1e9 / hbm_peak}
     if fp32:
         # precision form: the ray step reads and writes the 64-byte record
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
@@ -272,6 +355,7 @@ def gpu_arm(args, rank, world, local_rank):
                     "traffic": ADV32_TRAFFIC_BYTES_PER_RAY * rays_per_launch,
                     "traffic_source": "ncu dram bytes of k_advance32 on the 128x64 sphere, scaled by rays",
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                    "hbm": hbm_view,
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
     else:
         achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
@@ -279,9 +363,11 @@ def gpu_arm(args, rank, world, local_rank):
                     "peak": FP64_EQ_PEAK_TOPS, "unit": "TFLOP/s", "frac": achieved / FP64_EQ_PEAK_TOPS,
                     "traffic": ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch if ADV_TRAFFIC_BYTES_PER_RAY else None,
                     "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere, scaled by rays",
-                    "peak_source": "derived from unit counts and the 2.07 GHz clock: FP64-precision operations "
-                                   "as double-float on the FP32 pipes (4.48 T/s) plus the FP64 pipe (0.63 T/s)",
+                    "peak_source": "modelled (not measured) from unit counts and the 2.07 GHz clock: "
+                                   "FP64-precision operations as double-float on the FP32 pipes (4.48 T/s) plus "
+                                   "the FP64 pipe (0.63 T/s)",
                     "flops_per_ray_step": FLOPS_PER_RAY_STEP,
+                    "hbm": hbm_view,
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
 
     # end to end through the public API with host buffers: each step uploads that step's
@@ -320,17 +406,25 @@ def gpu_arm(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cval, sample = oracle_throughput(2, 0, "sphere_columnar" if args.workload == "sphere_columnar" else "sphere")
-        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "2 oracle steps right after the launch of the full workload (%d ray-volume steps, "
-                         "%.1f s), single thread" % (sample["ray_steps"], sample["seconds"])}
+        ncpu, cpu_model = host_cpu()
+        cval, sample = oracle_throughput(args.cpu_steps, 0,
+                                         "sphere_columnar" if args.workload == "sphere_columnar" else "sphere")
+        cpu = {"value": cval, "unit": UNIT, "cores": sample["threads"], "kind": "oracle", "cpu_model": cpu_model,
+               "host_cores": ncpu,
+               "sample": "%d oracle steps right after the launch of the full sphere workload (%d ray-volume steps, "
+                         "%.1f s), per-ray loops on %d threads" % (sample["steps"], sample["ray_steps"],
+                                                                   sample["seconds"], sample["threads"])}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc" if fp32 else "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32 kinematics, f64 accumulation" if fp32
+                      else "f64 state, sums and outputs; double-float (~48-bit) arithmetic on the FP32 pipes"),
+            "data": "synthetic",
             "config": {"workload": WORKLOAD if args.workload == "sphere" else args.workload, "rays_live_start": s0["n_live"], "rays_live_end": s1["n_live"],
-                       "ray_steps_timed": ray_steps,
+                       "ray_steps_timed": ray_steps, "timed_steps_of_run": step_window, "lead_in_steps": lead_in,
+                       "run": whole_run,
                        "step_call": "gwam_step_graph (one CUDA graph launch per step)" if use_graph else "gwam_step",
                        "l2": "working set > L2 (ray state ~0.12-0.24 GB + "
                        "grid fields ~0.4 GB per step), no flush", "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -558,6 +652,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--eager", action="store_true", help="time gwam_step calls instead of graph replays")
+    ap.add_argument("--lead-in", type=int, default=-1,
+                    help="untimed steps after the launch before the warm-up (default: half of the 200-step run)")
+    ap.add_argument("--e2e-steps", type=int, default=50, help="steps of the end-to-end measurement")
+    ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps of the CPU baseline sample")
     ap.add_argument("--train-steps", type=int, default=800,
                     help="surrogate workload: training steps (0: untrained weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
