@@ -102,6 +102,22 @@ def _declare(lib):
     lib.orc_get_action_scale.argtypes = [C.c_void_p, _D]
     lib.orc_set_threads.restype = C.c_int
     lib.orc_set_threads.argtypes = [C.c_void_p, C.c_int]
+    lib.orc_step_advance.argtypes = [C.c_void_p, C.c_double]
+    lib.orc_step_local.argtypes = [C.c_void_p, C.c_double]
+    lib.orc_step_grid.argtypes = [C.c_void_p, _D, _D]
+    lib.orc_set_owned_rows.argtypes = [C.c_void_p, C.c_long, C.c_long]
+    lib.orc_get_next_id.restype = C.c_int64
+    lib.orc_get_next_id.argtypes = [C.c_void_p]
+    lib.orc_set_next_id.argtypes = [C.c_void_p, C.c_int64]
+    lib.orc_remap_ids.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int64]
+    lib.orc_issued_before.restype = C.c_int64
+    lib.orc_issued_before.argtypes = [C.c_void_p, C.c_int64]
+    lib.orc_count_rays_outside.restype = C.c_int64
+    lib.orc_count_rays_outside.argtypes = [C.c_void_p]
+    lib.orc_take_rays_outside.restype = C.c_int64
+    lib.orc_take_rays_outside.argtypes = [C.c_void_p, _D, _P(C.c_int64), _P(C.c_int32), C.c_int64]
+    lib.orc_put_rays.argtypes = [C.c_void_p, C.c_int64, _D, _P(C.c_int64)]
+    lib.orc_set_field.argtypes = [C.c_void_p, C.c_int, _D]
     lib.orc_get_field.argtypes = [C.c_void_p, C.c_int, _D]
     lib.orc_get_gamma2.argtypes = [C.c_void_p, _D]
     lib.orc_get_field_abs.argtypes = [C.c_void_p, C.c_int, _D]
@@ -200,6 +216,65 @@ class Model:
         """Threads for the independent per-ray loops (results identical for any count); returns
         the count in effect."""
         return int(self._lib.orc_set_threads(self._h, int(n)))
+
+    # -- the phases of a step and the latitude-band hooks of a domain-decomposed run (App. B.2)
+    def step_advance(self, dt: float):
+        if self._lib.orc_step_advance(self._h, float(dt)) != 0:
+            raise ValueError("step failed")
+
+    def step_local(self, dt: float):
+        self._lib.orc_step_local(self._h, float(dt))
+
+    def step_grid(self):
+        shape = (self.nz, self.ny, self.nx)
+        du, dv = np.zeros(shape), np.zeros(shape)
+        self._lib.orc_step_grid(self._h, _dp(du), _dp(dv))
+        return du, dv
+
+    def set_owned_rows(self, j0: int, j1: int):
+        if self._lib.orc_set_owned_rows(self._h, int(j0), int(j1)) != 0:
+            raise ValueError("bad band")
+
+    @property
+    def next_id(self) -> int:
+        return int(self._lib.orc_get_next_id(self._h))
+
+    @next_id.setter
+    def next_id(self, v: int):
+        self._lib.orc_set_next_id(self._h, int(v))
+
+    def remap_ids(self, lo: int, hi: int, to: int):
+        """ids in [lo, hi) become id - lo + to"""
+        self._lib.orc_remap_ids(self._h, int(lo), int(hi), int(to))
+
+    def issued_before(self, q: int) -> int:
+        """new ids issued by the rays before array position q in the last advance"""
+        return int(self._lib.orc_issued_before(self._h, int(q)))
+
+    def take_rays_outside(self):
+        """Ray volumes whose carrier row left the owned band, removed: (states [n, 13], ids [n],
+        carrier rows [n])."""
+        n = int(self._lib.orc_count_rays_outside(self._h))
+        st = np.zeros((n, NSTATE))
+        ids = np.zeros(n, dtype=np.int64)
+        rows = np.zeros(n, dtype=np.int32)
+        if n:
+            got = self._lib.orc_take_rays_outside(self._h, _dp(st), ids.ctypes.data_as(_P(C.c_int64)),
+                                                  rows.ctypes.data_as(_P(C.c_int32)), n)
+            assert got == n
+        return st, ids, rows
+
+    def put_rays(self, states, ids):
+        st = np.ascontiguousarray(states, dtype=np.float64).reshape(-1, NSTATE)
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        if len(ids):
+            self._lib.orc_put_rays(self._h, len(ids), _dp(st), ids.ctypes.data_as(_P(C.c_int64)))
+
+    def set_field(self, name: str, values):
+        which = ALL_FIELD_NAMES.index(name)
+        a = _f64(values)
+        if self._lib.orc_set_field(self._h, which, _dp(a)) != 0:
+            raise ValueError(name)
 
     def set_background(self, u, v, n2, rho):
         arrs = [_f64(a).reshape(self.nz, self.ny, self.nx) for a in (u, v, n2, rho)]

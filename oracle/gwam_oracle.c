@@ -75,6 +75,10 @@ struct orc_model {
     int n_scale_current;                 /* n_scale belongs to the current ray array (the last step's
                                             saturation; cleared when rays are added or reordered) */
     int threads;                         /* threads for the per-ray loops (<= 1: serial) */
+    long row0, row1;                     /* rows [row0, row1) this model launches into (default all);
+                                            a latitude band of a domain-decomposed run */
+    int64_t *issued;                     /* issued[q]: new ids issued by rays 0..q-1 of the last advance */
+    int64_t issued_n;
 };
 
 #ifdef _OPENMP
@@ -422,6 +426,8 @@ orc_model *orc_create(const orc_grid *grid, const orc_params *params)
     orc_model *m = (orc_model *)calloc(1, sizeof(orc_model));
     m->G = *grid;
     m->P = *params;
+    m->row0 = 0;
+    m->row1 = grid->ny;
     size_t nc = (size_t)grid->nx * grid->ny * grid->nz;
     size_t ni = (size_t)grid->nx * grid->ny * (grid->nz + 1);
     m->u = calloc(nc, sizeof(double));
@@ -458,6 +464,7 @@ void orc_destroy(orc_model *m)
     free_fields(m);
     free_rays(m);
     free(m->n_scale);
+    free(m->issued);
     free(m->theta);
     free(m);
 }
@@ -706,7 +713,7 @@ static int launch_background_dt(orc_model *m, const orc_bg_source *src, double d
     if (!is_sphere(m) || !m->have_bg) return -1;
     if (src->n_az < 1 || src->n_c < 1) return -1;
     int nbins = src->n_az * src->n_c;
-    for (long j = 0; j < m->G.ny; ++j) {
+    for (long j = m->row0; j < m->row1; ++j) {
         double pdeg = row_lat(m, j) * 180.0 / M_PI;
         if (fabs(pdeg) > src->phi_max_deg) continue;      /* no launch poleward of 85 deg */
         double fbin = orc_fam(pdeg, src->tau, src->f_s, src->f_w) / nbins;
@@ -746,6 +753,7 @@ static int launch_spectral_dt(orc_model *m, int64_t n, const orc_spec *sp, doubl
     for (int64_t q = 0; q < n; ++q)
         if (sp[q].i < 0 || sp[q].i >= m->G.nx || sp[q].j < 0 || sp[q].j >= m->G.ny) return -1;
     for (int64_t q = 0; q < n; ++q) {
+        if (sp[q].j < m->row0 || sp[q].j >= m->row1) continue;     /* another band's column */
         if (dt > 0.0)
             ghost_one(m, sp[q].i, sp[q].j, sp[q].z_launch, sp[q].dz_launch, sp[q].theta, sp[q].c,
                       sp[q].lambda_h, sp[q].flux, sp[q].spectral_frac, dt);
@@ -1458,7 +1466,9 @@ int orc_get_field(const orc_model *m, int which, double *out)
 
 /* ------------------------------------------------------------------ the step */
 
-int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
+/* Phase 1 of a step: advance every ray volume (RK3), remove those that left, split the rest;
+ * the array is left in array order (not sorted). */
+int orc_step_advance(orc_model *m, double dt)
 {
     if (!(dt > 0.0) || !isfinite(dt) || !m->have_bg) return -1;
     int64_t n = m->n;
@@ -1475,8 +1485,13 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
         load_ray(m, q, sq);
         orc_advance_ray(m, sq, dt);
     }
+    free(m->issued);
+    m->issued = malloc(sizeof(int64_t) * (size_t)(n + 1));
+    m->issued_n = n;
+    const int64_t id0 = m->next_id;
     for (int64_t q = 0; q < n; ++q) {
         double s[NSTATE];
+        m->issued[q] = m->next_id - id0;
         memcpy(s, adv + (size_t)q * NSTATE, sizeof(s));
         int st = ray_status(m, s);
         if (st == 2) {
@@ -1503,6 +1518,7 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
             ++nn;
         }
     }
+    m->issued[n] = m->next_id - id0;
     free(adv);
     m->n = 0;
     reserve(m, nn);
@@ -1513,14 +1529,28 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
     memcpy(m->id, nid, sizeof(int64_t) * (size_t)nn);
     free(nid);
     m->n = nn;
+    return 0;
+}
+
+/* Phase 2 of a step: canonical order, per-column cap, saturation and projection -- all local to a
+ * carrier cell or column. */
+int orc_step_local(orc_model *m, double dt)
+{
+    if (!(dt > 0.0) || !isfinite(dt) || !m->have_bg) return -1;
     /* 2. reassign cells, canonical order (App. B.2: rays kept per parent cell) */
     sort_rays(m);
     /* 3. per-column cap */
     apply_cap(m);
     /* 4. saturation with the post-step state */
     if (m->P.saturation) apply_saturation(m, dt);
-    /* 5. projection, smoothing, divergence */
     project(m);
+    return 0;
+}
+
+/* Phase 3 of a step: smoothing and divergence of the projected fields, budget. */
+int orc_step_grid(orc_model *m, double *dudt, double *dvdt)
+{
+    /* 5. smoothing, divergence */
     if (m->P.smoothing) smooth_all(m);
     size_t nc = (size_t)m->G.nx * m->G.ny * m->G.nz;
     double *du = dudt ? dudt : malloc(nc * sizeof(double));
@@ -1539,6 +1569,13 @@ int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
     m->st.n_live = m->n;
     m->st.n_steps++;
     return 0;
+}
+
+int orc_step(orc_model *m, double dt, double *dudt, double *dvdt)
+{
+    if (orc_step_advance(m, dt)) return -1;
+    orc_step_local(m, dt);
+    return orc_step_grid(m, dudt, dvdt);
 }
 
 /* projection (and smoothing) of the current ray volumes without advancing them */
@@ -1578,6 +1615,103 @@ int orc_get_action_scale(const orc_model *m, double *out)
     for (int64_t q = 0; q < m->n; ++q)
         out[q] = (m->n_scale_current && m->n_scale) ? m->n_scale[q] : fabs(m->s[SN][q]);
     return 0;
+}
+
+/* ---------------------------------------------- latitude-band decomposition (App. B.2)
+ * A model may own the rows [j0, j1) of a latitude band: it launches only there, and after the
+ * advance phase the ray volumes whose carrier row left the band are taken out and handed to the
+ * band that owns them.  The grid stays whole; only the band's rows (and the halo rows its stencils
+ * read) carry meaning. */
+int orc_set_owned_rows(orc_model *m, long j0, long j1)
+{
+    if (j0 < 0 || j1 > m->G.ny || j0 >= j1) return -1;
+    m->row0 = j0;
+    m->row1 = j1;
+    return 0;
+}
+
+int64_t orc_get_next_id(const orc_model *m) { return m->next_id; }
+void orc_set_next_id(orc_model *m, int64_t id) { m->next_id = id; }
+
+/* ids in [lo, hi) become id - lo + to (provisional ids of a band turned into global ones) */
+void orc_remap_ids(orc_model *m, int64_t lo, int64_t hi, int64_t to)
+{
+    for (int64_t q = 0; q < m->n; ++q)
+        if (m->id[q] >= lo && m->id[q] < hi) m->id[q] = m->id[q] - lo + to;
+}
+
+/* new ids issued by the rays before array position q (0 <= q <= n) in the last advance */
+int64_t orc_issued_before(const orc_model *m, int64_t q)
+{
+    if (!m->issued || q < 0 || q > m->issued_n) return -1;
+    return m->issued[q];
+}
+
+static long ray_row(const orc_model *m, int64_t q)
+{
+    double s[NSTATE];
+    long i, j, k;
+    load_ray(m, q, s);
+    cell_ijk(m, s, &i, &j, &k);
+    return j;
+}
+
+int64_t orc_count_rays_outside(const orc_model *m)
+{
+    int64_t c = 0;
+    for (int64_t q = 0; q < m->n; ++q) {
+        long j = ray_row(m, q);
+        if (j < m->row0 || j >= m->row1) ++c;
+    }
+    return c;
+}
+
+/* Remove the ray volumes whose carrier row lies outside the owned rows; their states (row-major,
+ * 13 values each), ids and carrier rows go to out_state / out_ids / out_rows in array order (at most
+ * cap of them). */
+int64_t orc_take_rays_outside(orc_model *m, double *out_state, int64_t *out_ids, int32_t *out_rows, int64_t cap)
+{
+    int64_t w = 0, t = 0;
+    for (int64_t q = 0; q < m->n; ++q) {
+        long j = ray_row(m, q);
+        if (j < m->row0 || j >= m->row1) {
+            if (t >= cap) return -1;
+            for (int c = 0; c < NSTATE; ++c) out_state[(size_t)t * NSTATE + c] = m->s[c][q];
+            out_rows[t] = (int32_t)j;
+            out_ids[t++] = m->id[q];
+            continue;
+        }
+        for (int c = 0; c < NSTATE; ++c) m->s[c][w] = m->s[c][q];
+        m->id[w] = m->id[q];
+        m->cell[w] = m->cell[q];
+        ++w;
+    }
+    m->n = w;
+    m->n_scale_current = 0;
+    return t;
+}
+
+/* Append ray volumes handed over from another band (states row-major, ids kept; no tallies). */
+int orc_put_rays(orc_model *m, int64_t n, const double *state, const int64_t *ids)
+{
+    for (int64_t q = 0; q < n; ++q) append_ray(m, state + (size_t)q * NSTATE, ids[q]);
+    m->st.n_live = m->n;
+    return 0;
+}
+
+/* Overwrite a projected field (same numbering as orc_get_field): halo rows from a neighbour band */
+int orc_set_field(orc_model *m, int which, const double *in)
+{
+    size_t nc = (size_t)m->G.nx * m->G.ny * m->G.nz, ni = (size_t)m->G.nx * m->G.ny * (m->G.nz + 1);
+    if (which == 0 || which == 1) {
+        memcpy(m->fz[which], in, ni * sizeof(double));
+        return 0;
+    }
+    if (which >= 2 && which < 2 + NFIELD_H) {
+        memcpy(m->hf[which - 2], in, nc * sizeof(double));
+        return 0;
+    }
+    return -1;
 }
 
 int orc_set_threads(orc_model *m, int threads)

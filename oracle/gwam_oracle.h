@@ -108,6 +108,24 @@ int64_t orc_num_rays(const orc_model *m);
 /* state: 13 arrays of n in the order x y z k l m dX dY dZ Px Py Pz N (array order) */
 int orc_get_rays(const orc_model *m, double *state13, int64_t *ids, int32_t *cells);
 void orc_get_stats(const orc_model *m, orc_stats *out);
+/* the three phases of orc_step, for a domain-decomposed driver: advance (RK3, exits, splits; array
+ * order), local (canonical order, cap, saturation, projection), grid (smoothing, divergence, budget) */
+int orc_step_advance(orc_model *m, double dt);
+int orc_step_local(orc_model *m, double dt);
+int orc_step_grid(orc_model *m, double *dudt, double *dvdt);
+/* latitude band [j0, j1) owned by this model (launches only there); id counter; id remapping; new
+ * ids issued by the rays before an array position in the last advance; ray
+ * volumes whose carrier row left the band (count, take out: row-major states of 13 values + ids);
+ * ray volumes handed over (appended with their ids); projected fields overwritten (halo rows) */
+int orc_set_owned_rows(orc_model *m, long j0, long j1);
+int64_t orc_get_next_id(const orc_model *m);
+void orc_set_next_id(orc_model *m, int64_t id);
+void orc_remap_ids(orc_model *m, int64_t lo, int64_t hi, int64_t to);
+int64_t orc_issued_before(const orc_model *m, int64_t q);
+int64_t orc_count_rays_outside(const orc_model *m);
+int64_t orc_take_rays_outside(orc_model *m, double *out_state, int64_t *out_ids, int32_t *out_rows, int64_t cap);
+int orc_put_rays(orc_model *m, int64_t n, const double *state, const int64_t *ids);
+int orc_set_field(orc_model *m, int which, const double *in);
 /* threads for the independent per-ray loops (results bit-identical for any count; returns the count
  * in effect: 1 when built without OpenMP) */
 int orc_set_threads(orc_model *m, int threads);
