@@ -503,7 +503,8 @@ def surrogate_arm(args):
     """Surrogate inference: one step = one pass over a batch of 32 768 columns (normalisation and
     envelope test, 5 tensor-core GEMMs with fused bias/GELU, de-normalised drag scattered into the
     [nz][ny][nx] outputs).  The drag error is stated from a surrogate trained first on ray-tracer
-    drag (16 members of a 64 x 32 x 90 sphere: 12 for training, 4 held out for the error)."""
+    drag: 1 048 576 columns of 32 members of the 256 x 128 x 90 sphere (26 train, 2 validate the
+    early stopping, 4 held out for the error)."""
     import numpy as np
     import torch
 
@@ -513,22 +514,29 @@ def surrogate_arm(args):
 
     t_start = time.perf_counter()
     S = gwam.Surrogate(max_batch=SUR_BATCH, seed=1)
-    tsteps, tbatch = args.train_steps, 2048
-    te, base, train_cps, hist, info, ntr = None, None, None, [], None, 0
-    if tsteps > 0:
-        X, Y, info = surrogate.generate(members=16, nx=64, ny=32, nz=90, steps=120, avg=40, launch_every=5, tag=1)
-        ncol = info["ncol"]
-        ntr = 12 * ncol
-        S.fit_normalization(X[:ntr], Y[:ntr], margin=0.05)
+    te, base, train_cps, hist, infos, ntr, kept, nval, gen_s = None, None, None, [], None, 0, None, 0, None
+    if args.train_steps > 0:
+        X, Y, infos = surrogate.generate_1m()
+        gen_s = time.perf_counter() - t_start
+        ncol = infos[0]["ncol"]
+        tr, va, tm = surrogate.member_split(4, 8, ncol)
+        Xtr, Ytr = X[tr].contiguous(), Y[tr].contiguous()
+        Xva, Yva = X[va].contiguous(), Y[va].contiguous()
+        X, Y = X[tm].contiguous(), Y[tm].contiguous()          # the held-out members
+        ntr, nval = Xtr.shape[0], Xva.shape[0]
+        S.fit_normalization(Xtr, Ytr, margin=0.05)
+        cfg = dict(surrogate.TRAIN_1M, max_steps=min(args.train_steps, surrogate.TRAIN_1M["max_steps"]))
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        hist = surrogate.train(S, X[:ntr], Y[:ntr], steps=tsteps, batch=tbatch, lr=1e-3)
+        best, kept, hist = surrogate.train_early_stopping(S, Xtr, Ytr, Xva, Yva, 90, **cfg)
         e1.record()
         e1.synchronize()
-        train_cps = tsteps * tbatch / (e0.elapsed_time(e1) / 1000.0)
-        te = surrogate.drag_error(S, X[ntr:], Y[ntr:], 90)
-        ref = Y[ntr:].double()
-        base = float(torch.linalg.norm(ref - Y[:ntr].double().mean(dim=0)) / torch.linalg.norm(ref))
+        steps_run = hist[-1][0] if hist else 0
+        train_cps = steps_run * cfg["batch"] / (e0.elapsed_time(e1) / 1000.0)
+        te = surrogate.drag_error(S, X, Y, 90)
+        ref = Y.double()
+        base = float(torch.linalg.norm(ref - Ytr.double().mean(dim=0)) / torch.linalg.norm(ref))
+        del Xtr, Ytr, Xva, Yva
     else:
         # throughput only (profiling): untrained weights, unit normalisation, synthetic features
         X = torch.randn((SUR_BATCH, 368), device="cuda")
@@ -615,13 +623,18 @@ def surrogate_arm(args):
             "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
             "config": {"workload": "surrogate MLP 368-4x512-180 GELU, batch %d columns" % B,
-                       "drag_rel_l2_heldout": te["rel_l2"] if te else None, "drag_rel_l2_mean_baseline": base,
+                       "data": "1 048 576 columns from the FP64 tracer on 32 members of the 256x128x90 sphere "
+                               "(sphere workload jets + ensemble jet distribution, background and convective "
+                               "sources)" if te else "synthetic features, untrained",
+                       "drag_rel_l2_heldout": te["rel_l2"] if te else None,
+                       "drag_rel_l2_bound": 0.72, "drag_rel_l2_mean_baseline": base,
                        "fallback_heldout": te["n_fallback"] if te else None,
-                       "heldout_columns": int(Y.shape[0] - ntr) if te else 0,
-                       "train_columns": ntr, "train_steps": tsteps, "train_batch": tbatch,
-                       "train_columns_per_s": train_cps, "loss_history": hist,
-                       "tracer_columns_per_s": (X.shape[0] / (info["tracer_ms_per_step"] / 1000.0)) if info else None,
-                       "prep_seconds": prep_s, "fallback_in_batch": int(nfb.item()),
+                       "heldout_columns": int(Y.shape[0]) if te else 0,
+                       "train_columns": ntr, "validation_columns": nval, "kept_step": kept,
+                       "train_columns_per_s": train_cps, "validation_history": hist,
+                       "tracer_columns_per_s": (8 * infos[0]["ncol"] / (infos[0]["tracer_ms_per_step"] / 1000.0))
+                       if infos else None,
+                       "generation_seconds": gen_s, "prep_seconds": prep_s, "fallback_in_batch": int(nfb.item()),
                        "l2": "256 MB buffer written between timed passes"},
             "gpu_launches": args.steps * 6, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks}
@@ -656,8 +669,9 @@ def main():
                     help="untimed steps after the launch before the warm-up (default: half of the 200-step run)")
     ap.add_argument("--e2e-steps", type=int, default=50, help="steps of the end-to-end measurement")
     ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps of the CPU baseline sample")
-    ap.add_argument("--train-steps", type=int, default=800,
-                    help="surrogate workload: training steps (0: untrained weights, throughput only)")
+    ap.add_argument("--train-steps", type=int, default=1500,
+                    help="surrogate workload: at most this many training steps (early stopping; 0: untrained "
+                         "weights, throughput only)")
     ap.add_argument("--workload", default="sphere",
                     choices=["sphere", "sphere_half", "ensemble", "sphere_fp32", "sphere_half_fp32", "surrogate",
                              "sphere_columnar", "sphere_coupled", "sphere_ghost", "sphere_theta"],

@@ -339,6 +339,17 @@ int gwam_selftest_logratio(const double *a, const double *b, int64_t n, double *
 int gwam_gemm_bf16(const void *A, const void *B, int M, int N, int K, const float *bias, int gelu, int bn,
                    int out_bf16, void *C, void *stream);
 
+/* Self-test of the GEMM's bounded device waits (the failure detection of every spin-wait in the
+ * library's kernels; not in the paper): the gwam_gemm_bf16 kernel with tile width bn (as above) is
+ * launched with its TMA producer told to issue no copies and every mbarrier wait limited to
+ * wait_us microseconds (1 .. 2 000 000).  The MMA and epilogue warps wait on stages that never fill,
+ * give up after wait_us, wait (bounded) for the MMAs they issued -- none -- release their tensor
+ * memory and set the error word; the call returns GWAM_ETIMEOUT and the context stays usable (the
+ * next GEMM allocates the same tensor memory).  A, B, C as for gwam_gemm_bf16 (C FP32, not
+ * written).  Synchronises `stream`.  GWAM_EINVAL for bad arguments. */
+int gwam_selftest_gemm_timeout(const void *A, const void *B, int M, int N, int K, int bn, float *C,
+                               unsigned int wait_us, void *stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Column drag surrogate (not in the paper: an emulator of the ray tracer's column drag, with the
  * tracer as fallback).  An MLP n_in -> n_hidden (x n_layers, GELU(z) = z Phi(z)) -> n_out with

@@ -437,72 +437,11 @@ __device__ __forceinline__ void geometry_at(const Grid& G, double Y, double Z, G
     }
 }
 
-// Right-hand side for y = (X, Y, Z, k, l, m, eX, eY, eZ): the carrier moves with the mean of the
-// opposing face group velocities, the extents with their difference (Sec. 3b, App. B.1); the
-// wavenumber follows Eq. eikonal-sphere:1-3 (sphere) or kdot = -grad Omega (f-plane) with the
-// centre values.
-__device__ __forceinline__ void ray_rhs(const Grid& G, const NodeDF* __restrict__ bg, const double y[9], double F[9])
-{
-    const double k = y[3], l = y[4], m = y[5];
-    Bg b;
-    gather(G, bg, y[0], y[1], y[2], b);
-    Geo g;
-    geometry_at(G, y[1], y[2], g);
-    double f2, df2;
-    coriolis(G, g.sphi, g.cphi, f2, df2);
-    const double U = b.v[0], V = b.v[1], N2 = b.v[2], G2 = b.v[3];
-    const double kh2 = k * k + l * l, m2 = m * m;
-    const double mg2 = m2 + G2;
-    Disp d;
-    dispersion(kh2, mg2, N2, f2, d);
-    const double cgx = k * mg2 * d.c + U;
-    const double cgy = l * mg2 * d.c + V;
-    const double cgz = -m * kh2 * d.c;
-    // d Omega / d q at fixed wavevector
-    const double hwK = 0.5 * d.iw * d.iK2;           // 1 / (2 w K^2)
-    const double aN = kh2 * hwK;
-    const double aG = aN * d.D * d.iK2;
-    const double aF = mg2 * hwK;
-    double Gq[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) Gq[q] = k * b.d[0][q] + l * b.d[1][q] + aN * b.d[2][q] - aG * b.d[3][q];
-    Gq[1] += aF * df2;
-    if (G.geometry == 1) {
-        const double ir = g.ir;
-        F[3] = -Gq[0] * g.ihX + k * ir * (g.tphi * cgy - cgz);
-        F[4] = -Gq[1] * ir - ir * (l * cgz + k * g.tphi * cgx);
-        F[5] = -Gq[2] + ir * (k * cgx + l * cgy);
-    } else {
-        F[3] = -Gq[0];
-        F[4] = -Gq[1];
-        F[5] = -Gq[2];
-    }
-    // faces: first-order Taylor values along the face's own axis
-    const double ihX = g.ihX, ihY = g.ir;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        double vel[2];
-#pragma unroll
-        for (int sd = 0; sd < 2; ++sd) {
-            const double h = (sd == 0 ? 0.5 : -0.5) * y[6 + q];
-            const double N2f = N2 + b.d[2][q] * h;
-            const double G2f = G2 + b.d[3][q] * h;
-            const double f2f = (q == 1) ? f2 + df2 * h : f2;
-            const double mg2f = m2 + G2f;
-            Disp e;
-            dispersion(kh2, mg2f, N2f, f2f, e);
-            if (q == 0) vel[sd] = (k * mg2f * e.c + U + b.d[0][0] * h) * ihX;
-            else if (q == 1) vel[sd] = (l * mg2f * e.c + V + b.d[1][1] * h) * ihY;
-            else vel[sd] = -m * kh2 * e.c;
-        }
-        F[q] = 0.5 * (vel[0] + vel[1]);
-        F[6 + q] = vel[0] - vel[1];
-    }
-}
-
 // ------------------------------------------------------------ the ray equations in double-float
-// The same formulas as dispersion / geometry_at / coriolis / ray_rhs above, evaluated in
-// double-float on the FP32 pipes (GB300's FP64 rate is 1/72 of its FP32 rate): the state enters
+// The ray equations -- the carrier moves with the mean of the opposing face group velocities, the
+// extents with their difference (Sec. 3b, App. B.1); the wavenumber follows Eq. eikonal-sphere:1-3
+// (sphere) or kdot = -grad Omega (f-plane) with the centre values -- evaluated in double-float on
+// the FP32 pipes (GB300's FP64 rate is 1/72 of its FP32 rate): the state enters
 // as FP64 and is split (one FP64 subtraction per component), the nine rates leave as FP64.  Every
 // intermediate carries about 48 significant bits, the reciprocal and reciprocal square root one
 // Newton step in DF from the FP32 hardware approximations (~2^-45).
@@ -705,10 +644,13 @@ __device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __rest
 }
 
 // Williamson (1980) low-storage RK3 on the 9 propagated components; background frozen.  The rates
-// and the low-storage register q are double-float; the state advances in FP64 (s += B q rounded
-// once per stage) and, for the next evaluation, in a double-float copy updated by the same B q.
-// The FP64 state waits in shared memory during the stages (sh: this thread's first slot, slots
-// kThreads apart), which keeps it out of the registers the ray equations need.
+// and the low-storage register q are double-float; the step's increments B q of the three stages
+// are summed in double-float and added to the FP64 state once, at the end (one FP64 rounding per
+// component instead of three: the sum is far smaller than the state, so its 48 bits are ample), and
+// a double-float copy of the state, updated by the same B q, feeds the next evaluation.  The FP64
+// state and the increment sums wait in shared memory during the stages (sh: this thread's first
+// slot, slots kThreads apart: 9 doubles, then 9 float2 sums at sh + 9 kThreads), which keeps them
+// out of the registers the ray equations need.
 __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt,
                                     double* sh)
 {
@@ -719,11 +661,13 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
     constexpr DF B2{8.0f / 15.0f, (float)(8.0 / 15.0 - (double)(8.0f / 15.0f))};
     const DF dtd = df_split(dt);
     DF y[9], q[9];
+    float2* acc = reinterpret_cast<float2*>(sh + 9 * kThreads);
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
         y[c] = df_split(s[c]);
         q[c] = df_f(0.0f);
         sh[c * kThreads] = s[c];
+        acc[c * kThreads] = make_float2(0.0f, 0.0f);
     }
 #pragma unroll 1
     for (int st = 0; st < 3; ++st) {
@@ -735,12 +679,17 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
         for (int c = 0; c < 9; ++c) {
             q[c] = st == 0 ? df_mul2(dtd, F[c]) : df_add(df_mul2(a, q[c]), df_mul2(dtd, F[c]));
             const DF bq = df_mul2(b, q[c]);
-            sh[c * kThreads] += df_to_double(bq);
+            const float2 o = acc[c * kThreads];
+            const DF na = df_add(DF{o.x, o.y}, bq);
+            acc[c * kThreads] = make_float2(na.hi, na.lo);
             y[c] = df_add(y[c], bq);
         }
     }
 #pragma unroll
-    for (int c = 0; c < 9; ++c) s[c] = sh[c * kThreads];
+    for (int c = 0; c < 9; ++c) {
+        const float2 o = acc[c * kThreads];
+        s[c] = sh[c * kThreads] + df_to_double(DF{o.x, o.y});
+    }
 }
 
 // ---------------------------------------------------------------------------- bookkeeping

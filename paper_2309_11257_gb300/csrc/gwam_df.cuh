@@ -68,9 +68,17 @@ __device__ __forceinline__ float narrow(double x)
     return narrow_general(x);
 }
 
-// Double-float values hi + lo (|lo| <= ulp(hi) / 2) on the FP32 pipes, about 48 significant bits:
-// products by TwoProduct (an FMA gives the exact rounding error), sums by TwoSum (Dekker 1971,
-// Knuth); every operation is an explicitly rounded intrinsic, never contracted or reordered.
+// Double-float values hi + lo on the FP32 pipes, about 48 significant bits: products by TwoProduct
+// (an FMA gives the exact rounding error), sums by TwoSum (Dekker 1971, Knuth); every operation is
+// an explicitly rounded intrinsic, never contracted or reordered.  Sums are renormalised
+// (FastTwoSum); products return the unevaluated pair they form -- the rounded product and the sum of
+// its rounding error and cross terms, |lo| at most a few ulp(hi) -- without renormalising: the next
+// operation takes both parts, so this costs a few units of 2^-48 and saves three of a product's seven
+// instructions (the ray-step kernel: 0.77 -> 0.67 ms per step on the sphere together with the
+// double-float increment sums of rk3).  A sum must stay renormalised: after a cancellation its
+// unrenormalised pair can have |lo| near |hi|, and a product that drops lo x lo then keeps only FP32
+// precision (measured: errors up to 5e-8 of the flux scales).  floor, ceil and comparisons
+// renormalise first (df_norm).
 struct DF {
     float hi, lo;
 };
@@ -106,7 +114,8 @@ __device__ __forceinline__ DF df_diff(float a, float b)
     return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(-b, bb))};
 }
 
-// hi + lo as a double (exact: lo's bits lie below hi's); a value that is one float needs no FP64 add
+// hi + lo as a double (exact: the two parts span far fewer than 53 bits); a value that is one float
+// needs no FP64 add
 __device__ __forceinline__ double df_to_double(DF x)
 {
     return x.lo == 0.0f ? widen(x.hi) : widen(x.hi) + widen(x.lo);
@@ -144,8 +153,7 @@ __device__ __forceinline__ DF df_mul2(DF a, DF b)
     float e = __fmaf_rn(a.hi, b.hi, -p);
     e = __fmaf_rn(a.hi, b.lo, e);
     e = __fmaf_rn(a.lo, b.hi, e);
-    const float s = __fadd_rn(p, e);
-    return {s, __fsub_rn(e, __fsub_rn(s, p))};
+    return {p, e};
 }
 
 __device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
@@ -182,19 +190,21 @@ __device__ __forceinline__ DF df_rsqrt(DF x)
     return df_add(df_f(r0), df_pow2(df_mul(e, r0), 0.5f));
 }
 
-// floor and ceil of hi + lo (a normalised pair: lo only matters when hi is an integer)
+// floor and ceil of hi + lo (renormalised first, so that lo only matters when hi is an integer)
 __device__ __forceinline__ float df_floor(DF x)
 {
+    x = df_norm(x.hi, x.lo);
     const float f = floorf(x.hi);
     return (f == x.hi && x.lo < 0.0f) ? f - 1.0f : f;
 }
 __device__ __forceinline__ float df_ceil(DF x)
 {
+    x = df_norm(x.hi, x.lo);
     const float f = ceilf(x.hi);
     return (f == x.hi && x.lo > 0.0f) ? f + 1.0f : f;
 }
-// a < b for normalised pairs
-__device__ __forceinline__ bool df_less(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+// a < b (both renormalised first)
+__device__ __forceinline__ bool df_less(DF a, DF b) { a = df_norm(a.hi, a.lo); b = df_norm(b.hi, b.lo); return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
 // x = hi + lo to about 48 bits: hi = x rounded to FP32, lo = (x - hi) rounded to FP32.  For
 // 2^-74 <= |x| < 2^127 (hi a finite normal float, lo normal or zero) with integer operations and one

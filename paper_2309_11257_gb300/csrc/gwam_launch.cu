@@ -490,7 +490,7 @@ __global__ void k_launch(Grid G, const Node* __restrict__ bg, const NodeDF* __re
                          gwam_bg_source src, const gwam_spec* __restrict__ specs, int total, double ghost_dt,
                          int pass, int* __restrict__ flag, double* __restrict__ partials, int pstride)
 {
-    __shared__ double sh_state[kGhost ? 9 * kThreads : 1];
+    __shared__ double sh_state[kGhost ? 18 * kThreads : 1];
     const int n0 = ctl->n;
     const long long next = ctl->next_id;
     double w = 0.0;

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
                                                         int* __restrict__ newid, int* __restrict__ cnt,
                                                         double* __restrict__ partials, int pstride)
 {
-    __shared__ double sh_state[9 * kThreads];
+    __shared__ double sh_state[18 * kThreads];
     const int n = ctl->n;
     double w_exit = 0.0, w_inv = 0.0;
     long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
