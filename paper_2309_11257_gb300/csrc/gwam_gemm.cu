@@ -25,7 +25,8 @@ __device__ __forceinline__ uint64_t gtime()
 }
 
 // bounded wait for completion of the mbarrier phase with the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// (after limit_ns of %globaltimer time, or 2^31 polls)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns)
 {
     uint64_t t0 = 0;
     for (uint32_t it = 0; it < 0x7fffffffu; ++it) {
@@ -39,7 +40,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
         if ((it & 63u) == 0) {
             const uint64_t t = gtime();
             if (t0 == 0) t0 = t;
-            else if (t - t0 > kWaitNs) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
     return false;
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     __syncthreads();
     tc_after();
     const uint32_t tmem = tmem_slot;
+    const unsigned long long wlim = e.wait_ns ? e.wait_ns : kWaitNs;
     bool ok = true;
     double sq = 0.0;
 
@@ -308,12 +310,14 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
             int it = 0;
-            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+            // (self-test of the give-up path: no copy is issued, so the MMA and epilogue warps wait
+            // on stages that never fill and give up after wait_ns)
+            for (int t = blockIdx.x; t < total && ok && !e.skip_copies; t += gridDim.x) {
                 const int z = t / per_slice, r = t - z * per_slice;
                 const int m0 = (r / n_tiles) * kBM, n0 = (r % n_tiles) * BN;
                 for (int i = 0; i < nk; ++i, ++it) {
                     const int s = it % ST;
-                    if (it >= ST && !mbar_wait(saddr(&empty_bar[s]), (uint32_t)((it / ST - 1) & 1))) {
+                    if (it >= ST && !mbar_wait(saddr(&empty_bar[s]), (uint32_t)((it / ST - 1) & 1), wlim)) {
                         ok = false;
                         break;
                     }
@@ -341,7 +345,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             if (!ok) abort_flag = 1;
             // every issued copy has landed before the CTA may exit (immediate in the normal case)
             for (int i = it > ST ? it - ST : 0; i < it; ++i)
-                if (!mbar_wait(saddr(&full_bar[i % ST]), (uint32_t)((i / ST) & 1))) ok = false;
+                if (!mbar_wait(saddr(&full_bar[i % ST]), (uint32_t)((i / ST) & 1), wlim)) ok = false;
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
             int it = 0, tl = 0;
             for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++tl) {
                 const int acc = tl & 1;
-                if (tl >= 2 && !mbar_wait(saddr(&acce_bar[acc]), (uint32_t)((tl / 2 - 1) & 1))) {
+                if (tl >= 2 && !mbar_wait(saddr(&acce_bar[acc]), (uint32_t)((tl / 2 - 1) & 1), wlim)) {
                     ok = false;
                     break;
                 }
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 const uint32_t d = tmem + (uint32_t)acc * kAccStride;
                 for (int i = 0; i < nk; ++i, ++it) {
                     const int s = it % ST;
-                    if (abort_flag || !mbar_wait(saddr(&full_bar[s]), (uint32_t)((it / ST) & 1))) {
+                    if (abort_flag || !mbar_wait(saddr(&full_bar[s]), (uint32_t)((it / ST) & 1), wlim)) {
                         ok = false;
                         break;
                     }
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
                 pm[k] = (MODE == EPI_DRAG && n < e.n_true) ? e.ymu[n] : 0.0f;
             }
             const int rowmask = (MODE == EPI_DRAG && row < e.M) ? e.mask[row] : 0;
-            const bool got = mbar_wait(saddr(&accf_bar[acc]), (uint32_t)((tl / 2) & 1));
+            const bool got = mbar_wait(saddr(&accf_bar[acc]), (uint32_t)((tl / 2) & 1), wlim);
             if (!__all_sync(0xffffffffu, got) || abort_flag) {
                 ok = false;
                 break;
@@ -511,7 +515,7 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
         }
     }
     // every MMA has finished before the TMEM is released (bounded wait; immediate normally)
-    const bool fin = mbar_wait(saddr(&done_bar), 0u);
+    const bool fin = mbar_wait(saddr(&done_bar), 0u, wlim);
     if (!__syncthreads_and(ok && fin) && tid == 0 && e.err) atomicOr(e.err, 1);
     tc_after();
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
@@ -631,11 +635,10 @@ bool gemm_bf16_launch(const CUtensorMap& ta, const CUtensorMap& tb, const CUtens
 
 }  // namespace gwam
 
-// Self-test entry point (declared in gwam.h): C = act(A . B^T + bias) with BF16 A [M][K] and
-// B [N][K]; C FP32 [M][N], or BF16 [M][N] (written by TMA stores when N is a multiple of 8);
-// bn = 0 picks the tile width.
-extern "C" int gwam_gemm_bf16(const void* A, const void* B, int M, int N, int K, const float* bias, int gelu, int bn,
-                              int out_bf16, void* C, void* stream)
+namespace {
+
+int gemm_selftest(const void* A, const void* B, int M, int N, int K, const float* bias, int gelu, int bn, int out_bf16,
+                  void* C, unsigned long long wait_ns, int skip_copies, void* stream)
 {
     if (!A || !B || !C || M < 1 || N < 1 || K < 64 || K % 64 || (bn != 0 && bn != 64 && bn != 128 && bn != 192 &&
                                                                   bn != 256))
@@ -664,10 +667,33 @@ extern "C" int gwam_gemm_bf16(const void* A, const void* B, int M, int N, int K,
         e.ldcf = N;
     }
     e.err = err;
+    e.wait_ns = wait_ns;
+    e.skip_copies = skip_copies;
     const bool launched = gwam::gemm_bf16_launch(ta, tb, have_tc ? &tc : nullptr, K, use_bn, 1, e, s);
     int h = 0;
     cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaFreeAsync(err, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || !launched) return -5;
     return h ? -6 : 0;
+}
+
+}  // namespace
+
+// Self-test entry point (declared in gwam.h): C = act(A . B^T + bias) with BF16 A [M][K] and
+// B [N][K]; C FP32 [M][N], or BF16 [M][N] (written by TMA stores when N is a multiple of 8);
+// bn = 0 picks the tile width.
+extern "C" int gwam_gemm_bf16(const void* A, const void* B, int M, int N, int K, const float* bias, int gelu, int bn,
+                              int out_bf16, void* C, void* stream)
+{
+    return gemm_selftest(A, B, M, N, K, bias, gelu, bn, out_bf16, C, 0ull, 0, stream);
+}
+
+// Self-test of the bounded waits (declared in gwam.h): the same GEMM with its producer told to
+// issue no copies and every wait limited to wait_us microseconds; the kernel gives up, frees its
+// TMEM and reports, and the call returns GWAM_ETIMEOUT.
+extern "C" int gwam_selftest_gemm_timeout(const void* A, const void* B, int M, int N, int K, int bn, float* C,
+                                          unsigned int wait_us, void* stream)
+{
+    if (wait_us < 1 || wait_us > 2000000u) return -1;
+    return gemm_selftest(A, B, M, N, K, nullptr, 0, bn, 0, C, 1000ull * wait_us, 1, stream);
 }

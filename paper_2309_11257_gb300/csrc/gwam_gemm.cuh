@@ -57,6 +57,8 @@ struct GemmEpi {
     int ncol, nlev;
     int* err;                 // bit 0 set when a bounded wait gave up
     int tstore;               // set by gemm_bf16_launch: cb is written through an output tensor map
+    unsigned long long wait_ns;   // limit of every bounded wait (0: 2 s)
+    int skip_copies;          // self-test of the give-up path only: the producer issues no copies
 };
 
 // 2-D BF16 tensor map of a row-major [rows][cols] matrix with leading dimension ld (elements),

@@ -127,6 +127,7 @@ SIGNATURES = {
     "gwam_get_theta_tendency_host": (C.c_int, [_vp, _vp]),
     "gwam_load": (C.c_int, [_vp, C.c_char_p]),
     "gwam_gemm_bf16": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, _vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+    "gwam_selftest_gemm_timeout": (C.c_int, [_vp, _vp, C.c_int, C.c_int, C.c_int, C.c_int, _vp, C.c_uint, _vp]),
     "gwam_mlp_create": (C.c_int, [_P(_vp), _P(MlpConfig), _vp]),
     "gwam_mlp_destroy": (None, [_vp]),
     "gwam_mlp_last_error": (C.c_char_p, [_vp]),

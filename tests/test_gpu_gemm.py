@@ -90,3 +90,42 @@ def test_gemm_rejects_bad_shapes(gw):
     assert lib.gwam_gemm_bf16(p, p, 128, 64, 60, None, 0, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
     assert lib.gwam_gemm_bf16(p, p, 128, 64, 64, None, 0, 96, 0, C.c_void_p(Cd.data_ptr()), None) == -1
     assert lib.gwam_gemm_bf16(p, p, 0, 64, 64, None, 0, 0, 0, C.c_void_p(Cd.data_ptr()), None) == -1
+
+
+@pytest.mark.parametrize("bn", [64, 128, 192, 256])
+def test_bounded_waits_give_up_and_the_context_stays_usable(gw, bn):
+    """Failure detection of the library's spin-waits without a GPU fault: the GEMM's producer is
+    told to issue no copies and every mbarrier wait is limited to 2 ms, so its MMA and epilogue warps
+    wait on stages that never fill.  They give up, release their tensor memory and report: the call
+    returns GWAM_ETIMEOUT within a fraction of a second.  The next GEMM of the same tile width (whose
+    CTAs allocate the same tensor memory) and of another width then run to the correct result."""
+    import time
+    import torch
+    M, N, K = 512, bn, 256
+    g = torch.Generator().manual_seed(bn)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16)
+    B = (torch.randn(N, K, generator=g) / 8).to(torch.bfloat16)
+    Ad, Bd = A.cuda(), B.cuda()
+    Cd = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    s = torch.cuda.current_stream()
+    lib = gw.lib()
+    t0 = time.perf_counter()
+    rc = lib.gwam_selftest_gemm_timeout(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()), M, N, K, bn,
+                                        C.c_void_p(Cd.data_ptr()), 2000, C.c_void_p(s.cuda_stream))
+    elapsed = time.perf_counter() - t0
+    assert rc == gw.GWAM_ETIMEOUT
+    assert elapsed < 1.0
+    assert lib.gwam_selftest_gemm_timeout(None, None, M, N, K, bn, None, 2000, None) == gw.GWAM_EINVAL
+    assert lib.gwam_selftest_gemm_timeout(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()), M, N, K, bn,
+                                          C.c_void_p(Cd.data_ptr()), 0, C.c_void_p(s.cuda_stream)) == gw.GWAM_EINVAL
+    ref = A.double().numpy() @ B.double().numpy().T
+    S = np.abs(A.double().numpy()) @ np.abs(B.double().numpy()).T
+    for width in (bn, 64 if bn != 64 else 128):
+        Cd.fill_(float("nan"))
+        rc = lib.gwam_gemm_bf16(C.c_void_p(Ad.data_ptr()), C.c_void_p(Bd.data_ptr()), M, N, K, C.c_void_p(0), 0,
+                                width, 0, C.c_void_p(Cd.data_ptr()), C.c_void_p(s.cuda_stream))
+        assert rc == 0
+        got = Cd.cpu().double().numpy()
+        assert (np.abs(got - ref) <= 2e-5 * S + 1e-6 * np.abs(ref)).all()
+    torch.cuda.synchronize()
+    assert float(torch.ones(4, device="cuda").sum()) == 4.0     # the context answers
