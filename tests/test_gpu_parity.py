@@ -504,3 +504,30 @@ def test_async_host_entry_points_reject_and_report(gw):
     with pytest.raises(gw.GwamError) as e:
         T.synchronize()
     assert e.value.code == -4          # GWAM_ENUMERIC
+
+
+def test_double_float_near_the_fp32_exponent_limits(gw):
+    """The FP64 form computes in double-float pairs of FP32 values, whose exponent range is FP32's.
+    Ray volumes at its edges against the oracle, with the parity bars of the other cases: a
+    wavenumber component at the rounding level of an axis-aligned launch (cos(pi/2)|k_h| ~ 4e-21 1/m,
+    whose square, 1.6e-41, is below FP32's smallest normal), one of 1e-30 (its square flushes to
+    zero), and wave-action densities from 1e-2 to 1e25 (actions 1e-17 ... 1e10)."""
+    grid = synth.fplane_grid(nx=16, ny=16, nz=32, dz=1000.0)
+    bg = synth.perturbed(synth.uniform_background(grid, U=8.0), tag=51, rel=0.05)
+    params = dict(synth.DEFAULT_PARAMS, smoothing=1, saturation=1, cap_per_column=0)
+    base = synth.fplane_rays(grid, 250, tag=52, z_lo=3e3, z_hi=20e3)
+    kh = np.hypot(base["k"], base["l"])
+    r = {k: np.array(v, dtype=np.float64) for k, v in base.items()}
+    r["k"][:50], r["l"][:50] = np.cos(np.pi / 2) * kh[:50], kh[:50]          # k at the rounding level
+    r["k"][50:100], r["l"][50:100] = -kh[50:100], np.sin(np.pi) * kh[50:100]  # l at the rounding level
+    r["k"][100:150], r["l"][100:150] = 1e-30, kh[100:150]                  # k^2 flushes to zero in FP32
+    r["n"][150:200] = 1e25 * r["n"][150:200] / r["n"][150:200].max()        # very large densities
+    r["n"][200:250] = 1e-2                                                 # tiny actions
+    assert abs(r["k"][0]) < 1e-19 and abs(r["k"][0]) ** 2 < np.finfo(np.float32).tiny
+    T, O = _pair(gw, grid, params, bg, 20000)
+    T.add_rays(r)
+    O.add_rays(r)
+    for s in range(8):
+        du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
+        if s % 4 == 3:
+            _compare_all(T, O, grid, du, dv, odu, odv)
