@@ -48,7 +48,7 @@ def _source_table(grid, src, specs, members):
 
 
 def generate(members=16, nx=64, ny=32, nz=90, steps=120, avg=40, launch_every=5, tag=0, convection=True,
-             src_overrides=None, max_rays=None, dt=180.0):
+             src_overrides=None, max_rays=None, dt=180.0, conv_fraction=0.3, jet_member0=None):
     """Run the FP64 tracer on `members` backgrounds and return (X, Y, info): features
     [members * nx * ny][4 nz + 8] and drag targets [members * nx * ny][2 nz] as float32 CUDA
     tensors, member-major then column order (j, i).  The sources launch every `launch_every` steps
@@ -70,9 +70,13 @@ def generate(members=16, nx=64, ny=32, nz=90, steps=120, avg=40, launch_every=5,
         max_rays = int(members * ncol * 32 * (steps // launch_every + 2) * 1.5 + (members * ncol * 60 if convection else 0))
     T = gwam.Tracer(grid, params, max_rays=max_rays, members=members)
     bgs = []
+    if jet_member0 is not None:
+        # member 0 on a given unperturbed jet background (e.g. 60 m/s at 45 deg)
+        amps[0], lats[0] = jet_member0
     for m in range(members):
-        bg = synth.perturbed(synth.jet_background(grid, amp=float(amps[m]), lat_deg=float(lats[m])),
-                             tag=6000 + 97 * tag + m)
+        bg = synth.jet_background(grid, amp=float(amps[m]), lat_deg=float(lats[m]))
+        if not (m == 0 and jet_member0 is not None):
+            bg = synth.perturbed(bg, tag=6000 + 97 * tag + m)
         bgs.append([torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in bg])
         T.set_member_background(m, *bgs[-1])
     specs = [None] * members
@@ -80,7 +84,7 @@ def generate(members=16, nx=64, ny=32, nz=90, steps=120, avg=40, launch_every=5,
         allsp = []
         for m in range(members):
             sp = synth.convective_specs(grid, tag=7000 + 31 * tag + m, median=16.0, sigma=1.0, cap=512,
-                                        z_launch=10e3, col_fraction=0.3)
+                                        z_launch=10e3, col_fraction=conv_fraction)
             sp["member"] = m
             specs[m] = sp
             allsp.append(sp)
@@ -130,6 +134,75 @@ def train(S, X, Y, steps=2000, batch=4096, lr=1e-3, lr_end=1e-5, seed=1, log_eve
         if log_every and (it % log_every == 0 or it == steps - 1):
             hist.append((it, S.loss()))
     return hist
+
+
+def generate_1m(nx=256, ny=128, nz=90, members_per_run=8, runs=4, steps=100, avg=30, launch_every=10, tag=10):
+    """The surrogate's full data set: 1 048 576 columns (4 runs x 8 members of the 256 x 128 x 90
+    sphere) from the FP64 tracer on the sphere workload's background (60 m/s jets at 45 deg: member 0
+    of the first run, unperturbed) and the batched ensemble's (jets U[30, 80] m/s at U[30, 60] deg,
+    seeded perturbations, convective launches in every column with lognormal counts, median 16, capped
+    at 512, on top of the background source); sources relaunched every `launch_every` steps, targets
+    averaged over the last `avg` steps.  Returns X, Y (member-major) and the per-run infos."""
+    import torch
+    Xs, Ys, infos = [], [], []
+    for r in range(runs):
+        X, Y, info = generate(members=members_per_run, nx=nx, ny=ny, nz=nz, steps=steps, avg=avg,
+                              launch_every=launch_every, tag=tag + r, conv_fraction=1.0,
+                              jet_member0=(60.0, 45.0) if r == 0 else None)
+        Xs.append(X)
+        Ys.append(Y)
+        infos.append(info)
+    X = torch.cat(Xs)
+    Y = torch.cat(Ys)
+    del Xs, Ys
+    return X, Y, infos
+
+
+def member_split(runs, members_per_run, ncol, test_member=-1, val_members=((0, -2), (2, -2))):
+    """Boolean row masks (train, validation, test) of a member-major data set: the test set is
+    member `test_member` of every run (unseen jets, perturbations and sources), the validation set
+    the listed (run, member) pairs, the rest trains."""
+    import torch
+    n = runs * members_per_run * ncol
+    test = torch.zeros(n, dtype=torch.bool, device="cuda")
+    val = torch.zeros_like(test)
+    for r in range(runs):
+        m = test_member % members_per_run
+        test[(r * members_per_run + m) * ncol:(r * members_per_run + m + 1) * ncol] = True
+    for r, m in val_members:
+        m = m % members_per_run
+        val[(r * members_per_run + m) * ncol:(r * members_per_run + m + 1) * ncol] = True
+    return ~(test | val), val, test
+
+
+# training of the full data set: batches of 4096, Adam at 1e-3 with a cosine decay over at most 1500
+# steps, validated every 50 (the validation error is lowest after about one epoch; the network then
+# fits the columns' unpredictable convective part)
+TRAIN_1M = dict(max_steps=1500, every=50, batch=4096, lr=1e-3, patience=6)
+
+
+def train_early_stopping(S, Xtr, Ytr, Xva, Yva, nlev, max_steps=4000, every=250, batch=4096, lr=1e-3, lr_end=1e-5,
+                         seed=1, patience=4):
+    """Adam with a cosine learning-rate decay over max_steps; every `every` steps the drag relative
+    L2 on the validation columns is measured and the weights with the lowest one are kept (early
+    stopping after `patience` checks without improvement).  Returns (best validation error, step of
+    the kept weights, history [(step, training loss, validation error)])."""
+    best, best_params, best_step, bad, hist = float("inf"), None, 0, 0, []
+    for it in range(max_steps):
+        a = lr_end + 0.5 * (lr - lr_end) * (1.0 + math.cos(math.pi * it / max(1, max_steps - 1)))
+        S.train_step(Xtr, Ytr, batch, seed=seed * 1_000_003 + it, lr=a)
+        if (it + 1) % every == 0 or it == max_steps - 1:
+            e = drag_error(S, Xva, Yva, nlev)["rel_l2"]
+            hist.append((it + 1, S.loss(), e))
+            if e < best:
+                best, best_params, best_step, bad = e, S.params(), it + 1, 0
+            else:
+                bad += 1
+                if bad >= patience:
+                    break
+    if best_params is not None:
+        S.set_params(best_params)
+    return best, best_step, hist
 
 
 def drag_error(S, X, Y, nlev):
