@@ -58,10 +58,10 @@ BYTES_PER_CELL_STEP = 224.0
 # Representative window: the workloads run 200 steps; the timed steps follow an untimed lead-in.
 RUN_STEPS = 200
 HBM_PEAK = None
-# DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 39.8 MB, k_advance32:
-# 20.8 MB, each for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
-ADV_TRAFFIC_BYTES_PER_RAY = 156.7
-ADV32_TRAFFIC_BYTES_PER_RAY = 81.7
+# DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 39.7 MB, k_advance32:
+# 20.7 MB, each for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
+ADV_TRAFFIC_BYTES_PER_RAY = 156.5
+ADV32_TRAFFIC_BYTES_PER_RAY = 81.5
 
 
 def measured_peaks():
