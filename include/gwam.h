@@ -405,8 +405,9 @@ int gwam_mlp_last_loss_host(gwam_mlp *m, double *loss);
 /* Network outputs (normalised units) of the first `rows` rows of the last train step, [rows][n_out]. */
 int gwam_mlp_output_host(gwam_mlp *m, float *Y, int rows);
 /* Inference on ncol columns of features X [ncol][n_in]: for every column inside the envelope the
- * de-normalised drag y * sigma + mu is written to dudt[k * ncol + c] and dvdt[k * ncol + c]
- * (k < nlev, the [nz][ny][nx] layout with ncol = ny nx, FP64); fallback_mask[c] = 1 for columns
+ * de-normalised drag y * sigma + mu (one FP32 fused multiply-add, widened exactly) is written to
+ * dudt[k * ncol + c] and dvdt[k * ncol + c] (k < nlev, the [nz][ny][nx] layout with ncol = ny nx,
+ * FP64); fallback_mask[c] = 1 for columns
  * outside the envelope (their drag entries are not written), else 0; *n_fallback (device int32) =
  * their number.  Needs nlev >= 1 and n_out = 2 nlev.  Asynchronous. */
 int gwam_mlp_infer(gwam_mlp *m, const float *X, int64_t ncol, double *dudt, double *dvdt, int32_t *fallback_mask,
