@@ -296,6 +296,11 @@ __global__ void __launch_bounds__(64 + 32 * EPW, 1)
     const uint32_t stg_base = base + (uint32_t)ST * kStage;
     float* sbias = reinterpret_cast<float*>(smem_raw + (base - saddr(smem_raw)) + (size_t)ST * kStage +
                                             (e.tstore ? (size_t)EPW * kStgWarp : 0));
+    // programmatic dependent launch: the next kernel in the stream may start its own set-up now; this
+    // one waits until the previous kernel has completed before it reads anything from global memory
+    // (the set-up above touched only shared and tensor memory and the kernel parameters)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     if (e.bias) {
         const int npad = (e.N + 31) & ~31;
         for (int i = tid; i < npad; i += blockDim.x) sbias[i] = i < e.N ? e.bias[i] : 0.0f;
@@ -558,8 +563,19 @@ bool launch_mode(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap
     }
     const long long tiles = (long long)((e.N + BN - 1) / BN) * ((e.M + kBM - 1) / kBM) * ksplit;
     const int grid = (int)std::min<long long>(tiles, sms[dev]);
-    k_gemm_bf16<BN, ST, EPW, MODE><<<grid, 64 + 32 * EPW, shm, s>>>(ta, tb, tc, K, ksplit, e);
-    return cudaPeekAtLastError() == cudaSuccess;
+    // launched with programmatic stream serialisation: the set-up of this GEMM (barriers, tensor
+    // memory) overlaps the tail of the kernel before it, which it waits for before its first read
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(64 + 32 * EPW);
+    cfg.dynamicSmemBytes = shm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_gemm_bf16<BN, ST, EPW, MODE>, ta, tb, tc, K, ksplit, e) == cudaSuccess;
 }
 
 // one kernel per epilogue mode: each holds only its own epilogue code (a smaller instruction
