@@ -36,9 +36,9 @@ static void free_all(Context& c)
     void* ptrs[] = {c.bg, c.bg32, c.bgdf, c.ray32_mem[0], c.ray32_mem[1], c.rho, c.rho_inv, c.tables, c.tables32, c.tables_df,
                     c.bg_scratch, c.theta,
                     c.ray_mem[0], c.ray_mem[1], c.info, c.ccell, c.cslot, c.newid,
-                    c.ent_id, c.ent_src, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
-                    c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl, c.budget, c.partials,
-                    c.flag_dev, c.spec_buf};
+                    c.ent_id, c.ent_src, c.ent_cell, c.sorted_src, c.pj, c.k2, c.kappa, c.raycell, c.ecap, c.cnt, c.off, c.off2,
+                    c.overlist, c.biglist, c.scan_tmp, c.dudt_buf, c.dvdt_buf, c.ctl,
+                    c.budget, c.partials, c.flag_dev, c.spec_buf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int f = 0; f < NFIELD; ++f) {
@@ -349,6 +349,7 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         dalloc(c, c.newid, nr + 1);
         dalloc(c, c.ent_id, nr);
         dalloc(c, c.ent_src, nr);
+        dalloc(c, c.ent_cell, nr);
         dalloc(c, c.sorted_src, nr);
         dalloc(c, c.pj, nr);
         dalloc(c, c.k2, nr);

@@ -84,6 +84,7 @@ struct Context {
     int* newid = nullptr;           // ids needed per ray -> exclusive prefix
     long long* ent_id = nullptr;    // entry id (in cell-offset order)
     int* ent_src = nullptr;         // entry source: parent * 4 + child, < 0 removed by the cap
+    int* ent_cell = nullptr;        // entry cell (global)
     int* sorted_src = nullptr;      // entry source in canonical order
     double* pj = nullptr;           // saturation: P_j (incl. alpha_j)
     double* k2 = nullptr;           // saturation: K_j^2

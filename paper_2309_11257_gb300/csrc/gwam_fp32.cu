@@ -407,7 +407,7 @@ __device__ __forceinline__ long long id32(const Ray32SoA& A, int64_t i)
 __global__ void k_scatter32(Grid G, Ray32SoA A, Ctl* ctl, int64_t max_rays, const int* __restrict__ info,
                             const int4* __restrict__ ccell, const int4* __restrict__ cslot,
                             const int* __restrict__ newid, const int* __restrict__ off,
-                            long long* __restrict__ ent_id, int* __restrict__ ent_src)
+                            long long* __restrict__ ent_id, int* __restrict__ ent_src, int* __restrict__ ent_cell)
 {
     const int n = ctl->n;
     const long long next = ctl->next_id;
@@ -430,6 +430,7 @@ __global__ void k_scatter32(Grid G, Ray32SoA A, Ctl* ctl, int64_t max_rays, cons
             if (pos >= max_rays) continue;
             ent_id[pos] = c == 0 ? pid : with_member(member_of(pid), next + newid[i] + c - 1);
             ent_src[pos] = i * 4 + c;
+            ent_cell[pos] = cs[c];
         }
     }
 }
@@ -691,10 +692,7 @@ __global__ void k_step_begin(Ctl* ctl);
 __global__ void k_cap_find(Grid G, Params P, Ctl* ctl, const int* __restrict__ off, int* __restrict__ overlist);
 __global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
                           const long long* __restrict__ ent_id, const int* __restrict__ ent_src,
-                          int* __restrict__ sorted_src, int* __restrict__ biglist);
-__global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
-                              const int* __restrict__ biglist, const long long* __restrict__ ent_id,
-                              const int* __restrict__ ent_src, int* __restrict__ sorted_src);
+                          const int* __restrict__ ent_cell, int* __restrict__ sorted_src);
 __global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl);
 __global__ void __launch_bounds__(kThreads) k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
                                                           const int* __restrict__ raycell, int* __restrict__ runlist);
@@ -721,7 +719,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
     exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
     exclusive_scan(c, c.cnt, c.off, G.ncell_all, nullptr);
     k_scatter32<<<nb, kThreads, 0, s>>>(G, c.A32, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off,
-                                        c.ent_id, c.ent_src);
+                                        c.ent_id, c.ent_src, c.ent_cell);
     int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
     const int* off2 = c.off;
     if (P.cap > 0) {
@@ -732,8 +730,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
         off2 = c.off2;
         mask |= 1 << T_CAP;
     }
-    k_segsort<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.sorted_src, c.biglist);
-    k_segsort_big<<<nb, kThreads, 0, s>>>(c.ctl, c.off, off2, c.biglist, c.ent_id, c.ent_src, c.sorted_src);
+    k_segsort<<<nb, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.ent_cell, c.sorted_src);
     k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
     tune_mark(c, 2);
     k_materialize32<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A32, c.B32, c.bg32, c.ctl, off2, c.sorted_src, c.info,

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
 __global__ void k_scatter(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, const int* __restrict__ info,
                           const int4* __restrict__ ccell, const int4* __restrict__ cslot,
                           const int* __restrict__ newid, const int* __restrict__ off, long long* __restrict__ ent_id,
-                          int* __restrict__ ent_src)
+                          int* __restrict__ ent_src, int* __restrict__ ent_cell)
 {
     const int n = ctl->n;
     const long long next = ctl->next_id;
@@ -239,6 +239,7 @@ __global__ void k_scatter(Grid G, RaySoA A, Ctl* ctl, int64_t max_rays, const in
             if (pos >= max_rays) continue;
             ent_id[pos] = c == 0 ? pid : with_member(member_of(pid), next + newid[i] + c - 1);
             ent_src[pos] = i * 4 + c;
+            ent_cell[pos] = cs[c];
         }
     }
 }
@@ -312,65 +313,26 @@ __global__ void __launch_bounds__(kThreads) k_cap_apply(Grid G, Params P, RaySoA
     }
 }
 
-constexpr int kSmallSeg = 16;
-
-// Sort every cell's entries by id (canonical order) and drop the capped ones; long segments
-// are deferred to k_segsort_big.
+// Sort every cell's entries by id (canonical order) and drop the capped ones: a thread per entry
+// counts the valid entries of its cell with a smaller id -- its rank -- and writes its source
+// there.  No thread idles on the many empty cells, no per-thread arrays; cell segments are short
+// (a few entries, tens in the launch slab and above the ghost layer), so the count per entry is
+// cheap, and every entry of a warp reads the same few cells.
 __global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
                           const long long* __restrict__ ent_id, const int* __restrict__ ent_src,
-                          int* __restrict__ sorted_src, int* __restrict__ biglist)
+                          const int* __restrict__ ent_cell, int* __restrict__ sorted_src)
 {
     if (ctl->status) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G.ncell_all; c += gridDim.x * blockDim.x) {
-        const int a = off[c];
-        const int L = off[c + 1] - a;
-        if (L == 0) continue;
-        const int dest = off2[c];
-        if (L == 1) {
-            if (ent_src[a] >= 0) sorted_src[dest] = ent_src[a];
-            continue;
-        }
-        if (L > kSmallSeg) {
-            biglist[atomicAdd(&ctl->n_big, 1)] = c;
-            continue;
-        }
-        long long ids[kSmallSeg];
-        int srcs[kSmallSeg];
-        int m = 0;
-        for (int e = 0; e < L; ++e) {
-            const int src = ent_src[a + e];
-            if (src < 0) continue;
-            const long long id = ent_id[a + e];
-            int q = m;
-            while (q > 0 && ids[q - 1] > id) {
-                ids[q] = ids[q - 1];
-                srcs[q] = srcs[q - 1];
-                --q;
-            }
-            ids[q] = id;
-            srcs[q] = src;
-            ++m;
-        }
-        for (int e = 0; e < m; ++e) sorted_src[dest + e] = srcs[e];
-    }
-}
-
-__global__ void k_segsort_big(Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
-                              const int* __restrict__ biglist, const long long* __restrict__ ent_id,
-                              const int* __restrict__ ent_src, int* __restrict__ sorted_src)
-{
-    const int nbig = ctl->status ? 0 : ctl->n_big;
-    for (int w = blockIdx.x; w < nbig; w += gridDim.x) {
-        const int c = biglist[w];
-        const int a = off[c], b = off[c + 1], dest = off2[c];
-        for (int e = a + threadIdx.x; e < b; e += blockDim.x) {
-            const int src = ent_src[e];
-            if (src < 0) continue;
-            const long long id = ent_id[e];
-            int rank = 0;
-            for (int q = a; q < b; ++q) rank += (ent_src[q] >= 0) && (ent_id[q] < id);
-            sorted_src[dest + rank] = src;
-        }
+    const int total = off[G.ncell_all];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int src = ent_src[e];
+        if (src < 0) continue;
+        const int c = ent_cell[e];
+        const int a = off[c], b = off[c + 1];
+        const long long id = ent_id[e];
+        int rank = 0;
+        for (int q = a; q < b; ++q) rank += (ent_src[q] >= 0) && (ent_id[q] < id);
+        sorted_src[off2[c] + rank] = src;
     }
 }
 
@@ -880,7 +842,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
     exclusive_scan(c, c.cnt, c.off, G.ncell_all, nullptr);
     k_scatter<<<nb, kThreads, 0, s>>>(G, c.A, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off, c.ent_id,
-                                      c.ent_src);
+                                      c.ent_src, c.ent_cell);
     int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
     const int* off2 = c.off;
     if (P.cap > 0) {
@@ -891,8 +853,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
         off2 = c.off2;
         mask |= 1 << T_CAP;
     }
-    k_segsort<<<cell_blocks, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.sorted_src, c.biglist);
-    k_segsort_big<<<nb, kThreads, 0, s>>>(c.ctl, c.off, off2, c.biglist, c.ent_id, c.ent_src, c.sorted_src);
+    k_segsort<<<nb, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.ent_cell, c.sorted_src);
     k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
     tune_mark(c, 2);
     k_materialize<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A, c.B, c.bgdf, c.ctl, off2, c.sorted_src, c.info, c.newid,
