@@ -483,7 +483,9 @@ def ensemble_arm(args):
     rs = s1["ray_steps"] - s0["ray_steps"]
     line = {"metric": METRIC, "value": rs / (ms / 1000.0), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None,
+            "dtype": "f64 state, sums and outputs; double-float (~48-bit) arithmetic on the FP32 pipes",
+            "data": "synthetic",
             "config": {"workload": "ensemble: %d spheres 256x128x90, background + convective sources" % M,
                        "rays_launched": s0["n_launched"], "rays_live_start": s0["n_live"],
                        "rays_live_end": s1["n_live"], "convective_specs": nspec, "launch_shapes": tuned,

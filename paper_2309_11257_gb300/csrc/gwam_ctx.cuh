@@ -19,7 +19,7 @@ struct Ctl {
     int n_new;           // ray volumes after this step's re-binning
     int n_children;      // children produced this step (before the cap)
     int n_over;          // columns above the cap this step
-    int n_big;           // cells too large for the per-thread segment sort
+    int n_big;           // length of the saturation run list
     int status;          // sticky device status (gwam_status values)
     long long next_id;   // next unused ray id
     long long new_ids;   // ids issued this step
@@ -97,7 +97,7 @@ struct Context {
     int* off = nullptr;             // exclusive prefix of cnt (ncell + 1)
     int* off2 = nullptr;            // exclusive prefix after the cap (ncell + 1)
     int* overlist = nullptr;        // columns above the cap
-    int* biglist = nullptr;         // cells with long segments
+    int* biglist = nullptr;         // saturation run list: the cell of every run of equal cells
     int* scan_tmp = nullptr;        // block sums of the scans
     int64_t scan_tmp_cap = 0;
 

@@ -435,7 +435,7 @@ __device__ __forceinline__ void sat_run(int p, int b, int c, const double* __res
     for (int q = p; q < b; ++q) kappa[q] = kap;
 }
 
-// the listed runs, counted in ctl->n_big (reset by k_set_nnew once the segment sort is done)
+// the listed runs, counted in ctl->n_big (cleared by k_set_nnew before k_sat_heads lists them)
 __global__ void k_sat_kappa(const Ctl* ctl, const int* __restrict__ off2, const int* __restrict__ runlist,
                             const double* __restrict__ rho, const double* __restrict__ pj,
                             const double* __restrict__ k2, double dt, double* __restrict__ kappa)
@@ -753,7 +753,7 @@ __global__ void k_step_begin(Ctl* ctl)
     ctl->ray_steps += ctl->n;
 }
 
-// also frees the long-segment counter of the segment sort for the saturation's run list
+// the re-binned count, and the run-list counter cleared for the saturation
 __global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl)
 {
     ctl->n_new = off2[ncell];
