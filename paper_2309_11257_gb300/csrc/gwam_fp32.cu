@@ -343,12 +343,16 @@ __global__ void __launch_bounds__(kThreads) k_advance32(Grid G, Params P, Ray32S
                                                           Ctl* ctl, float dt, int* __restrict__ info,
                                                           int4* __restrict__ ccell, int4* __restrict__ cslot,
                                                           int* __restrict__ newid, int* __restrict__ cnt,
-                                                          double* __restrict__ partials, int pstride)
+                                                          double* __restrict__ partials, int pstride, ClearSet zs)
 {
+    __shared__ __align__(128) float4 zbuf[kClearPiece / 16];
     const int n = ctl->n;
+    ClearState cs;
+    clear_start(zs, zbuf, n, cs);
     double w_exit = 0.0, w_inv = 0.0;
     long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) clear_issue(zs, cs, cs.per);
         S32 s;
         load32(G, A, i, s);
         const int mem = member_of(s.id);
@@ -385,6 +389,7 @@ __global__ void __launch_bounds__(kThreads) k_advance32(Grid G, Params P, Ray32S
         cslot[i] = make_int4(sl[0], sl[1], sl[2], sl[3]);
         newid[i] = nch > 0 ? nch - 1 : 0;
     }
+    clear_finish(zs, cs);
     const double we = block_sum(w_exit);
     const double wi = block_sum(w_inv);
     const long long ne = block_sum(n_exit), ni = block_sum(n_inv), nv = block_sum(n_sv), nh = block_sum(n_sh);
@@ -500,6 +505,7 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
 {
     if (ctl->status) return;
     const int n_new = off2[G.ncell_all];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_new = n_new;   // the live count k_finalize closes the step with
     const int n_old = ctl->n;
     const long long next = ctl->next_id;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_new; p += gridDim.x * blockDim.x) {
@@ -693,7 +699,6 @@ __global__ void k_cap_find(Grid G, Params P, Ctl* ctl, const int* __restrict__ o
 __global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const int* __restrict__ off2,
                           const long long* __restrict__ ent_id, const int* __restrict__ ent_src,
                           const int* __restrict__ ent_cell, int* __restrict__ sorted_src);
-__global__ void k_set_nnew(const int* off2, int ncell, Ctl* ctl);
 __global__ void __launch_bounds__(kThreads) k_sat_heads(Ctl* ctl, const int* __restrict__ off2, int ncell_all,
                                                           const int* __restrict__ raycell, int* __restrict__ runlist);
 
@@ -713,7 +718,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
     prof_mark(c, 0);
     tune_mark(c, 0);
     k_advance32<<<la.blocks, la.threads, 0, s>>>(G, P, c.A32, c.bg32, c.ctl, (float)dt, c.info, c.ccell, c.cslot,
-                                                 c.newid, c.cnt, c.partials, c.max_blocks);
+                                                 c.newid, c.cnt, c.partials, c.max_blocks, clear_set(c));
     tune_mark(c, 1);
     prof_mark(c, 1);
     exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
@@ -731,7 +736,6 @@ void run_step32(Context& c, double dt, double* du, double* dv)
         mask |= 1 << T_CAP;
     }
     k_segsort<<<nb, kThreads, 0, s>>>(G, c.ctl, c.off, off2, c.ent_id, c.ent_src, c.ent_cell, c.sorted_src);
-    k_set_nnew<<<1, 1, 0, s>>>(off2, G.ncell_all, c.ctl);
     tune_mark(c, 2);
     k_materialize32<<<lm.blocks, lm.threads, 0, s>>>(G, P, c.A32, c.B32, c.bg32, c.ctl, off2, c.sorted_src, c.info,
                                                      c.newid, c.pj, reinterpret_cast<float*>(c.k2), c.raycell);
@@ -744,8 +748,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
                                               reinterpret_cast<float*>(c.kappa));
     }
     prof_mark(c, 3);
-    for (int f = 0; f < (P.theta_flux ? NFIELD : F_TL); ++f)
-        cudaMemsetAsync(c.field[f], 0, sizeof(double) * (size_t)c.field_len(f), s);
+    // (the projected fields were cleared by k_advance32)
     tune_mark(c, 4);
     if (P.theta_flux)
         k_project32<true><<<lp.blocks, lp.threads, 0, s>>>(
