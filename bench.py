@@ -58,10 +58,19 @@ BYTES_PER_CELL_STEP = 224.0
 # Representative window: the workloads run 200 steps; the timed steps follow an untimed lead-in.
 RUN_STEPS = 200
 HBM_PEAK = None
-# DRAM bytes per launch from the ncu captures in profiles/ (k_advance: 39.7 MB, k_advance32:
-# 20.7 MB, each for 253 952 rays on the 128 x 64 sphere), scaled by rays: bytes per ray volume.
-ADV_TRAFFIC_BYTES_PER_RAY = 156.5
-ADV32_TRAFFIC_BYTES_PER_RAY = 81.5
+# The ray-step kernels also clear the nine projected FP64 fields the step's projection accumulates
+# into (two interface fields of nz + 1 levels, seven centre fields of nz levels): algorithmic bytes
+# of that clearing, per launch.
+def clear_bytes(nx, ny, nz, theta=False):
+    # (with the potential-temperature flux projected, two more centre fields)
+    return 8.0 * nx * ny * (2 * (nz + 1) + (9 if theta else 7) * nz)
+
+
+# DRAM bytes per launch from the ncu captures in profiles/, as bytes per ray volume (reads and ray
+# writes, scaled by rays) plus the clearing writes (scaled by cells); None while the kernel has
+# changed since its counters were taken.
+ADV_TRAFFIC_BYTES_PER_RAY = None
+ADV32_TRAFFIC_BYTES_PER_RAY = None
 
 
 def measured_peaks():
@@ -338,22 +347,30 @@ def gpu_arm(args, rank, world, local_rank):
     hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
     ncell = nx * ny * nz
     ray_bytes = BYTES_PER_RAY_STEP_FP32 if fp32 else BYTES_PER_RAY_STEP_FP64
+    zero_bytes = clear_bytes(nx, ny, nz, theta=bool(params.get("theta_flux")))
+    kernel_bytes = ray_bytes * rays_per_launch + zero_bytes
     step_bytes = (BYTES_PER_RAY_STEP_FP32 if fp32 else 224.0) * rays_per_launch + BYTES_PER_CELL_STEP * ncell
     step_ms = ms_max / args.steps
     hbm_view = {"peak_gbs": hbm_peak, "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                "kernel_bytes_per_ray_step": ray_bytes,
-                "kernel_gbs": ray_bytes * rays_per_launch / (adv_ms / 1000.0) / 1e9,
-                "kernel_frac": ray_bytes * rays_per_launch / (adv_ms / 1000.0) / 1e9 / hbm_peak,
+                "kernel_bytes_per_ray_step": ray_bytes, "kernel_clearing_bytes": zero_bytes,
+                "kernel_gbs": kernel_bytes / (adv_ms / 1000.0) / 1e9,
+                "kernel_frac": kernel_bytes / (adv_ms / 1000.0) / 1e9 / hbm_peak,
+                "kernel_frac_rays_only": ray_bytes * rays_per_launch / (adv_ms / 1000.0) / 1e9 / hbm_peak,
                 "step_bytes": step_bytes, "step_gbs": step_bytes / (step_ms / 1000.0) / 1e9,
                 "step_frac": step_bytes / (step_ms / 1000.0) / 1e9 / hbm_peak}
     if fp32:
-        # precision form: the ray step reads and writes the 64-byte record
+        # precision form: the ray step reads and writes the 64-byte record and clears the projected fields
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
-        achieved = BYTES_PER_RAY_STEP_FP32 * rays_per_launch / (adv_ms / 1000.0) / 1e9
-        roofline = {"bound": "hbm", "kernel": "k_advance32 (FP32 RK3 ray step)", "achieved": achieved,
-                    "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                    "traffic": ADV32_TRAFFIC_BYTES_PER_RAY * rays_per_launch,
-                    "traffic_source": "ncu dram bytes of k_advance32 on the 128x64 sphere, scaled by rays",
+        achieved = kernel_bytes / (adv_ms / 1000.0) / 1e9
+        traffic = (ADV32_TRAFFIC_BYTES_PER_RAY * rays_per_launch + zero_bytes
+                   if ADV32_TRAFFIC_BYTES_PER_RAY is not None else None)
+        roofline = {"bound": "hbm", "kernel": "k_advance32 (FP32 RK3 ray step + clearing of the projected fields)",
+                    "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "bytes_per_launch": {"ray_records": BYTES_PER_RAY_STEP_FP32 * rays_per_launch,
+                                         "field_clearing": zero_bytes},
+                    "traffic": traffic,
+                    "traffic_source": "ncu dram bytes of k_advance32 on the 128x64 sphere: reads and ray writes "
+                                      "scaled by rays, plus the clearing writes",
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                     "hbm": hbm_view,
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
@@ -361,8 +378,10 @@ def gpu_arm(args, rank, world, local_rank):
         achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
         roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
                     "peak": FP64_EQ_PEAK_TOPS, "unit": "TFLOP/s", "frac": achieved / FP64_EQ_PEAK_TOPS,
-                    "traffic": ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch if ADV_TRAFFIC_BYTES_PER_RAY else None,
-                    "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere, scaled by rays",
+                    "traffic": (ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch + zero_bytes
+                                if ADV_TRAFFIC_BYTES_PER_RAY is not None else None),
+                    "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere: reads and ray writes "
+                                      "scaled by rays, plus the clearing writes",
                     "peak_source": "modelled (not measured) from unit counts and the 2.07 GHz clock: "
                                    "FP64-precision operations as double-float on the FP32 pipes (4.48 T/s) plus "
                                    "the FP64 pipe (0.63 T/s)",
