@@ -66,11 +66,13 @@ def clear_bytes(nx, ny, nz, theta=False):
     return 8.0 * nx * ny * (2 * (nz + 1) + (9 if theta else 7) * nz)
 
 
-# DRAM bytes per launch from the ncu captures in profiles/, as bytes per ray volume (reads and ray
-# writes, scaled by rays) plus the clearing writes (scaled by cells); None while the kernel has
-# changed since its counters were taken.
-ADV_TRAFFIC_BYTES_PER_RAY = None
-ADV32_TRAFFIC_BYTES_PER_RAY = None
+# DRAM bytes (read + write) of one launch in the ncu captures in profiles/, as a fraction of that
+# launch's algorithmic bytes (ray bytes x 253 952 rays + the clearing of the 128 x 64 x 90 fields):
+# k_advance 75.64 MB of 134.48 MB, k_advance32 53.95 MB of 85.72 MB (written field lines still in L2
+# when the kernel ends are not counted).  The bench's traffic is that fraction of its own launch's
+# algorithmic bytes; None while the kernel has changed since its counters were taken.
+ADV_TRAFFIC_FRACTION = 75.64 / 134.48
+ADV32_TRAFFIC_FRACTION = 53.95 / 85.72
 
 
 def measured_peaks():
@@ -362,15 +364,15 @@ def gpu_arm(args, rank, world, local_rank):
         # precision form: the ray step reads and writes the 64-byte record and clears the projected fields
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
         achieved = kernel_bytes / (adv_ms / 1000.0) / 1e9
-        traffic = (ADV32_TRAFFIC_BYTES_PER_RAY * rays_per_launch + zero_bytes
-                   if ADV32_TRAFFIC_BYTES_PER_RAY is not None else None)
+        traffic = ADV32_TRAFFIC_FRACTION * kernel_bytes if ADV32_TRAFFIC_FRACTION is not None else None
         roofline = {"bound": "hbm", "kernel": "k_advance32 (FP32 RK3 ray step + clearing of the projected fields)",
                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                     "bytes_per_launch": {"ray_records": BYTES_PER_RAY_STEP_FP32 * rays_per_launch,
                                          "field_clearing": zero_bytes},
                     "traffic": traffic,
-                    "traffic_source": "ncu dram bytes of k_advance32 on the 128x64 sphere: reads and ray writes "
-                                      "scaled by rays, plus the clearing writes",
+                    "traffic_source": "ncu dram bytes of k_advance32 on the 128x64 sphere (profiles/"
+                                      "k_advance32_sphere_half_fp32.md) as a fraction of that launch's algorithmic "
+                                      "bytes, times this launch's",
                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
                     "hbm": hbm_view,
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
@@ -378,10 +380,10 @@ def gpu_arm(args, rank, world, local_rank):
         achieved = FLOPS_PER_RAY_STEP * rays_per_launch / (adv_ms / 1000.0) / 1e12
         roofline = {"bound": "alu", "kernel": "k_advance (FP64 RK3 ray step)", "achieved": achieved,
                     "peak": FP64_EQ_PEAK_TOPS, "unit": "TFLOP/s", "frac": achieved / FP64_EQ_PEAK_TOPS,
-                    "traffic": (ADV_TRAFFIC_BYTES_PER_RAY * rays_per_launch + zero_bytes
-                                if ADV_TRAFFIC_BYTES_PER_RAY is not None else None),
-                    "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere: reads and ray writes "
-                                      "scaled by rays, plus the clearing writes",
+                    "traffic": ADV_TRAFFIC_FRACTION * kernel_bytes if ADV_TRAFFIC_FRACTION is not None else None,
+                    "traffic_source": "ncu dram bytes of k_advance on the 128x64 sphere (profiles/"
+                                      "k_advance_sphere_half_fp64.md) as a fraction of that launch's algorithmic "
+                                      "bytes (ray state, gathers, field clearing), times this launch's",
                     "peak_source": "modelled (not measured) from unit counts and the 2.07 GHz clock: "
                                    "FP64-precision operations as double-float on the FP32 pipes (4.48 T/s) plus "
                                    "the FP64 pipe (0.63 T/s)",
