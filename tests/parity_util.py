@@ -157,3 +157,21 @@ def assert_stats_match(gs, os_, rtol=RTOL):
     for k in W_STATS:
         a, b = gs[k], os_[k]
         assert abs(a - b) <= rtol * max(abs(b), 1e-300), (k, a, b)
+
+
+def odd_field_case():
+    """3 x 5 columns of 21 levels: the centre fields hold 315 values, an odd count, whose last
+    element (the top cell of the last column) the ray-step kernels clear apart from their 16-byte
+    stores; ray volumes are placed in that cell, propagating downward so that they stay."""
+    from paper_2309_11257_gb300 import synth
+    grid = synth.fplane_grid(nx=3, ny=5, nz=21, dx=50e3, dy=50e3, dz=500.0)
+    bg = synth.perturbed(synth.uniform_background(grid, U=5.0), tag=41, rel=0.1)
+    rays = synth.fplane_rays(grid, 300, tag=42, z_lo=1e3, z_hi=9e3)
+    top = synth.fplane_rays(grid, 40, tag=43, z_lo=10.1e3, z_hi=10.4e3, ext_z=100.0)
+    g = synth.rng(44)
+    top["x"] = g.uniform(2.05, 2.95, 40) * grid["dx"]
+    top["y"] = g.uniform(4.05, 4.95, 40) * grid["dy"]
+    top["m"] = -top["m"]
+    rays = {k: np.concatenate([rays[k], top[k]]) for k in rays}
+    params = dict(synth.DEFAULT_PARAMS, smoothing=0, saturation=1)
+    return grid, bg, rays, params

@@ -22,7 +22,7 @@ import pytest
 
 import oracle
 from paper_2309_11257_gb300 import synth
-from parity_util import scaled_error, state_errors
+from parity_util import odd_field_case, scaled_error, state_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -232,3 +232,27 @@ def test_precision_form_ensemble_and_graph(gw):
         outs.append(r)
     for n in ("id", "member", "cell") + tuple(oracle.STATE_NAMES):
         np.testing.assert_array_equal(outs[0][n], outs[1][n])
+
+
+def test_odd_field_lengths_are_cleared_every_step(gw):
+    """Fields of odd length (3 x 5 columns of 21 levels): the bulk copies clear the fields' 16-byte
+    part and thread 0 the last element, the top cell of the last column, where ray volumes are
+    placed; the fields are compared after each of four steps."""
+    import torch
+    grid, bg, rays, params = odd_field_case()
+    T = gw.Tracer(grid, dict(params, precision=1), max_rays=4096)
+    T.set_background(*[torch.from_numpy(a.copy()).cuda() for a in bg])
+    O = oracle.Model(grid, params)
+    O.set_background(*bg)
+    T.add_rays(rays)
+    O.add_rays(rays)
+    nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
+    du = torch.zeros((nz, ny, nx), dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    for _ in range(4):
+        T.step(120.0, du, dv)
+        odu, odv = O.step(120.0)
+        _report_and_check(T, O, grid, du.cpu().numpy(), dv.cpu().numpy(), odu, odv, "odd field lengths")
+        o_last = O.field("wad")[nz - 1, ny - 1, nx - 1]
+        assert o_last > 0.0
+        assert T.field("wad")[nz - 1, ny - 1, nx - 1] == pytest.approx(o_last, rel=FIELD_TOL)

@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_2309_11257_gb300 import synth
 from parity_util import (RTOL, assert_fields_match, assert_level_errors, assert_rays_match, assert_stats_match,
-                         level_error, state_errors)
+                         level_error, odd_field_case, state_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +63,22 @@ def _compare_all(T, O, grid, du=None, dv=None, odu=None, odv=None, fields=True, 
         for name in oracle.FIELD_NAMES:
             assert_fields_match(T.field(name), O.field(name), O.field_abs(name), name=name)
     return errs
+
+
+def test_odd_field_lengths_are_cleared_every_step(gw):
+    """Fields of odd length: every projected field compared element by element after each of four
+    steps (a value left from the previous step would add to this step's sums)."""
+    grid, bg, rays, params = odd_field_case()
+    T, O = _pair(gw, grid, params, bg, 4096)
+    T.add_rays(rays)
+    O.add_rays(rays)
+    nz, ny, nx = grid["nz"], grid["ny"], grid["nx"]
+    for _ in range(4):
+        du, dv, odu, odv = _step_both(T, O, 120.0, nz, ny, nx)
+        _compare_all(T, O, grid, du, dv, odu, odv)
+        assert O.field("wad")[nz - 1, ny - 1, nx - 1] > 0.0      # the odd last element carries action
+        assert T.field("wad")[nz - 1, ny - 1, nx - 1] == pytest.approx(O.field("wad")[nz - 1, ny - 1, nx - 1],
+                                                                       rel=1e-12)
 
 
 def test_fplane_workload_parity(gw):
