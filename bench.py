@@ -455,8 +455,12 @@ def gpu_arm(args, rank, world, local_rank):
             "e2e": e2e,
             "clocks": clocks,
         }
-        # coupling: set-up + gradients; ghost launch: 2 launch passes, 3 scan kernels, tallies, close
-        line["gpu_launches"] = args.steps * (launches_per_step(params) + (2 if coupled else 0) + (7 if ghost else 0))
+        # per step: the kernel nodes of the step graph (counted by the library from the captured graph),
+        # or the eager step's kernels; coupling adds the background set-up (2 kernels), a ghost-layer
+        # launch its 2 launch passes, the 2 kernels of its slot scan, the tally fold and the close
+        per_step = T.graph_kernel_count() if use_graph else launches_per_step(params, fp32)
+        line["gpu_launches"] = args.steps * (per_step + (2 if coupled else 0) + (6 if ghost else 0))
+        line["config"]["kernels_per_step"] = per_step
         print(json.dumps(line), flush=True)
     return 0
 
@@ -665,17 +669,21 @@ def surrogate_arm(args):
     return 0
 
 
-def launches_per_step(params) -> int:
-    """Kernels of the library per gwam_step (memsets excluded)."""
-    # begin, advance, 2 scans (3 kernels each), scatter, segsort x2, set_nnew, materialize, project,
-    # divergence, finalize
-    n = 1 + 1 + 3 + 3 + 1 + 2 + 1 + 1 + 1 + 1 + 1
+def launches_per_step(params, fp32=False) -> int:
+    """Kernels of the library per eager gwam_step (memsets excluded): begin, advance, two scans of two
+    kernels, scatter, segment sort, materialise, project, divergence, budget fold; the cap's find,
+    apply and scan; the saturation's run list and kappa; in the FP64 form the smoothing, or without
+    smoothing the split of the fields into double-float pairs; in the precision form the narrowing
+    pass and the smoothing."""
+    n = 1 + 1 + 2 * 2 + 1 + 1 + 1 + 1 + 1 + 1
     if params.get("cap_per_column", 0) > 0:
-        n += 2 + 3                                   # cap find/apply + scan
+        n += 2 + 2
     if params.get("saturation", 0):
-        n += 2                                       # short runs, long runs (one per lane)
-    if params.get("smoothing", 0):
-        n += 9
+        n += 2
+    if fp32:
+        n += 1 + (1 if params.get("smoothing", 0) else 0)
+    else:
+        n += 1
     return n
 
 

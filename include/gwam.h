@@ -446,6 +446,10 @@ int gwam_profile_read(gwam_ctx *ctx, double *ms_host, int64_t *steps);
  * phase times of the last replay of each of the two graphs (one per ray-buffer parity), averaged,
  * in ms_host[5], and in *replays how many graphs contributed (0 before the first replay). */
 int gwam_graph_profile_read(gwam_ctx *ctx, double *ms_host, int *replays);
+/* Kernel launches of one step graph replay: the number of kernel nodes of the captured step graphs
+ * (the largest, if they differ), counted from the graph itself when it was captured; *kernels = 0
+ * before the first gwam_step_graph.  Memset and event nodes are not kernels and are not counted. */
+int gwam_graph_kernel_count(gwam_ctx *ctx, int *kernels);
 /* Human-readable description of the last error on this context (never NULL). */
 const char *gwam_last_error(const gwam_ctx *ctx);
 /* Library version string. */

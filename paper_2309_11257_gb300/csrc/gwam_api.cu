@@ -841,6 +841,18 @@ static void graph_step(Context& c, double dt, double* dudt, double* dvdt)
             c.err = std::string("graph capture: ") + cudaGetErrorString(e);
             throw (int)GWAM_ECUDA;
         }
+        // the kernel nodes the graph launches per replay (gwam_graph_kernel_count)
+        size_t nn = 0;
+        int kern = 0;
+        if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+                for (size_t q = 0; q < nn; ++q) {
+                    cudaGraphNodeType t;
+                    if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+                }
+        }
+        c.gkernels[gi] = kern;
         e = cudaGraphInstantiate(&c.gexec[gi], graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
@@ -1318,6 +1330,17 @@ int gwam_graph_profile_read(gwam_ctx* ctx, double* ms_host, int* replays)
     }
     for (int p = 0; p < Context::kPhases; ++p) ms_host[p] = n ? ms_host[p] / n : 0.0;
     *replays = n;
+    API_END
+}
+
+int gwam_graph_kernel_count(gwam_ctx* ctx, int* kernels)
+{
+    API_BEGIN(ctx)
+    if (!kernels) return GWAM_EINVAL;
+    int k = 0;
+    for (int gi = 0; gi < Context::kGraphs; ++gi)
+        if (c.gexec[gi]) k = std::max(k, c.gkernels[gi]);
+    *kernels = k;
     API_END
 }
 

@@ -133,6 +133,7 @@ struct Context {
     bool gcap_prof = false;     // capturing: prof_mark records into gprof_ev[gcap_slot]
     int gcap_slot = 0;
     bool glaunched[kGraphs] = {};
+    int gkernels[kGraphs] = {};  // kernel nodes of each captured step graph
     int prof_pending = 0;
     int64_t prof_steps = 0;
     double prof_ms[kPhases] = {};

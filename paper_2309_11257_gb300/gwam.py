@@ -148,6 +148,7 @@ SIGNATURES = {
     "gwam_profile_enable": (C.c_int, [_vp, C.c_int]),
     "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
     "gwam_graph_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int)]),
+    "gwam_graph_kernel_count": (C.c_int, [_vp, _P(C.c_int)]),
     "gwam_last_error": (C.c_char_p, [_vp]),
     "gwam_version": (C.c_char_p, []),
 }
@@ -405,6 +406,12 @@ class Tracer:
         n = C.c_int()
         self._check(_lib.gwam_graph_profile_read(self._h, ms.ctypes.data_as(_vp), C.byref(n)), "graph_profile_read")
         return dict(zip(self.PHASES, ms.tolist())), n.value
+
+    def graph_kernel_count(self):
+        """Kernel launches per step-graph replay, counted from the captured graph."""
+        n = C.c_int()
+        self._check(_lib.gwam_graph_kernel_count(self._h, C.byref(n)), "graph_kernel_count")
+        return n.value
 
     def synchronize(self):
         self._check(_lib.gwam_synchronize(self._h), "synchronize")

@@ -547,3 +547,29 @@ def test_double_float_near_the_fp32_exponent_limits(gw):
         du, dv, odu, odv = _step_both(T, O, 300.0, grid["nz"], grid["ny"], grid["nx"])
         if s % 4 == 3:
             _compare_all(T, O, grid, du, dv, odu, odv)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_graph_kernel_count(gw, precision):
+    """The step graph's kernel nodes, counted by the library from the captured graph, equal the
+    eager step's kernels as the benchmark counts them (its gpu_launches)."""
+    import sys
+    import os
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    grid = synth.sphere_grid(nx=40, ny=20, nz=24, dz=1000.0)
+    for params in (dict(synth.DEFAULT_PARAMS, smoothing=1, saturation=1, cap_per_column=12),
+                   dict(synth.DEFAULT_PARAMS, smoothing=0, saturation=0, cap_per_column=0)):
+        params = dict(params, precision=precision)
+        T = gw.Tracer(grid, params, max_rays=100000)
+        bg = synth.jet_background(grid)
+        T.set_background(*[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in bg])
+        T.add_rays(synth.sphere_rays(grid, 500, tag=51))
+        assert T.graph_kernel_count() == 0
+        du = torch.zeros((grid["nz"], grid["ny"], grid["nx"]), dtype=torch.float64, device="cuda")
+        dv = torch.zeros_like(du)
+        T.step_graph(300.0, du, dv)
+        T.synchronize()
+        assert T.graph_kernel_count() == bench.launches_per_step(params, fp32=bool(precision)), params
+
