@@ -580,17 +580,21 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
         const DF W = q == 0 ? U : V;
         const DF dW = q == 0 ? b.d[0][0] : b.d[1][1];
         const DF S = q == 0 ? g.ihX : g.ir;
+        // the Taylor increments at the +h face, h = ext / 2; the -h face takes their negations (a
+        // product by -h is the negated product by h, bit for bit)
+        const DF h = df_pow2(ext, 0.5f);
+        const DF tn = df_mul2(dn, h), tg = df_mul2(dg, h), tw = df_mul2(dW, h);
+        const DF tf = q == 1 ? df_mul2(dfq, h) : zero;
         DF vel0 = zero, vel1 = zero;
 #pragma unroll 1
         for (int sd = 0; sd < 2; ++sd) {
-            const DF h = df_pow2(ext, sd == 0 ? 0.5f : -0.5f);
-            const DF N2f = df_add(N2, df_mul2(dn, h));
-            const DF G2f = df_add(G2, df_mul2(dg, h));
-            const DF f2f = q == 1 ? df_add(f2, df_mul2(dfq, h)) : f2;
+            const DF N2f = df_add(N2, sd == 0 ? tn : df_neg(tn));
+            const DF G2f = df_add(G2, sd == 0 ? tg : df_neg(tg));
+            const DF f2f = q == 1 ? df_add(f2, sd == 0 ? tf : df_neg(tf)) : f2;
             const DF mg2f = df_add(m2, G2f);
             DispDF e;
             dispersion_df(kh2, mg2f, N2f, f2f, e);
-            const DF v = q < 2 ? df_mul2(df_add(df_add(df_mul2(df_mul2(A, mg2f), e.c), W), df_mul2(dW, h)), S)
+            const DF v = q < 2 ? df_mul2(df_add(df_add(df_mul2(df_mul2(A, mg2f), e.c), W), sd == 0 ? tw : df_neg(tw)), S)
                                : df_neg(df_mul2(mkh2, e.c));
             if (sd == 0)
                 vel0 = v;
@@ -650,7 +654,9 @@ __device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __rest
 // a double-float copy of the state, updated by the same B q, feeds the next evaluation.  The FP64
 // state and the increment sums wait in shared memory during the stages (sh: this thread's first
 // slot, slots kThreads apart: 9 doubles, then 9 float2 sums at sh + 9 kThreads), which keeps them
-// out of the registers the ray equations need.
+// out of the registers the ray equations need; with kQShared the low-storage register q waits there
+// too (9 float2 at sh + 18 kThreads; 27 kThreads doubles in all).
+template <bool kQShared = false>
 __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt,
                                     double* sh)
 {
@@ -660,12 +666,13 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
     constexpr DF B1{15.0f / 16.0f, 0.0f};
     constexpr DF B2{8.0f / 15.0f, (float)(8.0 / 15.0 - (double)(8.0f / 15.0f))};
     const DF dtd = df_split(dt);
-    DF y[9], q[9];
+    DF y[9], q[kQShared ? 1 : 9];
     float2* acc = reinterpret_cast<float2*>(sh + 9 * kThreads);
+    float2* qs = acc + 9 * kThreads;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
         y[c] = df_split(s[c]);
-        q[c] = df_f(0.0f);
+        if (!kQShared) q[c] = df_f(0.0f);
         sh[c * kThreads] = s[c];
         acc[c * kThreads] = make_float2(0.0f, 0.0f);
     }
@@ -677,8 +684,16 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
         const DF b = st == 0 ? B0 : (st == 1 ? B1 : B2);
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            q[c] = st == 0 ? df_mul2(dtd, F[c]) : df_add(df_mul2(a, q[c]), df_mul2(dtd, F[c]));
-            const DF bq = df_mul2(b, q[c]);
+            DF qc;
+            if (kQShared) {
+                const float2 qo = qs[c * kThreads];
+                qc = st == 0 ? df_mul2(dtd, F[c]) : df_add(df_mul2(a, DF{qo.x, qo.y}), df_mul2(dtd, F[c]));
+                qs[c * kThreads] = make_float2(qc.hi, qc.lo);
+            } else {
+                qc = st == 0 ? df_mul2(dtd, F[c]) : df_add(df_mul2(a, q[c]), df_mul2(dtd, F[c]));
+                q[c] = qc;
+            }
+            const DF bq = df_mul2(b, qc);
             const float2 o = acc[c * kThreads];
             const DF na = df_add(DF{o.x, o.y}, bq);
             acc[c * kThreads] = make_float2(na.hi, na.lo);

@@ -237,13 +237,17 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 
 // ============================================================================ advance
 
+// RK3 register q in shared memory (rk3<true>): 27 doubles of shared memory per thread
+constexpr bool kAdvanceQShared = true;
+constexpr size_t kAdvanceSmem = sizeof(double) * (kAdvanceQShared ? 27 : 18) * kThreads;
+
 __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
                                                         Ctl* ctl, double dt, int* __restrict__ info,
                                                         int4* __restrict__ ccell, int4* __restrict__ cslot,
                                                         int* __restrict__ newid, int* __restrict__ cnt,
                                                         double* __restrict__ partials, int pstride, ClearSet zs)
 {
-    __shared__ double sh_state[18 * kThreads];
+    extern __shared__ double sh_state[];   // kAdvanceSmem bytes
     const int n = ctl->n;
     double w_exit = 0.0, w_inv = 0.0;
     long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
         load_ray(A, i, s, id);
         const int mem = member_of(id);
         const NodeDF* bgm = bg + (int64_t)mem * G.ncell;
-        rk3(G, bgm, s, dt, sh_state + threadIdx.x);
+        rk3<kAdvanceQShared>(G, bgm, s, dt, sh_state + threadIdx.x);
         wrap_position(G, s);
         const int st = ray_status(G, s);
         int code = 0, nch = 0;
@@ -873,6 +877,7 @@ void configure_launch_kernels();
 
 void configure_kernels()
 {
+    cudaFuncSetAttribute(k_advance, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdvanceSmem);
     configure_launch_kernels();
 }
 
@@ -923,7 +928,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     cudaMemsetAsync(c.partials, 0, sizeof(double) * NTALLY * (size_t)c.max_blocks, s);
     prof_mark(c, 0);
     tune_mark(c, 0);
-    k_advance<<<la.blocks, la.threads, 0, s>>>(G, P, c.A, c.bgdf, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
+    k_advance<<<la.blocks, la.threads, kAdvanceSmem, s>>>(G, P, c.A, c.bgdf, c.ctl, dt, c.info, c.ccell, c.cslot, c.newid, c.cnt,
                                                c.partials, c.max_blocks, clear_set(c));
     tune_mark(c, 1);
     prof_mark(c, 1);
