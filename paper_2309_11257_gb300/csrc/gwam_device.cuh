@@ -508,7 +508,10 @@ __device__ __forceinline__ void geometry_df(const Grid& G, DF Y, DF Z, GeoDF& g)
     }
 }
 
-__device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restrict__ bg, const DF y[9], DF R[9])
+// ext_sh: when given, the three extents are read from there (float2 pairs kThreads apart) instead of
+// y[6..8], which the caller then need not hold in registers
+__device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restrict__ bg, const DF y[9], DF R[9],
+                                           const float2* ext_sh = nullptr)
 {
     BgDF b;
     gather_df(G, bg, y[0], y[1], y[2], b);
@@ -572,7 +575,13 @@ __device__ __forceinline__ void ray_rhs_df(const Grid& G, const NodeDF* __restri
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         if (q < q0) continue;
-        const DF ext = q == 0 ? y[6] : (q == 1 ? y[7] : y[8]);
+        DF ext;
+        if (ext_sh) {
+            const float2 e2 = ext_sh[q * kThreads];
+            ext = DF{e2.x, e2.y};
+        } else {
+            ext = q == 0 ? y[6] : (q == 1 ? y[7] : y[8]);
+        }
         const DF dn = q == 0 ? b.d[2][0] : (q == 1 ? b.d[2][1] : b.d[2][2]);
         const DF dg = q == 0 ? b.d[3][0] : (q == 1 ? b.d[3][1] : b.d[3][2]);
         const DF dfq = q == 1 ? df2 : zero;     // f^2 varies along the meridional axis only
@@ -656,7 +665,7 @@ __device__ __forceinline__ void intrinsic_df(const Grid& G, const NodeDF* __rest
 // slot, slots kThreads apart: 9 doubles, then 9 float2 sums at sh + 9 kThreads), which keeps them
 // out of the registers the ray equations need; with kQShared the low-storage register q waits there
 // too (9 float2 at sh + 18 kThreads; 27 kThreads doubles in all).
-template <bool kQShared = false>
+template <bool kQShared = false, bool kExtShared = false>
 __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg, double s[NSTATE], double dt,
                                     double* sh)
 {
@@ -669,17 +678,19 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
     DF y[9], q[kQShared ? 1 : 9];
     float2* acc = reinterpret_cast<float2*>(sh + 9 * kThreads);
     float2* qs = acc + 9 * kThreads;
+    float2* es = qs + 9 * kThreads;   // the extents' double-float copy (kExtShared)
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
         y[c] = df_split(s[c]);
         if (!kQShared) q[c] = df_f(0.0f);
         sh[c * kThreads] = s[c];
         acc[c * kThreads] = make_float2(0.0f, 0.0f);
+        if (kExtShared && c >= 6) es[(c - 6) * kThreads] = make_float2(y[c].hi, y[c].lo);
     }
 #pragma unroll 1
     for (int st = 0; st < 3; ++st) {
         DF F[9];
-        ray_rhs_df(G, bg, y, F);
+        ray_rhs_df(G, bg, y, F, kExtShared ? es : nullptr);
         const DF a = st == 1 ? A1 : A2;
         const DF b = st == 0 ? B0 : (st == 1 ? B1 : B2);
 #pragma unroll
@@ -697,7 +708,13 @@ __device__ __forceinline__ void rk3(const Grid& G, const NodeDF* __restrict__ bg
             const float2 o = acc[c * kThreads];
             const DF na = df_add(DF{o.x, o.y}, bq);
             acc[c * kThreads] = make_float2(na.hi, na.lo);
-            y[c] = df_add(y[c], bq);
+            if (kExtShared && c >= 6) {
+                const float2 ye = es[(c - 6) * kThreads];
+                const DF yn = df_add(DF{ye.x, ye.y}, bq);
+                es[(c - 6) * kThreads] = make_float2(yn.hi, yn.lo);
+            } else {
+                y[c] = df_add(y[c], bq);
+            }
         }
     }
 #pragma unroll

@@ -237,9 +237,11 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 
 // ============================================================================ advance
 
-// RK3 register q in shared memory (rk3<true>): 27 doubles of shared memory per thread
+// RK3 register q (and the extents) in shared memory: 27 (36) doubles of shared memory per thread
 constexpr bool kAdvanceQShared = true;
-constexpr size_t kAdvanceSmem = sizeof(double) * (kAdvanceQShared ? 27 : 18) * kThreads;
+constexpr bool kAdvanceExtShared = true;
+constexpr size_t kAdvanceSmem =
+    sizeof(double) * (kAdvanceQShared ? (kAdvanceExtShared ? 36 : 27) : 18) * kThreads;
 
 __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
                                                         Ctl* ctl, double dt, int* __restrict__ info,
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
         load_ray(A, i, s, id);
         const int mem = member_of(id);
         const NodeDF* bgm = bg + (int64_t)mem * G.ncell;
-        rk3<kAdvanceQShared>(G, bgm, s, dt, sh_state + threadIdx.x);
+        rk3<kAdvanceQShared, kAdvanceQShared && kAdvanceExtShared>(G, bgm, s, dt, sh_state + threadIdx.x);
         wrap_position(G, s);
         const int st = ray_status(G, s);
         int code = 0, nch = 0;
