@@ -240,6 +240,7 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 // RK3 register q (and the extents) in shared memory: 27 (36) doubles of shared memory per thread
 constexpr bool kAdvanceQShared = true;
 constexpr bool kAdvanceExtShared = true;
+constexpr bool kAdvanceLateTail = true;   // P_x, P_y, P_z, N loaded after the RK3 stages
 constexpr size_t kAdvanceSmem =
     sizeof(double) * (kAdvanceQShared ? (kAdvanceExtShared ? 36 : 27) : 18) * kThreads;
 
@@ -256,10 +257,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s[NSTATE];
         long long id;
-        load_ray(A, i, s, id);
+        if (kAdvanceLateTail) {
+            // the nine propagated components and the id (its member selects the background) now;
+            // P_x, P_y, P_z and N, which the stages do not touch, after them: out of the registers the
+            // ray equations need
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double2 v = __ldg(&A.a[q][i]);
+                s[2 * q] = v.x;
+                s[2 * q + 1] = v.y;
+            }
+            s[SEZ] = __ldg(reinterpret_cast<const double*>(&A.a[4][i]));
+            id = __ldg(reinterpret_cast<const long long*>(&A.a[6][i]) + 1);
+        } else {
+            load_ray(A, i, s, id);
+        }
         const int mem = member_of(id);
         const NodeDF* bgm = bg + (int64_t)mem * G.ncell;
         rk3<kAdvanceQShared, kAdvanceQShared && kAdvanceExtShared>(G, bgm, s, dt, sh_state + threadIdx.x);
+        if (kAdvanceLateTail) {
+            s[SPX] = __ldg(reinterpret_cast<const double*>(&A.a[4][i]) + 1);
+            const double2 v = __ldg(&A.a[5][i]);
+            s[SPY] = v.x;
+            s[SPZ] = v.y;
+            s[SN] = __ldg(reinterpret_cast<const double*>(&A.a[6][i]));
+        }
         wrap_position(G, s);
         const int st = ray_status(G, s);
         int code = 0, nch = 0;
