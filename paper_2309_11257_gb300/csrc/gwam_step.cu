@@ -241,8 +241,9 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 constexpr bool kAdvanceQShared = true;
 constexpr bool kAdvanceExtShared = true;
 constexpr bool kAdvanceLateTail = true;   // P_x, P_y, P_z, N loaded after the RK3 stages
-constexpr size_t kAdvanceSmem =
-    sizeof(double) * (kAdvanceQShared ? (kAdvanceExtShared ? 36 : 27) : 18) * kThreads;
+constexpr int kAdvanceRkSlots = kAdvanceQShared ? (kAdvanceExtShared ? 36 : 27) : 18;
+// and six more per thread: the exit / invalid action sums and four counters
+constexpr size_t kAdvanceSmem = sizeof(double) * (kAdvanceRkSlots + 6) * kThreads;
 
 __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
                                                         Ctl* ctl, double dt, int* __restrict__ info,
@@ -252,8 +253,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
 {
     extern __shared__ double sh_state[];   // kAdvanceSmem bytes
     const int n = ctl->n;
-    double w_exit = 0.0, w_inv = 0.0;
-    long long n_exit = 0, n_inv = 0, n_sv = 0, n_sh = 0;
+    // this thread's exit / invalid action sums and its exit, invalid, vertical- and horizontal-split
+    // counters, updated in shared memory where they occur: not held in registers across the stages
+    double* const tw = sh_state + kAdvanceRkSlots * kThreads + threadIdx.x;
+    long long* const tn = reinterpret_cast<long long*>(tw + 2 * kThreads);
+    tw[0] = 0.0;
+    tw[kThreads] = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tn[c * kThreads] = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s[NSTATE];
         long long id;
@@ -287,25 +294,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
         int code = 0, nch = 0;
         int cc[4] = {-1, -1, -1, -1}, sl[4] = {0, 0, 0, 0};
         if (st == 2) {
-            ++n_inv;
+            tn[kThreads] += 1;
             const double w = ray_action(s);
-            if (isfinite(w)) w_inv += w;
+            if (isfinite(w)) tw[kThreads] += w;
         } else if (st == 1) {
-            ++n_exit;
-            w_exit += ray_action(s);
+            tn[0] += 1;
+            tw[0] += ray_action(s);
         } else {
             code = split_code(G, P, s);
             nch = num_children(code);
-            if (code & 1) ++n_sv;
-            if (code & 2) n_sh += (code & 1) ? 2 : 1;
+            if (code & 1) tn[2 * kThreads] += 1;
+            if (code & 2) tn[3 * kThreads] += (code & 1) ? 2 : 1;
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 if (c >= nch) break;
                 double ch[NSTATE];
                 make_child(G, s, code, c, ch);
                 if (ray_status(G, ch) != 0) {
-                    ++n_exit;
-                    w_exit += ray_action(ch);
+                    tn[0] += 1;
+                    tw[0] += ray_action(ch);
                 } else {
                     cc[c] = mem * G.ncell + cell_of(G, ch);
                     sl[c] = atomicAdd(&cnt[cc[c]], 1);
@@ -320,9 +327,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
     }
     // the projected fields, with stores (bulk copies were measured slower here: 0.680 -> 0.741 ms)
     clear_fields(zs);
-    const double we = block_sum(w_exit);
-    const double wi = block_sum(w_inv);
-    const long long ne = block_sum(n_exit), ni = block_sum(n_inv), nv = block_sum(n_sv), nh = block_sum(n_sh);
+    const double we = block_sum(tw[0]);
+    const double wi = block_sum(tw[kThreads]);
+    const long long ne = block_sum(tn[0]), ni = block_sum(tn[kThreads]), nv = block_sum(tn[2 * kThreads]),
+                    nh = block_sum(tn[3 * kThreads]);
     if (threadIdx.x == 0) {
         partials[T_EXIT * pstride + blockIdx.x] = we;
         partials[T_INVALID * pstride + blockIdx.x] = wi;
