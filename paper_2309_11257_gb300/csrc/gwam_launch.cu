@@ -20,11 +20,12 @@ __device__ __forceinline__ bool nonfinite_bits(double x)
 }
 
 // caller [nz][ny][nx] -> column-major node values (U, V, N^2, Gamma^2) and rho, transposed through
-// shared memory (kBgTile columns of a row per block).  Gamma^2 = (d ln rho / dz)^2 / 4 by centred
-// differences of ln rho (one-sided at the bottom and top), each difference taken as the logarithm of
-// the density ratio in double-float (df_log_ratio); 1/rho by the Newton reciprocal; f^2 of the row
-// from the host table.
-constexpr int kBgTile = 16;
+// shared memory (kBgTile columns of a row per block: 8 columns, 23 KB of shared memory, eight blocks
+// per SM; 16 columns, four blocks per SM, took 37 us more of the set-up).  Gamma^2 =
+// (d ln rho / dz)^2 / 4 by centred differences of ln rho (one-sided at the bottom and top), each
+// difference taken as the logarithm of the density ratio in double-float (df_log_ratio); 1/rho by
+// the Newton reciprocal; f^2 of the row from the host table.
+constexpr int kBgTile = 8;
 __global__ void k_set_background(Grid G, int gamma_mode, const double* __restrict__ u, const double* __restrict__ v,
                                  const double* __restrict__ n2, const double* __restrict__ rho, Node* __restrict__ bg,
                                  double* __restrict__ rho_c, double* __restrict__ rho_inv, int* flags)
@@ -83,7 +84,10 @@ __global__ void k_set_background(Grid G, int gamma_mode, const double* __restric
 // Node gradients by centred differences: periodic in x (and y on the f-plane), one-sided at the
 // pole rows and at the bottom and top levels.  The same pass writes the per-step gather copies of
 // the node: double-float pairs (FP64 form, bgdf) or FP32 (precision form, bg32), whichever is given.
-__global__ void k_node_gradients(Grid G, Node* __restrict__ bg, NodeDF* __restrict__ bgdf, Node32* __restrict__ bg32)
+// At most 85 registers, three blocks per SM: the pass waits on its neighbour loads (at 88 registers
+// and two blocks per SM the whole set-up took 0.267 ms, with three 0.241 ms).
+__global__ void __launch_bounds__(256, 3) k_node_gradients(Grid G, Node* __restrict__ bg, NodeDF* __restrict__ bgdf,
+                                                          Node32* __restrict__ bg32)
 {
     const int64_t total = (int64_t)G.ncell;
     const DF idx{G.df_inv_dX.x, G.df_inv_dX.y}, idy{G.df_inv_dY.x, G.df_inv_dY.y}, idz{G.df_inv_dz.x, G.df_inv_dz.y};
