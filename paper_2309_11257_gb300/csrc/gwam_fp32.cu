@@ -637,7 +637,7 @@ __global__ void __launch_bounds__(kThreads) k_project32(Grid G, Params P, Ray32S
 #pragma unroll
             for (int q = 0; q < NH; ++q) {
                 const double v = df_to_double(hv[q]);
-                // the whole cell is this run: store its sum (fields were zeroed before the launch)
+                // the whole cell is this run: store its sum (the ray-step kernel cleared the fields)
                 if (own) dst[q][key] = v;
                 else atomicAdd(&dst[q][key], v);
             }

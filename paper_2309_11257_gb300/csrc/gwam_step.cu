@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kThreads) k_project(Grid G, Params P, RaySoA B
 #pragma unroll
             for (int q = 0; q < NH; ++q) v[q] = df_to_double(hv[q]);
             if (own) {
-                // the whole cell is this run: store its sum (fields were zeroed before the launch)
+                // the whole cell is this run: store its sum (the ray-step kernel cleared the fields)
                 f_ll[key] = v[0];
                 f_lp[key] = v[1];
                 f_pl[key] = v[2];
