@@ -132,32 +132,6 @@ __device__ __forceinline__ T block_sum(T v)
     return r;
 }
 
-// Segmented inclusive warp scan by key: after the call the last lane of every run of equal keys
-// holds the run's total in v[]; returns true on that lane.  All 32 lanes must call it.
-template <int NV>
-__device__ __forceinline__ bool warp_segment_reduce(int key, double (&v)[NV])
-{
-    const int lane = threadIdx.x & 31;
-    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const int next = __shfl_down_sync(0xffffffffu, key, 1);
-    const bool head = (lane == 0) || (prev != key);
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    // every lane its own run (the usual case once ray volumes spread): nothing to combine, and
-    // no FP64 additions spent on it
-    if (heads == 0xffffffffu) return true;
-    const unsigned upto = heads & (0xffffffffu >> (31 - lane));
-    const int start = 31 - __clz(upto);
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double o = __shfl_up_sync(0xffffffffu, v[q], d);
-            if (lane - d >= start) v[q] += o;
-        }
-    }
-    return (lane == 31) || (next != key);
-}
-
 // True when this lane's run of equal keys touches neither lane 0 nor lane 31: with the ray array
 // sorted by key and a warp holding 32 consecutive entries, no other warp holds that key, so the
 // run's sum may be stored instead of added atomically (fewer L2 atomics, and deterministic).

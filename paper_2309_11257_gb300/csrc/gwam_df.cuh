@@ -121,9 +121,10 @@ __device__ __forceinline__ double df_to_double(DF x)
     return x.lo == 0.0f ? widen(x.hi) : widen(x.hi) + widen(x.lo);
 }
 
-// Segmented inclusive sum over runs of equal keys in a warp (as warp_segment_reduce) in
-// double-float: the FP32 pipes do the additions, the last lane of each run holds the run's sum.
-// Returns true on the last lane of a run.
+// Segmented inclusive sum over runs of equal keys in a warp, in double-float: the FP32 pipes do the
+// additions, the last lane of each run holds the run's sum (a scan by key at distances 1, 2, 4, ...).
+// Returns true on the last lane of a run.  All 32 lanes must call it; every lane its own run returns
+// at once.
 template <int NV>
 __device__ __forceinline__ bool warp_segment_reduce_df(int key, DF (&v)[NV])
 {
@@ -133,8 +134,12 @@ __device__ __forceinline__ bool warp_segment_reduce_df(int key, DF (&v)[NV])
     const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
     if (heads == 0xffffffffu) return true;
     const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    // the warp's longest run: the steps at distances beyond it would add nothing (no lane has a run
+    // partner that far back), so they are skipped -- the same sums, bit for bit
+    const unsigned longest = __reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
+        if ((unsigned)d >= longest) break;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             DF o;
