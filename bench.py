@@ -670,12 +670,12 @@ def surrogate_arm(args):
 
 
 def launches_per_step(params, fp32=False) -> int:
-    """Kernels of the library per eager gwam_step (memsets excluded): begin, advance, two scans of two
-    kernels, scatter, segment sort, materialise, project, divergence, budget fold; the cap's find,
-    apply and scan; the saturation's run list and kappa; in the FP64 form the smoothing, or without
-    smoothing the split of the fields into double-float pairs; in the precision form the narrowing
-    pass and the smoothing."""
-    n = 1 + 1 + 2 * 2 + 1 + 1 + 1 + 1 + 1 + 1
+    """Kernels of the library per eager gwam_step (memsets excluded): begin, advance, the two kernels
+    that scan the new-id and per-cell counts together, scatter, segment sort, materialise, project,
+    divergence, budget fold; the cap's find, apply and scan; the saturation's run list and kappa; in
+    the FP64 form the smoothing, or without smoothing the split of the fields into double-float
+    pairs; in the precision form the narrowing pass and the smoothing."""
+    n = 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1
     if params.get("cap_per_column", 0) > 0:
         n += 2 + 2
     if params.get("saturation", 0):

@@ -226,6 +226,9 @@ void launch_gather_rays(Context& c, double* state13, long long* ids, int* cells,
 void launch_field_to_caller(Context& c, const double* src, double* dst, int nlev);
 void launch_gamma_to_caller(Context& c, double* dst);
 void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n_dev);
+// two independent exclusive scans in one pair of launches
+void exclusive_scan2(Context& c, const int* in0, int* out0, int64_t n0, const int* n_dev0, const int* in1,
+                     int* out1, int64_t n1, const int* n_dev1);
 int scan_block_count(int64_t n);
 void scan_with_scratch(const int* in, int* out, int64_t n, int* bsum, cudaStream_t s);
 void finalize_tallies(Context& c, int slot_mask, int mode);

@@ -721,8 +721,7 @@ void run_step32(Context& c, double dt, double* du, double* dv)
                                                  c.newid, c.cnt, c.partials, c.max_blocks, clear_set(c));
     tune_mark(c, 1);
     prof_mark(c, 1);
-    exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
-    exclusive_scan(c, c.cnt, c.off, G.ncell_all, nullptr);
+    exclusive_scan2(c, c.newid, c.newid, c.max_rays, &c.ctl->n, c.cnt, c.off, G.ncell_all, nullptr);
     k_scatter32<<<nb, kThreads, 0, s>>>(G, c.A32, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off,
                                         c.ent_id, c.ent_src, c.ent_cell);
     int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);

@@ -160,33 +160,57 @@ __device__ __forceinline__ void store4(int* out, int64_t i, int64_t b, bool vec,
     if (i + 3 < b) out[i + 3] = r.w;
 }
 
-__global__ void __launch_bounds__(kThreads) k_part_sums(const int* in, int64_t n, const int* n_dev,
-                                                         int* __restrict__ psum, int nparts)
+// One scan of the launch: in[0..len) -> out, len = *n_dev if given (n its upper bound), its part
+// sums in psum[0..nparts).  A launch runs one or two independent scans, the second one's parts in
+// the blocks after the first one's.
+struct ScanJob {
+    const int* in;
+    int* out;
+    int64_t n;
+    const int* n_dev;
+    int* psum;
+    int nparts;
+};
+
+__device__ __forceinline__ const ScanJob& scan_job(const ScanJob& j0, const ScanJob& j1, int& part)
 {
-    const int len = scan_len(n, n_dev);
-    const int64_t chunk = part_chunk(len, nparts);
-    const int64_t a = (int64_t)blockIdx.x * chunk, b = a + chunk < len ? a + chunk : (int64_t)len;
-    const bool vec = (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+    part = blockIdx.x;
+    if (part < j0.nparts) return j0;
+    part -= j0.nparts;
+    return j1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_part_sums(ScanJob j0, ScanJob j1)
+{
+    int part;
+    const ScanJob& j = scan_job(j0, j1, part);
+    const int len = scan_len(j.n, j.n_dev);
+    const int64_t chunk = part_chunk(len, j.nparts);
+    const int64_t a = (int64_t)part * chunk, b = a + chunk < len ? a + chunk : (int64_t)len;
+    const bool vec = (reinterpret_cast<uintptr_t>(j.in) & 15) == 0;
     long long s = 0;
     for (int64_t i = a + 4 * threadIdx.x; i < b; i += kPartTile) {
-        const int4 v = load4(in, i, b, vec);
+        const int4 v = load4(j.in, i, b, vec);
         s += (long long)v.x + v.y + v.z + v.w;
     }
     const long long t = block_sum(s);
-    if (threadIdx.x == 0) psum[blockIdx.x] = (int)t;
+    if (threadIdx.x == 0) j.psum[part] = (int)t;
 }
 
-__global__ void __launch_bounds__(kThreads) k_part_scan(const int* in, int* out, int64_t n, const int* n_dev,
-                                                         const int* __restrict__ psum, int nparts)
+__global__ void __launch_bounds__(kThreads) k_part_scan(ScanJob j0, ScanJob j1)
 {
     __shared__ int wsum[kThreads / 32];
     __shared__ int base;
-    const int len = scan_len(n, n_dev);
-    const int64_t chunk = part_chunk(len, nparts);
-    const int64_t a = (int64_t)blockIdx.x * chunk, b = a + chunk < len ? a + chunk : (int64_t)len;
+    int part;
+    const ScanJob& j = scan_job(j0, j1, part);
+    const int* in = j.in;
+    int* out = j.out;
+    const int len = scan_len(j.n, j.n_dev);
+    const int64_t chunk = part_chunk(len, j.nparts);
+    const int64_t a = (int64_t)part * chunk, b = a + chunk < len ? a + chunk : (int64_t)len;
     const bool vec = ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     long long o = 0;
-    for (int q = threadIdx.x; q < (int)blockIdx.x; q += kThreads) o += psum[q];
+    for (int q = threadIdx.x; q < part; q += kThreads) o += j.psum[q];
     const long long ot = block_sum(o);
     if (threadIdx.x == 0) base = (int)ot;
     __syncthreads();
@@ -220,7 +244,15 @@ __global__ void __launch_bounds__(kThreads) k_part_scan(const int* in, int* out,
         carry += all;
         __syncthreads();
     }
-    if (blockIdx.x == nparts - 1 && threadIdx.x == 0) out[len] = carry;
+    if (part == j.nparts - 1 && threadIdx.x == 0) out[len] = carry;
+}
+
+static ScanJob scan_job_for(const Context& c, const int* in, int* out, int64_t n, const int* n_dev, int* psum,
+                            int64_t cap)
+{
+    int64_t np = std::min<int64_t>(2 * (int64_t)c.num_sms, (n + kPartTile - 1) / kPartTile);
+    np = std::max<int64_t>(1, std::min<int64_t>(np, cap));
+    return ScanJob{in, out, n, n_dev, psum, (int)np};
 }
 
 // Exclusive prefix of in[0..len) into out[0..len], out[len] = total; len = *n_dev if given
@@ -228,11 +260,22 @@ __global__ void __launch_bounds__(kThreads) k_part_scan(const int* in, int* out,
 // them, and out[len] lies outside every part).
 void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n_dev)
 {
-    int64_t np = std::min<int64_t>(2 * (int64_t)c.num_sms, (n + kPartTile - 1) / kPartTile);
-    np = std::max<int64_t>(1, std::min<int64_t>(np, c.scan_tmp_cap));
-    const int nparts = (int)np;
-    k_part_sums<<<nparts, kThreads, 0, c.stream>>>(in, n, n_dev, c.scan_tmp, nparts);
-    k_part_scan<<<nparts, kThreads, 0, c.stream>>>(in, out, n, n_dev, c.scan_tmp, nparts);
+    const ScanJob j0 = scan_job_for(c, in, out, n, n_dev, c.scan_tmp, c.scan_tmp_cap);
+    const ScanJob none{nullptr, nullptr, 0, nullptr, nullptr, 0};
+    k_part_sums<<<j0.nparts, kThreads, 0, c.stream>>>(j0, none);
+    k_part_scan<<<j0.nparts, kThreads, 0, c.stream>>>(j0, none);
+}
+
+// Two independent exclusive scans in the same two launches (the part sums of the second one
+// after the first one's in the scratch)
+void exclusive_scan2(Context& c, const int* in0, int* out0, int64_t n0, const int* n_dev0, const int* in1,
+                     int* out1, int64_t n1, const int* n_dev1)
+{
+    const int64_t half = c.scan_tmp_cap / 2;
+    const ScanJob j0 = scan_job_for(c, in0, out0, n0, n_dev0, c.scan_tmp, half);
+    const ScanJob j1 = scan_job_for(c, in1, out1, n1, n_dev1, c.scan_tmp + j0.nparts, c.scan_tmp_cap - j0.nparts);
+    k_part_sums<<<j0.nparts + j1.nparts, kThreads, 0, c.stream>>>(j0, j1);
+    k_part_scan<<<j0.nparts + j1.nparts, kThreads, 0, c.stream>>>(j0, j1);
 }
 
 // ============================================================================ advance
@@ -964,8 +1007,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
                                                c.partials, c.max_blocks, clear_set(c));
     tune_mark(c, 1);
     prof_mark(c, 1);
-    exclusive_scan(c, c.newid, c.newid, c.max_rays, &c.ctl->n);
-    exclusive_scan(c, c.cnt, c.off, G.ncell_all, nullptr);
+    exclusive_scan2(c, c.newid, c.newid, c.max_rays, &c.ctl->n, c.cnt, c.off, G.ncell_all, nullptr);
     k_scatter<<<nb, kThreads, 0, s>>>(G, c.A, c.ctl, c.max_rays, c.info, c.ccell, c.cslot, c.newid, c.off, c.ent_id,
                                       c.ent_src, c.ent_cell);
     int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
