@@ -42,9 +42,10 @@ WORKLOAD = "sphere 256x128x90, background source 983040 ray volumes, dt 180 s, F
 FLOPS_PER_RAY_STEP = 1460.0
 # Peak rate of FP64-precision operations on GB300 (one operation per add or multiply): the kernel
 # runs them as double-float pairs on the FP32 pipes (152 SMs x 128 lanes x 2.07 GHz = 40.3 T FP32
-# instructions/s; a double-float add takes 11 FP32 instructions, a multiply 7, 9 on average ->
-# 4.48 T/s) besides the FP64 pipe (2 per clock per SM -> 0.63 T/s); together 5.1 T/s.
-FP64_EQ_PEAK_TOPS = 152 * 128 * 2.07e9 / 9.0 / 1e12 + 152 * 2 * 2.07e9 / 1e12
+# instructions/s; a double-float add takes 11 FP32 instructions, a multiply 4 (its pair is passed on
+# unrenormalised), 7.5 on average -> 5.37 T/s) besides the FP64 pipe (2 per clock per SM ->
+# 0.63 T/s); together 6.0 T/s.
+FP64_EQ_PEAK_TOPS = 152 * 128 * 2.07e9 / 7.5 / 1e12 + 152 * 2 * 2.07e9 / 1e12
 # Precision form: algorithmic bytes of the ray step = the 64-byte ray record read and written once.
 BYTES_PER_RAY_STEP_FP32 = 128.0
 # FP64 form, HBM view of the ray step: the 112-byte ray state read and written once (224 B) plus the
@@ -385,8 +386,8 @@ def gpu_arm(args, rank, world, local_rank):
                                       "k_advance_sphere_half_fp64.md) as a fraction of that launch's algorithmic "
                                       "bytes (ray state, gathers, field clearing), times this launch's",
                     "peak_source": "modelled (not measured) from unit counts and the 2.07 GHz clock: "
-                                   "FP64-precision operations as double-float on the FP32 pipes (4.48 T/s) plus "
-                                   "the FP64 pipe (0.63 T/s)",
+                                   "FP64-precision operations as double-float on the FP32 pipes (5.37 T/s at 7.5 "
+                                   "instructions each) plus the FP64 pipe (0.63 T/s)",
                     "flops_per_ray_step": FLOPS_PER_RAY_STEP,
                     "hbm": hbm_view,
                     "phase_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()}}
