@@ -74,14 +74,33 @@ __global__ void __launch_bounds__(256) k_smooth_df(Grid G, FieldSetDF fs, int f0
 #pragma unroll
         for (int q = 0; q < kRowsDF + 2; ++q) v[q] = (live && ok) ? src[q][o] : 0.0;
     };
-    auto sums = [&](const double (&r)[kRowsDF + 2], DF (&cs)[kRowsDF]) {
+    // Most cells receive no ray volume, so whole columns of a warp's 32 levels are +0.0: their sums
+    // are +0.0 without the splits and additions (the same bits), and an output whose three column
+    // sums are all +0.0 is stored as such.  The flags are warp-uniform (votes).
+    auto sums = [&](const double (&r)[kRowsDF + 2], DF (&cs)[kRowsDF]) -> bool {
+        bool zero = true;
+#pragma unroll
+        for (int q = 0; q < kRowsDF + 2; ++q) zero = zero && __double_as_longlong(r[q]) == 0;
+        if (__all_sync(0xffffffffu, zero)) {
+#pragma unroll
+            for (int q = 0; q < kRowsDF; ++q) cs[q] = df_f(0.0f);
+            return true;
+        }
         DF v[kRowsDF + 2];
 #pragma unroll
         for (int q = 0; q < kRowsDF + 2; ++q) v[q] = df_split(r[q]);
 #pragma unroll
         for (int q = 0; q < kRowsDF; ++q) cs[q] = df_add(df_add(v[q], df_pow2(v[q + 1], 2.0f)), v[q + 2]);
+        return false;
     };
-    auto emit = [&](int i, const DF (&cm)[kRowsDF], const DF (&c0)[kRowsDF], const DF (&cp)[kRowsDF]) {
+    auto emit = [&](int i, const DF (&cm)[kRowsDF], const DF (&c0)[kRowsDF], const DF (&cp)[kRowsDF], bool zero) {
+        if (zero) {
+            if (live)
+#pragma unroll
+                for (int q = 0; q < kRowsDF; ++q)
+                    if (q < nrow) O[q * orow + (int64_t)i * nlev] = make_float2(0.0f, 0.0f);
+            return;
+        }
         if (live) {
 #pragma unroll
             for (int q = 0; q < kRowsDF; ++q) {
@@ -97,15 +116,17 @@ __global__ void __launch_bounds__(256) k_smooth_df(Grid G, FieldSetDF fs, int f0
     double ra[kRowsDF + 2], rb[kRowsDF + 2];
     loadraw(i0 - 1, true, ra);
     loadraw(i0, true, rb);
-    sums(ra, cm);
+    bool zm = sums(ra, cm);
     loadraw(i0 + 1, true, ra);
-    sums(rb, c0);
+    bool z0 = sums(rb, c0);
 #pragma unroll 1
     for (int i = i0; i < i1; ++i) {
         double rn[kRowsDF + 2];
         loadraw(i + 2, i + 2 <= i1, rn);
-        sums(ra, cp);
-        emit(i, cm, c0, cp);
+        const bool zp = sums(ra, cp);
+        emit(i, cm, c0, cp, zm && z0 && zp);
+        zm = z0;
+        z0 = zp;
 #pragma unroll
         for (int q = 0; q < kRowsDF; ++q) {
             cm[q] = c0[q];
