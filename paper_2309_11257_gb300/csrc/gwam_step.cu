@@ -280,12 +280,11 @@ void exclusive_scan2(Context& c, const int* in0, int* out0, int64_t n0, const in
 
 // ============================================================================ advance
 
-// RK3 register q (and the extents) in shared memory: 27 (36) doubles of shared memory per thread
-constexpr bool kAdvanceQShared = true;
-constexpr bool kAdvanceExtShared = true;
-constexpr bool kAdvanceLateTail = true;   // P_x, P_y, P_z, N loaded after the RK3 stages
-constexpr int kAdvanceRkSlots = kAdvanceQShared ? (kAdvanceExtShared ? 36 : 27) : 18;
-// and six more per thread: the exit / invalid action sums and four counters
+// Shared memory of k_advance, per thread (slots kThreads apart): the RK3 state, increment sums,
+// low-storage register and the extents' double-float copy (36 doubles, rk3<true, true>), then the
+// exit / invalid action sums and four counters (6) -- out of the 128 registers the ray equations
+// need at two blocks per SM (no spills)
+constexpr int kAdvanceRkSlots = 36;
 constexpr size_t kAdvanceSmem = sizeof(double) * (kAdvanceRkSlots + 6) * kThreads;
 
 __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySoA A, const NodeDF* __restrict__ bg,
@@ -307,31 +306,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_advance(Grid G, Params P, RaySo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s[NSTATE];
         long long id;
-        if (kAdvanceLateTail) {
-            // the nine propagated components and the id (its member selects the background) now;
-            // P_x, P_y, P_z and N, which the stages do not touch, after them: out of the registers the
-            // ray equations need
+        // the nine propagated components and the id (its member selects the background) now;
+        // P_x, P_y, P_z and N, which the stages do not touch, after them: out of the registers the
+        // ray equations need
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const double2 v = __ldg(&A.a[q][i]);
-                s[2 * q] = v.x;
-                s[2 * q + 1] = v.y;
-            }
-            s[SEZ] = __ldg(reinterpret_cast<const double*>(&A.a[4][i]));
-            id = __ldg(reinterpret_cast<const long long*>(&A.a[6][i]) + 1);
-        } else {
-            load_ray(A, i, s, id);
+        for (int q = 0; q < 4; ++q) {
+            const double2 v = __ldg(&A.a[q][i]);
+            s[2 * q] = v.x;
+            s[2 * q + 1] = v.y;
         }
+        s[SEZ] = __ldg(reinterpret_cast<const double*>(&A.a[4][i]));
+        id = __ldg(reinterpret_cast<const long long*>(&A.a[6][i]) + 1);
         const int mem = member_of(id);
         const NodeDF* bgm = bg + (int64_t)mem * G.ncell;
-        rk3<kAdvanceQShared, kAdvanceQShared && kAdvanceExtShared>(G, bgm, s, dt, sh_state + threadIdx.x);
-        if (kAdvanceLateTail) {
-            s[SPX] = __ldg(reinterpret_cast<const double*>(&A.a[4][i]) + 1);
+        rk3<true, true>(G, bgm, s, dt, sh_state + threadIdx.x);
+        s[SPX] = __ldg(reinterpret_cast<const double*>(&A.a[4][i]) + 1);
+        {
             const double2 v = __ldg(&A.a[5][i]);
             s[SPY] = v.x;
             s[SPZ] = v.y;
-            s[SN] = __ldg(reinterpret_cast<const double*>(&A.a[6][i]));
         }
+        s[SN] = __ldg(reinterpret_cast<const double*>(&A.a[6][i]));
         wrap_position(G, s);
         const int st = ray_status(G, s);
         int code = 0, nch = 0;
