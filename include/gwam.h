@@ -328,6 +328,16 @@ int gwam_selftest_split(const double *x, int64_t n, float *hi, float *lo, void *
  * when a == b).  Device pointers; synchronises `stream`. */
 int gwam_selftest_logratio(const double *a, const double *b, int64_t n, double *out, void *stream);
 
+/* Self-test of the step's exclusive scans (the re-binning's new-id and per-cell offsets, App. B.2
+ * parent-cell storage): out0[i] = in0[0] + ... + in0[i-1] for i <= n0 (out0[n0] = the total), by
+ * the context's two-pass scan over contiguous parts; with in1 != NULL a second, independent scan of
+ * in1[0..n1) into out1 runs in the same two launches (as the step pairs its two scans).  Device
+ * int32 arrays of any alignment (16-byte-aligned ones take the vector path); in == out is allowed;
+ * out must hold n + 1 values; totals must fit in int32.  Runs on the context's stream and
+ * synchronises it.  GWAM_EINVAL for negative sizes or missing arrays. */
+int gwam_selftest_scan(gwam_ctx *ctx, const int32_t *in0, int32_t *out0, int64_t n0, const int32_t *in1,
+                       int32_t *out1, int64_t n1);
+
 /* Self-test of the surrogate's tensor-core GEMM (tcgen05 + TMA, sm_103a): C = act(A . B^T + bias)
  * with A [M][K] and B [N][K] row-major BF16 device arrays (K contiguous, K a multiple of 64, base
  * addresses 16-byte aligned), bias [N] FP32 or NULL, act = GELU(z) = z Phi(z) when gelu != 0, C

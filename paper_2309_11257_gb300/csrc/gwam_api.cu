@@ -1333,6 +1333,19 @@ int gwam_graph_profile_read(gwam_ctx* ctx, double* ms_host, int* replays)
     API_END
 }
 
+int gwam_selftest_scan(gwam_ctx* ctx, const int32_t* in0, int32_t* out0, int64_t n0, const int32_t* in1,
+                       int32_t* out1, int64_t n1)
+{
+    API_BEGIN(ctx)
+    if (!in0 || !out0 || n0 < 0 || n0 > INT32_MAX - 1 || (in1 && (!out1 || n1 < 0 || n1 > INT32_MAX - 1)))
+        return GWAM_EINVAL;
+    if (in1) exclusive_scan2(c, in0, out0, n0, nullptr, in1, out1, n1, nullptr);
+    else exclusive_scan(c, in0, out0, n0, nullptr);
+    GWAM_CUDA(cudaStreamSynchronize(c.stream));
+    GWAM_CUDA(cudaGetLastError());
+    API_END
+}
+
 int gwam_graph_kernel_count(gwam_ctx* ctx, int* kernels)
 {
     API_BEGIN(ctx)

@@ -149,6 +149,7 @@ SIGNATURES = {
     "gwam_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int64)]),
     "gwam_graph_profile_read": (C.c_int, [_vp, _vp, _P(C.c_int)]),
     "gwam_graph_kernel_count": (C.c_int, [_vp, _P(C.c_int)]),
+    "gwam_selftest_scan": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, C.c_int64]),
     "gwam_last_error": (C.c_char_p, [_vp]),
     "gwam_version": (C.c_char_p, []),
 }
@@ -406,6 +407,11 @@ class Tracer:
         n = C.c_int()
         self._check(_lib.gwam_graph_profile_read(self._h, ms.ctypes.data_as(_vp), C.byref(n)), "graph_profile_read")
         return dict(zip(self.PHASES, ms.tolist())), n.value
+
+    def selftest_scan(self, in0, out0, n0, in1=None, out1=None, n1=0):
+        """Exclusive scans of device int32 arrays by the step's scan kernels (pointers as ints)."""
+        self._check(_lib.gwam_selftest_scan(self._h, _vp(in0), _vp(out0), int(n0), _vp(in1) if in1 else None,
+                                            _vp(out1) if out1 else None, int(n1)), "selftest_scan")
 
     def graph_kernel_count(self):
         """Kernel launches per step-graph replay, counted from the captured graph."""
