@@ -141,3 +141,46 @@ def test_autotune_keeps_parity(gw):
     T.step_graph(300.0, du, dv)
     oout = [O.step(300.0) for O in Os]
     _compare_members(T, Os, du.cpu().numpy(), dv.cpu().numpy(), oout)
+
+
+def test_precision_form_members_track_their_oracles(gw):
+    """The precision form with members: each member's drag against its own FP64 oracle within the
+    precision form's bars (column-scaled 1e-4), its live count within 0.5 %, the summed wave action
+    within 1e-5 (member-major arrays, the fields of all members cleared by the ray-step kernel)."""
+    import torch
+    M = 2
+    bgs, specs = _members(M), _specs(M)
+    p32 = dict(PARAMS, precision=1)
+    T = gw.Tracer(GRID, p32, max_rays=400000, members=M)
+    for m in range(M):
+        T.set_member_background(m, *[torch.from_numpy(a.copy()).cuda() for a in bgs[m]])
+    src = synth.background_source(z_launch=2e3)
+    T.launch_sources(src)
+    T.launch_spectral(np.concatenate(specs))
+    Os = []
+    for m in range(M):
+        O = oracle.Model(GRID, PARAMS)
+        O.set_background(*bgs[m])
+        O.launch_background(src)
+        O.launch_spectral(specs[m])
+        Os.append(O)
+    shape = (M, GRID["nz"], GRID["ny"], GRID["nx"])
+    du = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    dv = torch.zeros_like(du)
+    for _ in range(5):
+        T.step_graph(300.0, du, dv)
+        oout = [O.step(300.0) for O in Os]
+    g = T.rays()
+    col = lambda S: np.broadcast_to(S.max(axis=0, keepdims=True), S.shape)
+    for m in range(M):
+        n_g = int((g["member"] == m).sum())
+        n_o = len(Os[m].rays()["id"])
+        assert abs(n_g - n_o) <= 0.005 * max(n_o, 200), (m, n_g, n_o)
+        su, sv = Os[m].tendency_scale()
+        e_u = scaled_error(du[m].cpu().numpy(), oout[m][0], col(su))
+        e_v = scaled_error(dv[m].cpu().numpy(), oout[m][1], col(sv))
+        assert e_u <= 1e-4 and e_v <= 1e-4, (m, e_u, e_v)
+        assert np.abs(oout[m][0]).max() > 0.0
+    w = sum(O.stats()["w_total"] for O in Os)
+    assert abs(T.stats()["w_total"] - w) <= 1e-5 * abs(w)
+
