@@ -86,8 +86,55 @@ def measured_peaks():
 
 # ------------------------------------------------------------------------------------- clocks
 
+class _Nvml:
+    """The driver's NVML library through ctypes (read-only queries): SM clock, its maximum, and the
+    active clock-event reasons of one GPU; None where the library is missing."""
+
+    SM = 1   # NVML_CLOCK_SM
+    REASONS = (("sw_power_cap", 0x4), ("hw_slowdown", 0x8), ("sw_thermal_slowdown", 0x20),
+               ("hw_thermal_slowdown", 0x40))
+
+    @classmethod
+    def open(cls, index: int):
+        import ctypes
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return None
+            dev = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(dev)) != 0:
+                return None
+            self = cls()
+            self.ct, self.lib, self.dev = ctypes, lib, dev
+            self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+            mx = ctypes.c_uint()
+            self.max_mhz = float(mx.value) if lib.nvmlDeviceGetMaxClockInfo(dev, cls.SM, ctypes.byref(mx)) == 0 else None
+            return self
+        except Exception:
+            return None
+
+    def sample(self):
+        ct = self.ct
+        clk = ct.c_uint()
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, self.SM, ct.byref(clk)) != 0:
+            return None
+        mask = ct.c_ulonglong(0)
+        if self.reasons_fn is not None:
+            self.reasons_fn(self.dev, ct.byref(mask))
+        return float(clk.value), int(mask.value)
+
+    def close(self):
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
-    """nvidia-smi clocks/throttle reasons sampled every 200 ms while the timed region runs."""
+    """SM clock and clock-event reasons sampled while the timed region runs: from NVML every
+    millisecond (the samples of the region itself: settle() drops those taken before it), else
+    from nvidia-smi every 200 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -97,8 +144,17 @@ class ClockSampler:
         self.index = index
         self.lines = []
         self.proc = None
+        self.nvml = None
+        self.samples = []
+        self.running = False
 
     def start(self):
+        self.nvml = _Nvml.open(self.index)
+        if self.nvml is not None:
+            self.running = True
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -108,11 +164,34 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
+    def settle(self):
+        """Call right before the timed region."""
+        if self.nvml is not None:
+            time.sleep(0.05)
+            self.samples.clear()
+        else:
+            time.sleep(0.3)
+
+    def _poll(self):
+        while self.running:
+            v = self.nvml.sample()
+            if v is not None:
+                self.samples.append(v)
+            time.sleep(0.001)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.running = False
+            self.t.join(timeout=2)
+            self.nvml.close()
+            sm = [c for c, _ in self.samples]
+            reasons = sorted({nm for _, m in self.samples for nm, bit in _Nvml.REASONS if m & bit})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.nvml.max_mhz,
+                    "reasons": reasons, "samples": len(sm), "source": "NVML every 1 ms during the timed region"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -136,7 +215,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi every 200 ms"}
 
 
 # ------------------------------------------------------------------------------------- oracle arm
@@ -293,7 +372,7 @@ def gpu_arm(args, rank, world, local_rank):
     s0 = T.stats()
     sampler = ClockSampler(local_rank)
     sampler.start()
-    time.sleep(0.3)
+    sampler.settle()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -494,7 +573,7 @@ def ensemble_arm(args):
     s0 = T.stats()
     sampler = ClockSampler(0)
     sampler.start()
-    time.sleep(0.3)
+    sampler.settle()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -587,7 +666,7 @@ def surrogate_arm(args):
     S.profile(True)
     sampler = ClockSampler(0)
     sampler.start()
-    time.sleep(0.3)
+    sampler.settle()
     torch.cuda.synchronize()
     tot = 0.0
     for _ in range(args.steps):
