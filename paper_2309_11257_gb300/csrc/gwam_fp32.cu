@@ -372,7 +372,10 @@ __global__ void __launch_bounds__(kThreads) k_advance32(Grid G, Params P, Ray32S
             nch = num_children(code);
             if (code & 1) ++n_sv;
             if (code & 2) n_sh += (code & 1) ? 2 : 1;
-            for (int c = 0; c < nch; ++c) {
+            // unrolled with a guard, not bounded by nch: cc and sl stay in registers
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c >= nch) break;
                 S32 ch;
                 if (make_child32(G, s, code, c, ch) != 0) {
                     ++n_exit;

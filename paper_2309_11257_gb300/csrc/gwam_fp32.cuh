@@ -276,8 +276,6 @@ __device__ __forceinline__ void rhs32(const Grid& G, const Node32* __restrict__ 
 
 __device__ __forceinline__ void rk3_32(const Grid& G, const Node32* __restrict__ bg, S32& s, float dt)
 {
-    const float A[3] = {0.0f, -5.0f / 9.0f, -153.0f / 128.0f};
-    const float B[3] = {1.0f / 3.0f, 15.0f / 16.0f, 8.0f / 15.0f};
     float y[9] = {s.o[0], s.o[1], s.o[2], s.w[0], s.w[1], s.w[2], s.e[0], s.e[1], s.e[2]};
     float q[9];
 #pragma unroll
@@ -286,10 +284,14 @@ __device__ __forceinline__ void rk3_32(const Grid& G, const Node32* __restrict__
     for (int st = 0; st < 3; ++st) {
         float F[9];
         rhs32(G, bg, s, y, F);
+        // the stage's coefficients selected, not indexed (an array indexed by the rolled stage
+        // counter would live in local memory, whose loads share L1 with the gathers)
+        const float a = st == 0 ? 0.0f : (st == 1 ? -5.0f / 9.0f : -153.0f / 128.0f);
+        const float b = st == 0 ? 1.0f / 3.0f : (st == 1 ? 15.0f / 16.0f : 8.0f / 15.0f);
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            q[c] = A[st] * q[c] + dt * F[c];
-            y[c] += B[st] * q[c];
+            q[c] = a * q[c] + dt * F[c];
+            y[c] += b * q[c];
         }
     }
 #pragma unroll
@@ -364,19 +366,25 @@ __device__ __forceinline__ int make_child32(const Grid& G, const S32& p, int cod
     s = p;
     if (!code) return 0;
     const int nv = (code & 1) ? 2 : 1;
-    const float inv[3] = {G.f_inv_dX, G.f_inv_dY, G.f_inv_dz};
     if (code & 1) {
         const bool plus = (c % nv) == 1;
-        s.o[2] += (plus ? 0.25f : -0.25f) * s.e[2] * inv[2];
+        s.o[2] += (plus ? 0.25f : -0.25f) * s.e[2] * G.f_inv_dz;
         s.e[2] *= 0.5f;
         s.p[2] *= 0.5f;
     }
+    // the halved horizontal axis by branch, not by index: a state indexed at run time would be
+    // kept in local memory
     if (code & 2) {
-        const int ax = (code & 4) ? 1 : 0;
-        const bool plus = (c / nv) == 1;
-        s.o[ax] += (plus ? 0.25f : -0.25f) * s.e[ax] * inv[ax];
-        s.e[ax] *= 0.5f;
-        s.p[ax] *= 0.5f;
+        const float h = (c / nv) == 1 ? 0.25f : -0.25f;
+        if (code & 4) {
+            s.o[1] += h * s.e[1] * G.f_inv_dY;
+            s.e[1] *= 0.5f;
+            s.p[1] *= 0.5f;
+        } else {
+            s.o[0] += h * s.e[0] * G.f_inv_dX;
+            s.e[0] *= 0.5f;
+            s.p[0] *= 0.5f;
+        }
     }
     return renormalize32(G, s);
 }
