@@ -754,16 +754,14 @@ def launches_per_step(params, fp32=False) -> int:
     that scan the new-id and per-cell counts together, scatter, segment sort, materialise, project,
     divergence, budget fold; the cap's find, apply and scan; the saturation's run list and kappa; in
     the FP64 form the smoothing, or without smoothing the split of the fields into double-float
-    pairs; in the precision form the narrowing pass and the smoothing."""
+    pairs; in the precision form the smoothing (which narrows the FP64 fields as it reads them), or
+    without smoothing the narrowing pass."""
     n = 1 + 1 + 2 + 1 + 1 + 1 + 1 + 1 + 1
     if params.get("cap_per_column", 0) > 0:
         n += 2 + 2
     if params.get("saturation", 0):
         n += 2
-    if fp32:
-        n += 1 + (1 if params.get("smoothing", 0) else 0)
-    else:
-        n += 1
+    n += 1
     return n
 
 

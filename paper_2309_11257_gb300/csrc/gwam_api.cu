@@ -369,7 +369,8 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         c.scan_tmp_cap = (int64_t)scan_blocks + 1;
         if (c.f32) {
             for (int f = 0; f < NFIELD; ++f) {
-                dalloc(c, c.nar32[f], (size_t)c.field_len(f));
+                // the narrowed raw fields only without smoothing (the smoothing narrows as it loads)
+                if (!c.P.smoothing) dalloc(c, c.nar32[f], (size_t)c.field_len(f));
                 dalloc(c, c.sm32[f], (size_t)c.field_len(f));
             }
             dalloc(c, c.rho_inv32, ncell);

@@ -53,18 +53,20 @@ __device__ __forceinline__ float narrow_general(double x)
     return __uint_as_float(sign | r);
 }
 
-// Fast path of narrow for the usual case -- the result is a normal float or rounds up to infinity
-// -- with 32-bit operations on the two words of the double; everything else takes narrow_general.
+// Fast path of narrow for the usual cases -- the result is a normal float or rounds up to infinity,
+// or x has a zero exponent field (zeros and FP64 subnormals, far below the float range: a signed
+// zero) -- with 32-bit operations on the two words of the double and no branch between them;
+// everything else takes narrow_general.  The zeros are folded in because projected fields are
+// mostly empty cells: a warp mixing zeros and nonzeros would otherwise run both paths.
 __device__ __forceinline__ float narrow(double x)
 {
     const uint32_t hw = (uint32_t)__double2hiint(x), lw = (uint32_t)__double2loint(x);
     const uint32_t e = (hw >> 20) & 0x7FFu;
-    if (e - 897u < 254u) {                      // float exponent 1 .. 254
-        uint32_t r = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
-        const uint32_t rem = lw & 0x1FFFFFFFu;  // the 29 dropped bits
-        r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
-        return __uint_as_float((hw & 0x80000000u) | r);
-    }
+    uint32_t r = (((hw & 0x7FFFFFFFu) - (896u << 20)) << 3) | (lw >> 29);
+    const uint32_t rem = lw & 0x1FFFFFFFu;      // the 29 dropped bits
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    const bool normal = e - 897u < 254u;        // float exponent 1 .. 254
+    if (normal || e == 0u) return __uint_as_float((hw & 0x80000000u) | (normal ? r : 0u));
     return narrow_general(x);
 }
 

@@ -49,23 +49,32 @@ void convert_background32(Context& c, int member)
 // ---------------------------------------------------------------------------- FP32 grid phase
 // The precision form keeps the projection sums (and the saturation sums and the budget) in FP64;
 // smoothing and divergence run in FP32: GB300's FP64 rate is 1/64 of its FP32 rate, and these
-// stencils would otherwise be bound by it.  The projected FP64 fields are narrowed once, smoothed
-// and differenced in FP32, and du/dt, dv/dt widened to the caller's FP64 on the way out.
+// stencils would otherwise be bound by it.  The smoothing reads the projected FP64 fields and
+// narrows them as it loads (no FP32 copy of the raw fields is written and read back); without
+// smoothing the fields are narrowed once by k_narrow.  du/dt, dv/dt are widened to the caller's
+// FP64 on the way out.
 
+template <typename T>
 struct FieldSet32 {
-    const float* in[NFIELD];
+    const T* in[NFIELD];
     float* out[NFIELD];
 };
+
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return narrow(x); }
 
 // separable 1-2-1 x 1-2-1 smoothing (periodic in lambda, edge row reused at the poles).  A warp
 // owns 32 consecutive levels of kRows32 rows over a run of kSpan columns and slides a 3 x 3 window
 // along the rows: each new column costs kRows32 + 2 loads (the rows and their two neighbours) for
-// kRows32 outputs, and the column sums of the previous two columns stay in registers (two rows over
-// spans of 32 columns: measured faster than one row, or spans of 16 or 64).  Warp item = (field,
-// member, row group, level group, span).
+// kRows32 outputs, and the column sums of the previous two columns stay in registers.  All loads of
+// a pass (two columns) are issued before any of them is converted.  Three rows over spans of 32
+// columns, reading the FP64 fields: 5/3 loads per output, measured faster than two, four or six
+// rows or spans of 16 (more rows hold more registers).  Warp item = (field, member, row group,
+// level group, span).
 constexpr int kSpan = 32;
-constexpr int kRows32 = 2;
-__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, int f0, int nf)
+constexpr int kRows32 = 3;
+template <typename T>
+__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32<T> fs, int f0, int nf)
 {
     const int lane = threadIdx.x & 31;
     const int nlg = (G.nz + 1 + 31) / 32;                   // level groups (interface fields have nz + 1)
@@ -90,9 +99,9 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     const int j0 = rg * kRows32;
     const int nrow = min(kRows32, G.ny - j0);
     const int64_t base = (int64_t)mem * G.ncol;
-    const float* __restrict__ F = fs.in[f];
+    const T* __restrict__ F = fs.in[f];
     // source rows j0 - 1 .. j0 + kRows32 (clamped at the poles, wrapped on the f-plane)
-    const float* src[kRows32 + 2];
+    const T* src[kRows32 + 2];
 #pragma unroll
     for (int q = 0; q < kRows32 + 2; ++q) {
         int jj = j0 - 1 + q;
@@ -103,13 +112,22 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     float* O = fs.out[f] + (base + (int64_t)j0 * G.nx) * nlev + lev;
     const int64_t orow = (int64_t)G.nx * nlev;
     // vertical 1-2-1 column sums of the kRows32 rows at column i
-    auto colsums = [&](int i, float (&cs)[kRows32]) {
-        float v[kRows32 + 2];
+    auto loadcol = [&](int i, T (&raw)[kRows32 + 2]) {
         const int64_t o = (int64_t)i * nlev;
 #pragma unroll
-        for (int q = 0; q < kRows32 + 2; ++q) v[q] = live ? src[q][o] : 0.0f;
+        for (int q = 0; q < kRows32 + 2; ++q) raw[q] = live ? __ldg(src[q] + o) : T(0);
+    };
+    auto sums = [&](const T (&raw)[kRows32 + 2], float (&cs)[kRows32]) {
+        float v[kRows32 + 2];
+#pragma unroll
+        for (int q = 0; q < kRows32 + 2; ++q) v[q] = to_f32(raw[q]);
 #pragma unroll
         for (int q = 0; q < kRows32; ++q) cs[q] = v[q] + 2.0f * v[q + 1] + v[q + 2];
+    };
+    auto colsums = [&](int i, float (&cs)[kRows32]) {
+        T raw[kRows32 + 2];
+        loadcol(i, raw);
+        sums(raw, cs);
     };
     const int i0 = sp * kSpan, i1 = min(G.nx, i0 + kSpan);
     float cm[kRows32], c0[kRows32], cp[kRows32], cq[kRows32];
@@ -118,8 +136,13 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, 
     int i = i0;
     // two columns per pass with their loads issued together
     for (; i + 2 <= i1; i += 2) {
-        colsums(i + 1 == G.nx ? 0 : i + 1, cp);
-        colsums(i + 2 >= G.nx ? i + 2 - G.nx : i + 2, cq);
+        {
+            T ra[kRows32 + 2], rb[kRows32 + 2];
+            loadcol(i + 1 == G.nx ? 0 : i + 1, ra);
+            loadcol(i + 2 >= G.nx ? i + 2 - G.nx : i + 2, rb);
+            sums(ra, cp);
+            sums(rb, cq);
+        }
         if (live) {
 #pragma unroll
             for (int q = 0; q < kRows32; ++q) {
@@ -294,11 +317,12 @@ static void narrow_fields(Context& c, int f0, int f1)
     k_narrow<<<dim3((unsigned)blocks, (unsigned)(f1 - f0)), kThreads, 0, c.stream>>>(ns);
 }
 
+// the projected FP64 fields f0 .. f1-1, smoothed into their FP32 copies
 static void smooth32(Context& c, int f0, int f1)
 {
-    FieldSet32 fs{};
+    FieldSet32<double> fs{};
     for (int f = 0; f < NFIELD; ++f) {
-        fs.in[f] = c.nar32[f];
+        fs.in[f] = c.field[f];
         fs.out[f] = c.sm32[f];
     }
     const long long warps = (long long)(f1 - f0) * c.G.members * ((c.G.ny + kRows32 - 1) / kRows32) *
@@ -308,7 +332,6 @@ static void smooth32(Context& c, int f0, int f1)
 
 void smooth_field32(Context& c, int f)
 {
-    narrow_fields(c, f, f + 1);
     smooth32(c, f, f + 1);
     // widened into the FP64 smoothed copy the field readers use
     const int blocks = (int)std::min<int64_t>((c.field_len(f) + kThreads - 1) / kThreads, 8192);
@@ -321,11 +344,12 @@ static void grid_phase32(Context& c, double* du, double* dv, int mask)
     cudaStream_t s = c.stream;
     double* out_u = du ? du : c.dudt_buf;
     double* out_v = dv ? dv : c.dvdt_buf;
-    narrow_fields(c, 0, F_WAD);
-    float* const* fl = c.nar32;
+    float* const* fl = c.sm32;
     if (c.P.smoothing) {
         smooth32(c, 0, F_WAD);
-        fl = c.sm32;
+    } else {
+        narrow_fields(c, 0, F_WAD);
+        fl = c.nar32;
     }
     const int TW = G.nz <= 96 ? 32 : 16;
     const size_t shm = sizeof(float) * (2 * (size_t)TW * G.nz + G.nz);
