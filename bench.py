@@ -69,11 +69,11 @@ def clear_bytes(nx, ny, nz, theta=False):
 
 # DRAM bytes (read + write) of one launch in the ncu captures in profiles/, as a fraction of that
 # launch's algorithmic bytes (ray bytes x 253 952 rays + the clearing of the 128 x 64 x 90 fields):
-# k_advance 67.75 MB of 134.48 MB, k_advance32 53.95 MB of 85.72 MB (written field lines still in L2
+# k_advance 67.75 MB of 134.48 MB, k_advance32 40.77 MB of 85.72 MB (written field lines still in L2
 # when the kernel ends are not counted).  The bench's traffic is that fraction of its own launch's
 # algorithmic bytes; None while the kernel has changed since its counters were taken.
 ADV_TRAFFIC_FRACTION = 67.75 / 134.48
-ADV32_TRAFFIC_FRACTION = 53.95 / 85.72
+ADV32_TRAFFIC_FRACTION = 40.77 / 85.72
 
 
 def measured_peaks():

@@ -881,20 +881,38 @@ void launch_smooth(Context& c, int nf)
 
 // ============================================================================ budget, control
 
-// Fold the per-block partials of the slots in `mask` (block order: deterministic) into the
-// budget; mode 1 also closes a step (live count, ids, step counter).
+// Fold the per-block partials of the slots in `mask` into the budget (a fixed order:
+// deterministic); mode 1 also closes a step (live count, ids, step counter).  One warp per slot,
+// the slots side by side: lane l sums partials l, l + 32, ... of its slot, kFinUnroll loads issued
+// before they are added, then the lane sums by a fixed shuffle tree.  (A block looping over the
+// slots one after another, each ending in a block reduction, chained about 30 memory latencies:
+// 20 us a step.)
+constexpr int kFinUnroll = 16;
+static_assert(NTALLY * 32 <= kThreads, "k_finalize runs one warp per tally slot");
 __global__ void k_finalize(Ctl* ctl, DevBudget* bud, const double* __restrict__ partials, int nb, int mask, int mode)
 {
     __shared__ double acc[NTALLY];
-    for (int s = 0; s < NTALLY; ++s) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < NTALLY) {
         double v = 0.0;
-        if (mask & (1 << s))
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[s * nb + b];
-        // fixed-order block reduction
-        const double t = block_sum(v);
-        if (threadIdx.x == 0) acc[s] = t;
-        __syncthreads();
+        if (mask & (1 << w)) {
+            const double* __restrict__ p = partials + (int64_t)w * nb;
+            for (int b0 = 0; b0 < nb; b0 += 32 * kFinUnroll) {
+                double t[kFinUnroll];
+#pragma unroll
+                for (int u = 0; u < kFinUnroll; ++u) {
+                    const int b = b0 + u * 32 + lane;
+                    t[u] = b < nb ? p[b] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < kFinUnroll; ++u) v += t[u];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) acc[w] = v;
     }
+    __syncthreads();
     if (threadIdx.x != 0) return;
     if (mask & (1 << T_EXIT)) bud->w_exited += acc[T_EXIT];
     if (mask & (1 << T_INVALID)) bud->w_invalid += acc[T_INVALID];
