@@ -128,7 +128,12 @@ void scan_with_scratch(const int* in, int* out, int64_t n, int* bsum, cudaStream
 // part; k_part_scan adds up the sums of the parts before its own and scans its part tile by tile
 // (one int4 of items per thread, warp shuffles, a carry across tiles).  Few, long parts instead of
 // one block per 2048 items: no third kernel to scan the block sums, and no launch of ~1400 blocks.
+// Both passes take kPartGroup tiles at a time with all their loads issued first (one tile at a
+// time left a single 16-byte load per thread in flight, about half the HBM rate), and the scan
+// combines the group's tiles in one block-wide step (the warps' scans interleaved, two barriers per
+// group).
 constexpr int kPartTile = 4 * kThreads;
+constexpr int kPartGroup = 4;
 
 __device__ __forceinline__ int64_t part_chunk(int len, int nparts)
 {
@@ -189,9 +194,12 @@ __global__ void __launch_bounds__(kThreads) k_part_sums(ScanJob j0, ScanJob j1)
     const int64_t a = (int64_t)part * chunk, b = a + chunk < len ? a + chunk : (int64_t)len;
     const bool vec = (reinterpret_cast<uintptr_t>(j.in) & 15) == 0;
     long long s = 0;
-    for (int64_t i = a + 4 * threadIdx.x; i < b; i += kPartTile) {
-        const int4 v = load4(j.in, i, b, vec);
-        s += (long long)v.x + v.y + v.z + v.w;
+    for (int64_t i = a + 4 * threadIdx.x; i < b; i += kPartTile * kPartGroup) {
+        int4 v[kPartGroup];
+#pragma unroll
+        for (int u = 0; u < kPartGroup; ++u) v[u] = load4(j.in, i + u * kPartTile, b, vec);
+#pragma unroll
+        for (int u = 0; u < kPartGroup; ++u) s += (long long)v[u].x + v[u].y + v[u].z + v[u].w;
     }
     const long long t = block_sum(s);
     if (threadIdx.x == 0) j.psum[part] = (int)t;
@@ -199,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_part_sums(ScanJob j0, ScanJob j1)
 
 __global__ void __launch_bounds__(kThreads) k_part_scan(ScanJob j0, ScanJob j1)
 {
-    __shared__ int wsum[kThreads / 32];
+    __shared__ int wsum[kPartGroup][kThreads / 32];
     __shared__ int base;
     int part;
     const ScanJob& j = scan_job(j0, j1, part);
@@ -216,32 +224,48 @@ __global__ void __launch_bounds__(kThreads) k_part_scan(ScanJob j0, ScanJob j1)
     __syncthreads();
     int carry = base;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int64_t t0 = a; t0 < b; t0 += kPartTile) {
-        const int64_t i = t0 + 4 * threadIdx.x;
-        const int4 v = load4(in, i, b, vec);
-        const int tot = v.x + v.y + v.z + v.w;
-        int incl = tot;
+    for (int64_t t0 = a; t0 < b; t0 += kPartTile * kPartGroup) {
+        // tile u of the group: items t0 + u * kPartTile .. ; all of them read before any is written
+        // (in place, each item is written by the thread that read it)
+        int4 v[kPartGroup];
+        int tot[kPartGroup], incl[kPartGroup];
+#pragma unroll
+        for (int u = 0; u < kPartGroup; ++u) v[u] = load4(in, t0 + u * kPartTile + 4 * threadIdx.x, b, vec);
+#pragma unroll
+        for (int u = 0; u < kPartGroup; ++u) {
+            tot[u] = v[u].x + v[u].y + v[u].z + v[u].w;
+            incl[u] = tot[u];
+        }
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += u;
-        }
-        if (lane == 31) wsum[wid] = incl;
-        __syncthreads();
-        int before = 0, all = 0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const int x = wsum[w];
-            before += w < wid ? x : 0;
-            all += x;
+            for (int u = 0; u < kPartGroup; ++u) {
+                const int x = __shfl_up_sync(0xffffffffu, incl[u], d);
+                if (lane >= d) incl[u] += x;
+            }
         }
-        int4 r;
-        r.x = carry + before + incl - tot;
-        r.y = r.x + v.x;
-        r.z = r.y + v.y;
-        r.w = r.z + v.z;
-        store4(out, i, b, vec, r);
-        carry += all;
+        if (lane == 31) {
+#pragma unroll
+            for (int u = 0; u < kPartGroup; ++u) wsum[u][wid] = incl[u];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPartGroup; ++u) {
+            int before = 0, all = 0;
+#pragma unroll
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const int x = wsum[u][w];
+                before += w < wid ? x : 0;
+                all += x;
+            }
+            int4 r;
+            r.x = carry + before + incl[u] - tot[u];
+            r.y = r.x + v[u].x;
+            r.z = r.y + v[u].y;
+            r.w = r.z + v[u].z;
+            store4(out, t0 + u * kPartTile + 4 * threadIdx.x, b, vec, r);
+            carry += all;
+        }
         __syncthreads();
     }
     if (part == j.nparts - 1 && threadIdx.x == 0) out[len] = carry;
