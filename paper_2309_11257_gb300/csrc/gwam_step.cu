@@ -523,7 +523,20 @@ __global__ void k_segsort(Grid G, Ctl* ctl, const int* __restrict__ off, const i
         const int a = off[c], b = off[c + 1];
         const long long id = ent_id[e];
         int rank = 0;
-        for (int q = a; q < b; ++q) rank += (ent_src[q] >= 0) && (ent_id[q] < id);
+        int q = a;
+        // four entries per pass, their loads issued together
+        for (; q + 4 <= b; q += 4) {
+            int sv[4];
+            long long iv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                sv[u] = ent_src[q + u];
+                iv[u] = ent_id[q + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) rank += (sv[u] >= 0) && (iv[u] < id);
+        }
+        for (; q < b; ++q) rank += (ent_src[q] >= 0) && (ent_id[q] < id);
         sorted_src[off2[c] + rank] = src;
     }
 }
