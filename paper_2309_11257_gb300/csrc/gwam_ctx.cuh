@@ -230,7 +230,9 @@ void exclusive_scan(Context& c, const int* in, int* out, int64_t n, const int* n
 void exclusive_scan2(Context& c, const int* in0, int* out0, int64_t n0, const int* n_dev0, const int* in1,
                      int* out1, int64_t n1, const int* n_dev1);
 int scan_block_count(int64_t n);
-void scan_with_scratch(const int* in, int* out, int64_t n, int* bsum, cudaStream_t s);
+// histogram of the cells + exclusive scan (the two offsets entry points); each launch's own status
+cudaError_t launch_cell_offsets(const int32_t* cells, int64_t n, int32_t ncell, int* counts, int* scratch, int* flag,
+                                cudaStream_t s);
 void finalize_tallies(Context& c, int slot_mask, int mode);
 
 }  // namespace gwam

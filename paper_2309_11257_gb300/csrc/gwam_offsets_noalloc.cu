@@ -15,13 +15,6 @@ namespace gwam {
 constexpr int kNoallocScratchInts = 8194;
 static __device__ __align__(256) int g_noalloc_scratch[kNoallocScratchInts];
 
-__global__ void k_cell_histogram(const int32_t* __restrict__ cells, int64_t n, int32_t ncell, int* __restrict__ counts,
-                                 int* flag);
-__global__ void k_scan_reduce(const int* __restrict__ in, int64_t n, const int* n_dev, int* __restrict__ bsum);
-__global__ void k_scan_blocks(int* bsum, int nb);
-__global__ void k_scan_apply(const int* in, int* out, int64_t n, const int* n_dev, const int* __restrict__ bsum,
-                             int nb);
-
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -72,34 +65,7 @@ extern "C" int gwam_cell_offsets_noalloc(const int32_t* cells, int64_t n, int32_
     if (cudaMemsetAsync(offsets, 0, sizeof(int32_t) * ((size_t)ncell + 1), s) != cudaSuccess ||
         cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess)
         return GWAM_ECUDA;
-    // each launch reports its own status (cudaLaunchKernel), so an error that the caller's own
-    // earlier work left pending is neither reported as this call's nor cleared by it
-    int64_t n64 = n, ncell64 = ncell;
-    const int* no_dev = nullptr;
-    int* counts = offsets;
-    cudaError_t e = cudaSuccess;
-    if (n > 0) {
-        const int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 4096);
-        void* a[] = {(void*)&cells, (void*)&n64, (void*)&ncell, (void*)&counts, (void*)&flag};
-        e = cudaLaunchKernel((const void*)k_cell_histogram, dim3(blocks), dim3(kThreads), a, 0, s);
-    }
-    const int nb = scan_block_count(ncell64);
-    if (e == cudaSuccess) {
-        void* a[] = {(void*)&counts, (void*)&ncell64, (void*)&no_dev, (void*)&scratch};
-        e = cudaLaunchKernel((const void*)k_scan_reduce, dim3(nb), dim3(kThreads), a, 0, s);
-    }
-    if (e == cudaSuccess) {
-        int nbv = nb;
-        void* a[] = {(void*)&scratch, (void*)&nbv};
-        e = cudaLaunchKernel((const void*)k_scan_blocks, dim3(1), dim3(1024), a, 0, s);
-    }
-    if (e == cudaSuccess) {
-        int nbv = nb;
-        const int* in = counts;
-        const int* bs = scratch;
-        void* a[] = {(void*)&in, (void*)&counts, (void*)&ncell64, (void*)&no_dev, (void*)&bs, (void*)&nbv};
-        e = cudaLaunchKernel((const void*)k_scan_apply, dim3(nb), dim3(kThreads), a, 0, s);
-    }
+    const cudaError_t e = launch_cell_offsets(cells, n, ncell, offsets, scratch, flag, s);
     if (e != cudaSuccess) {
         cudaGetLastError();       // clear this call's own launch error
         cudaStreamSynchronize(s);

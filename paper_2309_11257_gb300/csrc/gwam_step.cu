@@ -17,6 +17,9 @@ namespace gwam {
 
 // ============================================================================ scans
 
+// Three-kernel exclusive scan (block sums, their scan, the blocks) of the offsets entry points
+// (launch_cell_offsets), whose scratch is sized by scan_block_count; the step's own scans are the
+// two-pass part scans below.
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kThreads * kScanItems;
 
@@ -113,16 +116,6 @@ __global__ void k_scan_apply(const int* in, int* out, int64_t n, const int* n_de
 }
 
 int scan_block_count(int64_t n) { return (int)((n + kScanTile - 1) / kScanTile) + 1; }
-
-// The same exclusive scan of n host-known elements with caller-provided block-sum scratch
-// (scan_block_count(n) + 1 ints).
-void scan_with_scratch(const int* in, int* out, int64_t n, int* bsum, cudaStream_t s)
-{
-    const int nb = scan_block_count(n);
-    k_scan_reduce<<<nb, kThreads, 0, s>>>(in, n, nullptr, bsum);
-    k_scan_blocks<<<1, 1024, 0, s>>>(bsum, nb);
-    k_scan_apply<<<nb, kThreads, 0, s>>>(in, out, n, nullptr, bsum, nb);
-}
 
 // The step's scans: two passes over at most two contiguous parts per SM.  k_part_sums sums each
 // part; k_part_scan adds up the sums of the parts before its own and scans its part tile by tile
