@@ -219,16 +219,6 @@ __device__ __forceinline__ void df_acc(float vh, float vl, float wh, float wl, f
     c = __fadd_rn(c, __fadd_rn(err, __fmaf_rn(wh, vl, __fmaf_rn(wl, vh, e))));
 }
 
-__device__ __forceinline__ void accumulate_node_df(const NodeDF* __restrict__ p, DF w, float (&s)[16], float (&c)[16])
-{
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        const float4 a = __ldg(p->q + e);
-        df_acc(a.x, a.y, w.hi, w.lo, s[2 * e], c[2 * e]);
-        df_acc(a.z, a.w, w.hi, w.lo, s[2 * e + 1], c[2 * e + 1]);
-    }
-}
-
 // Trilinear interpolation of the FP64 node values (U, V, N^2, Gamma^2) to (X, Y, Z).
 __device__ __forceinline__ void gather_values_fp64(const Grid& G, const Node* __restrict__ bg, double X, double Y,
                                                    double Z, double v[4])
@@ -834,30 +824,6 @@ __device__ __forceinline__ void make_child(const Grid& G, const double p[NSTATE]
     if (code) wrap_position(G, s);
 }
 
-// physical volume of the ray volume, and the volume of grid cell (j, k)
-__device__ __forceinline__ double ray_volume(const Grid& G, const double s[NSTATE], const Geo& g)
-{
-    return g.hX * s[SEX] * g.hY * s[SEY] * s[SEZ];
-}
-
-__device__ __forceinline__ double cell_volume(const Grid& G, int j, int k)
-{
-    if (G.geometry == 1) {
-        const double rc = G.radius + (k + 0.5) * G.dz;
-        return rc * rc * G.row_cos[j] * G.dX * G.dY * G.dz;
-    }
-    return G.dX * G.dY * G.dz;
-}
-
-// 1 / cell_volume
-__device__ __forceinline__ double inv_cell_volume(const Grid& G, int j, int k)
-{
-    if (G.geometry == 1) {
-        const double ir = G.lev_inv_r[k];
-        return ir * ir * G.row_inv_cos[j] * G.inv_dX * G.inv_dY * G.inv_dz;
-    }
-    return G.inv_dX * G.inv_dY * G.inv_dz;
-}
 
 // Intrinsic properties of a ray volume at its carrier position (saturation, projection, cap).
 struct Intr {
