@@ -535,8 +535,13 @@ __global__ void __launch_bounds__(kThreads) k_materialize32(Grid G, Params P, Ra
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->n_new = n_new;   // the live count k_finalize closes the step with
     const int n_old = ctl->n;
     const long long next = ctl->next_id;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_new; p += gridDim.x * blockDim.x) {
-        const int src = sorted_src[p];
+    const int stride = gridDim.x * blockDim.x;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int src_next = p < n_new ? sorted_src[p] : 0;
+    for (; p < n_new; p += stride) {
+        const int src = src_next;
+        // the next source index loaded a pass ahead (the parent's record load waits on it)
+        if (p + stride < n_new) src_next = sorted_src[p + stride];
         const int i = src >> 2, c = src & 3;
         if (src < 0 || i >= n_old) {
             set_status(ctl, GWAM_ECUDA);
