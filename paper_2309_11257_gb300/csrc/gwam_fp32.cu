@@ -260,15 +260,16 @@ __global__ void k_divergence32(Grid G, int TW, const float* __restrict__ fzl, co
         const int i = i0 + ii;
         if (i >= G.nx) continue;
         const int64_t o = ((int64_t)k * G.ny + j) * G.nx + i;
-        if (du) du[o] = (double)tu[k * TW + ii];
-        if (dv) dv[o] = (double)tv[k * TW + ii];
+        // widened by integer operations (the conversion instruction runs at the FP64 rate)
+        if (du) du[o] = widen(tu[k * TW + ii]);
+        if (dv) dv[o] = widen(tv[k * TW + ii]);
     }
 }
 
 __global__ void k_widen(const float* __restrict__ in, double* __restrict__ out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = (double)in[i];
+        out[i] = widen(in[i]);
 }
 
 // Saturation (Sec. 3c, Eq. turbulent-diffusivity) of the precision form: per carrier cell the
