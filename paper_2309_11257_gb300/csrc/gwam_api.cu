@@ -331,8 +331,12 @@ int gwam_init(gwam_ctx** out, const gwam_grid* grid, const gwam_params* params, 
         }
         c.f32 = params->precision == 1;
         // the precision form's projection (48 registers) gains from eight blocks per SM: 0.275 ->
-        // 0.265 ms on the 512 x 256 sphere; the FP64 form's kernels and the materialise pass do not
+        // 0.265 ms on the 512 x 256 sphere; the FP64 form's kernels and the materialise pass do not.
+        // The FP64 ray step (two resident 256-thread blocks per SM) runs as one wave of blocks:
+        // 0.585-0.592 -> 0.574-0.577 ms on the 256 x 128 sphere; the precision form's is slower so
+        // (0.532 -> 0.553 ms) and keeps four blocks per SM
         if (c.f32) c.lcfg[2] = LaunchCfg{kThreads, c.num_sms * 8};
+        else c.lcfg[0] = LaunchCfg{kThreads, c.num_sms * 2};
         for (int b = 0; b < 2; ++b) {
             if (c.f32) {
                 dalloc(c, c.ray32_mem[b], 4 * nr);
