@@ -54,14 +54,10 @@ void convert_background32(Context& c, int member)
 // smoothing the fields are narrowed once by k_narrow.  du/dt, dv/dt are widened to the caller's
 // FP64 on the way out.
 
-template <typename T>
 struct FieldSet32 {
-    const T* in[NFIELD];
+    const double* in[NFIELD];
     float* out[NFIELD];
 };
-
-__device__ __forceinline__ float to_f32(float x) { return x; }
-__device__ __forceinline__ float to_f32(double x) { return narrow(x); }
 
 // separable 1-2-1 x 1-2-1 smoothing (periodic in lambda, edge row reused at the poles).  A warp
 // owns 32 consecutive levels of kRows32 rows over a run of kSpan columns and slides a 3 x 3 window
@@ -73,8 +69,7 @@ __device__ __forceinline__ float to_f32(double x) { return narrow(x); }
 // level group, span).
 constexpr int kSpan = 32;
 constexpr int kRows32 = 3;
-template <typename T>
-__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32<T> fs, int f0, int nf)
+__global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32 fs, int f0, int nf)
 {
     const int lane = threadIdx.x & 31;
     const int nlg = (G.nz + 1 + 31) / 32;                   // level groups (interface fields have nz + 1)
@@ -99,9 +94,9 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32<T> f
     const int j0 = rg * kRows32;
     const int nrow = min(kRows32, G.ny - j0);
     const int64_t base = (int64_t)mem * G.ncol;
-    const T* __restrict__ F = fs.in[f];
+    const double* __restrict__ F = fs.in[f];
     // source rows j0 - 1 .. j0 + kRows32 (clamped at the poles, wrapped on the f-plane)
-    const T* src[kRows32 + 2];
+    const double* src[kRows32 + 2];
 #pragma unroll
     for (int q = 0; q < kRows32 + 2; ++q) {
         int jj = j0 - 1 + q;
@@ -112,20 +107,20 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32<T> f
     float* O = fs.out[f] + (base + (int64_t)j0 * G.nx) * nlev + lev;
     const int64_t orow = (int64_t)G.nx * nlev;
     // vertical 1-2-1 column sums of the kRows32 rows at column i
-    auto loadcol = [&](int i, T (&raw)[kRows32 + 2]) {
+    auto loadcol = [&](int i, double (&raw)[kRows32 + 2]) {
         const int64_t o = (int64_t)i * nlev;
 #pragma unroll
-        for (int q = 0; q < kRows32 + 2; ++q) raw[q] = live ? __ldg(src[q] + o) : T(0);
+        for (int q = 0; q < kRows32 + 2; ++q) raw[q] = live ? __ldg(src[q] + o) : 0.0;
     };
-    auto sums = [&](const T (&raw)[kRows32 + 2], float (&cs)[kRows32]) {
+    auto sums = [&](const double (&raw)[kRows32 + 2], float (&cs)[kRows32]) {
         float v[kRows32 + 2];
 #pragma unroll
-        for (int q = 0; q < kRows32 + 2; ++q) v[q] = to_f32(raw[q]);
+        for (int q = 0; q < kRows32 + 2; ++q) v[q] = narrow(raw[q]);
 #pragma unroll
         for (int q = 0; q < kRows32; ++q) cs[q] = v[q] + 2.0f * v[q + 1] + v[q + 2];
     };
     auto colsums = [&](int i, float (&cs)[kRows32]) {
-        T raw[kRows32 + 2];
+        double raw[kRows32 + 2];
         loadcol(i, raw);
         sums(raw, cs);
     };
@@ -137,7 +132,7 @@ __global__ void __launch_bounds__(256) k_smooth_fields32(Grid G, FieldSet32<T> f
     // two columns per pass with their loads issued together
     for (; i + 2 <= i1; i += 2) {
         {
-            T ra[kRows32 + 2], rb[kRows32 + 2];
+            double ra[kRows32 + 2], rb[kRows32 + 2];
             loadcol(i + 1 == G.nx ? 0 : i + 1, ra);
             loadcol(i + 2 >= G.nx ? i + 2 - G.nx : i + 2, rb);
             sums(ra, cp);
@@ -321,7 +316,7 @@ static void narrow_fields(Context& c, int f0, int f1)
 // the projected FP64 fields f0 .. f1-1, smoothed into their FP32 copies
 static void smooth32(Context& c, int f0, int f1)
 {
-    FieldSet32<double> fs{};
+    FieldSet32 fs{};
     for (int f = 0; f < NFIELD; ++f) {
         fs.in[f] = c.field[f];
         fs.out[f] = c.sm32[f];
