@@ -777,7 +777,8 @@ def main():
     ap.add_argument("--lead-in", type=int, default=-1,
                     help="untimed steps after the launch before the warm-up (default: half of the 200-step run)")
     ap.add_argument("--e2e-steps", type=int, default=50, help="steps of the end-to-end measurement")
-    ap.add_argument("--cpu-steps", type=int, default=4, help="oracle steps of the CPU baseline sample")
+    ap.add_argument("--cpu-steps", type=int, default=24,
+                    help="oracle steps of the CPU baseline sample (about 10 s on 16 host cores)")
     ap.add_argument("--train-steps", type=int, default=1500,
                     help="surrogate workload: at most this many training steps (early stopping; 0: untrained "
                          "weights, throughput only)")
