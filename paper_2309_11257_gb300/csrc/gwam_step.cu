@@ -1042,7 +1042,9 @@ void run_step(Context& c, double dt, double* du, double* dv)
     const Params& P = c.P;
     cudaStream_t s = c.stream;
     const int nb = c.grid_blocks;
-    const int cell_blocks = (int)std::min<int64_t>((G.ncell_all + kThreads - 1) / kThreads, 65535LL * 4);
+    // the cap's column pass: a thread per column (a grid sized by cells launched ~46 K mostly idle
+    // blocks on the 512 x 256 x 90 grid: 26 us a step)
+    const int col_blocks = (int)std::min<int64_t>((G.ncol_all + kThreads - 1) / kThreads, 65535LL * 4);
     const LaunchCfg& la = c.lcfg[0];
     const LaunchCfg& lm = c.lcfg[1];
     const LaunchCfg& lp = c.lcfg[2];
@@ -1061,7 +1063,7 @@ void run_step(Context& c, double dt, double* du, double* dv)
     int mask = (1 << T_EXIT) | (1 << T_INVALID) | (1 << T_SAT) | (1 << T_TOTAL);
     const int* off2 = c.off;
     if (P.cap > 0) {
-        k_cap_find<<<cell_blocks, kThreads, 0, s>>>(G, P, c.ctl, c.off, c.overlist);
+        k_cap_find<<<col_blocks, kThreads, 0, s>>>(G, P, c.ctl, c.off, c.overlist);
         k_cap_apply<<<nb, kThreads, 0, s>>>(G, P, c.A, c.bgdf, c.ctl, c.info, c.off, c.overlist, c.ent_id, c.ent_src,
                                             c.ecap, c.cnt, c.partials, c.max_blocks);
         exclusive_scan(c, c.cnt, c.off2, G.ncell_all, nullptr);
