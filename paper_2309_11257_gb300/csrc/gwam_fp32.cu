@@ -771,8 +771,10 @@ void run_step32(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation) {
-        k_sat_heads<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.biglist);
-        k_sat_kappa32<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj,
+        // both saturation passes on the largest grid (eight blocks per SM, all resident): shorter
+        // chains of per-block passes (saturation 0.070 -> 0.060 ms on the 512 x 256 sphere)
+        k_sat_heads<<<c.max_blocks, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.biglist);
+        k_sat_kappa32<<<c.max_blocks, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj,
                                               reinterpret_cast<const float*>(c.k2), (float)dt,
                                               reinterpret_cast<float*>(c.kappa));
     }

@@ -1077,8 +1077,10 @@ void run_step(Context& c, double dt, double* du, double* dv)
     tune_mark(c, 3);
     prof_mark(c, 2);
     if (P.saturation) {
-        k_sat_heads<<<nb, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.biglist);
-        k_sat_kappa<<<nb, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj, c.k2, dt, c.kappa);
+        // both saturation passes on the largest grid (eight blocks per SM, all resident): shorter
+        // chains of per-block passes (saturation 0.070 -> 0.060 ms on the 512 x 256 sphere)
+        k_sat_heads<<<c.max_blocks, kThreads, 0, s>>>(c.ctl, off2, G.ncell_all, c.raycell, c.biglist);
+        k_sat_kappa<<<c.max_blocks, kThreads, 0, s>>>(c.ctl, off2, c.biglist, c.rho, c.pj, c.k2, dt, c.kappa);
     }
     prof_mark(c, 3);
     // (the projected fields were cleared by k_advance)
