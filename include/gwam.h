@@ -277,7 +277,9 @@ int gwam_load(gwam_ctx *ctx, const char *path);
  * (a cudaStream_t, NULL = legacy default stream) and the call synchronises it.  The call allocates
  * its block-sum scratch (stream-ordered) and frees it before returning.  Errors: GWAM_EINVAL for
  * bad sizes or null pointers, or when a cell lies outside [0, ncell) (such entries are not
- * counted); GWAM_ENOMEM; GWAM_ECUDA. */
+ * counted); GWAM_ENOMEM; GWAM_ECUDA when one of its own launches, copies or the stream fails (each
+ * launch is checked by its own status: an error left pending by the caller's earlier work is
+ * neither reported as this call's nor cleared). */
 int gwam_cell_offsets(const int32_t *cells, int64_t n, int32_t ncell, int32_t *offsets, void *stream);
 
 /* gwam_cell_offsets for callers that cannot allocate device memory.  (The paper has no counterpart:
