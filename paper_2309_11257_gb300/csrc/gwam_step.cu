@@ -8,7 +8,7 @@
 //
 // Kernels read the live count from device memory, so a whole step is enqueued without a
 // host synchronisation.  Ray kernels run a fixed persistent grid so that the per-block FP64
-// partial sums, folded in block order, are deterministic.
+// partial sums, folded in a fixed order, are deterministic.
 #include <algorithm>
 
 #include "gwam_common.cuh"
